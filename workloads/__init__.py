@@ -1,0 +1,119 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle runs.
+
+This module only builds inputs (factor matrices, right-hand sides, tensors); it
+holds none of the regression method's arithmetic (no leverage scores, sampling,
+sampled products, preconditioning or iteration). Random numbers the method itself
+draws are not made here: both implementations derive them from (seed, call id).
+
+Recipes (all float64 generation with numpy's PCG64 ``default_rng(seed)``, cast to
+float32 for the device):
+
+* ``kron_problem``: N factors I_n x R_n. ``dist='gauss'``: i.i.d. N(0,1);
+  ``'lognormal_rows'``: each row scaled by exp(z), z ~ N(0, sigma^2) (skewed leverage);
+  ``'outliers'``: Gaussian with a seeded 10% of rows scaled by 20 (high-leverage rows);
+  ``'paper_e1'``: entries N(1, 0.001) read as mean 1, standard deviation sqrt(0.001).
+  Right-hand side: ``b = K x_true + noise`` with x_true ~ N(0,1)^R, noise Gaussian,
+  either absolute (``noise_abs``) or scaled to ``noise_rel * ||K x_true||``; or a
+  rank-(r,...,r) Tucker tensor plus relative noise (``b_kind='tucker'``); or all ones.
+* ``tucker_tensor``: X = G x_1 Q1 ... x_N QN + noise, G ~ N(0,1)^{R}, Qn orthonormal
+  (QR of a Gaussian), noise scaled to ``noise_rel * ||signal||``.
+* ``batched_shapes``: per-problem I_n ~ U{lo..hi}, R_n ~ U{rlo..rhi}.
+"""
+import numpy as np
+
+
+def _signal_from_core(core, factors):
+    """Multiply a dense core by one matrix per mode (builds a structured signal)."""
+    T = core
+    for n, F in enumerate(factors):
+        T = np.moveaxis(np.tensordot(F, T, axes=([1], [n])), 0, n)
+    return T
+
+
+def make_factors(I, R, dist="gauss", seed=0, sigma=1.0, outlier_frac=0.1, outlier_scale=20.0):
+    rng = np.random.default_rng(seed)
+    As = []
+    for In, Rn in zip(I, R):
+        if dist == "paper_e1":
+            A = rng.normal(1.0, np.sqrt(1e-3), size=(In, Rn))
+        else:
+            A = rng.standard_normal((In, Rn))
+        if dist == "lognormal_rows":
+            A = A * np.exp(sigma * rng.standard_normal(In))[:, None]
+        elif dist == "outliers":
+            k = max(1, int(round(outlier_frac * In)))
+            rows = rng.choice(In, size=k, replace=False)
+            A[rows] *= outlier_scale
+        As.append(A)
+    return As
+
+
+def kron_problem(I, R, dist="gauss", seed=0, noise_abs=None, noise_rel=None, b_kind="kron",
+                 tucker_rank=None, sigma=1.0):
+    """Returns dict(As=[float64 I_n x R_n], b=float64 (prod I), x_true or None)."""
+    I = [int(v) for v in I]
+    R = [int(v) for v in R]
+    As = make_factors(I, R, dist=dist, seed=seed, sigma=sigma)
+    rng = np.random.default_rng(seed + 1000003)
+    x_true = None
+    if b_kind == "ones":
+        b = np.ones(int(np.prod(I)))
+    else:
+        if b_kind == "kron":
+            x_true = rng.standard_normal(int(np.prod(R)))
+            sig = _signal_from_core(x_true.reshape(R), As)
+        elif b_kind == "tucker":
+            r = tucker_rank or R
+            core = rng.standard_normal(tuple(r))
+            facs = [rng.standard_normal((In, rn)) for In, rn in zip(I, r)]
+            sig = _signal_from_core(core, facs)
+        else:
+            raise ValueError(b_kind)
+        sig = sig.reshape(-1)
+        noise = rng.standard_normal(sig.shape[0])
+        if noise_abs is not None:
+            noise *= noise_abs
+        elif noise_rel is not None:
+            noise *= noise_rel * np.linalg.norm(sig) / np.linalg.norm(noise)
+        else:
+            noise[:] = 0.0
+        b = sig + noise
+    return dict(As=As, b=b, x_true=x_true, I=I, R=R)
+
+
+def tucker_tensor(I, R, seed=0, noise_rel=0.01):
+    """Synthetic Tucker tensor: Gaussian core, orthonormal factors, relative noise."""
+    rng = np.random.default_rng(seed)
+    core = rng.standard_normal(tuple(R))
+    Qs = []
+    for In, Rn in zip(I, R):
+        Q, _ = np.linalg.qr(rng.standard_normal((In, Rn)))
+        Qs.append(Q)
+    X = _signal_from_core(core, Qs)
+    noise = rng.standard_normal(X.shape)
+    noise *= noise_rel * np.linalg.norm(X) / np.linalg.norm(noise)
+    return dict(X=X + noise, core=core, Qs=Qs)
+
+
+def tucker_init(I, R, seed=0):
+    """Initial factors: Q factor of a seeded Gaussian I_n x R_n per mode."""
+    rng = np.random.default_rng(seed)
+    return [np.linalg.qr(rng.standard_normal((In, Rn)))[0] for In, Rn in zip(I, R)]
+
+
+def batched_shapes(nprob=64, N=3, ilo=64, ihi=1024, rlo=4, rhi=32, seed=2209):
+    rng = np.random.default_rng(seed)
+    I = rng.integers(ilo, ihi + 1, size=(nprob, N))
+    R = rng.integers(rlo, rhi + 1, size=(nprob, N))
+    return [(list(map(int, i)), list(map(int, r))) for i, r in zip(I, R)]
+
+
+# Named workloads (sizes of the paper-shaped synthetic configurations).
+CONFIGS = {
+    "kron_n2_256x16": dict(I=[256, 256], R=[16, 16], dist="gauss", noise_abs=0.01, eps=0.1, lam=0.0),
+    "kron_n3_512x32_lognormal": dict(I=[512, 512, 512], R=[32, 32, 32], dist="lognormal_rows",
+                                     noise_rel=0.05, eps=0.1, lam=0.0),
+    "kron_n3_1024x64_outliers": dict(I=[1024, 1024, 1024], R=[64, 64, 64], dist="outliers",
+                                     noise_rel=0.01, eps=0.05, lam=0.0, b_kind="tucker",
+                                     tucker_rank=[64, 64, 64]),
+}
