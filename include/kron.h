@@ -1,0 +1,243 @@
+/*
+ * kron.h - C ABI of the GB300 (sm_103a) Kronecker-regression library.
+ *
+ * The library computes the hot path of FastKroneckerRegression (Alg. 2 of
+ * "Subquadratic Kronecker Regression with Applications to Tensor Decomposition"):
+ * leverage-score row sampling of K = A(1) (x) ... (x) A(N) followed by Richardson
+ * iteration on the sampled system, preconditioned by the unsampled normal matrix;
+ * and its block-design extension FastFactorMatrixUpdate (Alg. 3) inside TuckerALS
+ * (Alg. 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Layout: row-major matrices, C-order tensors (last index fastest). Row
+ *    (i1..iN) of K is b[((i1*I2 + i2)*I3 + ...)*IN + iN]; the unknown x and the
+ *    Tucker core G are indexed the same way over (r1..rN). This is the ordering
+ *    under which K = A(1) (x) ... (x) A(N) multiplies vec(X) in Alg. 1.
+ *  - Pointers are DEVICE pointers owned by the caller unless a comment says "host".
+ *    (kr_opts.host_io = 1 switches the factor, right-hand-side and solution
+ *    pointers of the solver entry points to host memory; the library then copies
+ *    them in and out inside the call.)
+ *  - Every call is enqueued on the context's stream and returns when its outputs
+ *    are complete (the call synchronises the stream before returning).
+ *  - Errors: a kr_status code; kr_last_error() gives a message. Nothing is thrown
+ *    across the ABI. Device-side problems (non-finite values, divergence) are
+ *    reported through status codes, never by trapping the GPU.
+ *  - Limits: 1 <= N <= KR_MAX_MODES, 1 <= R_n <= I_n, R_n <= 64, I_n <= 65535,
+ *    prod(I_n) < 2^32, number of draws s < 2^31.
+ */
+#ifndef KRON_H
+#define KRON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define KR_API __attribute__((visibility("default")))
+#else
+#define KR_API
+#endif
+
+#define KR_MAX_MODES 8
+#define KR_MAX_RANK 64
+
+typedef enum {
+  KR_OK = 0,
+  KR_EINVAL = 1,      /* invalid argument (shape, range, null pointer) */
+  KR_ENOMEM = 2,      /* device allocation failed */
+  KR_ECUDA = 3,       /* a CUDA runtime call failed */
+  KR_ENONFINITE = 4,  /* NaN/Inf met in an input or an iterate */
+  KR_ERANK = 5,       /* a factor matrix is numerically rank deficient */
+  KR_ENOTCONV = 6,    /* max_iter reached before the stopping rule held */
+  KR_EDIVERGED = 7,   /* the Richardson step grew 3 times in a row */
+  KR_ETIMEOUT = 8,    /* a bounded device wait ran out */
+  KR_ENOTIMPL = 9     /* shape outside what this build supports */
+} kr_status;
+
+typedef struct kr_ctx kr_ctx;
+typedef struct kr_sketch kr_sketch;
+
+/* N factor matrices A[n] of shape I[n] x R[n] (row-major, FP32). */
+typedef struct {
+  int32_t N;
+  int64_t I[KR_MAX_MODES];
+  int32_t R[KR_MAX_MODES];
+  const float* A[KR_MAX_MODES];
+} kr_factors;
+
+/* Options of the solvers (zero-initialise, then set what is needed). */
+typedef struct {
+  double eps;            /* approximation parameter, 0 < eps < 1 (Alg. 2 input) */
+  double delta;          /* failure probability (recorded; the default sample count does not use it) */
+  double lambda;         /* L2 regularisation (kron_ridge, tucker_als_sweep); >= 0 */
+  double sample_scale;   /* c in s = ceil(c * R * ln(R) / eps); <= 0 selects 4 */
+  int64_t num_samples;   /* > 0 overrides the sample count s */
+  int32_t max_iter;      /* Richardson iteration cap; <= 0 selects 100 */
+  double tol;            /* stop when ||step|| <= tol * ||x||; <= 0 selects 1e-7 */
+  double step;           /* Richardson step; <= 0 selects the paper's 1 - sqrt(eps) */
+  int32_t precision;     /* 0: FP32 contractions. 1: BF16 tensor-core inner sweeps with FP32 refinement */
+  int32_t host_io;       /* 1: factors, b / X and x / A / G are host pointers */
+  uint64_t seed;         /* Philox key */
+  uint64_t call_id;      /* Philox counter word 3 (distinguishes sketches drawn with one seed) */
+} kr_opts;
+
+/* Host-side report filled by the solvers (may be NULL). */
+typedef struct {
+  int32_t iters;             /* Richardson iterations taken (last problem / last step) */
+  int32_t converged;         /* 1: ||step|| <= tol ||x||; 2: stalled at the FP32 rounding floor
+                                (no new minimum step for 8 iterations, smallest relative step
+                                within 100 tol); 0: not converged */
+  int64_t s;                 /* draws */
+  int64_t distinct;          /* distinct sampled rows */
+  double obj_sampled;        /* ||S(Kx - b)||^2 + lambda ||x||^2 at the returned x, FP64 accumulation */
+  double rel_update;         /* last ||step|| / ||x|| */
+  float t_ms[8];             /* leverage, sample, group+gather, rhs, iterate, final check, copies, total */
+} kr_report;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context bound to the current CUDA device and the given stream
+ * (cudaStream_t, may be NULL for the legacy default stream). The context owns its
+ * workspace, which grows on demand and is freed by kr_destroy. */
+KR_API kr_status kr_create(kr_ctx** ctx, void* cuda_stream);
+KR_API void kr_destroy(kr_ctx* ctx);
+KR_API kr_status kr_set_stream(kr_ctx* ctx, void* cuda_stream);
+/* Message of the last failed call on this context (static storage, valid until
+ * the next call on the context). */
+KR_API const char* kr_last_error(const kr_ctx* ctx);
+/* Number of kernels this context has launched so far (instrumentation). */
+KR_API int64_t kr_launch_count(const kr_ctx* ctx);
+
+/* Per-kernel timing (instrumentation, off by default). When enabled, the library
+ * records a CUDA event pair on its stream around every launch of the kernel kinds
+ * below; kr_timing_read synchronises the stream and returns, for one kind, the summed
+ * event time (ms) and the number of launches since the last reset. */
+enum {
+  KR_K_RESID = 0,      /* sampled residual + transpose accumulation (a7 + a8) */
+  KR_K_MODEPROD = 1,   /* mode-n products (KronMatMul, preconditioner) */
+  KR_K_SAMPLE = 2,     /* Philox sampling + cell histogram (a3) */
+  KR_K_SCATTER = 3,    /* counting-sort scatter (a4) */
+  KR_K_DEDUP = 4,      /* per-cell merge + gather of b (a4 + a5) */
+  KR_K_TABLES = 5,     /* Gram, Cholesky, leverage, CDF, eigen (a1 + a2) */
+  KR_K_VECTOR = 6,     /* Richardson update, reductions (a10) */
+  KR_K_KINDS = 7
+};
+KR_API kr_status kr_timing_enable(kr_ctx* ctx, int32_t on);
+KR_API kr_status kr_timing_read(kr_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
+KR_API kr_status kr_timing_reset(kr_ctx* ctx);
+
+/* ---------------------------------------------------------------- a1 + a2 */
+
+/* Statistical leverage scores and sampling tables of each factor
+ * (§3 eq. ridge leverage via SVD at lambda = 0; Lemma 4.1: the scores of K are the
+ * products of these; proof of Thm 4.5: one CDF per factor).
+ *  lev[n]  (device, I[n] doubles, may be NULL): l_i = a_i^T (A^T A)^-1 a_i, computed
+ *          from an FP64 Gram matrix and its FP64 Cholesky factor.
+ *  cdf[n]  (device, I[n] doubles, may be NULL): cdf[i] = fl(prefix_i / total),
+ *          left-to-right FP64 prefix; entries from the last positive-mass row on are 1.0.
+ *  prob[n] (device, I[n] doubles, may be NULL): l_i / total.
+ *  rank    (host, N ints, may be NULL): numerical rank of each factor
+ *          (= R[n] unless a Cholesky pivot falls below R * 2^-52 * max diagonal).
+ * Returns KR_ERANK if a factor is rank deficient (outputs for that factor undefined). */
+KR_API kr_status kron_leverage(kr_ctx* ctx, const kr_factors* f, double* const lev[],
+                        double* const cdf[], double* const prob[], int32_t* rank);
+
+/* ---------------------------------------------------------------- a3 */
+
+/* SampleRows on K from the product distribution (§3 Def. of leverage score
+ * sampling; Alg. 2 line "S <- RowSampling(K, s, P)"; coordinates drawn
+ * independently per factor, proof of Thm 4.5).
+ * Draw t, coordinate m (position in this call's mode list) uses the uniform
+ * u = (((wa << 32) | wb) >> 11) * 2^-53 from Philox4x32-10 (Salmon et al. 2011) with
+ * key (seed lo, seed hi) and counter (t lo, t hi, (m / 2) + 256 * row, call_id lo),
+ * words (w0, w1) for even m and (w2, w3) for odd m; the index is the smallest i
+ * with u < cdf[m][i] (bit-exact against any implementation of the same rule).
+ *  N, I   : number of modes in the list and their sizes (I is host).
+ *  cdf[m] : device tables as produced by kron_leverage.
+ *  prob[m]: device probabilities (needed only when w != NULL).
+ *  idx    : device s x N int32 (row t = draw t), may be NULL.
+ *  w      : device s floats, w_t = 1 / sqrt(s * prod_m prob[m][idx[t][m]]), may be NULL. */
+KR_API kr_status kron_sample(kr_ctx* ctx, int32_t N, const int64_t* I, const double* const cdf[],
+                      const double* const prob[], int64_t s, uint64_t seed, uint64_t call_id,
+                      int32_t row, int32_t* idx, float* w);
+
+/* ---------------------------------------------------------------- a3 + a4 + a5 */
+
+/* Draw s rows of K (as kron_sample) and group them (Thm 4.4 proof: the support of S
+ * split into cells = (i_1..i_{N-1}) and the last coordinate i_N), merging repeated
+ * rows into a multiplicity c_j with weight omega_j = c_j / (s prod_n p_n(i_n))
+ * (the same sketched objective as c_j rows of weight 1/(s p)); gather
+ * b~_j = b[key_j] (Alg. 2, "b~ = S b" up to the factor sqrt(omega_j)).
+ * b (device, prod I floats) may be NULL (no gather). The sketch lives in device
+ * memory owned by the returned handle; free it with kron_sketch_free. */
+KR_API kr_status kron_sketch(kr_ctx* ctx, const kr_factors* f, const double* const cdf[],
+                      const double* const prob[], const float* b, int64_t s, uint64_t seed,
+                      uint64_t call_id, int32_t row, kr_sketch** out);
+/* Number of distinct rows of a sketch. */
+KR_API int64_t kron_sketch_distinct(const kr_sketch* sk);
+/* Copy the sketch out in increasing linear-row order (device outputs; any may be NULL):
+ * keys (int64 linear row index), counts (int32), omega (float), btilde (float). */
+KR_API kr_status kron_sketch_export(kr_ctx* ctx, const kr_sketch* sk, int64_t* keys, int32_t* counts,
+                             float* omega, float* btilde);
+/* g = K~^T Omega (b~ - K~ x) for the sketch's rows (Thm 4.4 sampled products, Alg. 2
+ * Richardson gradient without the lambda term); obj (host, may be NULL) receives
+ * sum_j omega_j (b~_j - (Kx)_j)^2 accumulated in FP64. x, g: device R floats. */
+KR_API kr_status kron_sketch_residual(kr_ctx* ctx, const kr_sketch* sk, const kr_factors* f,
+                               const float* x, float* g, double* obj);
+KR_API void kron_sketch_free(kr_sketch* sk);
+
+/* ---------------------------------------------------------------- a7/a8 building block, a9 */
+
+/* KronMatMul (Lemma 4.3): y = (B(1) (x) ... (x) B(N)) x for matrices B(n) of shape
+ * J[n] x K[n] (row-major; trans[n] = 1 means the stored array is K[n] x J[n] and its
+ * transpose is used). x: prod K floats, y: prod J floats (device). */
+KR_API kr_status kron_matmul(kr_ctx* ctx, int32_t N, const int64_t* J, const int64_t* K,
+                      const float* const B[], const int32_t* trans, const float* x, float* y);
+
+/* Preconditioner of Alg. 2: d = M^+ g with M^+ = (V1 (x)...(x) VN) D (V1 (x)...(x) VN)^T,
+ * D = (S1^2 (x)...(x) SN^2 + lambda I)^+ (for lambda = 0: (A1^T A1)^-1 (x) ... (x) (AN^T AN)^-1
+ * from FP64 Cholesky inverses). g, d: device R floats. */
+KR_API kr_status kron_precond(kr_ctx* ctx, const kr_factors* f, double lambda, const float* g, float* d);
+
+/* Full objective ||Kx - b||^2 + lambda ||x||^2 (Thm 4.5's guarantee), FP64 accumulation
+ * over all prod I rows; result on the host. */
+KR_API kr_status kron_objective(kr_ctx* ctx, const kr_factors* f, const float* b, const float* x,
+                         double lambda, double* obj);
+
+/* ---------------------------------------------------------------- solvers */
+
+/* Alg. 2 FastKroneckerRegression with lambda = 0 (opts->lambda is ignored):
+ * x ~ argmin ||Kx - b||^2 over x in R^{R_1...R_N}. b: prod I floats; x: prod R floats
+ * (output; the iteration starts from 0). Returns KR_ENOTCONV (with x written) if
+ * max_iter is reached. */
+KR_API kr_status kron_regress(kr_ctx* ctx, const kr_factors* f, const float* b, const kr_opts* opts,
+                       float* x, kr_report* report);
+
+/* Alg. 2 with lambda = opts->lambda > 0 (ridge; sampling by statistical scores, the
+ * sqrt(lambda) I block is never sampled, Cor. 3.3 / Lemma 3.2). */
+KR_API kr_status kron_ridge(kr_ctx* ctx, const kr_factors* f, const float* b, const kr_opts* opts,
+                     float* x, kr_report* report);
+
+/* nprob independent ridge problems (host arrays of descriptors and pointers); each
+ * uses opts with call_id + problem index. reports: host array of nprob (may be NULL). */
+KR_API kr_status kron_ridge_batched(kr_ctx* ctx, int32_t nprob, const kr_factors* probs,
+                             const float* const b[], const kr_opts* opts, float* const x[],
+                             kr_report* reports);
+
+/* TuckerALS (Alg. 1) with sampled factor updates (Alg. 3, fresh sketch per factor row,
+ * Woodbury preconditioner) and sampled core updates (Alg. 2 with b = vec X).
+ * X: prod I floats; A[n]: I[n] x R[n] floats (in/out); G: prod R floats (in/out).
+ * Sweep k, step n (0..N-1 factor steps, N core step) draws with call id
+ * opts->call_id + k*(N+1) + n; factor row i uses counter row i. */
+KR_API kr_status tucker_als_sweep(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R,
+                           const float* X, float* const A[], float* G, const kr_opts* opts,
+                           int32_t sweeps, kr_report* report);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KRON_H */

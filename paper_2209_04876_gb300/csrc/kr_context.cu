@@ -1,0 +1,198 @@
+// Context, errors, workspace and argument validation of libkron.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include "kr_internal.cuh"
+
+kr_status kr_fail(kr_ctx* ctx, kr_status st, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return st;
+}
+
+kr_status kr_fail_cuda(kr_ctx* ctx, cudaError_t e, const char* what, const char* file, int line) {
+  kr_status st = (e == cudaErrorMemoryAllocation) ? KR_ENOMEM : KR_ECUDA;
+  return kr_fail(ctx, st, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+extern "C" kr_status kr_create(kr_ctx** out, void* stream) {
+  if (!out) return KR_EINVAL;
+  *out = nullptr;
+  kr_ctx* ctx = new kr_ctx();
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  int optin = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  ctx->smem_optin = (size_t)optin;
+  for (int i = 0; i < 10 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return e == cudaErrorMemoryAllocation ? KR_ENOMEM : KR_ECUDA;
+  }
+  ctx->stream = (cudaStream_t)stream;
+  *out = ctx;
+  return KR_OK;
+}
+
+extern "C" void kr_destroy(kr_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  for (auto& t : ctx->pending) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (auto e : ctx->pool) cudaEventDestroy(e);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
+  for (int i = 0; i < 10; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  delete ctx;
+}
+
+extern "C" kr_status kr_set_stream(kr_ctx* ctx, void* stream) {
+  if (!ctx) return KR_EINVAL;
+  ctx->stream = (cudaStream_t)stream;
+  return KR_OK;
+}
+
+extern "C" const char* kr_last_error(const kr_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" int64_t kr_launch_count(const kr_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+kr_status kr_ws_reserve(kr_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_size) return KR_OK;
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->ws) {
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_size = 0;
+  }
+  size_t want = bytes + bytes / 8 + (1 << 20);
+  cudaError_t e = cudaMalloc(&ctx->ws, want);
+  if (e != cudaSuccess) {
+    ctx->ws = nullptr;
+    cudaGetLastError();
+    return kr_fail(ctx, KR_ENOMEM, "workspace allocation of %zu bytes failed", want);
+  }
+  ctx->ws_size = want;
+  return KR_OK;
+}
+
+kr_status kr_hbuf_reserve(kr_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->hbuf_size) return KR_OK;
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
+  ctx->hbuf = nullptr;
+  ctx->hbuf_size = 0;
+  KR_CUDA(ctx, cudaMallocHost((void**)&ctx->hbuf, bytes));
+  ctx->hbuf_size = bytes;
+  return KR_OK;
+}
+
+int64_t kr_prod_I(const Modes& m) {
+  int64_t p = 1;
+  for (int n = 0; n < m.N; ++n) p *= m.I[n];
+  return p;
+}
+
+int64_t kr_prod_R(const Modes& m) {
+  int64_t p = 1;
+  for (int n = 0; n < m.N; ++n) p *= m.R[n];
+  return p;
+}
+
+kr_status kr_check_factors(kr_ctx* ctx, const kr_factors* f, Modes* m) {
+  if (!f) return kr_fail(ctx, KR_EINVAL, "factors: null descriptor");
+  if (f->N < 1 || f->N > KR_MAX_MODES) return kr_fail(ctx, KR_EINVAL, "factors: N=%d outside [1,%d]", f->N, KR_MAX_MODES);
+  m->N = f->N;
+  int64_t prodI = 1;
+  for (int n = 0; n < f->N; ++n) {
+    if (f->I[n] < 1 || f->I[n] > 65535)
+      return kr_fail(ctx, KR_EINVAL, "factors: I[%d]=%lld outside [1,65535]", n, (long long)f->I[n]);
+    if (f->R[n] < 1 || f->R[n] > KR_MAX_RANK)
+      return kr_fail(ctx, KR_EINVAL, "factors: R[%d]=%d outside [1,%d]", n, f->R[n], KR_MAX_RANK);
+    if (f->R[n] > f->I[n])
+      return kr_fail(ctx, KR_EINVAL, "factors: R[%d]=%d exceeds I[%d]=%lld", n, f->R[n], n, (long long)f->I[n]);
+    if (!f->A[n]) return kr_fail(ctx, KR_EINVAL, "factors: A[%d] is null", n);
+    m->I[n] = (int)f->I[n];
+    m->R[n] = f->R[n];
+    m->A[n] = f->A[n];
+    prodI *= f->I[n];
+  }
+  if (prodI >= (int64_t(1) << 32)) return kr_fail(ctx, KR_EINVAL, "factors: prod(I) >= 2^32");
+  return KR_OK;
+}
+
+// ------------------------------------------------------------------ timing instrumentation
+
+cudaEvent_t kr_timing_event(kr_ctx* ctx) {
+  if (!ctx->pool.empty()) {
+    cudaEvent_t e = ctx->pool.back();
+    ctx->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int kr_kind_of(const char* k) {
+  std::string s(k);
+  if (s.find("k_resid") != std::string::npos) return KR_K_RESID;
+  if (s.find("k_mode_product") != std::string::npos) return KR_K_MODEPROD;
+  if (s.find("k_sample") != std::string::npos) return KR_K_SAMPLE;
+  if (s.find("k_scatter") != std::string::npos) return KR_K_SCATTER;
+  if (s.find("k_dedup") != std::string::npos) return KR_K_DEDUP;
+  if (s.find("k_gram") != std::string::npos || s.find("k_chol") != std::string::npos ||
+      s.find("k_leverage") != std::string::npos || s.find("k_cdf") != std::string::npos ||
+      s.find("k_jacobi") != std::string::npos)
+    return KR_K_TABLES;
+  return KR_K_VECTOR;
+}
+
+static void kr_timing_drain(kr_ctx* ctx) {
+  for (auto& t : ctx->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      ctx->t_ms[t.kind] += ms;
+      ctx->t_n[t.kind] += 1;
+    }
+    ctx->pool.push_back(t.a);
+    ctx->pool.push_back(t.b);
+  }
+  ctx->pending.clear();
+  cudaGetLastError();
+}
+
+extern "C" kr_status kr_timing_enable(kr_ctx* ctx, int32_t on) {
+  if (!ctx) return KR_EINVAL;
+  ctx->timing = on != 0;
+  return KR_OK;
+}
+
+extern "C" kr_status kr_timing_read(kr_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches) {
+  if (!ctx || kind < 0 || kind >= KR_K_KINDS) return KR_EINVAL;
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  kr_timing_drain(ctx);
+  if (total_ms) *total_ms = ctx->t_ms[kind];
+  if (launches) *launches = ctx->t_n[kind];
+  return KR_OK;
+}
+
+extern "C" kr_status kr_timing_reset(kr_ctx* ctx) {
+  if (!ctx) return KR_EINVAL;
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  kr_timing_drain(ctx);
+  for (int k = 0; k < KR_K_KINDS; ++k) {
+    ctx->t_ms[k] = 0.0;
+    ctx->t_n[k] = 0;
+  }
+  return KR_OK;
+}

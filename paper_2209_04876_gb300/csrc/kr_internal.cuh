@@ -1,0 +1,189 @@
+// Internal definitions shared by the translation units of libkron.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/kron.h"
+
+#define KR_WARP 32
+
+// ------------------------------------------------------------------ context
+
+struct kr_ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int64_t launches = 0;
+  // grow-on-demand device workspace
+  char* ws = nullptr;
+  size_t ws_size = 0;
+  // pinned host buffer for small read-backs
+  char* hbuf = nullptr;
+  size_t hbuf_size = 0;
+  cudaEvent_t ev[10] = {};
+  // per-kernel timing (instrumentation)
+  bool timing = false;
+  struct Timed {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Timed> pending;
+  std::vector<cudaEvent_t> pool;
+  double t_ms[KR_K_KINDS] = {};
+  int64_t t_n[KR_K_KINDS] = {};
+};
+
+cudaEvent_t kr_timing_event(kr_ctx* ctx);
+int kr_kind_of(const char* kernel_name);
+
+kr_status kr_fail(kr_ctx* ctx, kr_status st, const char* fmt, ...);
+kr_status kr_fail_cuda(kr_ctx* ctx, cudaError_t e, const char* what, const char* file, int line);
+
+#define KR_TRY(expr)                         \
+  do {                                       \
+    kr_status _st = (expr);                  \
+    if (_st != KR_OK) return _st;            \
+  } while (0)
+
+#define KR_CUDA(ctx, expr)                                                         \
+  do {                                                                             \
+    cudaError_t _e = (expr);                                                       \
+    if (_e != cudaSuccess) return kr_fail_cuda((ctx), _e, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+// Launch and count; checks the launch error. With timing enabled, an event pair
+// brackets the launch on the same stream (kind from the kernel's name).
+#define KR_LAUNCH(ctx, kernel, grid, block, smem, ...)                                   \
+  do {                                                                                   \
+    cudaEvent_t _ea = nullptr, _eb = nullptr;                                            \
+    if ((ctx)->timing) {                                                                 \
+      _ea = kr_timing_event(ctx);                                                        \
+      _eb = kr_timing_event(ctx);                                                        \
+      cudaEventRecord(_ea, (ctx)->stream);                                               \
+    }                                                                                    \
+    kernel<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);                     \
+    (ctx)->launches++;                                                                   \
+    cudaError_t _e = cudaGetLastError();                                                 \
+    if (_e != cudaSuccess) return kr_fail_cuda((ctx), _e, #kernel, __FILE__, __LINE__);  \
+    if ((ctx)->timing) {                                                                 \
+      cudaEventRecord(_eb, (ctx)->stream);                                               \
+      (ctx)->pending.push_back({kr_kind_of(#kernel), _ea, _eb});                         \
+    }                                                                                    \
+  } while (0)
+
+// Ensures the workspace holds at least `bytes` (synchronises when it grows).
+kr_status kr_ws_reserve(kr_ctx* ctx, size_t bytes);
+kr_status kr_hbuf_reserve(kr_ctx* ctx, size_t bytes);
+
+// Bump allocator over a reserved region.
+struct Carve {
+  char* base;
+  size_t cap;
+  size_t off = 0;
+  Carve(char* b, size_t c) : base(b), cap(c) {}
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+// Size accounting twin of Carve.
+struct Need {
+  size_t off = 0;
+  template <class T>
+  void add(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    off += count * sizeof(T);
+  }
+};
+
+// ------------------------------------------------------------------ shapes
+
+struct Modes {
+  int N;
+  int I[KR_MAX_MODES];
+  int R[KR_MAX_MODES];
+  const float* A[KR_MAX_MODES];
+};
+
+kr_status kr_check_factors(kr_ctx* ctx, const kr_factors* f, Modes* m);
+int64_t kr_prod_I(const Modes& m);
+int64_t kr_prod_R(const Modes& m);
+
+// Per-mode device tables derived from the factors (a1 + a2).
+struct FactorTables {
+  int N = 0;
+  int I[KR_MAX_MODES] = {};
+  int R[KR_MAX_MODES] = {};
+  double* lev[KR_MAX_MODES] = {};    // I[n]
+  double* cdf[KR_MAX_MODES] = {};    // I[n]
+  double* prob[KR_MAX_MODES] = {};   // I[n]
+  uint64_t* thr[KR_MAX_MODES] = {};  // I[n]: integer thresholds ceil(cdf * 2^53)
+  float* invp[KR_MAX_MODES] = {};    // I[n]: 1 / p (FP32; 0 for zero-mass rows)
+  float* ginv[KR_MAX_MODES] = {};    // R x R: (A^T A)^-1 (FP32, from FP64 Cholesky)
+  float* V[KR_MAX_MODES] = {};       // R x R: eigenvectors of A^T A (columns, FP32)
+  float* sig2[KR_MAX_MODES] = {};    // R: eigenvalues of A^T A (FP32)
+  double* gram[KR_MAX_MODES] = {};   // R x R FP64
+  int rank[KR_MAX_MODES] = {};
+};
+
+// Computes Gram, Cholesky, leverage scores, CDF, thresholds, inverse probabilities,
+// and (if want_eig) the eigen-decomposition of each factor Gram matrix. Buffers are
+// carved from `cv` (which must be large enough: see kr_tables_need).
+void kr_tables_need(const Modes& m, bool want_eig, Need& nd);
+kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv, FactorTables& t,
+                          bool check_rank = true);
+
+// ------------------------------------------------------------------ mode products
+
+// out[p, j, q] = sum_k B[j, k] * in[p, k, q], B stored J x K (trans = 0) or K x J (trans = 1).
+kr_status kr_mode_product(kr_ctx* ctx, const float* in, float* out, int64_t P, int K, int64_t Q, int J,
+                          const float* B, int trans);
+// KronMatMul along the modes with B[n] != nullptr (identity elsewhere); intermediates
+// in tmp0/tmp1 (each must hold the largest intermediate), result in `out` (may be `in`).
+kr_status kr_kron_apply2(kr_ctx* ctx, int N, const int* dimsIn, const int* dimsOut, const float* const* B,
+                         const int* trans, const float* in, float* out, float* tmp0, float* tmp1);
+// d = M+ g (Alg. 2 preconditioner) from the factor tables; tmp0/tmp1 hold R floats each.
+kr_status kr_precond_apply(kr_ctx* ctx, const FactorTables& t, double lambda, const float* g, float* d, float* tmp0,
+                           float* tmp1);
+
+// ------------------------------------------------------------------ sketch
+
+struct kr_sketch {
+  int N = 0;
+  int I[KR_MAX_MODES] = {};
+  int64_t s = 0;
+  int64_t ncell = 0;   // prod_{n < N-1} I[n]
+  int IT = 0;          // I[N-1]
+  int64_t distinct = 0;
+  // device arrays (owned)
+  uint32_t* cell_start = nullptr;  // ncell
+  uint32_t* cell_nd = nullptr;     // ncell: distinct entries of the cell
+  uint32_t* ent = nullptr;         // s: packed (i_T | count << 16) at cell_start[c] + k
+  float* bt = nullptr;             // s: b~ at the same positions
+  float* cell_w = nullptr;         // ncell: prod_{n<N-1} (1/p_n(i_n)) / s
+  float* invpT = nullptr;          // IT: 1/p_{N-1}(i)
+  char* mem = nullptr;
+};
+
+// Sketch construction: check the shape, set dimensions, account/carve the sketch's own
+// arrays, then fill them (sampling, grouping, merging, gather) using scratch from `cv`.
+kr_status kr_sketch_check(kr_ctx* ctx, const Modes& m, int64_t s);
+void kr_sketch_setup(kr_sketch* sk, const Modes& m, int64_t s);
+void kr_sketch_own_need(const kr_sketch* sk, Need& nd);
+void kr_sketch_layout(kr_sketch* sk, Carve& cv);
+void kr_sketch_scratch_need(int64_t s, int64_t ncell, Need& nd);
+kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, const float* b, uint64_t seed,
+                         uint64_t call_id, int row, kr_sketch* sk, Carve& cv);
+// Residual/gradient pass: W[c, :] = sum_j omega_j (b~_j - <a_T, Y[c]>) a_T; obj partials.
+kr_status kr_sketch_resid(kr_ctx* ctx, const kr_sketch* sk, const float* AT, int RT, const float* Y,
+                          float* W, double* obj_partial, int nblocks);
+int kr_resid_blocks(kr_ctx* ctx);

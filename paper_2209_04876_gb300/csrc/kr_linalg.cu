@@ -1,0 +1,383 @@
+// a1 + a2: factor Gram matrices, Cholesky, leverage scores, sampling tables,
+// eigen-decompositions for the preconditioner.
+//
+// Leverage scores follow §3 (statistical scores l_i = a_i^T (A^T A)^-1 a_i, the
+// lambda = 0 case of the ridge-score definition); the sampling distribution of K
+// is their product (Lemma 4.1) and is drawn one coordinate at a time from one CDF
+// per factor (proof of Thm 4.5). The preconditioner of Alg. 2 needs
+// (A^T A)^-1 per factor when lambda = 0 and the eigen-decomposition
+// A^T A = V S^2 V^T when lambda > 0.
+//
+// Precision: Gram, Cholesky, triangular inverse, scores and CDF in FP64 (exact
+// FP32 x FP32 products, FP64 sums). The eigen-decomposition is FP32 Jacobi: the
+// preconditioner only needs to be a spectral approximation of the normal matrix
+// (Lemma 4.2), so its rounding affects the rate, not the fixed point.
+#include <math.h>
+
+#include "kr_internal.cuh"
+
+namespace {
+
+constexpr int GRAM_ROWS = 16;
+constexpr int MAXR = KR_MAX_RANK;
+constexpr int LD = MAXR + 1;
+
+struct ModePtrs {
+  int N;
+  int I[KR_MAX_MODES];
+  int R[KR_MAX_MODES];
+  const float* A[KR_MAX_MODES];
+  double* part[KR_MAX_MODES];
+  double* gram[KR_MAX_MODES];
+  double* linv[KR_MAX_MODES];
+  double* lev[KR_MAX_MODES];
+  double* cdf[KR_MAX_MODES];
+  double* prob[KR_MAX_MODES];
+  uint64_t* thr[KR_MAX_MODES];
+  float* invp[KR_MAX_MODES];
+  float* ginv[KR_MAX_MODES];
+  float* V[KR_MAX_MODES];
+  float* sig2[KR_MAX_MODES];
+  int* flags;  // per mode: 1 = rank deficient
+};
+
+// Partial Gram over GRAM_ROWS rows per block (upper triangle, FP64 accumulation).
+__global__ void k_gram_partial(ModePtrs mp) {
+  const int n = blockIdx.y;
+  const int I = mp.I[n], R = mp.R[n];
+  const int r0 = blockIdx.x * GRAM_ROWS;
+  if (r0 >= I) return;
+  const int rows = min(GRAM_ROWS, I - r0);
+  __shared__ double a[GRAM_ROWS][LD];
+  const float* A = mp.A[n];
+  for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
+    int rr = e / R, c = e % R;
+    a[rr][c] = (double)A[(int64_t)(r0 + rr) * R + c];
+  }
+  __syncthreads();
+  double* out = mp.part[n] + (int64_t)blockIdx.x * R * R;
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    int i = e / R, j = e % R;
+    if (i > j) continue;
+    double acc = 0.0;
+    for (int rr = 0; rr < rows; ++rr) acc = fma(a[rr][i], a[rr][j], acc);
+    out[e] = acc;
+  }
+}
+
+// Deterministic reduction of the partials (block order), mirrored to full symmetric.
+__global__ void k_gram_reduce(ModePtrs mp) {
+  const int n = blockIdx.x;
+  const int I = mp.I[n], R = mp.R[n];
+  const int nchunk = (I + GRAM_ROWS - 1) / GRAM_ROWS;
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    int i = e / R, j = e % R;
+    if (i > j) continue;
+    double acc = 0.0;
+    for (int c = 0; c < nchunk; ++c) acc += mp.part[n][(int64_t)c * R * R + e];
+    mp.gram[n][i * R + j] = acc;
+    mp.gram[n][j * R + i] = acc;
+  }
+}
+
+// One block per mode: Cholesky G = L L^T (FP64), L^-1, and (A^T A)^-1 in FP32.
+__global__ void k_cholesky(ModePtrs mp) {
+  const int n = blockIdx.x;
+  const int R = mp.R[n];
+  extern __shared__ double sm[];
+  double* L = sm;              // R x LD
+  double* X = sm + MAXR * LD;  // R x LD (L^-1)
+  __shared__ int bad;
+  __shared__ double maxdiag;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < R * R; e += blockDim.x) L[(e / R) * LD + (e % R)] = mp.gram[n][e];
+  if (tid == 0) {
+    bad = 0;
+    double md = 0.0;
+    for (int i = 0; i < R; ++i) md = fmax(md, mp.gram[n][i * R + i]);
+    maxdiag = md;
+  }
+  __syncthreads();
+  const double tol = maxdiag * (double)R * 1e-15;
+  for (int k = 0; k < R; ++k) {
+    __syncthreads();  // trailing update of step k-1 complete
+    double d = L[k * LD + k];
+    __syncthreads();  // every thread has read the pivot before it is overwritten
+    if (!(d > tol)) {  // also catches NaN
+      if (tid == 0) bad = 1;
+      d = 1.0;
+    }
+    double lkk = sqrt(d);
+    if (tid == 0) L[k * LD + k] = lkk;
+    for (int i = k + 1 + tid; i < R; i += blockDim.x) L[i * LD + k] = L[i * LD + k] / lkk;
+    __syncthreads();
+    int m = R - k - 1;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      int i = k + 1 + e / m, j = k + 1 + e % m;
+      if (j <= i) L[i * LD + j] = fma(-L[i * LD + k], L[j * LD + k], L[i * LD + j]);
+    }
+  }
+  __syncthreads();
+  // L^-1 by forward substitution, one column per thread.
+  for (int j = tid; j < R; j += blockDim.x) {
+    for (int i = 0; i < j; ++i) X[i * LD + j] = 0.0;
+    X[j * LD + j] = 1.0 / L[j * LD + j];
+    for (int i = j + 1; i < R; ++i) {
+      double acc = 0.0;
+      for (int k = j; k < i; ++k) acc = fma(L[i * LD + k], X[k * LD + j], acc);
+      X[i * LD + j] = -acc / L[i * LD + i];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < R * R; e += blockDim.x) mp.linv[n][e] = X[(e / R) * LD + (e % R)];
+  // (A^T A)^-1 = X^T X in FP32 (a preconditioner only needs a spectral approximation).
+  for (int e = tid; e < R * R; e += blockDim.x) {
+    int i = e / R, j = e % R;
+    int k0 = i > j ? i : j;
+    float acc = 0.f;
+    for (int k = k0; k < R; ++k) acc = fmaf((float)X[k * LD + i], (float)X[k * LD + j], acc);
+    mp.ginv[n][e] = acc;
+  }
+  if (tid == 0) mp.flags[n] = bad;
+}
+
+// l_i = ||L^-1 a_i||^2 in FP64, 64 rows per block.
+__global__ void k_leverage(ModePtrs mp) {
+  const int n = blockIdx.y;
+  const int I = mp.I[n], R = mp.R[n];
+  const int r0 = blockIdx.x * 64;
+  if (r0 >= I) return;
+  extern __shared__ double sm[];
+  double* X = sm;              // R x LD
+  double* a = sm + MAXR * LD;  // 64 x LD
+  const int rows = min(64, I - r0);
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) X[(e / R) * LD + (e % R)] = mp.linv[n][e];
+  for (int e = threadIdx.x; e < rows * R; e += blockDim.x)
+    a[(e / R) * LD + (e % R)] = (double)mp.A[n][(int64_t)(r0 + e / R) * R + (e % R)];
+  __syncthreads();
+  int t = threadIdx.x;
+  if (t < rows) {
+    double acc = 0.0;
+    for (int k = 0; k < R; ++k) {
+      double v = 0.0;
+      for (int m = 0; m <= k; ++m) v = fma(X[k * LD + m], a[t * LD + m], v);
+      acc = fma(v, v, acc);
+    }
+    mp.lev[n][r0 + t] = acc;
+  }
+}
+
+// One block per mode: left-to-right FP64 prefix, normalised CDF, integer thresholds,
+// probabilities and FP32 inverse probabilities.
+__global__ void k_cdf(ModePtrs mp) {
+  const int n = blockIdx.x;
+  const int I = mp.I[n];
+  double* cdf = mp.cdf[n];
+  const double* lev = mp.lev[n];
+  __shared__ double total;
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    int lp = -1;
+    for (int i = 0; i < I; ++i) {
+      double l = lev[i];
+      acc = __dadd_rn(acc, l);
+      cdf[i] = acc;
+      if (l > 0.0) lp = i;
+    }
+    total = acc;
+    last = lp;
+  }
+  __syncthreads();
+  const double T = total;
+  const int lp = last;
+  for (int i = threadIdx.x; i < I; i += blockDim.x) {
+    double c = (lp >= 0 && i >= lp) ? 1.0 : __ddiv_rn(cdf[i], T);
+    cdf[i] = c;
+    double l = lev[i];
+    mp.prob[n][i] = __ddiv_rn(l, T);
+    mp.invp[n][i] = l > 0.0 ? (float)__ddiv_rn(T, l) : 0.f;
+    // u < c  <=>  U < ceil(c * 2^53) for the 53-bit integer U with u = U * 2^-53
+    mp.thr[n][i] = (uint64_t)ceil(c * 9007199254740992.0);
+  }
+}
+
+// Cyclic Jacobi eigen-decomposition (FP32) of each Gram matrix, one block per mode,
+// parallel (round-robin) ordering of disjoint rotations.
+__global__ void k_jacobi(ModePtrs mp) {
+  const int n = blockIdx.x;
+  const int R = mp.R[n];
+  const int m = (R + 1) & ~1;
+  extern __shared__ float fs[];
+  float* A = fs;              // (MAXR+1) x LD
+  float* V = fs + (MAXR + 1) * LD;
+  __shared__ float cs[MAXR / 2 + 1], sn[MAXR / 2 + 1];
+  __shared__ int pp[MAXR / 2 + 1], qq[MAXR / 2 + 1];
+  __shared__ float red[2];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    int i = e / m, j = e % m;
+    A[i * LD + j] = (i < R && j < R) ? (float)mp.gram[n][i * R + j] : 0.f;
+    V[i * LD + j] = (i == j) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    for (int r = 0; r < m - 1; ++r) {
+      if (tid < m / 2) {
+        int k = tid;
+        // players 1..m-1 rotate around player 0
+        int p = (k == 0) ? 0 : 1 + ((k - 1 + r) % (m - 1));
+        int q = 1 + ((m - 2 - k + r) % (m - 1));
+        if (p > q) { int t = p; p = q; q = t; }
+        float apq = A[p * LD + q], app = A[p * LD + p], aqq = A[q * LD + q];
+        float c = 1.f, s = 0.f;
+        if (fabsf(apq) > 1e-30f * (fabsf(app) + fabsf(aqq)) && apq != 0.f) {
+          float tau = (aqq - app) / (2.f * apq);
+          float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+          c = rsqrtf(1.f + t * t);
+          s = t * c;
+        }
+        cs[k] = c; sn[k] = s; pp[k] = p; qq[k] = q;
+      }
+      __syncthreads();
+      for (int w = tid; w < (m / 2) * m; w += blockDim.x) {  // rows: A <- J^T A
+        int k = w / m, j = w % m;
+        float c = cs[k], s = sn[k];
+        if (s == 0.f) continue;
+        int p = pp[k], q = qq[k];
+        float ap = A[p * LD + j], aq = A[q * LD + j];
+        A[p * LD + j] = c * ap - s * aq;
+        A[q * LD + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      for (int w = tid; w < (m / 2) * m; w += blockDim.x) {  // columns: A <- A J, V <- V J
+        int k = w / m, i = w % m;
+        float c = cs[k], s = sn[k];
+        if (s == 0.f) continue;
+        int p = pp[k], q = qq[k];
+        float ap = A[i * LD + p], aq = A[i * LD + q];
+        A[i * LD + p] = c * ap - s * aq;
+        A[i * LD + q] = s * ap + c * aq;
+        float vp = V[i * LD + p], vq = V[i * LD + q];
+        V[i * LD + p] = c * vp - s * vq;
+        V[i * LD + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      float off = 0.f, dg = 0.f;
+      for (int i = 0; i < R; ++i)
+        for (int j = 0; j < R; ++j) {
+          float v = A[i * LD + j];
+          if (i == j) dg += v * v; else off += v * v;
+        }
+      red[0] = off; red[1] = dg;
+    }
+    __syncthreads();
+    bool done = red[0] <= 1e-14f * red[1];
+    __syncthreads();
+    if (done) break;
+  }
+  for (int e = tid; e < R * R; e += blockDim.x) mp.V[n][e] = V[(e / R) * LD + (e % R)];
+  for (int i = tid; i < R; i += blockDim.x) mp.sig2[n][i] = fmaxf(A[i * LD + i], 0.f);
+}
+
+}  // namespace
+
+void kr_tables_need(const Modes& m, bool want_eig, Need& nd) {
+  for (int n = 0; n < m.N; ++n) {
+    int I = m.I[n], R = m.R[n];
+    nd.add<double>((size_t)((I + GRAM_ROWS - 1) / GRAM_ROWS) * R * R);
+    nd.add<double>((size_t)R * R);  // gram
+    nd.add<double>((size_t)R * R);  // linv
+    nd.add<double>(I);
+    nd.add<double>(I);
+    nd.add<double>(I);
+    nd.add<uint64_t>(I);
+    nd.add<float>(I);
+    nd.add<float>((size_t)R * R);
+    if (want_eig) {
+      nd.add<float>((size_t)R * R);
+      nd.add<float>(R);
+    }
+  }
+  nd.add<int>(KR_MAX_MODES);
+}
+
+kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv, FactorTables& t, bool check_rank) {
+  ModePtrs mp = {};
+  mp.N = m.N;
+  t.N = m.N;
+  int maxI = 0;
+  for (int n = 0; n < m.N; ++n) {
+    int I = m.I[n], R = m.R[n];
+    mp.I[n] = I; mp.R[n] = R; mp.A[n] = m.A[n];
+    t.I[n] = I; t.R[n] = R;
+    mp.part[n] = cv.take<double>((size_t)((I + GRAM_ROWS - 1) / GRAM_ROWS) * R * R);
+    mp.gram[n] = t.gram[n] = cv.take<double>((size_t)R * R);
+    mp.linv[n] = cv.take<double>((size_t)R * R);
+    mp.lev[n] = t.lev[n] = cv.take<double>(I);
+    mp.cdf[n] = t.cdf[n] = cv.take<double>(I);
+    mp.prob[n] = t.prob[n] = cv.take<double>(I);
+    mp.thr[n] = t.thr[n] = cv.take<uint64_t>(I);
+    mp.invp[n] = t.invp[n] = cv.take<float>(I);
+    mp.ginv[n] = t.ginv[n] = cv.take<float>((size_t)R * R);
+    if (want_eig) {
+      mp.V[n] = t.V[n] = cv.take<float>((size_t)R * R);
+      mp.sig2[n] = t.sig2[n] = cv.take<float>(R);
+    }
+    maxI = I > maxI ? I : maxI;
+  }
+  mp.flags = cv.take<int>(KR_MAX_MODES);
+  if (cv.off > cv.cap) return kr_fail(ctx, KR_ENOMEM, "tables: workspace too small");
+
+  const size_t chol_smem = 2 * MAXR * LD * sizeof(double);
+  const size_t lev_smem = (MAXR * LD + 64 * LD) * sizeof(double);
+  const size_t jac_smem = 2 * (MAXR + 1) * LD * sizeof(float);
+  KR_CUDA(ctx, cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem));
+  KR_CUDA(ctx, cudaFuncSetAttribute(k_leverage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lev_smem));
+  KR_CUDA(ctx, cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jac_smem));
+  dim3 gg((maxI + GRAM_ROWS - 1) / GRAM_ROWS, m.N);
+  KR_LAUNCH(ctx, k_gram_partial, gg, 256, 0, mp);
+  KR_LAUNCH(ctx, k_gram_reduce, m.N, 256, 0, mp);
+  KR_LAUNCH(ctx, k_cholesky, m.N, 256, chol_smem, mp);
+  dim3 gl((maxI + 63) / 64, m.N);
+  KR_LAUNCH(ctx, k_leverage, gl, 64, lev_smem, mp);
+  KR_LAUNCH(ctx, k_cdf, m.N, 256, 0, mp);
+  if (want_eig) KR_LAUNCH(ctx, k_jacobi, m.N, 256, jac_smem, mp);
+  if (check_rank) {
+    KR_TRY(kr_hbuf_reserve(ctx, 4096));
+    int* hf = (int*)ctx->hbuf;
+    KR_CUDA(ctx, cudaMemcpyAsync(hf, mp.flags, sizeof(int) * m.N, cudaMemcpyDeviceToHost, ctx->stream));
+    KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int n = 0; n < m.N; ++n) {
+      t.rank[n] = hf[n] ? -1 : m.R[n];
+      if (hf[n]) return kr_fail(ctx, KR_ERANK, "factor %d is numerically rank deficient (Cholesky pivot)", n);
+    }
+  }
+  return KR_OK;
+}
+
+extern "C" kr_status kron_leverage(kr_ctx* ctx, const kr_factors* f, double* const lev[], double* const cdf[],
+                                   double* const prob[], int32_t* rank) {
+  if (!ctx) return KR_EINVAL;
+  Modes m;
+  KR_TRY(kr_check_factors(ctx, f, &m));
+  Need nd;
+  kr_tables_need(m, false, nd);
+  KR_TRY(kr_ws_reserve(ctx, nd.off));
+  Carve cv(ctx->ws, ctx->ws_size);
+  FactorTables t;
+  kr_status st = kr_tables_build(ctx, m, false, cv, t, true);
+  if (rank)
+    for (int n = 0; n < m.N; ++n) rank[n] = t.rank[n] < 0 ? -1 : m.R[n];
+  if (st != KR_OK && st != KR_ERANK) return st;
+  for (int n = 0; n < m.N; ++n) {
+    size_t bytes = sizeof(double) * m.I[n];
+    if (lev && lev[n]) KR_CUDA(ctx, cudaMemcpyAsync(lev[n], t.lev[n], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (cdf && cdf[n]) KR_CUDA(ctx, cudaMemcpyAsync(cdf[n], t.cdf[n], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (prob && prob[n]) KR_CUDA(ctx, cudaMemcpyAsync(prob[n], t.prob[n], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return st;
+}

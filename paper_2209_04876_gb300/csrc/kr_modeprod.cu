@@ -1,0 +1,244 @@
+// Mode-n products, KronMatMul (Lemma 4.3) and the Kronecker preconditioner of Alg. 2.
+//
+// One mode product maps a tensor viewed as (P, K, Q) to (P, J, Q):
+//   out[p, j, q] = sum_k B[j, k] in[p, k, q]
+// i.e. the n-mode product of §2 with P = prod of the leading dimensions and
+// Q = prod of the trailing ones. KronMatMul applies one such product per mode
+// (the recursion in the proof of Lemma 4.3, unrolled). The preconditioner
+// M+ = (V1 (x)...(x) VN) D (V1 (x)...(x) VN)^T of Alg. 2 is N products with V^T, a
+// diagonal scaling, and N products with V (square Kronecker mat-vec theorem, App. B);
+// for lambda = 0 it is N products with the (A^T A)^-1 factors.
+//
+// The kernel is an FP32 CUDA-core tiled GEMM over (J) x (P*Q) with the K reduction
+// staged through shared memory; FP32 accumulation.
+#include "kr_internal.cuh"
+
+namespace {
+
+constexpr int TJ = 64, TN = 64, TK = 16;
+
+__global__ void __launch_bounds__(256) k_mode_product(const float* __restrict__ in, float* __restrict__ out, int64_t P,
+                                                       int K, int64_t Q, int J, const float* __restrict__ B, int trans) {
+  __shared__ float Bs[TK][TJ + 4];
+  __shared__ float Xs[TK][TN + 4];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int j0 = blockIdx.y * TJ;
+  const int64_t n0 = (int64_t)blockIdx.x * TN;
+  const int64_t NN = P * Q;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += TK) {
+    // B tile: Bs[kk][jj] = B[j0+jj, k0+kk]
+    for (int e = threadIdx.x; e < TK * TJ; e += 256) {
+      int kk, jj;
+      if (trans) { jj = e % TJ; kk = e / TJ; } else { kk = e % TK; jj = e / TK; }
+      int j = j0 + jj, k = k0 + kk;
+      float v = 0.f;
+      if (j < J && k < K) v = trans ? B[(int64_t)k * J + j] : B[(int64_t)j * K + k];
+      Bs[kk][jj] = v;
+    }
+    // input tile: Xs[kk][nn] = in[p, k0+kk, q] with n = n0+nn = p*Q + q
+    for (int e = threadIdx.x; e < TK * TN; e += 256) {
+      int nn = e % TN, kk = e / TN;
+      int64_t n = n0 + nn;
+      int k = k0 + kk;
+      float v = 0.f;
+      if (n < NN && k < K) {
+        int64_t p = n / Q, q = n - p * Q;
+        v = in[(p * K + k) * Q + q];
+      }
+      Xs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      float bj[4], xn[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) bj[a] = Bs[kk][ty * 4 + a];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xn[a] = Xs[kk][tx * 4 + a];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(bj[a], xn[c], acc[a][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int j = j0 + ty * 4 + a;
+    if (j >= J) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int64_t n = n0 + tx * 4 + c;
+      if (n >= NN) continue;
+      int64_t p = n / Q, q = n - p * Q;
+      out[(p * J + j) * Q + q] = acc[a][c];
+    }
+  }
+}
+
+struct DiagArgs {
+  int N;
+  int R[KR_MAX_MODES];
+  const float* sig2[KR_MAX_MODES];
+};
+
+// x[r] *= 1 / (prod_n sig2_n[r_n] + lambda)  (pseudo-inverse: 0 where the sum is 0)
+__global__ void k_diag_scale(float* __restrict__ x, int64_t total, DiagArgs da, float lambda) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = i;
+    float prod = 1.f;
+    for (int n = da.N - 1; n >= 0; --n) {
+      int r = (int)(rem % da.R[n]);
+      rem /= da.R[n];
+      prod *= da.sig2[n][r];
+    }
+    float d = prod + lambda;
+    x[i] = d > 0.f ? x[i] / d : 0.f;
+  }
+}
+
+}  // namespace
+
+kr_status kr_mode_product(kr_ctx* ctx, const float* in, float* out, int64_t P, int K, int64_t Q, int J, const float* B,
+                          int trans) {
+  int64_t NN = P * Q;
+  dim3 grid((unsigned)((NN + TN - 1) / TN), (unsigned)((J + TJ - 1) / TJ));
+  if (grid.x == 0 || grid.y == 0) return KR_OK;
+  KR_LAUNCH(ctx, k_mode_product, grid, 256, 0, in, out, P, K, Q, J, B, trans);
+  return KR_OK;
+}
+
+// Applies B_n (dimsOut[n] x dimsIn[n], or its stored transpose) along every mode n
+// with B[n] != nullptr. Intermediates alternate between tmp0 and tmp1, the last
+// product writes `out`; no product reads and writes the same buffer, so `in` may be
+// `out`. tmp0/tmp1 must hold the largest intermediate.
+kr_status kr_kron_apply2(kr_ctx* ctx, int N, const int* dimsIn, const int* dimsOut, const float* const* B,
+                         const int* trans, const float* in, float* out, float* tmp0, float* tmp1) {
+  int cur[KR_MAX_MODES];
+  int active = 0;
+  int64_t tot = 1;
+  for (int n = 0; n < N; ++n) {
+    cur[n] = dimsIn[n];
+    tot *= dimsIn[n];
+    if (B[n]) ++active;
+  }
+  if (active == 0) {
+    if (out != in) KR_CUDA(ctx, cudaMemcpyAsync(out, in, sizeof(float) * tot, cudaMemcpyDeviceToDevice, ctx->stream));
+    return KR_OK;
+  }
+  const float* src = in;
+  if (active == 1 && in == out) {
+    KR_CUDA(ctx, cudaMemcpyAsync(tmp0, in, sizeof(float) * tot, cudaMemcpyDeviceToDevice, ctx->stream));
+    src = tmp0;
+  }
+  int a = 0;
+  for (int n = 0; n < N; ++n) {
+    if (!B[n]) continue;
+    int64_t P = 1, Q = 1;
+    for (int m = 0; m < n; ++m) P *= cur[m];
+    for (int m = n + 1; m < N; ++m) Q *= cur[m];
+    float* dst = (a == active - 1) ? out : (src == tmp0 ? tmp1 : tmp0);
+    KR_TRY(kr_mode_product(ctx, src, dst, P, cur[n], Q, dimsOut[n], B[n], trans ? trans[n] : 0));
+    cur[n] = dimsOut[n];
+    src = dst;
+    ++a;
+  }
+  return KR_OK;
+}
+
+kr_status kr_kron_apply(kr_ctx* ctx, int N, const int* dimsIn, const int* dimsOut, const float* const* B,
+                        const int* trans, const float* in, float* out, float* tmp, int64_t tmp_elems) {
+  return kr_kron_apply2(ctx, N, dimsIn, dimsOut, B, trans, in, out, tmp, tmp + tmp_elems);
+}
+
+// d = M+ g for Alg. 2's preconditioner built from tables t (tmp0, tmp1: R floats each).
+kr_status kr_precond_apply(kr_ctx* ctx, const FactorTables& t, double lambda, const float* g, float* d, float* tmp0,
+                           float* tmp1) {
+  const int N = t.N;
+  int dims[KR_MAX_MODES];
+  const float* B[KR_MAX_MODES];
+  int tr[KR_MAX_MODES];
+  int64_t R = 1;
+  for (int n = 0; n < N; ++n) {
+    dims[n] = t.R[n];
+    R *= t.R[n];
+  }
+  if (lambda == 0.0) {
+    for (int n = 0; n < N; ++n) {
+      B[n] = t.ginv[n];
+      tr[n] = 0;
+    }
+    return kr_kron_apply2(ctx, N, dims, dims, B, tr, g, d, tmp0, tmp1);
+  }
+  for (int n = 0; n < N; ++n) {
+    B[n] = t.V[n];
+    tr[n] = 1;  // V^T
+  }
+  KR_TRY(kr_kron_apply2(ctx, N, dims, dims, B, tr, g, d, tmp0, tmp1));
+  DiagArgs da = {};
+  da.N = N;
+  for (int n = 0; n < N; ++n) {
+    da.R[n] = t.R[n];
+    da.sig2[n] = t.sig2[n];
+  }
+  int grid = (int)((R + 255) / 256);
+  if (grid > ctx->num_sms * 8) grid = ctx->num_sms * 8;
+  KR_LAUNCH(ctx, k_diag_scale, grid, 256, 0, d, R, da, (float)lambda);
+  for (int n = 0; n < N; ++n) tr[n] = 0;  // V
+  return kr_kron_apply2(ctx, N, dims, dims, B, tr, d, d, tmp0, tmp1);
+}
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" kr_status kron_matmul(kr_ctx* ctx, int32_t N, const int64_t* J, const int64_t* K, const float* const B[],
+                                 const int32_t* trans, const float* x, float* y) {
+  if (!ctx) return KR_EINVAL;
+  if (N < 1 || N > KR_MAX_MODES || !J || !K || !B || !x || !y) return kr_fail(ctx, KR_EINVAL, "kron_matmul: bad arguments");
+  int din[KR_MAX_MODES], dout[KR_MAX_MODES], tr[KR_MAX_MODES];
+  int64_t cur = 1, mx = 1;
+  for (int n = 0; n < N; ++n) {
+    if (J[n] < 1 || K[n] < 1 || J[n] > (1 << 30) || K[n] > (1 << 30) || !B[n])
+      return kr_fail(ctx, KR_EINVAL, "kron_matmul: bad mode %d", n);
+    din[n] = (int)K[n];
+    dout[n] = (int)J[n];
+    tr[n] = trans ? trans[n] : 0;
+    cur *= K[n];
+  }
+  mx = cur;
+  for (int n = 0; n < N; ++n) {
+    cur = cur / K[n] * J[n];
+    if (cur > mx) mx = cur;
+  }
+  Need nd;
+  nd.add<float>(mx);
+  nd.add<float>(mx);
+  KR_TRY(kr_ws_reserve(ctx, nd.off));
+  Carve cv(ctx->ws, ctx->ws_size);
+  float* t0 = cv.take<float>(mx);
+  float* t1 = cv.take<float>(mx);
+  KR_TRY(kr_kron_apply2(ctx, N, din, dout, B, tr, x, y, t0, t1));
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return KR_OK;
+}
+
+extern "C" kr_status kron_precond(kr_ctx* ctx, const kr_factors* f, double lambda, const float* g, float* d) {
+  if (!ctx) return KR_EINVAL;
+  Modes m;
+  KR_TRY(kr_check_factors(ctx, f, &m));
+  if (!(lambda >= 0.0) || !g || !d) return kr_fail(ctx, KR_EINVAL, "kron_precond: bad lambda or null vector");
+  int64_t R = kr_prod_R(m);
+  Need nd;
+  kr_tables_need(m, lambda > 0.0, nd);
+  nd.add<float>(R);
+  nd.add<float>(R);
+  KR_TRY(kr_ws_reserve(ctx, nd.off));
+  Carve cv(ctx->ws, ctx->ws_size);
+  FactorTables t;
+  KR_TRY(kr_tables_build(ctx, m, lambda > 0.0, cv, t, true));
+  float* t0 = cv.take<float>(R);
+  float* t1 = cv.take<float>(R);
+  KR_TRY(kr_precond_apply(ctx, t, lambda, g, d, t0, t1));
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return KR_OK;
+}

@@ -1,0 +1,496 @@
+// a3 + a4 + a5: product-distribution sampling, grouping of the draws by cell,
+// merging of repeated rows, and the gather b~ = S b.
+//
+// SampleRows (§3 Def. of leverage score sampling) on K with the product
+// distribution of Lemma 4.1: every coordinate of a draw is sampled independently
+// from its factor's CDF (proof of Thm 4.5). The uniform for draw t and coordinate m
+// comes from Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), implemented here
+// from that paper's definition: round (x0,x1,x2,x3) -> (hi(M1 x2) ^ x1 ^ k0,
+// lo(M1 x2), hi(M0 x0) ^ x3 ^ k1, lo(M0 x0)), key bumped by the Weyl constants.
+// Counter (t lo, t hi, m/2 + 256*row, call id lo), key (seed lo, seed hi); words
+// (w0,w1) serve even m and (w2,w3) odd m; U = ((wa << 32) | wb) >> 11 and the drawn
+// index is the smallest i with U * 2^-53 < cdf[i], evaluated exactly in integers as
+// U < ceil(cdf[i] * 2^53).
+//
+// Grouping (the sets S_1, S_2 and B_S of the proof of Thm 4.4 with T = {N}):
+// cell = (i_1..i_{N-1}), the last coordinate i_N stays with the sample. A counting
+// sort by cell (histogram, scan, scatter), then per cell a table over i_N merges
+// repeated rows into multiplicities in increasing i_N order, and gathers b.
+#include "kr_internal.cuh"
+
+namespace {
+
+struct SampleModes {
+  int N;
+  int I[KR_MAX_MODES];
+  const uint64_t* thr[KR_MAX_MODES];
+  const double* prob[KR_MAX_MODES];
+  const float* invp[KR_MAX_MODES];
+};
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint64_t u53(uint32_t a, uint32_t b) {
+  return ((uint64_t(a) << 32) | uint64_t(b)) >> 11;
+}
+
+// Smallest i with U < thr[i] (thr non-decreasing, thr[n-1] = 2^53 > U).
+__device__ __forceinline__ int search_thr(const uint64_t* thr, int n, uint64_t U) {
+  int base = 0, len = n;
+  while (len > 1) {
+    int half = len >> 1;
+    base = (thr[base + half - 1] <= U) ? base + half : base;
+    len -= half;
+  }
+  return base;
+}
+
+// Draws the multi-index of draw t into idx[0..N).
+__device__ __forceinline__ void draw(const SampleModes& sm, const uint64_t* const* thr, uint64_t t,
+                                     uint32_t k0, uint32_t k1, uint32_t row, uint32_t cid, int* idx) {
+  for (int k = 0; 2 * k < sm.N; ++k) {
+    uint4 w = philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)k + 256u * row, cid), k0, k1);
+    idx[2 * k] = search_thr(thr[2 * k], sm.I[2 * k], u53(w.x, w.y));
+    if (2 * k + 1 < sm.N) idx[2 * k + 1] = search_thr(thr[2 * k + 1], sm.I[2 * k + 1], u53(w.z, w.w));
+  }
+}
+
+// Thresholds to shared memory when they fit (sum I_n <= 4096 entries = 32 KB).
+constexpr int THR_SMEM = 4096;
+
+__device__ __forceinline__ void load_thr(const SampleModes& sm, uint64_t* buf, const uint64_t** thr) {
+  int tot = 0;
+  for (int n = 0; n < sm.N; ++n) tot += sm.I[n];
+  if (tot <= THR_SMEM) {
+    int off = 0;
+    for (int n = 0; n < sm.N; ++n) {
+      for (int i = threadIdx.x; i < sm.I[n]; i += blockDim.x) buf[off + i] = sm.thr[n][i];
+      thr[n] = buf + off;
+      off += sm.I[n];
+    }
+  } else {
+    for (int n = 0; n < sm.N; ++n) thr[n] = sm.thr[n];
+  }
+  __syncthreads();
+}
+
+// kron_sample surface: indices (s x N) and weights 1/sqrt(s prod p).
+__global__ void k_sample_idx(SampleModes sm, int64_t s, uint32_t k0, uint32_t k1, uint32_t row, uint32_t cid,
+                             int32_t* __restrict__ idx_out, float* __restrict__ w_out) {
+  __shared__ uint64_t buf[THR_SMEM];
+  const uint64_t* thr[KR_MAX_MODES];
+  load_thr(sm, buf, thr);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < s; t += (int64_t)gridDim.x * blockDim.x) {
+    int idx[KR_MAX_MODES];
+    draw(sm, thr, (uint64_t)t, k0, k1, row, cid, idx);
+    if (idx_out)
+      for (int n = 0; n < sm.N; ++n) idx_out[t * sm.N + n] = idx[n];
+    if (w_out) {
+      double p = (double)s;
+      for (int n = 0; n < sm.N; ++n) p *= sm.prob[n][idx[n]];
+      w_out[t] = (float)(1.0 / sqrt(p));
+    }
+  }
+}
+
+// Solver path: cell id and last coordinate packed in one key; histogram by cell.
+// key = cell * IT + i_T (the linear row index).
+__global__ void k_sample_keys(SampleModes sm, int64_t s, uint32_t k0, uint32_t k1, uint32_t row, uint32_t cid,
+                              uint32_t* __restrict__ keys, uint32_t* __restrict__ cell_cnt) {
+  __shared__ uint64_t buf[THR_SMEM];
+  const uint64_t* thr[KR_MAX_MODES];
+  load_thr(sm, buf, thr);
+  const int N = sm.N;
+  const uint32_t IT = sm.I[N - 1];
+  for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x; t0 < s; t0 += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = t0 + threadIdx.x;
+    bool live = t < s;
+    uint32_t cell = 0;
+    if (live) {
+      int idx[KR_MAX_MODES];
+      draw(sm, thr, (uint64_t)t, k0, k1, row, cid, idx);
+      for (int n = 0; n < N - 1; ++n) cell = cell * (uint32_t)sm.I[n] + (uint32_t)idx[n];
+      keys[t] = cell * IT + (uint32_t)idx[N - 1];
+    }
+    // warp-aggregated histogram increment
+    unsigned act = __ballot_sync(0xffffffffu, live);
+    if (live) {
+      unsigned peers = __match_any_sync(act, cell);
+      int leader = __ffs(peers) - 1;
+      if ((int)(threadIdx.x & 31) == leader) atomicAdd(&cell_cnt[cell], (uint32_t)__popc(peers));
+    }
+  }
+}
+
+// Exclusive scan of n counters, single block of 1024 threads (n up to a few million).
+__global__ void k_scan_excl(const uint32_t* __restrict__ cnt, uint32_t* __restrict__ start, int64_t n) {
+  __shared__ uint32_t part[1024];
+  const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t a = threadIdx.x * per, b = min(n, a + per);
+  uint32_t sum = 0;
+  for (int64_t i = a; i < b; ++i) sum += cnt[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    uint32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - sum;
+  for (int64_t i = a; i < b; ++i) {
+    start[i] = run;
+    run += cnt[i];
+  }
+}
+
+// Scatter i_T of every draw into its cell's slot range.
+__global__ void k_scatter(const uint32_t* __restrict__ keys, int64_t s, uint32_t IT, const uint32_t* __restrict__ start,
+                          uint32_t* __restrict__ cursor, uint16_t* __restrict__ slot) {
+  for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x; t0 < s; t0 += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = t0 + threadIdx.x;
+    bool live = t < s;
+    uint32_t key = live ? keys[t] : 0u;
+    uint32_t cell = key / IT;
+    unsigned act = __ballot_sync(0xffffffffu, live);
+    if (live) {
+      unsigned peers = __match_any_sync(act, cell);
+      int leader = __ffs(peers) - 1;
+      int lane = threadIdx.x & 31;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&cursor[cell], (uint32_t)__popc(peers));
+      base = __shfl_sync(peers, base, leader);
+      uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+      slot[start[cell] + base + rank] = (uint16_t)(key - cell * IT);
+    }
+  }
+}
+
+// Per cell (one warp): count table over i_T in shared memory, then emit the distinct
+// entries in increasing i_T order with their multiplicities, gather b, and the
+// per-cell weight prod_{n<N-1} 1/p_n(i_n) / s.
+constexpr int DEDUP_WARPS = 4;
+constexpr int DEDUP_MAX_IT = 8192;
+
+__global__ void k_dedup(SampleModes sm, int64_t ncell, uint32_t IT, float inv_s, const uint32_t* __restrict__ start,
+                        const uint32_t* __restrict__ cnt, const uint16_t* __restrict__ slot, const float* __restrict__ b,
+                        uint32_t* __restrict__ ent, float* __restrict__ bt, uint32_t* __restrict__ nd,
+                        float* __restrict__ cell_w) {
+  extern __shared__ uint32_t tabs[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* tab = tabs + (size_t)warp * IT;
+  for (uint32_t i = lane; i < IT; i += 32) tab[i] = 0;
+  __syncwarp();
+  const uint32_t chunk = (IT + 31) / 32;
+  const uint32_t lo = min(IT, lane * chunk), hi = min(IT, lo + chunk);
+  for (int64_t c = (int64_t)blockIdx.x * DEDUP_WARPS + warp; c < ncell; c += (int64_t)gridDim.x * DEDUP_WARPS) {
+    const uint32_t n = cnt[c], base = start[c];
+    if (lane == 0) {
+      // weight of the cell: prod over the first N-1 coordinates of 1/p
+      float w = inv_s;
+      int64_t rem = c;
+      for (int m = sm.N - 2; m >= 0; --m) {
+        int i = (int)(rem % sm.I[m]);
+        rem /= sm.I[m];
+        w *= sm.invp[m][i];
+      }
+      cell_w[c] = w;
+    }
+    if (n == 0) {
+      if (lane == 0) nd[c] = 0;
+      continue;
+    }
+    for (uint32_t j = lane; j < n; j += 32) atomicAdd(&tab[slot[base + j]], 1u);
+    __syncwarp();
+    uint32_t mine = 0;
+    for (uint32_t i = lo; i < hi; ++i) {
+      uint32_t v = tab[i];
+      mine += (v + 65534u) / 65535u;  // entries needed (multiplicity stored in 16 bits)
+    }
+    uint32_t incl = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    uint32_t pos = base + incl - mine;
+    const int64_t rowbase = c * (int64_t)IT;
+    for (uint32_t i = lo; i < hi; ++i) {
+      uint32_t v = tab[i];
+      if (v == 0) continue;
+      tab[i] = 0;
+      float bv = b ? b[rowbase + i] : 0.f;
+      while (v > 0) {
+        uint32_t take = v > 65535u ? 65535u : v;
+        ent[pos] = i | (take << 16);
+        bt[pos] = bv;
+        ++pos;
+        v -= take;
+      }
+    }
+    uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane == 0) nd[c] = total;
+    __syncwarp();
+  }
+}
+
+// Sketch export: linear keys, counts, weights and b~ in increasing key order.
+__global__ void k_export(int64_t ncell, uint32_t IT, const uint32_t* __restrict__ start, const uint32_t* __restrict__ nd,
+                         const uint32_t* __restrict__ off, const uint32_t* __restrict__ ent, const float* __restrict__ bt,
+                         const float* __restrict__ cell_w, const float* __restrict__ invpT, int64_t* keys,
+                         int32_t* counts, float* omega, float* btilde) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t n = nd[c], b0 = start[c], o = off[c];
+    for (uint32_t k = 0; k < n; ++k) {
+      uint32_t e = ent[b0 + k];
+      uint32_t it = e & 0xFFFFu, ct = e >> 16;
+      if (keys) keys[o + k] = c * (int64_t)IT + it;
+      if (counts) counts[o + k] = (int32_t)ct;
+      if (omega) omega[o + k] = (float)ct * cell_w[c] * invpT[it];
+      if (btilde) btilde[o + k] = bt[b0 + k];
+    }
+  }
+}
+
+__global__ void k_sum_u32(const uint32_t* __restrict__ v, int64_t n, unsigned long long* out) {
+  unsigned long long acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) acc += v[i];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+SampleModes make_sample_modes(const Modes& m, const FactorTables& t) {
+  SampleModes sm = {};
+  sm.N = m.N;
+  for (int n = 0; n < m.N; ++n) {
+    sm.I[n] = m.I[n];
+    sm.thr[n] = t.thr[n];
+    sm.prob[n] = t.prob[n];
+    sm.invp[n] = t.invp[n];
+  }
+  return sm;
+}
+
+int grid_for(kr_ctx* ctx, int64_t work, int block, int per_sm = 8) {
+  int64_t g = (work + block - 1) / block;
+  int64_t cap = (int64_t)ctx->num_sms * per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+void kr_sketch_setup(kr_sketch* sk, const Modes& m, int64_t s) {
+  sk->N = m.N;
+  for (int n = 0; n < m.N; ++n) sk->I[n] = m.I[n];
+  sk->s = s;
+  int64_t ncell = 1;
+  for (int n = 0; n < m.N - 1; ++n) ncell *= m.I[n];
+  sk->ncell = ncell;
+  sk->IT = m.I[m.N - 1];
+}
+
+void kr_sketch_own_need(const kr_sketch* sk, Need& nd) {
+  nd.add<uint32_t>(sk->ncell);
+  nd.add<uint32_t>(sk->ncell);
+  nd.add<uint32_t>(sk->s);
+  nd.add<float>(sk->s);
+  nd.add<float>(sk->ncell);
+  nd.add<float>(sk->IT);
+}
+
+void kr_sketch_layout(kr_sketch* sk, Carve& cv) {
+  sk->cell_start = cv.take<uint32_t>(sk->ncell);
+  sk->cell_nd = cv.take<uint32_t>(sk->ncell);
+  sk->ent = cv.take<uint32_t>(sk->s);
+  sk->bt = cv.take<float>(sk->s);
+  sk->cell_w = cv.take<float>(sk->ncell);
+  sk->invpT = cv.take<float>(sk->IT);
+}
+
+kr_status kr_sketch_check(kr_ctx* ctx, const Modes& m, int64_t s) {
+  if (s < 1 || s >= (int64_t(1) << 31)) return kr_fail(ctx, KR_EINVAL, "sketch: s=%lld outside [1, 2^31)", (long long)s);
+  if (m.I[m.N - 1] > DEDUP_MAX_IT)
+    return kr_fail(ctx, KR_ENOTIMPL, "sketch: last mode size %d exceeds %d", m.I[m.N - 1], DEDUP_MAX_IT);
+  return KR_OK;
+}
+
+// Second phase of the sketch build, with scratch carved from `cv`.
+kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, const float* b, uint64_t seed,
+                         uint64_t call_id, int row, kr_sketch* sk, Carve& cv) {
+  const int N = m.N;
+  const int64_t s = sk->s, ncell = sk->ncell;
+  const uint32_t IT = (uint32_t)sk->IT;
+  uint32_t* keys = cv.take<uint32_t>(s);
+  uint32_t* cnt = cv.take<uint32_t>(ncell);
+  uint32_t* cursor = cv.take<uint32_t>(ncell);
+  uint16_t* slot = cv.take<uint16_t>(s);
+  unsigned long long* dsum = cv.take<unsigned long long>(1);
+  if (cv.off > cv.cap) return kr_fail(ctx, KR_ENOMEM, "sketch: workspace too small");
+  SampleModes sm = make_sample_modes(m, t);
+  KR_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * ncell, ctx->stream));
+  KR_CUDA(ctx, cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * ncell, ctx->stream));
+  KR_CUDA(ctx, cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), ctx->stream));
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32), cid = (uint32_t)call_id;
+  KR_LAUNCH(ctx, k_sample_keys, grid_for(ctx, s, 256), 256, 0, sm, s, k0, k1, (uint32_t)row, cid, keys, cnt);
+  KR_LAUNCH(ctx, k_scan_excl, 1, 1024, 0, cnt, sk->cell_start, ncell);
+  KR_LAUNCH(ctx, k_scatter, grid_for(ctx, s, 256), 256, 0, keys, s, IT, sk->cell_start, cursor, slot);
+  const size_t dsmem = (size_t)DEDUP_WARPS * IT * sizeof(uint32_t);
+  KR_CUDA(ctx, cudaFuncSetAttribute(k_dedup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+  KR_LAUNCH(ctx, k_dedup, grid_for(ctx, ncell, DEDUP_WARPS, 4), DEDUP_WARPS * 32, dsmem, sm, ncell, IT,
+            (float)(1.0 / (double)s), sk->cell_start, cnt, slot, b, sk->ent, sk->bt, sk->cell_nd, sk->cell_w);
+  KR_CUDA(ctx, cudaMemcpyAsync(sk->invpT, t.invp[N - 1], sizeof(float) * IT, cudaMemcpyDeviceToDevice, ctx->stream));
+  KR_LAUNCH(ctx, k_sum_u32, grid_for(ctx, ncell, 256, 2), 256, 0, sk->cell_nd, ncell, dsum);
+  KR_TRY(kr_hbuf_reserve(ctx, 4096));
+  KR_CUDA(ctx, cudaMemcpyAsync(ctx->hbuf, dsum, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  sk->distinct = (int64_t)(*(unsigned long long*)ctx->hbuf);
+  return KR_OK;
+}
+
+void kr_sketch_scratch_need(int64_t s, int64_t ncell, Need& nd) {
+  nd.add<uint32_t>(s);
+  nd.add<uint32_t>(ncell);
+  nd.add<uint32_t>(ncell);
+  nd.add<uint16_t>(s);
+  nd.add<unsigned long long>(1);
+}
+
+// ------------------------------------------------------------------ C ABI
+
+__global__ void k_thr_from_cdf(const double* cdf, uint64_t* thr, int n);
+__global__ void k_invp_from_prob(const double* prob, float* invp, int n);
+
+extern "C" kr_status kron_sample(kr_ctx* ctx, int32_t N, const int64_t* I, const double* const cdf[],
+                                 const double* const prob[], int64_t s, uint64_t seed, uint64_t call_id, int32_t row,
+                                 int32_t* idx, float* w) {
+  if (!ctx) return KR_EINVAL;
+  if (N < 1 || N > KR_MAX_MODES || !I || !cdf) return kr_fail(ctx, KR_EINVAL, "kron_sample: bad N or null arrays");
+  if (s < 1 || s >= (int64_t(1) << 31)) return kr_fail(ctx, KR_EINVAL, "kron_sample: s outside [1, 2^31)");
+  if (row < 0 || row >= (1 << 24)) return kr_fail(ctx, KR_EINVAL, "kron_sample: row outside [0, 2^24)");
+  if (w && !prob) return kr_fail(ctx, KR_EINVAL, "kron_sample: weights need prob");
+  Need nd;
+  for (int n = 0; n < N; ++n) {
+    if (I[n] < 1 || I[n] > 65535 || !cdf[n]) return kr_fail(ctx, KR_EINVAL, "kron_sample: bad I[%d] or cdf[%d]", n, n);
+    nd.add<uint64_t>(I[n]);
+  }
+  KR_TRY(kr_ws_reserve(ctx, nd.off));
+  Carve cv(ctx->ws, ctx->ws_size);
+  SampleModes sm = {};
+  sm.N = N;
+  for (int n = 0; n < N; ++n) {
+    sm.I[n] = (int)I[n];
+    uint64_t* thr = cv.take<uint64_t>(I[n]);
+    sm.thr[n] = thr;
+    sm.prob[n] = prob ? prob[n] : nullptr;
+  }
+  // thresholds from the caller's CDF tables
+  for (int n = 0; n < N; ++n) {
+    KR_LAUNCH(ctx, k_thr_from_cdf, grid_for(ctx, I[n], 256), 256, 0, cdf[n], const_cast<uint64_t*>(sm.thr[n]),
+              (int)I[n]);
+  }
+  KR_LAUNCH(ctx, k_sample_idx, grid_for(ctx, s, 256), 256, 0, sm, s, (uint32_t)seed, (uint32_t)(seed >> 32),
+            (uint32_t)row, (uint32_t)call_id, idx, w);
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return KR_OK;
+}
+
+__global__ void k_thr_from_cdf(const double* cdf, uint64_t* thr, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    thr[i] = (uint64_t)ceil(cdf[i] * 9007199254740992.0);
+}
+
+extern "C" kr_status kron_sketch(kr_ctx* ctx, const kr_factors* f, const double* const cdf[], const double* const prob[],
+                                 const float* b, int64_t s, uint64_t seed, uint64_t call_id, int32_t row,
+                                 kr_sketch** out) {
+  if (!ctx || !out) return KR_EINVAL;
+  *out = nullptr;
+  Modes m;
+  KR_TRY(kr_check_factors(ctx, f, &m));
+  if (!cdf || !prob) return kr_fail(ctx, KR_EINVAL, "kron_sketch: cdf and prob are required");
+  if (row < 0 || row >= (1 << 24)) return kr_fail(ctx, KR_EINVAL, "kron_sketch: row outside [0, 2^24)");
+  int64_t ncell = 1;
+  for (int n = 0; n < m.N - 1; ++n) ncell *= m.I[n];
+  Need nd;
+  for (int n = 0; n < m.N; ++n) {
+    nd.add<uint64_t>(m.I[n]);
+    nd.add<double>(m.I[n]);
+    nd.add<float>(m.I[n]);
+  }
+  kr_sketch_scratch_need(s, ncell, nd);
+  KR_TRY(kr_ws_reserve(ctx, nd.off));
+  Carve cv(ctx->ws, ctx->ws_size);
+  FactorTables t;
+  t.N = m.N;
+  for (int n = 0; n < m.N; ++n) {
+    t.thr[n] = cv.take<uint64_t>(m.I[n]);
+    t.prob[n] = const_cast<double*>(prob[n]);
+    t.invp[n] = cv.take<float>(m.I[n]);
+    KR_LAUNCH(ctx, k_thr_from_cdf, grid_for(ctx, m.I[n], 256), 256, 0, cdf[n], t.thr[n], m.I[n]);
+    KR_LAUNCH(ctx, k_invp_from_prob, grid_for(ctx, m.I[n], 256), 256, 0, prob[n], t.invp[n], m.I[n]);
+  }
+  KR_TRY(kr_sketch_check(ctx, m, s));
+  kr_sketch* sk = new kr_sketch();
+  kr_sketch_setup(sk, m, s);
+  Need own;
+  kr_sketch_own_need(sk, own);
+  cudaError_t e = cudaMalloc((void**)&sk->mem, own.off);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete sk;
+    return kr_fail(ctx, KR_ENOMEM, "kron_sketch: allocation of %zu bytes failed", own.off);
+  }
+  Carve oc(sk->mem, own.off);
+  kr_sketch_layout(sk, oc);
+  kr_status st = kr_sketch_fill(ctx, m, t, b, seed, call_id, row, sk, cv);
+  if (st != KR_OK) {
+    kron_sketch_free(sk);
+    return st;
+  }
+  *out = sk;
+  return KR_OK;
+}
+
+__global__ void k_invp_from_prob(const double* prob, float* invp, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double p = prob[i];
+    invp[i] = p > 0.0 ? (float)(1.0 / p) : 0.f;
+  }
+}
+
+extern "C" int64_t kron_sketch_distinct(const kr_sketch* sk) { return sk ? sk->distinct : 0; }
+
+extern "C" kr_status kron_sketch_export(kr_ctx* ctx, const kr_sketch* sk, int64_t* keys, int32_t* counts, float* omega,
+                                        float* btilde) {
+  if (!ctx || !sk) return KR_EINVAL;
+  Need nd;
+  nd.add<uint32_t>(sk->ncell);
+  KR_TRY(kr_ws_reserve(ctx, nd.off));
+  Carve cv(ctx->ws, ctx->ws_size);
+  uint32_t* off = cv.take<uint32_t>(sk->ncell);
+  KR_LAUNCH(ctx, k_scan_excl, 1, 1024, 0, sk->cell_nd, off, sk->ncell);
+  KR_LAUNCH(ctx, k_export, grid_for(ctx, sk->ncell, 128), 128, 0, sk->ncell, (uint32_t)sk->IT, sk->cell_start,
+            sk->cell_nd, off, sk->ent, sk->bt, sk->cell_w, sk->invpT, keys, counts, omega, btilde);
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return KR_OK;
+}
+
+extern "C" void kron_sketch_free(kr_sketch* sk) {
+  if (!sk) return;
+  if (sk->mem) {
+    cudaDeviceSynchronize();
+    cudaFree(sk->mem);
+  }
+  delete sk;
+}

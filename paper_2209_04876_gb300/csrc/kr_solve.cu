@@ -1,0 +1,677 @@
+// a6-a12: sampled products, Richardson iteration (Alg. 2), final checks, solvers.
+//
+// One Richardson step of Alg. 2,
+//   x <- x - (1 - sqrt(eps)) M+ (K~^T K~ x + lambda x - K~^T b~),
+// is evaluated with the sampled products of Thm 4.4 (T = the last mode):
+//   Y  = X x_1 A(1) ... x_{N-1} A(N-1)           (cells x R_N, mode products)
+//   r_j = omega_j (b~_j - <A(N)[i_j], Y[cell_j]>)  (per distinct sampled row)
+//   W[c] = sum_{j in c} r_j A(N)[i_j]             (cells x R_N)
+//   g  = W x_1 A(1)^T ... x_{N-1} A(N-1)^T         (= K~^T Omega (b~ - K~ x))
+//   x <- x + alpha M+ (g - lambda x)
+// The residual is formed per row from b~ in FP32 (explicit-residual form), so the
+// iteration itself refines the solution to FP32 working accuracy.
+#include <math.h>
+
+#include "kr_internal.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------ sampled residual
+
+struct ResidArgs {
+  const uint32_t* cell_start;
+  const uint32_t* cell_nd;
+  const uint32_t* ent;
+  const float* bt;
+  const float* cell_w;
+  const float* invpT;
+  const float* AT;  // IT x RT
+  int IT, RT;
+  const float* Y;   // ncell x RT
+  float* W;         // ncell x RT
+  int64_t ncell;
+  double* obj_partial;  // gridDim.x
+};
+
+// G = RTP/4 lanes per cell, each lane owns 4 consecutive columns; A_T in shared
+// memory (zero-padded to RTP columns) when it fits, else read through L1.
+template <int RTP, bool SMEM_A>
+__global__ void __launch_bounds__(256) k_resid(ResidArgs a) {
+  constexpr int G = RTP / 4;
+  constexpr int CPW = 32 / G;
+  extern __shared__ float4 sA4[];
+  float* sInvp = reinterpret_cast<float*>(sA4 + (SMEM_A ? (size_t)a.IT * G : 0));
+  const int RT = a.RT;
+  if (SMEM_A) {
+    for (int e = threadIdx.x; e < a.IT * RTP; e += blockDim.x) {
+      int i = e / RTP, r = e % RTP;
+      reinterpret_cast<float*>(sA4)[e] = r < RT ? a.AT[(int64_t)i * RT + r] : 0.f;
+    }
+  }
+  for (int i = threadIdx.x; i < a.IT; i += blockDim.x) sInvp[i] = a.invpT[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int g = lane % G, slot = lane / G;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  double obj = 0.0;
+  for (int64_t c0 = gw * CPW; c0 < a.ncell; c0 += warps * CPW) {
+    const int64_t c = c0 + slot;
+    const bool live = c < a.ncell;
+    const uint32_t n = live ? a.cell_nd[c] : 0u;
+    const uint32_t base = live ? a.cell_start[c] : 0u;
+    const float cw = live ? a.cell_w[c] : 0.f;
+    float y[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      int r = 4 * g + k;
+      y[k] = (live && r < RT) ? a.Y[c * RT + r] : 0.f;
+    }
+    float w[4] = {0.f, 0.f, 0.f, 0.f};
+    float objc = 0.f;
+    uint32_t nmax = n;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, off));
+    for (uint32_t j = 0; j < nmax; ++j) {
+      const bool act = j < n;
+      const uint32_t e = act ? a.ent[base + j] : 0u;
+      const float bj = act ? a.bt[base + j] : 0.f;
+      const int it = (int)(e & 0xFFFFu);
+      float av[4];
+      if (SMEM_A) {
+        float4 v = sA4[it * G + g];
+        av[0] = v.x; av[1] = v.y; av[2] = v.z; av[3] = v.w;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          int r = 4 * g + k;
+          av[k] = r < RT ? __ldg(&a.AT[(int64_t)it * RT + r]) : 0.f;
+        }
+      }
+      float part = av[0] * y[0];
+      part = fmaf(av[1], y[1], part);
+      part = fmaf(av[2], y[2], part);
+      part = fmaf(av[3], y[3], part);
+#pragma unroll
+      for (int off = G / 2; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+      const float om = act ? (float)(e >> 16) * cw * sInvp[it] : 0.f;
+      const float res = bj - part;
+      const float rr = om * res;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w[k] = fmaf(rr, av[k], w[k]);
+      objc = fmaf(rr, res, objc);
+    }
+    if (live) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        int r = 4 * g + k;
+        if (r < RT) a.W[c * RT + r] = w[k];
+      }
+      if (g == 0) obj += (double)objc;
+    }
+  }
+  // block reduction of the objective partial (FP64)
+  __shared__ double red[8];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) obj += __shfl_xor_sync(0xffffffffu, obj, off);
+  if (lane == 0) red[threadIdx.x >> 5] = obj;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    a.obj_partial[blockIdx.x] = t;
+  }
+}
+
+// ------------------------------------------------------------------ vector kernels
+
+// g <- g - lambda x (the lambda term of the Richardson gradient)
+__global__ void k_sub_lambda_x(float* __restrict__ g, const float* __restrict__ x, float lambda, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    g[i] = fmaf(-lambda, x[i], g[i]);
+}
+
+// x <- x + alpha d; partials of ||alpha d||^2, ||x||^2 and a non-finite flag.
+__global__ void k_update(float* __restrict__ x, const float* __restrict__ d, float alpha, int64_t n,
+                         double* __restrict__ part) {
+  double s1 = 0.0, s2 = 0.0, bad = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float st = alpha * d[i];
+    float xn = x[i] + st;
+    x[i] = xn;
+    s1 += (double)st * st;
+    s2 += (double)xn * xn;
+    if (!isfinite(xn)) bad = 1.0;
+  }
+  __shared__ double red[3][32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+    bad = fmax(bad, __shfl_xor_sync(0xffffffffu, bad, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s1;
+    red[1][threadIdx.x >> 5] = s2;
+    red[2][threadIdx.x >> 5] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, c = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += red[0][k];
+      b += red[1][k];
+      c = fmax(c, red[2][k]);
+    }
+    part[3 * blockIdx.x + 0] = a;
+    part[3 * blockIdx.x + 1] = b;
+    part[3 * blockIdx.x + 2] = c;
+  }
+}
+
+// Deterministic sum of per-block partials: out[k] = sum_b part[stride*b + k] (k < stride),
+// the last component combined with max (flags).
+__global__ void k_reduce_partials(const double* __restrict__ part, int nb, int stride, int maxlast,
+                                  double* __restrict__ out) {
+  int k = threadIdx.x;
+  if (k >= stride) return;
+  double acc = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    double v = part[(int64_t)stride * b + k];
+    acc = (maxlast && k == stride - 1) ? fmax(acc, v) : acc + v;
+  }
+  out[k] = acc;
+}
+
+__global__ void k_dot_self(const float* __restrict__ x, int64_t n, double* __restrict__ part) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += (double)x[i] * x[i];
+  __shared__ double red[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_check_finite(const float* __restrict__ v, int64_t n, int* __restrict__ flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(v[i])) *flag = 1;
+}
+
+// Full objective: per cell, all I_N rows: sum (<A_N[i], Y[c]> - b[c, i])^2 in FP64.
+__global__ void k_full_obj(const float* __restrict__ Y, const float* __restrict__ AT, const float* __restrict__ b,
+                           int64_t ncell, int IT, int RT, double* __restrict__ part) {
+  double acc = 0.0;
+  const int64_t total = ncell * IT;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = e / IT;
+    int i = (int)(e - c * IT);
+    float u = 0.f;
+    for (int r = 0; r < RT; ++r) u = fmaf(__ldg(&AT[(int64_t)i * RT + r]), __ldg(&Y[c * RT + r]), u);
+    double d = (double)u - (double)b[e];
+    acc += d * d;
+  }
+  __shared__ double red[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    part[blockIdx.x] = t;
+  }
+}
+
+int grid_cap(kr_ctx* ctx, int64_t work, int block, int per_sm) {
+  int64_t g = (work + block - 1) / block;
+  int64_t cap = (int64_t)ctx->num_sms * per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+int rt_pad(int RT) {
+  if (RT <= 4) return 4;
+  if (RT <= 8) return 8;
+  if (RT <= 16) return 16;
+  if (RT <= 32) return 32;
+  return 64;
+}
+
+template <int RTP>
+kr_status launch_resid_t(kr_ctx* ctx, const ResidArgs& a, int grid) {
+  size_t smemA = (size_t)a.IT * RTP * sizeof(float);
+  size_t smemI = (size_t)a.IT * sizeof(float);
+  if (smemA + smemI <= ctx->smem_optin) {
+    KR_CUDA(ctx, cudaFuncSetAttribute(k_resid<RTP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(smemA + smemI)));
+    KR_LAUNCH(ctx, (k_resid<RTP, true>), grid, 256, smemA + smemI, a);
+  } else {
+    KR_CUDA(ctx, cudaFuncSetAttribute(k_resid<RTP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemI));
+    KR_LAUNCH(ctx, (k_resid<RTP, false>), grid, 256, smemI, a);
+  }
+  return KR_OK;
+}
+
+}  // namespace
+
+int kr_resid_blocks(kr_ctx* ctx) { return ctx->num_sms * 2; }
+
+kr_status kr_sketch_resid(kr_ctx* ctx, const kr_sketch* sk, const float* AT, int RT, const float* Y, float* W,
+                          double* obj_partial, int nblocks) {
+  ResidArgs a;
+  a.cell_start = sk->cell_start;
+  a.cell_nd = sk->cell_nd;
+  a.ent = sk->ent;
+  a.bt = sk->bt;
+  a.cell_w = sk->cell_w;
+  a.invpT = sk->invpT;
+  a.AT = AT;
+  a.IT = sk->IT;
+  a.RT = RT;
+  a.Y = Y;
+  a.W = W;
+  a.ncell = sk->ncell;
+  a.obj_partial = obj_partial;
+  switch (rt_pad(RT)) {
+    case 4: return launch_resid_t<4>(ctx, a, nblocks);
+    case 8: return launch_resid_t<8>(ctx, a, nblocks);
+    case 16: return launch_resid_t<16>(ctx, a, nblocks);
+    case 32: return launch_resid_t<32>(ctx, a, nblocks);
+    default: return launch_resid_t<64>(ctx, a, nblocks);
+  }
+}
+
+// ------------------------------------------------------------------ the solver
+
+namespace {
+
+struct IterBufs {
+  float* x;      // R
+  float* Y;      // ncell x RT
+  float* W;      // ncell x RT
+  float* g;      // R
+  float* d;      // R
+  float* t0;     // max intermediate
+  float* t1;     // max intermediate
+  double* part;  // partials (3 * nblk)
+  double* red;   // 4 doubles
+};
+
+int64_t max_intermediate(const Modes& m) {
+  // forward: dims R -> (I_0..I_{N-2}, R_{N-1}); backward: the reverse; precond: R
+  int64_t mx = kr_prod_R(m);
+  int64_t cur = mx;
+  for (int n = 0; n < m.N - 1; ++n) {
+    cur = cur / m.R[n] * m.I[n];
+    if (cur > mx) mx = cur;
+  }
+  return mx;
+}
+
+// Forward sampled pass at x: Y, then the residual kernel (W and objective partials).
+kr_status forward_resid(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const IterBufs& bf, int nblk) {
+  const int N = m.N;
+  int din[KR_MAX_MODES], dout[KR_MAX_MODES], tr[KR_MAX_MODES];
+  const float* B[KR_MAX_MODES];
+  for (int n = 0; n < N; ++n) {
+    din[n] = m.R[n];
+    dout[n] = (n < N - 1) ? m.I[n] : m.R[n];
+    B[n] = (n < N - 1) ? m.A[n] : nullptr;
+    tr[n] = 0;
+  }
+  KR_TRY(kr_kron_apply2(ctx, N, din, dout, B, tr, bf.x, bf.Y, bf.t0, bf.t1));
+  return kr_sketch_resid(ctx, sk, m.A[N - 1], m.R[N - 1], bf.Y, bf.W, bf.part, nblk);
+}
+
+kr_status backward(kr_ctx* ctx, const Modes& m, const IterBufs& bf) {
+  const int N = m.N;
+  int din[KR_MAX_MODES], dout[KR_MAX_MODES], tr[KR_MAX_MODES];
+  const float* B[KR_MAX_MODES];
+  for (int n = 0; n < N; ++n) {
+    din[n] = (n < N - 1) ? m.I[n] : m.R[n];
+    dout[n] = m.R[n];
+    B[n] = (n < N - 1) ? m.A[n] : nullptr;
+    tr[n] = 1;  // A^T from the stored I x R array
+  }
+  return kr_kron_apply2(ctx, N, din, dout, B, tr, bf.W, bf.g, bf.t0, bf.t1);
+}
+
+struct SolveCfg {
+  double lambda, eps, alpha, tol;
+  int max_iter;
+  int64_t s;
+};
+
+enum StepCheck { STEP_CONTINUE, STEP_CONVERGED, STEP_FLOOR, STEP_DIVERGED, STEP_NONFINITE };
+
+// Stopping rule of the Richardson loop ("until convergence" in Alg. 2 and Alg. 3):
+// converged when ||step|| <= tol ||x||; stalled at the FP32 rounding floor when no new
+// minimum step was seen for 8 iterations and the smallest relative step is within
+// 100 tol; diverged when the step grew 3 times in a row and exceeds 16x its minimum.
+// h = {||step||^2, ||x||^2, non-finite flag}.
+StepCheck step_check(const double* h, double tol, double* prev_step, double* min_step, double* min_rel, int* grow,
+                     int* since_min, double* rel_out) {
+  const double step = sqrt(h[0]), xn = sqrt(h[1]);
+  if (h[2] != 0.0 || !isfinite(step) || !isfinite(xn)) return STEP_NONFINITE;
+  const double rel = xn > 0.0 ? step / xn : (step == 0.0 ? 0.0 : INFINITY);
+  *rel_out = rel;
+  if (rel <= tol) return STEP_CONVERGED;
+  if (step < *min_step) {
+    *min_step = step;
+    *since_min = 0;
+  } else {
+    ++*since_min;
+  }
+  if (rel < *min_rel) *min_rel = rel;
+  *grow = (step > *prev_step) ? *grow + 1 : 0;
+  *prev_step = step;
+  if (*grow >= 3 && step > 16.0 * *min_step) return STEP_DIVERGED;
+  if (*since_min >= 8 && *min_rel <= 100.0 * tol) return STEP_FLOOR;
+  return STEP_CONTINUE;
+}
+
+}  // namespace
+
+// Core Alg. 2 solve on device-resident inputs. Timings go to rep->t_ms if rep != NULL.
+kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const SolveCfg& cfg, uint64_t seed,
+                          uint64_t call_id, float* x_out, kr_report* rep) {
+  const int N = m.N;
+  const int64_t R = kr_prod_R(m);
+  const int RT = m.R[N - 1];
+  const int nblk = kr_resid_blocks(ctx);
+  KR_TRY(kr_sketch_check(ctx, m, cfg.s));
+  kr_sketch sk;
+  kr_sketch_setup(&sk, m, cfg.s);
+  const int64_t ncell = sk.ncell;
+  const int64_t mx = max_intermediate(m);
+  Need nd;
+  kr_tables_need(m, cfg.lambda > 0.0, nd);
+  kr_sketch_own_need(&sk, nd);
+  nd.add<float>(ncell * RT);  // Y
+  nd.add<float>(ncell * RT);  // W
+  nd.add<float>(R);           // g
+  nd.add<float>(R);           // d
+  nd.add<float>(mx);          // t0
+  nd.add<float>(mx);          // t1
+  nd.add<double>(3 * (size_t)(nblk > 1024 ? nblk : 1024));
+  nd.add<double>(4);
+  size_t before_scratch = nd.off;
+  kr_sketch_scratch_need(cfg.s, ncell, nd);
+  KR_TRY(kr_ws_reserve(ctx, nd.off));
+  KR_TRY(kr_hbuf_reserve(ctx, 4096));
+  Carve cv(ctx->ws, ctx->ws_size);
+  cudaEvent_t* ev = ctx->ev;
+  KR_CUDA(ctx, cudaEventRecord(ev[0], ctx->stream));
+  FactorTables t;
+  KR_TRY(kr_tables_build(ctx, m, cfg.lambda > 0.0, cv, t, true));
+  KR_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
+  kr_sketch_layout(&sk, cv);
+  IterBufs bf;
+  bf.x = x_out;
+  bf.Y = cv.take<float>(ncell * RT);
+  bf.W = cv.take<float>(ncell * RT);
+  bf.g = cv.take<float>(R);
+  bf.d = cv.take<float>(R);
+  bf.t0 = cv.take<float>(mx);
+  bf.t1 = cv.take<float>(mx);
+  bf.part = cv.take<double>(3 * (size_t)(nblk > 1024 ? nblk : 1024));
+  bf.red = cv.take<double>(4);
+  (void)before_scratch;
+  KR_TRY(kr_sketch_fill(ctx, m, t, b, seed, call_id, 0, &sk, cv));
+  KR_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
+  KR_CUDA(ctx, cudaMemsetAsync(bf.x, 0, sizeof(float) * R, ctx->stream));
+  KR_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
+  double* h = (double*)ctx->hbuf;
+  const int ublk = grid_cap(ctx, R, 256, 4);
+  int it = 0, grow = 0, converged = 0, since_min = 0;
+  double prev_step = INFINITY, rel = INFINITY, min_step = INFINITY, min_rel = INFINITY;
+  kr_status st = KR_OK;
+  for (it = 1; it <= cfg.max_iter; ++it) {
+    KR_TRY(forward_resid(ctx, m, &sk, bf, nblk));
+    KR_TRY(backward(ctx, m, bf));
+    if (cfg.lambda > 0.0) KR_LAUNCH(ctx, k_sub_lambda_x, ublk, 256, 0, bf.g, bf.x, (float)cfg.lambda, R);
+    KR_TRY(kr_precond_apply(ctx, t, cfg.lambda, bf.g, bf.d, bf.t0, bf.t1));
+    KR_LAUNCH(ctx, k_update, ublk, 256, 0, bf.x, bf.d, (float)cfg.alpha, R, bf.part);
+    KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, bf.part, ublk, 3, 1, bf.red);
+    KR_CUDA(ctx, cudaMemcpyAsync(h, bf.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    StepCheck sc = step_check(h, cfg.tol, &prev_step, &min_step, &min_rel, &grow, &since_min, &rel);
+    if (sc == STEP_NONFINITE) {
+      st = kr_fail(ctx, KR_ENONFINITE, "Richardson iterate became non-finite at iteration %d", it);
+      break;
+    }
+    if (sc == STEP_DIVERGED) {
+      st = kr_fail(ctx, KR_EDIVERGED, "Richardson step grew 3 times in a row past 16x its minimum (iteration %d)", it);
+      break;
+    }
+    if (sc == STEP_CONVERGED || sc == STEP_FLOOR) {
+      converged = sc == STEP_CONVERGED ? 1 : 2;
+      break;
+    }
+  }
+  if (it > cfg.max_iter) it = cfg.max_iter;
+  KR_CUDA(ctx, cudaEventRecord(ev[4], ctx->stream));
+  // final sampled objective at the returned x (FP64 accumulation)
+  KR_TRY(forward_resid(ctx, m, &sk, bf, nblk));
+  KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, bf.part, nblk, 1, 0, bf.red);
+  KR_LAUNCH(ctx, k_dot_self, ublk, 256, 0, bf.x, R, bf.part + 1024);
+  KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, bf.part + 1024, ublk, 1, 0, bf.red + 1);
+  KR_CUDA(ctx, cudaMemcpyAsync(h, bf.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  KR_CUDA(ctx, cudaEventRecord(ev[5], ctx->stream));
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (rep) {
+    rep->iters = it;
+    rep->converged = converged;
+    rep->s = cfg.s;
+    rep->distinct = sk.distinct;
+    rep->obj_sampled = h[0] + cfg.lambda * h[1];
+    rep->rel_update = rel;
+    float ms;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]); rep->t_ms[0] = ms;
+    cudaEventElapsedTime(&ms, ev[1], ev[2]); rep->t_ms[1] = ms;  // sample + group + gather
+    rep->t_ms[2] = 0.f;
+    cudaEventElapsedTime(&ms, ev[2], ev[3]); rep->t_ms[3] = ms;
+    cudaEventElapsedTime(&ms, ev[3], ev[4]); rep->t_ms[4] = ms;
+    cudaEventElapsedTime(&ms, ev[4], ev[5]); rep->t_ms[5] = ms;
+    cudaEventElapsedTime(&ms, ev[0], ev[5]); rep->t_ms[7] = ms;
+  }
+  if (st != KR_OK) return st;
+  if (!converged) return kr_fail(ctx, KR_ENOTCONV, "no convergence within %d iterations (rel step %.3e)", cfg.max_iter, rel);
+  return KR_OK;
+}
+
+namespace {
+
+int64_t default_samples(const kr_opts* o, int64_t R) {
+  if (o->num_samples > 0) return o->num_samples;
+  double c = o->sample_scale > 0 ? o->sample_scale : 4.0;
+  if (R <= 1) return 1;
+  double v = ceil(c * (double)R * log((double)R) / o->eps);
+  return v < 1 ? 1 : (int64_t)v;
+}
+
+kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr_opts* o, float* x, kr_report* rep,
+                      double lambda) {
+  if (!ctx) return KR_EINVAL;
+  if (!o || !b || !x) return kr_fail(ctx, KR_EINVAL, "solver: null opts, b or x");
+  Modes m;
+  KR_TRY(kr_check_factors(ctx, f, &m));
+  if (!(o->eps > 0.0 && o->eps < 1.0)) return kr_fail(ctx, KR_EINVAL, "solver: eps=%g outside (0,1)", o->eps);
+  if (!(lambda >= 0.0) || !isfinite(lambda)) return kr_fail(ctx, KR_EINVAL, "solver: lambda must be finite and >= 0");
+  SolveCfg cfg;
+  cfg.lambda = lambda;
+  cfg.eps = o->eps;
+  cfg.alpha = o->step > 0 ? o->step : 1.0 - sqrt(o->eps);
+  cfg.tol = o->tol > 0 ? o->tol : 1e-7;
+  cfg.max_iter = o->max_iter > 0 ? o->max_iter : 100;
+  const int64_t R = kr_prod_R(m), I = kr_prod_I(m);
+  cfg.s = default_samples(o, R);
+  if (rep) *rep = kr_report{};
+  if (!o->host_io) return kr_solve_device(ctx, m, b, cfg, o->seed, o->call_id, x, rep);
+  // host buffers: copy factors and b in, x out, inside the call
+  cudaEvent_t e0 = ctx->ev[6], e1 = ctx->ev[7];
+  size_t bytes = 0;
+  for (int n = 0; n < m.N; ++n) bytes += ((size_t)m.I[n] * m.R[n] * 4 + 255) & ~size_t(255);
+  bytes += ((size_t)I * 4 + 255) & ~size_t(255);
+  bytes += ((size_t)R * 4 + 255) & ~size_t(255);
+  char* dev = nullptr;
+  KR_CUDA(ctx, cudaMallocAsync((void**)&dev, bytes, ctx->stream));
+  KR_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+  Carve cv(dev, bytes);
+  Modes md = m;
+  for (int n = 0; n < m.N; ++n) {
+    float* a = cv.take<float>((size_t)m.I[n] * m.R[n]);
+    KR_CUDA(ctx, cudaMemcpyAsync(a, m.A[n], sizeof(float) * m.I[n] * m.R[n], cudaMemcpyHostToDevice, ctx->stream));
+    md.A[n] = a;
+  }
+  float* bd = cv.take<float>(I);
+  KR_CUDA(ctx, cudaMemcpyAsync(bd, b, sizeof(float) * I, cudaMemcpyHostToDevice, ctx->stream));
+  float* xd = cv.take<float>(R);
+  kr_status st = kr_solve_device(ctx, md, bd, cfg, o->seed, o->call_id, xd, rep);
+  if (st == KR_OK || st == KR_ENOTCONV) {
+    KR_CUDA(ctx, cudaMemcpyAsync(x, xd, sizeof(float) * R, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  KR_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+  cudaFreeAsync(dev, ctx->stream);
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (rep) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    rep->t_ms[6] = ms - rep->t_ms[7];
+    rep->t_ms[7] = ms;
+  }
+  return st;
+}
+
+}  // namespace
+
+extern "C" kr_status kron_regress(kr_ctx* ctx, const kr_factors* f, const float* b, const kr_opts* opts, float* x,
+                                  kr_report* report) {
+  return solve_entry(ctx, f, b, opts, x, report, 0.0);
+}
+
+extern "C" kr_status kron_ridge(kr_ctx* ctx, const kr_factors* f, const float* b, const kr_opts* opts, float* x,
+                                kr_report* report) {
+  if (!ctx) return KR_EINVAL;
+  if (!opts || !(opts->lambda > 0.0)) return kr_fail(ctx, KR_EINVAL, "kron_ridge: opts->lambda must be > 0");
+  return solve_entry(ctx, f, b, opts, x, report, opts->lambda);
+}
+
+extern "C" kr_status kron_ridge_batched(kr_ctx* ctx, int32_t nprob, const kr_factors* probs, const float* const b[],
+                                        const kr_opts* opts, float* const x[], kr_report* reports) {
+  if (!ctx) return KR_EINVAL;
+  if (nprob < 0 || (nprob > 0 && (!probs || !b || !x || !opts)))
+    return kr_fail(ctx, KR_EINVAL, "kron_ridge_batched: bad arguments");
+  kr_status worst = KR_OK;
+  for (int p = 0; p < nprob; ++p) {
+    kr_opts o = *opts;
+    o.call_id = opts->call_id + (uint64_t)p;
+    kr_status st = solve_entry(ctx, &probs[p], b[p], &o, x[p], reports ? &reports[p] : nullptr, opts->lambda);
+    if (st != KR_OK && st != KR_ENOTCONV) return st;
+    if (st != KR_OK) worst = st;
+  }
+  return worst;
+}
+
+extern "C" kr_status kron_sketch_residual(kr_ctx* ctx, const kr_sketch* sk, const kr_factors* f, const float* x,
+                                          float* g, double* obj) {
+  if (!ctx || !sk || !x || !g) return KR_EINVAL;
+  Modes m;
+  KR_TRY(kr_check_factors(ctx, f, &m));
+  if (m.N != sk->N) return kr_fail(ctx, KR_EINVAL, "kron_sketch_residual: N mismatch");
+  for (int n = 0; n < m.N; ++n)
+    if (m.I[n] != sk->I[n]) return kr_fail(ctx, KR_EINVAL, "kron_sketch_residual: I mismatch");
+  const int nblk = kr_resid_blocks(ctx);
+  const int64_t mx = max_intermediate(m);
+  const int RT = m.R[m.N - 1];
+  Need nd;
+  nd.add<float>(sk->ncell * RT);
+  nd.add<float>(sk->ncell * RT);
+  nd.add<float>(mx);
+  nd.add<float>(mx);
+  nd.add<double>(nblk);
+  nd.add<double>(4);
+  KR_TRY(kr_ws_reserve(ctx, nd.off));
+  KR_TRY(kr_hbuf_reserve(ctx, 4096));
+  Carve cv(ctx->ws, ctx->ws_size);
+  IterBufs bf;
+  bf.x = const_cast<float*>(x);
+  bf.Y = cv.take<float>(sk->ncell * RT);
+  bf.W = cv.take<float>(sk->ncell * RT);
+  bf.t0 = cv.take<float>(mx);
+  bf.t1 = cv.take<float>(mx);
+  bf.part = cv.take<double>(nblk);
+  bf.red = cv.take<double>(4);
+  bf.g = g;
+  bf.d = nullptr;
+  KR_TRY(forward_resid(ctx, m, sk, bf, nblk));
+  KR_TRY(backward(ctx, m, bf));
+  KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, bf.part, nblk, 1, 0, bf.red);
+  KR_CUDA(ctx, cudaMemcpyAsync(ctx->hbuf, bf.red, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (obj) *obj = *(double*)ctx->hbuf;
+  return KR_OK;
+}
+
+extern "C" kr_status kron_objective(kr_ctx* ctx, const kr_factors* f, const float* b, const float* x, double lambda,
+                                    double* obj) {
+  if (!ctx) return KR_EINVAL;
+  if (!b || !x || !obj) return kr_fail(ctx, KR_EINVAL, "kron_objective: null argument");
+  Modes m;
+  KR_TRY(kr_check_factors(ctx, f, &m));
+  const int N = m.N;
+  const int64_t R = kr_prod_R(m), mx = max_intermediate(m);
+  int64_t ncell = 1;
+  for (int n = 0; n < N - 1; ++n) ncell *= m.I[n];
+  const int RT = m.R[N - 1];
+  const int nblk = ctx->num_sms * 4;
+  Need nd;
+  nd.add<float>(ncell * RT);
+  nd.add<float>(mx);
+  nd.add<float>(mx);
+  nd.add<double>(nblk + 1024);
+  nd.add<double>(4);
+  KR_TRY(kr_ws_reserve(ctx, nd.off));
+  KR_TRY(kr_hbuf_reserve(ctx, 4096));
+  Carve cv(ctx->ws, ctx->ws_size);
+  float* Y = cv.take<float>(ncell * RT);
+  float* t0 = cv.take<float>(mx);
+  float* t1 = cv.take<float>(mx);
+  double* part = cv.take<double>(nblk + 1024);
+  double* red = cv.take<double>(4);
+  int din[KR_MAX_MODES], dout[KR_MAX_MODES], tr[KR_MAX_MODES];
+  const float* B[KR_MAX_MODES];
+  for (int n = 0; n < N; ++n) {
+    din[n] = m.R[n];
+    dout[n] = (n < N - 1) ? m.I[n] : m.R[n];
+    B[n] = (n < N - 1) ? m.A[n] : nullptr;
+    tr[n] = 0;
+  }
+  KR_TRY(kr_kron_apply2(ctx, N, din, dout, B, tr, x, Y, t0, t1));
+  KR_LAUNCH(ctx, k_full_obj, nblk, 256, 0, Y, m.A[N - 1], b, ncell, m.I[N - 1], RT, part);
+  KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, part, nblk, 1, 0, red);
+  const int ublk = grid_cap(ctx, R, 256, 4);
+  KR_LAUNCH(ctx, k_dot_self, ublk, 256, 0, x, R, part + nblk);
+  KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, part + nblk, ublk, 1, 0, red + 1);
+  KR_CUDA(ctx, cudaMemcpyAsync(ctx->hbuf, red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double* h = (double*)ctx->hbuf;
+  *obj = h[0] + lambda * h[1];
+  return KR_OK;
+}
+
+extern "C" kr_status tucker_als_sweep(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R, const float* X,
+                                      float* const A[], float* G, const kr_opts* opts, int32_t sweeps,
+                                      kr_report* report) {
+  (void)N; (void)I; (void)R; (void)X; (void)A; (void)G; (void)opts; (void)sweeps; (void)report;
+  if (!ctx) return KR_EINVAL;
+  return kr_fail(ctx, KR_ENOTIMPL, "tucker_als_sweep: not built yet");
+}
