@@ -165,6 +165,30 @@ KR_API kr_status kron_sample(kr_ctx* ctx, int32_t N, const int64_t* I, const dou
                       const double* const prob[], int64_t s, uint64_t seed, uint64_t call_id,
                       int32_t row, int32_t* idx, float* w);
 
+/* Allocation-free twin of kron_sample, for callers that must not allocate device
+ * memory: code that runs under a memory manager owning every byte of the GPU (a
+ * caching allocator with a fixed budget, where an extra cudaMalloc would fail or
+ * fragment its pool), and latency-critical paths that cannot afford cudaMalloc's
+ * device-wide synchronisation. The paper has no counterpart: this is a deployment
+ * entry point, not a step of the method.
+ * Inputs, outputs and the drawing rule are exactly those of kron_sample (outputs are
+ * identical). The one piece of scratch, the integer sampling thresholds
+ * ceil(cdf * 2^53), lives in a static device array of KR_NOALLOC_MAX_ROWS 64-bit
+ * entries (128 KB) that every GPU loading this library holds until the process exits.
+ * The call makes no device allocation and does not grow the context's workspace.
+ *  - sum over m of I[m] must not exceed KR_NOALLOC_MAX_ROWS; larger tables are
+ *    rejected with KR_EINVAL and a message naming the limit.
+ *  - The first call on a device looks up the array's device address (with the
+ *    context's device current); make that first call before any stream capture.
+ *  - Each call writes every threshold entry it reads before reading it, so nothing
+ *    left by an earlier call is used. All calls share the one array: calls whose work
+ *    overlaps on the GPU (other streams or host threads) race on it, so the caller
+ *    must keep them from overlapping. */
+#define KR_NOALLOC_MAX_ROWS 16384
+KR_API kr_status kron_sample_noalloc(kr_ctx* ctx, int32_t N, const int64_t* I, const double* const cdf[],
+                                     const double* const prob[], int64_t s, uint64_t seed,
+                                     uint64_t call_id, int32_t row, int32_t* idx, float* w);
+
 /* ---------------------------------------------------------------- a3 + a4 + a5 */
 
 /* Draw s rows of K (as kron_sample) and group them (Thm 4.4 proof: the support of S

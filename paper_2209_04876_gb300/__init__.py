@@ -21,7 +21,7 @@ STATUS = {0: "KR_OK", 1: "KR_EINVAL", 2: "KR_ENOMEM", 3: "KR_ECUDA", 4: "KR_ENON
 KERNEL_KINDS = {"resid": 0, "modeprod": 1, "sample": 2, "scatter": 3, "dedup": 4, "tables": 5, "vector": 6}
 EXPORTED = ["kr_create", "kr_destroy", "kr_set_stream", "kr_last_error", "kr_launch_count", "kr_timing_enable",
             "kr_timing_read", "kr_timing_reset", "kron_leverage",
-            "kron_sample", "kron_sketch", "kron_sketch_distinct", "kron_sketch_export", "kron_sketch_residual",
+            "kron_sample", "kron_sample_noalloc", "kron_sketch", "kron_sketch_distinct", "kron_sketch_export", "kron_sketch_residual",
             "kron_sketch_free", "kron_matmul", "kron_precond", "kron_objective", "kron_regress", "kron_ridge",
             "kron_ridge_batched", "tucker_als_sweep"]
 
@@ -82,6 +82,7 @@ def lib():
             "kr_timing_reset": (i32, [vp]),
             "kron_leverage": (i32, [vp, P(KrFactors), P(vp), P(vp), P(vp), P(i32)]),
             "kron_sample": (i32, [vp, i32, P(i64), P(vp), P(vp), i64, u64, u64, i32, vp, vp]),
+            "kron_sample_noalloc": (i32, [vp, i32, P(i64), P(vp), P(vp), i64, u64, u64, i32, vp, vp]),
             "kron_sketch": (i32, [vp, P(KrFactors), P(vp), P(vp), vp, i64, u64, u64, i32, P(vp)]),
             "kron_sketch_distinct": (i64, [vp]),
             "kron_sketch_export": (i32, [vp, vp, vp, vp, vp, vp]),
@@ -222,6 +223,25 @@ def kron_sample(cdfs, probs, s, seed, call_id, row=0, want_idx=True, want_w=True
     w = torch.empty(s, dtype=torch.float32, device=dev) if want_w else None
     st = lib().kron_sample(h, N, I, _ptr_array(cdfs), _ptr_array(probs) if probs is not None else None, int(s),
                            int(seed), int(call_id), int(row), _ptr(idx), _ptr(w))
+    _check(st, h)
+    return idx, w
+
+
+def kron_sample_noalloc(cdfs, probs, s, seed, call_id, row=0, idx=None, w=None):
+    """kron_sample for callers that cannot allocate device memory: the outputs are the
+    caller's (pass preallocated `idx` (s x N int32) / `w` (s float32) tensors, or let this
+    wrapper create them before the call), and the library's only scratch is a fixed
+    static device array (sum of table sizes <= 16384 rows)."""
+    h = context()
+    N = len(cdfs)
+    I = (ctypes.c_int64 * N)(*[c.shape[0] for c in cdfs])
+    dev = cdfs[0].device
+    if idx is None:
+        idx = torch.empty((s, N), dtype=torch.int32, device=dev)
+    if w is None and probs is not None:
+        w = torch.empty(s, dtype=torch.float32, device=dev)
+    st = lib().kron_sample_noalloc(h, N, I, _ptr_array(cdfs), _ptr_array(probs) if probs is not None else None,
+                                   int(s), int(seed), int(call_id), int(row), _ptr(idx), _ptr(w))
     _check(st, h)
     return idx, w
 

@@ -494,3 +494,70 @@ extern "C" void kron_sketch_free(kr_sketch* sk) {
   }
   delete sk;
 }
+
+// ------------------------------------------------------------------ allocation-free sampling
+
+#include <mutex>
+
+// Scratch of kron_sample_noalloc: integer thresholds of the caller's CDF tables.
+static __device__ __align__(256) uint64_t kr_noalloc_thr[KR_NOALLOC_MAX_ROWS];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex noalloc_mu;
+uint64_t* noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of kr_noalloc_thr on the current device, looked up once per device.
+kr_status noalloc_scratch(kr_ctx* ctx, uint64_t** out) {
+  int dev = -1;
+  KR_CUDA(ctx, cudaGetDevice(&dev));
+  if (dev != ctx->device) return kr_fail(ctx, KR_EINVAL, "kron_sample_noalloc: current device %d is not the context's device %d", dev, ctx->device);
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return kr_fail(ctx, KR_EINVAL, "kron_sample_noalloc: device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(noalloc_mu);
+  if (!noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, kr_noalloc_thr);
+    if (e != cudaSuccess || !p) return kr_fail_cuda(ctx, e, "cudaGetSymbolAddress(kr_noalloc_thr)", __FILE__, __LINE__);
+    noalloc_ptr[dev] = static_cast<uint64_t*>(p);
+  }
+  *out = noalloc_ptr[dev];
+  return KR_OK;
+}
+}  // namespace
+
+extern "C" kr_status kron_sample_noalloc(kr_ctx* ctx, int32_t N, const int64_t* I, const double* const cdf[],
+                                         const double* const prob[], int64_t s, uint64_t seed, uint64_t call_id,
+                                         int32_t row, int32_t* idx, float* w) {
+  if (!ctx) return KR_EINVAL;
+  if (N < 1 || N > KR_MAX_MODES || !I || !cdf) return kr_fail(ctx, KR_EINVAL, "kron_sample_noalloc: bad N or null arrays");
+  if (s < 1 || s >= (int64_t(1) << 31)) return kr_fail(ctx, KR_EINVAL, "kron_sample_noalloc: s outside [1, 2^31)");
+  if (row < 0 || row >= (1 << 24)) return kr_fail(ctx, KR_EINVAL, "kron_sample_noalloc: row outside [0, 2^24)");
+  if (w && !prob) return kr_fail(ctx, KR_EINVAL, "kron_sample_noalloc: weights need prob");
+  int64_t total = 0;
+  for (int n = 0; n < N; ++n) {
+    if (I[n] < 1 || I[n] > 65535 || !cdf[n])
+      return kr_fail(ctx, KR_EINVAL, "kron_sample_noalloc: bad I[%d] or cdf[%d]", n, n);
+    total += I[n];
+  }
+  if (total > KR_NOALLOC_MAX_ROWS)
+    return kr_fail(ctx, KR_EINVAL,
+                   "kron_sample_noalloc: the tables hold %lld rows in total, above the static scratch limit "
+                   "KR_NOALLOC_MAX_ROWS = %d (use kron_sample)",
+                   (long long)total, KR_NOALLOC_MAX_ROWS);
+  uint64_t* scratch = nullptr;
+  KR_TRY(noalloc_scratch(ctx, &scratch));
+  SampleModes sm = {};
+  sm.N = N;
+  int64_t off = 0;
+  for (int n = 0; n < N; ++n) {
+    sm.I[n] = (int)I[n];
+    sm.thr[n] = scratch + off;
+    sm.prob[n] = prob ? prob[n] : nullptr;
+    KR_LAUNCH(ctx, k_thr_from_cdf, grid_for(ctx, I[n], 256), 256, 0, cdf[n], scratch + off, (int)I[n]);
+    off += I[n];
+  }
+  KR_LAUNCH(ctx, k_sample_idx, grid_for(ctx, s, 256), 256, 0, sm, s, (uint32_t)seed, (uint32_t)(seed >> 32),
+            (uint32_t)row, (uint32_t)call_id, idx, w);
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return KR_OK;
+}
