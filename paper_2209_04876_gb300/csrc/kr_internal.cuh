@@ -171,6 +171,7 @@ struct kr_sketch {
   float* bt = nullptr;             // s: b~ at the same positions
   float* cell_w = nullptr;         // ncell: prod_{n<N-1} (1/p_n(i_n)) / s
   float* invpT = nullptr;          // IT: 1/p_{N-1}(i)
+  uint32_t* perm = nullptr;        // ncell: cells by decreasing distinct-row count (work balance)
   char* mem = nullptr;
 };
 
@@ -185,5 +186,12 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
                          uint64_t call_id, int row, kr_sketch* sk, Carve& cv);
 // Residual/gradient pass: W[c, :] = sum_j omega_j (b~_j - <a_T, Y[c]>) a_T; obj partials.
 kr_status kr_sketch_resid(kr_ctx* ctx, const kr_sketch* sk, const float* AT, int RT, const float* Y,
-                          float* W, double* obj_partial, int nblocks);
+                          float* W, double* obj_partial, int nblocks, int* used);
 int kr_resid_blocks(kr_ctx* ctx);
+
+// Exclusive scan of n u32 values (in may equal out); scratch carved from cv.
+void kr_scan_need(int64_t n, Need& nd);
+kr_status kr_scan_u32(kr_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n, Carve& cv);
+// perm = cells ordered by decreasing floor(log2(distinct rows)), stable (deterministic).
+void kr_perm_need(int64_t ncell, Need& nd);
+kr_status kr_balance_perm(kr_ctx* ctx, const uint32_t* nd, int64_t ncell, uint32_t* perm, Carve& cv);

@@ -15,65 +15,86 @@
 
 namespace {
 
-constexpr int TJ = 64, TN = 64, TK = 16;
+constexpr int TN = 64, TK = 16;
 
+// Tile: TJ rows of B (output index j) x 64 output columns n = p*Q + q, K staged in
+// chunks of 16 through shared memory. Each thread owns (TJ/16) x 4 outputs. The
+// (p, q) split of the columns a thread loads and stores is computed once, outside the
+// K loop.
+template <int TJ>
 __global__ void __launch_bounds__(256) k_mode_product(const float* __restrict__ in, float* __restrict__ out, int64_t P,
                                                        int K, int64_t Q, int J, const float* __restrict__ B, int trans) {
+  constexpr int RJ = TJ / 16;  // rows per thread
   __shared__ float Bs[TK][TJ + 4];
   __shared__ float Xs[TK][TN + 4];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int j0 = blockIdx.y * TJ;
   const int64_t n0 = (int64_t)blockIdx.x * TN;
   const int64_t NN = P * Q;
-  float acc[4][4] = {};
+  // input loads: every thread loads column nn = tid % 64 for k rows (tid / 64) + 4 i
+  const int ld_nn = threadIdx.x & (TN - 1);
+  const int ld_kk = threadIdx.x >> 6;  // 0..3
+  int64_t in_base = -1;
+  {
+    const int64_t n = n0 + ld_nn;
+    if (n < NN) {
+      const int64_t p = n / Q, q = n - p * Q;
+      in_base = p * K * Q + q;
+    }
+  }
+  // output columns of this thread
+  int64_t out_base[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int64_t n = n0 + tx * 4 + c;
+    out_base[c] = -1;
+    if (n < NN) {
+      const int64_t p = n / Q, q = n - p * Q;
+      out_base[c] = p * (int64_t)J * Q + q;
+    }
+  }
+  float acc[RJ][4];
+#pragma unroll
+  for (int a = 0; a < RJ; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
   for (int k0 = 0; k0 < K; k0 += TK) {
-    // B tile: Bs[kk][jj] = B[j0+jj, k0+kk]
     for (int e = threadIdx.x; e < TK * TJ; e += 256) {
       int kk, jj;
       if (trans) { jj = e % TJ; kk = e / TJ; } else { kk = e % TK; jj = e / TK; }
-      int j = j0 + jj, k = k0 + kk;
+      const int j = j0 + jj, k = k0 + kk;
       float v = 0.f;
       if (j < J && k < K) v = trans ? B[(int64_t)k * J + j] : B[(int64_t)j * K + k];
       Bs[kk][jj] = v;
     }
-    // input tile: Xs[kk][nn] = in[p, k0+kk, q] with n = n0+nn = p*Q + q
-    for (int e = threadIdx.x; e < TK * TN; e += 256) {
-      int nn = e % TN, kk = e / TN;
-      int64_t n = n0 + nn;
-      int k = k0 + kk;
-      float v = 0.f;
-      if (n < NN && k < K) {
-        int64_t p = n / Q, q = n - p * Q;
-        v = in[(p * K + k) * Q + q];
-      }
-      Xs[kk][nn] = v;
+#pragma unroll
+    for (int i = 0; i < TK / 4; ++i) {
+      const int kk = ld_kk + 4 * i;
+      const int k = k0 + kk;
+      Xs[kk][ld_nn] = (in_base >= 0 && k < K) ? in[in_base + (int64_t)k * Q] : 0.f;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
-      float bj[4], xn[4];
+      float bj[RJ], xn[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) bj[a] = Bs[kk][ty * 4 + a];
+      for (int a = 0; a < RJ; ++a) bj[a] = Bs[kk][ty * RJ + a];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) xn[a] = Xs[kk][tx * 4 + a];
+      for (int c = 0; c < 4; ++c) xn[c] = Xs[kk][tx * 4 + c];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < RJ; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(bj[a], xn[c], acc[a][c]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    int j = j0 + ty * 4 + a;
+  for (int a = 0; a < RJ; ++a) {
+    const int j = j0 + ty * RJ + a;
     if (j >= J) continue;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      int64_t n = n0 + tx * 4 + c;
-      if (n >= NN) continue;
-      int64_t p = n / Q, q = n - p * Q;
-      out[(p * J + j) * Q + q] = acc[a][c];
-    }
+    for (int c = 0; c < 4; ++c)
+      if (out_base[c] >= 0) out[out_base[c] + (int64_t)j * Q] = acc[a][c];
   }
 }
 
@@ -102,10 +123,15 @@ __global__ void k_diag_scale(float* __restrict__ x, int64_t total, DiagArgs da, 
 
 kr_status kr_mode_product(kr_ctx* ctx, const float* in, float* out, int64_t P, int K, int64_t Q, int J, const float* B,
                           int trans) {
-  int64_t NN = P * Q;
-  dim3 grid((unsigned)((NN + TN - 1) / TN), (unsigned)((J + TJ - 1) / TJ));
-  if (grid.x == 0 || grid.y == 0) return KR_OK;
-  KR_LAUNCH(ctx, k_mode_product, grid, 256, 0, in, out, P, K, Q, J, B, trans);
+  const int64_t NN = P * Q;
+  if (NN == 0 || J == 0) return KR_OK;
+  if (J <= 32) {
+    dim3 grid((unsigned)((NN + TN - 1) / TN), (unsigned)((J + 31) / 32));
+    KR_LAUNCH(ctx, k_mode_product<32>, grid, 256, 0, in, out, P, K, Q, J, B, trans);
+  } else {
+    dim3 grid((unsigned)((NN + TN - 1) / TN), (unsigned)((J + 63) / 64));
+    KR_LAUNCH(ctx, k_mode_product<64>, grid, 256, 0, in, out, P, K, Q, J, B, trans);
+  }
   return KR_OK;
 }
 

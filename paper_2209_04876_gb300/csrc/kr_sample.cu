@@ -132,28 +132,6 @@ __global__ void k_sample_keys(SampleModes sm, int64_t s, uint32_t k0, uint32_t k
   }
 }
 
-// Exclusive scan of n counters, single block of 1024 threads (n up to a few million).
-__global__ void k_scan_excl(const uint32_t* __restrict__ cnt, uint32_t* __restrict__ start, int64_t n) {
-  __shared__ uint32_t part[1024];
-  const int64_t per = (n + blockDim.x - 1) / blockDim.x;
-  const int64_t a = threadIdx.x * per, b = min(n, a + per);
-  uint32_t sum = 0;
-  for (int64_t i = a; i < b; ++i) sum += cnt[i];
-  part[threadIdx.x] = sum;
-  __syncthreads();
-  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-    uint32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  uint32_t run = part[threadIdx.x] - sum;
-  for (int64_t i = a; i < b; ++i) {
-    start[i] = run;
-    run += cnt[i];
-  }
-}
-
 // Scatter i_T of every draw into its cell's slot range.
 __global__ void k_scatter(const uint32_t* __restrict__ keys, int64_t s, uint32_t IT, const uint32_t* __restrict__ start,
                           uint32_t* __restrict__ cursor, uint16_t* __restrict__ slot) {
@@ -179,7 +157,7 @@ __global__ void k_scatter(const uint32_t* __restrict__ keys, int64_t s, uint32_t
 // Per cell (one warp): count table over i_T in shared memory, then emit the distinct
 // entries in increasing i_T order with their multiplicities, gather b, and the
 // per-cell weight prod_{n<N-1} 1/p_n(i_n) / s.
-constexpr int DEDUP_WARPS = 4;
+constexpr int DEDUP_WARPS = 8;
 constexpr int DEDUP_MAX_IT = 8192;
 
 __global__ void k_dedup(SampleModes sm, int64_t ncell, uint32_t IT, float inv_s, const uint32_t* __restrict__ start,
@@ -308,6 +286,7 @@ void kr_sketch_own_need(const kr_sketch* sk, Need& nd) {
   nd.add<float>(sk->s);
   nd.add<float>(sk->ncell);
   nd.add<float>(sk->IT);
+  nd.add<uint32_t>(sk->ncell);
 }
 
 void kr_sketch_layout(kr_sketch* sk, Carve& cv) {
@@ -317,6 +296,7 @@ void kr_sketch_layout(kr_sketch* sk, Carve& cv) {
   sk->bt = cv.take<float>(sk->s);
   sk->cell_w = cv.take<float>(sk->ncell);
   sk->invpT = cv.take<float>(sk->IT);
+  sk->perm = cv.take<uint32_t>(sk->ncell);
 }
 
 kr_status kr_sketch_check(kr_ctx* ctx, const Modes& m, int64_t s) {
@@ -344,12 +324,19 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   KR_CUDA(ctx, cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), ctx->stream));
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32), cid = (uint32_t)call_id;
   KR_LAUNCH(ctx, k_sample_keys, grid_for(ctx, s, 256), 256, 0, sm, s, k0, k1, (uint32_t)row, cid, keys, cnt);
-  KR_LAUNCH(ctx, k_scan_excl, 1, 1024, 0, cnt, sk->cell_start, ncell);
+  {
+    Carve sc = cv;  // scan scratch is transient
+    KR_TRY(kr_scan_u32(ctx, cnt, sk->cell_start, ncell, sc));
+  }
   KR_LAUNCH(ctx, k_scatter, grid_for(ctx, s, 256), 256, 0, keys, s, IT, sk->cell_start, cursor, slot);
   const size_t dsmem = (size_t)DEDUP_WARPS * IT * sizeof(uint32_t);
   KR_CUDA(ctx, cudaFuncSetAttribute(k_dedup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
-  KR_LAUNCH(ctx, k_dedup, grid_for(ctx, ncell, DEDUP_WARPS, 4), DEDUP_WARPS * 32, dsmem, sm, ncell, IT,
+  KR_LAUNCH(ctx, k_dedup, grid_for(ctx, ncell, DEDUP_WARPS, 8), DEDUP_WARPS * 32, dsmem, sm, ncell, IT,
             (float)(1.0 / (double)s), sk->cell_start, cnt, slot, b, sk->ent, sk->bt, sk->cell_nd, sk->cell_w);
+  {
+    Carve sc = cv;
+    KR_TRY(kr_balance_perm(ctx, sk->cell_nd, ncell, sk->perm, sc));
+  }
   KR_CUDA(ctx, cudaMemcpyAsync(sk->invpT, t.invp[N - 1], sizeof(float) * IT, cudaMemcpyDeviceToDevice, ctx->stream));
   KR_LAUNCH(ctx, k_sum_u32, grid_for(ctx, ncell, 256, 2), 256, 0, sk->cell_nd, ncell, dsum);
   KR_TRY(kr_hbuf_reserve(ctx, 4096));
@@ -365,6 +352,8 @@ void kr_sketch_scratch_need(int64_t s, int64_t ncell, Need& nd) {
   nd.add<uint32_t>(ncell);
   nd.add<uint16_t>(s);
   nd.add<unsigned long long>(1);
+  kr_scan_need(ncell, nd);
+  kr_perm_need(ncell, nd);
 }
 
 // ------------------------------------------------------------------ C ABI
@@ -476,10 +465,11 @@ extern "C" kr_status kron_sketch_export(kr_ctx* ctx, const kr_sketch* sk, int64_
   if (!ctx || !sk) return KR_EINVAL;
   Need nd;
   nd.add<uint32_t>(sk->ncell);
+  kr_scan_need(sk->ncell, nd);
   KR_TRY(kr_ws_reserve(ctx, nd.off));
   Carve cv(ctx->ws, ctx->ws_size);
   uint32_t* off = cv.take<uint32_t>(sk->ncell);
-  KR_LAUNCH(ctx, k_scan_excl, 1, 1024, 0, sk->cell_nd, off, sk->ncell);
+  KR_TRY(kr_scan_u32(ctx, sk->cell_nd, off, sk->ncell, cv));
   KR_LAUNCH(ctx, k_export, grid_for(ctx, sk->ncell, 128), 128, 0, sk->ncell, (uint32_t)sk->IT, sk->cell_start,
             sk->cell_nd, off, sk->ent, sk->bt, sk->cell_w, sk->invpT, keys, counts, omega, btilde);
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

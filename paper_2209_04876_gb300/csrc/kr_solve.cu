@@ -25,7 +25,8 @@ struct ResidArgs {
   const float* bt;
   const float* cell_w;
   const float* invpT;
-  const float* AT;  // IT x RT
+  const uint32_t* perm;  // processing order of the cells (may be null: identity)
+  const float* AT;       // IT x RT
   int IT, RT;
   const float* Y;   // ncell x RT
   float* W;         // ncell x RT
@@ -33,78 +34,112 @@ struct ResidArgs {
   double* obj_partial;  // gridDim.x
 };
 
-// G = RTP/4 lanes per cell, each lane owns 4 consecutive columns; A_T in shared
-// memory (zero-padded to RTP columns) when it fits, else read through L1.
+// Lanes per cell and columns per lane for a padded R_N.
+template <int RTP>
+struct ResidShape {
+  static constexpr int COLS = RTP >= 8 ? 8 : 4;
+  static constexpr int G = RTP / COLS;  // lanes per cell
+  static constexpr int CPW = 32 / G;    // cells per warp
+  static constexpr int LDA = RTP + 4;   // shared-memory row stride of A_N (floats)
+};
+constexpr int RESID_U = 4;  // sampled rows in flight per lane group
+
+// One lane group per cell: lane g owns columns [g*COLS, (g+1)*COLS) of Y[c] and W[c].
+// For RESID_U rows at a time: load (entry, b~) for all of them first, then the dot
+// products, the group reductions and the axpys, so several loads are in flight.
+// Cells are taken in `perm` order (similar distinct-row counts share a warp).
 template <int RTP, bool SMEM_A>
 __global__ void __launch_bounds__(256) k_resid(ResidArgs a) {
-  constexpr int G = RTP / 4;
-  constexpr int CPW = 32 / G;
-  extern __shared__ float4 sA4[];
-  float* sInvp = reinterpret_cast<float*>(sA4 + (SMEM_A ? (size_t)a.IT * G : 0));
+  using S = ResidShape<RTP>;
+  constexpr int COLS = S::COLS, G = S::G, CPW = S::CPW, LDA = S::LDA;
+  extern __shared__ float4 sm4[];
+  float* sA = reinterpret_cast<float*>(sm4);
+  float* sInvp = sA + (SMEM_A ? (size_t)a.IT * LDA : 0);
   const int RT = a.RT;
   if (SMEM_A) {
-    for (int e = threadIdx.x; e < a.IT * RTP; e += blockDim.x) {
-      int i = e / RTP, r = e % RTP;
-      reinterpret_cast<float*>(sA4)[e] = r < RT ? a.AT[(int64_t)i * RT + r] : 0.f;
+    for (int e = threadIdx.x; e < a.IT * LDA; e += blockDim.x) {
+      int i = e / LDA, r = e - i * LDA;
+      sA[e] = r < RT ? a.AT[(int64_t)i * RT + r] : 0.f;
     }
   }
   for (int i = threadIdx.x; i < a.IT; i += blockDim.x) sInvp[i] = a.invpT[i];
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int g = lane % G, slot = lane / G;
+  const int c0col = g * COLS;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   double obj = 0.0;
-  for (int64_t c0 = gw * CPW; c0 < a.ncell; c0 += warps * CPW) {
-    const int64_t c = c0 + slot;
-    const bool live = c < a.ncell;
+  for (int64_t q0 = gw * CPW; q0 < a.ncell; q0 += warps * CPW) {
+    const int64_t q = q0 + slot;
+    const bool live = q < a.ncell;
+    const int64_t c = live ? (a.perm ? (int64_t)a.perm[q] : q) : 0;
     const uint32_t n = live ? a.cell_nd[c] : 0u;
     const uint32_t base = live ? a.cell_start[c] : 0u;
     const float cw = live ? a.cell_w[c] : 0.f;
-    float y[4];
+    float y[COLS], w[COLS];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      int r = 4 * g + k;
+    for (int k = 0; k < COLS; ++k) {
+      int r = c0col + k;
       y[k] = (live && r < RT) ? a.Y[c * RT + r] : 0.f;
+      w[k] = 0.f;
     }
-    float w[4] = {0.f, 0.f, 0.f, 0.f};
     float objc = 0.f;
     uint32_t nmax = n;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, off));
-    for (uint32_t j = 0; j < nmax; ++j) {
-      const bool act = j < n;
-      const uint32_t e = act ? a.ent[base + j] : 0u;
-      const float bj = act ? a.bt[base + j] : 0.f;
-      const int it = (int)(e & 0xFFFFu);
-      float av[4];
-      if (SMEM_A) {
-        float4 v = sA4[it * G + g];
-        av[0] = v.x; av[1] = v.y; av[2] = v.z; av[3] = v.w;
-      } else {
+    for (uint32_t j = 0; j < nmax; j += RESID_U) {
+      uint32_t e[RESID_U];
+      float bj[RESID_U];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          int r = 4 * g + k;
-          av[k] = r < RT ? __ldg(&a.AT[(int64_t)it * RT + r]) : 0.f;
-        }
+      for (int u = 0; u < RESID_U; ++u) {
+        const bool act = j + u < n;
+        e[u] = act ? __ldg(&a.ent[base + j + u]) : 0u;
+        bj[u] = act ? __ldg(&a.bt[base + j + u]) : 0.f;
       }
-      float part = av[0] * y[0];
-      part = fmaf(av[1], y[1], part);
-      part = fmaf(av[2], y[2], part);
-      part = fmaf(av[3], y[3], part);
+      float av[RESID_U][COLS];
+      float part[RESID_U];
 #pragma unroll
-      for (int off = G / 2; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-      const float om = act ? (float)(e >> 16) * cw * sInvp[it] : 0.f;
-      const float res = bj - part;
-      const float rr = om * res;
+      for (int u = 0; u < RESID_U; ++u) {
+        const int it = (int)(e[u] & 0xFFFFu);
+        if (SMEM_A) {
+          const float4* row = reinterpret_cast<const float4*>(sA + (size_t)it * LDA + c0col);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) w[k] = fmaf(rr, av[k], w[k]);
-      objc = fmaf(rr, res, objc);
+          for (int v = 0; v < COLS / 4; ++v) {
+            float4 t = row[v];
+            av[u][4 * v + 0] = t.x; av[u][4 * v + 1] = t.y; av[u][4 * v + 2] = t.z; av[u][4 * v + 3] = t.w;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < COLS; ++k) {
+            int r = c0col + k;
+            av[u][k] = r < RT ? __ldg(&a.AT[(int64_t)it * RT + r]) : 0.f;
+          }
+        }
+        float p = av[u][0] * y[0];
+#pragma unroll
+        for (int k = 1; k < COLS; ++k) p = fmaf(av[u][k], y[k], p);
+        part[u] = p;
+      }
+#pragma unroll
+      for (int off = G / 2; off > 0; off >>= 1)
+#pragma unroll
+        for (int u = 0; u < RESID_U; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], off);
+#pragma unroll
+      for (int u = 0; u < RESID_U; ++u) {
+        const int it = (int)(e[u] & 0xFFFFu);
+        const float om = (float)(e[u] >> 16) * cw * sInvp[it];  // 0 for padding rows (count 0)
+        const float res = bj[u] - part[u];
+        const float rr = om * res;
+#pragma unroll
+        for (int k = 0; k < COLS; ++k) w[k] = fmaf(rr, av[u][k], w[k]);
+        objc = fmaf(rr, res, objc);
+      }
     }
     if (live) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        int r = 4 * g + k;
+      for (int k = 0; k < COLS; ++k) {
+        int r = c0col + k;
         if (r < RT) a.W[c * RT + r] = w[k];
       }
       if (g == 0) obj += (double)objc;
@@ -245,27 +280,40 @@ int rt_pad(int RT) {
   return 64;
 }
 
+// Launches at most `grid` blocks (resident blocks per SM x SMs); *used = blocks launched.
 template <int RTP>
-kr_status launch_resid_t(kr_ctx* ctx, const ResidArgs& a, int grid) {
-  size_t smemA = (size_t)a.IT * RTP * sizeof(float);
+kr_status launch_resid_t(kr_ctx* ctx, const ResidArgs& a, int grid, int* used) {
+  size_t smemA = (size_t)a.IT * ResidShape<RTP>::LDA * sizeof(float);
   size_t smemI = (size_t)a.IT * sizeof(float);
+  // grid = resident blocks per SM x SMs (a persistent, grid-stride sweep over the cells);
+  // `grid` is the cap that sizes the objective partials
+  int per_sm = 1;
   if (smemA + smemI <= ctx->smem_optin) {
     KR_CUDA(ctx, cudaFuncSetAttribute(k_resid<RTP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(smemA + smemI)));
-    KR_LAUNCH(ctx, (k_resid<RTP, true>), grid, 256, smemA + smemI, a);
-  } else {
-    KR_CUDA(ctx, cudaFuncSetAttribute(k_resid<RTP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemI));
-    KR_LAUNCH(ctx, (k_resid<RTP, false>), grid, 256, smemI, a);
+    KR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid<RTP, true>, 256, smemA + smemI));
+    int g = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
+    if (g > grid) g = grid;
+    KR_LAUNCH(ctx, (k_resid<RTP, true>), g, 256, smemA + smemI, a);
+    *used = g;
+    return KR_OK;
   }
+  KR_CUDA(ctx, cudaFuncSetAttribute(k_resid<RTP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemI));
+  KR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid<RTP, false>, 256, smemI));
+  int g = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
+  if (g > grid) g = grid;
+  KR_LAUNCH(ctx, (k_resid<RTP, false>), g, 256, smemI, a);
+  *used = g;
+  return KR_OK;
   return KR_OK;
 }
 
 }  // namespace
 
-int kr_resid_blocks(kr_ctx* ctx) { return ctx->num_sms * 2; }
+int kr_resid_blocks(kr_ctx* ctx) { return ctx->num_sms * 4; }
 
 kr_status kr_sketch_resid(kr_ctx* ctx, const kr_sketch* sk, const float* AT, int RT, const float* Y, float* W,
-                          double* obj_partial, int nblocks) {
+                          double* obj_partial, int nblocks, int* used) {
   ResidArgs a;
   a.cell_start = sk->cell_start;
   a.cell_nd = sk->cell_nd;
@@ -273,6 +321,7 @@ kr_status kr_sketch_resid(kr_ctx* ctx, const kr_sketch* sk, const float* AT, int
   a.bt = sk->bt;
   a.cell_w = sk->cell_w;
   a.invpT = sk->invpT;
+  a.perm = sk->perm;
   a.AT = AT;
   a.IT = sk->IT;
   a.RT = RT;
@@ -281,11 +330,11 @@ kr_status kr_sketch_resid(kr_ctx* ctx, const kr_sketch* sk, const float* AT, int
   a.ncell = sk->ncell;
   a.obj_partial = obj_partial;
   switch (rt_pad(RT)) {
-    case 4: return launch_resid_t<4>(ctx, a, nblocks);
-    case 8: return launch_resid_t<8>(ctx, a, nblocks);
-    case 16: return launch_resid_t<16>(ctx, a, nblocks);
-    case 32: return launch_resid_t<32>(ctx, a, nblocks);
-    default: return launch_resid_t<64>(ctx, a, nblocks);
+    case 4: return launch_resid_t<4>(ctx, a, nblocks, used);
+    case 8: return launch_resid_t<8>(ctx, a, nblocks, used);
+    case 16: return launch_resid_t<16>(ctx, a, nblocks, used);
+    case 32: return launch_resid_t<32>(ctx, a, nblocks, used);
+    default: return launch_resid_t<64>(ctx, a, nblocks, used);
   }
 }
 
@@ -316,8 +365,9 @@ int64_t max_intermediate(const Modes& m) {
   return mx;
 }
 
-// Forward sampled pass at x: Y, then the residual kernel (W and objective partials).
-kr_status forward_resid(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const IterBufs& bf, int nblk) {
+// Forward sampled pass at x: Y, then the residual kernel (W and objective partials;
+// *used = number of partials written).
+kr_status forward_resid(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const IterBufs& bf, int nblk, int* used) {
   const int N = m.N;
   int din[KR_MAX_MODES], dout[KR_MAX_MODES], tr[KR_MAX_MODES];
   const float* B[KR_MAX_MODES];
@@ -328,7 +378,7 @@ kr_status forward_resid(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const 
     tr[n] = 0;
   }
   KR_TRY(kr_kron_apply2(ctx, N, din, dout, B, tr, bf.x, bf.Y, bf.t0, bf.t1));
-  return kr_sketch_resid(ctx, sk, m.A[N - 1], m.R[N - 1], bf.Y, bf.W, bf.part, nblk);
+  return kr_sketch_resid(ctx, sk, m.A[N - 1], m.R[N - 1], bf.Y, bf.W, bf.part, nblk, used);
 }
 
 kr_status backward(kr_ctx* ctx, const Modes& m, const IterBufs& bf) {
@@ -435,7 +485,8 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   double prev_step = INFINITY, rel = INFINITY, min_step = INFINITY, min_rel = INFINITY;
   kr_status st = KR_OK;
   for (it = 1; it <= cfg.max_iter; ++it) {
-    KR_TRY(forward_resid(ctx, m, &sk, bf, nblk));
+    int used = 0;
+    KR_TRY(forward_resid(ctx, m, &sk, bf, nblk, &used));
     KR_TRY(backward(ctx, m, bf));
     if (cfg.lambda > 0.0) KR_LAUNCH(ctx, k_sub_lambda_x, ublk, 256, 0, bf.g, bf.x, (float)cfg.lambda, R);
     KR_TRY(kr_precond_apply(ctx, t, cfg.lambda, bf.g, bf.d, bf.t0, bf.t1));
@@ -460,8 +511,9 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   if (it > cfg.max_iter) it = cfg.max_iter;
   KR_CUDA(ctx, cudaEventRecord(ev[4], ctx->stream));
   // final sampled objective at the returned x (FP64 accumulation)
-  KR_TRY(forward_resid(ctx, m, &sk, bf, nblk));
-  KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, bf.part, nblk, 1, 0, bf.red);
+  int used = 0;
+  KR_TRY(forward_resid(ctx, m, &sk, bf, nblk, &used));
+  KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, bf.part, used, 1, 0, bf.red);
   KR_LAUNCH(ctx, k_dot_self, ublk, 256, 0, bf.x, R, bf.part + 1024);
   KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, bf.part + 1024, ublk, 1, 0, bf.red + 1);
   KR_CUDA(ctx, cudaMemcpyAsync(h, bf.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -612,9 +664,10 @@ extern "C" kr_status kron_sketch_residual(kr_ctx* ctx, const kr_sketch* sk, cons
   bf.red = cv.take<double>(4);
   bf.g = g;
   bf.d = nullptr;
-  KR_TRY(forward_resid(ctx, m, sk, bf, nblk));
+  int used = 0;
+  KR_TRY(forward_resid(ctx, m, sk, bf, nblk, &used));
   KR_TRY(backward(ctx, m, bf));
-  KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, bf.part, nblk, 1, 0, bf.red);
+  KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, bf.part, used, 1, 0, bf.red);
   KR_CUDA(ctx, cudaMemcpyAsync(ctx->hbuf, bf.red, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (obj) *obj = *(double*)ctx->hbuf;
