@@ -252,6 +252,22 @@ KR_API kr_status kron_ridge_batched(kr_ctx* ctx, int32_t nprob, const kr_factors
                              const float* const b[], const kr_opts* opts, float* const x[],
                              kr_report* reports);
 
+/* Alg. 3 FastFactorMatrixUpdate for mode n (App. C): every row i of X_(n) solves the
+ * penalised sketched problem in z = G_(n)^T y (Lemmas 5.1, 5.2) with its own sketch
+ * (Philox counter row i) over the modes m != n, Richardson-iterated with the Woodbury
+ * form of the unsampled preconditioner (standard sign), and row i of A[n] becomes
+ * (G_(n)^T)^+ z. The I[n] rows are solved together as one batch; the stopping rule
+ * is applied to the largest per-row relative step. opts->lambda is the L2 weight,
+ * w = (1 + 12/eps) prod_{m != n} sigma_max(A(m))^2. X: prod I floats; A[m]: I[m] x R[m];
+ * G: prod R floats (C-order); A[n] is overwritten. Needs R[n] <= prod_{m != n} R[m]
+ * (else KR_EINVAL), prod_{m != n} R[m] <= 24576 (else KR_ENOTIMPL) and a full-row-rank
+ * G_(n) (else KR_ERANK). The terms of the update that cancel in the row space of
+ * G_(n)^T (w z and G+ (w G z)) and the output rows are formed in FP64; the sampled terms
+ * and the preconditioner in FP32. */
+KR_API kr_status tucker_factor_update(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R,
+                                      const float* X, float* const A[], const float* G, int32_t n,
+                                      const kr_opts* opts, kr_report* report);
+
 /* TuckerALS (Alg. 1) with sampled factor updates (Alg. 3, fresh sketch per factor row,
  * Woodbury preconditioner) and sampled core updates (Alg. 2 with b = vec X).
  * X: prod I floats; A[n]: I[n] x R[n] floats (in/out); G: prod R floats (in/out).

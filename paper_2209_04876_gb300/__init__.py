@@ -23,7 +23,7 @@ EXPORTED = ["kr_create", "kr_destroy", "kr_set_stream", "kr_last_error", "kr_lau
             "kr_timing_read", "kr_timing_reset", "kron_leverage",
             "kron_sample", "kron_sample_noalloc", "kron_sketch", "kron_sketch_distinct", "kron_sketch_export", "kron_sketch_residual",
             "kron_sketch_free", "kron_matmul", "kron_precond", "kron_objective", "kron_regress", "kron_ridge",
-            "kron_ridge_batched", "tucker_als_sweep"]
+            "kron_ridge_batched", "tucker_factor_update", "tucker_als_sweep"]
 
 
 class KronError(RuntimeError):
@@ -94,6 +94,7 @@ def lib():
             "kron_regress": (i32, [vp, P(KrFactors), vp, P(KrOpts), vp, P(KrReport)]),
             "kron_ridge": (i32, [vp, P(KrFactors), vp, P(KrOpts), vp, P(KrReport)]),
             "kron_ridge_batched": (i32, [vp, i32, P(KrFactors), P(vp), P(KrOpts), P(vp), P(KrReport)]),
+            "tucker_factor_update": (i32, [vp, i32, P(i64), P(i32), vp, P(vp), vp, i32, P(KrOpts), P(KrReport)]),
             "tucker_als_sweep": (i32, [vp, i32, P(i64), P(i32), vp, P(vp), vp, P(KrOpts), i32, P(KrReport)]),
         }
         for name, (res, args) in sig.items():
@@ -160,6 +161,13 @@ def _dev_f32(t, device=None):
     t = torch.as_tensor(t)
     if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
         t = t.to(device="cuda" if device is None else device, dtype=torch.float32).contiguous()
+    return t
+
+
+def _inout(t, name):
+    """In-place arguments must already be contiguous float32 device tensors (no copy)."""
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous float32 CUDA tensor (it is updated in place)" % name)
     return t
 
 
@@ -392,12 +400,34 @@ def kron_ridge_batched(problems, lam, eps=0.1, seed=0, call_id=0, **kw):
     return xs, [r.as_dict() for r in reps]
 
 
+def tucker_factor_update(X, As, G, n, lam, eps=0.1, seed=0, call_id=0, raise_notconv=True, **kw):
+    """Alg. 3 for mode n: overwrites As[n] (device float32) in place; returns the report."""
+    h = context()
+    N = len(As)
+    X = _dev_f32(X)
+    for k, A in enumerate(As):
+        _inout(A, "As[%d]" % k)
+    _inout(G, "G")
+    I = (ctypes.c_int64 * N)(*[A.shape[0] for A in As])
+    R = (ctypes.c_int32 * N)(*[A.shape[1] for A in As])
+    o = _opts(eps=eps, lam=lam, seed=seed, call_id=call_id, **kw)
+    rep = KrReport()
+    st = lib().tucker_factor_update(h, N, I, R, _ptr(X), _ptr_array(As), _ptr(G), int(n), ctypes.byref(o),
+                                    ctypes.byref(rep))
+    if st != 0 and (raise_notconv or st != 6):
+        _check(st, h)
+    return rep.as_dict()
+
+
 def tucker_als_sweep(X, As, G, lam, eps=0.1, sweeps=1, seed=0, call_id=0, **kw):
     """Sampled TuckerALS sweeps (Alg. 1 with Alg. 3 factor steps and Alg. 2 core steps).
     As and G are updated in place (device float32 tensors); returns the report."""
     h = context()
     N = len(As)
     X = _dev_f32(X)
+    for k, A in enumerate(As):
+        _inout(A, "As[%d]" % k)
+    _inout(G, "G")
     I = (ctypes.c_int64 * N)(*[A.shape[0] for A in As])
     R = (ctypes.c_int32 * N)(*[A.shape[1] for A in As])
     o = _opts(eps=eps, lam=lam, seed=seed, call_id=call_id, **kw)

@@ -132,6 +132,7 @@ struct FactorTables {
   float* V[KR_MAX_MODES] = {};       // R x R: eigenvectors of A^T A (columns, FP32)
   float* sig2[KR_MAX_MODES] = {};    // R: eigenvalues of A^T A (FP32)
   double* gram[KR_MAX_MODES] = {};   // R x R FP64
+  double* linv[KR_MAX_MODES] = {};   // R x R FP64: inverse of the Cholesky factor of the Gram
   int rank[KR_MAX_MODES] = {};
 };
 
@@ -151,6 +152,8 @@ kr_status kr_mode_product(kr_ctx* ctx, const float* in, float* out, int64_t P, i
 // in tmp0/tmp1 (each must hold the largest intermediate), result in `out` (may be `in`).
 kr_status kr_kron_apply2(kr_ctx* ctx, int N, const int* dimsIn, const int* dimsOut, const float* const* B,
                          const int* trans, const float* in, float* out, float* tmp0, float* tmp1);
+// x[i] /= prod_n sig2_n[r_n] + shift (trailing dims of t; a leading batch axis allowed).
+kr_status kr_diag_scale(kr_ctx* ctx, const FactorTables& t, double shift, float* x, int64_t total);
 // d = M+ g (Alg. 2 preconditioner) from the factor tables; tmp0/tmp1 hold R floats each.
 kr_status kr_precond_apply(kr_ctx* ctx, const FactorTables& t, double lambda, const float* g, float* d, float* tmp0,
                            float* tmp1);
@@ -160,8 +163,12 @@ kr_status kr_precond_apply(kr_ctx* ctx, const FactorTables& t, double lambda, co
 struct kr_sketch {
   int N = 0;
   int I[KR_MAX_MODES] = {};
-  int64_t s = 0;
-  int64_t ncell = 0;   // prod_{n < N-1} I[n]
+  int64_t s = 0;       // all draws (nrow * s_row)
+  int64_t s_row = 0;   // draws per row batch
+  int nrow = 1;        // row batches (Tucker factor rows; 1 for a plain solve)
+  int64_t ncell_inner = 0;  // prod_{n < N-1} I[n]
+  int64_t xI = 1, xPafter = 1;  // gather map from a batch row into X (see k_dedup)
+  int64_t ncell = 0;   // nrow * ncell_inner
   int IT = 0;          // I[N-1]
   int64_t distinct = 0;
   // device arrays (owned)
@@ -179,6 +186,7 @@ struct kr_sketch {
 // arrays, then fill them (sampling, grouping, merging, gather) using scratch from `cv`.
 kr_status kr_sketch_check(kr_ctx* ctx, const Modes& m, int64_t s);
 void kr_sketch_setup(kr_sketch* sk, const Modes& m, int64_t s);
+void kr_sketch_setup_rows(kr_sketch* sk, const Modes& m, int64_t s_row, int nrow, int64_t xI, int64_t xPafter);
 void kr_sketch_own_need(const kr_sketch* sk, Need& nd);
 void kr_sketch_layout(kr_sketch* sk, Carve& cv);
 void kr_sketch_scratch_need(int64_t s, int64_t ncell, Need& nd);
@@ -195,3 +203,19 @@ kr_status kr_scan_u32(kr_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
 // perm = cells ordered by decreasing floor(log2(distinct rows)), stable (deterministic).
 void kr_perm_need(int64_t ncell, Need& nd);
 kr_status kr_balance_perm(kr_ctx* ctx, const uint32_t* nd, int64_t ncell, uint32_t* perm, Carve& cv);
+
+// ------------------------------------------------------------------ solvers
+
+struct SolveCfg {
+  double lambda, eps, alpha, tol;
+  int max_iter;
+  int64_t s;
+};
+
+enum StepCheck { STEP_CONTINUE, STEP_CONVERGED, STEP_FLOOR, STEP_DIVERGED, STEP_NONFINITE };
+StepCheck step_check(const double* h, double tol, double* prev_step, double* min_step, double* min_rel, int* grow,
+                     int* since_min, double* rel_out, double rel_override);
+
+// Alg. 2 on device-resident factors and b; x (R floats) is written.
+kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const SolveCfg& cfg, uint64_t seed,
+                          uint64_t call_id, float* x_out, kr_report* rep);

@@ -315,7 +315,7 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
     t.I[n] = I; t.R[n] = R;
     mp.part[n] = cv.take<double>((size_t)((I + GRAM_ROWS - 1) / GRAM_ROWS) * R * R);
     mp.gram[n] = t.gram[n] = cv.take<double>((size_t)R * R);
-    mp.linv[n] = cv.take<double>((size_t)R * R);
+    mp.linv[n] = t.linv[n] = cv.take<double>((size_t)R * R);
     mp.lev[n] = t.lev[n] = cv.take<double>(I);
     mp.cdf[n] = t.cdf[n] = cv.take<double>(I);
     mp.prob[n] = t.prob[n] = cv.take<double>(I);

@@ -215,6 +215,22 @@ kr_status kr_precond_apply(kr_ctx* ctx, const FactorTables& t, double lambda, co
   return kr_kron_apply2(ctx, N, dims, dims, B, tr, d, d, tmp0, tmp1);
 }
 
+// x[i] /= prod_n sig2_n[r_n] + shift over the trailing dims of t (a leading batch axis is
+// allowed: total may be a multiple of prod R).
+kr_status kr_diag_scale(kr_ctx* ctx, const FactorTables& t, double shift, float* x, int64_t total) {
+  DiagArgs da = {};
+  da.N = t.N;
+  for (int n = 0; n < t.N; ++n) {
+    da.R[n] = t.R[n];
+    da.sig2[n] = t.sig2[n];
+  }
+  int grid = (int)((total + 255) / 256);
+  if (grid > ctx->num_sms * 8) grid = ctx->num_sms * 8;
+  if (grid < 1) grid = 1;
+  KR_LAUNCH(ctx, k_diag_scale, grid, 256, 0, x, total, da, (float)shift);
+  return KR_OK;
+}
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" kr_status kron_matmul(kr_ctx* ctx, int32_t N, const int64_t* J, const int64_t* K, const float* const B[],

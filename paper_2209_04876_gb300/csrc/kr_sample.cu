@@ -104,22 +104,34 @@ __global__ void k_sample_idx(SampleModes sm, int64_t s, uint32_t k0, uint32_t k1
 }
 
 // Solver path: cell id and last coordinate packed in one key; histogram by cell.
-// key = cell * IT + i_T (the linear row index).
-__global__ void k_sample_keys(SampleModes sm, int64_t s, uint32_t k0, uint32_t k1, uint32_t row, uint32_t cid,
-                              uint32_t* __restrict__ keys, uint32_t* __restrict__ cell_cnt) {
+// Draws come in nrow batches of s_row (one batch per Tucker factor row; nrow = 1 for a
+// plain solve). Draw t of batch r uses Philox counter row row0 + r. The key is
+// cell * IT + i_T with cell = r * ncell_inner + (i_1..i_{N-1}) (the linear row index of
+// the batched system).
+__global__ void k_sample_keys(SampleModes sm, int64_t s_row, int nrow, uint32_t k0, uint32_t k1, uint32_t row0,
+                              uint32_t cid, int64_t ncell_inner, uint32_t* __restrict__ keys,
+                              uint32_t* __restrict__ cell_cnt) {
   __shared__ uint64_t buf[THR_SMEM];
   const uint64_t* thr[KR_MAX_MODES];
   load_thr(sm, buf, thr);
   const int N = sm.N;
   const uint32_t IT = sm.I[N - 1];
-  for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x; t0 < s; t0 += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t total = s_row * nrow;
+  for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x; t0 < total; t0 += (int64_t)gridDim.x * blockDim.x) {
     int64_t t = t0 + threadIdx.x;
-    bool live = t < s;
+    bool live = t < total;
     uint32_t cell = 0;
     if (live) {
+      uint32_t r = 0;
+      int64_t tl = t;
+      if (nrow > 1) {
+        r = (uint32_t)((uint64_t)t / (uint64_t)s_row);
+        tl = t - (int64_t)r * s_row;
+      }
       int idx[KR_MAX_MODES];
-      draw(sm, thr, (uint64_t)t, k0, k1, row, cid, idx);
+      draw(sm, thr, (uint64_t)tl, k0, k1, row0 + r, cid, idx);
       for (int n = 0; n < N - 1; ++n) cell = cell * (uint32_t)sm.I[n] + (uint32_t)idx[n];
+      cell += r * (uint32_t)ncell_inner;
       keys[t] = cell * IT + (uint32_t)idx[N - 1];
     }
     // warp-aggregated histogram increment
@@ -160,7 +172,12 @@ __global__ void k_scatter(const uint32_t* __restrict__ keys, int64_t s, uint32_t
 constexpr int DEDUP_WARPS = 8;
 constexpr int DEDUP_MAX_IT = 8192;
 
-__global__ void k_dedup(SampleModes sm, int64_t ncell, uint32_t IT, float inv_s, const uint32_t* __restrict__ start,
+// Batched rows: cell c belongs to row c / ncell_inner; its entry (c, i) is the row-major
+// index key = (c % ncell_inner) * IT + i over the sampled modes, and b is read at
+// ((key / xPafter) * xI + row) * xPafter + key % xPafter (X_(n) row `row`; for a plain
+// solve xI = xPafter = 1 and the index is the key itself).
+__global__ void k_dedup(SampleModes sm, int64_t ncell, int64_t ncell_inner, int64_t xI, int64_t xPafter, uint32_t IT,
+                        float inv_s, const uint32_t* __restrict__ start,
                         const uint32_t* __restrict__ cnt, const uint16_t* __restrict__ slot, const float* __restrict__ b,
                         uint32_t* __restrict__ ent, float* __restrict__ bt, uint32_t* __restrict__ nd,
                         float* __restrict__ cell_w) {
@@ -173,10 +190,11 @@ __global__ void k_dedup(SampleModes sm, int64_t ncell, uint32_t IT, float inv_s,
   const uint32_t lo = min(IT, lane * chunk), hi = min(IT, lo + chunk);
   for (int64_t c = (int64_t)blockIdx.x * DEDUP_WARPS + warp; c < ncell; c += (int64_t)gridDim.x * DEDUP_WARPS) {
     const uint32_t n = cnt[c], base = start[c];
+    const int64_t c_in = c % ncell_inner, row = c / ncell_inner;
     if (lane == 0) {
       // weight of the cell: prod over the first N-1 coordinates of 1/p
       float w = inv_s;
-      int64_t rem = c;
+      int64_t rem = c_in;
       for (int m = sm.N - 2; m >= 0; --m) {
         int i = (int)(rem % sm.I[m]);
         rem /= sm.I[m];
@@ -202,12 +220,17 @@ __global__ void k_dedup(SampleModes sm, int64_t ncell, uint32_t IT, float inv_s,
       if (lane >= off) incl += v;
     }
     uint32_t pos = base + incl - mine;
-    const int64_t rowbase = c * (int64_t)IT;
+    const int64_t rowbase = c_in * (int64_t)IT;
     for (uint32_t i = lo; i < hi; ++i) {
       uint32_t v = tab[i];
       if (v == 0) continue;
       tab[i] = 0;
-      float bv = b ? b[rowbase + i] : 0.f;
+      float bv = 0.f;
+      if (b) {
+        const int64_t key = rowbase + i;
+        const int64_t bi = (xPafter == 1 && xI == 1) ? key : ((key / xPafter) * xI + row) * xPafter + key % xPafter;
+        bv = b[bi];
+      }
       while (v > 0) {
         uint32_t take = v > 65535u ? 65535u : v;
         ent[pos] = i | (take << 16);
@@ -269,14 +292,21 @@ int grid_for(kr_ctx* ctx, int64_t work, int block, int per_sm = 8) {
 
 }  // namespace
 
-void kr_sketch_setup(kr_sketch* sk, const Modes& m, int64_t s) {
+void kr_sketch_setup(kr_sketch* sk, const Modes& m, int64_t s) { kr_sketch_setup_rows(sk, m, s, 1, 1, 1); }
+
+void kr_sketch_setup_rows(kr_sketch* sk, const Modes& m, int64_t s_row, int nrow, int64_t xI, int64_t xPafter) {
   sk->N = m.N;
   for (int n = 0; n < m.N; ++n) sk->I[n] = m.I[n];
-  sk->s = s;
+  sk->s_row = s_row;
+  sk->nrow = nrow;
+  sk->s = s_row * nrow;
   int64_t ncell = 1;
   for (int n = 0; n < m.N - 1; ++n) ncell *= m.I[n];
-  sk->ncell = ncell;
+  sk->ncell_inner = ncell;
+  sk->ncell = ncell * nrow;
   sk->IT = m.I[m.N - 1];
+  sk->xI = xI;
+  sk->xPafter = xPafter;
 }
 
 void kr_sketch_own_need(const kr_sketch* sk, Need& nd) {
@@ -323,7 +353,8 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   KR_CUDA(ctx, cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * ncell, ctx->stream));
   KR_CUDA(ctx, cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), ctx->stream));
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32), cid = (uint32_t)call_id;
-  KR_LAUNCH(ctx, k_sample_keys, grid_for(ctx, s, 256), 256, 0, sm, s, k0, k1, (uint32_t)row, cid, keys, cnt);
+  KR_LAUNCH(ctx, k_sample_keys, grid_for(ctx, s, 256), 256, 0, sm, sk->s_row, sk->nrow, k0, k1, (uint32_t)row, cid,
+            sk->ncell_inner, keys, cnt);
   {
     Carve sc = cv;  // scan scratch is transient
     KR_TRY(kr_scan_u32(ctx, cnt, sk->cell_start, ncell, sc));
@@ -331,8 +362,9 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   KR_LAUNCH(ctx, k_scatter, grid_for(ctx, s, 256), 256, 0, keys, s, IT, sk->cell_start, cursor, slot);
   const size_t dsmem = (size_t)DEDUP_WARPS * IT * sizeof(uint32_t);
   KR_CUDA(ctx, cudaFuncSetAttribute(k_dedup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
-  KR_LAUNCH(ctx, k_dedup, grid_for(ctx, ncell, DEDUP_WARPS, 8), DEDUP_WARPS * 32, dsmem, sm, ncell, IT,
-            (float)(1.0 / (double)s), sk->cell_start, cnt, slot, b, sk->ent, sk->bt, sk->cell_nd, sk->cell_w);
+  KR_LAUNCH(ctx, k_dedup, grid_for(ctx, ncell, DEDUP_WARPS, 8), DEDUP_WARPS * 32, dsmem, sm, ncell, sk->ncell_inner,
+            sk->xI, sk->xPafter, IT, (float)(1.0 / (double)sk->s_row), sk->cell_start, cnt, slot, b, sk->ent, sk->bt,
+            sk->cell_nd, sk->cell_w);
   {
     Carve sc = cv;
     KR_TRY(kr_balance_perm(ctx, sk->cell_nd, ncell, sk->perm, sc));

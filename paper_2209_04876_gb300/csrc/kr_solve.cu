@@ -394,24 +394,20 @@ kr_status backward(kr_ctx* ctx, const Modes& m, const IterBufs& bf) {
   return kr_kron_apply2(ctx, N, din, dout, B, tr, bf.W, bf.g, bf.t0, bf.t1);
 }
 
-struct SolveCfg {
-  double lambda, eps, alpha, tol;
-  int max_iter;
-  int64_t s;
-};
+}  // namespace
 
-enum StepCheck { STEP_CONTINUE, STEP_CONVERGED, STEP_FLOOR, STEP_DIVERGED, STEP_NONFINITE };
-
-// Stopping rule of the Richardson loop ("until convergence" in Alg. 2 and Alg. 3):
+// Stopping rule of the Richardson loops ("until convergence" in Alg. 2 and Alg. 3):
 // converged when ||step|| <= tol ||x||; stalled at the FP32 rounding floor when no new
 // minimum step was seen for 8 iterations and the smallest relative step is within
 // 100 tol; diverged when the step grew 3 times in a row and exceeds 16x its minimum.
-// h = {||step||^2, ||x||^2, non-finite flag}.
+// h = {||step||^2, ||x||^2, non-finite flag}; rel_override >= 0 replaces ||step||/||x||
+// (the batched factor step passes its largest per-row ratio).
 StepCheck step_check(const double* h, double tol, double* prev_step, double* min_step, double* min_rel, int* grow,
-                     int* since_min, double* rel_out) {
+                     int* since_min, double* rel_out, double rel_override) {
   const double step = sqrt(h[0]), xn = sqrt(h[1]);
   if (h[2] != 0.0 || !isfinite(step) || !isfinite(xn)) return STEP_NONFINITE;
-  const double rel = xn > 0.0 ? step / xn : (step == 0.0 ? 0.0 : INFINITY);
+  double rel = xn > 0.0 ? step / xn : (step == 0.0 ? 0.0 : INFINITY);
+  if (rel_override >= 0.0) rel = rel_override;
   *rel_out = rel;
   if (rel <= tol) return STEP_CONVERGED;
   if (step < *min_step) {
@@ -427,8 +423,6 @@ StepCheck step_check(const double* h, double tol, double* prev_step, double* min
   if (*since_min >= 8 && *min_rel <= 100.0 * tol) return STEP_FLOOR;
   return STEP_CONTINUE;
 }
-
-}  // namespace
 
 // Core Alg. 2 solve on device-resident inputs. Timings go to rep->t_ms if rep != NULL.
 kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const SolveCfg& cfg, uint64_t seed,
@@ -494,7 +488,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, bf.part, ublk, 3, 1, bf.red);
     KR_CUDA(ctx, cudaMemcpyAsync(h, bf.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    StepCheck sc = step_check(h, cfg.tol, &prev_step, &min_step, &min_rel, &grow, &since_min, &rel);
+    StepCheck sc = step_check(h, cfg.tol, &prev_step, &min_step, &min_rel, &grow, &since_min, &rel, -1.0);
     if (sc == STEP_NONFINITE) {
       st = kr_fail(ctx, KR_ENONFINITE, "Richardson iterate became non-finite at iteration %d", it);
       break;
@@ -719,12 +713,4 @@ extern "C" kr_status kron_objective(kr_ctx* ctx, const kr_factors* f, const floa
   double* h = (double*)ctx->hbuf;
   *obj = h[0] + lambda * h[1];
   return KR_OK;
-}
-
-extern "C" kr_status tucker_als_sweep(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R, const float* X,
-                                      float* const A[], float* G, const kr_opts* opts, int32_t sweeps,
-                                      kr_report* report) {
-  (void)N; (void)I; (void)R; (void)X; (void)A; (void)G; (void)opts; (void)sweeps; (void)report;
-  if (!ctx) return KR_EINVAL;
-  return kr_fail(ctx, KR_ENOTIMPL, "tucker_als_sweep: not built yet");
 }

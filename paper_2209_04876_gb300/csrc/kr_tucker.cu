@@ -1,0 +1,657 @@
+// Alg. 3 FastFactorMatrixUpdate, batched over the rows of one factor, and Alg. 1
+// TuckerALS (sampled factor steps, then a sampled core step).
+//
+// Factor step for mode n (App. C): with K = (x)_{m != n} A(m), G = G_(n) (R_n x R_{!=n},
+// columns in C-order over the other modes), G+ = pinv(G) and the penalty
+// w = (1 + 12/eps) prod_{m != n} sigma_max(A(m))^2, each row i of X_(n) solves
+//   min_z ||S_i (K z - b_i)||^2 + lambda ||(G^T)^+ z||^2 + w ||N z||^2,  N = I - G+ G,
+// by the Richardson iteration of Alg. 3,
+//   z <- z - (1 - sqrt(eps)) M^-1 ((K~^T K~ + w I) z + lambda G+ (G+)^T z - w G+ G z - K~^T b~),
+// with a fresh sketch S_i per row, and returns a_i = (G+)^T z. The preconditioner is the
+// unsampled M = K^T K + w I + G+ (lambda (G+)^T - w G), inverted with the Woodbury
+// identity (standard sign)
+//   M^-1 = A^-1 - A^-1 U (I + V A^-1 U)^-1 V A^-1,  A = K^T K + w I, U = G+, V = lambda (G+)^T - w G,
+// where A^-1 = (x)V_m (S_m^2 (x)... + w)^-1 (x)V_m^T from the factor eigen-decompositions.
+//
+// All rows of the factor run together: the row index is a leading batch axis of every
+// mode product, the sketch keys draws by (row, cell), and b~ is gathered from X_(n).
+// The capacitance I + V A^-1 U is accumulated and inverted in FP64 (its entries cancel
+// to about 1/(1 + 12/eps) of the terms that form them).
+#include <math.h>
+
+#include "kr_internal.cuh"
+
+namespace {
+
+struct Dims {
+  int N;
+  int R[KR_MAX_MODES];
+};
+
+// G (C-order over R) -> Gn (R_n x Rne) and Gt = Gn^T (Rne x R_n).
+__global__ void k_unfold(const float* __restrict__ G, Dims d, int n, int64_t Rtot, int Rne, float* __restrict__ Gn,
+                         float* __restrict__ Gt) {
+  const int Rn = d.R[n];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < Rtot; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = e;
+    int idx[KR_MAX_MODES];
+    for (int m = d.N - 1; m >= 0; --m) {
+      idx[m] = (int)(rem % d.R[m]);
+      rem /= d.R[m];
+    }
+    int64_t k = 0;
+    for (int m = 0; m < d.N; ++m)
+      if (m != n) k = k * d.R[m] + idx[m];
+    const float v = G[e];
+    Gn[(int64_t)idx[n] * Rne + k] = v;
+    Gt[k * Rn + idx[n]] = v;
+  }
+}
+
+// out = ca * a + cb * b
+__global__ void k_lin2(float* __restrict__ out, const float* __restrict__ a, float ca, const float* __restrict__ b,
+                       float cb, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = ca * a[i] + cb * b[i];
+}
+
+// grad = w z + corr - g_sk  (in place in corr)
+__global__ void k_grad(float* __restrict__ corr, const float* __restrict__ z, float w, const float* __restrict__ gsk,
+                       int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    corr[i] = fmaf(w, z[i], corr[i]) - gsk[i];
+}
+
+// Hinv = L^-T L^-1 = (G_(n) G_(n)^T)^-1 in FP64 from the inverse Cholesky factor (one block).
+__global__ void k_hinv(const double* __restrict__ linv, int Rn, double* __restrict__ hinv) {
+  for (int e = threadIdx.x; e < Rn * Rn; e += blockDim.x) {
+    const int i = e / Rn, j = e % Rn;
+    double acc = 0.0;
+    for (int k = i > j ? i : j; k < Rn; ++k) acc = fma(linv[k * Rn + i], linv[k * Rn + j], acc);
+    hinv[e] = acc;
+  }
+}
+
+// G+ = G_(n)^T Hinv in FP64 (Rne x R_n), and its FP32 copy for the preconditioner.
+__global__ void k_gp64(const float* __restrict__ Gt, const double* __restrict__ hinv, int Rn, int64_t Rne,
+                       double* __restrict__ gp64, float* __restrict__ gp32) {
+  const int64_t tot = Rne * Rn;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e / Rn;
+    const int a = (int)(e % Rn);
+    double acc = 0.0;
+    for (int b = 0; b < Rn; ++b) acc = fma((double)Gt[k * Rn + b], hinv[b * Rn + a], acc);
+    gp64[e] = acc;
+    gp32[e] = (float)acc;
+  }
+}
+
+// Per row i (one block): the deterministic part of Alg. 3's gradient in FP64,
+//   grad = w z + G+ (lambda (G+)^T z - w G z) - gsk,
+// where w z and G+ (w G z) cancel in the row space of G^T (exactly, for exact G+), so the
+// combination is formed in FP64 from the FP32 iterate. With out_a != null the block
+// instead writes the factor row a_i = (G+)^T z_i.
+constexpr int PEN_MAXRN = KR_MAX_RANK;
+__global__ void __launch_bounds__(256) k_penalty_rows(const float* __restrict__ Z, const float* __restrict__ Gn,
+                                                      const double* __restrict__ gp64, const float* __restrict__ gsk,
+                                                      int Rn, int Rne, double lambda, double w,
+                                                      float* __restrict__ grad, float* __restrict__ out_a) {
+  extern __shared__ double zs[];  // Rne
+  __shared__ double tv[PEN_MAXRN], uv[PEN_MAXRN];
+  const int64_t row = blockIdx.x;
+  const float* z = Z + row * Rne;
+  for (int k = threadIdx.x; k < Rne; k += blockDim.x) zs[k] = (double)z[k];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int a = warp; a < Rn; a += nw) {
+    double t = 0.0, u = 0.0;
+    for (int k = lane; k < Rne; k += 32) {
+      t = fma((double)Gn[(int64_t)a * Rne + k], zs[k], t);
+      u = fma(gp64[(int64_t)k * Rn + a], zs[k], u);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      t += __shfl_xor_sync(0xffffffffu, t, off);
+      u += __shfl_xor_sync(0xffffffffu, u, off);
+    }
+    if (lane == 0) {
+      tv[a] = t;
+      uv[a] = u;
+    }
+  }
+  __syncthreads();
+  if (out_a) {
+    for (int a = threadIdx.x; a < Rn; a += blockDim.x) out_a[row * Rn + a] = (float)uv[a];
+    return;
+  }
+  for (int a = threadIdx.x; a < Rn; a += blockDim.x) tv[a] = lambda * uv[a] - w * tv[a];
+  __syncthreads();
+  for (int k = threadIdx.x; k < Rne; k += blockDim.x) {
+    double c = 0.0;
+    for (int a = 0; a < Rn; ++a) c = fma(gp64[(int64_t)k * Rn + a], tv[a], c);
+    grad[row * Rne + k] = (float)(w * zs[k] + c - (double)gsk[row * Rne + k]);
+  }
+}
+
+// Vw[a][k] = lambda * Gp[k][a] - w * Gn[a][k]  (R_n x Rne);  GpT[a][k] = Gp[k][a]
+__global__ void k_vw(const float* __restrict__ Gp, const float* __restrict__ Gn, int Rn, int Rne, float lambda, float w,
+                     float* __restrict__ Vw, float* __restrict__ GpT) {
+  const int64_t tot = (int64_t)Rn * Rne;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e / Rne), k = (int)(e % Rne);
+    const float gp = Gp[(int64_t)k * Rn + a];
+    GpT[e] = gp;
+    Vw[e] = lambda * gp - w * Gn[e];
+  }
+}
+
+// C[a][b] = delta_ab + sum_k Vw[a][k] AinvUt[b][k], FP64 accumulation; block per (a, b).
+__global__ void k_capacitance(const float* __restrict__ Vw, const float* __restrict__ AinvUt, int Rn, int Rne,
+                              double* __restrict__ C) {
+  const int a = blockIdx.x / Rn, b = blockIdx.x % Rn;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < Rne; k += blockDim.x)
+    acc += (double)Vw[(int64_t)a * Rne + k] * (double)AinvUt[(int64_t)b * Rne + k];
+  __shared__ double red[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    C[blockIdx.x] = t + (a == b ? 1.0 : 0.0);
+  }
+}
+
+// Gauss-Jordan inverse with partial pivoting in FP64 (one block, n <= 64).
+__global__ void k_gauss_jordan(const double* __restrict__ C, int n, float* __restrict__ Cinv, int* __restrict__ bad) {
+  extern __shared__ double aug[];  // n x 2n
+  const int w2 = 2 * n;
+  __shared__ int piv;
+  __shared__ double pv;
+  for (int e = threadIdx.x; e < n * w2; e += blockDim.x) {
+    const int i = e / w2, j = e % w2;
+    aug[e] = j < n ? C[i * n + j] : (j - n == i ? 1.0 : 0.0);
+  }
+  if (threadIdx.x == 0) *bad = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      int p = k;
+      double best = fabs(aug[k * w2 + k]);
+      for (int i = k + 1; i < n; ++i) {
+        double v = fabs(aug[i * w2 + k]);
+        if (v > best) { best = v; p = i; }
+      }
+      piv = p;
+      pv = aug[p * w2 + k];
+      if (!(best > 0.0)) *bad = 1;
+    }
+    __syncthreads();
+    const int p = piv;
+    const double pivot = pv != 0.0 ? pv : 1.0;
+    if (p != k)
+      for (int j = threadIdx.x; j < w2; j += blockDim.x) {
+        double t = aug[k * w2 + j];
+        aug[k * w2 + j] = aug[p * w2 + j];
+        aug[p * w2 + j] = t;
+      }
+    __syncthreads();
+    for (int j = threadIdx.x; j < w2; j += blockDim.x) aug[k * w2 + j] /= pivot;
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * w2; e += blockDim.x) {
+      const int i = e / w2, j = e % w2;
+      if (i == k) continue;
+      const double f = aug[i * w2 + k];
+      if (j != k) aug[e] -= f * aug[k * w2 + j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (i != k) aug[i * w2 + k] = 0.0;
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Cinv[e] = (float)aug[(e / n) * w2 + n + (e % n)];
+}
+
+// z <- z - alpha d, one block per row; rowstat[r] = {||step||^2, ||z||^2, non-finite}.
+__global__ void k_row_update(float* __restrict__ z, const float* __restrict__ d, float alpha, int L,
+                             double* __restrict__ rowstat) {
+  const int64_t base = (int64_t)blockIdx.x * L;
+  double s1 = 0.0, s2 = 0.0, bad = 0.0;
+  for (int k = threadIdx.x; k < L; k += blockDim.x) {
+    const float st = alpha * d[base + k];
+    const float zn = z[base + k] - st;
+    z[base + k] = zn;
+    s1 += (double)st * st;
+    s2 += (double)zn * zn;
+    if (!isfinite(zn)) bad = 1.0;
+  }
+  __shared__ double red[3][32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+    bad = fmax(bad, __shfl_xor_sync(0xffffffffu, bad, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s1;
+    red[1][threadIdx.x >> 5] = s2;
+    red[2][threadIdx.x >> 5] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, c = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += red[0][k];
+      b += red[1][k];
+      c = fmax(c, red[2][k]);
+    }
+    rowstat[3 * (int64_t)blockIdx.x + 0] = a;
+    rowstat[3 * (int64_t)blockIdx.x + 1] = b;
+    rowstat[3 * (int64_t)blockIdx.x + 2] = c;
+  }
+}
+
+// out = {sum ||step||^2, sum ||z||^2, any non-finite, max_r ||step_r|| / ||z_r||} (one block).
+__global__ void k_rows_reduce(const double* __restrict__ rowstat, int nrow, double* __restrict__ out) {
+  double s1 = 0, s2 = 0, bad = 0, mx = 0;
+  for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
+    const double a = rowstat[3 * r], b = rowstat[3 * r + 1];
+    s1 += a;
+    s2 += b;
+    bad = fmax(bad, rowstat[3 * r + 2]);
+    const double rel = b > 0.0 ? sqrt(a / b) : (a > 0.0 ? INFINITY : 0.0);
+    mx = fmax(mx, rel);
+  }
+  __shared__ double red[4][32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+    bad = fmax(bad, __shfl_xor_sync(0xffffffffu, bad, off));
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s1;
+    red[1][threadIdx.x >> 5] = s2;
+    red[2][threadIdx.x >> 5] = bad;
+    red[3][threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, c = 0, d = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += red[0][k];
+      b += red[1][k];
+      c = fmax(c, red[2][k]);
+      d = fmax(d, red[3][k]);
+    }
+    out[0] = a;
+    out[1] = b;
+    out[2] = c;
+    out[3] = d;
+  }
+}
+
+int grid_of(kr_ctx* ctx, int64_t work) {
+  int64_t g = (work + 255) / 256;
+  if (g > ctx->num_sms * 8) g = ctx->num_sms * 8;
+  return g < 1 ? 1 : (int)g;
+}
+
+// Batched A^-1 = (x)V (S^2 + w)^-1 (x)V^T over the other modes for `nrow` vectors.
+kr_status base_apply(kr_ctx* ctx, const FactorTables& to, int nrow, double w, const float* in, float* out, float* t0,
+                     float* t1) {
+  const int No = to.N;
+  int dims[KR_MAX_MODES];
+  const float* B[KR_MAX_MODES];
+  int tr[KR_MAX_MODES];
+  dims[0] = nrow;
+  B[0] = nullptr;
+  tr[0] = 0;
+  int64_t Rne = 1;
+  for (int m = 0; m < No; ++m) {
+    dims[m + 1] = to.R[m];
+    B[m + 1] = to.V[m];
+    tr[m + 1] = 1;
+    Rne *= to.R[m];
+  }
+  KR_TRY(kr_kron_apply2(ctx, No + 1, dims, dims, B, tr, in, out, t0, t1));
+  KR_TRY(kr_diag_scale(ctx, to, w, out, Rne * nrow));
+  for (int m = 0; m < No; ++m) tr[m + 1] = 0;
+  return kr_kron_apply2(ctx, No + 1, dims, dims, B, tr, out, out, t0, t1);
+}
+
+struct FactorStep {
+  int n;
+  int No;
+  int Rn;
+  int64_t Rne;
+  int In;
+};
+
+}  // namespace
+
+// One Alg. 3 factor update of mode n (A[n] overwritten). Returns the iteration count.
+kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const float* G, int n, const SolveCfg& cfg,
+                         uint64_t seed, uint64_t call_id, float* An_out, kr_report* rep) {
+  const int N = m.N;
+  const int No = N - 1;
+  const int Rn = m.R[n], In = m.I[n];
+  Modes mo;
+  mo.N = No;
+  int64_t Rne = 1, Pafter = 1;
+  for (int k = 0, j = 0; k < N; ++k) {
+    if (k == n) continue;
+    mo.I[j] = m.I[k];
+    mo.R[j] = m.R[k];
+    mo.A[j] = m.A[k];
+    Rne *= m.R[k];
+    ++j;
+  }
+  for (int k = n + 1; k < N; ++k) Pafter *= m.I[k];
+  if (Rn > Rne)
+    return kr_fail(ctx, KR_EINVAL, "factor step %d: R_n=%d exceeds prod of the other ranks (%lld): G_(n) cannot have full row rank",
+                   n, Rn, (long long)Rne);
+  if (Rne > 24576)
+    return kr_fail(ctx, KR_ENOTIMPL, "factor step %d: prod of the other ranks %lld > 24576", n, (long long)Rne);
+  KR_TRY(kr_sketch_check(ctx, mo, cfg.s * In));
+  kr_sketch sk;
+  kr_sketch_setup_rows(&sk, mo, cfg.s, In, In, Pafter);
+  const int RT = mo.R[No - 1];
+  const int64_t cells = sk.ncell;
+  // largest batched intermediate: forward (In, I_o..., R_T) or the precond (In, Rne); also Rn x Rne batches
+  int64_t mx = (int64_t)In * Rne;
+  {
+    int64_t cur = (int64_t)In * Rne;
+    for (int k = 0; k < No - 1; ++k) {
+      cur = cur / mo.R[k] * mo.I[k];
+      if (cur > mx) mx = cur;
+    }
+  }
+  if ((int64_t)Rn * Rne > mx) mx = (int64_t)Rn * Rne;
+  Modes mg;  // G_(n)^T as a one-mode "factor" for its Gram / Cholesky / inverse
+  mg.N = 1;
+  mg.I[0] = (int)Rne;
+  mg.R[0] = Rn;
+  Need nd;
+  kr_tables_need(m, true, nd);
+  kr_tables_need(mg, false, nd);
+  kr_sketch_own_need(&sk, nd);
+  const int64_t ZL = (int64_t)In * Rne;
+  for (int k = 0; k < 5; ++k) nd.add<float>(ZL);      // Z, Gb, Gr, D, spare
+  nd.add<float>(cells * RT);                          // Y
+  nd.add<float>(cells * RT);                          // W
+  nd.add<float>(mx);                                  // t0
+  nd.add<float>(mx);                                  // t1
+  for (int k = 0; k < 3; ++k) nd.add<float>((int64_t)In * Rn);  // U1, U2, S3
+  for (int k = 0; k < 6; ++k) nd.add<float>((int64_t)Rn * Rne);  // Gn, Gt, Gp, GpT, Vw, AinvUt
+  nd.add<double>((int64_t)Rn * Rn);                   // Hinv (FP64)
+  nd.add<double>((int64_t)Rn * Rne);                  // G+ (FP64)
+  nd.add<double>((int64_t)Rn * Rn);                   // C
+  nd.add<float>((int64_t)Rn * Rn);                    // Cinv
+  nd.add<double>(3 * (int64_t)In + 8);                // row stats, reductions
+  nd.add<int>(8);
+  nd.add<double>(1024);                               // resid partials
+  kr_sketch_scratch_need(sk.s, cells, nd);
+  KR_TRY(kr_ws_reserve(ctx, nd.off));
+  KR_TRY(kr_hbuf_reserve(ctx, 4096));
+  Carve cv(ctx->ws, ctx->ws_size);
+  FactorTables ta;
+  KR_TRY(kr_tables_build(ctx, m, true, cv, ta, true));
+  FactorTables to;  // the other modes' tables
+  to.N = No;
+  for (int k = 0, j = 0; k < N; ++k) {
+    if (k == n) continue;
+    to.I[j] = ta.I[k];
+    to.R[j] = ta.R[k];
+    to.thr[j] = ta.thr[k];
+    to.invp[j] = ta.invp[k];
+    to.prob[j] = ta.prob[k];
+    to.V[j] = ta.V[k];
+    to.sig2[j] = ta.sig2[k];
+    to.ginv[j] = ta.ginv[k];
+    ++j;
+  }
+  // G_(n), its transpose, and G+ = G_(n)^T (G_(n) G_(n)^T)^-1
+  float* Gn = cv.take<float>((int64_t)Rn * Rne);
+  float* Gt = cv.take<float>((int64_t)Rn * Rne);
+  float* Gp = cv.take<float>((int64_t)Rn * Rne);
+  float* GpT = cv.take<float>((int64_t)Rn * Rne);
+  float* Vw = cv.take<float>((int64_t)Rn * Rne);
+  float* AinvUt = cv.take<float>((int64_t)Rn * Rne);
+  Dims dg;
+  dg.N = N;
+  for (int k = 0; k < N; ++k) dg.R[k] = m.R[k];
+  const int64_t Rtot = Rne * Rn;
+  KR_LAUNCH(ctx, k_unfold, grid_of(ctx, Rtot), 256, 0, G, dg, n, Rtot, (int)Rne, Gn, Gt);
+  mg.A[0] = Gt;
+  FactorTables tg;
+  {
+    kr_status st = kr_tables_build(ctx, mg, false, cv, tg, true);
+    if (st == KR_ERANK) return kr_fail(ctx, KR_ERANK, "factor step %d: the core unfolding G_(n) is rank deficient", n);
+    KR_TRY(st);
+  }
+  KR_CUDA(ctx, cudaFuncSetAttribute(k_penalty_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(double) * Rne)));
+  // G+ = G_(n)^T (G_(n) G_(n)^T)^-1 in FP64 (and FP32 for the preconditioner)
+  double* hinv = cv.take<double>((int64_t)Rn * Rn);
+  double* gp64 = cv.take<double>((int64_t)Rn * Rne);
+  KR_LAUNCH(ctx, k_hinv, 1, 256, 0, tg.linv[0], Rn, hinv);
+  KR_LAUNCH(ctx, k_gp64, grid_of(ctx, Rtot), 256, 0, Gt, hinv, Rn, Rne, gp64, Gp);
+  // w = (1 + 12/eps) prod_{m != n} sigma_max^2 (eigenvalues of the other Gram matrices)
+  {
+    float* hs = (float*)ctx->hbuf;
+    for (int k = 0; k < No; ++k)
+      KR_CUDA(ctx, cudaMemcpyAsync(hs + 64 * k, to.sig2[k], sizeof(float) * to.R[k], cudaMemcpyDeviceToHost, ctx->stream));
+    KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  double w = 1.0 + 12.0 / cfg.eps;
+  for (int k = 0; k < No; ++k) {
+    float mxv = 0.f;
+    const float* hs = (const float*)ctx->hbuf + 64 * k;
+    for (int i = 0; i < to.R[k]; ++i) mxv = hs[i] > mxv ? hs[i] : mxv;
+    w *= (double)mxv;
+  }
+  const float wf = (float)w, lf = (float)cfg.lambda;
+  KR_LAUNCH(ctx, k_vw, grid_of(ctx, Rtot), 256, 0, Gp, Gn, Rn, (int)Rne, lf, wf, Vw, GpT);
+  // iteration buffers
+  kr_sketch_layout(&sk, cv);
+  float* Z = cv.take<float>(ZL);
+  float* Gb = cv.take<float>(ZL);
+  float* Gr = cv.take<float>(ZL);
+  float* D = cv.take<float>(ZL);
+  float* spare = cv.take<float>(ZL);  // keeps the layout of the size accounting
+  float* Y = cv.take<float>(cells * RT);
+  float* W = cv.take<float>(cells * RT);
+  float* t0 = cv.take<float>(mx);
+  float* t1 = cv.take<float>(mx);
+  float* U1 = cv.take<float>((int64_t)In * Rn);
+  float* U2 = cv.take<float>((int64_t)In * Rn);
+  float* S3 = cv.take<float>((int64_t)In * Rn);  // keeps the layout of the size accounting
+  (void)S3;
+  double* C = cv.take<double>((int64_t)Rn * Rn);
+  float* Cinv = cv.take<float>((int64_t)Rn * Rn);
+  double* rowstat = cv.take<double>(3 * (int64_t)In + 8);
+  double* red = rowstat + 3 * (int64_t)In;
+  int* flag = cv.take<int>(8);
+  double* rpart = cv.take<double>(1024);
+  (void)spare;
+  // A^-1 U (rows: A^-1 applied to each column of G+), capacitance and its inverse
+  KR_TRY(base_apply(ctx, to, Rn, w, GpT, AinvUt, t0, t1));
+  KR_LAUNCH(ctx, k_capacitance, Rn * Rn, 256, 0, Vw, AinvUt, Rn, (int)Rne, C);
+  {
+    const size_t sm = (size_t)Rn * 2 * Rn * sizeof(double);
+    KR_CUDA(ctx, cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    KR_LAUNCH(ctx, k_gauss_jordan, 1, 256, sm, C, Rn, Cinv, flag);
+  }
+  // batched sketch: row i of X_(n), fresh draws per row (counter row = i)
+  KR_TRY(kr_sketch_fill(ctx, mo, to, X, seed, call_id, 0, &sk, cv));
+  KR_CUDA(ctx, cudaMemsetAsync(Z, 0, sizeof(float) * ZL, ctx->stream));
+  // mode-product plans over the batch axis
+  int dfw_in[KR_MAX_MODES], dfw_out[KR_MAX_MODES], trf[KR_MAX_MODES], trb[KR_MAX_MODES];
+  const float* Bf[KR_MAX_MODES];
+  dfw_in[0] = dfw_out[0] = In;
+  Bf[0] = nullptr;
+  trf[0] = trb[0] = 0;
+  for (int k = 0; k < No; ++k) {
+    dfw_in[k + 1] = mo.R[k];
+    dfw_out[k + 1] = (k < No - 1) ? mo.I[k] : mo.R[k];
+    Bf[k + 1] = (k < No - 1) ? mo.A[k] : nullptr;
+    trf[k + 1] = 0;
+    trb[k + 1] = 1;
+  }
+  const int nblk = kr_resid_blocks(ctx);
+  double* h = (double*)ctx->hbuf;
+  int it = 0, grow = 0, since_min = 0, converged = 0;
+  double prev_step = INFINITY, min_step = INFINITY, min_rel = INFINITY, rel = INFINITY;
+  kr_status st = KR_OK;
+  for (it = 1; it <= cfg.max_iter; ++it) {
+    int used = 0;
+    // sampled part: Gb = K~^T Omega (b~ - K~ z) per row
+    KR_TRY(kr_kron_apply2(ctx, No + 1, dfw_in, dfw_out, Bf, trf, Z, Y, t0, t1));
+    KR_TRY(kr_sketch_resid(ctx, &sk, mo.A[No - 1], RT, Y, W, rpart, nblk, &used));
+    KR_TRY(kr_kron_apply2(ctx, No + 1, dfw_out, dfw_in, Bf, trb, W, Gb, t0, t1));
+    // grad = w z + G+ (lambda (G+)^T z - w G z) - Gb  (FP64 combination, one block per row)
+    KR_LAUNCH(ctx, k_penalty_rows, In, 256, sizeof(double) * Rne, Z, Gn, gp64, Gb, Rn, (int)Rne, cfg.lambda, w, Gr,
+              (float*)nullptr);
+    // d = M^-1 grad (Woodbury)
+    KR_TRY(base_apply(ctx, to, In, w, Gr, D, t0, t1));
+    KR_TRY(kr_mode_product(ctx, D, U1, In, (int)Rne, 1, Rn, Vw, 0));
+    KR_TRY(kr_mode_product(ctx, U1, U2, In, Rn, 1, Rn, Cinv, 0));
+    KR_TRY(kr_mode_product(ctx, U2, Gr, In, Rn, 1, (int)Rne, AinvUt, 1));
+    KR_LAUNCH(ctx, k_lin2, grid_of(ctx, ZL), 256, 0, D, D, 1.f, Gr, -1.f, ZL);
+    // z <- z - alpha d; stopping rule on the largest per-row relative step
+    KR_LAUNCH(ctx, k_row_update, In, 256, 0, Z, D, (float)cfg.alpha, (int)Rne, rowstat);
+    KR_LAUNCH(ctx, k_rows_reduce, 1, 256, 0, rowstat, In, red);
+    KR_CUDA(ctx, cudaMemcpyAsync(h, red, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    KR_CUDA(ctx, cudaMemcpyAsync(h + 4, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (it == 1 && *(int*)(h + 4) != 0)
+      return kr_fail(ctx, KR_ERANK, "factor step %d: the Woodbury capacitance matrix is singular", n);
+    StepCheck sc = step_check(h, cfg.tol, &prev_step, &min_step, &min_rel, &grow, &since_min, &rel, h[3]);
+    if (sc == STEP_NONFINITE) {
+      st = kr_fail(ctx, KR_ENONFINITE, "factor step %d: iterate became non-finite at iteration %d", n, it);
+      break;
+    }
+    if (sc == STEP_DIVERGED) {
+      st = kr_fail(ctx, KR_EDIVERGED, "factor step %d: Richardson step grew 3 times past 16x its minimum", n);
+      break;
+    }
+    if (sc == STEP_CONVERGED || sc == STEP_FLOOR) {
+      converged = sc == STEP_CONVERGED ? 1 : 2;
+      break;
+    }
+  }
+  if (it > cfg.max_iter) it = cfg.max_iter;
+  // a_i = (G+)^T z_i  (the new factor rows, FP64 accumulation)
+  KR_LAUNCH(ctx, k_penalty_rows, In, 256, sizeof(double) * Rne, Z, Gn, gp64, Gb, Rn, (int)Rne, cfg.lambda, w, Gr,
+            An_out);
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (rep) {
+    rep->iters = it;
+    rep->converged = converged;
+    rep->s = cfg.s;
+    rep->distinct = sk.distinct;
+    rep->rel_update = rel;
+  }
+  if (st != KR_OK) return st;
+  if (!converged) return kr_fail(ctx, KR_ENOTCONV, "factor step %d: no convergence in %d iterations", n, cfg.max_iter);
+  return KR_OK;
+}
+
+namespace {
+
+kr_status tucker_args(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R, const float* X, float* const A[],
+                      const float* G, const kr_opts* o, Modes* m) {
+  if (!o || !I || !R || !X || !A || !G) return kr_fail(ctx, KR_EINVAL, "tucker: null argument");
+  if (N < 2 || N > KR_MAX_MODES) return kr_fail(ctx, KR_EINVAL, "tucker: N=%d outside [2,%d]", N, KR_MAX_MODES);
+  if (!(o->eps > 0.0 && o->eps < 1.0)) return kr_fail(ctx, KR_EINVAL, "tucker: eps outside (0,1)");
+  if (!(o->lambda >= 0.0) || !isfinite(o->lambda)) return kr_fail(ctx, KR_EINVAL, "tucker: lambda must be >= 0");
+  if (o->host_io) return kr_fail(ctx, KR_ENOTIMPL, "tucker: host_io is not supported; pass device pointers");
+  kr_factors f = {};
+  f.N = N;
+  for (int n = 0; n < N; ++n) {
+    f.I[n] = I[n];
+    f.R[n] = R[n];
+    f.A[n] = A[n];
+  }
+  return kr_check_factors(ctx, &f, m);
+}
+
+SolveCfg cfg_from(const kr_opts* o, int64_t Rsz) {
+  SolveCfg c;
+  c.lambda = o->lambda;
+  c.eps = o->eps;
+  c.alpha = o->step > 0 ? o->step : 1.0 - sqrt(o->eps);
+  c.tol = o->tol > 0 ? o->tol : 1e-7;
+  c.max_iter = o->max_iter > 0 ? o->max_iter : 100;
+  if (o->num_samples > 0) {
+    c.s = o->num_samples;
+  } else {
+    const double sc = o->sample_scale > 0 ? o->sample_scale : 4.0;
+    c.s = Rsz <= 1 ? 1 : (int64_t)ceil(sc * (double)Rsz * log((double)Rsz) / o->eps);
+    if (c.s < 1) c.s = 1;
+  }
+  return c;
+}
+
+}  // namespace
+
+extern "C" kr_status tucker_factor_update(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R, const float* X,
+                                          float* const A[], const float* G, int32_t n, const kr_opts* opts,
+                                          kr_report* report) {
+  if (!ctx) return KR_EINVAL;
+  Modes m;
+  KR_TRY(tucker_args(ctx, N, I, R, X, A, G, opts, &m));
+  if (n < 0 || n >= N) return kr_fail(ctx, KR_EINVAL, "tucker_factor_update: mode %d outside [0,%d)", n, N);
+  int64_t Rne = 1;
+  for (int k = 0; k < N; ++k)
+    if (k != n) Rne *= R[k];
+  SolveCfg cfg = cfg_from(opts, Rne);
+  if (report) *report = kr_report{};
+  return kr_factor_step(ctx, m, X, G, n, cfg, opts->seed, opts->call_id, A[n], report);
+}
+
+extern "C" kr_status tucker_als_sweep(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R, const float* X,
+                                      float* const A[], float* G, const kr_opts* opts, int32_t sweeps,
+                                      kr_report* report) {
+  if (!ctx) return KR_EINVAL;
+  Modes m;
+  KR_TRY(tucker_args(ctx, N, I, R, X, A, G, opts, &m));
+  if (sweeps < 0) return kr_fail(ctx, KR_EINVAL, "tucker_als_sweep: sweeps < 0");
+  if (report) *report = kr_report{};
+  cudaEvent_t e0 = ctx->ev[8], e1 = ctx->ev[9];
+  KR_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+  int total_iters = 0;
+  kr_report r = {};
+  for (int k = 0; k < sweeps; ++k) {
+    for (int n = 0; n < N; ++n) {
+      int64_t Rne = 1;
+      for (int j = 0; j < N; ++j)
+        if (j != n) Rne *= R[j];
+      SolveCfg cfg = cfg_from(opts, Rne);
+      const uint64_t cid = opts->call_id + (uint64_t)k * (N + 1) + n;
+      kr_status st = kr_factor_step(ctx, m, X, G, n, cfg, opts->seed, cid, A[n], &r);
+      total_iters += r.iters;
+      if (st != KR_OK && st != KR_ENOTCONV) return st;
+    }
+    // core step: Alg. 2 with b = vec X, K = A(1) (x) ... (x) A(N)
+    SolveCfg cfg = cfg_from(opts, kr_prod_R(m));
+    const uint64_t cid = opts->call_id + (uint64_t)k * (N + 1) + N;
+    kr_status st = kr_solve_device(ctx, m, X, cfg, opts->seed, cid, G, &r);
+    total_iters += r.iters;
+    if (st != KR_OK && st != KR_ENOTCONV) return st;
+  }
+  KR_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (report) {
+    *report = r;
+    report->iters = total_iters;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    report->t_ms[7] = ms;
+  }
+  return KR_OK;
+}

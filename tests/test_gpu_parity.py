@@ -28,7 +28,7 @@ SHAPES = [
 
 
 def dev(a, dtype=torch.float32):
-    return torch.tensor(np.asarray(a), dtype=dtype, device="cuda")
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
 def host(t):
