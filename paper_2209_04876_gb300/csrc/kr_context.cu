@@ -50,6 +50,7 @@ extern "C" void kr_destroy(kr_ctx* ctx) {
   }
   for (auto e : ctx->pool) cudaEventDestroy(e);
   if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->split_buf) cudaFree(ctx->split_buf);
   if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
   for (int i = 0; i < 10; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
@@ -82,6 +83,22 @@ kr_status kr_ws_reserve(kr_ctx* ctx, size_t bytes) {
     return kr_fail(ctx, KR_ENOMEM, "workspace allocation of %zu bytes failed", want);
   }
   ctx->ws_size = want;
+  return KR_OK;
+}
+
+kr_status kr_split_reserve(kr_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->split_size) return KR_OK;
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->split_buf) cudaFree(ctx->split_buf);
+  ctx->split_buf = nullptr;
+  ctx->split_size = 0;
+  cudaError_t e = cudaMalloc((void**)&ctx->split_buf, bytes);
+  if (e != cudaSuccess) {
+    ctx->split_buf = nullptr;
+    cudaGetLastError();
+    return kr_fail(ctx, KR_ENOMEM, "split-K buffer allocation of %zu bytes failed", bytes);
+  }
+  ctx->split_size = bytes;
   return KR_OK;
 }
 

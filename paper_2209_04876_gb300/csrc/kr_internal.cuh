@@ -23,6 +23,9 @@ struct kr_ctx {
   // grow-on-demand device workspace
   char* ws = nullptr;
   size_t ws_size = 0;
+  // split-K partial sums of the mode products (grown on demand)
+  float* split_buf = nullptr;
+  size_t split_size = 0;
   // pinned host buffer for small read-backs
   char* hbuf = nullptr;
   size_t hbuf_size = 0;
@@ -80,6 +83,7 @@ kr_status kr_fail_cuda(kr_ctx* ctx, cudaError_t e, const char* what, const char*
 // Ensures the workspace holds at least `bytes` (synchronises when it grows).
 kr_status kr_ws_reserve(kr_ctx* ctx, size_t bytes);
 kr_status kr_hbuf_reserve(kr_ctx* ctx, size_t bytes);
+kr_status kr_split_reserve(kr_ctx* ctx, size_t bytes);
 
 // Bump allocator over a reserved region.
 struct Carve {
@@ -179,6 +183,7 @@ struct kr_sketch {
   float* cell_w = nullptr;         // ncell: prod_{n<N-1} (1/p_n(i_n)) / s
   float* invpT = nullptr;          // IT: 1/p_{N-1}(i)
   uint32_t* perm = nullptr;        // ncell: cells by decreasing distinct-row count (work balance)
+  uint4* desc = nullptr;           // ncell, in perm order: {cell, start, distinct, weight bits}
   char* mem = nullptr;
 };
 

@@ -25,8 +25,8 @@ template <int TJ>
 __global__ void __launch_bounds__(256) k_mode_product(const float* __restrict__ in, float* __restrict__ out, int64_t P,
                                                        int K, int64_t Q, int J, const float* __restrict__ B, int trans) {
   constexpr int RJ = TJ / 16;  // rows per thread
-  __shared__ float Bs[TK][TJ + 4];
-  __shared__ float Xs[TK][TN + 4];
+  __shared__ __align__(16) float Bs[TK][TJ + 4];
+  __shared__ __align__(16) float Xs[TK][TN + 4];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int j0 = blockIdx.y * TJ;
   const int64_t n0 = (int64_t)blockIdx.x * TN;
@@ -77,10 +77,17 @@ __global__ void __launch_bounds__(256) k_mode_product(const float* __restrict__ 
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
       float bj[RJ], xn[4];
-#pragma unroll
-      for (int a = 0; a < RJ; ++a) bj[a] = Bs[kk][ty * RJ + a];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) xn[c] = Xs[kk][tx * 4 + c];
+      if (RJ == 4) {
+        const float4 t = *reinterpret_cast<const float4*>(&Bs[kk][ty * 4]);
+        bj[0] = t.x; bj[1] = t.y; bj[2] = t.z; bj[3] = t.w;
+      } else {
+        const float2 t = *reinterpret_cast<const float2*>(&Bs[kk][ty * 2]);
+        bj[0] = t.x; bj[1] = t.y;
+      }
+      {
+        const float4 t = *reinterpret_cast<const float4*>(&Xs[kk][tx * 4]);
+        xn[0] = t.x; xn[1] = t.y; xn[2] = t.z; xn[3] = t.w;
+      }
 #pragma unroll
       for (int a = 0; a < RJ; ++a)
 #pragma unroll
@@ -95,6 +102,117 @@ __global__ void __launch_bounds__(256) k_mode_product(const float* __restrict__ 
 #pragma unroll
     for (int c = 0; c < 4; ++c)
       if (out_base[c] >= 0) out[out_base[c] + (int64_t)j * Q] = acc[a][c];
+  }
+}
+
+// Register-blocked SGEMM form of the mode product for Q % 4 == 0 (then four consecutive
+// output columns n = p*Q + q share p and are contiguous in memory). Tile BM rows of B x
+// 128 columns, K staged 32 at a time with the next stage prefetched into registers; each
+// thread owns BM/16 rows x 8 columns (columns tx*4..+3 and 64+tx*4..+3, so the quarter-warp
+// shared-memory reads are conflict-free), float4 loads of the input and float4 stores.
+constexpr int SG_BN = 128, SG_BK = 32;
+
+// Split K: block z covers K rows [z * kchunk, min(K, (z+1) * kchunk)) and writes its
+// partial sum to out + z * zstride (zstride = 0 when gridDim.z == 1).
+template <int BM>
+__global__ void __launch_bounds__(256, 2) k_mode_product_q4(const float* __restrict__ in, float* __restrict__ out,
+                                                         int64_t P, int K, int64_t Q, int J, const float* __restrict__ B,
+                                                         int trans, int kchunk, int64_t zstride) {
+  constexpr int RM = BM / 16;
+  __shared__ __align__(16) float Bs[SG_BK][BM + 4];
+  __shared__ __align__(16) float Xs[SG_BK][SG_BN + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int j0 = blockIdx.y * BM;
+  const int64_t n0 = (int64_t)blockIdx.x * SG_BN;
+  const int64_t NN = P * Q;
+  // input: thread loads float4 column group nl = tid % 32 for k rows tid/32 + 8 i
+  const int nl = (tid & 31) * 4;
+  const int kl = tid >> 5;
+  int64_t in_base = -1;
+  {
+    const int64_t n = n0 + nl;
+    if (n < NN) {
+      const int64_t p = n / Q, q = n - p * Q;
+      in_base = p * K * Q + q;
+    }
+  }
+  const int kend = min(K, (int)(blockIdx.z + 1) * kchunk);
+  float4 xr[4];
+  auto load_stage = [&](int k0) {  // input tile into registers (prefetch)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = k0 + kl + 8 * i;
+      xr[i] = (in_base >= 0 && k < kend) ? __ldg(reinterpret_cast<const float4*>(in + in_base + (int64_t)k * Q))
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  auto store_stage = [&](int k0) {  // registers -> shared; the small B tile straight from L1/L2
+#pragma unroll
+    for (int i = 0; i < 4; ++i) *reinterpret_cast<float4*>(&Xs[kl + 8 * i][nl]) = xr[i];
+#pragma unroll 4
+    for (int i = 0; i < BM * SG_BK / 256; ++i) {
+      const int e = tid + 256 * i;
+      int jj, kk;
+      if (trans) { jj = e % BM; kk = e / BM; } else { kk = e % SG_BK; jj = e / SG_BK; }
+      const int j = j0 + jj, k = k0 + kk;
+      Bs[kk][jj] = (j < J && k < kend) ? (trans ? __ldg(&B[(int64_t)k * J + j]) : __ldg(&B[(int64_t)j * K + k])) : 0.f;
+    }
+  };
+  float acc[RM][8];
+#pragma unroll
+  for (int a = 0; a < RM; ++a)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[a][c] = 0.f;
+  const int kb = blockIdx.z * kchunk;
+  const int ke = min(K, kb + kchunk);
+  out += (int64_t)blockIdx.z * zstride;
+  load_stage(kb);
+  for (int k0 = kb; k0 < ke; k0 += SG_BK) {
+    store_stage(k0);
+    __syncthreads();
+    if (k0 + SG_BK < ke) load_stage(k0 + SG_BK);  // in flight during the compute below
+#pragma unroll 8
+    for (int kk = 0; kk < SG_BK; ++kk) {
+      float av[RM], xv[8];
+#pragma unroll
+      for (int a = 0; a < RM; a += 2) {
+        const float2 t = *reinterpret_cast<const float2*>(&Bs[kk][ty * RM + a]);
+        av[a] = t.x;
+        av[a + 1] = t.y;
+      }
+      const float4 x0 = *reinterpret_cast<const float4*>(&Xs[kk][tx * 4]);
+      const float4 x1 = *reinterpret_cast<const float4*>(&Xs[kk][64 + tx * 4]);
+      xv[0] = x0.x; xv[1] = x0.y; xv[2] = x0.z; xv[3] = x0.w;
+      xv[4] = x1.x; xv[5] = x1.y; xv[6] = x1.z; xv[7] = x1.w;
+#pragma unroll
+      for (int a = 0; a < RM; ++a)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[a][c] = fmaf(av[a], xv[c], acc[a][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t n = n0 + h * 64 + tx * 4;
+    if (n >= NN) continue;
+    const int64_t p = n / Q, q = n - p * Q;
+    const int64_t ob = p * (int64_t)J * Q + q;
+#pragma unroll
+    for (int a = 0; a < RM; ++a) {
+      const int j = j0 + ty * RM + a;
+      if (j >= J) continue;
+      *reinterpret_cast<float4*>(out + ob + (int64_t)j * Q) =
+          make_float4(acc[a][4 * h + 0], acc[a][4 * h + 1], acc[a][4 * h + 2], acc[a][4 * h + 3]);
+    }
+  }
+}
+
+// out[i] = sum_z part[z * n + i] in increasing z (deterministic split-K reduction).
+__global__ void k_splitk_reduce(const float* __restrict__ part, int S, int64_t n, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int z = 0; z < S; ++z) acc += part[(int64_t)z * n + i];
+    out[i] = acc;
   }
 }
 
@@ -125,6 +243,40 @@ kr_status kr_mode_product(kr_ctx* ctx, const float* in, float* out, int64_t P, i
                           int trans) {
   const int64_t NN = P * Q;
   if (NN == 0 || J == 0) return KR_OK;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+  if (Q % 4 == 0 && aligned) {
+    const int BM = J <= 32 ? 32 : 64;
+    dim3 grid((unsigned)((NN + SG_BN - 1) / SG_BN), (unsigned)((J + BM - 1) / BM), 1);
+    // split K when the output alone gives too few blocks to fill the GPU
+    int S = 1, kchunk = K;
+    const int64_t blocks = (int64_t)grid.x * grid.y;
+    const int64_t outn = NN * J;
+    if (K >= 4 * SG_BK && blocks < 2 * ctx->num_sms) {
+      int64_t want = (2 * ctx->num_sms + blocks - 1) / blocks;
+      int64_t maxs = K / SG_BK;
+      S = (int)(want < maxs ? want : maxs);
+      if ((int64_t)S * outn > (int64_t(1) << 24)) S = (int)((int64_t(1) << 24) / outn);
+      if (S < 1) S = 1;
+      kchunk = ((K + S - 1) / S + SG_BK - 1) / SG_BK * SG_BK;
+      S = (K + kchunk - 1) / kchunk;
+    }
+    float* dst = out;
+    if (S > 1) {
+      KR_TRY(kr_split_reserve(ctx, (size_t)S * outn * sizeof(float)));
+      dst = ctx->split_buf;
+    }
+    grid.z = (unsigned)S;
+    if (BM == 32)
+      KR_LAUNCH(ctx, k_mode_product_q4<32>, grid, 256, 0, in, dst, P, K, Q, J, B, trans, kchunk, S > 1 ? outn : 0);
+    else
+      KR_LAUNCH(ctx, k_mode_product_q4<64>, grid, 256, 0, in, dst, P, K, Q, J, B, trans, kchunk, S > 1 ? outn : 0);
+    if (S > 1) {
+      int rg = (int)((outn + 255) / 256);
+      if (rg > ctx->num_sms * 8) rg = ctx->num_sms * 8;
+      KR_LAUNCH(ctx, k_splitk_reduce, rg, 256, 0, dst, S, outn, out);
+    }
+    return KR_OK;
+  }
   if (J <= 32) {
     dim3 grid((unsigned)((NN + TN - 1) / TN), (unsigned)((J + 31) / 32));
     KR_LAUNCH(ctx, k_mode_product<32>, grid, 256, 0, in, out, P, K, Q, J, B, trans);

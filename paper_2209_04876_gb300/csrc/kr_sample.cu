@@ -263,6 +263,16 @@ __global__ void k_export(int64_t ncell, uint32_t IT, const uint32_t* __restrict_
   }
 }
 
+// Cell descriptors in processing order: one 16-byte load per cell in the residual pass.
+__global__ void k_build_desc(const uint32_t* __restrict__ perm, const uint32_t* __restrict__ start,
+                             const uint32_t* __restrict__ nd, const float* __restrict__ cw, int64_t ncell,
+                             uint4* __restrict__ desc) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < ncell; q += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = perm[q];
+    desc[q] = make_uint4(c, start[c], nd[c], __float_as_uint(cw[c]));
+  }
+}
+
 __global__ void k_sum_u32(const uint32_t* __restrict__ v, int64_t n, unsigned long long* out) {
   unsigned long long acc = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) acc += v[i];
@@ -317,6 +327,7 @@ void kr_sketch_own_need(const kr_sketch* sk, Need& nd) {
   nd.add<float>(sk->ncell);
   nd.add<float>(sk->IT);
   nd.add<uint32_t>(sk->ncell);
+  nd.add<uint4>(sk->ncell);
 }
 
 void kr_sketch_layout(kr_sketch* sk, Carve& cv) {
@@ -327,6 +338,7 @@ void kr_sketch_layout(kr_sketch* sk, Carve& cv) {
   sk->cell_w = cv.take<float>(sk->ncell);
   sk->invpT = cv.take<float>(sk->IT);
   sk->perm = cv.take<uint32_t>(sk->ncell);
+  sk->desc = cv.take<uint4>(sk->ncell);
 }
 
 kr_status kr_sketch_check(kr_ctx* ctx, const Modes& m, int64_t s) {
@@ -369,6 +381,8 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
     Carve sc = cv;
     KR_TRY(kr_balance_perm(ctx, sk->cell_nd, ncell, sk->perm, sc));
   }
+  KR_LAUNCH(ctx, k_build_desc, grid_for(ctx, ncell, 256), 256, 0, sk->perm, sk->cell_start, sk->cell_nd, sk->cell_w,
+            ncell, sk->desc);
   KR_CUDA(ctx, cudaMemcpyAsync(sk->invpT, t.invp[N - 1], sizeof(float) * IT, cudaMemcpyDeviceToDevice, ctx->stream));
   KR_LAUNCH(ctx, k_sum_u32, grid_for(ctx, ncell, 256, 2), 256, 0, sk->cell_nd, ncell, dsum);
   KR_TRY(kr_hbuf_reserve(ctx, 4096));

@@ -26,6 +26,7 @@ struct ResidArgs {
   const float* cell_w;
   const float* invpT;
   const uint32_t* perm;  // processing order of the cells (may be null: identity)
+  const uint4* desc;     // per processed cell: {cell, start, distinct, weight bits}
   const float* AT;       // IT x RT
   int IT, RT;
   const float* Y;   // ncell x RT
@@ -42,14 +43,18 @@ struct ResidShape {
   static constexpr int CPW = 32 / G;    // cells per warp
   static constexpr int LDA = RTP + 4;   // shared-memory row stride of A_N (floats)
 };
-constexpr int RESID_U = 4;  // sampled rows in flight per lane group
+constexpr int RESID_D = 4;          // chunks of G rows in flight per lane group
+constexpr int RESID_THREADS = 512;  // 16 warps share one copy of A_N in shared memory
 
-// One lane group per cell: lane g owns columns [g*COLS, (g+1)*COLS) of Y[c] and W[c].
-// For RESID_U rows at a time: load (entry, b~) for all of them first, then the dot
-// products, the group reductions and the axpys, so several loads are in flight.
-// Cells are taken in `perm` order (similar distinct-row counts share a warp).
+// One lane group of G lanes per cell: lane g owns columns [g*COLS, (g+1)*COLS) of Y[c]
+// and W[c]. The cell's (entry, b~) stream is read in chunks of G rows, lane g loading row
+// g of a chunk (distinct addresses, coalesced within the group); a ring of RESID_D chunks
+// per lane keeps RESID_D*G rows in flight. Each row is broadcast to the group with a
+// shuffle, its dot product with y is reduced over the group, and the axpy into w reads
+// the A_N row from shared memory again. Cells are taken in `perm` order (similar
+// distinct-row counts share a warp).
 template <int RTP, bool SMEM_A>
-__global__ void __launch_bounds__(256) k_resid(ResidArgs a) {
+__global__ void __launch_bounds__(RESID_THREADS, 2) k_resid(ResidArgs a) {
   using S = ResidShape<RTP>;
   constexpr int COLS = S::COLS, G = S::G, CPW = S::CPW, LDA = S::LDA;
   extern __shared__ float4 sm4[];
@@ -66,74 +71,117 @@ __global__ void __launch_bounds__(256) k_resid(ResidArgs a) {
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int g = lane % G, slot = lane / G;
+  const int gbase = slot * G;  // first lane of this group
   const int c0col = g * COLS;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   double obj = 0.0;
+  // descriptor of this lane group's first cell; the next one is prefetched while the
+  // current cell is processed
+  uint4 dnext = make_uint4(0u, 0u, 0u, 0u);
+  if (gw * CPW + slot < a.ncell) dnext = __ldg(&a.desc[gw * CPW + slot]);
   for (int64_t q0 = gw * CPW; q0 < a.ncell; q0 += warps * CPW) {
     const int64_t q = q0 + slot;
     const bool live = q < a.ncell;
-    const int64_t c = live ? (a.perm ? (int64_t)a.perm[q] : q) : 0;
-    const uint32_t n = live ? a.cell_nd[c] : 0u;
-    const uint32_t base = live ? a.cell_start[c] : 0u;
-    const float cw = live ? a.cell_w[c] : 0.f;
-    float y[COLS], w[COLS];
-#pragma unroll
-    for (int k = 0; k < COLS; ++k) {
-      int r = c0col + k;
-      y[k] = (live && r < RT) ? a.Y[c * RT + r] : 0.f;
-      w[k] = 0.f;
+    const uint4 dc = dnext;
+    {
+      const int64_t qn = q + warps * CPW;
+      if (qn < a.ncell) dnext = __ldg(&a.desc[qn]);
     }
+    const int64_t c = live ? (int64_t)dc.x : 0;
+    const uint32_t n = live ? dc.z : 0u;
+    const uint32_t base = live ? dc.y : 0u;
+    const float cw = live ? __uint_as_float(dc.w) : 0.f;
+    float y[COLS], w[COLS];
+    if (live && (RT % 4) == 0 && c0col + COLS <= RT) {
+      const float4* yr = reinterpret_cast<const float4*>(a.Y + c * RT + c0col);
+#pragma unroll
+      for (int v = 0; v < COLS / 4; ++v) {
+        const float4 t = __ldg(&yr[v]);
+        y[4 * v + 0] = t.x; y[4 * v + 1] = t.y; y[4 * v + 2] = t.z; y[4 * v + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) {
+        int r = c0col + k;
+        y[k] = (live && r < RT) ? a.Y[c * RT + r] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < COLS; ++k) w[k] = 0.f;
     float objc = 0.f;
     uint32_t nmax = n;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, off));
-    for (uint32_t j = 0; j < nmax; j += RESID_U) {
-      uint32_t e[RESID_U];
-      float bj[RESID_U];
+    const uint32_t nchunk = (nmax + G - 1) / G;
+    uint32_t ring_e[RESID_D];
+    float ring_b[RESID_D];
 #pragma unroll
-      for (int u = 0; u < RESID_U; ++u) {
-        const bool act = j + u < n;
-        e[u] = act ? __ldg(&a.ent[base + j + u]) : 0u;
-        bj[u] = act ? __ldg(&a.bt[base + j + u]) : 0.f;
-      }
-      float av[RESID_U][COLS];
-      float part[RESID_U];
+    for (int d = 0; d < RESID_D; ++d) {
+      const uint32_t j = (uint32_t)d * G + g;
+      const bool act = j < n;
+      ring_e[d] = act ? __ldg(&a.ent[base + j]) : 0u;
+      ring_b[d] = act ? __ldg(&a.bt[base + j]) : 0.f;
+    }
+    for (uint32_t k0 = 0; k0 < nchunk; k0 += RESID_D) {
 #pragma unroll
-      for (int u = 0; u < RESID_U; ++u) {
-        const int it = (int)(e[u] & 0xFFFFu);
-        if (SMEM_A) {
-          const float4* row = reinterpret_cast<const float4*>(sA + (size_t)it * LDA + c0col);
-#pragma unroll
-          for (int v = 0; v < COLS / 4; ++v) {
-            float4 t = row[v];
-            av[u][4 * v + 0] = t.x; av[u][4 * v + 1] = t.y; av[u][4 * v + 2] = t.z; av[u][4 * v + 3] = t.w;
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < COLS; ++k) {
-            int r = c0col + k;
-            av[u][k] = r < RT ? __ldg(&a.AT[(int64_t)it * RT + r]) : 0.f;
-          }
+      for (int d = 0; d < RESID_D; ++d) {
+        const uint32_t e_mine = ring_e[d];
+        const float b_mine = ring_b[d];
+        {  // refill this slot with chunk k0 + d + RESID_D
+          const uint32_t j = (k0 + d + RESID_D) * G + g;
+          const bool act = j < n;
+          ring_e[d] = act ? __ldg(&a.ent[base + j]) : 0u;
+          ring_b[d] = act ? __ldg(&a.bt[base + j]) : 0.f;
         }
-        float p = av[u][0] * y[0];
+        if (k0 + d >= nchunk) continue;  // warp-uniform
 #pragma unroll
-        for (int k = 1; k < COLS; ++k) p = fmaf(av[u][k], y[k], p);
-        part[u] = p;
-      }
+        for (int sidx = 0; sidx < G; ++sidx) {
+          const uint32_t e = __shfl_sync(0xffffffffu, e_mine, gbase + sidx);
+          const float bj = __shfl_sync(0xffffffffu, b_mine, gbase + sidx);
+          const int it = (int)(e & 0xFFFFu);
+          float p = 0.f;
+          if (SMEM_A) {
+            const float4* row = reinterpret_cast<const float4*>(sA + (size_t)it * LDA + c0col);
 #pragma unroll
-      for (int off = G / 2; off > 0; off >>= 1)
+            for (int v = 0; v < COLS / 4; ++v) {
+              const float4 t = row[v];
+              p = fmaf(t.x, y[4 * v + 0], p);
+              p = fmaf(t.y, y[4 * v + 1], p);
+              p = fmaf(t.z, y[4 * v + 2], p);
+              p = fmaf(t.w, y[4 * v + 3], p);
+            }
+          } else {
 #pragma unroll
-        for (int u = 0; u < RESID_U; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], off);
+            for (int k = 0; k < COLS; ++k) {
+              int r = c0col + k;
+              if (r < RT) p = fmaf(__ldg(&a.AT[(int64_t)it * RT + r]), y[k], p);
+            }
+          }
 #pragma unroll
-      for (int u = 0; u < RESID_U; ++u) {
-        const int it = (int)(e[u] & 0xFFFFu);
-        const float om = (float)(e[u] >> 16) * cw * sInvp[it];  // 0 for padding rows (count 0)
-        const float res = bj[u] - part[u];
-        const float rr = om * res;
+          for (int off = G / 2; off > 0; off >>= 1) p += __shfl_xor_sync(0xffffffffu, p, off);
+          const float om = (float)(e >> 16) * cw * sInvp[it];  // 0 for rows past the cell (count 0)
+          const float res = bj - p;
+          const float rr = om * res;
+          if (SMEM_A) {
+            const float4* row = reinterpret_cast<const float4*>(sA + (size_t)it * LDA + c0col);
 #pragma unroll
-        for (int k = 0; k < COLS; ++k) w[k] = fmaf(rr, av[u][k], w[k]);
-        objc = fmaf(rr, res, objc);
+            for (int v = 0; v < COLS / 4; ++v) {
+              const float4 t = row[v];
+              w[4 * v + 0] = fmaf(rr, t.x, w[4 * v + 0]);
+              w[4 * v + 1] = fmaf(rr, t.y, w[4 * v + 1]);
+              w[4 * v + 2] = fmaf(rr, t.z, w[4 * v + 2]);
+              w[4 * v + 3] = fmaf(rr, t.w, w[4 * v + 3]);
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < COLS; ++k) {
+              int r = c0col + k;
+              if (r < RT) w[k] = fmaf(rr, __ldg(&a.AT[(int64_t)it * RT + r]), w[k]);
+            }
+          }
+          objc = fmaf(rr, res, objc);
+        }
       }
     }
     if (live) {
@@ -146,7 +194,7 @@ __global__ void __launch_bounds__(256) k_resid(ResidArgs a) {
     }
   }
   // block reduction of the objective partial (FP64)
-  __shared__ double red[8];
+  __shared__ double red[RESID_THREADS / 32];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) obj += __shfl_xor_sync(0xffffffffu, obj, off);
   if (lane == 0) red[threadIdx.x >> 5] = obj;
@@ -205,17 +253,28 @@ __global__ void k_update(float* __restrict__ x, const float* __restrict__ d, flo
 }
 
 // Deterministic sum of per-block partials: out[k] = sum_b part[stride*b + k] (k < stride),
-// the last component combined with max (flags).
-__global__ void k_reduce_partials(const double* __restrict__ part, int nb, int stride, int maxlast,
-                                  double* __restrict__ out) {
-  int k = threadIdx.x;
-  if (k >= stride) return;
-  double acc = 0.0;
-  for (int b = 0; b < nb; ++b) {
-    double v = part[(int64_t)stride * b + k];
-    acc = (maxlast && k == stride - 1) ? fmax(acc, v) : acc + v;
+// the last component combined with max (flags) when maxlast. One block of 256 threads:
+// fixed strided partial sums, then a fixed-order tree, so the result is reproducible.
+__global__ void __launch_bounds__(256) k_reduce_partials(const double* __restrict__ part, int nb, int stride,
+                                                         int maxlast, double* __restrict__ out) {
+  __shared__ double red[256];
+  for (int k = 0; k < stride; ++k) {
+    const bool mx = maxlast && k == stride - 1;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      const double v = part[(int64_t)stride * b + k];
+      acc = mx ? fmax(acc, v) : acc + v;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+      if ((int)threadIdx.x < off) red[threadIdx.x] = mx ? fmax(red[threadIdx.x], red[threadIdx.x + off])
+                                                       : red[threadIdx.x] + red[threadIdx.x + off];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = red[0];
+    __syncthreads();
   }
-  out[k] = acc;
 }
 
 __global__ void k_dot_self(const float* __restrict__ x, int64_t n, double* __restrict__ part) {
@@ -291,18 +350,19 @@ kr_status launch_resid_t(kr_ctx* ctx, const ResidArgs& a, int grid, int* used) {
   if (smemA + smemI <= ctx->smem_optin) {
     KR_CUDA(ctx, cudaFuncSetAttribute(k_resid<RTP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(smemA + smemI)));
-    KR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid<RTP, true>, 256, smemA + smemI));
+    KR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid<RTP, true>, RESID_THREADS,
+                                                               smemA + smemI));
     int g = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
     if (g > grid) g = grid;
-    KR_LAUNCH(ctx, (k_resid<RTP, true>), g, 256, smemA + smemI, a);
+    KR_LAUNCH(ctx, (k_resid<RTP, true>), g, RESID_THREADS, smemA + smemI, a);
     *used = g;
     return KR_OK;
   }
   KR_CUDA(ctx, cudaFuncSetAttribute(k_resid<RTP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemI));
-  KR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid<RTP, false>, 256, smemI));
+  KR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid<RTP, false>, RESID_THREADS, smemI));
   int g = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
   if (g > grid) g = grid;
-  KR_LAUNCH(ctx, (k_resid<RTP, false>), g, 256, smemI, a);
+  KR_LAUNCH(ctx, (k_resid<RTP, false>), g, RESID_THREADS, smemI, a);
   *used = g;
   return KR_OK;
   return KR_OK;
@@ -322,6 +382,7 @@ kr_status kr_sketch_resid(kr_ctx* ctx, const kr_sketch* sk, const float* AT, int
   a.cell_w = sk->cell_w;
   a.invpT = sk->invpT;
   a.perm = sk->perm;
+  a.desc = sk->desc;
   a.AT = AT;
   a.IT = sk->IT;
   a.RT = RT;
@@ -485,7 +546,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     if (cfg.lambda > 0.0) KR_LAUNCH(ctx, k_sub_lambda_x, ublk, 256, 0, bf.g, bf.x, (float)cfg.lambda, R);
     KR_TRY(kr_precond_apply(ctx, t, cfg.lambda, bf.g, bf.d, bf.t0, bf.t1));
     KR_LAUNCH(ctx, k_update, ublk, 256, 0, bf.x, bf.d, (float)cfg.alpha, R, bf.part);
-    KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, bf.part, ublk, 3, 1, bf.red);
+    KR_LAUNCH(ctx, k_reduce_partials, 1, 256, 0, bf.part, ublk, 3, 1, bf.red);
     KR_CUDA(ctx, cudaMemcpyAsync(h, bf.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     StepCheck sc = step_check(h, cfg.tol, &prev_step, &min_step, &min_rel, &grow, &since_min, &rel, -1.0);
@@ -507,9 +568,9 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   // final sampled objective at the returned x (FP64 accumulation)
   int used = 0;
   KR_TRY(forward_resid(ctx, m, &sk, bf, nblk, &used));
-  KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, bf.part, used, 1, 0, bf.red);
+  KR_LAUNCH(ctx, k_reduce_partials, 1, 256, 0, bf.part, used, 1, 0, bf.red);
   KR_LAUNCH(ctx, k_dot_self, ublk, 256, 0, bf.x, R, bf.part + 1024);
-  KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, bf.part + 1024, ublk, 1, 0, bf.red + 1);
+  KR_LAUNCH(ctx, k_reduce_partials, 1, 256, 0, bf.part + 1024, ublk, 1, 0, bf.red + 1);
   KR_CUDA(ctx, cudaMemcpyAsync(h, bf.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   KR_CUDA(ctx, cudaEventRecord(ev[5], ctx->stream));
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -661,7 +722,7 @@ extern "C" kr_status kron_sketch_residual(kr_ctx* ctx, const kr_sketch* sk, cons
   int used = 0;
   KR_TRY(forward_resid(ctx, m, sk, bf, nblk, &used));
   KR_TRY(backward(ctx, m, bf));
-  KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, bf.part, used, 1, 0, bf.red);
+  KR_LAUNCH(ctx, k_reduce_partials, 1, 256, 0, bf.part, used, 1, 0, bf.red);
   KR_CUDA(ctx, cudaMemcpyAsync(ctx->hbuf, bf.red, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (obj) *obj = *(double*)ctx->hbuf;
@@ -704,10 +765,10 @@ extern "C" kr_status kron_objective(kr_ctx* ctx, const kr_factors* f, const floa
   }
   KR_TRY(kr_kron_apply2(ctx, N, din, dout, B, tr, x, Y, t0, t1));
   KR_LAUNCH(ctx, k_full_obj, nblk, 256, 0, Y, m.A[N - 1], b, ncell, m.I[N - 1], RT, part);
-  KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, part, nblk, 1, 0, red);
+  KR_LAUNCH(ctx, k_reduce_partials, 1, 256, 0, part, nblk, 1, 0, red);
   const int ublk = grid_cap(ctx, R, 256, 4);
   KR_LAUNCH(ctx, k_dot_self, ublk, 256, 0, x, R, part + nblk);
-  KR_LAUNCH(ctx, k_reduce_partials, 1, 32, 0, part + nblk, ublk, 1, 0, red + 1);
+  KR_LAUNCH(ctx, k_reduce_partials, 1, 256, 0, part + nblk, ublk, 1, 0, red + 1);
   KR_CUDA(ctx, cudaMemcpyAsync(ctx->hbuf, red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   double* h = (double*)ctx->hbuf;

@@ -1,0 +1,133 @@
+"""Parity at the full sizes of the paper-shaped workloads, in the bench's launch
+configuration, against the CPU oracle (FP64): the whole sketch bit-exactly, the
+(1+eps) guarantee against the closed-form optimum, and stationarity of the returned x
+for the sampled problem; Tucker rows the oracle can recompute one by one."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2209_04876_gb300 as kr
+from oracle import kron as ko
+from oracle import tucker as tk
+from workloads import CONFIGS, kron_problem, tucker_init, tucker_tensor
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    kr.lib()
+
+
+def dev(a, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def test_bench_workload_512cubed_full_size():
+    """The bench workload (N=3, 512x32 log-normal rows, b of length 512^3, eps=0.1) with
+    the bench's solver settings."""
+    w = CONFIGS["kron_n3_512x32_lognormal"]
+    prob = kron_problem(w["I"], w["R"], dist=w["dist"], seed=2209, noise_rel=w["noise_rel"])
+    As32 = [np.ascontiguousarray(A, dtype=np.float32) for A in prob["As"]]
+    b32 = np.ascontiguousarray(prob["b"], dtype=np.float32)
+    As_d = [dev(A) for A in As32]
+    b_d = dev(b32)
+    eps, seed, cid = w["eps"], 1, 0
+    x, rep = kr.kron_regress(As_d, b_d, eps=eps, seed=seed, call_id=cid, tol=1e-7, max_iter=200)
+    assert rep["converged"] and rep["s"] == ko.sample_count(32 ** 3, eps)
+    # 1) the sketch: every draw, bit-exact (grouped rows and multiplicities)
+    tab = kr.kron_leverage(As_d)
+    sk = kr.kron_sketch(As_d, tab["cdf"], tab["prob"], b_d, rep["s"], seed, cid)
+    keys, counts, omega, bt = (v.cpu().numpy() for v in sk.export())
+    sk.free()
+    assert keys.shape[0] == rep["distinct"]
+    cdfs = [c.cpu().numpy() for c in tab["cdf"]]
+    probs = [p.cpu().numpy() for p in tab["prob"]]
+    idx = ko.sample_draws(cdfs, rep["s"], seed, cid)
+    rk, rc = ko.group_samples(idx, w["I"])
+    del idx
+    np.testing.assert_array_equal(keys, rk)
+    np.testing.assert_array_equal(counts, rc)
+    np.testing.assert_array_equal(bt, b32[rk])
+    # 2) Thm 4.5: f(x) <= (1 + eps) OPT with OPT from the closed form (FP64)
+    As64 = [A.astype(np.float64) for A in As32]
+    b64 = b32.astype(np.float64)
+    xh = x.cpu().numpy().astype(np.float64)
+    opt = ko.objective(As64, b64, ko.closed_form_ls(As64, b64), 0.0)
+    f = ko.objective(As64, b64, xh, 0.0)
+    assert f <= (1 + eps) * opt
+    # 3) x is the sampled minimiser to FP32 working accuracy: the preconditioned FP64
+    #    gradient of the sampled objective at x is small relative to x
+    smp = ko.Sample(rk, rc, ko.sample_weights(rk, rc, probs, w["I"], rep["s"]), rep["s"])
+    g = ko.sampled_gradient(As64, b64[rk], smp, xh, 0.0)
+    step = ko.KronPreconditioner(As64, 0.0).apply(g)
+    assert np.linalg.norm(step) <= 1e-5 * np.linalg.norm(xh)
+    # the reported sampled objective is the oracle's at x
+    f_s = ko.sampled_objective(As64, b64[rk], smp, xh, 0.0)
+    assert abs(rep["obj_sampled"] - f_s) <= 1e-5 * f_s
+
+
+def test_n2_256x16_exact_sampled_solution():
+    """N=2, A(n) 256x16 Gaussian, b = K x_true + 0.01 N(0,1): x against the dense QR
+    solution of the same sampled system."""
+    w = CONFIGS["kron_n2_256x16"]
+    prob = kron_problem(w["I"], w["R"], dist="gauss", seed=1, noise_abs=w["noise_abs"])
+    As = [np.asarray(A, np.float32).astype(np.float64) for A in prob["As"]]
+    b = prob["b"].astype(np.float32).astype(np.float64)
+    x, rep = kr.kron_regress([dev(A) for A in As], dev(b), eps=w["eps"], seed=3, call_id=4, tol=1e-7,
+                             max_iter=300)
+    tab = kr.kron_leverage([dev(A) for A in As])
+    smp = ko.draw_sample(As, rep["s"], 3, 4, cdfs=[c.cpu().numpy() for c in tab["cdf"]],
+                         probs=[p.cpu().numpy() for p in tab["prob"]])
+    assert smp.keys.shape[0] == rep["distinct"]
+    xs = ko.sampled_exact_solve(As, b[smp.keys], smp, 0.0)
+    xg = x.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(xg - xs) <= 1e-5 * np.linalg.norm(xs)
+    opt = ko.objective(As, b, ko.closed_form_ls(As, b), 0.0)
+    assert ko.objective(As, b, xg, 0.0) <= (1 + w["eps"]) * opt
+
+
+def test_tucker_256cubed_rank16():
+    """Tucker workload: 256^3 tensor of multilinear rank (16,16,16) + 1% noise, lambda =
+    1e-3, eps = 0.1. (a) Alg. 3 rows at full size against the oracle's Alg. 3 on the same
+    per-row sketches (a sample of rows); (b) 10 sampled sweeps reach exact-ALS quality."""
+    I, R = [256, 256, 256], [16, 16, 16]
+    data = tucker_tensor(I, R, seed=11, noise_rel=0.01)
+    X = np.ascontiguousarray(data["X"], dtype=np.float32)
+    X64 = X.astype(np.float64)
+    As = [np.asarray(A, np.float32).astype(np.float64) for A in tucker_init(I, R, seed=12)]
+    G = tk.initial_core(X64, As).astype(np.float32).astype(np.float64)
+    lam, eps, seed = 1e-3, 0.1, 5
+    # (a) one factor step of mode 1
+    n = 1
+    A_gpu = [dev(A) for A in As]
+    rep = kr.tucker_factor_update(dev(X), A_gpu, dev(G), n, lam, eps=eps, seed=seed, call_id=7, tol=1e-7,
+                                  max_iter=300)
+    assert rep["converged"]
+    others = [m for m in range(3) if m != n]
+    tab = kr.kron_leverage([A_gpu[m] for m in others])
+    cdfs = [c.cpu().numpy() for c in tab["cdf"]]
+    probs = [p.cpu().numpy() for p in tab["prob"]]
+    rows = [0, 1, 77, 128, 255]
+    A_ref, _ = tk.fast_factor_matrix_update(X64, As, G, n, lam, eps, seed, 7, tol=1e-12, max_iter=3000, rows=rows,
+                                            cdfs=cdfs, probs=probs)
+    got = A_gpu[n].cpu().numpy().astype(np.float64)
+    bar = max(1e-5, 4 * np.finfo(np.float32).eps * np.linalg.cond(tk.unfold(G, n)))
+    for i in rows:
+        assert np.linalg.norm(got[i] - A_ref[i]) <= bar * np.linalg.norm(A_ref[i])
+    # (b) 10 sweeps
+    A_gpu = [dev(A) for A in As]
+    G_gpu = dev(G)
+    kr.tucker_als_sweep(dev(X), A_gpu, G_gpu, lam, eps=eps, sweeps=10, seed=seed, call_id=100, tol=1e-7,
+                        max_iter=300)
+    rre_gpu = tk.rre(X64, G_gpu.cpu().numpy().astype(np.float64).reshape(R),
+                     [A.cpu().numpy().astype(np.float64) for A in A_gpu])
+    he = []
+    tk.tucker_als(X64, As, G, lam, 10, sampled=False, history=he)
+    assert rre_gpu <= (1 + 2 * eps) * he[-1]
+    assert rre_gpu < 2e-4
