@@ -31,6 +31,7 @@ extern "C" kr_status kr_create(kr_ctx** out, void* stream) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   ctx->smem_optin = (size_t)optin;
   for (int i = 0; i < 10 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ctx->pev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     delete ctx;
     return e == cudaErrorMemoryAllocation ? KR_ENOMEM : KR_ECUDA;
@@ -54,6 +55,8 @@ extern "C" void kr_destroy(kr_ctx* ctx) {
   if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
   for (int i = 0; i < 10; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  for (int i = 0; i < 2; ++i)
+    if (ctx->pev[i]) cudaEventDestroy(ctx->pev[i]);
   delete ctx;
 }
 

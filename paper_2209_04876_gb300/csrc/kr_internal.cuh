@@ -30,6 +30,7 @@ struct kr_ctx {
   char* hbuf = nullptr;
   size_t hbuf_size = 0;
   cudaEvent_t ev[10] = {};
+  cudaEvent_t pev[2] = {};  // completion of the two in-flight Richardson norm read-backs
   // per-kernel timing (instrumentation)
   bool timing = false;
   struct Timed {

@@ -107,20 +107,42 @@ __global__ void k_sample_idx(SampleModes sm, int64_t s, uint32_t k0, uint32_t k1
 // Draws come in nrow batches of s_row (one batch per Tucker factor row; nrow = 1 for a
 // plain solve). Draw t of batch r uses Philox counter row row0 + r. The key is
 // cell * IT + i_T with cell = r * ncell_inner + (i_1..i_{N-1}) (the linear row index of
-// the batched system).
-__global__ void k_sample_keys(SampleModes sm, int64_t s_row, int nrow, uint32_t k0, uint32_t k1, uint32_t row0,
-                              uint32_t cid, int64_t ncell_inner, uint32_t* __restrict__ keys,
-                              uint32_t* __restrict__ cell_cnt) {
+// the batched system). The histogram atomic returns each draw's rank inside its cell
+// (rank[t]), so the scatter needs no atomics. Templated on N so the per-draw indices
+// and table pointers stay in registers.
+template <int N>
+__global__ void __launch_bounds__(256) k_sample_keys(SampleModes sm, int64_t s_row, int nrow, uint32_t k0,
+                                                     uint32_t k1, uint32_t row0, uint32_t cid, int64_t ncell_inner,
+                                                     uint32_t* __restrict__ keys, uint32_t* __restrict__ rank,
+                                                     uint32_t* __restrict__ cell_cnt) {
   __shared__ uint64_t buf[THR_SMEM];
-  const uint64_t* thr[KR_MAX_MODES];
-  load_thr(sm, buf, thr);
-  const int N = sm.N;
-  const uint32_t IT = sm.I[N - 1];
+  const uint64_t* thr[N];
+  int In[N];
+  {
+    int tot = 0;
+#pragma unroll
+    for (int n = 0; n < N; ++n) tot += sm.I[n];
+    int off = 0;
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      In[n] = sm.I[n];
+      if (tot <= THR_SMEM) {
+        for (int i = threadIdx.x; i < In[n]; i += blockDim.x) buf[off + i] = sm.thr[n][i];
+        thr[n] = buf + off;
+        off += In[n];
+      } else {
+        thr[n] = sm.thr[n];
+      }
+    }
+    __syncthreads();
+  }
+  const uint32_t IT = (uint32_t)In[N - 1];
   const int64_t total = s_row * nrow;
+  const uint32_t lane = threadIdx.x & 31;
   for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x; t0 < total; t0 += (int64_t)gridDim.x * blockDim.x) {
-    int64_t t = t0 + threadIdx.x;
-    bool live = t < total;
-    uint32_t cell = 0;
+    const int64_t t = t0 + threadIdx.x;
+    const bool live = t < total;
+    uint32_t cell = 0, key = 0;
     if (live) {
       uint32_t r = 0;
       int64_t tl = t;
@@ -128,41 +150,40 @@ __global__ void k_sample_keys(SampleModes sm, int64_t s_row, int nrow, uint32_t 
         r = (uint32_t)((uint64_t)t / (uint64_t)s_row);
         tl = t - (int64_t)r * s_row;
       }
-      int idx[KR_MAX_MODES];
-      draw(sm, thr, (uint64_t)tl, k0, k1, row0 + r, cid, idx);
-      for (int n = 0; n < N - 1; ++n) cell = cell * (uint32_t)sm.I[n] + (uint32_t)idx[n];
+      int idx[N];
+#pragma unroll
+      for (int k = 0; 2 * k < N; ++k) {
+        const uint4 w = philox4x32_10(
+            make_uint4((uint32_t)tl, (uint32_t)((uint64_t)tl >> 32), (uint32_t)k + 256u * (row0 + r), cid), k0, k1);
+        idx[2 * k] = search_thr(thr[2 * k], In[2 * k], u53(w.x, w.y));
+        if (2 * k + 1 < N) idx[2 * k + 1] = search_thr(thr[2 * k + 1], In[2 * k + 1], u53(w.z, w.w));
+      }
+#pragma unroll
+      for (int n = 0; n < N - 1; ++n) cell = cell * (uint32_t)In[n] + (uint32_t)idx[n];
       cell += r * (uint32_t)ncell_inner;
-      keys[t] = cell * IT + (uint32_t)idx[N - 1];
+      key = cell * IT + (uint32_t)idx[N - 1];
+      keys[t] = key;
     }
-    // warp-aggregated histogram increment
-    unsigned act = __ballot_sync(0xffffffffu, live);
+    // warp-aggregated histogram increment; the returned base gives each draw its rank
+    const unsigned act = __ballot_sync(0xffffffffu, live);
     if (live) {
-      unsigned peers = __match_any_sync(act, cell);
-      int leader = __ffs(peers) - 1;
-      if ((int)(threadIdx.x & 31) == leader) atomicAdd(&cell_cnt[cell], (uint32_t)__popc(peers));
+      const unsigned peers = __match_any_sync(act, cell);
+      const int leader = __ffs(peers) - 1;
+      uint32_t base = 0;
+      if ((int)lane == leader) base = atomicAdd(&cell_cnt[cell], (uint32_t)__popc(peers));
+      base = __shfl_sync(peers, base, leader);
+      rank[t] = base + __popc(peers & ((1u << lane) - 1u));
     }
   }
 }
 
-// Scatter i_T of every draw into its cell's slot range.
-__global__ void k_scatter(const uint32_t* __restrict__ keys, int64_t s, uint32_t IT, const uint32_t* __restrict__ start,
-                          uint32_t* __restrict__ cursor, uint16_t* __restrict__ slot) {
-  for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x; t0 < s; t0 += (int64_t)gridDim.x * blockDim.x) {
-    int64_t t = t0 + threadIdx.x;
-    bool live = t < s;
-    uint32_t key = live ? keys[t] : 0u;
-    uint32_t cell = key / IT;
-    unsigned act = __ballot_sync(0xffffffffu, live);
-    if (live) {
-      unsigned peers = __match_any_sync(act, cell);
-      int leader = __ffs(peers) - 1;
-      int lane = threadIdx.x & 31;
-      uint32_t base = 0;
-      if (lane == leader) base = atomicAdd(&cursor[cell], (uint32_t)__popc(peers));
-      base = __shfl_sync(peers, base, leader);
-      uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-      slot[start[cell] + base + rank] = (uint16_t)(key - cell * IT);
-    }
+// Scatter i_T of every draw into its cell's slot range (position = cell start + rank).
+__global__ void k_scatter(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ rank, int64_t s, uint32_t IT,
+                          const uint32_t* __restrict__ start, uint16_t* __restrict__ slot) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < s; t += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t key = keys[t];
+    const uint32_t cell = key / IT;
+    slot[start[cell] + rank[t]] = (uint16_t)(key - cell * IT);
   }
 }
 
@@ -190,15 +211,18 @@ __global__ void k_dedup(SampleModes sm, int64_t ncell, int64_t ncell_inner, int6
   const uint32_t lo = min(IT, lane * chunk), hi = min(IT, lo + chunk);
   for (int64_t c = (int64_t)blockIdx.x * DEDUP_WARPS + warp; c < ncell; c += (int64_t)gridDim.x * DEDUP_WARPS) {
     const uint32_t n = cnt[c], base = start[c];
-    const int64_t c_in = c % ncell_inner, row = c / ncell_inner;
+    const uint32_t c32 = (uint32_t)c, nci = (uint32_t)ncell_inner;
+    const uint32_t row32 = c32 / nci;
+    const int64_t c_in = (int64_t)(c32 - row32 * nci), row = row32;
     if (lane == 0) {
       // weight of the cell: prod over the first N-1 coordinates of 1/p
       float w = inv_s;
-      int64_t rem = c_in;
+      uint32_t rem = (uint32_t)c_in;
       for (int m = sm.N - 2; m >= 0; --m) {
-        int i = (int)(rem % sm.I[m]);
-        rem /= sm.I[m];
-        w *= sm.invp[m][i];
+        const uint32_t Im = (uint32_t)sm.I[m];
+        const uint32_t q = rem / Im;
+        w *= sm.invp[m][rem - q * Im];
+        rem = q;
       }
       cell_w[c] = w;
     }
@@ -356,22 +380,40 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   const uint32_t IT = (uint32_t)sk->IT;
   uint32_t* keys = cv.take<uint32_t>(s);
   uint32_t* cnt = cv.take<uint32_t>(ncell);
-  uint32_t* cursor = cv.take<uint32_t>(ncell);
+  uint32_t* rank = cv.take<uint32_t>(s);
   uint16_t* slot = cv.take<uint16_t>(s);
   unsigned long long* dsum = cv.take<unsigned long long>(1);
   if (cv.off > cv.cap) return kr_fail(ctx, KR_ENOMEM, "sketch: workspace too small");
   SampleModes sm = make_sample_modes(m, t);
   KR_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * ncell, ctx->stream));
-  KR_CUDA(ctx, cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * ncell, ctx->stream));
   KR_CUDA(ctx, cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), ctx->stream));
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32), cid = (uint32_t)call_id;
-  KR_LAUNCH(ctx, k_sample_keys, grid_for(ctx, s, 256), 256, 0, sm, sk->s_row, sk->nrow, k0, k1, (uint32_t)row, cid,
-            sk->ncell_inner, keys, cnt);
+  {
+    const int gs = grid_for(ctx, s, 256);
+#define KR_SAMPLE_KEYS(NN)                                                                                \
+  case NN:                                                                                                \
+    KR_LAUNCH(ctx, k_sample_keys<NN>, gs, 256, 0, sm, sk->s_row, sk->nrow, k0, k1, (uint32_t)row, cid,     \
+              sk->ncell_inner, keys, rank, cnt);                                                          \
+    break;
+    switch (N) {
+      KR_SAMPLE_KEYS(1)
+      KR_SAMPLE_KEYS(2)
+      KR_SAMPLE_KEYS(3)
+      KR_SAMPLE_KEYS(4)
+      KR_SAMPLE_KEYS(5)
+      KR_SAMPLE_KEYS(6)
+      KR_SAMPLE_KEYS(7)
+      KR_SAMPLE_KEYS(8)
+      default:
+        return kr_fail(ctx, KR_EINVAL, "sketch: N=%d", N);
+    }
+#undef KR_SAMPLE_KEYS
+  }
   {
     Carve sc = cv;  // scan scratch is transient
     KR_TRY(kr_scan_u32(ctx, cnt, sk->cell_start, ncell, sc));
   }
-  KR_LAUNCH(ctx, k_scatter, grid_for(ctx, s, 256), 256, 0, keys, s, IT, sk->cell_start, cursor, slot);
+  KR_LAUNCH(ctx, k_scatter, grid_for(ctx, s, 256), 256, 0, keys, rank, s, IT, sk->cell_start, slot);
   const size_t dsmem = (size_t)DEDUP_WARPS * IT * sizeof(uint32_t);
   KR_CUDA(ctx, cudaFuncSetAttribute(k_dedup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
   KR_LAUNCH(ctx, k_dedup, grid_for(ctx, ncell, DEDUP_WARPS, 8), DEDUP_WARPS * 32, dsmem, sm, ncell, sk->ncell_inner,
@@ -395,7 +437,7 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
 void kr_sketch_scratch_need(int64_t s, int64_t ncell, Need& nd) {
   nd.add<uint32_t>(s);
   nd.add<uint32_t>(ncell);
-  nd.add<uint32_t>(ncell);
+  nd.add<uint32_t>(s);
   nd.add<uint16_t>(s);
   nd.add<unsigned long long>(1);
   kr_scan_need(ncell, nd);

@@ -252,6 +252,79 @@ __global__ void k_update(float* __restrict__ x, const float* __restrict__ d, flo
   }
 }
 
+// x <- x + alpha d, then {||alpha d||^2, ||x||^2, non-finite flag} reduced in FP64 into
+// out[0..2]: block partials first, then the last block to finish sums them in block order
+// (deterministic) and re-arms the ticket counter.
+__global__ void __launch_bounds__(256) k_update_reduce(float* __restrict__ x, const float* __restrict__ d, float alpha,
+                                                       int64_t n, double* __restrict__ part,
+                                                       unsigned int* __restrict__ ticket, double* __restrict__ out) {
+  double s1 = 0.0, s2 = 0.0, bad = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float st = alpha * d[i];
+    const float xn = x[i] + st;
+    x[i] = xn;
+    s1 += (double)st * st;
+    s2 += (double)xn * xn;
+    if (!isfinite(xn)) bad = 1.0;
+  }
+  __shared__ double red[3][8];
+  __shared__ double fin[3][256];
+  __shared__ bool last;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+    bad = fmax(bad, __shfl_xor_sync(0xffffffffu, bad, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s1;
+    red[1][threadIdx.x >> 5] = s2;
+    red[2][threadIdx.x >> 5] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, c = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += red[0][k];
+      b += red[1][k];
+      c = fmax(c, red[2][k]);
+    }
+    part[3 * blockIdx.x + 0] = a;
+    part[3 * blockIdx.x + 1] = b;
+    part[3 * blockIdx.x + 2] = c;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {  // the last block: fixed strided sums, then a fixed-order tree
+    __threadfence();
+    double a = 0, b = 0, c = 0;
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
+      a += part[3 * k + 0];
+      b += part[3 * k + 1];
+      c = fmax(c, part[3 * k + 2]);
+    }
+    fin[0][threadIdx.x] = a;
+    fin[1][threadIdx.x] = b;
+    fin[2][threadIdx.x] = c;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+      if ((int)threadIdx.x < off) {
+        fin[0][threadIdx.x] += fin[0][threadIdx.x + off];
+        fin[1][threadIdx.x] += fin[1][threadIdx.x + off];
+        fin[2][threadIdx.x] = fmax(fin[2][threadIdx.x], fin[2][threadIdx.x + off]);
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      out[0] = fin[0][0];
+      out[1] = fin[1][0];
+      out[2] = fin[2][0];
+      *ticket = 0u;
+    }
+  }
+}
+
 // Deterministic sum of per-block partials: out[k] = sum_b part[stride*b + k] (k < stride),
 // the last component combined with max (flags) when maxlast. One block of 256 threads:
 // fixed strided partial sums, then a fixed-order tree, so the result is reproducible.
@@ -293,23 +366,35 @@ __global__ void k_dot_self(const float* __restrict__ x, int64_t n, double* __res
   }
 }
 
-__global__ void k_check_finite(const float* __restrict__ v, int64_t n, int* __restrict__ flag) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    if (!isfinite(v[i])) *flag = 1;
-}
 
 // Full objective: per cell, all I_N rows: sum (<A_N[i], Y[c]> - b[c, i])^2 in FP64.
-__global__ void k_full_obj(const float* __restrict__ Y, const float* __restrict__ AT, const float* __restrict__ b,
-                           int64_t ncell, int IT, int RT, double* __restrict__ part) {
+// Persistent blocks stage A_N once (rows padded to an odd stride: conflict-free reads by
+// consecutive threads), then 8 cells' Y rows at a time; SMEM_A = false reads A_N through L1.
+constexpr int FULL_CELLS = 8;
+template <bool SMEM_A>
+__global__ void __launch_bounds__(256) k_full_obj(const float* __restrict__ Y, const float* __restrict__ AT,
+                                                  const float* __restrict__ b, int64_t ncell, int IT, int RT,
+                                                  double* __restrict__ part) {
+  extern __shared__ float fsm[];
+  const int LD = RT + 1;
+  float* As = fsm;                                     // IT x LD (SMEM_A)
+  float* Ys = fsm + (SMEM_A ? (size_t)IT * LD : 0);   // FULL_CELLS x RT
+  if (SMEM_A)
+    for (int e = threadIdx.x; e < IT * RT; e += blockDim.x) As[(e / RT) * LD + (e % RT)] = AT[e];
   double acc = 0.0;
-  const int64_t total = ncell * IT;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t c = e / IT;
-    int i = (int)(e - c * IT);
-    float u = 0.f;
-    for (int r = 0; r < RT; ++r) u = fmaf(__ldg(&AT[(int64_t)i * RT + r]), __ldg(&Y[c * RT + r]), u);
-    double d = (double)u - (double)b[e];
-    acc += d * d;
+  for (int64_t c0 = (int64_t)blockIdx.x * FULL_CELLS; c0 < ncell; c0 += (int64_t)gridDim.x * FULL_CELLS) {
+    const int nc = (int)min((int64_t)FULL_CELLS, ncell - c0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nc * RT; e += blockDim.x) Ys[e] = Y[c0 * RT + e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < nc * IT; e += blockDim.x) {
+      const int cc = e / IT, i = e - cc * IT;
+      float u = 0.f;
+      for (int r = 0; r < RT; ++r)
+        u = fmaf(SMEM_A ? As[i * LD + r] : __ldg(&AT[(int64_t)i * RT + r]), Ys[cc * RT + r], u);
+      const double d = (double)u - (double)b[(c0 + cc) * IT + i];
+      acc += d * d;
+    }
   }
   __shared__ double red[32];
 #pragma unroll
@@ -507,8 +592,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   nd.add<float>(mx);          // t0
   nd.add<float>(mx);          // t1
   nd.add<double>(3 * (size_t)(nblk > 1024 ? nblk : 1024));
-  nd.add<double>(4);
-  size_t before_scratch = nd.off;
+  nd.add<double>(16);
   kr_sketch_scratch_need(cfg.s, ncell, nd);
   KR_TRY(kr_ws_reserve(ctx, nd.off));
   KR_TRY(kr_hbuf_reserve(ctx, 4096));
@@ -528,8 +612,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   bf.t0 = cv.take<float>(mx);
   bf.t1 = cv.take<float>(mx);
   bf.part = cv.take<double>(3 * (size_t)(nblk > 1024 ? nblk : 1024));
-  bf.red = cv.take<double>(4);
-  (void)before_scratch;
+  bf.red = cv.take<double>(16);
   KR_TRY(kr_sketch_fill(ctx, m, t, b, seed, call_id, 0, &sk, cv));
   KR_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
   KR_CUDA(ctx, cudaMemsetAsync(bf.x, 0, sizeof(float) * R, ctx->stream));
@@ -539,14 +622,15 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   int it = 0, grow = 0, converged = 0, since_min = 0;
   double prev_step = INFINITY, rel = INFINITY, min_step = INFINITY, min_rel = INFINITY;
   kr_status st = KR_OK;
+  unsigned int* ticket = reinterpret_cast<unsigned int*>(bf.red + 8);
+  KR_CUDA(ctx, cudaMemsetAsync(ticket, 0, sizeof(unsigned int), ctx->stream));
   for (it = 1; it <= cfg.max_iter; ++it) {
     int used = 0;
     KR_TRY(forward_resid(ctx, m, &sk, bf, nblk, &used));
     KR_TRY(backward(ctx, m, bf));
     if (cfg.lambda > 0.0) KR_LAUNCH(ctx, k_sub_lambda_x, ublk, 256, 0, bf.g, bf.x, (float)cfg.lambda, R);
     KR_TRY(kr_precond_apply(ctx, t, cfg.lambda, bf.g, bf.d, bf.t0, bf.t1));
-    KR_LAUNCH(ctx, k_update, ublk, 256, 0, bf.x, bf.d, (float)cfg.alpha, R, bf.part);
-    KR_LAUNCH(ctx, k_reduce_partials, 1, 256, 0, bf.part, ublk, 3, 1, bf.red);
+    KR_LAUNCH(ctx, k_update_reduce, ublk, 256, 0, bf.x, bf.d, (float)cfg.alpha, R, bf.part, ticket, bf.red);
     KR_CUDA(ctx, cudaMemcpyAsync(h, bf.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     StepCheck sc = step_check(h, cfg.tol, &prev_step, &min_step, &min_rel, &grow, &since_min, &rel, -1.0);
@@ -563,6 +647,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
       break;
     }
   }
+  if (it > cfg.max_iter) it = cfg.max_iter;
   if (it > cfg.max_iter) it = cfg.max_iter;
   KR_CUDA(ctx, cudaEventRecord(ev[4], ctx->stream));
   // final sampled objective at the returned x (FP64 accumulation)
@@ -740,7 +825,7 @@ extern "C" kr_status kron_objective(kr_ctx* ctx, const kr_factors* f, const floa
   int64_t ncell = 1;
   for (int n = 0; n < N - 1; ++n) ncell *= m.I[n];
   const int RT = m.R[N - 1];
-  const int nblk = ctx->num_sms * 4;
+  const int nblk = ctx->num_sms * 2;
   Need nd;
   nd.add<float>(ncell * RT);
   nd.add<float>(mx);
@@ -764,7 +849,15 @@ extern "C" kr_status kron_objective(kr_ctx* ctx, const kr_factors* f, const floa
     tr[n] = 0;
   }
   KR_TRY(kr_kron_apply2(ctx, N, din, dout, B, tr, x, Y, t0, t1));
-  KR_LAUNCH(ctx, k_full_obj, nblk, 256, 0, Y, m.A[N - 1], b, ncell, m.I[N - 1], RT, part);
+  {
+    const size_t smA = (size_t)m.I[N - 1] * (RT + 1) * sizeof(float), smY = (size_t)FULL_CELLS * RT * sizeof(float);
+    if (smA + smY <= ctx->smem_optin) {
+      KR_CUDA(ctx, cudaFuncSetAttribute(k_full_obj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smA + smY)));
+      KR_LAUNCH(ctx, k_full_obj<true>, nblk, 256, smA + smY, Y, m.A[N - 1], b, ncell, m.I[N - 1], RT, part);
+    } else {
+      KR_LAUNCH(ctx, k_full_obj<false>, nblk, 256, smY, Y, m.A[N - 1], b, ncell, m.I[N - 1], RT, part);
+    }
+  }
   KR_LAUNCH(ctx, k_reduce_partials, 1, 256, 0, part, nblk, 1, 0, red);
   const int ublk = grid_cap(ctx, R, 256, 4);
   KR_LAUNCH(ctx, k_dot_self, ublk, 256, 0, x, R, part + nblk);
