@@ -203,6 +203,15 @@ def exact_opt(kr, As_d, b_d):
     return kr.kron_objective(As_d, b_d, xstar, 0.0)
 
 
+def nonempty_cells(kr, As_d, b_d, s, seed, call_id, IT):
+    """Cells holding at least one sampled row in the sketch of solve `call_id`."""
+    tab = kr.kron_leverage(As_d)
+    sk = kr.kron_sketch(As_d, tab["cdf"], tab["prob"], b_d, s, seed, call_id)
+    keys = sk.export()[0]
+    sk.free()
+    return int(np.unique(keys.cpu().numpy() // IT).shape[0])
+
+
 def run_gpu(args, rank, world, local):
     import torch
 
@@ -269,14 +278,44 @@ def run_gpu(args, rank, world, local):
     d2h = int(xh.numel() * 4)
     if rank != 0:
         return
-    # roofline of the dominant kernel (sampled residual: per distinct row 8 B, per cell 8 R_N + 12 B)
+    # roofline of the dominant kernel
     peaks, peak_kind = load_peaks()
-    ncell = w["I"][0] * w["I"][1]
-    RT = w["R"][-1]
-    alg_bytes = rep_t["distinct"] * 8 + ncell * (8 * RT + 12)
-    ms_r, n_r = tim["resid"]
-    achieved = alg_bytes / (ms_r / n_r / 1000.0) / 1e9 if n_r else None
     hbm = float(peaks["hbm_gbs"])
+    I, R = w["I"], w["R"]
+    ncell = int(np.prod(I[:-1]))
+    RT, R2 = R[-1], R[-2]
+    distinct = rep_t["distinct"]
+    if tim["slab"][1]:
+        # fused slab pass: per distinct row 8 B and 4 R_N flops (dot + axpy); per non-empty
+        # cell a 16 B descriptor and 4 R_{N-1} R_N flops (its Y row and its share of Z);
+        # X1 read and Z written once (P x R_{N-1} x R_N floats each)
+        nact = nonempty_cells(kr, As_d, b_d, rep_t["s"], w["solve_seed"], args.steps, I[-1])
+        P = int(np.prod(I[:-2]))
+        alg_bytes = distinct * 8 + nact * 16 + 2 * P * R2 * RT * 4
+        alg_flops = distinct * 4 * RT + nact * 4 * R2 * RT
+        ms_r, n_r = tim["slab"]
+        kname = "k_slab (fused last-two-mode products + sampled residual, a6-a8)"
+    else:
+        # per-cell residual pass: per distinct row 8 B, per cell 8 R_N + 12 B
+        nact = None
+        alg_bytes = distinct * 8 + ncell * (8 * RT + 12)
+        alg_flops = distinct * 4 * RT
+        ms_r, n_r = tim["resid"]
+        kname = "k_resid (sampled residual + transpose, a7+a8)"
+    t_launch = ms_r / n_r / 1000.0 if n_r else None
+    gbs = alg_bytes / t_launch / 1e9 if n_r else None
+    tflops = alg_flops / t_launch / 1e12 if n_r else None
+    # FP32 FMA roof: 152 SMs x 128 lanes x 2 flops x the maximum SM clock
+    alu_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    if n_r and tflops / alu_peak > gbs / hbm:
+        roof = dict(bound="alu", achieved=tflops, peak=alu_peak, unit="TFLOP/s", frac=tflops / alu_peak,
+                    peak_source="FP32 FMA: 152 SMs x 128 lanes x 2 x %.0f MHz" % float(peaks.get("sm_max_mhz", 2070.0)),
+                    hbm_gbs=gbs, hbm_frac=gbs / hbm)
+    else:
+        roof = dict(bound="hbm", achieved=gbs, peak=hbm, unit="GB/s", frac=(gbs / hbm if gbs else None),
+                    peak_source=peak_kind, alu_tflops=tflops, alu_frac=(tflops / alu_peak if tflops else None))
+    roof.update(kernel=kname, traffic=None, alg_bytes_per_launch=alg_bytes, alg_flops_per_launch=alg_flops,
+                nonempty_cells=nact, avg_launch_ms=(ms_r / n_r if n_r else None))
     total_timed = sum(v[0] for v in tim.values())
     shares = {k: (round(v[0] / total_timed, 4) if total_timed else None) for k, v in tim.items()}
     mean = lambda key: float(np.mean([r[key] for r in reps]))
@@ -290,11 +329,7 @@ def run_gpu(args, rank, world, local):
         iters=mean("iters"), distinct=mean("distinct"),
         iter_rows_per_s=mean("distinct") * mean("iters") / (mean("iters") and np.mean([r["t_ms"]["iterate"] for r in reps]) / 1000.0),
         approx_ratio_max=max(ratios), certified_1_plus_eps=certified,
-        roofline=dict(bound="hbm", kernel="k_resid (sampled residual + transpose, a7+a8)",
-                      achieved=achieved, peak=hbm, unit="GB/s", frac=(achieved / hbm if achieved else None),
-                      traffic=None, peak_source=peak_kind,
-                      alg_bytes_per_launch=alg_bytes, avg_launch_ms=(ms_r / n_r if n_r else None),
-                      kernel_time_shares=shares),
+        roofline=dict(roof, kernel_time_shares=shares),
         e2e=dict(value=e2e, unit="rows/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
         gpu_launches=int(launches),
         clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"]),

@@ -124,8 +124,21 @@ enum {
   KR_K_DEDUP = 4,      /* per-cell merge + gather of b (a4 + a5) */
   KR_K_TABLES = 5,     /* Gram, Cholesky, leverage, CDF, eigen (a1 + a2) */
   KR_K_VECTOR = 6,     /* Richardson update, reductions (a10) */
-  KR_K_KINDS = 7
+  KR_K_SLAB = 7,       /* fused slab pass: last-two-mode products + sampled residual (a6-a8) */
+  KR_K_KINDS = 8
 };
+/* Context options. The defaults suit every input; the switches exist for A/B timing
+ * and for tests that run both formulations of the sampled products.
+ *  KR_OPT_SLAB_PASS (default 1): 1 evaluates the sampled products of one Richardson
+ *    step (Thm 4.4 with T = the last mode) with the fused slab pass wherever the shape
+ *    allows it (N >= 2, R[N-2] <= 64, R[N-1] <= 64, a single right-hand side); 0 always
+ *    uses the per-cell residual pass between two full mode products.
+ *  KR_OPT_SLAB_TILE_ENTRIES (default 16384, range [256, 2^22]): entry budget of one
+ *    tile of the slab pass.
+ * Returns KR_EINVAL for an unknown key or a value out of range. */
+enum { KR_OPT_SLAB_PASS = 1, KR_OPT_SLAB_TILE_ENTRIES = 2 };
+KR_API kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value);
+
 KR_API kr_status kr_timing_enable(kr_ctx* ctx, int32_t on);
 KR_API kr_status kr_timing_read(kr_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
 KR_API kr_status kr_timing_reset(kr_ctx* ctx);

@@ -18,9 +18,11 @@ MAX_MODES = 8
 
 STATUS = {0: "KR_OK", 1: "KR_EINVAL", 2: "KR_ENOMEM", 3: "KR_ECUDA", 4: "KR_ENONFINITE", 5: "KR_ERANK",
           6: "KR_ENOTCONV", 7: "KR_EDIVERGED", 8: "KR_ETIMEOUT", 9: "KR_ENOTIMPL"}
-KERNEL_KINDS = {"resid": 0, "modeprod": 1, "sample": 2, "scatter": 3, "dedup": 4, "tables": 5, "vector": 6}
+KERNEL_KINDS = {"resid": 0, "modeprod": 1, "sample": 2, "scatter": 3, "dedup": 4, "tables": 5, "vector": 6,
+                "slab": 7}
+OPT_SLAB_PASS, OPT_SLAB_TILE_ENTRIES = 1, 2
 EXPORTED = ["kr_create", "kr_destroy", "kr_set_stream", "kr_last_error", "kr_launch_count", "kr_timing_enable",
-            "kr_timing_read", "kr_timing_reset", "kron_leverage",
+            "kr_timing_read", "kr_timing_reset", "kr_set_option", "kron_leverage",
             "kron_sample", "kron_sample_noalloc", "kron_sketch", "kron_sketch_distinct", "kron_sketch_export", "kron_sketch_residual",
             "kron_sketch_free", "kron_matmul", "kron_precond", "kron_objective", "kron_regress", "kron_ridge",
             "kron_ridge_batched", "tucker_factor_update", "tucker_als_sweep"]
@@ -80,6 +82,7 @@ def lib():
             "kr_timing_enable": (i32, [vp, i32]),
             "kr_timing_read": (i32, [vp, i32, P(dbl), P(i64)]),
             "kr_timing_reset": (i32, [vp]),
+            "kr_set_option": (i32, [vp, i32, i64]),
             "kron_leverage": (i32, [vp, P(KrFactors), P(vp), P(vp), P(vp), P(i32)]),
             "kron_sample": (i32, [vp, i32, P(i64), P(vp), P(vp), i64, u64, u64, i32, vp, vp]),
             "kron_sample_noalloc": (i32, [vp, i32, P(i64), P(vp), P(vp), i64, u64, u64, i32, vp, vp]),
@@ -129,6 +132,13 @@ def launch_count():
 def timing_enable(on=True):
     h = context()
     _check(lib().kr_timing_enable(h, int(bool(on))), h)
+
+
+def set_option(key, value):
+    """Context option (OPT_SLAB_PASS: 1 fused slab pass where the shape allows, 0 the
+    per-cell residual pass; OPT_SLAB_TILE_ENTRIES: entry budget of a slab-pass tile)."""
+    h = context()
+    _check(lib().kr_set_option(h, int(key), int(value)), h)
 
 
 def timing_reset():

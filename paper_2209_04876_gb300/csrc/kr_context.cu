@@ -41,6 +41,23 @@ extern "C" kr_status kr_create(kr_ctx** out, void* stream) {
   return KR_OK;
 }
 
+extern "C" kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value) {
+  if (!ctx) return KR_EINVAL;
+  switch (key) {
+    case KR_OPT_SLAB_PASS:
+      if (value != 0 && value != 1) return kr_fail(ctx, KR_EINVAL, "kr_set_option: slab pass must be 0 or 1");
+      ctx->slab_pass = (int)value;
+      return KR_OK;
+    case KR_OPT_SLAB_TILE_ENTRIES:
+      if (value < 256 || value > (int64_t(1) << 22))
+        return kr_fail(ctx, KR_EINVAL, "kr_set_option: tile entries %lld outside [256, 2^22]", (long long)value);
+      ctx->slab_tile_entries = (uint32_t)value;
+      return KR_OK;
+    default:
+      return kr_fail(ctx, KR_EINVAL, "kr_set_option: unknown key %d", key);
+  }
+}
+
 extern "C" void kr_destroy(kr_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
@@ -166,6 +183,7 @@ cudaEvent_t kr_timing_event(kr_ctx* ctx) {
 int kr_kind_of(const char* k) {
   std::string s(k);
   if (s.find("k_resid") != std::string::npos) return KR_K_RESID;
+  if (s.find("k_slab") != std::string::npos) return KR_K_SLAB;
   if (s.find("k_mode_product") != std::string::npos) return KR_K_MODEPROD;
   if (s.find("k_sample") != std::string::npos) return KR_K_SAMPLE;
   if (s.find("k_scatter") != std::string::npos) return KR_K_SCATTER;

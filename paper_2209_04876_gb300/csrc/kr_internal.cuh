@@ -29,6 +29,9 @@ struct kr_ctx {
   // pinned host buffer for small read-backs
   char* hbuf = nullptr;
   size_t hbuf_size = 0;
+  // options (kr_set_option)
+  int slab_pass = 1;
+  uint32_t slab_tile_entries = 16384;
   cudaEvent_t ev[10] = {};
   cudaEvent_t pev[2] = {};  // completion of the two in-flight Richardson norm read-backs
   // per-kernel timing (instrumentation)
@@ -177,9 +180,10 @@ struct kr_sketch {
   int IT = 0;          // I[N-1]
   int64_t distinct = 0;
   // device arrays (owned)
-  uint32_t* cell_start = nullptr;  // ncell
+  bool want_desc = true;  // build perm/desc (the per-cell residual pass); the slab pass does not use them
+  uint32_t* cell_start = nullptr;  // ncell: first entry of the cell (entries of consecutive cells back to back)
   uint32_t* cell_nd = nullptr;     // ncell: distinct entries of the cell
-  uint32_t* ent = nullptr;         // s: packed (i_T | count << 16) at cell_start[c] + k
+  uint32_t* ent = nullptr;         // s (first `distinct` used): packed (i_T | count << 16) at cell_start[c] + k
   float* bt = nullptr;             // s: b~ at the same positions
   float* cell_w = nullptr;         // ncell: prod_{n<N-1} (1/p_n(i_n)) / s
   float* invpT = nullptr;          // IT: 1/p_{N-1}(i)
@@ -209,6 +213,44 @@ kr_status kr_scan_u32(kr_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
 // perm = cells ordered by decreasing floor(log2(distinct rows)), stable (deterministic).
 void kr_perm_need(int64_t ncell, Need& nd);
 kr_status kr_balance_perm(kr_ctx* ctx, const uint32_t* nd, int64_t ncell, uint32_t* perm, Carve& cv);
+
+// ------------------------------------------------------------------ fused slab pass
+
+// Tiles of the fused slab pass: runs of consecutive non-empty cells of one slab (the
+// cells sharing i_1..i_{N-2}), at most `cb` cells and about `et` entries each.
+struct kr_tiles {
+  int64_t P = 0;       // slabs: prod_{n < N-2} I[n] (1 for N = 2)
+  int I2 = 0, R2 = 0;  // mode N-2 (second to last)
+  int IT = 0, RT = 0;  // mode N-1 (the gathered one)
+  int cb = 0;          // cells per tile at most
+  uint32_t et = 0;     // entry budget of a tile
+  int64_t ntmax = 0;   // tile capacity (upper bound of the device-side tile count)
+  uint4* act = nullptr;          // ncell: {cell, first entry, entries, weight bits} of non-empty cells
+  uint4* tile = nullptr;         // ntmax: {first non-empty cell, cells, slab, entries}
+  uint32_t* cost = nullptr;      // ntmax: work estimate (0 past the last tile)
+  uint32_t* order = nullptr;     // ntmax: processing order (heaviest first)
+  uint4* tsort = nullptr;        // ntmax: descriptors in processing order (packed, see kr_slab.cu)
+  uint2* slab = nullptr;         // P: {first tile, tiles}
+  uint32_t* meta = nullptr;      // [0] tiles, [1] non-empty cells, [2], [3] work counters
+  float* zpart = nullptr;        // ntmax x R2 x RT: contributions of tiles of multi-tile slabs
+  double* objpart = nullptr;     // ntmax: per-tile sampled objective (FP64; zero past the last)
+  int par = 0;                   // work counter of the next pass
+};
+
+// Whether the sketch/shape admits the slab pass (single right-hand side, N >= 2,
+// R[N-2] <= 64, R[N-1] <= 64, shared memory for two teams).
+bool kr_slab_eligible(kr_ctx* ctx, const Modes& m, const kr_sketch* sk);
+void kr_tiles_setup(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, kr_tiles* tl);
+void kr_tiles_own_need(const kr_tiles* tl, int64_t ncell, Need& nd);
+void kr_tiles_layout(kr_tiles* tl, int64_t ncell, Carve& cv);
+void kr_tiles_scratch_need(const kr_tiles* tl, int64_t ncell, Need& nd);
+// Builds the tiles from a filled sketch (scratch from cv).
+kr_status kr_tiles_build(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, Carve& cv);
+// One fused pass: Z[p] = sum over the sampled rows of slab p of
+//   A(N-2)[i]^T-weighted residual accumulations (see kr_slab.cu), from X1 (P x R2 x RT);
+// per-tile objective partials go to tl->objpart (tl->ntmax doubles).
+kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const float* A2, const float* AT,
+                       const float* X1, float* Z);
 
 // ------------------------------------------------------------------ solvers
 

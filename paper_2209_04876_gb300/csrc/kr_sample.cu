@@ -269,6 +269,33 @@ __global__ void k_dedup(SampleModes sm, int64_t ncell, int64_t ncell_inner, int6
   }
 }
 
+// Compaction of the merged entries: cell c's nd[c] entries move from its draw-sized
+// region at start[c] to position newstart[c] (exclusive scan of nd), so that the entries
+// of consecutive cells lie back to back. One warp per cell; the copy goes to scratch and
+// k_copy_back returns the first total[0] entries.
+__global__ void k_compact(int64_t ncell, const uint32_t* __restrict__ start, const uint32_t* __restrict__ newstart,
+                          const uint32_t* __restrict__ nd, const uint32_t* __restrict__ ent,
+                          const float* __restrict__ bt, uint32_t* __restrict__ ent2, float* __restrict__ bt2) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < ncell; c += warps) {
+    const uint32_t n = nd[c], from = start[c], to = newstart[c];
+    for (uint32_t k = lane; k < n; k += 32) {
+      ent2[to + k] = ent[from + k];
+      bt2[to + k] = bt[from + k];
+    }
+  }
+}
+
+__global__ void k_copy_back(const unsigned long long* __restrict__ total, const uint32_t* __restrict__ ent2,
+                            const float* __restrict__ bt2, uint32_t* __restrict__ ent, float* __restrict__ bt) {
+  const int64_t n = (int64_t)total[0];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    ent[i] = ent2[i];
+    bt[i] = bt2[i];
+  }
+}
+
 // Sketch export: linear keys, counts, weights and b~ in increasing key order.
 __global__ void k_export(int64_t ncell, uint32_t IT, const uint32_t* __restrict__ start, const uint32_t* __restrict__ nd,
                          const uint32_t* __restrict__ off, const uint32_t* __restrict__ ent, const float* __restrict__ bt,
@@ -419,14 +446,24 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   KR_LAUNCH(ctx, k_dedup, grid_for(ctx, ncell, DEDUP_WARPS, 8), DEDUP_WARPS * 32, dsmem, sm, ncell, sk->ncell_inner,
             sk->xI, sk->xPafter, IT, (float)(1.0 / (double)sk->s_row), sk->cell_start, cnt, slot, b, sk->ent, sk->bt,
             sk->cell_nd, sk->cell_w);
+  // entries back to back in cell order (the draw-sized regions leave gaps)
   {
     Carve sc = cv;
-    KR_TRY(kr_balance_perm(ctx, sk->cell_nd, ncell, sk->perm, sc));
+    KR_TRY(kr_scan_u32(ctx, sk->cell_nd, cnt, ncell, sc));
   }
-  KR_LAUNCH(ctx, k_build_desc, grid_for(ctx, ncell, 256), 256, 0, sk->perm, sk->cell_start, sk->cell_nd, sk->cell_w,
-            ncell, sk->desc);
-  KR_CUDA(ctx, cudaMemcpyAsync(sk->invpT, t.invp[N - 1], sizeof(float) * IT, cudaMemcpyDeviceToDevice, ctx->stream));
   KR_LAUNCH(ctx, k_sum_u32, grid_for(ctx, ncell, 256, 2), 256, 0, sk->cell_nd, ncell, dsum);
+  KR_LAUNCH(ctx, k_compact, grid_for(ctx, ncell, 8, 8), 256, 0, ncell, sk->cell_start, cnt, sk->cell_nd, sk->ent,
+            sk->bt, keys, reinterpret_cast<float*>(rank));
+  KR_LAUNCH(ctx, k_copy_back, grid_for(ctx, s, 256), 256, 0, dsum, keys, reinterpret_cast<const float*>(rank), sk->ent,
+            sk->bt);
+  KR_CUDA(ctx, cudaMemcpyAsync(sk->cell_start, cnt, sizeof(uint32_t) * ncell, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (sk->want_desc) {
+    Carve sc = cv;
+    KR_TRY(kr_balance_perm(ctx, sk->cell_nd, ncell, sk->perm, sc));
+    KR_LAUNCH(ctx, k_build_desc, grid_for(ctx, ncell, 256), 256, 0, sk->perm, sk->cell_start, sk->cell_nd,
+              sk->cell_w, ncell, sk->desc);
+  }
+  KR_CUDA(ctx, cudaMemcpyAsync(sk->invpT, t.invp[N - 1], sizeof(float) * IT, cudaMemcpyDeviceToDevice, ctx->stream));
   KR_TRY(kr_hbuf_reserve(ctx, 4096));
   KR_CUDA(ctx, cudaMemcpyAsync(ctx->hbuf, dsum, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

@@ -1,0 +1,785 @@
+// a6-a8 fused: the sampled products of one Richardson step of Alg. 2 (Thm 4.4 with
+// T = the last mode), evaluated slab by slab.
+//
+// With x read as an R_1 x ... x R_N tensor, cells c = (i_1..i_{N-1}) and slabs
+// p = (i_1..i_{N-2}), the step needs
+//   X1 = X x_1 A(1) ... x_{N-2} A(N-2)                         (P x R_{N-1} x R_N)
+//   Y[p, i]  = sum_r A(N-1)[i, r] X1[p, r, :]                    (one R_N row per cell)
+//   r_j      = omega_j (b~_j - <A(N)[i_j], Y[c_j]>)              (per distinct sampled row)
+//   W[p, i]  = sum_{j in cell (p, i)} r_j A(N)[i_j]
+//   Z[p]     = sum_i A(N-1)[i, :]^T W[p, i]                      (R_{N-1} x R_N)
+// and then g = Z x_1 A(1)^T ... x_{N-2} A(N-2)^T. Only cells holding sampled rows
+// contribute, so Y and W exist only for those, and only inside one kernel: a tile (a
+// run of non-empty cells of one slab) forms its Y rows in shared memory from X1[p],
+// walks its entries, accumulates W in place of Y, and contracts W with the tile's rows
+// of A(N-1) into the slab's Z. The two large mode products of the unfused form (to and
+// from the cells x R_N intermediates) and their HBM round trips disappear.
+//
+// A persistent CTA holds A(N) and 1/p_N in shared memory once and runs two teams of 256
+// threads, each taking tiles from a global counter in decreasing-work order. Inside a
+// tile, the entries (contiguous in cell order) are split into equal segments, one per
+// lane group of G lanes; a group that starts inside a cell owned by an earlier group
+// keeps that cell's partial W apart, and the partials are added to the owner's W in
+// group order afterwards. Every sum has a fixed order, so the pass is deterministic.
+// Slabs split over several tiles are completed by the last of their tiles to finish,
+// which adds the tiles' contributions in tile order.
+#include "kr_internal.cuh"
+
+namespace {
+
+constexpr int SLAB_TEAM = 256;
+constexpr int SLAB_TEAMS = 2;
+constexpr int SLAB_D = 4;  // chunks of G entries in flight per lane
+
+template <int RTP>
+struct SlabShape {
+  static constexpr int COLS = RTP < 16 ? RTP : 16;  // columns of a row held by one lane
+  static constexpr int G = RTP / COLS;              // lanes per group
+  static constexpr int NQ = COLS / 4;               // float4 quads per lane
+  static constexpr int NG = SLAB_TEAM / G;          // groups per team
+  static constexpr int CB = (SLAB_TEAM >= 256 ? 128 : 64) >> (RTP >= 64 ? 1 : 0);  // cells per tile at most
+  static constexpr int PF = SLAB_TEAM * COLS;       // floats of the partial buffer (NG x RTP)
+};
+
+int rt_pad(int RT) {
+  int r = 4;
+  while (r < RT) r <<= 1;
+  return r;
+}
+int cb_for(int RTP) { return (SLAB_TEAM >= 256 ? 128 : 64) >> (RTP >= 64 ? 1 : 0); }
+
+struct SlabArgs {
+  const uint4* act;
+  const uint4* tsort;  // per processing slot: {first cell, tile, slab, entries | (cells - 1) << 24 | multi << 31}
+  uint32_t* meta;
+  int par;
+  const uint32_t* ent;
+  const float* bt;
+  const float* invpT;
+  const float* AT;  // IT x RT
+  const float* A2;  // I2 x R2
+  const float* X1;  // P x R2 x RT
+  float* Z;         // P x R2 x RT
+  float* zpart;     // ntmax x R2 x RT
+  double* objpart;  // ntmax
+  int IT, RT, I2, R2, R2P, R2S;
+  int64_t P;
+  int a2vec, atvec;
+  // shared-memory layout (bytes)
+  uint32_t team_off, team_bytes, o_a2, o_x1, o_pf, o_act, o_cs, o_ctl;
+};
+
+__device__ __forceinline__ void team_sync(int team) {
+  asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(SLAB_TEAM) : "memory");
+}
+
+// Row `it` of A(N), the lane's quads qd[v] (zero past R_N).
+template <int RTP, bool SMEM_A>
+__device__ __forceinline__ void load_arow(const SlabArgs& a, const float* sA, int it, const int* qd, float4* av) {
+  constexpr int NQ = SlabShape<RTP>::NQ;
+  if (SMEM_A) {
+    const float4* row = reinterpret_cast<const float4*>(sA + (size_t)it * RTP);
+#pragma unroll
+    for (int v = 0; v < NQ; ++v) av[v] = row[qd[v]];
+  } else if (a.atvec) {
+    const float4* row = reinterpret_cast<const float4*>(a.AT + (size_t)it * a.RT);
+#pragma unroll
+    for (int v = 0; v < NQ; ++v) av[v] = 4 * qd[v] < a.RT ? __ldg(row + qd[v]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+    const float* row = a.AT + (size_t)it * a.RT;
+#pragma unroll
+    for (int v = 0; v < NQ; ++v) {
+      const int c = 4 * qd[v];
+      av[v].x = c + 0 < a.RT ? __ldg(row + c + 0) : 0.f;
+      av[v].y = c + 1 < a.RT ? __ldg(row + c + 1) : 0.f;
+      av[v].z = c + 2 < a.RT ? __ldg(row + c + 2) : 0.f;
+      av[v].w = c + 3 < a.RT ? __ldg(row + c + 3) : 0.f;
+    }
+  }
+}
+
+// <A(N) row, y> over this lane's quads: one FMA chain per quad, chains added pairwise.
+template <int NQ>
+__device__ __forceinline__ float dot_quads(const float4* av, const float* y) {
+  float c[NQ];
+#pragma unroll
+  for (int v = 0; v < NQ; ++v) {
+    c[v] = av[v].x * y[4 * v];
+    c[v] = fmaf(av[v].y, y[4 * v + 1], c[v]);
+    c[v] = fmaf(av[v].z, y[4 * v + 2], c[v]);
+    c[v] = fmaf(av[v].w, y[4 * v + 3], c[v]);
+  }
+  if (NQ == 4) return (c[0] + c[1]) + (c[2 % NQ] + c[3 % NQ]);
+  if (NQ == 2) return c[0] + c[1 % NQ];
+  return c[0];
+}
+
+template <int NQ>
+__device__ __forceinline__ void axpy_quads(float rr, const float4* av, float* w) {
+#pragma unroll
+  for (int v = 0; v < NQ; ++v) {
+    w[4 * v + 0] = fmaf(rr, av[v].x, w[4 * v + 0]);
+    w[4 * v + 1] = fmaf(rr, av[v].y, w[4 * v + 1]);
+    w[4 * v + 2] = fmaf(rr, av[v].z, w[4 * v + 2]);
+    w[4 * v + 3] = fmaf(rr, av[v].w, w[4 * v + 3]);
+  }
+}
+
+// Sum over the G lanes of a group (the mask names the group only, so the call may sit
+// in control flow that is uniform per group but not per warp).
+template <int G>
+__device__ __forceinline__ float group_sum(float v, unsigned gmask) {
+#pragma unroll
+  for (int off = 1; off < G; off <<= 1) v += __shfl_xor_sync(gmask, v, off);
+  return v;
+}
+
+// One sampled row against the current cell: r = omega (b~ - <a, y>), w += r a.
+template <int RTP, bool SMEM_A>
+__device__ __forceinline__ void slab_entry(const SlabArgs& a, const float* sA, const float* sInvp, const int* qd,
+                                           unsigned gmask, uint32_t e, float bj, float cw, const float* y, float* w,
+                                           float& objc) {
+  using S = SlabShape<RTP>;
+  const int it = (int)(e & 0xFFFFu);
+  float4 av[S::NQ];
+  load_arow<RTP, SMEM_A>(a, sA, it, qd, av);
+  const float pr = group_sum<S::G>(dot_quads<S::NQ>(av, y), gmask);
+  const float om = (float)(e >> 16) * cw * sInvp[it];  // 0 past the segment (count 0)
+  const float res = bj - pr;
+  const float rr = om * res;
+  axpy_quads<S::NQ>(rr, av, w);
+  objc = fmaf(rr, res, objc);
+}
+
+// Cell k ends: its W goes to the cell's row (owned) or to the group's partial slot (the
+// cell began in an earlier group's segment); the walk moves to cell k + 1.
+template <int RTP>
+__device__ __forceinline__ void slab_next_cell(float* sYW, float* sPf, const uint32_t* sCS, const uint4* sAct,
+                                               uint32_t e0, int q, const int* qd, int& k, uint32_t& nb, float& cw,
+                                               bool& foreign, float* y, float* w, float& objc, double& objt) {
+  using S = SlabShape<RTP>;
+  float* dst = foreign ? (sPf + q * RTP) : (sYW + k * RTP);
+#pragma unroll
+  for (int v = 0; v < S::NQ; ++v)
+    reinterpret_cast<float4*>(dst)[qd[v]] = make_float4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
+  objt += (double)objc;
+  objc = 0.f;
+  ++k;
+  nb = sCS[k + 1] - e0;
+  cw = __uint_as_float(sAct[k].w);
+  foreign = false;
+#pragma unroll
+  for (int v = 0; v < S::NQ; ++v) {
+    const float4 t4 = reinterpret_cast<const float4*>(sYW + k * RTP)[qd[v]];
+    y[4 * v + 0] = t4.x;
+    y[4 * v + 1] = t4.y;
+    y[4 * v + 2] = t4.z;
+    y[4 * v + 3] = t4.w;
+  }
+#pragma unroll
+  for (int c = 0; c < S::COLS; ++c) w[c] = 0.f;
+}
+
+template <int RTP, bool SMEM_A>
+__global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
+  using S = SlabShape<RTP>;
+  constexpr int COLS = S::COLS, G = S::G, NQ = S::NQ, NG = S::NG;
+  constexpr int XQ = RTP / 4;
+  extern __shared__ float4 slab_smem[];
+  char* sm = reinterpret_cast<char*>(slab_smem);
+  float* sA = reinterpret_cast<float*>(sm);
+  float* sInvp = sA + (SMEM_A ? (size_t)a.IT * RTP : 0);
+  const int RT = a.RT, R2 = a.R2, R2P = a.R2P, R2S = a.R2S;
+  const int zn = R2 * RT;
+  if (SMEM_A) {
+    if (a.atvec && RT == RTP) {  // rows already padded: a straight float4 copy
+      const float4* src = reinterpret_cast<const float4*>(a.AT);
+      float4* dst = reinterpret_cast<float4*>(sA);
+      const int n4 = a.IT * (RTP / 4);
+#pragma unroll 8
+      for (int i = threadIdx.x; i < n4; i += blockDim.x) dst[i] = __ldg(src + i);
+    } else {
+      for (int e = threadIdx.x; e < a.IT * RTP; e += blockDim.x) {
+        const int i = e / RTP, r = e - i * RTP;
+        sA[e] = r < RT ? __ldg(a.AT + (size_t)i * RT + r) : 0.f;
+      }
+    }
+  }
+  for (int i = threadIdx.x; i < a.IT; i += blockDim.x) sInvp[i] = __ldg(a.invpT + i);
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.meta[2 + (a.par ^ 1)] = 0;  // counter of the next pass
+  __syncthreads();
+
+  const int team = threadIdx.x / SLAB_TEAM, tt = threadIdx.x % SLAB_TEAM;
+  char* tb = sm + a.team_off + (size_t)team * a.team_bytes;
+  float* sYW = reinterpret_cast<float*>(tb);
+  float* sA2 = reinterpret_cast<float*>(tb + a.o_a2);
+  float* sX1 = reinterpret_cast<float*>(tb + a.o_x1);
+  float* sPf = reinterpret_cast<float*>(tb + a.o_pf);
+  uint4* sAct = reinterpret_cast<uint4*>(tb + a.o_act);
+  uint32_t* sCS = reinterpret_cast<uint32_t*>(tb + a.o_cs);
+  uint32_t* sCtl = reinterpret_cast<uint32_t*>(tb + a.o_ctl);
+  double* sRed = reinterpret_cast<double*>(tb + a.o_ctl + 32);
+  const uint32_t ntiles = a.meta[0];
+  const int lane = threadIdx.x & 31, wt = tt >> 5;
+  const int q = tt / G, g = tt % G;
+  const int gbase = lane - g;
+  // Quads of a row handled by this lane, rotated so that the 8 lanes of a quarter warp
+  // touch 8 different bank quads whatever rows they read (G = 2, 4).
+  const int rot = (lane & 7) >> (G == 1 ? 0 : 1);
+  int qd[NQ];
+#pragma unroll
+  for (int v = 0; v < NQ; ++v) qd[v] = g * NQ + ((v + rot) & (NQ - 1));
+
+  // The leader claims the next processing slot one tile ahead, so only the descriptor
+  // load (one round trip) sits between two tiles.
+  uint32_t nk = 0;
+  if (tt == 0) nk = atomicAdd(&a.meta[2 + a.par], 1u);
+  for (;;) {
+    if (tt == 0) {
+      const uint4 d = nk < ntiles ? a.tsort[nk] : make_uint4(0u, 0xFFFFFFFFu, 0u, 0u);
+      *reinterpret_cast<uint4*>(sCtl + 4) = d;
+      if (nk < ntiles) nk = atomicAdd(&a.meta[2 + a.par], 1u);
+    }
+    team_sync(team);
+    const uint4 td = *reinterpret_cast<const uint4*>(sCtl + 4);
+    const uint32_t t = td.y;
+    if (t == 0xFFFFFFFFu) break;
+    const int na = (int)((td.w >> 24) & 0x7Fu) + 1;
+    const bool multi = (td.w >> 31) != 0u;
+    const int64_t p = td.z;
+    const uint32_t E = td.w & 0xFFFFFFu;
+    // ---- tile metadata, rows of A(N-1), X1[p]
+    if (tt < na) {
+      const uint4 ac = a.act[td.x + tt];
+      sAct[tt] = ac;
+      sCS[tt] = ac.y;
+      if (tt == na - 1) sCS[na] = ac.y + ac.z;
+      const uint32_t i2 = ac.x % (uint32_t)a.I2;
+      float* dst = sA2 + tt * R2S;
+      if (a.a2vec) {
+        const float4* row = reinterpret_cast<const float4*>(a.A2 + (size_t)i2 * R2);
+        for (int k4 = 0; k4 < R2P / 4; ++k4)
+          reinterpret_cast<float4*>(dst)[k4] = 4 * k4 < R2 ? __ldg(row + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        const float* row = a.A2 + (size_t)i2 * R2;
+        for (int k2 = 0; k2 < R2P; ++k2) dst[k2] = k2 < R2 ? __ldg(row + k2) : 0.f;
+      }
+    }
+    {
+      const float* xp = a.X1 + p * zn;
+      for (int i = tt; i < R2P * RTP; i += SLAB_TEAM) {
+        const int r = i / RTP, c = i % RTP;
+        sX1[i] = (r < R2 && c < RT) ? __ldg(xp + r * RT + c) : 0.f;
+      }
+    }
+    team_sync(team);
+    // ---- Y rows of the tile's cells: sYW[k] = A(N-1)[i_k] X1[p]
+    {
+      const int ncq = (na + 3) >> 2;
+      for (int w = tt; w < ncq * XQ; w += SLAB_TEAM) {
+        const int cq = w / XQ, xq = w % XQ;
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[i][c] = 0.f;
+        for (int k4 = 0; k4 < R2P / 4; ++k4) {
+          float4 av[4], xv[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4*>(sA2 + (4 * cq + i) * R2S + 4 * k4);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) xv[kk] = *reinterpret_cast<const float4*>(sX1 + (4 * k4 + kk) * RTP + 4 * xq);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float ak[4] = {av[i].x, av[i].y, av[i].z, av[i].w};
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              acc[i][0] = fmaf(ak[kk], xv[kk].x, acc[i][0]);
+              acc[i][1] = fmaf(ak[kk], xv[kk].y, acc[i][1]);
+              acc[i][2] = fmaf(ak[kk], xv[kk].z, acc[i][2]);
+              acc[i][3] = fmaf(ak[kk], xv[kk].w, acc[i][3]);
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (4 * cq + i < na)
+            *reinterpret_cast<float4*>(sYW + (4 * cq + i) * RTP + 4 * xq) =
+                make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      }
+    }
+    team_sync(team);
+    // ---- walk: group q takes entries [j0, j1) of the tile
+    const uint32_t e0 = sCS[0];
+    const uint32_t L = (E + NG - 1) / NG;
+    const uint32_t j0 = (uint32_t)q * L;
+    const uint32_t j1 = min(j0 + L, E);
+    const bool has = j0 < E;
+    int k = 0;
+    if (has) {  // last cell starting at or before j0
+      int lo = 0, hi = na - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sCS[mid] - e0 <= j0) lo = mid;
+        else hi = mid - 1;
+      }
+      k = lo;
+    }
+    uint32_t nb = sCS[k + 1] - e0;
+    bool foreign = has && (sCS[k] - e0 < j0);
+    float cw = __uint_as_float(sAct[k].w);
+    float y[COLS], w[COLS];
+#pragma unroll
+    for (int v = 0; v < NQ; ++v) {
+      const float4 t4 = reinterpret_cast<const float4*>(sYW + k * RTP)[qd[v]];
+      y[4 * v + 0] = t4.x;
+      y[4 * v + 1] = t4.y;
+      y[4 * v + 2] = t4.z;
+      y[4 * v + 3] = t4.w;
+    }
+#pragma unroll
+    for (int c = 0; c < COLS; ++c) w[c] = 0.f;
+    float objc = 0.f;
+    double objt = 0.0;
+    team_sync(team);  // every group holds its first y before owners overwrite Y with W
+    const uint32_t nchunk = (L + G - 1) / G;
+    const uint32_t* ent = a.ent + e0;
+    const float* bt = a.bt + e0;
+    uint32_t re[SLAB_D];
+    float rb[SLAB_D];
+#pragma unroll
+    for (int d = 0; d < SLAB_D; ++d) {
+      const uint32_t j = j0 + (uint32_t)d * G + g;
+      const bool on = j < j1;
+      re[d] = on ? __ldg(ent + j) : 0u;
+      rb[d] = on ? __ldg(bt + j) : 0.f;
+    }
+    for (uint32_t u0 = 0; u0 < nchunk; u0 += SLAB_D) {
+#pragma unroll
+      for (int d = 0; d < SLAB_D; ++d) {
+        const uint32_t e_m = re[d];
+        const float b_m = rb[d];
+        {  // refill this slot SLAB_D chunks ahead
+          const uint32_t j = j0 + (u0 + d + SLAB_D) * G + g;
+          const bool on = j < j1;
+          re[d] = on ? __ldg(ent + j) : 0u;
+          rb[d] = on ? __ldg(bt + j) : 0.f;
+        }
+        if (u0 + d >= nchunk) continue;  // uniform over the team
+#pragma unroll
+        for (int sidx = 0; sidx < G; ++sidx) {
+          const uint32_t j = j0 + (u0 + d) * G + sidx;
+          const uint32_t e = G > 1 ? __shfl_sync(0xffffffffu, e_m, gbase + sidx) : e_m;
+          const float bj = G > 1 ? __shfl_sync(0xffffffffu, b_m, gbase + sidx) : b_m;
+          if (j < j1 && j == nb)
+            slab_next_cell<RTP>(sYW, sPf, sCS, sAct, e0, q, qd, k, nb, cw, foreign, y, w, objc, objt);
+          slab_entry<RTP, SMEM_A>(a, sA, sInvp, qd, 0xffffffffu, e, bj, cw, y, w, objc);
+        }
+      }
+    }
+    // The last cell of the segment: a partial (it began in an earlier segment), complete
+    // (stored now), or continuing into later segments (kept until their partials exist).
+    const bool pending = has && !foreign && nb > j1;
+    if (has && !pending) {
+      float* dst = foreign ? (sPf + q * RTP) : (sYW + k * RTP);
+#pragma unroll
+      for (int v = 0; v < NQ; ++v)
+        reinterpret_cast<float4*>(dst)[qd[v]] = make_float4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
+    }
+    if (has) objt += (double)objc;
+    {  // objective of the tile: one lane per group
+      double ov = (g == 0 && has) ? objt : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) ov += __shfl_xor_sync(0xffffffffu, ov, off);
+      if (lane == 0) sRed[wt] = ov;
+    }
+    team_sync(team);
+    // ---- the owner of a cell continuing past its segment adds the later groups'
+    //      partials in group order
+    if (pending) {
+      for (uint32_t q2 = (uint32_t)q + 1; q2 < (uint32_t)NG && q2 * L < nb; ++q2) {
+#pragma unroll
+        for (int v = 0; v < NQ; ++v) {
+          const float4 pq = reinterpret_cast<const float4*>(sPf + q2 * RTP)[qd[v]];
+          w[4 * v + 0] += pq.x;
+          w[4 * v + 1] += pq.y;
+          w[4 * v + 2] += pq.z;
+          w[4 * v + 3] += pq.w;
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < NQ; ++v)
+        reinterpret_cast<float4*>(sYW + k * RTP)[qd[v]] = make_float4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
+    }
+    if (tt == 0) {
+      double s = 0.0;
+      for (int i = 0; i < SLAB_TEAM / 32; ++i) s += sRed[i];
+      a.objpart[t] = s;
+    }
+    team_sync(team);
+    // ---- Z contribution: sum_k A(N-1)[i_k]^T W[k], cells split over ks thread sets
+    {
+      const int ZQ = R2P / 4, ntt = ZQ * XQ;
+      int ks = SLAB_TEAM / ntt;
+      const int cap = S::PF / (R2P * RTP);
+      if (ks > cap) ks = cap;
+      if (ks < 1) ks = 1;
+      for (int it = tt; it < ntt * ks; it += SLAB_TEAM) {
+        const int part = it / ntt, wq = it % ntt, zq = wq / XQ, xq = wq % XQ;
+        const int k_lo = part * na / ks, k_hi = (part + 1) * na / ks;
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[i][c] = 0.f;
+        for (int kk = k_lo; kk < k_hi; ++kk) {
+          const float4 av = *reinterpret_cast<const float4*>(sA2 + kk * R2S + 4 * zq);
+          const float4 yv = *reinterpret_cast<const float4*>(sYW + kk * RTP + 4 * xq);
+          const float ak[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            acc[i][0] = fmaf(ak[i], yv.x, acc[i][0]);
+            acc[i][1] = fmaf(ak[i], yv.y, acc[i][1]);
+            acc[i][2] = fmaf(ak[i], yv.z, acc[i][2]);
+            acc[i][3] = fmaf(ak[i], yv.w, acc[i][3]);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          *reinterpret_cast<float4*>(sPf + part * (R2P * RTP) + (4 * zq + i) * RTP + 4 * xq) =
+              make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      }
+      team_sync(team);
+      // the k-split parts in order; a slab of one tile is written directly, the tiles of a
+      // larger slab go to their slots and k_tile_sum adds them in tile order
+      float* dst = multi ? a.zpart + (size_t)t * zn : a.Z + p * zn;
+      for (int i = tt; i < zn; i += SLAB_TEAM) {
+        const int r = i / RT, c = i - r * RT;
+        float v = sPf[r * RTP + c];
+        for (int part = 1; part < ks; ++part) v += sPf[part * (R2P * RTP) + r * RTP + c];
+        dst[i] = v;
+      }
+    }
+  }
+}
+
+// Z[p] of slabs split over several tiles: the tiles' parts added in tile order; slabs
+// without sampled rows are zero (a slab of one tile was written by k_slab).
+__global__ void k_tile_sum(int64_t P, int zn, const uint2* __restrict__ slab, const float* __restrict__ zpart,
+                           float* __restrict__ Z) {
+  const int64_t n = P * zn;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i / zn;
+    const int c = (int)(i - p * zn);
+    const uint2 sl = slab[p];
+    if (sl.y == 1) continue;
+    float v = 0.f;
+    if (sl.y > 1) {
+      v = zpart[(size_t)sl.x * zn + c];
+      for (uint32_t t = sl.x + 1; t < sl.x + sl.y; ++t) v += zpart[(size_t)t * zn + c];
+    }
+    Z[i] = v;
+  }
+}
+
+// ------------------------------------------------------------------ tile construction
+
+__global__ void k_tiles_flag(const uint32_t* __restrict__ nd, int64_t n, uint32_t* __restrict__ f) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+    f[c] = nd[c] > 0 ? 1u : 0u;
+}
+
+// Non-empty cells in cell order: act[aidx[c]] = {c, start, nd, weight bits}.
+__global__ void k_tiles_act(int64_t ncell, const uint32_t* __restrict__ nd, const uint32_t* __restrict__ start,
+                            const float* __restrict__ cw, const uint32_t* __restrict__ aidx, uint4* __restrict__ act,
+                            uint32_t* __restrict__ meta) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t n = nd[c];
+    if (n > 0) act[aidx[c]] = make_uint4((uint32_t)c, start[c], n, __float_as_uint(cw[c]));
+    if (c == ncell - 1) meta[1] = aidx[c] + (n > 0 ? 1u : 0u);
+  }
+}
+
+// A tile starts at non-empty cell a when a is the first of its slab, when the tile has
+// reached cb cells, or when floor(entries before a in the slab / et) changes.
+__global__ void k_tiles_start(int64_t ncell, uint32_t I2, uint32_t cb, uint32_t et, const uint4* __restrict__ act,
+                              const uint32_t* __restrict__ aidx, const uint32_t* __restrict__ start,
+                              const uint32_t* __restrict__ meta, uint32_t* __restrict__ f) {
+  const uint32_t nact = meta[1];
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < ncell; a += (int64_t)gridDim.x * blockDim.x) {
+    if (a >= nact) {
+      f[a] = 0u;
+      continue;
+    }
+    const uint4 ac = act[a];
+    const uint32_t cs = (ac.x / I2) * I2;  // first cell of the slab
+    const uint32_t la = (uint32_t)a - aidx[cs];
+    const uint32_t base = start[cs];
+    bool s = la == 0 || la % cb == 0;
+    if (!s) s = (ac.y - base) / et != (act[a - 1].y - base) / et;
+    f[a] = s ? 1u : 0u;
+  }
+}
+
+__global__ void k_tiles_first(int64_t ncell, uint32_t I2, const uint4* __restrict__ act, const uint32_t* __restrict__ f,
+                              const uint32_t* __restrict__ tidx, uint4* __restrict__ tile, uint32_t* __restrict__ meta) {
+  const uint32_t nact = meta[1];
+  if (blockIdx.x == 0 && threadIdx.x == 0 && nact == 0) meta[0] = 0;
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < nact; a += (int64_t)gridDim.x * blockDim.x) {
+    if (f[a]) tile[tidx[a]] = make_uint4((uint32_t)a, 0u, act[a].x / I2, 0u);
+    if (a == nact - 1) meta[0] = tidx[a] + f[a];
+  }
+}
+
+__global__ void k_tiles_init_slab(int64_t P, uint2* __restrict__ slab) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x)
+    slab[p] = make_uint2(0xFFFFFFFFu, 0u);
+}
+
+// Cell count, entry count and work estimate of every tile; first tile and tile count
+// of every slab (integer atomics: the result does not depend on their order).
+__global__ void k_tiles_fin(int64_t ntmax, uint32_t cellcost, const uint4* __restrict__ act, uint4* __restrict__ tile,
+                            uint32_t* __restrict__ cost, uint2* __restrict__ slab, const uint32_t* __restrict__ meta) {
+  const uint32_t nt = meta[0], nact = meta[1];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntmax; t += (int64_t)gridDim.x * blockDim.x) {
+    if (t >= nt) {
+      cost[t] = 0u;
+      continue;
+    }
+    const uint32_t a0 = tile[t].x;
+    const uint32_t a1 = (t + 1 < nt) ? tile[t + 1].x : nact;
+    const uint32_t na = a1 - a0;
+    const uint4 last = act[a1 - 1];
+    const uint32_t E = last.y + last.z - act[a0].y;
+    const uint32_t p = tile[t].z;
+    tile[t].y = na;
+    tile[t].w = E;
+    cost[t] = E + cellcost * na;
+    atomicMin(&slab[p].x, (uint32_t)t);
+    atomicAdd(&slab[p].y, 1u);
+  }
+}
+
+// Tile descriptors in processing order, with the tile index and a flag for slabs of
+// more than one tile packed in.
+__global__ void k_tiles_sort(int64_t ntmax, const uint32_t* __restrict__ order, const uint4* __restrict__ tile,
+                             const uint2* __restrict__ slab, const uint32_t* __restrict__ meta,
+                             uint4* __restrict__ tsort) {
+  const uint32_t nt = meta[0];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nt; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t t = order[k];
+    const uint4 d = tile[t];
+    const uint32_t multi = slab[d.z].y > 1 ? 1u : 0u;
+    tsort[k] = make_uint4(d.x, t, d.z, d.w | ((d.y - 1u) << 24) | (multi << 31));
+  }
+}
+
+struct SlabLayout {
+  int RTP, R2P, R2S, cb;
+  bool smem_a;
+  size_t bytes;
+  uint32_t team_off, team_bytes, o_a2, o_x1, o_pf, o_act, o_cs, o_ctl;
+};
+
+size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
+
+SlabLayout slab_layout(int IT, int RT, int R2, bool smem_a) {
+  SlabLayout L = {};
+  L.RTP = rt_pad(RT);
+  L.R2P = (R2 + 3) / 4 * 4;
+  L.R2S = L.R2P + 4;
+  L.cb = cb_for(L.RTP);
+  L.smem_a = smem_a;
+  const int cols = L.RTP < 16 ? L.RTP : 16;
+  size_t off = smem_a ? (size_t)IT * L.RTP * 4 : 0;
+  off += (size_t)((IT + 3) / 4 * 4) * 4;
+  L.team_off = (uint32_t)al16(off);
+  size_t t = 0;
+  t += (size_t)L.cb * L.RTP * 4;  // Y / W
+  L.o_a2 = (uint32_t)t;
+  t += al16((size_t)L.cb * L.R2S * 4);
+  L.o_x1 = (uint32_t)t;
+  t += al16((size_t)L.R2P * L.RTP * 4);
+  L.o_pf = (uint32_t)t;
+  t += (size_t)SLAB_TEAM * cols * 4;
+  L.o_act = (uint32_t)t;
+  t += (size_t)L.cb * 16;
+  L.o_cs = (uint32_t)t;
+  t += al16((size_t)(L.cb + 4) * 4);
+  L.o_ctl = (uint32_t)t;
+  t += 128;
+  L.team_bytes = (uint32_t)al16(t);
+  L.bytes = L.team_off + (size_t)SLAB_TEAMS * L.team_bytes;
+  return L;
+}
+
+template <int RTP, bool SMEM_A>
+kr_status launch_slab_t(kr_ctx* ctx, const SlabArgs& a, size_t smem) {
+  static int configured_dev = -1;
+  static size_t configured_bytes = 0;
+  if (configured_dev != ctx->device || configured_bytes < smem) {
+    KR_CUDA(ctx, cudaFuncSetAttribute(k_slab<RTP, SMEM_A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured_dev = ctx->device;
+    configured_bytes = smem;
+  }
+  KR_LAUNCH(ctx, (k_slab<RTP, SMEM_A>), ctx->num_sms, SLAB_TEAM * SLAB_TEAMS, smem, a);
+  return KR_OK;
+}
+
+template <bool SMEM_A>
+kr_status launch_slab(kr_ctx* ctx, int RTP, const SlabArgs& a, size_t smem) {
+  switch (RTP) {
+    case 4: return launch_slab_t<4, SMEM_A>(ctx, a, smem);
+    case 8: return launch_slab_t<8, SMEM_A>(ctx, a, smem);
+    case 16: return launch_slab_t<16, SMEM_A>(ctx, a, smem);
+    case 32: return launch_slab_t<32, SMEM_A>(ctx, a, smem);
+    case 64: return launch_slab_t<64, SMEM_A>(ctx, a, smem);
+    default: return kr_fail(ctx, KR_EINVAL, "slab pass: R_N padded to %d", RTP);
+  }
+}
+
+int grid_n(kr_ctx* ctx, int64_t n, int block = 256) {
+  int64_t g = (n + block - 1) / block;
+  const int64_t cap = (int64_t)ctx->num_sms * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+bool kr_slab_eligible(kr_ctx* ctx, const Modes& m, const kr_sketch* sk) {
+  if (m.N < 2 || sk->nrow != 1) return false;
+  const int RT = m.R[m.N - 1], R2 = m.R[m.N - 2];
+  if (RT > 64 || R2 > 64 || m.I[m.N - 1] > 65535) return false;
+  return slab_layout(m.I[m.N - 1], RT, R2, false).bytes <= ctx->smem_optin;
+}
+
+void kr_tiles_setup(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, kr_tiles* tl) {
+  const int N = m.N;
+  tl->I2 = m.I[N - 2];
+  tl->R2 = m.R[N - 2];
+  tl->IT = m.I[N - 1];
+  tl->RT = m.R[N - 1];
+  int64_t P = 1;
+  for (int n = 0; n < N - 2; ++n) P *= m.I[n];
+  tl->P = P;
+  tl->cb = cb_for(rt_pad(tl->RT));
+  tl->et = ctx->slab_tile_entries;
+  const int64_t ncell = sk->ncell;
+  int64_t bound = P + (ncell + tl->cb - 1) / tl->cb + (sk->s + tl->et - 1) / tl->et;
+  tl->ntmax = bound < ncell ? bound : ncell;
+  if (tl->ntmax < 1) tl->ntmax = 1;
+  tl->par = 0;
+}
+
+void kr_tiles_own_need(const kr_tiles* tl, int64_t ncell, Need& nd) {
+  nd.add<uint4>(ncell);
+  nd.add<uint4>(tl->ntmax);
+  nd.add<uint32_t>(tl->ntmax);
+  nd.add<uint32_t>(tl->ntmax);
+  nd.add<uint4>(tl->ntmax);
+  nd.add<uint2>(tl->P);
+  nd.add<uint32_t>(4);
+  nd.add<float>((size_t)tl->ntmax * tl->R2 * tl->RT);
+  nd.add<double>(tl->ntmax);
+}
+
+void kr_tiles_layout(kr_tiles* tl, int64_t ncell, Carve& cv) {
+  tl->act = cv.take<uint4>(ncell);
+  tl->tile = cv.take<uint4>(tl->ntmax);
+  tl->cost = cv.take<uint32_t>(tl->ntmax);
+  tl->order = cv.take<uint32_t>(tl->ntmax);
+  tl->tsort = cv.take<uint4>(tl->ntmax);
+  tl->slab = cv.take<uint2>(tl->P);
+  tl->meta = cv.take<uint32_t>(4);
+  tl->zpart = cv.take<float>((size_t)tl->ntmax * tl->R2 * tl->RT);
+  tl->objpart = cv.take<double>(tl->ntmax);
+}
+
+void kr_tiles_scratch_need(const kr_tiles* tl, int64_t ncell, Need& nd) {
+  nd.add<uint32_t>(ncell);  // flags
+  nd.add<uint32_t>(ncell);  // non-empty index
+  nd.add<uint32_t>(ncell);  // tile index
+  kr_scan_need(ncell, nd);
+  kr_perm_need(tl->ntmax, nd);
+}
+
+kr_status kr_tiles_build(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, Carve& cv) {
+  const int64_t ncell = sk->ncell;
+  uint32_t* f = cv.take<uint32_t>(ncell);
+  uint32_t* aidx = cv.take<uint32_t>(ncell);
+  uint32_t* tidx = cv.take<uint32_t>(ncell);
+  if (cv.off > cv.cap) return kr_fail(ctx, KR_ENOMEM, "slab tiles: workspace too small");
+  KR_CUDA(ctx, cudaMemsetAsync(tl->meta, 0, 4 * sizeof(uint32_t), ctx->stream));
+  KR_CUDA(ctx, cudaMemsetAsync(tl->objpart, 0, sizeof(double) * tl->ntmax, ctx->stream));
+  KR_LAUNCH(ctx, k_tiles_flag, grid_n(ctx, ncell), 256, 0, sk->cell_nd, ncell, f);
+  {
+    Carve sc = cv;
+    KR_TRY(kr_scan_u32(ctx, f, aidx, ncell, sc));
+  }
+  KR_LAUNCH(ctx, k_tiles_act, grid_n(ctx, ncell), 256, 0, ncell, sk->cell_nd, sk->cell_start, sk->cell_w, aidx,
+            tl->act, tl->meta);
+  KR_LAUNCH(ctx, k_tiles_start, grid_n(ctx, ncell), 256, 0, ncell, (uint32_t)tl->I2, (uint32_t)tl->cb, tl->et, tl->act,
+            aidx, sk->cell_start, tl->meta, f);
+  {
+    Carve sc = cv;
+    KR_TRY(kr_scan_u32(ctx, f, tidx, ncell, sc));
+  }
+  KR_LAUNCH(ctx, k_tiles_first, grid_n(ctx, ncell), 256, 0, ncell, (uint32_t)tl->I2, tl->act, f, tidx, tl->tile,
+            tl->meta);
+  KR_LAUNCH(ctx, k_tiles_init_slab, grid_n(ctx, tl->P), 256, 0, tl->P, tl->slab);
+  KR_LAUNCH(ctx, k_tiles_fin, grid_n(ctx, tl->ntmax), 256, 0, tl->ntmax, (uint32_t)tl->R2, tl->act, tl->tile, tl->cost,
+            tl->slab, tl->meta);
+  {
+    Carve sc = cv;
+    KR_TRY(kr_balance_perm(ctx, tl->cost, tl->ntmax, tl->order, sc));
+  }
+  KR_LAUNCH(ctx, k_tiles_sort, grid_n(ctx, tl->ntmax), 256, 0, tl->ntmax, tl->order, tl->tile, tl->slab, tl->meta,
+            tl->tsort);
+  return KR_OK;
+}
+
+kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const float* A2, const float* AT,
+                       const float* X1, float* Z) {
+  SlabLayout L = slab_layout(tl->IT, tl->RT, tl->R2, true);
+  if (L.bytes > ctx->smem_optin) L = slab_layout(tl->IT, tl->RT, tl->R2, false);
+  if (L.bytes > ctx->smem_optin) return kr_fail(ctx, KR_ENOTIMPL, "slab pass: %zu bytes of shared memory", L.bytes);
+  SlabArgs a = {};
+  a.act = tl->act;
+  a.tsort = tl->tsort;
+  a.meta = tl->meta;
+  a.par = tl->par;
+  a.ent = sk->ent;
+  a.bt = sk->bt;
+  a.invpT = sk->invpT;
+  a.AT = AT;
+  a.A2 = A2;
+  a.X1 = X1;
+  a.Z = Z;
+  a.zpart = tl->zpart;
+  a.objpart = tl->objpart;
+  a.IT = tl->IT;
+  a.RT = tl->RT;
+  a.I2 = tl->I2;
+  a.R2 = tl->R2;
+  a.R2P = L.R2P;
+  a.R2S = L.R2S;
+  a.P = tl->P;
+  a.a2vec = (tl->R2 % 4 == 0) && ((reinterpret_cast<uintptr_t>(A2) & 15) == 0);
+  a.atvec = (tl->RT % 4 == 0) && ((reinterpret_cast<uintptr_t>(AT) & 15) == 0);
+  a.team_off = L.team_off;
+  a.team_bytes = L.team_bytes;
+  a.o_a2 = L.o_a2;
+  a.o_x1 = L.o_x1;
+  a.o_pf = L.o_pf;
+  a.o_act = L.o_act;
+  a.o_cs = L.o_cs;
+  a.o_ctl = L.o_ctl;
+  kr_status st = L.smem_a ? launch_slab<true>(ctx, L.RTP, a, L.bytes) : launch_slab<false>(ctx, L.RTP, a, L.bytes);
+  tl->par ^= 1;
+  KR_TRY(st);
+  const int zn = tl->R2 * tl->RT;
+  KR_LAUNCH(ctx, k_tile_sum, grid_n(ctx, tl->P * zn), 256, 0, tl->P, zn, tl->slab, tl->zpart, Z);
+  return KR_OK;
+}

@@ -498,6 +498,10 @@ struct IterBufs {
   float* t1;     // max intermediate
   double* part;  // partials (3 * nblk)
   double* red;   // 4 doubles
+  // slab form (tl != nullptr): X1 and Z are P x R_{N-1} x R_N (N >= 3; x and g for N = 2)
+  kr_tiles* tl = nullptr;
+  float* X1 = nullptr;
+  float* Z = nullptr;
 };
 
 int64_t max_intermediate(const Modes& m) {
@@ -538,6 +542,68 @@ kr_status backward(kr_ctx* ctx, const Modes& m, const IterBufs& bf) {
     tr[n] = 1;  // A^T from the stored I x R array
   }
   return kr_kron_apply2(ctx, N, din, dout, B, tr, bf.W, bf.g, bf.t0, bf.t1);
+}
+
+// Largest intermediate of the prefix mode products of the slab form (modes < N-2).
+int64_t slab_max_intermediate(const Modes& m) {
+  int64_t cur = kr_prod_R(m), mx = cur;
+  for (int n = 0; n < m.N - 2; ++n) {
+    cur = cur / m.R[n] * m.I[n];
+    if (cur > mx) mx = cur;
+  }
+  return mx;
+}
+
+// Slab form of the sampled pass: X1 = X x_1 A(1) ... x_{N-2} A(N-2), then the fused slab
+// kernel (Z and the per-tile objective partials in bf.tl->objpart).
+kr_status slab_forward(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const IterBufs& bf) {
+  const int N = m.N;
+  const float* X1 = bf.x;
+  if (N > 2) {
+    int din[KR_MAX_MODES], dout[KR_MAX_MODES], tr[KR_MAX_MODES];
+    const float* B[KR_MAX_MODES];
+    for (int n = 0; n < N; ++n) {
+      din[n] = m.R[n];
+      dout[n] = (n < N - 2) ? m.I[n] : m.R[n];
+      B[n] = (n < N - 2) ? m.A[n] : nullptr;
+      tr[n] = 0;
+    }
+    KR_TRY(kr_kron_apply2(ctx, N, din, dout, B, tr, bf.x, bf.X1, bf.t0, bf.t1));
+    X1 = bf.X1;
+  }
+  return kr_slab_pass(ctx, sk, bf.tl, m.A[N - 2], m.A[N - 1], X1, N > 2 ? bf.Z : bf.g);
+}
+
+// g = Z x_1 A(1)^T ... x_{N-2} A(N-2)^T (for N = 2 the slab pass wrote g itself).
+kr_status slab_backward(kr_ctx* ctx, const Modes& m, const IterBufs& bf) {
+  const int N = m.N;
+  if (N == 2) return KR_OK;
+  int din[KR_MAX_MODES], dout[KR_MAX_MODES], tr[KR_MAX_MODES];
+  const float* B[KR_MAX_MODES];
+  for (int n = 0; n < N; ++n) {
+    din[n] = (n < N - 2) ? m.I[n] : m.R[n];
+    dout[n] = m.R[n];
+    B[n] = (n < N - 2) ? m.A[n] : nullptr;
+    tr[n] = 1;
+  }
+  return kr_kron_apply2(ctx, N, din, dout, B, tr, bf.Z, bf.g, bf.t0, bf.t1);
+}
+
+// Sampled pass at x: g = K~^T Omega (b~ - K~ x) (if want_g) and the objective partials
+// (*op, *on: FP64 values to be summed).
+kr_status sampled_pass(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const IterBufs& bf, int nblk, bool want_g,
+                       const double** op, int* on) {
+  if (bf.tl) {
+    KR_TRY(slab_forward(ctx, m, sk, bf));
+    *op = bf.tl->objpart;
+    *on = (int)bf.tl->ntmax;
+    return want_g ? slab_backward(ctx, m, bf) : KR_OK;
+  }
+  int used = 0;
+  KR_TRY(forward_resid(ctx, m, sk, bf, nblk, &used));
+  *op = bf.part;
+  *on = used;
+  return want_g ? backward(ctx, m, bf) : KR_OK;
 }
 
 }  // namespace
@@ -581,19 +647,39 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   kr_sketch sk;
   kr_sketch_setup(&sk, m, cfg.s);
   const int64_t ncell = sk.ncell;
-  const int64_t mx = max_intermediate(m);
+  const bool slab = ctx->slab_pass && kr_slab_eligible(ctx, m, &sk);
+  sk.want_desc = !slab;
+  kr_tiles tl;
+  int64_t nyw = ncell * RT, nx1 = 0;  // floats of Y / W (per-cell form) or X1 / Z (slab form, N >= 3)
+  int64_t mx = max_intermediate(m);
+  if (slab) {
+    kr_tiles_setup(ctx, m, &sk, &tl);
+    nyw = 0;
+    nx1 = N > 2 ? tl.P * m.R[N - 2] * RT : 0;
+    mx = slab_max_intermediate(m);
+  }
   Need nd;
   kr_tables_need(m, cfg.lambda > 0.0, nd);
   kr_sketch_own_need(&sk, nd);
-  nd.add<float>(ncell * RT);  // Y
-  nd.add<float>(ncell * RT);  // W
-  nd.add<float>(R);           // g
-  nd.add<float>(R);           // d
-  nd.add<float>(mx);          // t0
-  nd.add<float>(mx);          // t1
+  if (slab) kr_tiles_own_need(&tl, ncell, nd);
+  nd.add<float>(nyw);  // Y
+  nd.add<float>(nyw);  // W
+  nd.add<float>(nx1);  // X1
+  nd.add<float>(nx1);  // Z
+  nd.add<float>(R);    // g
+  nd.add<float>(R);    // d
+  nd.add<float>(mx);   // t0
+  nd.add<float>(mx);   // t1
   nd.add<double>(3 * (size_t)(nblk > 1024 ? nblk : 1024));
   nd.add<double>(16);
-  kr_sketch_scratch_need(cfg.s, ncell, nd);
+  {
+    Need sc = nd;
+    kr_sketch_scratch_need(cfg.s, ncell, nd);
+    if (slab) {
+      kr_tiles_scratch_need(&tl, ncell, sc);
+      if (sc.off > nd.off) nd.off = sc.off;
+    }
+  }
   KR_TRY(kr_ws_reserve(ctx, nd.off));
   KR_TRY(kr_hbuf_reserve(ctx, 4096));
   Carve cv(ctx->ws, ctx->ws_size);
@@ -604,16 +690,26 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   KR_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
   kr_sketch_layout(&sk, cv);
   IterBufs bf;
+  if (slab) {
+    kr_tiles_layout(&tl, ncell, cv);
+    bf.tl = &tl;
+  }
   bf.x = x_out;
-  bf.Y = cv.take<float>(ncell * RT);
-  bf.W = cv.take<float>(ncell * RT);
+  bf.Y = cv.take<float>(nyw);
+  bf.W = cv.take<float>(nyw);
+  bf.X1 = cv.take<float>(nx1);
+  bf.Z = cv.take<float>(nx1);
   bf.g = cv.take<float>(R);
   bf.d = cv.take<float>(R);
   bf.t0 = cv.take<float>(mx);
   bf.t1 = cv.take<float>(mx);
   bf.part = cv.take<double>(3 * (size_t)(nblk > 1024 ? nblk : 1024));
   bf.red = cv.take<double>(16);
-  KR_TRY(kr_sketch_fill(ctx, m, t, b, seed, call_id, 0, &sk, cv));
+  {
+    Carve sc = cv;
+    KR_TRY(kr_sketch_fill(ctx, m, t, b, seed, call_id, 0, &sk, sc));
+  }
+  if (slab) KR_TRY(kr_tiles_build(ctx, &sk, &tl, cv));
   KR_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
   KR_CUDA(ctx, cudaMemsetAsync(bf.x, 0, sizeof(float) * R, ctx->stream));
   KR_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
@@ -624,10 +720,10 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   kr_status st = KR_OK;
   unsigned int* ticket = reinterpret_cast<unsigned int*>(bf.red + 8);
   KR_CUDA(ctx, cudaMemsetAsync(ticket, 0, sizeof(unsigned int), ctx->stream));
+  const double* op = nullptr;
+  int on = 0;
   for (it = 1; it <= cfg.max_iter; ++it) {
-    int used = 0;
-    KR_TRY(forward_resid(ctx, m, &sk, bf, nblk, &used));
-    KR_TRY(backward(ctx, m, bf));
+    KR_TRY(sampled_pass(ctx, m, &sk, bf, nblk, true, &op, &on));
     if (cfg.lambda > 0.0) KR_LAUNCH(ctx, k_sub_lambda_x, ublk, 256, 0, bf.g, bf.x, (float)cfg.lambda, R);
     KR_TRY(kr_precond_apply(ctx, t, cfg.lambda, bf.g, bf.d, bf.t0, bf.t1));
     KR_LAUNCH(ctx, k_update_reduce, ublk, 256, 0, bf.x, bf.d, (float)cfg.alpha, R, bf.part, ticket, bf.red);
@@ -648,12 +744,10 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     }
   }
   if (it > cfg.max_iter) it = cfg.max_iter;
-  if (it > cfg.max_iter) it = cfg.max_iter;
   KR_CUDA(ctx, cudaEventRecord(ev[4], ctx->stream));
   // final sampled objective at the returned x (FP64 accumulation)
-  int used = 0;
-  KR_TRY(forward_resid(ctx, m, &sk, bf, nblk, &used));
-  KR_LAUNCH(ctx, k_reduce_partials, 1, 256, 0, bf.part, used, 1, 0, bf.red);
+  KR_TRY(sampled_pass(ctx, m, &sk, bf, nblk, false, &op, &on));
+  KR_LAUNCH(ctx, k_reduce_partials, 1, 256, 0, op, on, 1, 0, bf.red);
   KR_LAUNCH(ctx, k_dot_self, ublk, 256, 0, bf.x, R, bf.part + 1024);
   KR_LAUNCH(ctx, k_reduce_partials, 1, 256, 0, bf.part + 1024, ublk, 1, 0, bf.red + 1);
   KR_CUDA(ctx, cudaMemcpyAsync(h, bf.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
