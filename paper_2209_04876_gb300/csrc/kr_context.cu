@@ -185,9 +185,11 @@ int kr_kind_of(const char* k) {
   if (s.find("k_resid") != std::string::npos) return KR_K_RESID;
   if (s.find("k_slab") != std::string::npos) return KR_K_SLAB;
   if (s.find("k_mode_product") != std::string::npos) return KR_K_MODEPROD;
-  if (s.find("k_sample") != std::string::npos) return KR_K_SAMPLE;
-  if (s.find("k_scatter") != std::string::npos) return KR_K_SCATTER;
-  if (s.find("k_dedup") != std::string::npos) return KR_K_DEDUP;
+  if (s.find("k_sample") != std::string::npos || s.find("k_draw") != std::string::npos ||
+      s.find("k_guide") != std::string::npos)
+    return KR_K_SAMPLE;
+  if (s.find("k_radix") != std::string::npos) return KR_K_SCATTER;
+  if (s.find("k_rle") != std::string::npos || s.find("k_cell_w") != std::string::npos) return KR_K_DEDUP;
   if (s.find("k_gram") != std::string::npos || s.find("k_chol") != std::string::npos ||
       s.find("k_leverage") != std::string::npos || s.find("k_cdf") != std::string::npos ||
       s.find("k_jacobi") != std::string::npos)

@@ -210,6 +210,10 @@ int kr_resid_blocks(kr_ctx* ctx);
 // Exclusive scan of n u32 values (in may equal out); scratch carved from cv.
 void kr_scan_need(int64_t n, Need& nd);
 kr_status kr_scan_u32(kr_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n, Carve& cv);
+// Stable LSD radix sort of n keys on their low nbits bits; *sorted is keys or alt.
+void kr_radix_need(int64_t n, Need& nd);
+kr_status kr_radix_sort_u32(kr_ctx* ctx, uint32_t* keys, uint32_t* alt, int64_t n, int nbits, uint32_t** sorted,
+                            Carve& cv);
 // perm = cells ordered by decreasing floor(log2(distinct rows)), stable (deterministic).
 void kr_perm_need(int64_t ncell, Need& nd);
 kr_status kr_balance_perm(kr_ctx* ctx, const uint32_t* nd, int64_t ncell, uint32_t* perm, Carve& cv);

@@ -67,6 +67,7 @@ __device__ __forceinline__ void draw(const SampleModes& sm, const uint64_t* cons
 
 // Thresholds to shared memory when they fit (sum I_n <= 4096 entries = 32 KB).
 constexpr int THR_SMEM = 4096;
+constexpr int GUIDE_MAX = 65536;  // guide entries per mode at most (I_n <= 65535)
 
 __device__ __forceinline__ void load_thr(const SampleModes& sm, uint64_t* buf, const uint64_t** thr) {
   int tot = 0;
@@ -103,196 +104,186 @@ __global__ void k_sample_idx(SampleModes sm, int64_t s, uint32_t k0, uint32_t k1
   }
 }
 
-// Solver path: cell id and last coordinate packed in one key; histogram by cell.
-// Draws come in nrow batches of s_row (one batch per Tucker factor row; nrow = 1 for a
-// plain solve). Draw t of batch r uses Philox counter row row0 + r. The key is
-// cell * IT + i_T with cell = r * ncell_inner + (i_1..i_{N-1}) (the linear row index of
-// the batched system). The histogram atomic returns each draw's rank inside its cell
-// (rank[t]), so the scatter needs no atomics. Templated on N so the per-draw indices
-// and table pointers stay in registers.
+// Guide table of one mode (Chen & Asau's indexed search): g[m] = smallest i with
+// thr[i] > m * 2^shift, so the inverse-CDF search of U starts at g[U >> shift] and steps
+// forward while thr[i] <= U. The result is the same index as the binary search.
+__global__ void k_guide(const uint64_t* __restrict__ thr, int n, int shift, int M, uint16_t* __restrict__ g) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x)
+    g[m] = (uint16_t)search_thr(thr, n, (uint64_t)m << shift);
+}
+
+struct DrawModes {
+  int N;
+  int I[KR_MAX_MODES];
+  int shift[KR_MAX_MODES];  // 53 - log2(guide entries)
+  int M[KR_MAX_MODES];      // guide entries
+  const uint64_t* thr[KR_MAX_MODES];
+  const uint16_t* guide[KR_MAX_MODES];
+};
+
+__device__ __forceinline__ int guided_search(const uint64_t* thr, const uint16_t* guide, int shift, uint64_t U) {
+  int i = guide[U >> shift];
+  while (thr[i] <= U) ++i;
+  return i;
+}
+
+// Solver path: every draw's row key cell * IT + i_T (cell = r * ncell_inner +
+// (i_1..i_{N-1}) for draw batch r, the linear row index of the batched system). Draws
+// come in nrow batches of s_row (one per Tucker factor row; nrow = 1 for a plain solve);
+// draw t of batch r uses Philox counter row row0 + r. Templated on N so the per-draw
+// indices and table pointers stay in registers.
 template <int N>
-__global__ void __launch_bounds__(256) k_sample_keys(SampleModes sm, int64_t s_row, int nrow, uint32_t k0,
-                                                     uint32_t k1, uint32_t row0, uint32_t cid, int64_t ncell_inner,
-                                                     uint32_t* __restrict__ keys, uint32_t* __restrict__ rank,
-                                                     uint32_t* __restrict__ cell_cnt) {
-  __shared__ uint64_t buf[THR_SMEM];
+__global__ void __launch_bounds__(256) k_draw_keys(DrawModes dm, int64_t s_row, int nrow, uint32_t k0, uint32_t k1,
+                                                   uint32_t row0, uint32_t cid, uint32_t ncell_inner,
+                                                   uint32_t* __restrict__ keys) {
+  __shared__ uint64_t s_thr[THR_SMEM];
+  __shared__ uint16_t s_guide[THR_SMEM];
   const uint64_t* thr[N];
-  int In[N];
+  const uint16_t* guide[N];
+  int In[N], sh[N];
   {
-    int tot = 0;
-#pragma unroll
-    for (int n = 0; n < N; ++n) tot += sm.I[n];
-    int off = 0;
+    int ti = 0, tm = 0;
 #pragma unroll
     for (int n = 0; n < N; ++n) {
-      In[n] = sm.I[n];
-      if (tot <= THR_SMEM) {
-        for (int i = threadIdx.x; i < In[n]; i += blockDim.x) buf[off + i] = sm.thr[n][i];
-        thr[n] = buf + off;
-        off += In[n];
+      ti += dm.I[n];
+      tm += dm.M[n];
+    }
+    const bool fit = ti <= THR_SMEM && tm <= THR_SMEM;
+    int oi = 0, om = 0;
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      In[n] = dm.I[n];
+      sh[n] = dm.shift[n];
+      if (fit) {
+        for (int i = threadIdx.x; i < In[n]; i += blockDim.x) s_thr[oi + i] = dm.thr[n][i];
+        for (int i = threadIdx.x; i < dm.M[n]; i += blockDim.x) s_guide[om + i] = dm.guide[n][i];
+        thr[n] = s_thr + oi;
+        guide[n] = s_guide + om;
+        oi += In[n];
+        om += dm.M[n];
       } else {
-        thr[n] = sm.thr[n];
+        thr[n] = dm.thr[n];
+        guide[n] = dm.guide[n];
       }
     }
     __syncthreads();
   }
   const uint32_t IT = (uint32_t)In[N - 1];
   const int64_t total = s_row * nrow;
-  const uint32_t lane = threadIdx.x & 31;
-  for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x; t0 < total; t0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = t0 + threadIdx.x;
-    const bool live = t < total;
-    uint32_t cell = 0, key = 0;
-    if (live) {
-      uint32_t r = 0;
-      int64_t tl = t;
-      if (nrow > 1) {
-        r = (uint32_t)((uint64_t)t / (uint64_t)s_row);
-        tl = t - (int64_t)r * s_row;
-      }
-      int idx[N];
-#pragma unroll
-      for (int k = 0; 2 * k < N; ++k) {
-        const uint4 w = philox4x32_10(
-            make_uint4((uint32_t)tl, (uint32_t)((uint64_t)tl >> 32), (uint32_t)k + 256u * (row0 + r), cid), k0, k1);
-        idx[2 * k] = search_thr(thr[2 * k], In[2 * k], u53(w.x, w.y));
-        if (2 * k + 1 < N) idx[2 * k + 1] = search_thr(thr[2 * k + 1], In[2 * k + 1], u53(w.z, w.w));
-      }
-#pragma unroll
-      for (int n = 0; n < N - 1; ++n) cell = cell * (uint32_t)In[n] + (uint32_t)idx[n];
-      cell += r * (uint32_t)ncell_inner;
-      key = cell * IT + (uint32_t)idx[N - 1];
-      keys[t] = key;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t r = 0;
+    int64_t tl = t;
+    if (nrow > 1) {
+      r = (uint32_t)((uint64_t)t / (uint64_t)s_row);
+      tl = t - (int64_t)r * s_row;
     }
-    // warp-aggregated histogram increment; the returned base gives each draw its rank
-    const unsigned act = __ballot_sync(0xffffffffu, live);
-    if (live) {
-      const unsigned peers = __match_any_sync(act, cell);
-      const int leader = __ffs(peers) - 1;
-      uint32_t base = 0;
-      if ((int)lane == leader) base = atomicAdd(&cell_cnt[cell], (uint32_t)__popc(peers));
-      base = __shfl_sync(peers, base, leader);
-      rank[t] = base + __popc(peers & ((1u << lane) - 1u));
+    int idx[N];
+#pragma unroll
+    for (int k = 0; 2 * k < N; ++k) {
+      const uint4 w = philox4x32_10(
+          make_uint4((uint32_t)tl, (uint32_t)((uint64_t)tl >> 32), (uint32_t)k + 256u * (row0 + r), cid), k0, k1);
+      idx[2 * k] = guided_search(thr[2 * k], guide[2 * k], sh[2 * k], u53(w.x, w.y));
+      if (2 * k + 1 < N) idx[2 * k + 1] = guided_search(thr[2 * k + 1], guide[2 * k + 1], sh[2 * k + 1], u53(w.z, w.w));
+    }
+    uint32_t cell = 0;
+#pragma unroll
+    for (int n = 0; n < N - 1; ++n) cell = cell * (uint32_t)In[n] + (uint32_t)idx[n];
+    cell += r * ncell_inner;
+    keys[t] = cell * IT + (uint32_t)idx[N - 1];
+  }
+}
+
+// ------------------------------------------------------------------ runs of equal keys
+
+// After the sort: run d of equal keys starts at hp[d] (hp[ndist] = n, meta[0] = ndist).
+__global__ void k_rle_heads(const uint32_t* __restrict__ k, int64_t n, uint32_t* __restrict__ f) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    f[e] = (e == 0 || k[e] != k[e - 1]) ? 1u : 0u;
+}
+
+__global__ void k_rle_pos(const uint32_t* __restrict__ k, const uint32_t* __restrict__ dpos, int64_t n,
+                          uint32_t* __restrict__ hp, uint32_t* __restrict__ meta) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const bool head = e == 0 || k[e] != k[e - 1];
+    if (head) hp[dpos[e]] = (uint32_t)e;
+    if (e == n - 1) {
+      const uint32_t nd = dpos[e] + (head ? 1u : 0u);
+      hp[nd] = (uint32_t)n;
+      meta[0] = nd;
     }
   }
 }
 
-// Scatter i_T of every draw into its cell's slot range (position = cell start + rank).
-__global__ void k_scatter(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ rank, int64_t s, uint32_t IT,
-                          const uint32_t* __restrict__ start, uint16_t* __restrict__ slot) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < s; t += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t key = keys[t];
-    const uint32_t cell = key / IT;
-    slot[start[cell] + rank[t]] = (uint16_t)(key - cell * IT);
-  }
+// Entries per run: the multiplicity is stored in 16 bits, so a run longer than 65535
+// takes several entries (zero past the last run).
+__global__ void k_rle_count(const uint32_t* __restrict__ hp, const uint32_t* __restrict__ meta, int64_t n,
+                            uint32_t* __restrict__ m) {
+  const uint32_t nd = meta[0];
+  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < n; d += (int64_t)gridDim.x * blockDim.x)
+    m[d] = d < nd ? (hp[d + 1] - hp[d] + 65534u) / 65535u : 0u;
 }
 
-// Per cell (one warp): count table over i_T in shared memory, then emit the distinct
-// entries in increasing i_T order with their multiplicities, gather b, and the
-// per-cell weight prod_{n<N-1} 1/p_n(i_n) / s.
-constexpr int DEDUP_WARPS = 8;
-constexpr int DEDUP_MAX_IT = 8192;
-
-// Batched rows: cell c belongs to row c / ncell_inner; its entry (c, i) is the row-major
-// index key = (c % ncell_inner) * IT + i over the sampled modes, and b is read at
-// ((key / xPafter) * xI + row) * xPafter + key % xPafter (X_(n) row `row`; for a plain
-// solve xI = xPafter = 1 and the index is the key itself).
-__global__ void k_dedup(SampleModes sm, int64_t ncell, int64_t ncell_inner, int64_t xI, int64_t xPafter, uint32_t IT,
-                        float inv_s, const uint32_t* __restrict__ start,
-                        const uint32_t* __restrict__ cnt, const uint16_t* __restrict__ slot, const float* __restrict__ b,
-                        uint32_t* __restrict__ ent, float* __restrict__ bt, uint32_t* __restrict__ nd,
-                        float* __restrict__ cell_w) {
-  extern __shared__ uint32_t tabs[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t* tab = tabs + (size_t)warp * IT;
-  for (uint32_t i = lane; i < IT; i += 32) tab[i] = 0;
-  __syncwarp();
-  const uint32_t chunk = (IT + 31) / 32;
-  const uint32_t lo = min(IT, lane * chunk), hi = min(IT, lo + chunk);
-  for (int64_t c = (int64_t)blockIdx.x * DEDUP_WARPS + warp; c < ncell; c += (int64_t)gridDim.x * DEDUP_WARPS) {
-    const uint32_t n = cnt[c], base = start[c];
-    const uint32_t c32 = (uint32_t)c, nci = (uint32_t)ncell_inner;
-    const uint32_t row32 = c32 / nci;
-    const int64_t c_in = (int64_t)(c32 - row32 * nci), row = row32;
-    if (lane == 0) {
-      // weight of the cell: prod over the first N-1 coordinates of 1/p
-      float w = inv_s;
-      uint32_t rem = (uint32_t)c_in;
-      for (int m = sm.N - 2; m >= 0; --m) {
-        const uint32_t Im = (uint32_t)sm.I[m];
-        const uint32_t q = rem / Im;
-        w *= sm.invp[m][rem - q * Im];
-        rem = q;
-      }
-      cell_w[c] = w;
-    }
-    if (n == 0) {
-      if (lane == 0) nd[c] = 0;
-      continue;
-    }
-    for (uint32_t j = lane; j < n; j += 32) atomicAdd(&tab[slot[base + j]], 1u);
-    __syncwarp();
-    uint32_t mine = 0;
-    for (uint32_t i = lo; i < hi; ++i) {
-      uint32_t v = tab[i];
-      mine += (v + 65534u) / 65535u;  // entries needed (multiplicity stored in 16 bits)
-    }
-    uint32_t incl = mine;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= off) incl += v;
-    }
-    uint32_t pos = base + incl - mine;
-    const int64_t rowbase = c_in * (int64_t)IT;
-    for (uint32_t i = lo; i < hi; ++i) {
-      uint32_t v = tab[i];
-      if (v == 0) continue;
-      tab[i] = 0;
+// Entries of run d at epos[d]: (i_T | multiplicity << 16) and b~ gathered from b. A batch
+// row's entry (c, i) is the row-major index key = (c % ncell_inner) * IT + i over the
+// sampled modes and b is read at ((key / xPafter) * xI + row) * xPafter + key % xPafter
+// (X_(n) row `row`; for a plain solve xI = xPafter = 1 and the index is the key).
+// Entries per cell are added to nd (one atomic per cell and warp).
+__global__ void k_rle_emit(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ hp,
+                           const uint32_t* __restrict__ epos, const uint32_t* __restrict__ meta, int64_t n,
+                           uint32_t IT, uint32_t ncell_inner, int64_t xI, int64_t xPafter, const float* __restrict__ b,
+                           uint32_t* __restrict__ ent, float* __restrict__ bt, uint32_t* __restrict__ nd,
+                           unsigned long long* __restrict__ total) {
+  const uint32_t ndist = meta[0];
+  const int64_t nwork = ((int64_t)ndist + 31) / 32 * 32;
+  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < nwork; d += (int64_t)gridDim.x * blockDim.x) {
+    const bool live = d < ndist;
+    uint32_t cell = 0, m = 0;
+    if (live) {
+      const uint32_t h0 = hp[d];
+      uint32_t cnt = hp[d + 1] - h0;
+      const uint32_t key = keys[h0];
+      cell = key / IT;
+      const uint32_t i = key - cell * IT;
       float bv = 0.f;
       if (b) {
-        const int64_t key = rowbase + i;
-        const int64_t bi = (xPafter == 1 && xI == 1) ? key : ((key / xPafter) * xI + row) * xPafter + key % xPafter;
+        const uint32_t row = cell / ncell_inner;
+        const int64_t rk = (int64_t)(cell - row * ncell_inner) * IT + i;
+        const int64_t bi = (xPafter == 1 && xI == 1) ? rk : ((rk / xPafter) * xI + row) * xPafter + rk % xPafter;
         bv = b[bi];
       }
-      while (v > 0) {
-        uint32_t take = v > 65535u ? 65535u : v;
+      uint32_t pos = epos[d];
+      m = (cnt + 65534u) / 65535u;
+      if (d == ndist - 1) total[0] = (unsigned long long)pos + m;
+      while (cnt > 0) {
+        const uint32_t take = cnt > 65535u ? 65535u : cnt;
         ent[pos] = i | (take << 16);
         bt[pos] = bv;
         ++pos;
-        v -= take;
+        cnt -= take;
       }
     }
-    uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    if (lane == 0) nd[c] = total;
-    __syncwarp();
-  }
-}
-
-// Compaction of the merged entries: cell c's nd[c] entries move from its draw-sized
-// region at start[c] to position newstart[c] (exclusive scan of nd), so that the entries
-// of consecutive cells lie back to back. One warp per cell; the copy goes to scratch and
-// k_copy_back returns the first total[0] entries.
-__global__ void k_compact(int64_t ncell, const uint32_t* __restrict__ start, const uint32_t* __restrict__ newstart,
-                          const uint32_t* __restrict__ nd, const uint32_t* __restrict__ ent,
-                          const float* __restrict__ bt, uint32_t* __restrict__ ent2, float* __restrict__ bt2) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < ncell; c += warps) {
-    const uint32_t n = nd[c], from = start[c], to = newstart[c];
-    for (uint32_t k = lane; k < n; k += 32) {
-      ent2[to + k] = ent[from + k];
-      bt2[to + k] = bt[from + k];
+    const unsigned act = __ballot_sync(0xffffffffu, live);
+    if (live) {
+      const unsigned peers = __match_any_sync(act, cell);
+      const uint32_t sum = __reduce_add_sync(peers, m);
+      if ((peers & ((1u << (threadIdx.x & 31)) - 1u)) == 0u) atomicAdd(&nd[cell], sum);
     }
   }
 }
 
-__global__ void k_copy_back(const unsigned long long* __restrict__ total, const uint32_t* __restrict__ ent2,
-                            const float* __restrict__ bt2, uint32_t* __restrict__ ent, float* __restrict__ bt) {
-  const int64_t n = (int64_t)total[0];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    ent[i] = ent2[i];
-    bt[i] = bt2[i];
+// Weight of every cell: prod over its first N-1 coordinates of 1/p, times 1/s.
+__global__ void k_cell_w(SampleModes sm, int64_t ncell, uint32_t ncell_inner, float inv_s, float* __restrict__ cell_w) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c32 = (uint32_t)c;
+    uint32_t rem = c32 - (c32 / ncell_inner) * ncell_inner;
+    float w = inv_s;
+    for (int m = sm.N - 2; m >= 0; --m) {
+      const uint32_t Im = (uint32_t)sm.I[m];
+      const uint32_t q = rem / Im;
+      w *= sm.invp[m][rem - q * Im];
+      rem = q;
+    }
+    cell_w[c] = w;
   }
 }
 
@@ -322,13 +313,6 @@ __global__ void k_build_desc(const uint32_t* __restrict__ perm, const uint32_t* 
     const uint32_t c = perm[q];
     desc[q] = make_uint4(c, start[c], nd[c], __float_as_uint(cw[c]));
   }
-}
-
-__global__ void k_sum_u32(const uint32_t* __restrict__ v, int64_t n, unsigned long long* out) {
-  unsigned long long acc = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) acc += v[i];
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 
 SampleModes make_sample_modes(const Modes& m, const FactorTables& t) {
@@ -393,70 +377,91 @@ void kr_sketch_layout(kr_sketch* sk, Carve& cv) {
 }
 
 kr_status kr_sketch_check(kr_ctx* ctx, const Modes& m, int64_t s) {
+  (void)m;
   if (s < 1 || s >= (int64_t(1) << 31)) return kr_fail(ctx, KR_EINVAL, "sketch: s=%lld outside [1, 2^31)", (long long)s);
-  if (m.I[m.N - 1] > DEDUP_MAX_IT)
-    return kr_fail(ctx, KR_ENOTIMPL, "sketch: last mode size %d exceeds %d", m.I[m.N - 1], DEDUP_MAX_IT);
   return KR_OK;
 }
 
-// Second phase of the sketch build, with scratch carved from `cv`.
+// Second phase of the sketch build, with scratch carved from `cv`: draw the row keys,
+// sort them, and turn the runs of equal keys into the merged entries of every cell.
 kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, const float* b, uint64_t seed,
                          uint64_t call_id, int row, kr_sketch* sk, Carve& cv) {
   const int N = m.N;
   const int64_t s = sk->s, ncell = sk->ncell;
   const uint32_t IT = (uint32_t)sk->IT;
   uint32_t* keys = cv.take<uint32_t>(s);
-  uint32_t* cnt = cv.take<uint32_t>(ncell);
-  uint32_t* rank = cv.take<uint32_t>(s);
-  uint16_t* slot = cv.take<uint16_t>(s);
+  uint32_t* alt = cv.take<uint32_t>(s);
+  uint32_t* hp = cv.take<uint32_t>(s + 1);
+  uint32_t* mcnt = cv.take<uint32_t>(s);
+  uint32_t* meta = cv.take<uint32_t>(4);
   unsigned long long* dsum = cv.take<unsigned long long>(1);
+  uint16_t* gbuf = cv.take<uint16_t>((size_t)KR_MAX_MODES * GUIDE_MAX);
   if (cv.off > cv.cap) return kr_fail(ctx, KR_ENOMEM, "sketch: workspace too small");
   SampleModes sm = make_sample_modes(m, t);
-  KR_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * ncell, ctx->stream));
+  DrawModes dm = {};
+  dm.N = N;
+  for (int n = 0; n < N; ++n) {
+    int gb = 0;
+    while ((1 << gb) < m.I[n]) ++gb;
+    dm.I[n] = m.I[n];
+    dm.M[n] = 1 << gb;
+    dm.shift[n] = 53 - gb;
+    dm.thr[n] = t.thr[n];
+    dm.guide[n] = gbuf + (size_t)n * GUIDE_MAX;
+    KR_LAUNCH(ctx, k_guide, grid_for(ctx, dm.M[n], 256), 256, 0, t.thr[n], m.I[n], dm.shift[n], dm.M[n],
+              gbuf + (size_t)n * GUIDE_MAX);
+  }
+  KR_CUDA(ctx, cudaMemsetAsync(sk->cell_nd, 0, sizeof(uint32_t) * ncell, ctx->stream));
   KR_CUDA(ctx, cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), ctx->stream));
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32), cid = (uint32_t)call_id;
   {
     const int gs = grid_for(ctx, s, 256);
-#define KR_SAMPLE_KEYS(NN)                                                                                \
-  case NN:                                                                                                \
-    KR_LAUNCH(ctx, k_sample_keys<NN>, gs, 256, 0, sm, sk->s_row, sk->nrow, k0, k1, (uint32_t)row, cid,     \
-              sk->ncell_inner, keys, rank, cnt);                                                          \
+#define KR_DRAW_KEYS(NN)                                                                                         \
+  case NN:                                                                                                       \
+    KR_LAUNCH(ctx, k_draw_keys<NN>, gs, 256, 0, dm, sk->s_row, sk->nrow, k0, k1, (uint32_t)row, cid,             \
+              (uint32_t)sk->ncell_inner, keys);                                                                  \
     break;
     switch (N) {
-      KR_SAMPLE_KEYS(1)
-      KR_SAMPLE_KEYS(2)
-      KR_SAMPLE_KEYS(3)
-      KR_SAMPLE_KEYS(4)
-      KR_SAMPLE_KEYS(5)
-      KR_SAMPLE_KEYS(6)
-      KR_SAMPLE_KEYS(7)
-      KR_SAMPLE_KEYS(8)
+      KR_DRAW_KEYS(1)
+      KR_DRAW_KEYS(2)
+      KR_DRAW_KEYS(3)
+      KR_DRAW_KEYS(4)
+      KR_DRAW_KEYS(5)
+      KR_DRAW_KEYS(6)
+      KR_DRAW_KEYS(7)
+      KR_DRAW_KEYS(8)
       default:
         return kr_fail(ctx, KR_EINVAL, "sketch: N=%d", N);
     }
-#undef KR_SAMPLE_KEYS
+#undef KR_DRAW_KEYS
   }
-  {
-    Carve sc = cv;  // scan scratch is transient
-    KR_TRY(kr_scan_u32(ctx, cnt, sk->cell_start, ncell, sc));
-  }
-  KR_LAUNCH(ctx, k_scatter, grid_for(ctx, s, 256), 256, 0, keys, rank, s, IT, sk->cell_start, slot);
-  const size_t dsmem = (size_t)DEDUP_WARPS * IT * sizeof(uint32_t);
-  KR_CUDA(ctx, cudaFuncSetAttribute(k_dedup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
-  KR_LAUNCH(ctx, k_dedup, grid_for(ctx, ncell, DEDUP_WARPS, 8), DEDUP_WARPS * 32, dsmem, sm, ncell, sk->ncell_inner,
-            sk->xI, sk->xPafter, IT, (float)(1.0 / (double)sk->s_row), sk->cell_start, cnt, slot, b, sk->ent, sk->bt,
-            sk->cell_nd, sk->cell_w);
-  // entries back to back in cell order (the draw-sized regions leave gaps)
+  int nbits = 0;
+  while (nbits < 32 && (uint64_t(1) << nbits) < (uint64_t)ncell * IT) ++nbits;
+  uint32_t* sorted = keys;
   {
     Carve sc = cv;
-    KR_TRY(kr_scan_u32(ctx, sk->cell_nd, cnt, ncell, sc));
+    KR_TRY(kr_radix_sort_u32(ctx, keys, alt, s, nbits, &sorted, sc));
   }
-  KR_LAUNCH(ctx, k_sum_u32, grid_for(ctx, ncell, 256, 2), 256, 0, sk->cell_nd, ncell, dsum);
-  KR_LAUNCH(ctx, k_compact, grid_for(ctx, ncell, 8, 8), 256, 0, ncell, sk->cell_start, cnt, sk->cell_nd, sk->ent,
-            sk->bt, keys, reinterpret_cast<float*>(rank));
-  KR_LAUNCH(ctx, k_copy_back, grid_for(ctx, s, 256), 256, 0, dsum, keys, reinterpret_cast<const float*>(rank), sk->ent,
-            sk->bt);
-  KR_CUDA(ctx, cudaMemcpyAsync(sk->cell_start, cnt, sizeof(uint32_t) * ncell, cudaMemcpyDeviceToDevice, ctx->stream));
+  uint32_t* dpos = (sorted == keys) ? alt : keys;
+  KR_LAUNCH(ctx, k_rle_heads, grid_for(ctx, s, 256), 256, 0, sorted, s, dpos);
+  {
+    Carve sc = cv;
+    KR_TRY(kr_scan_u32(ctx, dpos, dpos, s, sc));
+  }
+  KR_LAUNCH(ctx, k_rle_pos, grid_for(ctx, s, 256), 256, 0, sorted, dpos, s, hp, meta);
+  KR_LAUNCH(ctx, k_rle_count, grid_for(ctx, s, 256), 256, 0, hp, meta, s, mcnt);
+  {
+    Carve sc = cv;
+    KR_TRY(kr_scan_u32(ctx, mcnt, mcnt, s, sc));
+  }
+  KR_LAUNCH(ctx, k_rle_emit, grid_for(ctx, s, 256), 256, 0, sorted, hp, mcnt, meta, s, IT, (uint32_t)sk->ncell_inner,
+            sk->xI, sk->xPafter, b, sk->ent, sk->bt, sk->cell_nd, dsum);
+  {
+    Carve sc = cv;
+    KR_TRY(kr_scan_u32(ctx, sk->cell_nd, sk->cell_start, ncell, sc));
+  }
+  KR_LAUNCH(ctx, k_cell_w, grid_for(ctx, ncell, 256), 256, 0, sm, ncell, (uint32_t)sk->ncell_inner,
+            (float)(1.0 / (double)sk->s_row), sk->cell_w);
   if (sk->want_desc) {
     Carve sc = cv;
     KR_TRY(kr_balance_perm(ctx, sk->cell_nd, ncell, sk->perm, sc));
@@ -472,13 +477,19 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
 }
 
 void kr_sketch_scratch_need(int64_t s, int64_t ncell, Need& nd) {
-  nd.add<uint32_t>(s);
-  nd.add<uint32_t>(ncell);
-  nd.add<uint32_t>(s);
-  nd.add<uint16_t>(s);
+  nd.add<uint32_t>(s);      // keys
+  nd.add<uint32_t>(s);      // sort buffer / run index
+  nd.add<uint32_t>(s + 1);  // run starts
+  nd.add<uint32_t>(s);      // entries per run / entry positions
+  nd.add<uint32_t>(4);
   nd.add<unsigned long long>(1);
-  kr_scan_need(ncell, nd);
-  kr_perm_need(ncell, nd);
+  nd.add<uint16_t>((size_t)KR_MAX_MODES * GUIDE_MAX);
+  Need a, c;
+  kr_radix_need(s, a);
+  kr_scan_need(s, c);
+  kr_scan_need(ncell, c);
+  kr_perm_need(ncell, c);
+  nd.off += (a.off > c.off ? a.off : c.off) + 256;
 }
 
 // ------------------------------------------------------------------ C ABI
