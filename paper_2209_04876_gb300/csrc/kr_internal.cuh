@@ -252,9 +252,9 @@ void kr_tiles_scratch_need(const kr_tiles* tl, int64_t ncell, Need& nd);
 kr_status kr_tiles_build(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, Carve& cv);
 // One fused pass: Z[p] = sum over the sampled rows of slab p of
 //   A(N-2)[i]^T-weighted residual accumulations (see kr_slab.cu), from X1 (P x R2 x RT);
-// per-tile objective partials go to tl->objpart (tl->ntmax doubles).
+// with want_obj the per-tile objective partials go to tl->objpart (tl->ntmax doubles).
 kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const float* A2, const float* AT,
-                       const float* X1, float* Z);
+                       const float* X1, float* Z, bool want_obj);
 
 // ------------------------------------------------------------------ solvers
 

@@ -66,31 +66,66 @@ __global__ void k_gram_partial(ModePtrs mp) {
 }
 
 // Deterministic reduction of the partials (block order), mirrored to full symmetric.
+// One thread per upper-triangle entry; loads are issued in batches ahead of the sum.
 __global__ void k_gram_reduce(ModePtrs mp) {
-  const int n = blockIdx.x;
+  const int n = blockIdx.y;
   const int I = mp.I[n], R = mp.R[n];
   const int nchunk = (I + GRAM_ROWS - 1) / GRAM_ROWS;
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-    int i = e / R, j = e % R;
-    if (i > j) continue;
-    double acc = 0.0;
-    for (int c = 0; c < nchunk; ++c) acc += mp.part[n][(int64_t)c * R * R + e];
-    mp.gram[n][i * R + j] = acc;
-    mp.gram[n][j * R + i] = acc;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= R * R) return;
+  const int i = e / R, j = e % R;
+  if (i > j) return;
+  const double* part = mp.part[n] + e;
+  double acc = 0.0;
+  for (int c0 = 0; c0 < nchunk; c0 += 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (c0 + u < nchunk) ? part[(int64_t)(c0 + u) * R * R] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (c0 + u < nchunk) acc += v[u];
   }
+  mp.gram[n][i * R + j] = acc;
+  mp.gram[n][j * R + i] = acc;
+}
+
+// 1/sqrt(d) for d > 0 in FP64: an FP32 estimate of the reduced argument refined by two
+// Newton steps y <- y (3 - d y^2) / 2 (each doubles the correct bits: 24 -> 48 -> 96, so
+// the result is within an ulp or two). FP64 square root and division are long dependent
+// sequences on this part; the Newton form keeps the pivot chain of the Cholesky short.
+__device__ __forceinline__ double rsqrt_fp64(double d) {
+  const int e = (int)((__double_as_longlong(d) >> 52) & 0x7FF) - 1023;
+  if (e < -1000 || e > 1000) return 1.0 / sqrt(d);
+  const int h = e >> 1;  // d = m * 4^h with m in [1, 4)
+  const double m = d * __longlong_as_double((long long)(1023 - 2 * h) << 52);
+  double y = (double)rsqrtf((float)m) * __longlong_as_double((long long)(1023 - h) << 52);
+  const double hd = 0.5 * d;
+  y = y * fma(-hd, y * y, 1.5);
+  y = y * fma(-hd, y * y, 1.5);
+  return y;
 }
 
 // One block per mode: Cholesky G = L L^T (FP64), L^-1, and (A^T A)^-1 in FP32.
+// L^-1 by block doubling: with L padded to RP = 2^k rows by the identity, every level
+// turns inverted diagonal blocks of size bs into inverted blocks of size 2 bs through
+// [A 0; C D]^-1 = [A^-1 0; -D^-1 C A^-1, D^-1] (two bs x bs products per level).
 __global__ void k_cholesky(ModePtrs mp) {
   const int n = blockIdx.x;
   const int R = mp.R[n];
+  int RP = 1;
+  while (RP < R) RP <<= 1;
   extern __shared__ double sm[];
-  double* L = sm;              // R x LD
-  double* X = sm + MAXR * LD;  // R x LD (L^-1)
+  double* L = sm;                  // RP x LD
+  double* X = sm + MAXR * LD;      // RP x LD (L^-1)
+  double* S = sm + 2 * MAXR * LD;  // RP x LD (scratch products)
   __shared__ int bad;
   __shared__ double maxdiag;
+  __shared__ double pinv;
   const int tid = threadIdx.x;
-  for (int e = tid; e < R * R; e += blockDim.x) L[(e / R) * LD + (e % R)] = mp.gram[n][e];
+  for (int e = tid; e < RP * RP; e += blockDim.x) {
+    const int i = e / RP, j = e % RP;
+    L[i * LD + j] = (i < R && j < R) ? mp.gram[n][i * R + j] : (i == j ? 1.0 : 0.0);
+  }
   if (tid == 0) {
     bad = 0;
     double md = 0.0;
@@ -100,35 +135,68 @@ __global__ void k_cholesky(ModePtrs mp) {
   __syncthreads();
   const double tol = maxdiag * (double)R * 1e-15;
   for (int k = 0; k < R; ++k) {
-    __syncthreads();  // trailing update of step k-1 complete
-    double d = L[k * LD + k];
-    __syncthreads();  // every thread has read the pivot before it is overwritten
-    if (!(d > tol)) {  // also catches NaN
-      if (tid == 0) bad = 1;
-      d = 1.0;
+    if (tid == 0) {  // the pivot: one reciprocal square root per step
+      double d = L[k * LD + k];
+      if (!(d > tol)) {  // also catches NaN
+        bad = 1;
+        d = 1.0;
+      }
+      const double y = rsqrt_fp64(d);
+      L[k * LD + k] = d * y;
+      pinv = y;
     }
-    double lkk = sqrt(d);
-    if (tid == 0) L[k * LD + k] = lkk;
-    for (int i = k + 1 + tid; i < R; i += blockDim.x) L[i * LD + k] = L[i * LD + k] / lkk;
     __syncthreads();
-    int m = R - k - 1;
+    const double inv = pinv;
+    for (int i = k + 1 + tid; i < R; i += blockDim.x) L[i * LD + k] *= inv;
+    __syncthreads();
+    const int m = R - k - 1;
     for (int e = tid; e < m * m; e += blockDim.x) {
-      int i = k + 1 + e / m, j = k + 1 + e % m;
+      const int i = k + 1 + e / m, j = k + 1 + e % m;
       if (j <= i) L[i * LD + j] = fma(-L[i * LD + k], L[j * LD + k], L[i * LD + j]);
     }
+    __syncthreads();
+  }
+  // L^-1: diagonal blocks of size 1, then doubling
+  for (int e = tid; e < RP * RP; e += blockDim.x) {
+    const int i = e / RP, j = e % RP;
+    X[i * LD + j] = (i == j) ? 1.0 / L[i * LD + i] : 0.0;
   }
   __syncthreads();
-  // L^-1 by forward substitution, one column per thread.
-  for (int j = tid; j < R; j += blockDim.x) {
-    for (int i = 0; i < j; ++i) X[i * LD + j] = 0.0;
-    X[j * LD + j] = 1.0 / L[j * LD + j];
-    for (int i = j + 1; i < R; ++i) {
-      double acc = 0.0;
-      for (int k = j; k < i; ++k) acc = fma(L[i * LD + k], X[k * LD + j], acc);
-      X[i * LD + j] = -acc / L[i * LD + i];
+  for (int bs = 1; bs < RP; bs <<= 1) {
+    const int per = bs * bs, npair = RP / (2 * bs);
+    // S[B, A] = L[B, A] X[A, A]
+    for (int e = tid; e < npair * per; e += blockDim.x) {
+      const int pr = e / per, rc = e - pr * per, r = rc / bs, c = rc - r * bs;
+      const int a0 = pr * 2 * bs, b0 = a0 + bs;
+      double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+      int t = c;  // X[A, A] is lower triangular: rows t >= c
+      for (; t + 3 < bs; t += 4) {
+        p0 = fma(L[(b0 + r) * LD + a0 + t], X[(a0 + t) * LD + a0 + c], p0);
+        p1 = fma(L[(b0 + r) * LD + a0 + t + 1], X[(a0 + t + 1) * LD + a0 + c], p1);
+        p2 = fma(L[(b0 + r) * LD + a0 + t + 2], X[(a0 + t + 2) * LD + a0 + c], p2);
+        p3 = fma(L[(b0 + r) * LD + a0 + t + 3], X[(a0 + t + 3) * LD + a0 + c], p3);
+      }
+      for (; t < bs; ++t) p0 = fma(L[(b0 + r) * LD + a0 + t], X[(a0 + t) * LD + a0 + c], p0);
+      S[(b0 + r) * LD + a0 + c] = (p0 + p1) + (p2 + p3);
     }
+    __syncthreads();
+    // X[B, A] = -X[B, B] S[B, A]
+    for (int e = tid; e < npair * per; e += blockDim.x) {
+      const int pr = e / per, rc = e - pr * per, r = rc / bs, c = rc - r * bs;
+      const int a0 = pr * 2 * bs, b0 = a0 + bs;
+      double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+      int t = 0;  // X[B, B] is lower triangular: columns t <= r
+      for (; t + 3 <= r; t += 4) {
+        p0 = fma(X[(b0 + r) * LD + b0 + t], S[(b0 + t) * LD + a0 + c], p0);
+        p1 = fma(X[(b0 + r) * LD + b0 + t + 1], S[(b0 + t + 1) * LD + a0 + c], p1);
+        p2 = fma(X[(b0 + r) * LD + b0 + t + 2], S[(b0 + t + 2) * LD + a0 + c], p2);
+        p3 = fma(X[(b0 + r) * LD + b0 + t + 3], S[(b0 + t + 3) * LD + a0 + c], p3);
+      }
+      for (; t <= r; ++t) p0 = fma(X[(b0 + r) * LD + b0 + t], S[(b0 + t) * LD + a0 + c], p0);
+      X[(b0 + r) * LD + a0 + c] = -((p0 + p1) + (p2 + p3));
+    }
+    __syncthreads();
   }
-  __syncthreads();
   for (int e = tid; e < R * R; e += blockDim.x) mp.linv[n][e] = X[(e / R) * LD + (e % R)];
   // (A^T A)^-1 = X^T X in FP32 (a preconditioner only needs a spectral approximation).
   for (int e = tid; e < R * R; e += blockDim.x) {
@@ -141,58 +209,92 @@ __global__ void k_cholesky(ModePtrs mp) {
   if (tid == 0) mp.flags[n] = bad;
 }
 
-// l_i = ||L^-1 a_i||^2 in FP64, 64 rows per block.
-__global__ void k_leverage(ModePtrs mp) {
+// l_i = ||L^-1 a_i||^2 in FP64: LEV_ROWS rows per block, one warp per row, a lane per
+// component of L^-1 a_i, the squares summed over the warp in a fixed tree order.
+constexpr int LEV_ROWS = 8;
+__global__ void __launch_bounds__(LEV_ROWS * 32) k_leverage(ModePtrs mp) {
   const int n = blockIdx.y;
   const int I = mp.I[n], R = mp.R[n];
-  const int r0 = blockIdx.x * 64;
+  const int r0 = blockIdx.x * LEV_ROWS;
   if (r0 >= I) return;
   extern __shared__ double sm[];
   double* X = sm;              // R x LD
-  double* a = sm + MAXR * LD;  // 64 x LD
-  const int rows = min(64, I - r0);
+  double* a = sm + MAXR * LD;  // LEV_ROWS x LD
+  const int rows = min(LEV_ROWS, I - r0);
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) X[(e / R) * LD + (e % R)] = mp.linv[n][e];
   for (int e = threadIdx.x; e < rows * R; e += blockDim.x)
     a[(e / R) * LD + (e % R)] = (double)mp.A[n][(int64_t)(r0 + e / R) * R + (e % R)];
   __syncthreads();
-  int t = threadIdx.x;
-  if (t < rows) {
-    double acc = 0.0;
-    for (int k = 0; k < R; ++k) {
-      double v = 0.0;
-      for (int m = 0; m <= k; ++m) v = fma(X[k * LD + m], a[t * LD + m], v);
-      acc = fma(v, v, acc);
-    }
-    mp.lev[n][r0 + t] = acc;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w >= rows) return;
+  double acc = 0.0;
+  for (int k = lane; k < R; k += 32) {
+    double v = 0.0;
+    for (int m = 0; m <= k; ++m) v = fma(X[k * LD + m], a[w * LD + m], v);
+    acc = fma(v, v, acc);
   }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) mp.lev[n][r0 + w] = acc;
 }
 
-// One block per mode: left-to-right FP64 prefix, normalised CDF, integer thresholds,
-// probabilities and FP32 inverse probabilities.
-__global__ void k_cdf(ModePtrs mp) {
+// One block per mode: left-to-right FP64 prefix of the scores (the convention of the
+// sampling tables), normalised CDF, integer thresholds, probabilities and FP32 inverse
+// probabilities. The prefix is one dependent chain of additions: the scores are staged in
+// shared memory and one thread adds them from registers in batches, so the chain holds
+// nothing but the additions; the index of the last positive score is a parallel max.
+constexpr int CDF_THREADS = 256;
+constexpr int CDF_CHUNK = 4096;
+__global__ void __launch_bounds__(CDF_THREADS) k_cdf(ModePtrs mp) {
   const int n = blockIdx.x;
   const int I = mp.I[n];
   double* cdf = mp.cdf[n];
   const double* lev = mp.lev[n];
+  __shared__ double chunk[CDF_CHUNK];
   __shared__ double total;
   __shared__ int last;
-  if (threadIdx.x == 0) {
-    double acc = 0.0;
+  if (threadIdx.x == 0) last = -1;
+  __syncthreads();
+  {
     int lp = -1;
-    for (int i = 0; i < I; ++i) {
-      double l = lev[i];
-      acc = __dadd_rn(acc, l);
-      cdf[i] = acc;
-      if (l > 0.0) lp = i;
-    }
-    total = acc;
-    last = lp;
+    for (int i = threadIdx.x; i < I; i += blockDim.x)
+      if (lev[i] > 0.0) lp = i;
+    if (lp >= 0) atomicMax(&last, lp);
   }
+  double acc = 0.0;  // thread 0 only
+  for (int c0 = 0; c0 < I; c0 += CDF_CHUNK) {
+    const int cn = min(CDF_CHUNK, I - c0);
+    for (int i = threadIdx.x; i < cn; i += blockDim.x) chunk[i] = lev[c0 + i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int i = 0;
+      for (; i + 16 <= cn; i += 16) {
+        double v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) v[u] = chunk[i + u];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          acc = __dadd_rn(acc, v[u]);
+          v[u] = acc;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) chunk[i + u] = v[u];
+      }
+      for (; i < cn; ++i) {
+        acc = __dadd_rn(acc, chunk[i]);
+        chunk[i] = acc;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cn; i += blockDim.x) cdf[c0 + i] = chunk[i];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) total = acc;
   __syncthreads();
   const double T = total;
-  const int lp = last;
+  const int lpos = last;
   for (int i = threadIdx.x; i < I; i += blockDim.x) {
-    double c = (lp >= 0 && i >= lp) ? 1.0 : __ddiv_rn(cdf[i], T);
+    double c = (lpos >= 0 && i >= lpos) ? 1.0 : __ddiv_rn(cdf[i], T);
     cdf[i] = c;
     double l = lev[i];
     mp.prob[n][i] = __ddiv_rn(l, T);
@@ -331,19 +433,21 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
   mp.flags = cv.take<int>(KR_MAX_MODES);
   if (cv.off > cv.cap) return kr_fail(ctx, KR_ENOMEM, "tables: workspace too small");
 
-  const size_t chol_smem = 2 * MAXR * LD * sizeof(double);
-  const size_t lev_smem = (MAXR * LD + 64 * LD) * sizeof(double);
+  const size_t chol_smem = 3 * MAXR * LD * sizeof(double);
+  const size_t lev_smem = (MAXR * LD + LEV_ROWS * LD) * sizeof(double);
   const size_t jac_smem = 2 * (MAXR + 1) * LD * sizeof(float);
   KR_CUDA(ctx, cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem));
   KR_CUDA(ctx, cudaFuncSetAttribute(k_leverage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lev_smem));
   KR_CUDA(ctx, cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jac_smem));
   dim3 gg((maxI + GRAM_ROWS - 1) / GRAM_ROWS, m.N);
   KR_LAUNCH(ctx, k_gram_partial, gg, 256, 0, mp);
-  KR_LAUNCH(ctx, k_gram_reduce, m.N, 256, 0, mp);
+  int maxR = 0;
+  for (int n = 0; n < m.N; ++n) maxR = m.R[n] > maxR ? m.R[n] : maxR;
+  KR_LAUNCH(ctx, k_gram_reduce, dim3((maxR * maxR + 255) / 256, m.N), 256, 0, mp);
   KR_LAUNCH(ctx, k_cholesky, m.N, 256, chol_smem, mp);
-  dim3 gl((maxI + 63) / 64, m.N);
-  KR_LAUNCH(ctx, k_leverage, gl, 64, lev_smem, mp);
-  KR_LAUNCH(ctx, k_cdf, m.N, 256, 0, mp);
+  dim3 gl((maxI + LEV_ROWS - 1) / LEV_ROWS, m.N);
+  KR_LAUNCH(ctx, k_leverage, gl, LEV_ROWS * 32, lev_smem, mp);
+  KR_LAUNCH(ctx, k_cdf, m.N, CDF_THREADS, 0, mp);
   if (want_eig) KR_LAUNCH(ctx, k_jacobi, m.N, 256, jac_smem, mp);
   if (check_rank) {
     KR_TRY(kr_hbuf_reserve(ctx, 4096));

@@ -65,6 +65,7 @@ struct SlabArgs {
   int IT, RT, I2, R2, R2P, R2S;
   int64_t P;
   int a2vec, atvec;
+  int want_obj;  // per-tile objective partials (only the final pass of a solve reads them)
   // shared-memory layout (bytes)
   uint32_t team_off, team_bytes, o_a2, o_x1, o_pf, o_act, o_cs, o_ctl;
 };
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
         reinterpret_cast<float4*>(dst)[qd[v]] = make_float4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
     }
     if (has) objt += (double)objc;
-    {  // objective of the tile: one lane per group
+    if (a.want_obj) {  // objective of the tile: one lane per group
       double ov = (g == 0 && has) ? objt : 0.0;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) ov += __shfl_xor_sync(0xffffffffu, ov, off);
@@ -411,7 +412,7 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
       for (int v = 0; v < NQ; ++v)
         reinterpret_cast<float4*>(sYW + k * RTP)[qd[v]] = make_float4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
     }
-    if (tt == 0) {
+    if (tt == 0 && a.want_obj) {
       double s = 0.0;
       for (int i = 0; i < SLAB_TEAM / 32; ++i) s += sRed[i];
       a.objpart[t] = s;
@@ -741,7 +742,7 @@ kr_status kr_tiles_build(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, Carve& 
 }
 
 kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const float* A2, const float* AT,
-                       const float* X1, float* Z) {
+                       const float* X1, float* Z, bool want_obj) {
   SlabLayout L = slab_layout(tl->IT, tl->RT, tl->R2, true);
   if (L.bytes > ctx->smem_optin) L = slab_layout(tl->IT, tl->RT, tl->R2, false);
   if (L.bytes > ctx->smem_optin) return kr_fail(ctx, KR_ENOTIMPL, "slab pass: %zu bytes of shared memory", L.bytes);
@@ -768,6 +769,7 @@ kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const flo
   a.P = tl->P;
   a.a2vec = (tl->R2 % 4 == 0) && ((reinterpret_cast<uintptr_t>(A2) & 15) == 0);
   a.atvec = (tl->RT % 4 == 0) && ((reinterpret_cast<uintptr_t>(AT) & 15) == 0);
+  a.want_obj = want_obj ? 1 : 0;
   a.team_off = L.team_off;
   a.team_bytes = L.team_bytes;
   a.o_a2 = L.o_a2;

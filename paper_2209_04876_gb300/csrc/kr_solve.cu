@@ -252,12 +252,45 @@ __global__ void k_update(float* __restrict__ x, const float* __restrict__ d, flo
   }
 }
 
-// x <- x + alpha d, then {||alpha d||^2, ||x||^2, non-finite flag} reduced in FP64 into
-// out[0..2]: block partials first, then the last block to finish sums them in block order
-// (deterministic) and re-arms the ticket counter.
+// {||step||^2, ||x||^2, non-finite flag} of the block's elements in FP64, as fixed-order
+// trees (warp shuffles, then one warp over the warp partials), written to
+// part[3 * blockIdx.x + 0..2]; the host adds the blocks' partials in block order. Called
+// by all threads of a block of at most 1024 threads, once per kernel.
+__device__ __forceinline__ void step_norms_block(double s1, double s2, double bad, double* __restrict__ part) {
+  __shared__ double red[3][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+    bad = fmax(bad, __shfl_xor_sync(0xffffffffu, bad, off));
+  }
+  if (lane == 0) {
+    red[0][w] = s1;
+    red[1][w] = s2;
+    red[2][w] = bad;
+  }
+  __syncthreads();
+  if (w == 0) {
+    double a = lane < nw ? red[0][lane] : 0.0, b = lane < nw ? red[1][lane] : 0.0,
+           c = lane < nw ? red[2][lane] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, off);
+      b += __shfl_xor_sync(0xffffffffu, b, off);
+      c = fmax(c, __shfl_xor_sync(0xffffffffu, c, off));
+    }
+    if (lane == 0) {
+      part[3 * blockIdx.x + 0] = a;
+      part[3 * blockIdx.x + 1] = b;
+      part[3 * blockIdx.x + 2] = c;
+    }
+  }
+}
+
+// x <- x + alpha d, with the step norms (step_norms_block).
 __global__ void __launch_bounds__(256) k_update_reduce(float* __restrict__ x, const float* __restrict__ d, float alpha,
-                                                       int64_t n, double* __restrict__ part,
-                                                       unsigned int* __restrict__ ticket, double* __restrict__ out) {
+                                                       int64_t n, double* __restrict__ part) {
   double s1 = 0.0, s2 = 0.0, bad = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float st = alpha * d[i];
@@ -267,62 +300,289 @@ __global__ void __launch_bounds__(256) k_update_reduce(float* __restrict__ x, co
     s2 += (double)xn * xn;
     if (!isfinite(xn)) bad = 1.0;
   }
-  __shared__ double red[3][8];
-  __shared__ double fin[3][256];
-  __shared__ bool last;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
-    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-    bad = fmax(bad, __shfl_xor_sync(0xffffffffu, bad, off));
+  step_norms_block(s1, s2, bad, part);
+}
+
+// ------------------------------------------------------------------ preconditioned step, fused
+
+// The preconditioner of Alg. 2 is a Kronecker product, M+ = B_1 (x) ... (x) B_N
+// (B_n = G_n^-1 for lambda = 0; V_n^T, a diagonal, V_n for lambda > 0), so
+// d = M+ (g - lambda x) splits into the first mode (mixing the R_1 slabs of the iterate)
+// and the other modes (inside one slab of Q = R / R_1 entries). k_pc_mode0 applies the
+// first-mode matrix, optionally forming g - lambda x on the way in and the update
+// x <- x + alpha d with its norms on the way out; k_pc_slab applies the other modes to one
+// slab in shared memory (for lambda > 0: V^T, the diagonal, then V), optionally with the
+// update.
+struct PcModes {
+  int N;
+  int R[KR_MAX_MODES];
+  const float* B[KR_MAX_MODES];   // per mode: R x R
+  const float* B2[KR_MAX_MODES];  // lambda > 0: V applied after the diagonal
+  const float* sig2[KR_MAX_MODES];
+  int trans;                      // B applied transposed (V^T)
+  float lambda;
+};
+
+// out[j, q] = sum_k B0'[j, k] (in[k, q] - lambda xl[k, q]); B0' = B0 or B0^T. A block
+// takes a panel of PC_TQ columns q: the panel of the input and B0 are staged in shared
+// memory. With x != nullptr the result is the step: x <- x + alpha out, norms reduced.
+constexpr int PC_TQ = 32;
+__global__ void __launch_bounds__(256) k_pc_mode0(const float* __restrict__ in, const float* __restrict__ xl,
+                                                  float lambda, const float* __restrict__ B0, int trans, int R0,
+                                                  int Q, float* __restrict__ out, float* __restrict__ x,
+                                                  float alpha, double* __restrict__ part) {
+  __shared__ float sB[KR_MAX_RANK * KR_MAX_RANK];
+  __shared__ float sIn[KR_MAX_RANK * PC_TQ];
+  for (int e = threadIdx.x; e < R0 * R0; e += blockDim.x) {
+    const int j = e / R0, k = e - j * R0;
+    sB[e] = trans ? __ldg(B0 + k * R0 + j) : __ldg(B0 + e);  // sB[j * R0 + k] = B0'[j, k]
   }
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = s1;
-    red[1][threadIdx.x >> 5] = s2;
-    red[2][threadIdx.x >> 5] = bad;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0, b = 0, c = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-      a += red[0][k];
-      b += red[1][k];
-      c = fmax(c, red[2][k]);
-    }
-    part[3 * blockIdx.x + 0] = a;
-    part[3 * blockIdx.x + 1] = b;
-    part[3 * blockIdx.x + 2] = c;
-    __threadfence();
-    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (last) {  // the last block: fixed strided sums, then a fixed-order tree
-    __threadfence();
-    double a = 0, b = 0, c = 0;
-    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
-      a += part[3 * k + 0];
-      b += part[3 * k + 1];
-      c = fmax(c, part[3 * k + 2]);
-    }
-    fin[0][threadIdx.x] = a;
-    fin[1][threadIdx.x] = b;
-    fin[2][threadIdx.x] = c;
+  double s1 = 0.0, s2 = 0.0, bad = 0.0;
+  for (int q0 = blockIdx.x * PC_TQ; q0 < Q; q0 += gridDim.x * PC_TQ) {
+    const int tq = min(PC_TQ, Q - q0);
     __syncthreads();
-    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-      if ((int)threadIdx.x < off) {
-        fin[0][threadIdx.x] += fin[0][threadIdx.x + off];
-        fin[1][threadIdx.x] += fin[1][threadIdx.x + off];
-        fin[2][threadIdx.x] = fmax(fin[2][threadIdx.x], fin[2][threadIdx.x + off]);
+    for (int e = threadIdx.x; e < R0 * PC_TQ; e += blockDim.x) {
+      const int k = e / PC_TQ, c = e - k * PC_TQ;
+      float v = 0.f;
+      if (c < tq) {
+        const int64_t gi = (int64_t)k * Q + q0 + c;
+        v = __ldg(in + gi);
+        if (xl) v = fmaf(-lambda, __ldg(xl + gi), v);
+      }
+      sIn[e] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < R0 * PC_TQ; e += blockDim.x) {
+      const int j = e / PC_TQ, c = e - j * PC_TQ;
+      if (c >= tq) continue;
+      const float* brow = sB + j * R0;
+      float acc = 0.f;
+      for (int k = 0; k < R0; ++k) acc = fmaf(brow[k], sIn[k * PC_TQ + c], acc);
+      const int64_t gi = (int64_t)j * Q + q0 + c;
+      if (x) {
+        const float st = alpha * acc;
+        const float xn = x[gi] + st;
+        x[gi] = xn;
+        s1 += (double)st * st;
+        s2 += (double)xn * xn;
+        if (!isfinite(xn)) bad = 1.0;
+      } else {
+        out[gi] = acc;
+      }
+    }
+  }
+  if (x) step_norms_block(s1, s2, bad, part);
+}
+
+// In shared memory: t (R_1 x ... x R_{N-1}) <- B applied along every mode of the slab
+// (B staged in sB transposed: mode m at offset boff[m], entry (k, j) = B'[j, k], so lanes
+// with consecutive output rows j read consecutive words, and lanes sharing j broadcast).
+__device__ void pc_slab_modes(const PcModes& pm, const float* sB, const int* boff, float* t, float* u, int Q) {
+  float* src = t;
+  float* dst = u;
+  int P = 1;
+  for (int m = 1; m < pm.N; ++m) {
+    const int Rm = pm.R[m];
+    const int Qm = Q / P / Rm;  // entries after mode m
+    const float* Bm = sB + boff[m];
+    for (int e = threadIdx.x; e < Q; e += blockDim.x) {
+      const int p = e / (Rm * Qm);
+      const int rest = e - p * Rm * Qm;
+      const int jj = rest / Qm;
+      const int qq = rest - jj * Qm;
+      const float* col = src + p * Rm * Qm + qq;
+      const float* bcol = Bm + jj;
+      float acc = 0.f;
+      for (int k = 0; k < Rm; ++k) acc = fmaf(bcol[k * Rm], col[k * Qm], acc);
+      dst[e] = acc;
+    }
+    __syncthreads();
+    float* tmp = src;
+    src = dst;
+    dst = tmp;
+    P *= Rm;
+  }
+  if (src != t) {
+    for (int e = threadIdx.x; e < Q; e += blockDim.x) t[e] = src[e];
+    __syncthreads();
+  }
+}
+
+// The whole step in one kernel when the iterate fits in shared memory: block j stages
+// in - lambda xl (all R_1 x Q entries), forms slab j of the first-mode product from row j
+// of B0', applies the other modes (rest != 0; for lambda > 0 also the diagonal and the
+// second set), then writes out[j] or takes the step (x != nullptr) with its norms.
+__global__ void __launch_bounds__(1024) k_pc_fused(PcModes pm, const float* __restrict__ in,
+                                                   const float* __restrict__ xl, float lambda,
+                                                   const float* __restrict__ B0, int trans0, int rest, int R0, int Q,
+                                                   float* __restrict__ out, float* __restrict__ x, float alpha,
+                                                   double* __restrict__ part) {
+  extern __shared__ float pc_smem[];
+  float* full = pc_smem;          // R0 x Q
+  float* t = full + (size_t)R0 * Q;
+  float* u = t + Q;
+  float* b0 = u + Q;              // row j of B0'
+  float* sB = b0 + KR_MAX_RANK;   // other modes, transposed (as in k_pc_slab)
+  const int j = blockIdx.x;
+  int boff[KR_MAX_MODES], boff2[KR_MAX_MODES];
+  int off = 0;
+  if (rest) {
+    for (int m = 1; m < pm.N; ++m) {
+      const int Rm = pm.R[m];
+      boff[m] = off;
+      for (int e = threadIdx.x; e < Rm * Rm; e += blockDim.x) {
+        const int k = e / Rm, jj = e - k * Rm;
+        sB[off + e] = pm.trans ? __ldg(pm.B[m] + k * Rm + jj) : __ldg(pm.B[m] + jj * Rm + k);
+      }
+      off += Rm * Rm;
+    }
+    if (pm.lambda > 0.f) {
+      for (int m = 1; m < pm.N; ++m) {
+        const int Rm = pm.R[m];
+        boff2[m] = off;
+        for (int e = threadIdx.x; e < Rm * Rm; e += blockDim.x) {
+          const int k = e / Rm, jj = e - k * Rm;
+          sB[off + e] = __ldg(pm.B2[m] + jj * Rm + k);
+        }
+        off += Rm * Rm;
+      }
+    }
+  }
+  for (int k = threadIdx.x; k < R0; k += blockDim.x) b0[k] = trans0 ? __ldg(B0 + k * R0 + j) : __ldg(B0 + j * R0 + k);
+  const int64_t tot = (int64_t)R0 * Q;
+  if ((Q & 3) == 0) {
+    const float4* in4 = reinterpret_cast<const float4*>(in);
+    const float4* xl4 = reinterpret_cast<const float4*>(xl);
+    float4* f4 = reinterpret_cast<float4*>(full);
+#pragma unroll 8
+    for (int64_t e = threadIdx.x; e < tot / 4; e += blockDim.x) {
+      float4 v = __ldg(in4 + e);
+      if (xl) {
+        const float4 w = __ldg(xl4 + e);
+        v.x = fmaf(-lambda, w.x, v.x);
+        v.y = fmaf(-lambda, w.y, v.y);
+        v.z = fmaf(-lambda, w.z, v.z);
+        v.w = fmaf(-lambda, w.w, v.w);
+      }
+      f4[e] = v;
+    }
+  } else {
+    for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+      float v = __ldg(in + e);
+      if (xl) v = fmaf(-lambda, __ldg(xl + e), v);
+      full[e] = v;
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+    float acc = 0.f;
+    for (int k = 0; k < R0; ++k) acc = fmaf(b0[k], full[(int64_t)k * Q + q], acc);
+    t[q] = acc;
+  }
+  __syncthreads();
+  if (rest) {
+    pc_slab_modes(pm, sB, boff, t, u, Q);
+    if (pm.lambda > 0.f) {
+      const float s0 = pm.sig2[0][j];
+      for (int e = threadIdx.x; e < Q; e += blockDim.x) {
+        int rem = e;
+        float prod = 1.f;
+        for (int m = pm.N - 1; m >= 1; --m) {
+          const int q = rem / pm.R[m];
+          prod *= pm.sig2[m][rem - q * pm.R[m]];
+          rem = q;
+        }
+        prod *= s0;
+        const float dv = prod + pm.lambda;
+        t[e] = dv > 0.f ? t[e] / dv : 0.f;
       }
       __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      out[0] = fin[0][0];
-      out[1] = fin[1][0];
-      out[2] = fin[2][0];
-      *ticket = 0u;
+      pc_slab_modes(pm, sB, boff2, t, u, Q);
     }
   }
+  double s1 = 0.0, s2 = 0.0, bad = 0.0;
+  for (int e = threadIdx.x; e < Q; e += blockDim.x) {
+    if (x) {
+      const float st = alpha * t[e];
+      const float xn = x[(int64_t)j * Q + e] + st;
+      x[(int64_t)j * Q + e] = xn;
+      s1 += (double)st * st;
+      s2 += (double)xn * xn;
+      if (!isfinite(xn)) bad = 1.0;
+    } else {
+      out[(int64_t)j * Q + e] = t[e];
+    }
+  }
+  if (x) step_norms_block(s1, s2, bad, part);
+}
+
+// One block per slab j of the first mode: the other modes (and, for lambda > 0, the
+// diagonal and the second set of modes); with x != nullptr the step and its norms.
+// Shared memory: the slab twice, then the matrices of modes 1..N-1 (both sets).
+__global__ void __launch_bounds__(1024) k_pc_slab(PcModes pm, const float* __restrict__ in, int Q,
+                                                  float* __restrict__ out, float* __restrict__ x, float alpha,
+                                                  double* __restrict__ part) {
+  extern __shared__ float pc_smem[];
+  float* t = pc_smem;
+  float* u = pc_smem + Q;
+  float* sB = pc_smem + 2 * Q;
+  int boff[KR_MAX_MODES], boff2[KR_MAX_MODES];
+  int off = 0;
+  for (int m = 1; m < pm.N; ++m) {
+    const int Rm = pm.R[m];
+    boff[m] = off;
+    for (int e = threadIdx.x; e < Rm * Rm; e += blockDim.x) {  // e = k * Rm + j
+      const int k = e / Rm, j = e - k * Rm;
+      sB[off + e] = pm.trans ? __ldg(pm.B[m] + k * Rm + j) : __ldg(pm.B[m] + j * Rm + k);
+    }
+    off += Rm * Rm;
+  }
+  if (pm.lambda > 0.f) {
+    for (int m = 1; m < pm.N; ++m) {
+      const int Rm = pm.R[m];
+      boff2[m] = off;
+      for (int e = threadIdx.x; e < Rm * Rm; e += blockDim.x) {
+        const int k = e / Rm, j = e - k * Rm;
+        sB[off + e] = __ldg(pm.B2[m] + j * Rm + k);
+      }
+      off += Rm * Rm;
+    }
+  }
+  const int j = blockIdx.x;
+  for (int e = threadIdx.x; e < Q; e += blockDim.x) t[e] = in[(int64_t)j * Q + e];
+  __syncthreads();
+  pc_slab_modes(pm, sB, boff, t, u, Q);
+  if (pm.lambda > 0.f) {
+    const float s0 = pm.sig2[0][j];
+    for (int e = threadIdx.x; e < Q; e += blockDim.x) {
+      int rem = e;
+      float prod = 1.f;
+      for (int m = pm.N - 1; m >= 1; --m) {
+        const int q = rem / pm.R[m];
+        prod *= pm.sig2[m][rem - q * pm.R[m]];
+        rem = q;
+      }
+      prod *= s0;
+      const float dv = prod + pm.lambda;
+      t[e] = dv > 0.f ? t[e] / dv : 0.f;
+    }
+    __syncthreads();
+    pc_slab_modes(pm, sB, boff2, t, u, Q);
+  }
+  double s1 = 0.0, s2 = 0.0, bad = 0.0;
+  for (int e = threadIdx.x; e < Q; e += blockDim.x) {
+    if (x) {
+      const float st = alpha * t[e];
+      const float xn = x[(int64_t)j * Q + e] + st;
+      x[(int64_t)j * Q + e] = xn;
+      s1 += (double)st * st;
+      s2 += (double)xn * xn;
+      if (!isfinite(xn)) bad = 1.0;
+    } else {
+      out[(int64_t)j * Q + e] = t[e];
+    }
+  }
+  if (x) step_norms_block(s1, s2, bad, part);
 }
 
 // Deterministic sum of per-block partials: out[k] = sum_b part[stride*b + k] (k < stride),
@@ -544,6 +804,93 @@ kr_status backward(kr_ctx* ctx, const Modes& m, const IterBufs& bf) {
   return kr_kron_apply2(ctx, N, din, dout, B, tr, bf.W, bf.g, bf.t0, bf.t1);
 }
 
+// Whether `func` can run with `dyn` bytes of dynamic shared memory next to its static
+// shared memory; if so the kernel's dynamic limit is raised to at least `dyn`.
+template <class F>
+kr_status smem_fit(kr_ctx* ctx, F func, size_t dyn, bool* fits) {
+  cudaFuncAttributes fa;
+  KR_CUDA(ctx, cudaFuncGetAttributes(&fa, func));
+  *fits = dyn + fa.sharedSizeBytes <= ctx->smem_optin;
+  if (*fits && dyn > (size_t)fa.maxDynamicSharedSizeBytes)
+    KR_CUDA(ctx, cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  return KR_OK;
+}
+
+// One preconditioned Richardson step, x <- x + alpha M+ (g - lambda x); the last kernel
+// writes the FP64 partials {||alpha d||^2, ||x||^2, non-finite flag} of its *nparts
+// blocks to part (the caller adds them in block order). One kernel when the iterate fits
+// in shared memory (two for lambda > 0), else the first mode and the slabs' other modes
+// as two (three), else the per-mode sequence. tmp0..tmp2: R floats.
+kr_status pc_step(kr_ctx* ctx, const FactorTables& t, double lambda, float* g, float* x, float alpha, float* tmp0,
+                  float* tmp1, float* tmp2, int ublk, double* part, int* nparts) {
+  const int N = t.N;
+  int64_t R = 1;
+  for (int n = 0; n < N; ++n) R *= t.R[n];
+  const int R0 = t.R[0];
+  const int64_t Q = R / R0;
+  size_t nb = 0;
+  for (int n = 1; n < N; ++n) nb += (size_t)t.R[n] * t.R[n];
+  if (lambda > 0.0) nb *= 2;
+  const size_t smem = (2 * (size_t)Q + nb) * sizeof(float);
+  bool split = false;
+  if (Q <= (int64_t(1) << 20)) KR_TRY(smem_fit(ctx, k_pc_slab, smem, &split));
+  if (!split) {
+    if (lambda > 0.0) KR_LAUNCH(ctx, k_sub_lambda_x, ublk, 256, 0, g, x, (float)lambda, R);
+    KR_TRY(kr_precond_apply(ctx, t, lambda, g, tmp0, tmp1, tmp2));
+    KR_LAUNCH(ctx, k_update_reduce, ublk, 256, 0, x, tmp0, alpha, R, part);
+    *nparts = ublk;
+    return KR_OK;
+  }
+  PcModes pm = {};
+  pm.N = N;
+  for (int n = 0; n < N; ++n) {
+    pm.R[n] = t.R[n];
+    pm.B[n] = lambda > 0.0 ? t.V[n] : t.ginv[n];
+    pm.B2[n] = t.V[n];
+    pm.sig2[n] = t.sig2[n];
+  }
+  pm.trans = lambda > 0.0 ? 1 : 0;
+  pm.lambda = (float)lambda;
+
+  int g0 = (int)((Q + PC_TQ - 1) / PC_TQ);
+  if (g0 > ctx->num_sms * 4) g0 = ctx->num_sms * 4;
+  const int sthreads = Q >= 1024 ? 1024 : (Q <= 256 ? 256 : (int)((Q + 31) / 32 * 32));
+  const float* xl = lambda > 0.0 ? x : nullptr;
+  const int Qi = (int)Q;
+  const size_t fsmem = ((size_t)R + 2 * (size_t)Q + KR_MAX_RANK + nb) * sizeof(float);
+  bool fused = false;
+  KR_TRY(smem_fit(ctx, k_pc_fused, fsmem, &fused));
+  if (fused) {
+    if (lambda == 0.0) {
+      KR_LAUNCH(ctx, k_pc_fused, R0, sthreads, fsmem, pm, g, nullptr, 0.f, pm.B[0], 0, N > 1 ? 1 : 0, R0, Qi,
+                nullptr, x, alpha, part);
+      *nparts = R0;
+      return KR_OK;
+    }
+    KR_LAUNCH(ctx, k_pc_fused, R0, sthreads, fsmem, pm, g, x, (float)lambda, pm.B[0], 1, 1, R0, Qi, tmp0, nullptr,
+              0.f, part);
+    KR_LAUNCH(ctx, k_pc_fused, R0, sthreads, fsmem, pm, tmp0, nullptr, 0.f, pm.B2[0], 0, 0, R0, Qi, nullptr, x,
+              alpha, part);
+    *nparts = R0;
+    return KR_OK;
+  }
+  if (lambda == 0.0 && N == 1) {
+    KR_LAUNCH(ctx, k_pc_mode0, g0, 256, 0, g, xl, 0.f, pm.B[0], 0, R0, Qi, nullptr, x, alpha, part);
+    *nparts = g0;
+    return KR_OK;
+  }
+  KR_LAUNCH(ctx, k_pc_mode0, g0, 256, 0, g, xl, (float)lambda, pm.B[0], pm.trans, R0, Qi, tmp0, nullptr, 0.f, part);
+  if (lambda == 0.0) {
+    KR_LAUNCH(ctx, k_pc_slab, R0, sthreads, smem, pm, tmp0, Qi, nullptr, x, alpha, part);
+    *nparts = R0;
+    return KR_OK;
+  }
+  KR_LAUNCH(ctx, k_pc_slab, R0, sthreads, smem, pm, tmp0, Qi, tmp1, nullptr, 0.f, part);
+  KR_LAUNCH(ctx, k_pc_mode0, g0, 256, 0, tmp1, nullptr, 0.f, pm.B2[0], 0, R0, Qi, nullptr, x, alpha, part);
+  *nparts = g0;
+  return KR_OK;
+}
+
 // Largest intermediate of the prefix mode products of the slab form (modes < N-2).
 int64_t slab_max_intermediate(const Modes& m) {
   int64_t cur = kr_prod_R(m), mx = cur;
@@ -556,7 +903,7 @@ int64_t slab_max_intermediate(const Modes& m) {
 
 // Slab form of the sampled pass: X1 = X x_1 A(1) ... x_{N-2} A(N-2), then the fused slab
 // kernel (Z and the per-tile objective partials in bf.tl->objpart).
-kr_status slab_forward(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const IterBufs& bf) {
+kr_status slab_forward(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const IterBufs& bf, bool want_obj) {
   const int N = m.N;
   const float* X1 = bf.x;
   if (N > 2) {
@@ -571,7 +918,7 @@ kr_status slab_forward(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const I
     KR_TRY(kr_kron_apply2(ctx, N, din, dout, B, tr, bf.x, bf.X1, bf.t0, bf.t1));
     X1 = bf.X1;
   }
-  return kr_slab_pass(ctx, sk, bf.tl, m.A[N - 2], m.A[N - 1], X1, N > 2 ? bf.Z : bf.g);
+  return kr_slab_pass(ctx, sk, bf.tl, m.A[N - 2], m.A[N - 1], X1, N > 2 ? bf.Z : bf.g, want_obj);
 }
 
 // g = Z x_1 A(1)^T ... x_{N-2} A(N-2)^T (for N = 2 the slab pass wrote g itself).
@@ -594,7 +941,7 @@ kr_status slab_backward(kr_ctx* ctx, const Modes& m, const IterBufs& bf) {
 kr_status sampled_pass(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const IterBufs& bf, int nblk, bool want_g,
                        const double** op, int* on) {
   if (bf.tl) {
-    KR_TRY(slab_forward(ctx, m, sk, bf));
+    KR_TRY(slab_forward(ctx, m, sk, bf, !want_g));
     *op = bf.tl->objpart;
     *on = (int)bf.tl->ntmax;
     return want_g ? slab_backward(ctx, m, bf) : KR_OK;
@@ -718,17 +1065,22 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   int it = 0, grow = 0, converged = 0, since_min = 0;
   double prev_step = INFINITY, rel = INFINITY, min_step = INFINITY, min_rel = INFINITY;
   kr_status st = KR_OK;
-  unsigned int* ticket = reinterpret_cast<unsigned int*>(bf.red + 8);
-  KR_CUDA(ctx, cudaMemsetAsync(ticket, 0, sizeof(unsigned int), ctx->stream));
   const double* op = nullptr;
   int on = 0;
   for (it = 1; it <= cfg.max_iter; ++it) {
     KR_TRY(sampled_pass(ctx, m, &sk, bf, nblk, true, &op, &on));
-    if (cfg.lambda > 0.0) KR_LAUNCH(ctx, k_sub_lambda_x, ublk, 256, 0, bf.g, bf.x, (float)cfg.lambda, R);
-    KR_TRY(kr_precond_apply(ctx, t, cfg.lambda, bf.g, bf.d, bf.t0, bf.t1));
-    KR_LAUNCH(ctx, k_update_reduce, ublk, 256, 0, bf.x, bf.d, (float)cfg.alpha, R, bf.part, ticket, bf.red);
-    KR_CUDA(ctx, cudaMemcpyAsync(h, bf.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    int np = 0;
+    KR_TRY(pc_step(ctx, t, cfg.lambda, bf.g, bf.x, (float)cfg.alpha, bf.d, bf.t0, bf.t1, ublk, bf.part, &np));
+    KR_TRY(kr_hbuf_reserve(ctx, sizeof(double) * (3 * (size_t)np + 8)));
+    h = (double*)ctx->hbuf;
+    KR_CUDA(ctx, cudaMemcpyAsync(h + 8, bf.part, 3 * (size_t)np * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    h[0] = h[1] = h[2] = 0.0;
+    for (int b = 0; b < np; ++b) {  // block order
+      h[0] += h[8 + 3 * b];
+      h[1] += h[8 + 3 * b + 1];
+      h[2] = fmax(h[2], h[8 + 3 * b + 2]);
+    }
     StepCheck sc = step_check(h, cfg.tol, &prev_step, &min_step, &min_rel, &grow, &since_min, &rel, -1.0);
     if (sc == STEP_NONFINITE) {
       st = kr_fail(ctx, KR_ENONFINITE, "Richardson iterate became non-finite at iteration %d", it);
