@@ -235,6 +235,11 @@ struct kr_tiles {
   uint32_t* order = nullptr;     // ntmax: processing order (heaviest first)
   uint4* tsort = nullptr;        // ntmax: descriptors in processing order (packed, see kr_slab.cu)
   uint2* slab = nullptr;         // P: {first tile, tiles}
+  uint32_t* tstart = nullptr;    // P + 1: first tile of every slab (tiles are in slab order)
+  // backward fold of the last prefix mode (k_tile_reduce): groups p' of Iq slabs, Rq rows
+  int64_t Pq = 1;
+  int Iq = 1, Rq = 1, nc = 1;
+  float* zred = nullptr;         // nc x Pq x Rq x R2 x RT chunk partials (nc > 1)
   uint32_t* meta = nullptr;      // [0] tiles, [1] non-empty cells, [2], [3] work counters
   float* zpart = nullptr;        // ntmax x R2 x RT: contributions of tiles of multi-tile slabs
   double* objpart = nullptr;     // ntmax: per-tile sampled objective (FP64; zero past the last)
@@ -250,11 +255,14 @@ void kr_tiles_layout(kr_tiles* tl, int64_t ncell, Carve& cv);
 void kr_tiles_scratch_need(const kr_tiles* tl, int64_t ncell, Need& nd);
 // Builds the tiles from a filled sketch (scratch from cv).
 kr_status kr_tiles_build(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, Carve& cv);
-// One fused pass: Z[p] = sum over the sampled rows of slab p of
-//   A(N-2)[i]^T-weighted residual accumulations (see kr_slab.cu), from X1 (P x R2 x RT);
-// with want_obj the per-tile objective partials go to tl->objpart (tl->ntmax doubles).
+// One fused pass from X1 (P x R2 x RT): every tile's contribution to its slab's
+// Z[p] = sum_i A(N-2)[i]^T W[p, i] goes to tl->zpart (see kr_slab.cu); with want_obj the
+// per-tile objective partials go to tl->objpart (tl->ntmax doubles).
 kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const float* A2, const float* AT,
-                       const float* X1, float* Z, bool want_obj);
+                       const float* X1, bool want_obj);
+// W[p', r, :] = sum over the tiles of the slabs p' * Iq + i of Aq[i, r] zpart[t, :]
+// (Aq = A(N-3) for N >= 3, nullptr for N = 2): Pq x Rq x R2 x RT floats.
+kr_status kr_tile_reduce(kr_ctx* ctx, kr_tiles* tl, const float* Aq, float* W);
 
 // ------------------------------------------------------------------ solvers
 

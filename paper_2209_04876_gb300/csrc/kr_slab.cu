@@ -59,13 +59,11 @@ struct SlabArgs {
   const float* AT;  // IT x RT
   const float* A2;  // I2 x R2
   const float* X1;  // P x R2 x RT
-  float* Z;         // P x R2 x RT
   float* zpart;     // ntmax x R2 x RT
   double* objpart;  // ntmax
   int IT, RT, I2, R2, R2P, R2S;
   int64_t P;
   int a2vec, atvec;
-  int want_obj;  // per-tile objective partials (only the final pass of a solve reads them)
   // shared-memory layout (bytes)
   uint32_t team_off, team_bytes, o_a2, o_x1, o_pf, o_act, o_cs, o_ctl;
 };
@@ -135,8 +133,9 @@ __device__ __forceinline__ float group_sum(float v, unsigned gmask) {
   return v;
 }
 
-// One sampled row against the current cell: r = omega (b~ - <a, y>), w += r a.
-template <int RTP, bool SMEM_A>
+// One sampled row against the current cell: r = omega (b~ - <a, y>), w += r a (and the
+// objective term r (b~ - <a, y>) when OBJ).
+template <int RTP, bool SMEM_A, bool OBJ>
 __device__ __forceinline__ void slab_entry(const SlabArgs& a, const float* sA, const float* sInvp, const int* qd,
                                            unsigned gmask, uint32_t e, float bj, float cw, const float* y, float* w,
                                            float& objc) {
@@ -149,12 +148,12 @@ __device__ __forceinline__ void slab_entry(const SlabArgs& a, const float* sA, c
   const float res = bj - pr;
   const float rr = om * res;
   axpy_quads<S::NQ>(rr, av, w);
-  objc = fmaf(rr, res, objc);
+  if (OBJ) objc = fmaf(rr, res, objc);
 }
 
 // Cell k ends: its W goes to the cell's row (owned) or to the group's partial slot (the
 // cell began in an earlier group's segment); the walk moves to cell k + 1.
-template <int RTP>
+template <int RTP, bool OBJ>
 __device__ __forceinline__ void slab_next_cell(float* sYW, float* sPf, const uint32_t* sCS, const uint4* sAct,
                                                uint32_t e0, int q, const int* qd, int& k, uint32_t& nb, float& cw,
                                                bool& foreign, float* y, float* w, float& objc, double& objt) {
@@ -163,8 +162,10 @@ __device__ __forceinline__ void slab_next_cell(float* sYW, float* sPf, const uin
 #pragma unroll
   for (int v = 0; v < S::NQ; ++v)
     reinterpret_cast<float4*>(dst)[qd[v]] = make_float4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
-  objt += (double)objc;
-  objc = 0.f;
+  if (OBJ) {
+    objt += (double)objc;
+    objc = 0.f;
+  }
   ++k;
   nb = sCS[k + 1] - e0;
   cw = __uint_as_float(sAct[k].w);
@@ -181,7 +182,7 @@ __device__ __forceinline__ void slab_next_cell(float* sYW, float* sPf, const uin
   for (int c = 0; c < S::COLS; ++c) w[c] = 0.f;
 }
 
-template <int RTP, bool SMEM_A>
+template <int RTP, bool SMEM_A, bool OBJ>
 __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
   using S = SlabShape<RTP>;
   constexpr int COLS = S::COLS, G = S::G, NQ = S::NQ, NG = S::NG;
@@ -246,7 +247,6 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
     const uint32_t t = td.y;
     if (t == 0xFFFFFFFFu) break;
     const int na = (int)((td.w >> 24) & 0x7Fu) + 1;
-    const bool multi = (td.w >> 31) != 0u;
     const int64_t p = td.z;
     const uint32_t E = td.w & 0xFFFFFFu;
     // ---- tile metadata, rows of A(N-1), X1[p]
@@ -373,8 +373,8 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
           const uint32_t e = G > 1 ? __shfl_sync(0xffffffffu, e_m, gbase + sidx) : e_m;
           const float bj = G > 1 ? __shfl_sync(0xffffffffu, b_m, gbase + sidx) : b_m;
           if (j < j1 && j == nb)
-            slab_next_cell<RTP>(sYW, sPf, sCS, sAct, e0, q, qd, k, nb, cw, foreign, y, w, objc, objt);
-          slab_entry<RTP, SMEM_A>(a, sA, sInvp, qd, 0xffffffffu, e, bj, cw, y, w, objc);
+            slab_next_cell<RTP, OBJ>(sYW, sPf, sCS, sAct, e0, q, qd, k, nb, cw, foreign, y, w, objc, objt);
+          slab_entry<RTP, SMEM_A, OBJ>(a, sA, sInvp, qd, 0xffffffffu, e, bj, cw, y, w, objc);
         }
       }
     }
@@ -387,8 +387,8 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
       for (int v = 0; v < NQ; ++v)
         reinterpret_cast<float4*>(dst)[qd[v]] = make_float4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
     }
-    if (has) objt += (double)objc;
-    if (a.want_obj) {  // objective of the tile: one lane per group
+    if (OBJ && has) objt += (double)objc;
+    if (OBJ) {  // objective of the tile: one lane per group
       double ov = (g == 0 && has) ? objt : 0.0;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) ov += __shfl_xor_sync(0xffffffffu, ov, off);
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
       for (int v = 0; v < NQ; ++v)
         reinterpret_cast<float4*>(sYW + k * RTP)[qd[v]] = make_float4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
     }
-    if (tt == 0 && a.want_obj) {
+    if (OBJ && tt == 0) {
       double s = 0.0;
       for (int i = 0; i < SLAB_TEAM / 32; ++i) s += sRed[i];
       a.objpart[t] = s;
@@ -451,9 +451,8 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
               make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
       }
       team_sync(team);
-      // the k-split parts in order; a slab of one tile is written directly, the tiles of a
-      // larger slab go to their slots and k_tile_sum adds them in tile order
-      float* dst = multi ? a.zpart + (size_t)t * zn : a.Z + p * zn;
+      // the k-split parts in order, to the tile's slot (k_tile_reduce adds the tiles)
+      float* dst = a.zpart + (size_t)t * zn;
       for (int i = tt; i < zn; i += SLAB_TEAM) {
         const int r = i / RT, c = i - r * RT;
         float v = sPf[r * RTP + c];
@@ -464,23 +463,76 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
   }
 }
 
-// Z[p] of slabs split over several tiles: the tiles' parts added in tile order; slabs
-// without sampled rows are zero (a slab of one tile was written by k_slab).
-__global__ void k_tile_sum(int64_t P, int zn, const uint2* __restrict__ slab, const float* __restrict__ zpart,
-                           float* __restrict__ Z) {
-  const int64_t n = P * zn;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = i / zn;
-    const int c = (int)(i - p * zn);
-    const uint2 sl = slab[p];
-    if (sl.y == 1) continue;
-    float v = 0.f;
-    if (sl.y > 1) {
-      v = zpart[(size_t)sl.x * zn + c];
-      for (uint32_t t = sl.x + 1; t < sl.x + sl.y; ++t) v += zpart[(size_t)t * zn + c];
-    }
-    Z[i] = v;
+// The backward product of the last prefix mode folded into the sum over tiles:
+// W[p', r, :] = sum_i Aq[i, r] Z[p' Iq + i, :] with Z[p] = sum of the tiles of slab p
+// (tiles of slab p: [tstart[p], tstart[p + 1]); Aq = A(N-2) for N >= 3; for N = 2 there
+// is no prefix mode: Iq = Rq = 1, weight 1). The Iq slabs of a group are split into nc
+// chunks of at most TR_MAXS slabs (blockIdx.y) and the columns into panels (blockIdx.x):
+// a block forms Z of its slabs for its panel in shared memory (tiles in order), then
+// part[c] = sum over its slabs of Aq rows x Z (slab order); k_tile_reduce2 adds the chunks
+// in order.
+constexpr int TR_MAXS = 64;  // slabs per chunk at most
+constexpr int TR_QP = 64;    // columns per block
+__global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict__ tstart, int Iq,
+                                                      const float* __restrict__ zpart, const float* __restrict__ Aq,
+                                                      int Rq, int zn, int nc, int64_t Pq, float* __restrict__ part) {
+  __shared__ uint32_t s_ts[TR_MAXS + 1];
+  __shared__ float s_z[TR_MAXS][TR_QP];
+  __shared__ float s_a[TR_MAXS][KR_MAX_RANK];
+  const int64_t pq = blockIdx.z;
+  const int c = blockIdx.y;
+  const int qb = blockIdx.x * TR_QP;
+  const int per = (Iq + nc - 1) / nc;
+  const int i0 = min(Iq, c * per), i1 = min(Iq, i0 + per), S = i1 - i0;
+  for (int k = threadIdx.x; k <= S; k += blockDim.x) s_ts[k] = tstart[pq * Iq + i0 + k];
+  for (int e = threadIdx.x; e < S * Rq; e += blockDim.x) {
+    const int i = e / Rq, r = e - i * Rq;
+    s_a[i][r] = Aq ? __ldg(Aq + (size_t)(i0 + i) * Rq + r) : 1.f;
   }
+  __syncthreads();
+  // Z of the chunk's slabs for this panel: tiles of one slab in order
+#pragma unroll 4
+  for (int e = threadIdx.x; e < S * TR_QP; e += blockDim.x) {
+    const int i = e / TR_QP, qq = e - i * TR_QP, q = qb + qq;
+    float z = 0.f;
+    if (q < zn)
+      for (uint32_t t = s_ts[i]; t < s_ts[i + 1]; ++t) z += __ldg(zpart + (size_t)t * zn + q);
+    s_z[i][qq] = z;
+  }
+  __syncthreads();
+  // part[c][pq][r][q] = sum_i Aq[i0 + i, r] Z[i, q] in slab order
+  float* out = part + ((size_t)c * Pq + pq) * Rq * zn;
+  for (int e = threadIdx.x; e < Rq * TR_QP; e += blockDim.x) {
+    const int r = e / TR_QP, qq = e - r * TR_QP, q = qb + qq;
+    if (q >= zn) continue;
+    float acc = 0.f;
+    for (int i = 0; i < S; ++i) acc = fmaf(s_a[i][r], s_z[i][qq], acc);
+    out[(size_t)r * zn + q] = acc;
+  }
+}
+
+__global__ void k_tile_reduce2(const float* __restrict__ part, int nc, int64_t total, float* __restrict__ W) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int c0 = 0; c0 < nc; c0 += 16) {  // loads of a batch in flight together, added in order
+      float v[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) v[c] = c0 + c < nc ? __ldg(part + (size_t)(c0 + c) * total + e) : 0.f;
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c0 + c < nc) s = (c0 + c == 0) ? v[c] : s + v[c];
+    }
+    W[e] = s;
+  }
+}
+
+// tstart[P] = tiles (after the exclusive scan of the per-slab tile counts).
+__global__ void k_tiles_counts(int64_t P, const uint2* __restrict__ slab, uint32_t* __restrict__ cnt) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x)
+    cnt[p] = slab[p].y;
+}
+__global__ void k_tiles_tail(int64_t P, const uint32_t* __restrict__ meta, uint32_t* __restrict__ tstart) {
+  tstart[P] = meta[0];
 }
 
 // ------------------------------------------------------------------ tile construction
@@ -614,27 +666,27 @@ SlabLayout slab_layout(int IT, int RT, int R2, bool smem_a) {
   return L;
 }
 
-template <int RTP, bool SMEM_A>
+template <int RTP, bool SMEM_A, bool OBJ>
 kr_status launch_slab_t(kr_ctx* ctx, const SlabArgs& a, size_t smem) {
   static int configured_dev = -1;
   static size_t configured_bytes = 0;
   if (configured_dev != ctx->device || configured_bytes < smem) {
-    KR_CUDA(ctx, cudaFuncSetAttribute(k_slab<RTP, SMEM_A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    KR_CUDA(ctx, cudaFuncSetAttribute(k_slab<RTP, SMEM_A, OBJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured_dev = ctx->device;
     configured_bytes = smem;
   }
-  KR_LAUNCH(ctx, (k_slab<RTP, SMEM_A>), ctx->num_sms, SLAB_TEAM * SLAB_TEAMS, smem, a);
+  KR_LAUNCH(ctx, (k_slab<RTP, SMEM_A, OBJ>), ctx->num_sms, SLAB_TEAM * SLAB_TEAMS, smem, a);
   return KR_OK;
 }
 
-template <bool SMEM_A>
+template <bool SMEM_A, bool OBJ>
 kr_status launch_slab(kr_ctx* ctx, int RTP, const SlabArgs& a, size_t smem) {
   switch (RTP) {
-    case 4: return launch_slab_t<4, SMEM_A>(ctx, a, smem);
-    case 8: return launch_slab_t<8, SMEM_A>(ctx, a, smem);
-    case 16: return launch_slab_t<16, SMEM_A>(ctx, a, smem);
-    case 32: return launch_slab_t<32, SMEM_A>(ctx, a, smem);
-    case 64: return launch_slab_t<64, SMEM_A>(ctx, a, smem);
+    case 4: return launch_slab_t<4, SMEM_A, OBJ>(ctx, a, smem);
+    case 8: return launch_slab_t<8, SMEM_A, OBJ>(ctx, a, smem);
+    case 16: return launch_slab_t<16, SMEM_A, OBJ>(ctx, a, smem);
+    case 32: return launch_slab_t<32, SMEM_A, OBJ>(ctx, a, smem);
+    case 64: return launch_slab_t<64, SMEM_A, OBJ>(ctx, a, smem);
     default: return kr_fail(ctx, KR_EINVAL, "slab pass: R_N padded to %d", RTP);
   }
 }
@@ -672,6 +724,20 @@ void kr_tiles_setup(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, kr_tiles* 
   tl->ntmax = bound < ncell ? bound : ncell;
   if (tl->ntmax < 1) tl->ntmax = 1;
   tl->par = 0;
+  if (N >= 3) {
+    tl->Iq = m.I[N - 3];
+    tl->Rq = m.R[N - 3];
+  } else {
+    tl->Iq = 1;
+    tl->Rq = 1;
+  }
+  tl->Pq = P / tl->Iq;
+  // chunks of about 16 slabs (at most 64 = TR_MAXS), at most 32 chunks unless the
+  // 64-slab limit needs more
+  int nc = tl->Iq / 16;
+  nc = nc < 1 ? 1 : (nc > 32 ? 32 : nc);
+  const int need = (tl->Iq + 63) / 64;
+  tl->nc = nc > need ? nc : need;
 }
 
 void kr_tiles_own_need(const kr_tiles* tl, int64_t ncell, Need& nd) {
@@ -681,6 +747,8 @@ void kr_tiles_own_need(const kr_tiles* tl, int64_t ncell, Need& nd) {
   nd.add<uint32_t>(tl->ntmax);
   nd.add<uint4>(tl->ntmax);
   nd.add<uint2>(tl->P);
+  nd.add<uint32_t>(tl->P + 1);
+  nd.add<float>(tl->nc > 1 ? (size_t)tl->nc * tl->Pq * tl->Rq * tl->R2 * tl->RT : 0);
   nd.add<uint32_t>(4);
   nd.add<float>((size_t)tl->ntmax * tl->R2 * tl->RT);
   nd.add<double>(tl->ntmax);
@@ -693,6 +761,8 @@ void kr_tiles_layout(kr_tiles* tl, int64_t ncell, Carve& cv) {
   tl->order = cv.take<uint32_t>(tl->ntmax);
   tl->tsort = cv.take<uint4>(tl->ntmax);
   tl->slab = cv.take<uint2>(tl->P);
+  tl->tstart = cv.take<uint32_t>(tl->P + 1);
+  tl->zred = cv.take<float>(tl->nc > 1 ? (size_t)tl->nc * tl->Pq * tl->Rq * tl->R2 * tl->RT : 0);
   tl->meta = cv.take<uint32_t>(4);
   tl->zpart = cv.take<float>((size_t)tl->ntmax * tl->R2 * tl->RT);
   tl->objpart = cv.take<double>(tl->ntmax);
@@ -738,11 +808,17 @@ kr_status kr_tiles_build(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, Carve& 
   }
   KR_LAUNCH(ctx, k_tiles_sort, grid_n(ctx, tl->ntmax), 256, 0, tl->ntmax, tl->order, tl->tile, tl->slab, tl->meta,
             tl->tsort);
+  KR_LAUNCH(ctx, k_tiles_counts, grid_n(ctx, tl->P), 256, 0, tl->P, tl->slab, tl->tstart);
+  {
+    Carve sc = cv;
+    KR_TRY(kr_scan_u32(ctx, tl->tstart, tl->tstart, tl->P, sc));
+  }
+  KR_LAUNCH(ctx, k_tiles_tail, 1, 1, 0, tl->P, tl->meta, tl->tstart);
   return KR_OK;
 }
 
 kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const float* A2, const float* AT,
-                       const float* X1, float* Z, bool want_obj) {
+                       const float* X1, bool want_obj) {
   SlabLayout L = slab_layout(tl->IT, tl->RT, tl->R2, true);
   if (L.bytes > ctx->smem_optin) L = slab_layout(tl->IT, tl->RT, tl->R2, false);
   if (L.bytes > ctx->smem_optin) return kr_fail(ctx, KR_ENOTIMPL, "slab pass: %zu bytes of shared memory", L.bytes);
@@ -757,7 +833,6 @@ kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const flo
   a.AT = AT;
   a.A2 = A2;
   a.X1 = X1;
-  a.Z = Z;
   a.zpart = tl->zpart;
   a.objpart = tl->objpart;
   a.IT = tl->IT;
@@ -769,7 +844,6 @@ kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const flo
   a.P = tl->P;
   a.a2vec = (tl->R2 % 4 == 0) && ((reinterpret_cast<uintptr_t>(A2) & 15) == 0);
   a.atvec = (tl->RT % 4 == 0) && ((reinterpret_cast<uintptr_t>(AT) & 15) == 0);
-  a.want_obj = want_obj ? 1 : 0;
   a.team_off = L.team_off;
   a.team_bytes = L.team_bytes;
   a.o_a2 = L.o_a2;
@@ -778,10 +852,22 @@ kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const flo
   a.o_act = L.o_act;
   a.o_cs = L.o_cs;
   a.o_ctl = L.o_ctl;
-  kr_status st = L.smem_a ? launch_slab<true>(ctx, L.RTP, a, L.bytes) : launch_slab<false>(ctx, L.RTP, a, L.bytes);
+  kr_status st = L.smem_a ? (want_obj ? launch_slab<true, true>(ctx, L.RTP, a, L.bytes)
+                                      : launch_slab<true, false>(ctx, L.RTP, a, L.bytes))
+                         : (want_obj ? launch_slab<false, true>(ctx, L.RTP, a, L.bytes)
+                                     : launch_slab<false, false>(ctx, L.RTP, a, L.bytes));
   tl->par ^= 1;
-  KR_TRY(st);
+  return st;
+}
+
+kr_status kr_tile_reduce(kr_ctx* ctx, kr_tiles* tl, const float* Aq, float* W) {
   const int zn = tl->R2 * tl->RT;
-  KR_LAUNCH(ctx, k_tile_sum, grid_n(ctx, tl->P * zn), 256, 0, tl->P, zn, tl->slab, tl->zpart, Z);
+  const dim3 grid((unsigned)((zn + TR_QP - 1) / TR_QP), (unsigned)tl->nc, (unsigned)tl->Pq);
+  float* part = tl->nc > 1 ? tl->zred : W;
+  KR_LAUNCH(ctx, k_tile_reduce1, grid, 256, 0, tl->tstart, tl->Iq, tl->zpart, Aq, tl->Rq, zn, tl->nc, tl->Pq, part);
+  if (tl->nc > 1) {
+    const int64_t total = tl->Pq * tl->Rq * zn;
+    KR_LAUNCH(ctx, k_tile_reduce2, grid_n(ctx, total), 256, 0, tl->zred, tl->nc, total, W);
+  }
   return KR_OK;
 }

@@ -918,19 +918,21 @@ kr_status slab_forward(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const I
     KR_TRY(kr_kron_apply2(ctx, N, din, dout, B, tr, bf.x, bf.X1, bf.t0, bf.t1));
     X1 = bf.X1;
   }
-  return kr_slab_pass(ctx, sk, bf.tl, m.A[N - 2], m.A[N - 1], X1, N > 2 ? bf.Z : bf.g, want_obj);
+  return kr_slab_pass(ctx, sk, bf.tl, m.A[N - 2], m.A[N - 1], X1, want_obj);
 }
 
-// g = Z x_1 A(1)^T ... x_{N-2} A(N-2)^T (for N = 2 the slab pass wrote g itself).
+// g = Z x_1 A(1)^T ... x_{N-2} A(N-2)^T: the sum over the tiles folded with the last
+// prefix mode (mode N-2 in the paper's 1-based count), then the earlier prefix modes.
 kr_status slab_backward(kr_ctx* ctx, const Modes& m, const IterBufs& bf) {
   const int N = m.N;
-  if (N == 2) return KR_OK;
+  if (N <= 3) return kr_tile_reduce(ctx, bf.tl, N == 3 ? m.A[0] : nullptr, bf.g);
+  KR_TRY(kr_tile_reduce(ctx, bf.tl, m.A[N - 3], bf.Z));
   int din[KR_MAX_MODES], dout[KR_MAX_MODES], tr[KR_MAX_MODES];
   const float* B[KR_MAX_MODES];
   for (int n = 0; n < N; ++n) {
-    din[n] = (n < N - 2) ? m.I[n] : m.R[n];
+    din[n] = (n < N - 3) ? m.I[n] : m.R[n];
     dout[n] = m.R[n];
-    B[n] = (n < N - 2) ? m.A[n] : nullptr;
+    B[n] = (n < N - 3) ? m.A[n] : nullptr;
     tr[n] = 1;
   }
   return kr_kron_apply2(ctx, N, din, dout, B, tr, bf.Z, bf.g, bf.t0, bf.t1);
