@@ -135,8 +135,13 @@ enum {
  *    uses the per-cell residual pass between two full mode products.
  *  KR_OPT_SLAB_TILE_ENTRIES (default 16384, range [256, 2^22]): entry budget of one
  *    tile of the slab pass.
+ *  KR_OPT_DEVICE_LOOP (default 1): 1 runs the Richardson steps after the first as one CUDA
+ *    graph (a conditional loop whose body is one step and a device-side evaluation of the
+ *    stopping rule), 0 returns to the host after every step. Both apply the same rule to
+ *    the same device-side sums, so they give identical results. Per-kernel timing
+ *    (kr_timing_enable) always uses the host loop.
  * Returns KR_EINVAL for an unknown key or a value out of range. */
-enum { KR_OPT_SLAB_PASS = 1, KR_OPT_SLAB_TILE_ENTRIES = 2 };
+enum { KR_OPT_SLAB_PASS = 1, KR_OPT_SLAB_TILE_ENTRIES = 2, KR_OPT_DEVICE_LOOP = 3 };
 KR_API kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value);
 
 KR_API kr_status kr_timing_enable(kr_ctx* ctx, int32_t on);

@@ -53,6 +53,10 @@ extern "C" kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value) {
         return kr_fail(ctx, KR_EINVAL, "kr_set_option: tile entries %lld outside [256, 2^22]", (long long)value);
       ctx->slab_tile_entries = (uint32_t)value;
       return KR_OK;
+    case KR_OPT_DEVICE_LOOP:
+      if (value != 0 && value != 1) return kr_fail(ctx, KR_EINVAL, "kr_set_option: device loop must be 0 or 1");
+      ctx->device_loop = (int)value;
+      return KR_OK;
     default:
       return kr_fail(ctx, KR_EINVAL, "kr_set_option: unknown key %d", key);
   }

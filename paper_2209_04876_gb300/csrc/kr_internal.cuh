@@ -32,6 +32,7 @@ struct kr_ctx {
   // options (kr_set_option)
   int slab_pass = 1;
   uint32_t slab_tile_entries = 16384;
+  int device_loop = 1;  // Richardson iterations 2.. as one CUDA graph with a conditional loop
   cudaEvent_t ev[10] = {};
   cudaEvent_t pev[2] = {};  // completion of the two in-flight Richardson norm read-backs
   // per-kernel timing (instrumentation)
@@ -240,10 +241,9 @@ struct kr_tiles {
   int64_t Pq = 1;
   int Iq = 1, Rq = 1, nc = 1;
   float* zred = nullptr;         // nc x Pq x Rq x R2 x RT chunk partials (nc > 1)
-  uint32_t* meta = nullptr;      // [0] tiles, [1] non-empty cells, [2], [3] work counters
+  uint32_t* meta = nullptr;      // [0] tiles, [1] non-empty cells, [2] work counter (zero between passes)
   float* zpart = nullptr;        // ntmax x R2 x RT: contributions of tiles of multi-tile slabs
   double* objpart = nullptr;     // ntmax: per-tile sampled objective (FP64; zero past the last)
-  int par = 0;                   // work counter of the next pass
 };
 
 // Whether the sketch/shape admits the slab pass (single right-hand side, N >= 2,
@@ -272,8 +272,8 @@ struct SolveCfg {
   int64_t s;
 };
 
-enum StepCheck { STEP_CONTINUE, STEP_CONVERGED, STEP_FLOOR, STEP_DIVERGED, STEP_NONFINITE };
-StepCheck step_check(const double* h, double tol, double* prev_step, double* min_step, double* min_rel, int* grow,
+enum StepCheck { STEP_CONTINUE, STEP_CONVERGED, STEP_FLOOR, STEP_DIVERGED, STEP_NONFINITE, STEP_MAXITER };
+__host__ __device__ StepCheck step_check(const double* h, double tol, double* prev_step, double* min_step, double* min_rel, int* grow,
                      int* since_min, double* rel_out, double rel_override);
 
 // Alg. 2 on device-resident factors and b; x (R floats) is written.

@@ -245,7 +245,9 @@ kr_status kr_mode_product(kr_ctx* ctx, const float* in, float* out, int64_t P, i
   if (NN == 0 || J == 0) return KR_OK;
   const bool aligned = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
   if (Q % 4 == 0 && aligned) {
-    const int BM = J <= 32 ? 32 : 64;
+    // 64-row tiles unless they leave SMs idle (then 32-row tiles double the blocks)
+    int BM = J <= 32 ? 32 : 64;
+    if (BM == 64 && ((NN + SG_BN - 1) / SG_BN) * ((J + 63) / 64) < ctx->num_sms) BM = 32;
     dim3 grid((unsigned)((NN + SG_BN - 1) / SG_BN), (unsigned)((J + BM - 1) / BM), 1);
     // split K when the output alone gives too few blocks to fill the GPU
     int S = 1, kchunk = K;

@@ -52,7 +52,6 @@ struct SlabArgs {
   const uint4* act;
   const uint4* tsort;  // per processing slot: {first cell, tile, slab, entries | (cells - 1) << 24 | multi << 31}
   uint32_t* meta;
-  int par;
   const uint32_t* ent;
   const float* bt;
   const float* invpT;
@@ -208,7 +207,6 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
     }
   }
   for (int i = threadIdx.x; i < a.IT; i += blockDim.x) sInvp[i] = __ldg(a.invpT + i);
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.meta[2 + (a.par ^ 1)] = 0;  // counter of the next pass
   __syncthreads();
 
   const int team = threadIdx.x / SLAB_TEAM, tt = threadIdx.x % SLAB_TEAM;
@@ -235,12 +233,12 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
   // The leader claims the next processing slot one tile ahead, so only the descriptor
   // load (one round trip) sits between two tiles.
   uint32_t nk = 0;
-  if (tt == 0) nk = atomicAdd(&a.meta[2 + a.par], 1u);
+  if (tt == 0) nk = atomicAdd(&a.meta[2], 1u);
   for (;;) {
     if (tt == 0) {
       const uint4 d = nk < ntiles ? a.tsort[nk] : make_uint4(0u, 0xFFFFFFFFu, 0u, 0u);
       *reinterpret_cast<uint4*>(sCtl + 4) = d;
-      if (nk < ntiles) nk = atomicAdd(&a.meta[2 + a.par], 1u);
+      if (nk < ntiles) nk = atomicAdd(&a.meta[2], 1u);
     }
     team_sync(team);
     const uint4 td = *reinterpret_cast<const uint4*>(sCtl + 4);
@@ -475,7 +473,10 @@ constexpr int TR_MAXS = 64;  // slabs per chunk at most
 constexpr int TR_QP = 64;    // columns per block
 __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict__ tstart, int Iq,
                                                       const float* __restrict__ zpart, const float* __restrict__ Aq,
-                                                      int Rq, int zn, int nc, int64_t Pq, float* __restrict__ part) {
+                                                      int Rq, int zn, int nc, int64_t Pq, float* __restrict__ part,
+                                                      uint32_t* __restrict__ counter) {
+  // the slab pass that produced zpart has finished (stream order): re-arm its work counter
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) *counter = 0u;
   __shared__ uint32_t s_ts[TR_MAXS + 1];
   __shared__ float s_z[TR_MAXS][TR_QP];
   __shared__ float s_a[TR_MAXS][KR_MAX_RANK];
@@ -723,7 +724,6 @@ void kr_tiles_setup(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, kr_tiles* 
   int64_t bound = P + (ncell + tl->cb - 1) / tl->cb + (sk->s + tl->et - 1) / tl->et;
   tl->ntmax = bound < ncell ? bound : ncell;
   if (tl->ntmax < 1) tl->ntmax = 1;
-  tl->par = 0;
   if (N >= 3) {
     tl->Iq = m.I[N - 3];
     tl->Rq = m.R[N - 3];
@@ -826,7 +826,6 @@ kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const flo
   a.act = tl->act;
   a.tsort = tl->tsort;
   a.meta = tl->meta;
-  a.par = tl->par;
   a.ent = sk->ent;
   a.bt = sk->bt;
   a.invpT = sk->invpT;
@@ -852,11 +851,11 @@ kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const flo
   a.o_act = L.o_act;
   a.o_cs = L.o_cs;
   a.o_ctl = L.o_ctl;
+  if (want_obj) KR_CUDA(ctx, cudaMemsetAsync(tl->meta + 2, 0, sizeof(uint32_t), ctx->stream));
   kr_status st = L.smem_a ? (want_obj ? launch_slab<true, true>(ctx, L.RTP, a, L.bytes)
                                       : launch_slab<true, false>(ctx, L.RTP, a, L.bytes))
                          : (want_obj ? launch_slab<false, true>(ctx, L.RTP, a, L.bytes)
                                      : launch_slab<false, false>(ctx, L.RTP, a, L.bytes));
-  tl->par ^= 1;
   return st;
 }
 
@@ -864,7 +863,8 @@ kr_status kr_tile_reduce(kr_ctx* ctx, kr_tiles* tl, const float* Aq, float* W) {
   const int zn = tl->R2 * tl->RT;
   const dim3 grid((unsigned)((zn + TR_QP - 1) / TR_QP), (unsigned)tl->nc, (unsigned)tl->Pq);
   float* part = tl->nc > 1 ? tl->zred : W;
-  KR_LAUNCH(ctx, k_tile_reduce1, grid, 256, 0, tl->tstart, tl->Iq, tl->zpart, Aq, tl->Rq, zn, tl->nc, tl->Pq, part);
+  KR_LAUNCH(ctx, k_tile_reduce1, grid, 256, 0, tl->tstart, tl->Iq, tl->zpart, Aq, tl->Rq, zn, tl->nc, tl->Pq, part,
+            tl->meta + 2);
   if (tl->nc > 1) {
     const int64_t total = tl->Pq * tl->Rq * zn;
     KR_LAUNCH(ctx, k_tile_reduce2, grid_n(ctx, total), 256, 0, tl->zred, tl->nc, total, W);

@@ -214,44 +214,6 @@ __global__ void k_sub_lambda_x(float* __restrict__ g, const float* __restrict__ 
     g[i] = fmaf(-lambda, x[i], g[i]);
 }
 
-// x <- x + alpha d; partials of ||alpha d||^2, ||x||^2 and a non-finite flag.
-__global__ void k_update(float* __restrict__ x, const float* __restrict__ d, float alpha, int64_t n,
-                         double* __restrict__ part) {
-  double s1 = 0.0, s2 = 0.0, bad = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float st = alpha * d[i];
-    float xn = x[i] + st;
-    x[i] = xn;
-    s1 += (double)st * st;
-    s2 += (double)xn * xn;
-    if (!isfinite(xn)) bad = 1.0;
-  }
-  __shared__ double red[3][32];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
-    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-    bad = fmax(bad, __shfl_xor_sync(0xffffffffu, bad, off));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = s1;
-    red[1][threadIdx.x >> 5] = s2;
-    red[2][threadIdx.x >> 5] = bad;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0, b = 0, c = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-      a += red[0][k];
-      b += red[1][k];
-      c = fmax(c, red[2][k]);
-    }
-    part[3 * blockIdx.x + 0] = a;
-    part[3 * blockIdx.x + 1] = b;
-    part[3 * blockIdx.x + 2] = c;
-  }
-}
-
 // {||step||^2, ||x||^2, non-finite flag} of the block's elements in FP64, as fixed-order
 // trees (warp shuffles, then one warp over the warp partials), written to
 // part[3 * blockIdx.x + 0..2]; the host adds the blocks' partials in block order. Called
@@ -302,6 +264,82 @@ __global__ void __launch_bounds__(256) k_update_reduce(float* __restrict__ x, co
   }
   step_norms_block(s1, s2, bad, part);
 }
+
+// Richardson state on the device: the stopping rule of Alg. 2 is evaluated by k_rich_check
+// after every step, so a run of iterations needs no host round trip.
+struct RichState {
+  double h[3];  // last {||step||^2, ||x||^2, non-finite flag}
+  double prev_step, min_step, min_rel, rel;
+  int grow, since_min, it, status;  // status: StepCheck (0 = continue)
+};
+
+// The stopping rule of Alg. 2 after one step, by one block (at least 256 threads): the
+// step's block partials summed strided per thread and then by a fixed tree, the rule
+// applied to the state, the iteration counted (max_iter ends the loop in any case) and,
+// inside the graph, the loop condition set.
+__device__ void rich_check_block(const double* __restrict__ part, int np, double tol, int max_iter,
+                                 RichState* __restrict__ st, cudaGraphConditionalHandle hnd, int use_hnd) {
+  __shared__ double r[3][256];
+  const int t = threadIdx.x;
+  if (t < 256) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int k = t; k < np; k += 256) {
+      a += __ldcg(part + 3 * k + 0);
+      b += __ldcg(part + 3 * k + 1);
+      c = fmax(c, __ldcg(part + 3 * k + 2));
+    }
+    r[0][t] = a;
+    r[1][t] = b;
+    r[2][t] = c;
+  }
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (t < off) {
+      r[0][t] += r[0][t + off];
+      r[1][t] += r[1][t + off];
+      r[2][t] = fmax(r[2][t], r[2][t + off]);
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    const double h[3] = {r[0][0], r[1][0], r[2][0]};
+    st->h[0] = h[0];
+    st->h[1] = h[1];
+    st->h[2] = h[2];
+    int status = step_check(h, tol, &st->prev_step, &st->min_step, &st->min_rel, &st->grow, &st->since_min, &st->rel,
+                            -1.0);
+    st->it += 1;
+    if (status == STEP_CONTINUE && st->it >= max_iter) status = STEP_MAXITER;
+    st->status = status;
+    if (use_hnd) cudaGraphSetConditional(hnd, status == STEP_CONTINUE ? 1u : 0u);
+  }
+}
+
+__global__ void k_rich_init(RichState* st) {
+  st->h[0] = st->h[1] = st->h[2] = 0.0;
+  st->prev_step = st->min_step = st->min_rel = st->rel = INFINITY;
+  st->grow = st->since_min = st->it = 0;
+  st->status = STEP_CONTINUE;
+}
+
+// Sums the step's block partials (strided per thread, then a fixed tree), applies the
+// stopping rule, counts the iteration (max_iter ends the loop in any case) and, inside
+// the graph, sets the loop condition.
+__global__ void __launch_bounds__(256) k_rich_check(const double* __restrict__ part, int np, double tol, int max_iter,
+                                                    RichState* __restrict__ st, cudaGraphConditionalHandle hnd,
+                                                    int use_hnd) {
+  rich_check_block(part, np, tol, max_iter, st, hnd, use_hnd);
+}
+
+// Stopping-rule arguments handed to the kernel that ends a step.
+struct RichArgs {
+  RichState* st;
+  double tol;
+  int max_iter;
+  cudaGraphConditionalHandle hnd;
+  int use_hnd;
+  unsigned int* ticket;  // zero between steps
+};
 
 // ------------------------------------------------------------------ preconditioned step, fused
 
@@ -416,7 +454,7 @@ __global__ void __launch_bounds__(1024) k_pc_fused(PcModes pm, const float* __re
                                                    const float* __restrict__ xl, float lambda,
                                                    const float* __restrict__ B0, int trans0, int rest, int R0, int Q,
                                                    float* __restrict__ out, float* __restrict__ x, float alpha,
-                                                   double* __restrict__ part) {
+                                                   double* __restrict__ part, RichArgs ra) {
   extern __shared__ float pc_smem[];
   float* full = pc_smem;          // R0 x Q
   float* t = full + (size_t)R0 * Q;
@@ -514,6 +552,19 @@ __global__ void __launch_bounds__(1024) k_pc_fused(PcModes pm, const float* __re
     }
   }
   if (x) step_norms_block(s1, s2, bad, part);
+  if (x && ra.st) {  // the last block to finish evaluates the stopping rule
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      last = atomicAdd(ra.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      rich_check_block(part, gridDim.x, ra.tol, ra.max_iter, ra.st, ra.hnd, ra.use_hnd);
+      if (threadIdx.x == 0) *ra.ticket = 0u;
+    }
+  }
 }
 
 // One block per slab j of the first mode: the other modes (and, for lambda > 0, the
@@ -758,6 +809,7 @@ struct IterBufs {
   float* t1;     // max intermediate
   double* part;  // partials (3 * nblk)
   double* red;   // 4 doubles
+  RichState* rich = nullptr;  // device stopping-rule state
   // slab form (tl != nullptr): X1 and Z are P x R_{N-1} x R_N (N >= 3; x and g for N = 2)
   kr_tiles* tl = nullptr;
   float* X1 = nullptr;
@@ -821,8 +873,23 @@ kr_status smem_fit(kr_ctx* ctx, F func, size_t dyn, bool* fits) {
 // blocks to part (the caller adds them in block order). One kernel when the iterate fits
 // in shared memory (two for lambda > 0), else the first mode and the slabs' other modes
 // as two (three), else the per-mode sequence. tmp0..tmp2: R floats.
+kr_status pc_step_core(kr_ctx* ctx, const FactorTables& t, double lambda, float* g, float* x, float alpha,
+                       float* tmp0, float* tmp1, float* tmp2, int ublk, double* part, const RichArgs& ra,
+                       int* nparts, bool* checked);
+
 kr_status pc_step(kr_ctx* ctx, const FactorTables& t, double lambda, float* g, float* x, float alpha, float* tmp0,
-                  float* tmp1, float* tmp2, int ublk, double* part, int* nparts) {
+                  float* tmp1, float* tmp2, int ublk, double* part, const RichArgs& ra) {
+  int np = 0;
+  bool checked = false;
+  KR_TRY(pc_step_core(ctx, t, lambda, g, x, alpha, tmp0, tmp1, tmp2, ublk, part, ra, &np, &checked));
+  if (!checked) KR_LAUNCH(ctx, k_rich_check, 1, 256, 0, part, np, ra.tol, ra.max_iter, ra.st, ra.hnd, ra.use_hnd);
+  return KR_OK;
+}
+
+// The step itself; *checked when the last kernel also applied the stopping rule.
+kr_status pc_step_core(kr_ctx* ctx, const FactorTables& t, double lambda, float* g, float* x, float alpha,
+                       float* tmp0, float* tmp1, float* tmp2, int ublk, double* part, const RichArgs& ra,
+                       int* nparts, bool* checked) {
   const int N = t.N;
   int64_t R = 1;
   for (int n = 0; n < N; ++n) R *= t.R[n];
@@ -863,15 +930,19 @@ kr_status pc_step(kr_ctx* ctx, const FactorTables& t, double lambda, float* g, f
   if (fused) {
     if (lambda == 0.0) {
       KR_LAUNCH(ctx, k_pc_fused, R0, sthreads, fsmem, pm, g, nullptr, 0.f, pm.B[0], 0, N > 1 ? 1 : 0, R0, Qi,
-                nullptr, x, alpha, part);
+                nullptr, x, alpha, part, ra);
       *nparts = R0;
+      *checked = true;
       return KR_OK;
     }
+    RichArgs none = ra;
+    none.st = nullptr;
     KR_LAUNCH(ctx, k_pc_fused, R0, sthreads, fsmem, pm, g, x, (float)lambda, pm.B[0], 1, 1, R0, Qi, tmp0, nullptr,
-              0.f, part);
+              0.f, part, none);
     KR_LAUNCH(ctx, k_pc_fused, R0, sthreads, fsmem, pm, tmp0, nullptr, 0.f, pm.B2[0], 0, 0, R0, Qi, nullptr, x,
-              alpha, part);
+              alpha, part, ra);
     *nparts = R0;
+    *checked = true;
     return KR_OK;
   }
   if (lambda == 0.0 && N == 1) {
@@ -963,7 +1034,8 @@ kr_status sampled_pass(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const I
 // 100 tol; diverged when the step grew 3 times in a row and exceeds 16x its minimum.
 // h = {||step||^2, ||x||^2, non-finite flag}; rel_override >= 0 replaces ||step||/||x||
 // (the batched factor step passes its largest per-row ratio).
-StepCheck step_check(const double* h, double tol, double* prev_step, double* min_step, double* min_rel, int* grow,
+__host__ __device__ StepCheck step_check(const double* h, double tol, double* prev_step, double* min_step,
+                                         double* min_rel, int* grow,
                      int* since_min, double* rel_out, double rel_override) {
   const double step = sqrt(h[0]), xn = sqrt(h[1]);
   if (h[2] != 0.0 || !isfinite(step) || !isfinite(xn)) return STEP_NONFINITE;
@@ -984,6 +1056,7 @@ StepCheck step_check(const double* h, double tol, double* prev_step, double* min
   if (*since_min >= 8 && *min_rel <= 100.0 * tol) return STEP_FLOOR;
   return STEP_CONTINUE;
 }
+
 
 // Core Alg. 2 solve on device-resident inputs. Timings go to rep->t_ms if rep != NULL.
 kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const SolveCfg& cfg, uint64_t seed,
@@ -1021,6 +1094,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   nd.add<float>(mx);   // t1
   nd.add<double>(3 * (size_t)(nblk > 1024 ? nblk : 1024));
   nd.add<double>(16);
+  nd.add<RichState>(1);
   {
     Need sc = nd;
     kr_sketch_scratch_need(cfg.s, ncell, nd);
@@ -1054,6 +1128,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   bf.t1 = cv.take<float>(mx);
   bf.part = cv.take<double>(3 * (size_t)(nblk > 1024 ? nblk : 1024));
   bf.red = cv.take<double>(16);
+  bf.rich = cv.take<RichState>(1);
   {
     Carve sc = cv;
     KR_TRY(kr_sketch_fill(ctx, m, t, b, seed, call_id, 0, &sk, sc));
@@ -1064,40 +1139,87 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   KR_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
   double* h = (double*)ctx->hbuf;
   const int ublk = grid_cap(ctx, R, 256, 4);
-  int it = 0, grow = 0, converged = 0, since_min = 0;
-  double prev_step = INFINITY, rel = INFINITY, min_step = INFINITY, min_rel = INFINITY;
+  int it = 0, converged = 0;
+  double rel = INFINITY;
   kr_status st = KR_OK;
   const double* op = nullptr;
   int on = 0;
-  for (it = 1; it <= cfg.max_iter; ++it) {
+  KR_LAUNCH(ctx, k_rich_init, 1, 1, 0, bf.rich);
+  RichState* hs = reinterpret_cast<RichState*>(ctx->hbuf);
+  // One Richardson step and the stopping rule on the device (inside the graph the check
+  // also sets the loop condition).
+  unsigned int* ticket = reinterpret_cast<unsigned int*>(bf.red + 8);
+  KR_CUDA(ctx, cudaMemsetAsync(ticket, 0, sizeof(unsigned int), ctx->stream));
+  auto one_step = [&](cudaGraphConditionalHandle hnd, int use_hnd) -> kr_status {
     KR_TRY(sampled_pass(ctx, m, &sk, bf, nblk, true, &op, &on));
-    int np = 0;
-    KR_TRY(pc_step(ctx, t, cfg.lambda, bf.g, bf.x, (float)cfg.alpha, bf.d, bf.t0, bf.t1, ublk, bf.part, &np));
-    KR_TRY(kr_hbuf_reserve(ctx, sizeof(double) * (3 * (size_t)np + 8)));
-    h = (double*)ctx->hbuf;
-    KR_CUDA(ctx, cudaMemcpyAsync(h + 8, bf.part, 3 * (size_t)np * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    RichArgs ra;
+    ra.st = bf.rich;
+    ra.tol = cfg.tol;
+    ra.max_iter = cfg.max_iter;
+    ra.hnd = hnd;
+    ra.use_hnd = use_hnd;
+    ra.ticket = ticket;
+    return pc_step(ctx, t, cfg.lambda, bf.g, bf.x, (float)cfg.alpha, bf.d, bf.t0, bf.t1, ublk, bf.part, ra);
+  };
+  auto read_state = [&]() -> kr_status {
+    KR_CUDA(ctx, cudaMemcpyAsync(hs, bf.rich, sizeof(RichState), cudaMemcpyDeviceToHost, ctx->stream));
     KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    h[0] = h[1] = h[2] = 0.0;
-    for (int b = 0; b < np; ++b) {  // block order
-      h[0] += h[8 + 3 * b];
-      h[1] += h[8 + 3 * b + 1];
-      h[2] = fmax(h[2], h[8 + 3 * b + 2]);
+    return KR_OK;
+  };
+  // The first step runs from the host: it grows every buffer and sets every kernel
+  // attribute the steps need, so the captured steps allocate nothing.
+  KR_TRY(one_step(0, 0));
+  KR_TRY(read_state());
+  if (hs->status == STEP_CONTINUE && ctx->device_loop && !ctx->timing) {
+    // Steps 2.. as one graph: a conditional WHILE node whose body is one captured step;
+    // k_rich_check clears the condition on convergence, failure or max_iter.
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle hnd = 0;
+    bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+    ok = ok && cudaGraphConditionalHandleCreate(&hnd, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hnd;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    ok = ok && cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    int64_t per_step = 0;
+    if (ok && cudaStreamBeginCaptureToGraph(ctx->stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+      const int64_t l0 = ctx->launches;
+      const kr_status cs = one_step(hnd, 1);
+      cudaGraph_t captured = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &captured);
+      per_step = ctx->launches - l0;
+      ctx->launches = l0;
+      ok = cs == KR_OK && ce == cudaSuccess;
+    } else {
+      ok = false;
     }
-    StepCheck sc = step_check(h, cfg.tol, &prev_step, &min_step, &min_rel, &grow, &since_min, &rel, -1.0);
-    if (sc == STEP_NONFINITE) {
-      st = kr_fail(ctx, KR_ENONFINITE, "Richardson iterate became non-finite at iteration %d", it);
-      break;
+    ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (ok) {
+      const int it0 = hs->it;
+      KR_CUDA(ctx, cudaGraphLaunch(exec, ctx->stream));
+      KR_TRY(read_state());
+      ctx->launches += per_step * (hs->it - it0);
     }
-    if (sc == STEP_DIVERGED) {
-      st = kr_fail(ctx, KR_EDIVERGED, "Richardson step grew 3 times in a row past 16x its minimum (iteration %d)", it);
-      break;
-    }
-    if (sc == STEP_CONVERGED || sc == STEP_FLOOR) {
-      converged = sc == STEP_CONVERGED ? 1 : 2;
-      break;
-    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) cudaGetLastError();  // graphs unavailable: the host loop below takes over
   }
-  if (it > cfg.max_iter) it = cfg.max_iter;
+  while (hs->status == STEP_CONTINUE) {
+    KR_TRY(one_step(0, 0));
+    KR_TRY(read_state());
+  }
+  it = hs->it;
+  rel = hs->rel;
+  if (hs->status == STEP_NONFINITE) st = kr_fail(ctx, KR_ENONFINITE, "Richardson iterate became non-finite at iteration %d", it);
+  if (hs->status == STEP_DIVERGED)
+    st = kr_fail(ctx, KR_EDIVERGED, "Richardson step grew 3 times in a row past 16x its minimum (iteration %d)", it);
+  if (hs->status == STEP_CONVERGED) converged = 1;
+  if (hs->status == STEP_FLOOR) converged = 2;
   KR_CUDA(ctx, cudaEventRecord(ev[4], ctx->stream));
   // final sampled objective at the returned x (FP64 accumulation)
   KR_TRY(sampled_pass(ctx, m, &sk, bf, nblk, false, &op, &on));

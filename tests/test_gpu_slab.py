@@ -31,6 +31,7 @@ def _default_options():
     yield
     kr.set_option(kr.OPT_SLAB_PASS, 1)
     kr.set_option(kr.OPT_SLAB_TILE_ENTRIES, 16384)
+    kr.set_option(kr.OPT_DEVICE_LOOP, 1)
     kr.timing_enable(False)
 
 
@@ -139,9 +140,43 @@ def test_slab_pass_is_deterministic(budget):
     assert r1["obj_sampled"] == r2["obj_sampled"] and r1["iters"] == r2["iters"]
 
 
+@pytest.mark.parametrize("I,R,lam", [([64, 48, 40], [4, 3, 5], 0.0), ([40, 30, 50], [3, 4, 5], 0.3),
+                                     ([256, 256], [16, 16], 0.0)])
+def test_device_loop_matches_host_loop(I, R, lam):
+    """Richardson steps as one CUDA graph (device-side stopping rule) give the same iterate,
+    bit for bit, and the same iteration count as returning to the host after every step."""
+    As, b = _problem(I, R, "lognormal_rows", seed=25)
+    out = []
+    for loop in (1, 0):
+        kr.set_option(kr.OPT_DEVICE_LOOP, loop)
+        l0 = kr.launch_count()
+        if lam > 0:
+            x, rep = kr.kron_ridge([dev(A) for A in As], dev(b), lam, eps=0.1, seed=4, call_id=2, tol=1e-7,
+                                   max_iter=500)
+        else:
+            x, rep = kr.kron_regress([dev(A) for A in As], dev(b), eps=0.1, seed=4, call_id=2, tol=1e-7,
+                                     max_iter=500)
+        out.append((x, rep, kr.launch_count() - l0))
+    (xg, rg, lg), (xh, rh, lh) = out
+    assert torch.equal(xg, xh)
+    assert rg["iters"] == rh["iters"] and rg["converged"] == rh["converged"]
+    assert rg["obj_sampled"] == rh["obj_sampled"]
+    assert lg == lh  # launches inside the graph are counted per step
+
+
+def test_device_loop_stops_at_max_iter():
+    As, b = _problem([64, 48, 40], [4, 3, 5], "gauss", seed=26)
+    with pytest.raises(kr.KronError) as e:
+        kr.kron_regress([dev(A) for A in As], dev(b), eps=0.1, seed=4, call_id=2, tol=1e-14, max_iter=5)
+    assert e.value.name == "KR_ENOTCONV"
+    x, rep = kr.kron_regress([dev(A) for A in As], dev(b), eps=0.1, seed=4, call_id=2, tol=1e-14, max_iter=5,
+                             raise_notconv=False)
+    assert rep["iters"] == 5
+
+
 def test_set_option_rejects_bad_values():
     for key, val in [(kr.OPT_SLAB_PASS, 2), (kr.OPT_SLAB_TILE_ENTRIES, 100), (kr.OPT_SLAB_TILE_ENTRIES, (1 << 22) + 1),
-                     (99, 1)]:
+                     (kr.OPT_DEVICE_LOOP, 7), (99, 1)]:
         with pytest.raises(kr.KronError) as e:
             kr.set_option(key, val)
         assert e.value.name == "KR_EINVAL"
