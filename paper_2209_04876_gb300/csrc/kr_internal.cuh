@@ -85,6 +85,49 @@ kr_status kr_fail_cuda(kr_ctx* ctx, cudaError_t e, const char* what, const char*
     }                                                                                    \
   } while (0)
 
+// Programmatic dependent launch: a kernel launched with KR_LAUNCH_PDL may start (and run
+// its prologue) while the previous kernel on the stream finishes. Every such kernel calls
+// kr_pdl_wait() before it reads anything the previous kernels wrote (and before it
+// completes), and may call kr_pdl_trigger() once all its blocks have started, so that the
+// next kernel's blocks are scheduled as this one's retire. Without the launch attribute
+// both are no-ops.
+__device__ __forceinline__ void kr_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void kr_pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t kr_launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                          Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+#define KR_LAUNCH_PDL(ctx, kernel, grid, block, smem, ...)                                  \
+  do {                                                                                      \
+    cudaEvent_t _ea = nullptr, _eb = nullptr;                                               \
+    if ((ctx)->timing) {                                                                    \
+      _ea = kr_timing_event(ctx);                                                           \
+      _eb = kr_timing_event(ctx);                                                           \
+      cudaEventRecord(_ea, (ctx)->stream);                                                  \
+    }                                                                                       \
+    cudaError_t _e = kr_launch_pdl(kernel, dim3(grid), dim3(block), (smem), (ctx)->stream, __VA_ARGS__); \
+    (ctx)->launches++;                                                                      \
+    if (_e == cudaSuccess) _e = cudaGetLastError();                                         \
+    if (_e != cudaSuccess) return kr_fail_cuda((ctx), _e, #kernel, __FILE__, __LINE__);     \
+    if ((ctx)->timing) {                                                                    \
+      cudaEventRecord(_eb, (ctx)->stream);                                                  \
+      (ctx)->pending.push_back({kr_kind_of(#kernel), _ea, _eb});                            \
+    }                                                                                       \
+  } while (0)
+
 // Ensures the workspace holds at least `bytes` (synchronises when it grows).
 kr_status kr_ws_reserve(kr_ctx* ctx, size_t bytes);
 kr_status kr_hbuf_reserve(kr_ctx* ctx, size_t bytes);

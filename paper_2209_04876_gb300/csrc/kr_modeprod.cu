@@ -27,6 +27,8 @@ __global__ void __launch_bounds__(256) k_mode_product(const float* __restrict__ 
   constexpr int RJ = TJ / 16;  // rows per thread
   __shared__ __align__(16) float Bs[TK][TJ + 4];
   __shared__ __align__(16) float Xs[TK][TN + 4];
+  kr_pdl_trigger();
+  kr_pdl_wait();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int j0 = blockIdx.y * TJ;
   const int64_t n0 = (int64_t)blockIdx.x * TN;
@@ -121,6 +123,8 @@ __global__ void __launch_bounds__(256, 2) k_mode_product_q4(const float* __restr
   constexpr int RM = BM / 16;
   __shared__ __align__(16) float Bs[SG_BK][BM + 4];
   __shared__ __align__(16) float Xs[SG_BK][SG_BN + 4];
+  kr_pdl_trigger();
+  kr_pdl_wait();  // `in` is the previous kernel's output
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int j0 = blockIdx.y * BM;
   const int64_t n0 = (int64_t)blockIdx.x * SG_BN;
@@ -209,6 +213,8 @@ __global__ void __launch_bounds__(256, 2) k_mode_product_q4(const float* __restr
 
 // out[i] = sum_z part[z * n + i] in increasing z (deterministic split-K reduction).
 __global__ void k_splitk_reduce(const float* __restrict__ part, int S, int64_t n, float* __restrict__ out) {
+  kr_pdl_trigger();
+  kr_pdl_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float acc = 0.f;
     for (int z = 0; z < S; ++z) acc += part[(int64_t)z * n + i];
@@ -269,22 +275,22 @@ kr_status kr_mode_product(kr_ctx* ctx, const float* in, float* out, int64_t P, i
     }
     grid.z = (unsigned)S;
     if (BM == 32)
-      KR_LAUNCH(ctx, k_mode_product_q4<32>, grid, 256, 0, in, dst, P, K, Q, J, B, trans, kchunk, S > 1 ? outn : 0);
+      KR_LAUNCH_PDL(ctx, k_mode_product_q4<32>, grid, 256, 0, in, dst, P, K, Q, J, B, trans, kchunk, S > 1 ? outn : 0);
     else
-      KR_LAUNCH(ctx, k_mode_product_q4<64>, grid, 256, 0, in, dst, P, K, Q, J, B, trans, kchunk, S > 1 ? outn : 0);
+      KR_LAUNCH_PDL(ctx, k_mode_product_q4<64>, grid, 256, 0, in, dst, P, K, Q, J, B, trans, kchunk, S > 1 ? outn : 0);
     if (S > 1) {
       int rg = (int)((outn + 255) / 256);
       if (rg > ctx->num_sms * 8) rg = ctx->num_sms * 8;
-      KR_LAUNCH(ctx, k_splitk_reduce, rg, 256, 0, dst, S, outn, out);
+      KR_LAUNCH_PDL(ctx, k_splitk_reduce, rg, 256, 0, dst, S, outn, out);
     }
     return KR_OK;
   }
   if (J <= 32) {
     dim3 grid((unsigned)((NN + TN - 1) / TN), (unsigned)((J + 31) / 32));
-    KR_LAUNCH(ctx, k_mode_product<32>, grid, 256, 0, in, out, P, K, Q, J, B, trans);
+    KR_LAUNCH_PDL(ctx, k_mode_product<32>, grid, 256, 0, in, out, P, K, Q, J, B, trans);
   } else {
     dim3 grid((unsigned)((NN + TN - 1) / TN), (unsigned)((J + 63) / 64));
-    KR_LAUNCH(ctx, k_mode_product<64>, grid, 256, 0, in, out, P, K, Q, J, B, trans);
+    KR_LAUNCH_PDL(ctx, k_mode_product<64>, grid, 256, 0, in, out, P, K, Q, J, B, trans);
   }
   return KR_OK;
 }

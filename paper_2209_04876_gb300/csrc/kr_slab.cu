@@ -208,6 +208,8 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
   }
   for (int i = threadIdx.x; i < a.IT; i += blockDim.x) sInvp[i] = __ldg(a.invpT + i);
   __syncthreads();
+  kr_pdl_trigger();
+  kr_pdl_wait();  // X1 and the work counter come from the previous kernels
 
   const int team = threadIdx.x / SLAB_TEAM, tt = threadIdx.x % SLAB_TEAM;
   char* tb = sm + a.team_off + (size_t)team * a.team_bytes;
@@ -475,8 +477,6 @@ __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict
                                                       const float* __restrict__ zpart, const float* __restrict__ Aq,
                                                       int Rq, int zn, int nc, int64_t Pq, float* __restrict__ part,
                                                       uint32_t* __restrict__ counter) {
-  // the slab pass that produced zpart has finished (stream order): re-arm its work counter
-  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) *counter = 0u;
   __shared__ uint32_t s_ts[TR_MAXS + 1];
   __shared__ float s_z[TR_MAXS][TR_QP];
   __shared__ float s_a[TR_MAXS][KR_MAX_RANK];
@@ -490,6 +490,10 @@ __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict
     const int i = e / Rq, r = e - i * Rq;
     s_a[i][r] = Aq ? __ldg(Aq + (size_t)(i0 + i) * Rq + r) : 1.f;
   }
+  kr_pdl_trigger();
+  kr_pdl_wait();  // zpart: the slab pass has finished
+  // ... and its work counter can be re-armed for the next pass
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) *counter = 0u;
   __syncthreads();
   // Z of the chunk's slabs for this panel: tiles of one slab in order
 #pragma unroll 4
@@ -513,6 +517,8 @@ __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict
 }
 
 __global__ void k_tile_reduce2(const float* __restrict__ part, int nc, int64_t total, float* __restrict__ W) {
+  kr_pdl_trigger();
+  kr_pdl_wait();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     float s = 0.f;
     for (int c0 = 0; c0 < nc; c0 += 16) {  // loads of a batch in flight together, added in order
@@ -676,7 +682,7 @@ kr_status launch_slab_t(kr_ctx* ctx, const SlabArgs& a, size_t smem) {
     configured_dev = ctx->device;
     configured_bytes = smem;
   }
-  KR_LAUNCH(ctx, (k_slab<RTP, SMEM_A, OBJ>), ctx->num_sms, SLAB_TEAM * SLAB_TEAMS, smem, a);
+  KR_LAUNCH_PDL(ctx, (k_slab<RTP, SMEM_A, OBJ>), ctx->num_sms, SLAB_TEAM * SLAB_TEAMS, smem, a);
   return KR_OK;
 }
 
@@ -863,11 +869,11 @@ kr_status kr_tile_reduce(kr_ctx* ctx, kr_tiles* tl, const float* Aq, float* W) {
   const int zn = tl->R2 * tl->RT;
   const dim3 grid((unsigned)((zn + TR_QP - 1) / TR_QP), (unsigned)tl->nc, (unsigned)tl->Pq);
   float* part = tl->nc > 1 ? tl->zred : W;
-  KR_LAUNCH(ctx, k_tile_reduce1, grid, 256, 0, tl->tstart, tl->Iq, tl->zpart, Aq, tl->Rq, zn, tl->nc, tl->Pq, part,
-            tl->meta + 2);
+  KR_LAUNCH_PDL(ctx, k_tile_reduce1, grid, 256, 0, tl->tstart, tl->Iq, tl->zpart, Aq, tl->Rq, zn, tl->nc, tl->Pq,
+                part, tl->meta + 2);
   if (tl->nc > 1) {
     const int64_t total = tl->Pq * tl->Rq * zn;
-    KR_LAUNCH(ctx, k_tile_reduce2, grid_n(ctx, total), 256, 0, tl->zred, tl->nc, total, W);
+    KR_LAUNCH_PDL(ctx, k_tile_reduce2, grid_n(ctx, total), 256, 0, tl->zred, tl->nc, total, W);
   }
   return KR_OK;
 }

@@ -487,6 +487,8 @@ __global__ void __launch_bounds__(1024) k_pc_fused(PcModes pm, const float* __re
     }
   }
   for (int k = threadIdx.x; k < R0; k += blockDim.x) b0[k] = trans0 ? __ldg(B0 + k * R0 + j) : __ldg(B0 + j * R0 + k);
+  kr_pdl_trigger();
+  kr_pdl_wait();  // the gradient (and x) come from the previous kernels
   const int64_t tot = (int64_t)R0 * Q;
   if ((Q & 3) == 0) {
     const float4* in4 = reinterpret_cast<const float4*>(in);
@@ -929,18 +931,18 @@ kr_status pc_step_core(kr_ctx* ctx, const FactorTables& t, double lambda, float*
   KR_TRY(smem_fit(ctx, k_pc_fused, fsmem, &fused));
   if (fused) {
     if (lambda == 0.0) {
-      KR_LAUNCH(ctx, k_pc_fused, R0, sthreads, fsmem, pm, g, nullptr, 0.f, pm.B[0], 0, N > 1 ? 1 : 0, R0, Qi,
-                nullptr, x, alpha, part, ra);
+      KR_LAUNCH_PDL(ctx, k_pc_fused, R0, sthreads, fsmem, pm, g, (const float*)nullptr, 0.f, pm.B[0], 0,
+                    N > 1 ? 1 : 0, R0, Qi, (float*)nullptr, x, alpha, part, ra);
       *nparts = R0;
       *checked = true;
       return KR_OK;
     }
     RichArgs none = ra;
     none.st = nullptr;
-    KR_LAUNCH(ctx, k_pc_fused, R0, sthreads, fsmem, pm, g, x, (float)lambda, pm.B[0], 1, 1, R0, Qi, tmp0, nullptr,
-              0.f, part, none);
-    KR_LAUNCH(ctx, k_pc_fused, R0, sthreads, fsmem, pm, tmp0, nullptr, 0.f, pm.B2[0], 0, 0, R0, Qi, nullptr, x,
-              alpha, part, ra);
+    KR_LAUNCH_PDL(ctx, k_pc_fused, R0, sthreads, fsmem, pm, g, (const float*)x, (float)lambda, pm.B[0], 1, 1, R0,
+                  Qi, tmp0, (float*)nullptr, 0.f, part, none);
+    KR_LAUNCH_PDL(ctx, k_pc_fused, R0, sthreads, fsmem, pm, (const float*)tmp0, (const float*)nullptr, 0.f,
+                  pm.B2[0], 0, 0, R0, Qi, (float*)nullptr, x, alpha, part, ra);
     *nparts = R0;
     *checked = true;
     return KR_OK;
