@@ -473,6 +473,7 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
 // in order.
 constexpr int TR_MAXS = 64;  // slabs per chunk at most
 constexpr int TR_QP = 64;    // columns per block
+constexpr int TR_TB = 60;    // tile rows staged per batch (keeps the block under 48 KB)
 __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict__ tstart, int Iq,
                                                       const float* __restrict__ zpart, const float* __restrict__ Aq,
                                                       int Rq, int zn, int nc, int64_t Pq, float* __restrict__ part,
@@ -480,6 +481,7 @@ __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict
   __shared__ uint32_t s_ts[TR_MAXS + 1];
   __shared__ float s_z[TR_MAXS][TR_QP];
   __shared__ float s_a[TR_MAXS][KR_MAX_RANK];
+  __shared__ __align__(16) float s_t[TR_TB][TR_QP];
   const int64_t pq = blockIdx.z;
   const int c = blockIdx.y;
   const int qb = blockIdx.x * TR_QP;
@@ -490,21 +492,44 @@ __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict
     const int i = e / Rq, r = e - i * Rq;
     s_a[i][r] = Aq ? __ldg(Aq + (size_t)(i0 + i) * Rq + r) : 1.f;
   }
+  for (int e = threadIdx.x; e < S * TR_QP; e += blockDim.x) (&s_z[0][0])[e] = 0.f;
   kr_pdl_trigger();
   kr_pdl_wait();  // zpart: the slab pass has finished
   // ... and its work counter can be re-armed for the next pass
   if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) *counter = 0u;
   __syncthreads();
-  // Z of the chunk's slabs for this panel: tiles of one slab in order
-#pragma unroll 4
-  for (int e = threadIdx.x; e < S * TR_QP; e += blockDim.x) {
-    const int i = e / TR_QP, qq = e - i * TR_QP, q = qb + qq;
-    float z = 0.f;
-    if (q < zn)
-      for (uint32_t t = s_ts[i]; t < s_ts[i + 1]; ++t) z += __ldg(zpart + (size_t)t * zn + q);
-    s_z[i][qq] = z;
+  // Z of the chunk's slabs for this panel, tiles of one slab added in tile order. The
+  // chunk's tiles are contiguous; a batch of tile rows is staged with independent loads
+  // (16 bytes each where the row layout allows), then every (slab, column) adds the
+  // batch's tiles of its slab.
+  const uint32_t t0 = s_ts[0], t1 = s_ts[S];
+  const bool vec = (zn & 3) == 0;
+  for (uint32_t tb = t0; tb < t1; tb += TR_TB) {
+    const int nt = (int)min((uint32_t)TR_TB, t1 - tb);
+    if (vec) {
+      for (int e = threadIdx.x; e < nt * (TR_QP / 4); e += blockDim.x) {
+        const int tl = e / (TR_QP / 4), c4 = e - tl * (TR_QP / 4), q = qb + 4 * c4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q < zn) v = __ldg(reinterpret_cast<const float4*>(zpart + (size_t)(tb + tl) * zn + q));
+        *reinterpret_cast<float4*>(&s_t[tl][4 * c4]) = v;
+      }
+    } else {
+      for (int e = threadIdx.x; e < nt * TR_QP; e += blockDim.x) {
+        const int tl = e / TR_QP, qq = e - tl * TR_QP, q = qb + qq;
+        s_t[tl][qq] = q < zn ? __ldg(zpart + (size_t)(tb + tl) * zn + q) : 0.f;
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < S * TR_QP; e += blockDim.x) {
+      const int i = e / TR_QP, qq = e - i * TR_QP;
+      const uint32_t lo = max(s_ts[i], tb), hi = min(s_ts[i + 1], tb + (uint32_t)nt);
+      if (lo >= hi) continue;
+      float z = s_z[i][qq];
+      for (uint32_t t = lo; t < hi; ++t) z += s_t[t - tb][qq];
+      s_z[i][qq] = z;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   // part[c][pq][r][q] = sum_i Aq[i0 + i, r] Z[i, q] in slab order
   float* out = part + ((size_t)c * Pq + pq) * Rq * zn;
   for (int e = threadIdx.x; e < Rq * TR_QP; e += blockDim.x) {
@@ -516,9 +541,38 @@ __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict
   }
 }
 
-__global__ void k_tile_reduce2(const float* __restrict__ part, int nc, int64_t total, float* __restrict__ W) {
+// W = sum over the nc chunks of part, in chunk order; four columns per thread when the
+// length allows, the loads of a batch of chunks in flight together.
+__global__ void __launch_bounds__(128) k_tile_reduce2(const float* __restrict__ part, int nc, int64_t total,
+                                                      float* __restrict__ W) {
   kr_pdl_trigger();
   kr_pdl_wait();
+  if ((total & 3) == 0) {
+    const int64_t n4 = total >> 2;
+    const float4* p4 = reinterpret_cast<const float4*>(part);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x) {
+      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int c0 = 0; c0 < nc; c0 += 16) {
+        float4 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = c0 + c < nc ? __ldg(p4 + (size_t)(c0 + c) * n4 + e) : s;
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          if (c0 + c < nc) {
+            if (c0 + c == 0) {
+              s = v[c];
+            } else {
+              s.x += v[c].x;
+              s.y += v[c].y;
+              s.z += v[c].z;
+              s.w += v[c].w;
+            }
+          }
+      }
+      reinterpret_cast<float4*>(W)[e] = s;
+    }
+    return;
+  }
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     float s = 0.f;
     for (int c0 = 0; c0 < nc; c0 += 16) {  // loads of a batch in flight together, added in order
@@ -873,7 +927,8 @@ kr_status kr_tile_reduce(kr_ctx* ctx, kr_tiles* tl, const float* Aq, float* W) {
                 part, tl->meta + 2);
   if (tl->nc > 1) {
     const int64_t total = tl->Pq * tl->Rq * zn;
-    KR_LAUNCH_PDL(ctx, k_tile_reduce2, grid_n(ctx, total), 256, 0, tl->zred, tl->nc, total, W);
+    const int64_t work = (total & 3) == 0 ? total / 4 : total;
+    KR_LAUNCH_PDL(ctx, k_tile_reduce2, grid_n(ctx, work, 128), 128, 0, tl->zred, tl->nc, total, W);
   }
   return KR_OK;
 }

@@ -214,18 +214,20 @@ __global__ void k_sub_lambda_x(float* __restrict__ g, const float* __restrict__ 
     g[i] = fmaf(-lambda, x[i], g[i]);
 }
 
-// {||step||^2, ||x||^2, non-finite flag} of the block's elements in FP64, as fixed-order
-// trees (warp shuffles, then one warp over the warp partials), written to
-// part[3 * blockIdx.x + 0..2]; the host adds the blocks' partials in block order. Called
-// by all threads of a block of at most 1024 threads, once per kernel.
-__device__ __forceinline__ void step_norms_block(double s1, double s2, double bad, double* __restrict__ part) {
-  __shared__ double red[3][32];
+// {||step||^2, ||x||^2, non-finite flag} of the block's elements, written to
+// part[3 * blockIdx.x + 0..2] in FP64. Inside the block the sums are FP32 fixed-order trees
+// (per thread, warp shuffles, then one warp over the warp sums): FP64 arithmetic issues at
+// a small fraction of the FP32 rate on this part, and a stopping-rule norm needs no more
+// than FP32's relative precision (about 1e-6 after the tree). The blocks' partials are
+// added in FP64. Called by all threads of a block of at most 1024 threads, once per kernel.
+__device__ __forceinline__ void step_norms_block(float s1, float s2, float bad, double* __restrict__ part) {
+  __shared__ float red[3][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     s1 += __shfl_xor_sync(0xffffffffu, s1, off);
     s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-    bad = fmax(bad, __shfl_xor_sync(0xffffffffu, bad, off));
+    bad = fmaxf(bad, __shfl_xor_sync(0xffffffffu, bad, off));
   }
   if (lane == 0) {
     red[0][w] = s1;
@@ -234,18 +236,17 @@ __device__ __forceinline__ void step_norms_block(double s1, double s2, double ba
   }
   __syncthreads();
   if (w == 0) {
-    double a = lane < nw ? red[0][lane] : 0.0, b = lane < nw ? red[1][lane] : 0.0,
-           c = lane < nw ? red[2][lane] : 0.0;
+    float a = lane < nw ? red[0][lane] : 0.f, b = lane < nw ? red[1][lane] : 0.f, c = lane < nw ? red[2][lane] : 0.f;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
       a += __shfl_xor_sync(0xffffffffu, a, off);
       b += __shfl_xor_sync(0xffffffffu, b, off);
-      c = fmax(c, __shfl_xor_sync(0xffffffffu, c, off));
+      c = fmaxf(c, __shfl_xor_sync(0xffffffffu, c, off));
     }
     if (lane == 0) {
-      part[3 * blockIdx.x + 0] = a;
-      part[3 * blockIdx.x + 1] = b;
-      part[3 * blockIdx.x + 2] = c;
+      part[3 * blockIdx.x + 0] = (double)a;
+      part[3 * blockIdx.x + 1] = (double)b;
+      part[3 * blockIdx.x + 2] = (double)c;
     }
   }
 }
@@ -253,14 +254,14 @@ __device__ __forceinline__ void step_norms_block(double s1, double s2, double ba
 // x <- x + alpha d, with the step norms (step_norms_block).
 __global__ void __launch_bounds__(256) k_update_reduce(float* __restrict__ x, const float* __restrict__ d, float alpha,
                                                        int64_t n, double* __restrict__ part) {
-  double s1 = 0.0, s2 = 0.0, bad = 0.0;
+  float s1 = 0.f, s2 = 0.f, bad = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float st = alpha * d[i];
     const float xn = x[i] + st;
     x[i] = xn;
-    s1 += (double)st * st;
-    s2 += (double)xn * xn;
-    if (!isfinite(xn)) bad = 1.0;
+    s1 = fmaf(st, st, s1);
+    s2 = fmaf(xn, xn, s2);
+    if (!isfinite(xn)) bad = 1.f;
   }
   step_norms_block(s1, s2, bad, part);
 }
@@ -273,36 +274,28 @@ struct RichState {
   int grow, since_min, it, status;  // status: StepCheck (0 = continue)
 };
 
-// The stopping rule of Alg. 2 after one step, by one block (at least 256 threads): the
-// step's block partials summed strided per thread and then by a fixed tree, the rule
-// applied to the state, the iteration counted (max_iter ends the loop in any case) and,
-// inside the graph, the loop condition set.
+// The stopping rule of Alg. 2 after one step, evaluated by the first warp of a block: the
+// step's block partials summed in FP64 (strided per lane, then warp shuffles: a fixed
+// order), the rule applied to the state, the iteration counted (max_iter ends the loop
+// in any case) and, inside the graph, the loop condition set.
 __device__ void rich_check_block(const double* __restrict__ part, int np, double tol, int max_iter,
                                  RichState* __restrict__ st, cudaGraphConditionalHandle hnd, int use_hnd) {
-  __shared__ double r[3][256];
-  const int t = threadIdx.x;
-  if (t < 256) {
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int k = t; k < np; k += 256) {
-      a += __ldcg(part + 3 * k + 0);
-      b += __ldcg(part + 3 * k + 1);
-      c = fmax(c, __ldcg(part + 3 * k + 2));
-    }
-    r[0][t] = a;
-    r[1][t] = b;
-    r[2][t] = c;
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int k = lane; k < np; k += 32) {
+    a += __ldcg(part + 3 * k + 0);
+    b += __ldcg(part + 3 * k + 1);
+    c = fmax(c, __ldcg(part + 3 * k + 2));
   }
-  __syncthreads();
-  for (int off = 128; off > 0; off >>= 1) {
-    if (t < off) {
-      r[0][t] += r[0][t + off];
-      r[1][t] += r[1][t + off];
-      r[2][t] = fmax(r[2][t], r[2][t + off]);
-    }
-    __syncthreads();
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, off);
+    b += __shfl_xor_sync(0xffffffffu, b, off);
+    c = fmax(c, __shfl_xor_sync(0xffffffffu, c, off));
   }
-  if (t == 0) {
-    const double h[3] = {r[0][0], r[1][0], r[2][0]};
+  if (lane == 0) {
+    const double h[3] = {a, b, c};
     st->h[0] = h[0];
     st->h[1] = h[1];
     st->h[2] = h[2];
@@ -325,7 +318,7 @@ __global__ void k_rich_init(RichState* st) {
 // Sums the step's block partials (strided per thread, then a fixed tree), applies the
 // stopping rule, counts the iteration (max_iter ends the loop in any case) and, inside
 // the graph, sets the loop condition.
-__global__ void __launch_bounds__(256) k_rich_check(const double* __restrict__ part, int np, double tol, int max_iter,
+__global__ void __launch_bounds__(32) k_rich_check(const double* __restrict__ part, int np, double tol, int max_iter,
                                                     RichState* __restrict__ st, cudaGraphConditionalHandle hnd,
                                                     int use_hnd) {
   rich_check_block(part, np, tol, max_iter, st, hnd, use_hnd);
@@ -375,7 +368,7 @@ __global__ void __launch_bounds__(256) k_pc_mode0(const float* __restrict__ in, 
     const int j = e / R0, k = e - j * R0;
     sB[e] = trans ? __ldg(B0 + k * R0 + j) : __ldg(B0 + e);  // sB[j * R0 + k] = B0'[j, k]
   }
-  double s1 = 0.0, s2 = 0.0, bad = 0.0;
+  float s1 = 0.f, s2 = 0.f, bad = 0.f;
   for (int q0 = blockIdx.x * PC_TQ; q0 < Q; q0 += gridDim.x * PC_TQ) {
     const int tq = min(PC_TQ, Q - q0);
     __syncthreads();
@@ -401,9 +394,9 @@ __global__ void __launch_bounds__(256) k_pc_mode0(const float* __restrict__ in, 
         const float st = alpha * acc;
         const float xn = x[gi] + st;
         x[gi] = xn;
-        s1 += (double)st * st;
-        s2 += (double)xn * xn;
-        if (!isfinite(xn)) bad = 1.0;
+        s1 = fmaf(st, st, s1);
+        s2 = fmaf(xn, xn, s2);
+        if (!isfinite(xn)) bad = 1.f;
       } else {
         out[gi] = acc;
       }
@@ -415,6 +408,8 @@ __global__ void __launch_bounds__(256) k_pc_mode0(const float* __restrict__ in, 
 // In shared memory: t (R_1 x ... x R_{N-1}) <- B applied along every mode of the slab
 // (B staged in sB transposed: mode m at offset boff[m], entry (k, j) = B'[j, k], so lanes
 // with consecutive output rows j read consecutive words, and lanes sharing j broadcast).
+// With R_m a multiple of 4 and aligned operands a thread forms four consecutive output rows
+// from one 16-byte load of B per k, and lanes take consecutive trailing positions q.
 __device__ void pc_slab_modes(const PcModes& pm, const float* sB, const int* boff, float* t, float* u, int Q) {
   float* src = t;
   float* dst = u;
@@ -423,16 +418,50 @@ __device__ void pc_slab_modes(const PcModes& pm, const float* sB, const int* bof
     const int Rm = pm.R[m];
     const int Qm = Q / P / Rm;  // entries after mode m
     const float* Bm = sB + boff[m];
-    for (int e = threadIdx.x; e < Q; e += blockDim.x) {
-      const int p = e / (Rm * Qm);
-      const int rest = e - p * Rm * Qm;
-      const int jj = rest / Qm;
-      const int qq = rest - jj * Qm;
-      const float* col = src + p * Rm * Qm + qq;
-      const float* bcol = Bm + jj;
-      float acc = 0.f;
-      for (int k = 0; k < Rm; ++k) acc = fmaf(bcol[k * Rm], col[k * Qm], acc);
-      dst[e] = acc;
+    // the vector path reads B and (for the last mode) writes dst 16 bytes at a time: both
+    // addresses must be 16-byte aligned, which the caller's layout does not guarantee
+    const bool vec = (Rm & 3) == 0 && (reinterpret_cast<uintptr_t>(Bm) & 15) == 0 &&
+                     (Qm != 1 || (reinterpret_cast<uintptr_t>(dst) & 15) == 0);
+    if (vec) {
+      const int R4 = Rm >> 2;
+      const int items = Q >> 2;
+      for (int e = threadIdx.x; e < items; e += blockDim.x) {
+        const int qq = e % Qm;
+        const int rest = e / Qm;
+        const int jq = rest % R4;
+        const int p = rest / R4;
+        const float* col = src + (size_t)p * Rm * Qm + qq;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < Rm; ++k) {
+          const float v = col[k * Qm];
+          const float4 bk = *reinterpret_cast<const float4*>(Bm + k * Rm + 4 * jq);
+          acc.x = fmaf(bk.x, v, acc.x);
+          acc.y = fmaf(bk.y, v, acc.y);
+          acc.z = fmaf(bk.z, v, acc.z);
+          acc.w = fmaf(bk.w, v, acc.w);
+        }
+        float* o = dst + (size_t)p * Rm * Qm + (4 * jq) * Qm + qq;
+        if (Qm == 1) {
+          *reinterpret_cast<float4*>(o) = acc;
+        } else {
+          o[0] = acc.x;
+          o[Qm] = acc.y;
+          o[2 * Qm] = acc.z;
+          o[3 * Qm] = acc.w;
+        }
+      }
+    } else {
+      for (int e = threadIdx.x; e < Q; e += blockDim.x) {
+        const int p = e / (Rm * Qm);
+        const int rest = e - p * Rm * Qm;
+        const int jj = rest / Qm;
+        const int qq = rest - jj * Qm;
+        const float* col = src + p * Rm * Qm + qq;
+        const float* bcol = Bm + jj;
+        float acc = 0.f;
+        for (int k = 0; k < Rm; ++k) acc = fmaf(bcol[k * Rm], col[k * Qm], acc);
+        dst[e] = acc;
+      }
     }
     __syncthreads();
     float* tmp = src;
@@ -540,15 +569,15 @@ __global__ void __launch_bounds__(1024) k_pc_fused(PcModes pm, const float* __re
       pc_slab_modes(pm, sB, boff2, t, u, Q);
     }
   }
-  double s1 = 0.0, s2 = 0.0, bad = 0.0;
+  float s1 = 0.f, s2 = 0.f, bad = 0.f;
   for (int e = threadIdx.x; e < Q; e += blockDim.x) {
     if (x) {
       const float st = alpha * t[e];
       const float xn = x[(int64_t)j * Q + e] + st;
       x[(int64_t)j * Q + e] = xn;
-      s1 += (double)st * st;
-      s2 += (double)xn * xn;
-      if (!isfinite(xn)) bad = 1.0;
+      s1 = fmaf(st, st, s1);
+      s2 = fmaf(xn, xn, s2);
+      if (!isfinite(xn)) bad = 1.f;
     } else {
       out[(int64_t)j * Q + e] = t[e];
     }
@@ -622,15 +651,15 @@ __global__ void __launch_bounds__(1024) k_pc_slab(PcModes pm, const float* __res
     __syncthreads();
     pc_slab_modes(pm, sB, boff2, t, u, Q);
   }
-  double s1 = 0.0, s2 = 0.0, bad = 0.0;
+  float s1 = 0.f, s2 = 0.f, bad = 0.f;
   for (int e = threadIdx.x; e < Q; e += blockDim.x) {
     if (x) {
       const float st = alpha * t[e];
       const float xn = x[(int64_t)j * Q + e] + st;
       x[(int64_t)j * Q + e] = xn;
-      s1 += (double)st * st;
-      s2 += (double)xn * xn;
-      if (!isfinite(xn)) bad = 1.0;
+      s1 = fmaf(st, st, s1);
+      s2 = fmaf(xn, xn, s2);
+      if (!isfinite(xn)) bad = 1.f;
     } else {
       out[(int64_t)j * Q + e] = t[e];
     }
@@ -884,7 +913,7 @@ kr_status pc_step(kr_ctx* ctx, const FactorTables& t, double lambda, float* g, f
   int np = 0;
   bool checked = false;
   KR_TRY(pc_step_core(ctx, t, lambda, g, x, alpha, tmp0, tmp1, tmp2, ublk, part, ra, &np, &checked));
-  if (!checked) KR_LAUNCH(ctx, k_rich_check, 1, 256, 0, part, np, ra.tol, ra.max_iter, ra.st, ra.hnd, ra.use_hnd);
+  if (!checked) KR_LAUNCH(ctx, k_rich_check, 1, 32, 0, part, np, ra.tol, ra.max_iter, ra.st, ra.hnd, ra.use_hnd);
   return KR_OK;
 }
 

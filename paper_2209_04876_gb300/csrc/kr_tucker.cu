@@ -215,24 +215,27 @@ __global__ void k_gauss_jordan(const double* __restrict__ C, int n, float* __res
 }
 
 // z <- z - alpha d, one block per row; rowstat[r] = {||step||^2, ||z||^2, non-finite}.
+// The sums inside the block are FP32 fixed-order trees (FP64 issues at a small fraction of
+// the FP32 rate here; a stopping-rule norm needs no more than FP32's relative precision);
+// rowstat holds them in FP64 for the sums over rows.
 __global__ void k_row_update(float* __restrict__ z, const float* __restrict__ d, float alpha, int L,
                              double* __restrict__ rowstat) {
   const int64_t base = (int64_t)blockIdx.x * L;
-  double s1 = 0.0, s2 = 0.0, bad = 0.0;
+  float s1 = 0.f, s2 = 0.f, bad = 0.f;
   for (int k = threadIdx.x; k < L; k += blockDim.x) {
     const float st = alpha * d[base + k];
     const float zn = z[base + k] - st;
     z[base + k] = zn;
-    s1 += (double)st * st;
-    s2 += (double)zn * zn;
-    if (!isfinite(zn)) bad = 1.0;
+    s1 = fmaf(st, st, s1);
+    s2 = fmaf(zn, zn, s2);
+    if (!isfinite(zn)) bad = 1.f;
   }
-  __shared__ double red[3][32];
+  __shared__ float red[3][32];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     s1 += __shfl_xor_sync(0xffffffffu, s1, off);
     s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-    bad = fmax(bad, __shfl_xor_sync(0xffffffffu, bad, off));
+    bad = fmaxf(bad, __shfl_xor_sync(0xffffffffu, bad, off));
   }
   if ((threadIdx.x & 31) == 0) {
     red[0][threadIdx.x >> 5] = s1;
@@ -241,15 +244,15 @@ __global__ void k_row_update(float* __restrict__ z, const float* __restrict__ d,
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0, b = 0, c = 0;
+    float a = 0.f, b = 0.f, c = 0.f;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
       a += red[0][k];
       b += red[1][k];
-      c = fmax(c, red[2][k]);
+      c = fmaxf(c, red[2][k]);
     }
-    rowstat[3 * (int64_t)blockIdx.x + 0] = a;
-    rowstat[3 * (int64_t)blockIdx.x + 1] = b;
-    rowstat[3 * (int64_t)blockIdx.x + 2] = c;
+    rowstat[3 * (int64_t)blockIdx.x + 0] = (double)a;
+    rowstat[3 * (int64_t)blockIdx.x + 1] = (double)b;
+    rowstat[3 * (int64_t)blockIdx.x + 2] = (double)c;
   }
 }
 
