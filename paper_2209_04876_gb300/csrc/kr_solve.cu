@@ -266,20 +266,65 @@ __global__ void __launch_bounds__(256) k_update_reduce(float* __restrict__ x, co
   step_norms_block(s1, s2, bad, part);
 }
 
-// Richardson state on the device: the stopping rule of Alg. 2 is evaluated by k_rich_check
-// after every step, so a run of iterations needs no host round trip.
+// Richardson state on the device: the stopping rule of Alg. 2 is evaluated on the device
+// after every step, so a run of iterations needs no host round trip. The rule works on
+// squared norms (no FP64 square root on the device; one divide for the ratio):
+// ||step|| <= tol ||x||  <=>  h0 <= tol^2 h1, and the step comparisons of the guards
+// compare squares. The host takes sqrt(h0 / h1) of the last step for the report.
 struct RichState {
   double h[3];  // last {||step||^2, ||x||^2, non-finite flag}
-  double prev_step, min_step, min_rel, rel;
+  double prev_h0, min_h0, min_q;  // previous and smallest ||step||^2, smallest h0 / h1
   int grow, since_min, it, status;  // status: StepCheck (0 = continue)
 };
 
+// The state fields the rule reads, fetched once per kernel right after its dependency
+// wait (only the last block of a step writes the state, at its very end), so the check
+// does not wait for them.
+struct RichSnap {
+  double prev_h0, min_h0, min_q;
+  int grow, since_min, it;
+};
+__device__ __forceinline__ RichSnap rich_load(const RichState* st) {
+  RichSnap r;
+  r.prev_h0 = __ldcg(&st->prev_h0);
+  r.min_h0 = __ldcg(&st->min_h0);
+  r.min_q = __ldcg(&st->min_q);
+  r.grow = __ldcg(&st->grow);
+  r.since_min = __ldcg(&st->since_min);
+  r.it = __ldcg(&st->it);
+  return r;
+}
+
+// The rule after one step: the same guards as step_check (converged, diverged: three
+// growths in a row past 16x the smallest step, floor: no new smallest step for 8 steps
+// with the ratio once within 100 tol), on squares.
+__device__ int step_check_sq(const double* h, double tol, RichSnap& r) {
+  const double h0 = h[0], h1 = h[1];
+  if (h[2] != 0.0 || !isfinite(h0) || !isfinite(h1)) return STEP_NONFINITE;
+  const double q = h1 > 0.0 ? h0 / h1 : (h0 == 0.0 ? 0.0 : INFINITY);
+  if (q <= tol * tol) return STEP_CONVERGED;
+  if (h0 < r.min_h0) {
+    r.min_h0 = h0;
+    r.since_min = 0;
+  } else {
+    ++r.since_min;
+  }
+  if (q < r.min_q) r.min_q = q;
+  r.grow = (h0 > r.prev_h0) ? r.grow + 1 : 0;
+  r.prev_h0 = h0;
+  if (r.grow >= 3 && h0 > 256.0 * r.min_h0) return STEP_DIVERGED;
+  if (r.since_min >= 8 && r.min_q <= 1e4 * tol * tol) return STEP_FLOOR;
+  return STEP_CONTINUE;
+}
+
 // The stopping rule of Alg. 2 after one step, evaluated by the first warp of a block: the
 // step's block partials summed in FP64 (strided per lane, then warp shuffles: a fixed
-// order), the rule applied to the state, the iteration counted (max_iter ends the loop
-// in any case) and, inside the graph, the loop condition set.
+// order), the rule applied to the state (snapshot `snap`, valid in thread 0), the
+// iteration counted (max_iter ends the loop in any case) and, inside the graph, the loop
+// condition set.
 __device__ void rich_check_block(const double* __restrict__ part, int np, double tol, int max_iter,
-                                 RichState* __restrict__ st, cudaGraphConditionalHandle hnd, int use_hnd) {
+                                 RichState* __restrict__ st, RichSnap snap, cudaGraphConditionalHandle hnd,
+                                 int use_hnd) {
   if (threadIdx.x >= 32) return;
   const int lane = threadIdx.x;
   double a = 0.0, b = 0.0, c = 0.0;
@@ -296,13 +341,18 @@ __device__ void rich_check_block(const double* __restrict__ part, int np, double
   }
   if (lane == 0) {
     const double h[3] = {a, b, c};
+    int status = step_check_sq(h, tol, snap);
+    snap.it += 1;
+    if (status == STEP_CONTINUE && snap.it >= max_iter) status = STEP_MAXITER;
     st->h[0] = h[0];
     st->h[1] = h[1];
     st->h[2] = h[2];
-    int status = step_check(h, tol, &st->prev_step, &st->min_step, &st->min_rel, &st->grow, &st->since_min, &st->rel,
-                            -1.0);
-    st->it += 1;
-    if (status == STEP_CONTINUE && st->it >= max_iter) status = STEP_MAXITER;
+    st->prev_h0 = snap.prev_h0;
+    st->min_h0 = snap.min_h0;
+    st->min_q = snap.min_q;
+    st->grow = snap.grow;
+    st->since_min = snap.since_min;
+    st->it = snap.it;
     st->status = status;
     if (use_hnd) cudaGraphSetConditional(hnd, status == STEP_CONTINUE ? 1u : 0u);
   }
@@ -310,18 +360,20 @@ __device__ void rich_check_block(const double* __restrict__ part, int np, double
 
 __global__ void k_rich_init(RichState* st) {
   st->h[0] = st->h[1] = st->h[2] = 0.0;
-  st->prev_step = st->min_step = st->min_rel = st->rel = INFINITY;
+  st->prev_h0 = st->min_h0 = st->min_q = INFINITY;
   st->grow = st->since_min = st->it = 0;
   st->status = STEP_CONTINUE;
 }
 
-// Sums the step's block partials (strided per thread, then a fixed tree), applies the
-// stopping rule, counts the iteration (max_iter ends the loop in any case) and, inside
-// the graph, sets the loop condition.
+// Sums the step's block partials, applies the stopping rule, counts the iteration (max_iter
+// ends the loop in any case) and, inside the graph, sets the loop condition.
 __global__ void __launch_bounds__(32) k_rich_check(const double* __restrict__ part, int np, double tol, int max_iter,
                                                     RichState* __restrict__ st, cudaGraphConditionalHandle hnd,
                                                     int use_hnd) {
-  rich_check_block(part, np, tol, max_iter, st, hnd, use_hnd);
+  kr_pdl_wait();
+  RichSnap snap = {};
+  if (threadIdx.x == 0) snap = rich_load(st);
+  rich_check_block(part, np, tol, max_iter, st, snap, hnd, use_hnd);
 }
 
 // Stopping-rule arguments handed to the kernel that ends a step.
@@ -405,16 +457,18 @@ __global__ void __launch_bounds__(256) k_pc_mode0(const float* __restrict__ in, 
   if (x) step_norms_block(s1, s2, bad, part);
 }
 
-// In shared memory: t (R_1 x ... x R_{N-1}) <- B applied along every mode of the slab
-// (B staged in sB transposed: mode m at offset boff[m], entry (k, j) = B'[j, k], so lanes
-// with consecutive output rows j read consecutive words, and lanes sharing j broadcast).
-// With R_m a multiple of 4 and aligned operands a thread forms four consecutive output rows
-// from one 16-byte load of B per k, and lanes take consecutive trailing positions q.
-__device__ void pc_slab_modes(const PcModes& pm, const float* sB, const int* boff, float* t, float* u, int Q) {
+// In shared memory: t (P0 x R_m0 x ... x R_{N-1}, Q entries) <- B applied along modes
+// m0..N-1 (B staged in sB transposed: mode m at offset boff[m], entry (k, j) = B'[j, k], so
+// lanes with consecutive output rows j read consecutive words, and lanes sharing j
+// broadcast). With R_m a multiple of 4 and aligned operands a thread forms four
+// consecutive output rows from one 16-byte load of B per k, and lanes take consecutive
+// trailing positions q.
+__device__ void pc_modes_from(const PcModes& pm, const float* sB, const int* boff, float* t, float* u, int Q, int m0,
+                              int P0) {
   float* src = t;
   float* dst = u;
-  int P = 1;
-  for (int m = 1; m < pm.N; ++m) {
+  int P = P0;
+  for (int m = m0; m < pm.N; ++m) {
     const int Rm = pm.R[m];
     const int Qm = Q / P / Rm;  // entries after mode m
     const float* Bm = sB + boff[m];
@@ -475,6 +529,12 @@ __device__ void pc_slab_modes(const PcModes& pm, const float* sB, const int* bof
   }
 }
 
+// A whole slab of modes 1..N-1.
+__device__ __forceinline__ void pc_slab_modes(const PcModes& pm, const float* sB, const int* boff, float* t, float* u,
+                                              int Q) {
+  pc_modes_from(pm, sB, boff, t, u, Q, 1, 1);
+}
+
 // The whole step in one kernel when the iterate fits in shared memory: block j stages
 // in - lambda xl (all R_1 x Q entries), forms slab j of the first-mode product from row j
 // of B0', applies the other modes (rest != 0; for lambda > 0 also the diagonal and the
@@ -518,6 +578,8 @@ __global__ void __launch_bounds__(1024) k_pc_fused(PcModes pm, const float* __re
   for (int k = threadIdx.x; k < R0; k += blockDim.x) b0[k] = trans0 ? __ldg(B0 + k * R0 + j) : __ldg(B0 + j * R0 + k);
   kr_pdl_trigger();
   kr_pdl_wait();  // the gradient (and x) come from the previous kernels
+  RichSnap snap = {};
+  if (threadIdx.x == 0 && x && ra.st) snap = rich_load(ra.st);
   const int64_t tot = (int64_t)R0 * Q;
   if ((Q & 3) == 0) {
     const float4* in4 = reinterpret_cast<const float4*>(in);
@@ -592,7 +654,7 @@ __global__ void __launch_bounds__(1024) k_pc_fused(PcModes pm, const float* __re
     __syncthreads();
     if (last) {
       __threadfence();
-      rich_check_block(part, gridDim.x, ra.tol, ra.max_iter, ra.st, ra.hnd, ra.use_hnd);
+      rich_check_block(part, gridDim.x, ra.tol, ra.max_iter, ra.st, snap, ra.hnd, ra.use_hnd);
       if (threadIdx.x == 0) *ra.ticket = 0u;
     }
   }
@@ -665,6 +727,78 @@ __global__ void __launch_bounds__(1024) k_pc_slab(PcModes pm, const float* __res
     }
   }
   if (x) step_norms_block(s1, s2, bad, part);
+}
+
+// The step when the first mode of the preconditioner has already been applied (for
+// lambda = 0 the tile reduction folds G_1^-1 into its weights, so `in` holds
+// G_1^-1 x_1 g): what remains acts inside each slab j of the first mode. Block (j, s)
+// stages slab j, forms rows [s nr, (s+1) nr) of its mode-1 product (nr = R_1 / S), applies
+// modes 2..N-1 to those rows, takes the step on them with the FP32 block norms, and the
+// last block to finish evaluates the stopping rule. Shared memory: the slab, two buffers
+// of the block's rows, the matrices of modes 1..N-1 (transposed).
+__global__ void __launch_bounds__(256) k_pc_rows(PcModes pm, const float* __restrict__ in, int Q, int S,
+                                                 float* __restrict__ x, float alpha, double* __restrict__ part,
+                                                 RichArgs ra) {
+  extern __shared__ float pc_smem[];
+  const int R1 = pm.R[1], Q1 = Q / R1, nr = R1 / S, nq = nr * Q1;
+  float* full = pc_smem;
+  float* t = full + Q;
+  float* u = t + nq;
+  float* sB = u + nq;
+  int boff[KR_MAX_MODES];
+  int off = 0;
+  for (int m = 1; m < pm.N; ++m) {
+    const int Rm = pm.R[m];
+    boff[m] = off;
+    for (int e = threadIdx.x; e < Rm * Rm; e += blockDim.x) {  // e = k * Rm + jj
+      const int k = e / Rm, jj = e - k * Rm;
+      sB[off + e] = __ldg(pm.B[m] + jj * Rm + k);
+    }
+    off += Rm * Rm;
+  }
+  kr_pdl_trigger();
+  kr_pdl_wait();  // `in` and x come from the previous kernels
+  RichSnap snap = {};
+  if (threadIdx.x == 0 && ra.st) snap = rich_load(ra.st);
+  const int j = blockIdx.x / S, s = blockIdx.x - j * S;
+  const float* src = in + (int64_t)j * Q;
+  for (int e = threadIdx.x; e < Q; e += blockDim.x) full[e] = __ldg(src + e);
+  __syncthreads();
+  {  // mode 1, rows jj = s nr .. s nr + nr - 1
+    const float* B1 = sB + boff[1];
+    for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+      const int jr = e / Q1, q = e - jr * Q1, jj = s * nr + jr;
+      float acc = 0.f;
+      for (int k = 0; k < R1; ++k) acc = fmaf(B1[k * R1 + jj], full[k * Q1 + q], acc);
+      t[e] = acc;
+    }
+  }
+  __syncthreads();
+  pc_modes_from(pm, sB, boff, t, u, nq, 2, nr);
+  float s1 = 0.f, s2 = 0.f, bad = 0.f;
+  float* xr = x + (int64_t)j * Q + (int64_t)s * nq;
+  for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+    const float st = alpha * t[e];
+    const float xn = xr[e] + st;
+    xr[e] = xn;
+    s1 = fmaf(st, st, s1);
+    s2 = fmaf(xn, xn, s2);
+    if (!isfinite(xn)) bad = 1.f;
+  }
+  step_norms_block(s1, s2, bad, part);
+  if (ra.st) {  // the last block to finish evaluates the stopping rule
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      last = atomicAdd(ra.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      rich_check_block(part, gridDim.x, ra.tol, ra.max_iter, ra.st, snap, ra.hnd, ra.use_hnd);
+      if (threadIdx.x == 0) *ra.ticket = 0u;
+    }
+  }
 }
 
 // Deterministic sum of per-block partials: out[k] = sum_b part[stride*b + k] (k < stride),
@@ -845,6 +979,9 @@ struct IterBufs {
   kr_tiles* tl = nullptr;
   float* X1 = nullptr;
   float* Z = nullptr;
+  // N = 3, lambda = 0: A(1) G_1^-1, the weights of the tile reduction with the first mode
+  // of the preconditioner folded in (then g holds G_1^-1 x_1 gradient)
+  float* B1 = nullptr;
 };
 
 int64_t max_intermediate(const Modes& m) {
@@ -908,10 +1045,36 @@ kr_status pc_step_core(kr_ctx* ctx, const FactorTables& t, double lambda, float*
                        float* tmp0, float* tmp1, float* tmp2, int ublk, double* part, const RichArgs& ra,
                        int* nparts, bool* checked);
 
+// With mode0_done (lambda = 0, N >= 2) g already holds G_1^-1 x_1 (gradient) and the
+// step applies the other modes only (k_pc_rows).
 kr_status pc_step(kr_ctx* ctx, const FactorTables& t, double lambda, float* g, float* x, float alpha, float* tmp0,
-                  float* tmp1, float* tmp2, int ublk, double* part, const RichArgs& ra) {
+                  float* tmp1, float* tmp2, int ublk, double* part, const RichArgs& ra, bool mode0_done = false) {
   int np = 0;
   bool checked = false;
+  if (mode0_done) {
+    const int N = t.N;
+    int64_t Q = 1;
+    size_t nb = 0;
+    for (int n = 1; n < N; ++n) {
+      Q *= t.R[n];
+      nb += (size_t)t.R[n] * t.R[n];
+    }
+    const int R1 = t.R[1];
+    const int S = (R1 % 4 == 0) ? 4 : (R1 % 2 == 0 ? 2 : 1);
+    const int64_t nq = Q / S;
+    PcModes pm = {};
+    pm.N = N;
+    for (int n = 0; n < N; ++n) {
+      pm.R[n] = t.R[n];
+      pm.B[n] = t.ginv[n];
+    }
+    const size_t smem = ((size_t)Q + 2 * (size_t)nq + nb) * sizeof(float);
+    bool fits = false;
+    KR_TRY(smem_fit(ctx, k_pc_rows, smem, &fits));
+    if (!fits) return kr_fail(ctx, KR_EINVAL, "preconditioned step: slab of %lld entries too large", (long long)Q);
+    KR_LAUNCH_PDL(ctx, k_pc_rows, t.R[0] * S, 256, smem, pm, (const float*)g, (int)Q, S, x, alpha, part, ra);
+    return KR_OK;
+  }
   KR_TRY(pc_step_core(ctx, t, lambda, g, x, alpha, tmp0, tmp1, tmp2, ublk, part, ra, &np, &checked));
   if (!checked) KR_LAUNCH(ctx, k_rich_check, 1, 32, 0, part, np, ra.tol, ra.max_iter, ra.st, ra.hnd, ra.use_hnd);
   return KR_OK;
@@ -1027,7 +1190,7 @@ kr_status slab_forward(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const I
 // prefix mode (mode N-2 in the paper's 1-based count), then the earlier prefix modes.
 kr_status slab_backward(kr_ctx* ctx, const Modes& m, const IterBufs& bf) {
   const int N = m.N;
-  if (N <= 3) return kr_tile_reduce(ctx, bf.tl, N == 3 ? m.A[0] : nullptr, bf.g);
+  if (N <= 3) return kr_tile_reduce(ctx, bf.tl, N == 3 ? (bf.B1 ? bf.B1 : m.A[0]) : nullptr, bf.g);
   KR_TRY(kr_tile_reduce(ctx, bf.tl, m.A[N - 3], bf.Z));
   int din[KR_MAX_MODES], dout[KR_MAX_MODES], tr[KR_MAX_MODES];
   const float* B[KR_MAX_MODES];
@@ -1126,6 +1289,9 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   nd.add<double>(3 * (size_t)(nblk > 1024 ? nblk : 1024));
   nd.add<double>(16);
   nd.add<RichState>(1);
+  // the first preconditioner mode folded into the tile reduction (lambda = 0, N = 3)
+  const bool fold0 = slab && N == 3 && cfg.lambda == 0.0;
+  nd.add<float>(fold0 ? (size_t)m.I[0] * m.R[0] : 0);
   {
     Need sc = nd;
     kr_sketch_scratch_need(cfg.s, ncell, nd);
@@ -1160,6 +1326,10 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   bf.part = cv.take<double>(3 * (size_t)(nblk > 1024 ? nblk : 1024));
   bf.red = cv.take<double>(16);
   bf.rich = cv.take<RichState>(1);
+  if (fold0) {  // B1 = A(1) G_1^-1 (G_1^-1 symmetric: row i of B1 = G_1^-1 applied to row i of A(1))
+    bf.B1 = cv.take<float>((size_t)m.I[0] * m.R[0]);
+    KR_TRY(kr_mode_product(ctx, m.A[0], bf.B1, m.I[0], m.R[0], 1, m.R[0], t.ginv[0], 0));
+  }
   {
     Carve sc = cv;
     KR_TRY(kr_sketch_fill(ctx, m, t, b, seed, call_id, 0, &sk, sc));
@@ -1190,7 +1360,8 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     ra.hnd = hnd;
     ra.use_hnd = use_hnd;
     ra.ticket = ticket;
-    return pc_step(ctx, t, cfg.lambda, bf.g, bf.x, (float)cfg.alpha, bf.d, bf.t0, bf.t1, ublk, bf.part, ra);
+    return pc_step(ctx, t, cfg.lambda, bf.g, bf.x, (float)cfg.alpha, bf.d, bf.t0, bf.t1, ublk, bf.part, ra,
+                   bf.B1 != nullptr);
   };
   auto read_state = [&]() -> kr_status {
     KR_CUDA(ctx, cudaMemcpyAsync(hs, bf.rich, sizeof(RichState), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1245,7 +1416,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     KR_TRY(read_state());
   }
   it = hs->it;
-  rel = hs->rel;
+  rel = hs->h[1] > 0.0 ? sqrt(hs->h[0]) / sqrt(hs->h[1]) : (hs->h[0] == 0.0 ? 0.0 : INFINITY);
   if (hs->status == STEP_NONFINITE) st = kr_fail(ctx, KR_ENONFINITE, "Richardson iterate became non-finite at iteration %d", it);
   if (hs->status == STEP_DIVERGED)
     st = kr_fail(ctx, KR_EDIVERGED, "Richardson step grew 3 times in a row past 16x its minimum (iteration %d)", it);
