@@ -1,13 +1,14 @@
-// Stable LSD radix sort of 32-bit keys (8-bit digits), used to group the sampled rows
+// Stable LSD radix sort of 32-bit keys (9-bit digits), used to group the sampled rows
 // of a sketch by (cell, last coordinate): after the sort, repeated rows are adjacent
 // and cells appear in increasing order (the sets S_1, S_2, B_S of the proof of
 // Thm 4.4 with T = the last mode).
 //
 // Each pass: per-tile digit histograms (digit-major table), an exclusive scan of the
 // table, then a stable scatter. Inside a tile of 4096 keys every warp owns a contiguous
-// 512-key chunk and ranks its keys round by round (lanes of equal digit found with
-// eight ballots); the per-warp counts give every key its place in the tile, the tile is
-// reordered in shared memory and written out digit run by digit run.
+// 512-key chunk and ranks its keys round by round (lanes of equal digit found with nine
+// ballots); the per-warp counts give every key its place in the tile, the tile is
+// reordered in shared memory and written out digit run by digit run. Nine-bit digits sort
+// the 27-bit row keys of a 512^3 problem in three passes.
 #include "kr_internal.cuh"
 
 namespace {
@@ -16,13 +17,16 @@ constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_BITS = 8;
+constexpr int RS_BITS = 9;
 constexpr int RS_BUCKETS = 1 << RS_BITS;
+constexpr int RS_DPT = RS_BUCKETS / RS_THREADS;  // digits per thread in the per-digit steps
+static_assert(RS_DPT * RS_THREADS == RS_BUCKETS, "digits per thread");
 
 __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __restrict__ in, int64_t n, int shift,
                                                            uint32_t* __restrict__ hist, int nblk) {
   __shared__ uint32_t h[RS_BUCKETS];
-  h[threadIdx.x] = 0u;
+#pragma unroll
+  for (int k = 0; k < RS_DPT; ++k) h[threadIdx.x + k * RS_THREADS] = 0u;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * RS_TILE;
 #pragma unroll 4
@@ -31,12 +35,16 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __res
     if (idx < n) atomicAdd(&h[(__ldg(in + idx) >> shift) & (RS_BUCKETS - 1)], 1u);
   }
   __syncthreads();
-  hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+#pragma unroll
+  for (int k = 0; k < RS_DPT; ++k) {
+    const int d = threadIdx.x + k * RS_THREADS;
+    hist[(int64_t)d * nblk + blockIdx.x] = h[d];
+  }
 }
 
 // hist: exclusive scan of the digit-major table (first output position of every
 // (digit, tile)).
-__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t* __restrict__ in,
+__global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter(const uint32_t* __restrict__ in,
                                                               uint32_t* __restrict__ out, int64_t n, int shift,
                                                               const uint32_t* __restrict__ hist, int nblk) {
   __shared__ uint32_t s_keys[RS_TILE];
@@ -50,7 +58,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t* __
   const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
   for (int i = 0; i < RS_BUCKETS / 32; ++i) s_wcnt[warp][i * 32 + lane] = 0u;
-  s_glob[threadIdx.x] = hist[(int64_t)threadIdx.x * nblk + blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < RS_DPT; ++k) {
+    const int d = threadIdx.x + k * RS_THREADS;
+    s_glob[d] = hist[(int64_t)d * nblk + blockIdx.x];
+  }
   __syncwarp();
   uint32_t key[RS_ITEMS], rank[RS_ITEMS];
 #pragma unroll
@@ -73,12 +85,15 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t* __
     __syncwarp();
   }
   __syncthreads();
-  {  // tile totals per digit, exclusive scan over digits, then per-warp starts
-    const int d = threadIdx.x;
-    uint32_t tot = 0;
+  {  // tile totals per digit (RS_DPT consecutive digits per thread), exclusive scan over
+     // digits, then per-warp starts
+    const int d0 = threadIdx.x * RS_DPT;
+    uint32_t mine = 0;
 #pragma unroll
-    for (int w = 0; w < RS_WARPS; ++w) tot += s_wcnt[w][d];
-    uint32_t inc = tot;
+    for (int k = 0; k < RS_DPT; ++k)
+#pragma unroll
+      for (int w = 0; w < RS_WARPS; ++w) mine += s_wcnt[w][d0 + k];
+    uint32_t inc = mine;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
       const uint32_t v = __shfl_up_sync(0xffffffffu, inc, off);
@@ -88,13 +103,17 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t* __
     __syncthreads();
     uint32_t before = 0;
     for (int w = 0; w < warp; ++w) before += s_wtot[w];
-    uint32_t acc = before + inc - tot;
-    s_loc[d] = acc;
+    uint32_t acc = before + inc - mine;
 #pragma unroll
-    for (int w = 0; w < RS_WARPS; ++w) {
-      const uint32_t c = s_wcnt[w][d];
-      s_wcnt[w][d] = acc;
-      acc += c;
+    for (int k = 0; k < RS_DPT; ++k) {
+      const int d = d0 + k;
+      s_loc[d] = acc;
+#pragma unroll
+      for (int w = 0; w < RS_WARPS; ++w) {
+        const uint32_t c = s_wcnt[w][d];
+        s_wcnt[w][d] = acc;
+        acc += c;
+      }
     }
   }
   __syncthreads();
