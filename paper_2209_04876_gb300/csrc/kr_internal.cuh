@@ -244,8 +244,12 @@ void kr_sketch_setup_rows(kr_sketch* sk, const Modes& m, int64_t s_row, int nrow
 void kr_sketch_own_need(const kr_sketch* sk, Need& nd);
 void kr_sketch_layout(kr_sketch* sk, Carve& cv);
 void kr_sketch_scratch_need(int64_t s, int64_t ncell, Need& nd);
+// With defer_distinct the distinct-row count is copied to the context's pinned buffer at
+// KR_HBUF_DISTINCT without a synchronisation (sk->distinct = -1 until the caller reads it
+// after its next stream synchronisation).
+constexpr size_t KR_HBUF_DISTINCT = 2048;
 kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, const float* b, uint64_t seed,
-                         uint64_t call_id, int row, kr_sketch* sk, Carve& cv);
+                         uint64_t call_id, int row, kr_sketch* sk, Carve& cv, bool defer_distinct = false);
 // Residual/gradient pass: W[c, :] = sum_j omega_j (b~_j - <a_T, Y[c]>) a_T; obj partials.
 kr_status kr_sketch_resid(kr_ctx* ctx, const kr_sketch* sk, const float* AT, int RT, const float* Y,
                           float* W, double* obj_partial, int nblocks, int* used);

@@ -385,7 +385,7 @@ kr_status kr_sketch_check(kr_ctx* ctx, const Modes& m, int64_t s) {
 // Second phase of the sketch build, with scratch carved from `cv`: draw the row keys,
 // sort them, and turn the runs of equal keys into the merged entries of every cell.
 kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, const float* b, uint64_t seed,
-                         uint64_t call_id, int row, kr_sketch* sk, Carve& cv) {
+                         uint64_t call_id, int row, kr_sketch* sk, Carve& cv, bool defer_distinct) {
   const int N = m.N;
   const int64_t s = sk->s, ncell = sk->ncell;
   const uint32_t IT = (uint32_t)sk->IT;
@@ -470,6 +470,12 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   }
   KR_CUDA(ctx, cudaMemcpyAsync(sk->invpT, t.invp[N - 1], sizeof(float) * IT, cudaMemcpyDeviceToDevice, ctx->stream));
   KR_TRY(kr_hbuf_reserve(ctx, 4096));
+  if (defer_distinct) {  // read by the caller after its next synchronisation
+    KR_CUDA(ctx, cudaMemcpyAsync((char*)ctx->hbuf + KR_HBUF_DISTINCT, dsum, sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    sk->distinct = -1;
+    return KR_OK;
+  }
   KR_CUDA(ctx, cudaMemcpyAsync(ctx->hbuf, dsum, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   sk->distinct = (int64_t)(*(unsigned long long*)ctx->hbuf);

@@ -1332,7 +1332,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   }
   {
     Carve sc = cv;
-    KR_TRY(kr_sketch_fill(ctx, m, t, b, seed, call_id, 0, &sk, sc));
+    KR_TRY(kr_sketch_fill(ctx, m, t, b, seed, call_id, 0, &sk, sc, true));
   }
   if (slab) KR_TRY(kr_tiles_build(ctx, &sk, &tl, cv));
   KR_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
@@ -1431,6 +1431,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   KR_CUDA(ctx, cudaMemcpyAsync(h, bf.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   KR_CUDA(ctx, cudaEventRecord(ev[5], ctx->stream));
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  sk.distinct = (int64_t)(*(const unsigned long long*)((const char*)ctx->hbuf + KR_HBUF_DISTINCT));
   if (rep) {
     rep->iters = it;
     rep->converged = converged;
