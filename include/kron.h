@@ -79,7 +79,7 @@ typedef struct {
   int32_t max_iter;      /* Richardson iteration cap; <= 0 selects 100 */
   double tol;            /* stop when ||step|| <= tol * ||x||; <= 0 selects 1e-7 */
   double step;           /* Richardson step; <= 0 selects the paper's 1 - sqrt(eps) */
-  int32_t precision;     /* 0: FP32 contractions. 1: BF16 tensor-core inner sweeps with FP32 refinement */
+  int32_t precision;     /* 0: FP32 contractions (the only value this build accepts; others give KR_ENOTIMPL) */
   int32_t host_io;       /* 1: factors, b / X and x / A / G are host pointers */
   uint64_t seed;         /* Philox key */
   uint64_t call_id;      /* Philox counter word 3 (distinguishes sketches drawn with one seed) */

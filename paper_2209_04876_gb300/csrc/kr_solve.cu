@@ -1470,6 +1470,7 @@ kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr
   Modes m;
   KR_TRY(kr_check_factors(ctx, f, &m));
   if (!(o->eps > 0.0 && o->eps < 1.0)) return kr_fail(ctx, KR_EINVAL, "solver: eps=%g outside (0,1)", o->eps);
+  if (o->precision != 0) return kr_fail(ctx, KR_ENOTIMPL, "solver: precision=%d (only 0, FP32, is built)", o->precision);
   if (!(lambda >= 0.0) || !isfinite(lambda)) return kr_fail(ctx, KR_EINVAL, "solver: lambda must be finite and >= 0");
   SolveCfg cfg;
   cfg.lambda = lambda;

@@ -571,6 +571,7 @@ kr_status tucker_args(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R
   if (!o || !I || !R || !X || !A || !G) return kr_fail(ctx, KR_EINVAL, "tucker: null argument");
   if (N < 2 || N > KR_MAX_MODES) return kr_fail(ctx, KR_EINVAL, "tucker: N=%d outside [2,%d]", N, KR_MAX_MODES);
   if (!(o->eps > 0.0 && o->eps < 1.0)) return kr_fail(ctx, KR_EINVAL, "tucker: eps outside (0,1)");
+  if (o->precision != 0) return kr_fail(ctx, KR_ENOTIMPL, "tucker: precision=%d (only 0, FP32, is built)", o->precision);
   if (!(o->lambda >= 0.0) || !isfinite(o->lambda)) return kr_fail(ctx, KR_EINVAL, "tucker: lambda must be >= 0");
   if (o->host_io) return kr_fail(ctx, KR_ENOTIMPL, "tucker: host_io is not supported; pass device pointers");
   kr_factors f = {};

@@ -283,6 +283,9 @@ def test_invalid_arguments():
     with pytest.raises(kr.KronError) as e:  # R > I
         kr.kron_regress([dev(np.ones((2, 3))), As[1]], dev(np.ones(10)), eps=0.1)
     assert e.value.name == "KR_EINVAL"
+    with pytest.raises(kr.KronError) as e:  # only FP32 contractions are built
+        kr.kron_regress(As, b, eps=0.1, precision=1)
+    assert e.value.name == "KR_ENOTIMPL"
 
 
 def test_nonfinite_rhs_reports_enonfinite():
