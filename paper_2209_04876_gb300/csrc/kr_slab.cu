@@ -61,6 +61,7 @@ struct SlabArgs {
   float* zpart;     // ntmax x R2 x RT
   double* objpart;  // ntmax
   int IT, RT, I2, R2, R2P, R2S;
+  int mma, XS;  // Y and Z on tensor cores (3xTF32); row stride of the split X1[p] (floats)
   int64_t P;
   int a2vec, atvec;
   // shared-memory layout (bytes)
@@ -69,6 +70,30 @@ struct SlabArgs {
 
 __device__ __forceinline__ void team_sync(int team) {
   asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(SLAB_TEAM) : "memory");
+}
+
+// FP32-accurate products on the TF32 tensor path: x = hi + lo with hi = tf32(x) and
+// lo = tf32(x - hi), and a.b ~ a_hi.b_hi + a_hi.b_lo + a_lo.b_hi (the dropped lo.lo term is
+// below FP32 rounding), each an m16n8k8 TF32 MMA with FP32 accumulation.
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, const uint32_t* b) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ void mma_tf32x3(float* c, const uint32_t* ah, const uint32_t* al, const uint32_t* bh,
+                                           const uint32_t* bl) {
+  mma_tf32(c, al, bh);
+  mma_tf32(c, ah, bl);
+  mma_tf32(c, ah, bh);
 }
 
 // Row `it` of A(N), the lane's quads qd[v] (zero past R_N).
@@ -186,6 +211,8 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
   using S = SlabShape<RTP>;
   constexpr int COLS = S::COLS, G = S::G, NQ = S::NQ, NG = S::NG;
   constexpr int XQ = RTP / 4;
+  constexpr int NT8 = RTP >= 8 ? RTP / 8 : 1;   // n tiles of the tensor-core products
+  const bool mma = RTP >= 8 && a.mma;
   extern __shared__ float4 slab_smem[];
   char* sm = reinterpret_cast<char*>(slab_smem);
   float* sA = reinterpret_cast<float*>(sm);
@@ -265,17 +292,71 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
         const float* row = a.A2 + (size_t)i2 * R2;
         for (int k2 = 0; k2 < R2P; ++k2) dst[k2] = k2 < R2 ? __ldg(row + k2) : 0.f;
       }
+    } else if (mma && tt < ((na + 7) & ~7)) {
+      // rows past the last cell up to the next multiple of 8 are the padding of the
+      // tensor-core Z product's last k step: zero in both operands (A(N-1) rows here, W rows
+      // of sYW below), so they add exactly nothing
+      for (int k2 = 0; k2 < R2P; ++k2) sA2[tt * R2S + k2] = 0.f;
+#pragma unroll
+      for (int c = 0; c < RTP; ++c) sYW[tt * RTP + c] = 0.f;
     }
     {
       const float* xp = a.X1 + p * zn;
-      for (int i = tt; i < R2P * RTP; i += SLAB_TEAM) {
-        const int r = i / RTP, c = i % RTP;
-        sX1[i] = (r < R2 && c < RT) ? __ldg(xp + r * RT + c) : 0.f;
+      if (mma) {  // X1[p] split once into TF32 hi / lo planes, rows of XS floats
+        uint32_t* xh = reinterpret_cast<uint32_t*>(sX1);
+        uint32_t* xl = xh + R2P * a.XS;
+        for (int i = tt; i < R2P * RTP; i += SLAB_TEAM) {
+          const int r = i / RTP, c = i % RTP;
+          const float v = (r < R2 && c < RT) ? __ldg(xp + r * RT + c) : 0.f;
+          tf32_split(v, xh[r * a.XS + c], xl[r * a.XS + c]);
+        }
+      } else {
+        for (int i = tt; i < R2P * RTP; i += SLAB_TEAM) {
+          const int r = i / RTP, c = i % RTP;
+          sX1[i] = (r < R2 && c < RT) ? __ldg(xp + r * RT + c) : 0.f;
+        }
       }
     }
     team_sync(team);
     // ---- Y rows of the tile's cells: sYW[k] = A(N-1)[i_k] X1[p]
-    {
+    if (mma) {
+      // one 16-row block of cells per warp, all RTP columns: m16n8k8 fragments (A = rows of
+      // A(N-1): a0 (g, q), a1 (g + 8, q), a2 (g, q + 4), a3 (g + 8, q + 4); B = X1[p]: b0 (q, g),
+      // b1 (q + 4, g); C: (g, 2q), (g, 2q + 1), (g + 8, 2q), (g + 8, 2q + 1) with g = lane / 4,
+      // q = lane % 4: fr and fc below)
+      const int fr = lane >> 2, fc = lane & 3;
+      const uint32_t* xh = reinterpret_cast<const uint32_t*>(sX1);
+      const uint32_t* xl = xh + R2P * a.XS;
+      const int nmt = (na + 15) >> 4;
+      for (int mt = wt; mt < nmt; mt += SLAB_TEAM / 32) {
+        float acc[NT8][4];
+#pragma unroll
+        for (int nt = 0; nt < NT8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+        const float* ar0 = sA2 + (16 * mt + fr) * R2S + fc;
+        const float* ar1 = ar0 + 8 * R2S;
+        for (int ks = 0; ks < R2P / 8; ++ks) {
+          uint32_t ah[4], al[4];
+          tf32_split(ar0[8 * ks], ah[0], al[0]);
+          tf32_split(ar1[8 * ks], ah[1], al[1]);
+          tf32_split(ar0[8 * ks + 4], ah[2], al[2]);
+          tf32_split(ar1[8 * ks + 4], ah[3], al[3]);
+          const uint32_t* bh0 = xh + (8 * ks + fc) * a.XS + fr;
+          const uint32_t* bl0 = xl + (8 * ks + fc) * a.XS + fr;
+#pragma unroll
+          for (int nt = 0; nt < NT8; ++nt) {
+            const uint32_t bh[2] = {bh0[8 * nt], bh0[8 * nt + 4 * a.XS]};
+            const uint32_t bl[2] = {bl0[8 * nt], bl0[8 * nt + 4 * a.XS]};
+            mma_tf32x3(acc[nt], ah, al, bh, bl);
+          }
+        }
+        const int r0 = 16 * mt + fr, r1 = r0 + 8;
+#pragma unroll
+        for (int nt = 0; nt < NT8; ++nt) {
+          if (r0 < na) *reinterpret_cast<float2*>(sYW + r0 * RTP + 8 * nt + 2 * fc) = make_float2(acc[nt][0], acc[nt][1]);
+          if (r1 < na) *reinterpret_cast<float2*>(sYW + r1 * RTP + 8 * nt + 2 * fc) = make_float2(acc[nt][2], acc[nt][3]);
+        }
+      }
+    } else {
       const int ncq = (na + 3) >> 2;
       for (int w = tt; w < ncq * XQ; w += SLAB_TEAM) {
         const int cq = w / XQ, xq = w % XQ;
@@ -418,8 +499,48 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
       a.objpart[t] = s;
     }
     team_sync(team);
-    // ---- Z contribution: sum_k A(N-1)[i_k]^T W[k], cells split over ks thread sets
-    {
+    // ---- Z contribution: sum_k A(N-1)[i_k]^T W[k]
+    if (mma) {
+      // one 16 x 8 block of Z per warp step over all cells (k): A = A(N-1)^T (a0 at
+      // (m = fr, k = fc): row k of the staged rows, column m), B = W (b0 at (k = fc, n = fr));
+      // the cells past na up to the next multiple of 8 are zero in both operands
+      const int fr = lane >> 2, fc = lane & 3;
+      const int nnt = NT8, nblk = (R2 / 16) * nnt, nks = (na + 7) >> 3;
+      float* dst = a.zpart + (size_t)t * zn;
+      for (int b = wt; b < nblk; b += SLAB_TEAM / 32) {
+        const int mt = b / nnt, nt = b - mt * nnt;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const float* ac = sA2 + fc * R2S + 16 * mt + fr;
+        const float* wc = sYW + fc * RTP + 8 * nt + fr;
+        for (int ks = 0; ks < nks; ++ks) {
+          const float* a0 = ac + 8 * ks * R2S;
+          const float* w0 = wc + 8 * ks * RTP;
+          uint32_t ah[4], al[4], bh[2], bl[2];
+          tf32_split(a0[0], ah[0], al[0]);
+          tf32_split(a0[8], ah[1], al[1]);
+          tf32_split(a0[4 * R2S], ah[2], al[2]);
+          tf32_split(a0[4 * R2S + 8], ah[3], al[3]);
+          tf32_split(w0[0], bh[0], bl[0]);
+          tf32_split(w0[4 * RTP], bh[1], bl[1]);
+          mma_tf32x3(acc, ah, al, bh, bl);
+        }
+        // scalar stores: rows of R_N floats need not keep pairs 8-byte aligned (odd R_N),
+        // and the padding columns c >= R_N are dropped
+        const int r0 = 16 * mt + fr, c0 = 8 * nt + 2 * fc;
+        float* z0 = dst + r0 * RT;
+        float* z1 = z0 + 8 * RT;
+        if (c0 < RT) {
+          z0[c0] = acc[0];
+          z1[c0] = acc[2];
+        }
+        if (c0 + 1 < RT) {
+          z0[c0 + 1] = acc[1];
+          z1[c0 + 1] = acc[3];
+        }
+      }
+      continue;
+    }
+    {  // SIMT form: cells split over ks thread sets
       const int ZQ = R2P / 4, ntt = ZQ * XQ;
       int ks = SLAB_TEAM / ntt;
       const int cap = S::PF / (R2P * RTP);
@@ -689,7 +810,7 @@ __global__ void k_tiles_sort(int64_t ntmax, const uint32_t* __restrict__ order, 
 }
 
 struct SlabLayout {
-  int RTP, R2P, R2S, cb;
+  int RTP, R2P, R2S, cb, mma, XS;
   bool smem_a;
   size_t bytes;
   uint32_t team_off, team_bytes, o_a2, o_x1, o_pf, o_act, o_cs, o_ctl;
@@ -702,6 +823,9 @@ SlabLayout slab_layout(int IT, int RT, int R2, bool smem_a) {
   L.RTP = rt_pad(RT);
   L.R2P = (R2 + 3) / 4 * 4;
   L.R2S = L.R2P + 4;
+  // Y and Z on the TF32 tensor path when the fragments tile the shapes exactly
+  L.mma = (R2 % 16 == 0 && L.RTP >= 8) ? 1 : 0;
+  L.XS = L.RTP + 8;  // row stride of the split X1[p] planes: conflict-free B fragment loads
   L.cb = cb_for(L.RTP);
   L.smem_a = smem_a;
   const int cols = L.RTP < 16 ? L.RTP : 16;
@@ -713,7 +837,7 @@ SlabLayout slab_layout(int IT, int RT, int R2, bool smem_a) {
   L.o_a2 = (uint32_t)t;
   t += al16((size_t)L.cb * L.R2S * 4);
   L.o_x1 = (uint32_t)t;
-  t += al16((size_t)L.R2P * L.RTP * 4);
+  t += al16(L.mma ? (size_t)2 * L.R2P * L.XS * 4 : (size_t)L.R2P * L.RTP * 4);
   L.o_pf = (uint32_t)t;
   t += (size_t)SLAB_TEAM * cols * 4;
   L.o_act = (uint32_t)t;
@@ -900,6 +1024,8 @@ kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const flo
   a.R2 = tl->R2;
   a.R2P = L.R2P;
   a.R2S = L.R2S;
+  a.mma = L.mma;
+  a.XS = L.XS;
   a.P = tl->P;
   a.a2vec = (tl->R2 % 4 == 0) && ((reinterpret_cast<uintptr_t>(A2) & 15) == 0);
   a.atvec = (tl->RT % 4 == 0) && ((reinterpret_cast<uintptr_t>(AT) & 15) == 0);

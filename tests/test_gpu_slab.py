@@ -2,7 +2,8 @@
 Thm 4.4 with T = the last mode, evaluated slab by slab) against the oracle.
 
 Every variant of the kernel is run: R_N padded to 4, 8, 16 and 64 lanes' worth of
-columns, R_{N-1} = 64, A(N) in shared memory and read through L1, N = 2 (one slab),
+columns, R_{N-1} = 64, the tensor-core form of the tile products (R_{N-1} a multiple of
+16), A(N) in shared memory and read through L1, N = 2 (one slab),
 3 and 4 (prefix mode products), slabs without sampled rows, and a small tile budget that
 splits cells across lane groups and slabs across tiles. The per-cell formulation is run
 on the same inputs as a cross-check of the two evaluation orders.
@@ -92,6 +93,11 @@ SHAPES = [
     ([20, 30, 100], [1, 3, 64], "lognormal_rows", 0),  # R_N = 64, A(N) in shared memory
     ([3, 4, 2000], [1, 2, 64], "gauss", 0),        # R_N = 64, A(N) too large for shared memory
     ([40, 30, 50], [3, 4, 5], "gauss", 25),        # 25 of 40 slabs never sampled
+    # R_{N-1} a multiple of 16: Y and Z on the TF32 tensor path (three products per term)
+    ([40, 50, 60], [3, 16, 8], "lognormal_rows", 0),  # one n tile
+    ([24, 64, 48], [2, 32, 24], "gauss", 0),          # R_N = 24 padded to 32 (padding columns dropped)
+    ([16, 40, 80], [2, 16, 64], "outliers", 0),       # R_N = 64, A(N) in shared memory
+    ([6, 70, 40], [2, 32, 32], "lognormal_rows", 4),  # bench ranks, slabs without sampled rows
 ]
 
 
