@@ -131,3 +131,53 @@ def test_tucker_256cubed_rank16():
     tk.tucker_als(X64, As, G, lam, 10, sampled=False, history=he)
     assert rre_gpu <= (1 + 2 * eps) * he[-1]
     assert rre_gpu < 2e-4
+
+
+def test_large_1024cubed_r64_outliers():
+    """The largest workload: N=3, A(n) 1024x64 Gaussian with 10% of rows scaled x20, b a
+    rank-(64,64,64) Tucker tensor + 1% noise (1024^3 FP32, 4 GB), eps = 0.05, so
+    s = 261,654,300 draws. Every draw cannot be regrouped on the host in test time, so the
+    checks are properties that hold at any size and draws recomputed one by one by the
+    oracle: the multiplicities sum to s, keys are strictly increasing, three windows of
+    200k draws (start, middle, end) drawn by the oracle's sampler are all present with at
+    least their window multiplicity, the gathered b and the weights c / (s p) of those rows
+    are exact, and Thm 4.5's f(x) <= (1 + eps) OPT holds with f and OPT in FP64 from the
+    oracle (closed form)."""
+    w = CONFIGS["kron_n3_1024x64_outliers"]
+    prob = kron_problem(w["I"], w["R"], dist=w["dist"], seed=2210, noise_rel=w["noise_rel"], b_kind=w["b_kind"],
+                        tucker_rank=w["tucker_rank"])
+    As32 = [np.ascontiguousarray(A, dtype=np.float32) for A in prob["As"]]
+    b32 = np.ascontiguousarray(prob["b"], dtype=np.float32)
+    del prob
+    As_d = [dev(A) for A in As32]
+    b_d = dev(b32)
+    eps, seed, cid = w["eps"], 3, 1
+    x, rep = kr.kron_regress(As_d, b_d, eps=eps, seed=seed, call_id=cid, tol=1e-7, max_iter=200)
+    s = rep["s"]
+    assert rep["converged"] and s == ko.sample_count(64 ** 3, eps) == 261654300
+    tab = kr.kron_leverage(As_d)
+    sk = kr.kron_sketch(As_d, tab["cdf"], tab["prob"], b_d, s, seed, cid)
+    keys, counts, omega, bt = (v.cpu().numpy() for v in sk.export())
+    sk.free()
+    del b_d
+    torch.cuda.empty_cache()
+    assert keys.shape[0] == rep["distinct"]
+    assert int(counts.astype(np.int64).sum()) == s
+    assert np.all(np.diff(keys) > 0)
+    cdfs = [c.cpu().numpy() for c in tab["cdf"]]
+    probs = [p.cpu().numpy() for p in tab["prob"]]
+    for t0 in (0, s // 2, s - 200000):
+        idx = ko.sample_draws(cdfs, 200000, seed, cid, t0=t0)
+        wk, wc = ko.group_samples(idx, w["I"])
+        pos = np.searchsorted(keys, wk)
+        assert np.all(pos < keys.shape[0]) and np.array_equal(keys[pos], wk)
+        assert np.all(counts[pos] >= wc)
+        np.testing.assert_array_equal(bt[pos], b32[wk])
+        np.testing.assert_allclose(omega[pos], ko.sample_weights(wk, counts[pos], probs, w["I"], s), rtol=1e-6)
+    del keys, counts, omega, bt
+    As64 = [A.astype(np.float64) for A in As32]
+    b64 = b32.astype(np.float64)
+    del b32
+    opt = ko.objective(As64, b64, ko.closed_form_ls(As64, b64), 0.0)
+    f = ko.objective(As64, b64, x.cpu().numpy().astype(np.float64), 0.0)
+    assert f <= (1 + eps) * opt
