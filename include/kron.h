@@ -140,8 +140,12 @@ enum {
  *    stopping rule), 0 returns to the host after every step. Both apply the same rule to
  *    the same device-side sums, so they give identical results. Per-kernel timing
  *    (kr_timing_enable) always uses the host loop.
+ *  KR_OPT_BATCH_WORKERS (default 4, range [1, 32]): problems of kron_ridge_batched solved
+ *    concurrently, each by a worker context with its own stream and workspace (created on
+ *    first use, kept until kr_destroy). 1 solves them one after another on ctx's stream.
+ *    Every problem's result is the same whatever the number of workers.
  * Returns KR_EINVAL for an unknown key or a value out of range. */
-enum { KR_OPT_SLAB_PASS = 1, KR_OPT_SLAB_TILE_ENTRIES = 2, KR_OPT_DEVICE_LOOP = 3 };
+enum { KR_OPT_SLAB_PASS = 1, KR_OPT_SLAB_TILE_ENTRIES = 2, KR_OPT_DEVICE_LOOP = 3, KR_OPT_BATCH_WORKERS = 4 };
 KR_API kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value);
 
 KR_API kr_status kr_timing_enable(kr_ctx* ctx, int32_t on);
@@ -265,7 +269,11 @@ KR_API kr_status kron_ridge(kr_ctx* ctx, const kr_factors* f, const float* b, co
                      float* x, kr_report* report);
 
 /* nprob independent ridge problems (host arrays of descriptors and pointers); each
- * uses opts with call_id + problem index. reports: host array of nprob (may be NULL). */
+ * uses opts with call_id + problem index. reports: host array of nprob (may be NULL).
+ * The problems run concurrently on KR_OPT_BATCH_WORKERS worker contexts (host threads,
+ * one stream each), after the work already enqueued on ctx's stream; the call returns
+ * when all are done. Returns the first hard error (lowest problem index, its message in
+ * kr_last_error), else KR_ENOTCONV if any problem did not converge, else KR_OK. */
 KR_API kr_status kron_ridge_batched(kr_ctx* ctx, int32_t nprob, const kr_factors* probs,
                              const float* const b[], const kr_opts* opts, float* const x[],
                              kr_report* reports);

@@ -2,6 +2,8 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <mutex>
+
 #include "kr_internal.cuh"
 
 kr_status kr_fail(kr_ctx* ctx, kr_status st, const char* fmt, ...) {
@@ -19,6 +21,17 @@ kr_status kr_fail(kr_ctx* ctx, kr_status st, const char* fmt, ...) {
 kr_status kr_fail_cuda(kr_ctx* ctx, cudaError_t e, const char* what, const char* file, int line) {
   kr_status st = (e == cudaErrorMemoryAllocation) ? KR_ENOMEM : KR_ECUDA;
   return kr_fail(ctx, st, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+static std::mutex g_smem_attr_mu;
+
+kr_status kr_func_smem(kr_ctx* ctx, const void* func, size_t bytes) {
+  std::lock_guard<std::mutex> lock(g_smem_attr_mu);
+  cudaFuncAttributes fa;
+  KR_CUDA(ctx, cudaFuncGetAttributes(&fa, func));
+  if (bytes > (size_t)fa.maxDynamicSharedSizeBytes)
+    KR_CUDA(ctx, cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return KR_OK;
 }
 
 extern "C" kr_status kr_create(kr_ctx** out, void* stream) {
@@ -57,6 +70,10 @@ extern "C" kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value) {
       if (value != 0 && value != 1) return kr_fail(ctx, KR_EINVAL, "kr_set_option: device loop must be 0 or 1");
       ctx->device_loop = (int)value;
       return KR_OK;
+    case KR_OPT_BATCH_WORKERS:
+      if (value < 1 || value > 32) return kr_fail(ctx, KR_EINVAL, "kr_set_option: batch workers must be in [1, 32]");
+      ctx->batch_workers = (int)value;
+      return KR_OK;
     default:
       return kr_fail(ctx, KR_EINVAL, "kr_set_option: unknown key %d", key);
   }
@@ -66,6 +83,8 @@ extern "C" void kr_destroy(kr_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
+  for (kr_ctx* w : ctx->workers) kr_destroy(w);
+  for (cudaStream_t s : ctx->worker_streams) cudaStreamDestroy(s);
   for (auto& t : ctx->pending) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);

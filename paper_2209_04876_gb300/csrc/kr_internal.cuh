@@ -33,6 +33,10 @@ struct kr_ctx {
   int slab_pass = 1;
   uint32_t slab_tile_entries = 16384;
   int device_loop = 1;  // Richardson iterations 2.. as one CUDA graph with a conditional loop
+  int batch_workers = 4;  // kron_ridge_batched: problems solved concurrently (worker contexts)
+  // worker contexts of kron_ridge_batched, each with its own stream and workspace (owned)
+  std::vector<kr_ctx*> workers;
+  std::vector<cudaStream_t> worker_streams;
   cudaEvent_t ev[10] = {};
   cudaEvent_t pev[2] = {};  // completion of the two in-flight Richardson norm read-backs
   // per-kernel timing (instrumentation)
@@ -48,6 +52,16 @@ struct kr_ctx {
 };
 
 cudaEvent_t kr_timing_event(kr_ctx* ctx);
+
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it). The
+// limit is a per-function setting shared by every context and host thread, so the
+// query-and-raise is serialised process-wide; a launch sized for an earlier, larger limit
+// stays valid.
+kr_status kr_func_smem(kr_ctx* ctx, const void* func, size_t bytes);
+template <class F>
+kr_status kr_smem_attr(kr_ctx* ctx, F* func, size_t bytes) {
+  return kr_func_smem(ctx, reinterpret_cast<const void*>(func), bytes);
+}
 int kr_kind_of(const char* kernel_name);
 
 kr_status kr_fail(kr_ctx* ctx, kr_status st, const char* fmt, ...);

@@ -436,9 +436,9 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
   const size_t chol_smem = 3 * MAXR * LD * sizeof(double);
   const size_t lev_smem = (MAXR * LD + LEV_ROWS * LD) * sizeof(double);
   const size_t jac_smem = 2 * (MAXR + 1) * LD * sizeof(float);
-  KR_CUDA(ctx, cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem));
-  KR_CUDA(ctx, cudaFuncSetAttribute(k_leverage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lev_smem));
-  KR_CUDA(ctx, cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jac_smem));
+  KR_TRY(kr_smem_attr(ctx, k_cholesky, chol_smem));
+  KR_TRY(kr_smem_attr(ctx, k_leverage, lev_smem));
+  KR_TRY(kr_smem_attr(ctx, k_jacobi, jac_smem));
   dim3 gg((maxI + GRAM_ROWS - 1) / GRAM_ROWS, m.N);
   KR_LAUNCH(ctx, k_gram_partial, gg, 256, 0, mp);
   int maxR = 0;

@@ -853,13 +853,7 @@ SlabLayout slab_layout(int IT, int RT, int R2, bool smem_a) {
 
 template <int RTP, bool SMEM_A, bool OBJ>
 kr_status launch_slab_t(kr_ctx* ctx, const SlabArgs& a, size_t smem) {
-  static int configured_dev = -1;
-  static size_t configured_bytes = 0;
-  if (configured_dev != ctx->device || configured_bytes < smem) {
-    KR_CUDA(ctx, cudaFuncSetAttribute(k_slab<RTP, SMEM_A, OBJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured_dev = ctx->device;
-    configured_bytes = smem;
-  }
+  KR_TRY(kr_smem_attr(ctx, k_slab<RTP, SMEM_A, OBJ>, smem));
   KR_LAUNCH_PDL(ctx, (k_slab<RTP, SMEM_A, OBJ>), ctx->num_sms, SLAB_TEAM * SLAB_TEAMS, smem, a);
   return KR_OK;
 }

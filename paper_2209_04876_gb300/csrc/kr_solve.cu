@@ -12,6 +12,9 @@
 // iteration itself refines the solution to FP32 working accuracy.
 #include <math.h>
 
+#include <atomic>
+#include <thread>
+
 #include "kr_internal.cuh"
 
 namespace {
@@ -909,8 +912,7 @@ kr_status launch_resid_t(kr_ctx* ctx, const ResidArgs& a, int grid, int* used) {
   // `grid` is the cap that sizes the objective partials
   int per_sm = 1;
   if (smemA + smemI <= ctx->smem_optin) {
-    KR_CUDA(ctx, cudaFuncSetAttribute(k_resid<RTP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(smemA + smemI)));
+    KR_TRY(kr_smem_attr(ctx, k_resid<RTP, true>, smemA + smemI));
     KR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid<RTP, true>, RESID_THREADS,
                                                                smemA + smemI));
     int g = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
@@ -919,7 +921,7 @@ kr_status launch_resid_t(kr_ctx* ctx, const ResidArgs& a, int grid, int* used) {
     *used = g;
     return KR_OK;
   }
-  KR_CUDA(ctx, cudaFuncSetAttribute(k_resid<RTP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemI));
+  KR_TRY(kr_smem_attr(ctx, k_resid<RTP, false>, smemI));
   KR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid<RTP, false>, RESID_THREADS, smemI));
   int g = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
   if (g > grid) g = grid;
@@ -1031,8 +1033,7 @@ kr_status smem_fit(kr_ctx* ctx, F func, size_t dyn, bool* fits) {
   cudaFuncAttributes fa;
   KR_CUDA(ctx, cudaFuncGetAttributes(&fa, func));
   *fits = dyn + fa.sharedSizeBytes <= ctx->smem_optin;
-  if (*fits && dyn > (size_t)fa.maxDynamicSharedSizeBytes)
-    KR_CUDA(ctx, cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  if (*fits) KR_TRY(kr_smem_attr(ctx, func, dyn));
   return KR_OK;
 }
 
@@ -1531,18 +1532,83 @@ extern "C" kr_status kron_ridge(kr_ctx* ctx, const kr_factors* f, const float* b
   return solve_entry(ctx, f, b, opts, x, report, opts->lambda);
 }
 
+// Worker contexts for concurrent problems: a context each, on its own non-blocking stream,
+// created on first use and kept by `ctx`; options follow ctx's.
+static kr_status kr_workers_reserve(kr_ctx* ctx, int n) {
+  while ((int)ctx->workers.size() < n) {
+    cudaStream_t s = nullptr;
+    KR_CUDA(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    kr_ctx* w = nullptr;
+    const kr_status st = kr_create(&w, s);
+    if (st != KR_OK) {
+      cudaStreamDestroy(s);
+      return kr_fail(ctx, st, "kron_ridge_batched: worker context creation failed");
+    }
+    ctx->workers.push_back(w);
+    ctx->worker_streams.push_back(s);
+  }
+  for (int i = 0; i < n; ++i) {
+    kr_ctx* w = ctx->workers[i];
+    w->slab_pass = ctx->slab_pass;
+    w->slab_tile_entries = ctx->slab_tile_entries;
+    w->device_loop = ctx->device_loop;
+    w->timing = false;
+  }
+  return KR_OK;
+}
+
 extern "C" kr_status kron_ridge_batched(kr_ctx* ctx, int32_t nprob, const kr_factors* probs, const float* const b[],
                                         const kr_opts* opts, float* const x[], kr_report* reports) {
   if (!ctx) return KR_EINVAL;
   if (nprob < 0 || (nprob > 0 && (!probs || !b || !x || !opts)))
     return kr_fail(ctx, KR_EINVAL, "kron_ridge_batched: bad arguments");
+  const int W = nprob < ctx->batch_workers ? nprob : ctx->batch_workers;
+  if (W <= 1) {  // one after another on ctx's stream
+    kr_status worst = KR_OK;
+    for (int p = 0; p < nprob; ++p) {
+      kr_opts o = *opts;
+      o.call_id = opts->call_id + (uint64_t)p;
+      kr_status st = solve_entry(ctx, &probs[p], b[p], &o, x[p], reports ? &reports[p] : nullptr, opts->lambda);
+      if (st != KR_OK && st != KR_ENOTCONV) return st;
+      if (st != KR_OK) worst = st;
+    }
+    return worst;
+  }
+  KR_TRY(kr_workers_reserve(ctx, W));
+  // the problems' inputs may come from work enqueued on ctx's stream
+  KR_CUDA(ctx, cudaEventRecord(ctx->ev[9], ctx->stream));
+  for (int i = 0; i < W; ++i) KR_CUDA(ctx, cudaStreamWaitEvent(ctx->worker_streams[i], ctx->ev[9], 0));
+  std::vector<kr_status> st(nprob, KR_OK);
+  std::vector<std::string> msg(nprob);
+  std::atomic<int> next{0};
+  std::vector<int64_t> l0(W);
+  for (int i = 0; i < W; ++i) l0[i] = ctx->workers[i]->launches;
+  auto run = [&](int wi) {
+    kr_ctx* w = ctx->workers[wi];
+    for (;;) {
+      const int p = next.fetch_add(1);
+      if (p >= nprob) break;
+      kr_opts o = *opts;
+      o.call_id = opts->call_id + (uint64_t)p;
+      st[p] = solve_entry(w, &probs[p], b[p], &o, x[p], reports ? &reports[p] : nullptr, opts->lambda);
+      if (st[p] != KR_OK) msg[p] = w->err;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int i = 1; i < W; ++i) pool.emplace_back(run, i);
+  run(0);
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < W; ++i) ctx->launches += ctx->workers[i]->launches - l0[i];
   kr_status worst = KR_OK;
   for (int p = 0; p < nprob; ++p) {
-    kr_opts o = *opts;
-    o.call_id = opts->call_id + (uint64_t)p;
-    kr_status st = solve_entry(ctx, &probs[p], b[p], &o, x[p], reports ? &reports[p] : nullptr, opts->lambda);
-    if (st != KR_OK && st != KR_ENOTCONV) return st;
-    if (st != KR_OK) worst = st;
+    if (st[p] != KR_OK && st[p] != KR_ENOTCONV) {
+      ctx->err = msg[p];
+      return st[p];
+    }
+    if (st[p] == KR_ENOTCONV && worst == KR_OK) {
+      worst = KR_ENOTCONV;
+      ctx->err = msg[p];
+    }
   }
   return worst;
 }
@@ -1626,7 +1692,7 @@ extern "C" kr_status kron_objective(kr_ctx* ctx, const kr_factors* f, const floa
   {
     const size_t smA = (size_t)m.I[N - 1] * (RT + 1) * sizeof(float), smY = (size_t)FULL_CELLS * RT * sizeof(float);
     if (smA + smY <= ctx->smem_optin) {
-      KR_CUDA(ctx, cudaFuncSetAttribute(k_full_obj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smA + smY)));
+      KR_TRY(kr_smem_attr(ctx, k_full_obj<true>, smA + smY));
       KR_LAUNCH(ctx, k_full_obj<true>, nblk, 256, smA + smY, Y, m.A[N - 1], b, ncell, m.I[N - 1], RT, part);
     } else {
       KR_LAUNCH(ctx, k_full_obj<false>, nblk, 256, smY, Y, m.A[N - 1], b, ncell, m.I[N - 1], RT, part);

@@ -436,8 +436,7 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     if (st == KR_ERANK) return kr_fail(ctx, KR_ERANK, "factor step %d: the core unfolding G_(n) is rank deficient", n);
     KR_TRY(st);
   }
-  KR_CUDA(ctx, cudaFuncSetAttribute(k_penalty_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(sizeof(double) * Rne)));
+  KR_TRY(kr_smem_attr(ctx, k_penalty_rows, sizeof(double) * Rne));
   // G+ = G_(n)^T (G_(n) G_(n)^T)^-1 in FP64 (and FP32 for the preconditioner)
   double* hinv = cv.take<double>((int64_t)Rn * Rn);
   double* gp64 = cv.take<double>((int64_t)Rn * Rne);
@@ -486,7 +485,7 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   KR_LAUNCH(ctx, k_capacitance, Rn * Rn, 256, 0, Vw, AinvUt, Rn, (int)Rne, C);
   {
     const size_t sm = (size_t)Rn * 2 * Rn * sizeof(double);
-    KR_CUDA(ctx, cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    KR_TRY(kr_smem_attr(ctx, k_gauss_jordan, sm));
     KR_LAUNCH(ctx, k_gauss_jordan, 1, 256, sm, C, Rn, Cinv, flag);
   }
   // batched sketch: row i of X_(n), fresh draws per row (counter row = i)

@@ -1,0 +1,86 @@
+"""The batched ridge (many independent Kronecker ridge problems of uneven shapes, each
+an Alg. 2 solve with its own sketch): solved concurrently on worker contexts, every
+problem's result is bit-identical to solving it alone, whatever the number of workers;
+a hard error in one problem is reported for the batch."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2209_04876_gb300 as kr
+from oracle import kron as ko
+from workloads import kron_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    kr.lib()
+
+
+@pytest.fixture(autouse=True)
+def _default_workers():
+    yield
+    kr.set_option(kr.OPT_BATCH_WORKERS, 4)
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def _problems():
+    # uneven shapes drawn once from a seeded generator: N = 2 and 3, I_n in [16, 96],
+    # R_n in [2, 8], a mix of factor distributions (the batched-ridge workload in miniature)
+    rng = np.random.default_rng(2209)
+    out = []
+    for k in range(9):
+        N = 3 if k % 3 else 2
+        I = [int(v) for v in rng.integers(16, 97, size=N)]
+        R = [int(min(v, i)) for v, i in zip(rng.integers(2, 9, size=N), I)]
+        prob = kron_problem(I, R, dist=["gauss", "lognormal_rows", "outliers"][k % 3], seed=100 + k, noise_rel=0.01)
+        out.append(([A.astype(np.float32) for A in prob["As"]], prob["b"].astype(np.float32)))
+    return out
+
+
+@pytest.mark.parametrize("workers", [1, 3, 4, 9])
+def test_batched_matches_individual_solves(workers):
+    probs = _problems()
+    lam, eps, seed, cid = 1e-3, 0.1, 11, 40
+    kr.set_option(kr.OPT_BATCH_WORKERS, workers)
+    xs, reps = kr.kron_ridge_batched([([dev(A) for A in As], dev(b)) for As, b in probs], lam, eps=eps, seed=seed,
+                                     call_id=cid, tol=1e-7, max_iter=300)
+    for p, (As, b) in enumerate(probs):
+        x1, r1 = kr.kron_ridge([dev(A) for A in As], dev(b), lam, eps=eps, seed=seed, call_id=cid + p, tol=1e-7,
+                               max_iter=300)
+        assert torch.equal(xs[p], x1)
+        assert reps[p]["iters"] == r1["iters"] and reps[p]["distinct"] == r1["distinct"]
+        assert reps[p]["obj_sampled"] == r1["obj_sampled"]
+
+
+def test_batched_against_oracle():
+    """One problem of the batch against the oracle's solve on the same sample."""
+    probs = _problems()
+    lam, eps, seed, cid = 1e-3, 0.1, 12, 70
+    xs, reps = kr.kron_ridge_batched([([dev(A) for A in As], dev(b)) for As, b in probs], lam, eps=eps, seed=seed,
+                                     call_id=cid, tol=1e-7, max_iter=300)
+    p = 4
+    As = [A.astype(np.float64) for A in probs[p][0]]
+    b = probs[p][1].astype(np.float64)
+    t = kr.kron_leverage([dev(A) for A in probs[p][0]])
+    smp = ko.draw_sample(As, reps[p]["s"], seed, cid + p, cdfs=[c.cpu().numpy() for c in t["cdf"]],
+                         probs=[q.cpu().numpy() for q in t["prob"]])
+    xs_ref, _ = ko.richardson(As, b[smp.keys], smp, lam, eps, tol=1e-13, max_iter=5000)
+    got = xs[p].cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got - xs_ref) <= 1e-5 * np.linalg.norm(xs_ref)
+
+
+def test_batched_reports_first_hard_error():
+    probs = _problems()[:4]
+    bad = ([np.ones((3, 4), np.float32), probs[1][0][1]], np.ones(3 * probs[1][0][1].shape[0], np.float32))  # R > I
+    batch = [([dev(A) for A in As], dev(b)) for As, b in probs[:2]] + [([dev(A) for A in bad[0]], dev(bad[1]))]
+    with pytest.raises(kr.KronError) as e:
+        kr.kron_ridge_batched(batch, 1e-3, eps=0.1, seed=1, call_id=0)
+    assert e.value.name == "KR_EINVAL"
