@@ -600,8 +600,8 @@ __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict
                                                       int Rq, int zn, int nc, int64_t Pq, float* __restrict__ part,
                                                       uint32_t* __restrict__ counter) {
   __shared__ uint32_t s_ts[TR_MAXS + 1];
-  __shared__ float s_z[TR_MAXS][TR_QP];
-  __shared__ float s_a[TR_MAXS][KR_MAX_RANK];
+  __shared__ __align__(16) float s_z[TR_MAXS][TR_QP];
+  __shared__ __align__(16) float s_a[TR_MAXS][KR_MAX_RANK];
   __shared__ __align__(16) float s_t[TR_TB][TR_QP];
   const int64_t pq = blockIdx.z;
   const int c = blockIdx.y;
@@ -609,9 +609,10 @@ __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict
   const int per = (Iq + nc - 1) / nc;
   const int i0 = min(Iq, c * per), i1 = min(Iq, i0 + per), S = i1 - i0;
   for (int k = threadIdx.x; k <= S; k += blockDim.x) s_ts[k] = tstart[pq * Iq + i0 + k];
-  for (int e = threadIdx.x; e < S * Rq; e += blockDim.x) {
-    const int i = e / Rq, r = e - i * Rq;
-    s_a[i][r] = Aq ? __ldg(Aq + (size_t)(i0 + i) * Rq + r) : 1.f;
+  const int Rq4 = (Rq + 3) & ~3;  // ranks padded with zeros to the 4-rank blocks below
+  for (int e = threadIdx.x; e < S * Rq4; e += blockDim.x) {
+    const int i = e / Rq4, r = e - i * Rq4;
+    s_a[i][r] = r < Rq ? (Aq ? __ldg(Aq + (size_t)(i0 + i) * Rq + r) : 1.f) : 0.f;
   }
   for (int e = threadIdx.x; e < S * TR_QP; e += blockDim.x) (&s_z[0][0])[e] = 0.f;
   kr_pdl_trigger();
@@ -651,14 +652,32 @@ __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict
     }
     __syncthreads();
   }
-  // part[c][pq][r][q] = sum_i Aq[i0 + i, r] Z[i, q] in slab order
+  // part[c][pq][r][q] = sum_i Aq[i0 + i, r] Z[i, q] in slab order; a thread forms 4 ranks x
+  // 2 columns (one 16-byte load of Aq's row and one 8-byte load of Z per slab)
   float* out = part + ((size_t)c * Pq + pq) * Rq * zn;
-  for (int e = threadIdx.x; e < Rq * TR_QP; e += blockDim.x) {
-    const int r = e / TR_QP, qq = e - r * TR_QP, q = qb + qq;
+  const int R4 = (Rq + 3) >> 2;
+  for (int e = threadIdx.x; e < R4 * (TR_QP / 2); e += blockDim.x) {
+    const int r4 = e / (TR_QP / 2), q2 = e - r4 * (TR_QP / 2), r0 = 4 * r4, qq = 2 * q2, q = qb + qq;
     if (q >= zn) continue;
-    float acc = 0.f;
-    for (int i = 0; i < S; ++i) acc = fmaf(s_a[i][r], s_z[i][qq], acc);
-    out[(size_t)r * zn + q] = acc;
+    float acc[4][2] = {};
+    for (int i = 0; i < S; ++i) {
+      const float4 av = *reinterpret_cast<const float4*>(&s_a[i][r0]);
+      const float2 zv = *reinterpret_cast<const float2*>(&s_z[i][qq]);
+      acc[0][0] = fmaf(av.x, zv.x, acc[0][0]);
+      acc[0][1] = fmaf(av.x, zv.y, acc[0][1]);
+      acc[1][0] = fmaf(av.y, zv.x, acc[1][0]);
+      acc[1][1] = fmaf(av.y, zv.y, acc[1][1]);
+      acc[2][0] = fmaf(av.z, zv.x, acc[2][0]);
+      acc[2][1] = fmaf(av.z, zv.y, acc[2][1]);
+      acc[3][0] = fmaf(av.w, zv.x, acc[3][0]);
+      acc[3][1] = fmaf(av.w, zv.y, acc[3][1]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (r0 + j >= Rq) break;
+      out[(size_t)(r0 + j) * zn + q] = acc[j][0];
+      if (q + 1 < zn) out[(size_t)(r0 + j) * zn + q + 1] = acc[j][1];
+    }
   }
 }
 
