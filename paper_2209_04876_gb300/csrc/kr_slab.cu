@@ -594,27 +594,45 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
 // in order.
 constexpr int TR_MAXS = 64;  // slabs per chunk at most
 constexpr int TR_QP = 64;    // columns per block
-constexpr int TR_TB = 60;    // tile rows staged per batch (keeps the block under 48 KB)
+// Shared memory of k_tile_reduce1 (floats, rows of 16 bytes): tile starts (TR_MAXS + 1,
+// padded to 68), Z of the chunk's slabs (per x TR_QP), Aq rows (per x Rq4), then as many
+// staged tile rows (TR_QP each) as the 48 KB budget leaves, at most 256.
+struct TileReduceSmem {
+  int per, rq4, tb;
+  size_t bytes;
+};
+TileReduceSmem tile_reduce_smem(int per, int Rq) {
+  TileReduceSmem L;
+  L.per = per;
+  L.rq4 = (Rq + 3) & ~3;
+  const size_t fixed = (68 + (size_t)per * TR_QP + (size_t)per * L.rq4) * sizeof(float);
+  const size_t budget = 48 * 1024;
+  int tb = fixed < budget ? (int)((budget - fixed) / (TR_QP * sizeof(float))) : 0;
+  L.tb = tb > 256 ? 256 : (tb < 16 ? 16 : tb);
+  L.bytes = fixed + (size_t)L.tb * TR_QP * sizeof(float);
+  return L;
+}
 __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict__ tstart, int Iq,
                                                       const float* __restrict__ zpart, const float* __restrict__ Aq,
                                                       int Rq, int zn, int nc, int64_t Pq, float* __restrict__ part,
-                                                      uint32_t* __restrict__ counter) {
-  __shared__ uint32_t s_ts[TR_MAXS + 1];
-  __shared__ __align__(16) float s_z[TR_MAXS][TR_QP];
-  __shared__ __align__(16) float s_a[TR_MAXS][KR_MAX_RANK];
-  __shared__ __align__(16) float s_t[TR_TB][TR_QP];
+                                                      uint32_t* __restrict__ counter, int TB) {
+  extern __shared__ float4 tr_smem[];
   const int64_t pq = blockIdx.z;
   const int c = blockIdx.y;
   const int qb = blockIdx.x * TR_QP;
   const int per = (Iq + nc - 1) / nc;
   const int i0 = min(Iq, c * per), i1 = min(Iq, i0 + per), S = i1 - i0;
-  for (int k = threadIdx.x; k <= S; k += blockDim.x) s_ts[k] = tstart[pq * Iq + i0 + k];
   const int Rq4 = (Rq + 3) & ~3;  // ranks padded with zeros to the 4-rank blocks below
+  uint32_t* s_ts = reinterpret_cast<uint32_t*>(tr_smem);
+  float* s_z = reinterpret_cast<float*>(tr_smem) + 68;  // [per][TR_QP]
+  float* s_a = s_z + (size_t)per * TR_QP;                // [per][Rq4]
+  float* s_t = s_a + (size_t)per * Rq4;                  // [TB][TR_QP]
+  for (int k = threadIdx.x; k <= S; k += blockDim.x) s_ts[k] = tstart[pq * Iq + i0 + k];
   for (int e = threadIdx.x; e < S * Rq4; e += blockDim.x) {
     const int i = e / Rq4, r = e - i * Rq4;
-    s_a[i][r] = r < Rq ? (Aq ? __ldg(Aq + (size_t)(i0 + i) * Rq + r) : 1.f) : 0.f;
+    s_a[e] = r < Rq ? (Aq ? __ldg(Aq + (size_t)(i0 + i) * Rq + r) : 1.f) : 0.f;
   }
-  for (int e = threadIdx.x; e < S * TR_QP; e += blockDim.x) (&s_z[0][0])[e] = 0.f;
+  for (int e = threadIdx.x; e < S * TR_QP; e += blockDim.x) s_z[e] = 0.f;
   kr_pdl_trigger();
   kr_pdl_wait();  // zpart: the slab pass has finished
   // ... and its work counter can be re-armed for the next pass
@@ -626,19 +644,19 @@ __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict
   // batch's tiles of its slab.
   const uint32_t t0 = s_ts[0], t1 = s_ts[S];
   const bool vec = (zn & 3) == 0;
-  for (uint32_t tb = t0; tb < t1; tb += TR_TB) {
-    const int nt = (int)min((uint32_t)TR_TB, t1 - tb);
+  for (uint32_t tb = t0; tb < t1; tb += (uint32_t)TB) {
+    const int nt = (int)min((uint32_t)TB, t1 - tb);
     if (vec) {
       for (int e = threadIdx.x; e < nt * (TR_QP / 4); e += blockDim.x) {
         const int tl = e / (TR_QP / 4), c4 = e - tl * (TR_QP / 4), q = qb + 4 * c4;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (q < zn) v = __ldg(reinterpret_cast<const float4*>(zpart + (size_t)(tb + tl) * zn + q));
-        *reinterpret_cast<float4*>(&s_t[tl][4 * c4]) = v;
+        *reinterpret_cast<float4*>(s_t + tl * TR_QP + 4 * c4) = v;
       }
     } else {
       for (int e = threadIdx.x; e < nt * TR_QP; e += blockDim.x) {
         const int tl = e / TR_QP, qq = e - tl * TR_QP, q = qb + qq;
-        s_t[tl][qq] = q < zn ? __ldg(zpart + (size_t)(tb + tl) * zn + q) : 0.f;
+        s_t[tl * TR_QP + qq] = q < zn ? __ldg(zpart + (size_t)(tb + tl) * zn + q) : 0.f;
       }
     }
     __syncthreads();
@@ -646,9 +664,9 @@ __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict
       const int i = e / TR_QP, qq = e - i * TR_QP;
       const uint32_t lo = max(s_ts[i], tb), hi = min(s_ts[i + 1], tb + (uint32_t)nt);
       if (lo >= hi) continue;
-      float z = s_z[i][qq];
-      for (uint32_t t = lo; t < hi; ++t) z += s_t[t - tb][qq];
-      s_z[i][qq] = z;
+      float z = s_z[i * TR_QP + qq];
+      for (uint32_t t = lo; t < hi; ++t) z += s_t[(t - tb) * TR_QP + qq];
+      s_z[i * TR_QP + qq] = z;
     }
     __syncthreads();
   }
@@ -661,8 +679,8 @@ __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict
     if (q >= zn) continue;
     float acc[4][2] = {};
     for (int i = 0; i < S; ++i) {
-      const float4 av = *reinterpret_cast<const float4*>(&s_a[i][r0]);
-      const float2 zv = *reinterpret_cast<const float2*>(&s_z[i][qq]);
+      const float4 av = *reinterpret_cast<const float4*>(s_a + i * Rq4 + r0);
+      const float2 zv = *reinterpret_cast<const float2*>(s_z + i * TR_QP + qq);
       acc[0][0] = fmaf(av.x, zv.x, acc[0][0]);
       acc[0][1] = fmaf(av.x, zv.y, acc[0][1]);
       acc[1][0] = fmaf(av.y, zv.x, acc[1][0]);
@@ -1062,8 +1080,9 @@ kr_status kr_tile_reduce(kr_ctx* ctx, kr_tiles* tl, const float* Aq, float* W) {
   const int zn = tl->R2 * tl->RT;
   const dim3 grid((unsigned)((zn + TR_QP - 1) / TR_QP), (unsigned)tl->nc, (unsigned)tl->Pq);
   float* part = tl->nc > 1 ? tl->zred : W;
-  KR_LAUNCH_PDL(ctx, k_tile_reduce1, grid, 256, 0, tl->tstart, tl->Iq, tl->zpart, Aq, tl->Rq, zn, tl->nc, tl->Pq,
-                part, tl->meta + 2);
+  const TileReduceSmem L = tile_reduce_smem((tl->Iq + tl->nc - 1) / tl->nc, tl->Rq);
+  KR_LAUNCH_PDL(ctx, k_tile_reduce1, grid, 256, L.bytes, tl->tstart, tl->Iq, tl->zpart, Aq, tl->Rq, zn, tl->nc, tl->Pq,
+                part, tl->meta + 2, L.tb);
   if (tl->nc > 1) {
     const int64_t total = tl->Pq * tl->Rq * zn;
     const int64_t work = (total & 3) == 0 ? total / 4 : total;
