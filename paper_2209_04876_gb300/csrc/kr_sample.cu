@@ -13,9 +13,10 @@
 // U < ceil(cdf[i] * 2^53).
 //
 // Grouping (the sets S_1, S_2 and B_S of the proof of Thm 4.4 with T = {N}):
-// cell = (i_1..i_{N-1}), the last coordinate i_N stays with the sample. A counting
-// sort by cell (histogram, scan, scatter), then per cell a table over i_N merges
-// repeated rows into multiplicities in increasing i_N order, and gathers b.
+// cell = (i_1..i_{N-1}), the last coordinate i_N stays with the sample. Every draw
+// writes its row key cell * I_N + i_N; a stable radix sort of the keys (kr_sort.cu)
+// makes repeated rows adjacent and orders cells; runs of equal keys become the merged
+// entries (i_N, multiplicity) of each cell in increasing i_N order, with b gathered.
 #include "kr_internal.cuh"
 
 namespace {
