@@ -85,12 +85,18 @@ extern "C" void kr_destroy(kr_ctx* ctx) {
   else cudaDeviceSynchronize();
   for (kr_ctx* w : ctx->workers) kr_destroy(w);
   for (cudaStream_t s : ctx->worker_streams) cudaStreamDestroy(s);
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamDestroy(ctx->copy_stream);
+  }
+  if (ctx->b_ready) cudaEventDestroy(ctx->b_ready);
   for (auto& t : ctx->pending) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
   }
   for (auto e : ctx->pool) cudaEventDestroy(e);
   if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->io) cudaFree(ctx->io);
   if (ctx->split_buf) cudaFree(ctx->split_buf);
   if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
   for (int i = 0; i < 10; ++i)
@@ -109,6 +115,25 @@ extern "C" kr_status kr_set_stream(kr_ctx* ctx, void* stream) {
 extern "C" const char* kr_last_error(const kr_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 extern "C" int64_t kr_launch_count(const kr_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+kr_status kr_io_reserve(kr_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->io_size) return KR_OK;
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->copy_stream) KR_CUDA(ctx, cudaStreamSynchronize(ctx->copy_stream));
+  if (ctx->io) {
+    cudaFree(ctx->io);
+    ctx->io = nullptr;
+    ctx->io_size = 0;
+  }
+  cudaError_t e = cudaMalloc(&ctx->io, bytes);
+  if (e != cudaSuccess) {
+    ctx->io = nullptr;
+    cudaGetLastError();
+    return kr_fail(ctx, KR_ENOMEM, "host-buffer staging allocation of %zu bytes failed", bytes);
+  }
+  ctx->io_size = bytes;
+  return KR_OK;
+}
 
 kr_status kr_ws_reserve(kr_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->ws_size) return KR_OK;

@@ -37,6 +37,15 @@ struct kr_ctx {
   // worker contexts of kron_ridge_batched, each with its own stream and workspace (owned)
   std::vector<kr_ctx*> workers;
   std::vector<cudaStream_t> worker_streams;
+  // host-buffer solves: b is copied in on its own stream while the solve stream builds the
+  // tables and draws; the gather waits for b_ready (created on first use, owned)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t b_ready = nullptr;
+  // device copies of a host-buffer solve's factors, b and x (grow-on-demand, kept)
+  char* io = nullptr;
+  size_t io_size = 0;
+  // set during a host-buffer solve: the event the gather of b waits for (nullptr: none)
+  cudaEvent_t b_wait = nullptr;
   cudaEvent_t ev[10] = {};
   cudaEvent_t pev[2] = {};  // completion of the two in-flight Richardson norm read-backs
   // per-kernel timing (instrumentation)
@@ -144,6 +153,8 @@ cudaError_t kr_launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_
 
 // Ensures the workspace holds at least `bytes` (synchronises when it grows).
 kr_status kr_ws_reserve(kr_ctx* ctx, size_t bytes);
+// The same for the device copies of a host-buffer solve's inputs and output.
+kr_status kr_io_reserve(kr_ctx* ctx, size_t bytes);
 kr_status kr_hbuf_reserve(kr_ctx* ctx, size_t bytes);
 kr_status kr_split_reserve(kr_ctx* ctx, size_t bytes);
 

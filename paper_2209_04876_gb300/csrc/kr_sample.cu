@@ -455,6 +455,9 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
     Carve sc = cv;
     KR_TRY(kr_scan_u32(ctx, mcnt, mcnt, s, sc));
   }
+  // b may still be arriving on the context's copy stream (host-buffer solves): the gather
+  // is its first reader
+  if (ctx->b_wait) KR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->b_wait, 0));
   KR_LAUNCH(ctx, k_rle_emit, grid_for(ctx, s, 256), 256, 0, sorted, hp, mcnt, meta, s, IT, (uint32_t)sk->ncell_inner,
             sk->xI, sk->xPafter, b, sk->ent, sk->bt, sk->cell_nd, dsum);
   {

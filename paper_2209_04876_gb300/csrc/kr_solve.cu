@@ -1489,8 +1489,8 @@ kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr
   for (int n = 0; n < m.N; ++n) bytes += ((size_t)m.I[n] * m.R[n] * 4 + 255) & ~size_t(255);
   bytes += ((size_t)I * 4 + 255) & ~size_t(255);
   bytes += ((size_t)R * 4 + 255) & ~size_t(255);
-  char* dev = nullptr;
-  KR_CUDA(ctx, cudaMallocAsync((void**)&dev, bytes, ctx->stream));
+  KR_TRY(kr_io_reserve(ctx, bytes));
+  char* dev = ctx->io;
   KR_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
   Carve cv(dev, bytes);
   Modes md = m;
@@ -1500,14 +1500,28 @@ kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr
     md.A[n] = a;
   }
   float* bd = cv.take<float>(I);
-  KR_CUDA(ctx, cudaMemcpyAsync(bd, b, sizeof(float) * I, cudaMemcpyHostToDevice, ctx->stream));
+  // b on the copy stream, overlapping the tables, draws and sort of the solve stream; the
+  // gather waits for it
+  if (!ctx->copy_stream) {
+    KR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    KR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->b_ready, cudaEventDisableTiming));
+  }
+  // after the factors: copies in one direction share the copy engine, and the solve stream's
+  // first kernels need the factors, not b
+  KR_CUDA(ctx, cudaEventRecord(ctx->b_ready, ctx->stream));
+  KR_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->b_ready, 0));
+  KR_CUDA(ctx, cudaMemcpyAsync(bd, b, sizeof(float) * I, cudaMemcpyHostToDevice, ctx->copy_stream));
+  KR_CUDA(ctx, cudaEventRecord(ctx->b_ready, ctx->copy_stream));
   float* xd = cv.take<float>(R);
+  ctx->b_wait = ctx->b_ready;
   kr_status st = kr_solve_device(ctx, md, bd, cfg, o->seed, o->call_id, xd, rep);
+  ctx->b_wait = nullptr;
+  // the staging buffer is reused by the next call: order it after the copy in every case
+  KR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->b_ready, 0));
   if (st == KR_OK || st == KR_ENOTCONV) {
     KR_CUDA(ctx, cudaMemcpyAsync(x, xd, sizeof(float) * R, cudaMemcpyDeviceToHost, ctx->stream));
   }
   KR_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
-  cudaFreeAsync(dev, ctx->stream);
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (rep) {
     float ms = 0;

@@ -246,8 +246,12 @@ def test_objective_full():
     assert abs(f - ref) <= 1e-6 * ref
 
 
-def test_host_io_matches_device_path():
-    prob = kron_problem([64, 48, 40], [4, 3, 5], seed=15, noise_rel=0.05)
+@pytest.mark.parametrize("I,R", [([64, 48, 40], [4, 3, 5]),
+                                 ([256, 256, 256], [16, 16, 16])])  # b's copy outlasts the draws and sort
+def test_host_io_matches_device_path(I, R):
+    """Host buffers: b is copied on the context's copy stream while the solve stream builds
+    the tables, draws and sorts; the result is the device path's, bit for bit."""
+    prob = kron_problem(I, R, seed=15, noise_rel=0.05)
     As = [np.asarray(A, dtype=np.float32) for A in prob["As"]]
     b = prob["b"].astype(np.float32)
     xd, rd = kr.kron_regress([dev(A) for A in As], dev(b), eps=0.1, seed=3, call_id=1)
