@@ -142,6 +142,22 @@ __global__ void __launch_bounds__(256, 2) k_mode_product_q4(const float* __restr
   }
   const int kend = min(K, (int)(blockIdx.z + 1) * kchunk);
   float4 xr[4];
+  constexpr int NB = BM * SG_BK / 256;  // B-tile entries per thread
+  // 32-row tiles prefetch the small B tile with the input tile (all loads of a stage in
+  // flight together); 64-row tiles have no registers to spare and read it at the store
+  constexpr bool PRE_B = BM <= 32;
+  float br[PRE_B ? NB : 1];
+  auto b_entry = [&](int i, int k0) -> float {
+    const int e = tid + 256 * i;
+    int jj, kk;
+    if (trans) { jj = e % BM; kk = e / BM; } else { kk = e % SG_BK; jj = e / SG_BK; }
+    const int j = j0 + jj, k = k0 + kk;
+    return (j < J && k < kend) ? (trans ? __ldg(&B[(int64_t)k * J + j]) : __ldg(&B[(int64_t)j * K + k])) : 0.f;
+  };
+  auto b_slot = [&](int i, int& jj, int& kk) {
+    const int e = tid + 256 * i;
+    if (trans) { jj = e % BM; kk = e / BM; } else { kk = e % SG_BK; jj = e / SG_BK; }
+  };
   auto load_stage = [&](int k0) {  // input tile into registers (prefetch)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -149,17 +165,20 @@ __global__ void __launch_bounds__(256, 2) k_mode_product_q4(const float* __restr
       xr[i] = (in_base >= 0 && k < kend) ? __ldg(reinterpret_cast<const float4*>(in + in_base + (int64_t)k * Q))
                                          : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    if constexpr (PRE_B) {
+#pragma unroll
+      for (int i = 0; i < NB; ++i) br[i] = b_entry(i, k0);
+    }
   };
-  auto store_stage = [&](int k0) {  // registers -> shared; the small B tile straight from L1/L2
+  auto store_stage = [&](int k0) {  // registers -> shared; the B tile from registers or L1/L2
 #pragma unroll
     for (int i = 0; i < 4; ++i) *reinterpret_cast<float4*>(&Xs[kl + 8 * i][nl]) = xr[i];
-#pragma unroll 4
-    for (int i = 0; i < BM * SG_BK / 256; ++i) {
-      const int e = tid + 256 * i;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
       int jj, kk;
-      if (trans) { jj = e % BM; kk = e / BM; } else { kk = e % SG_BK; jj = e / SG_BK; }
-      const int j = j0 + jj, k = k0 + kk;
-      Bs[kk][jj] = (j < J && k < kend) ? (trans ? __ldg(&B[(int64_t)k * J + j]) : __ldg(&B[(int64_t)j * K + k])) : 0.f;
+      b_slot(i, jj, kk);
+      if constexpr (PRE_B) Bs[kk][jj] = br[i];
+      else Bs[kk][jj] = b_entry(i, k0);
     }
   };
   float acc[RM][8];
