@@ -195,53 +195,172 @@ __global__ void __launch_bounds__(256) k_draw_keys(DrawModes dm, int64_t s_row, 
 }
 
 // ------------------------------------------------------------------ runs of equal keys
+//
+// Runs of equal sorted keys become the merged entries of the sketch in four passes that
+// touch the keys twice: heads counted per tile of 4096 keys, the run starts written in
+// order (the tile counts scanned), entries past one per run counted per tile of runs (a
+// multiplicity above 65535 takes several entries; such runs are rare), then the entries
+// emitted with b gathered.
 
-// After the sort: run d of equal keys starts at hp[d] (hp[ndist] = n, meta[0] = ndist).
-__global__ void k_rle_heads(const uint32_t* __restrict__ k, int64_t n, uint32_t* __restrict__ f) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    f[e] = (e == 0 || k[e] != k[e - 1]) ? 1u : 0u;
+constexpr int RLE_THREADS = 256;
+constexpr int RLE_ITEMS = 16;
+constexpr int RLE_TILE = RLE_THREADS * RLE_ITEMS;  // keys (or runs) per block
+
+// Words of the run merge's per-tile arrays (head counts, their offsets, extras, theirs).
+int64_t rle_scratch_words(int64_t s) { return 4 * ((s + RLE_TILE - 1) / RLE_TILE); }
+
+__device__ __forceinline__ uint32_t rle_block_sum(uint32_t v, uint32_t* sh) {  // sh: RLE_THREADS / 32 words
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  uint32_t t = 0;
+#pragma unroll
+  for (int w = 0; w < RLE_THREADS / 32; ++w) t += sh[w];
+  __syncthreads();
+  return t;
 }
 
-__global__ void k_rle_pos(const uint32_t* __restrict__ k, const uint32_t* __restrict__ dpos, int64_t n,
-                          uint32_t* __restrict__ hp, uint32_t* __restrict__ meta) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const bool head = e == 0 || k[e] != k[e - 1];
-    if (head) hp[dpos[e]] = (uint32_t)e;
-    if (e == n - 1) {
-      const uint32_t nd = dpos[e] + (head ? 1u : 0u);
-      hp[nd] = (uint32_t)n;
-      meta[0] = nd;
+// Exclusive block scan (block of RLE_THREADS threads); sh: RLE_THREADS / 32 + 1 words.
+__device__ __forceinline__ uint32_t rle_block_excl(uint32_t v, uint32_t* sh, uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += t;
+  }
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < RLE_THREADS / 32 ? sh[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, wi, off);
+      if (lane >= off) wi += t;
+    }
+    if (lane < RLE_THREADS / 32) sh[lane] = wi - w;
+    if (lane == RLE_THREADS / 32 - 1) sh[RLE_THREADS / 32] = wi;
+  }
+  __syncthreads();
+  const uint32_t r = sh[warp] + incl - v;
+  *total = sh[RLE_THREADS / 32];
+  __syncthreads();
+  return r;
+}
+
+// Run heads per tile of the sorted keys (a head starts a run of equal keys).
+__global__ void __launch_bounds__(RLE_THREADS) k_rle_tcount(const uint32_t* __restrict__ k, int64_t n,
+                                                            uint32_t* __restrict__ tcnt) {
+  __shared__ uint32_t sh[RLE_THREADS / 32];
+  const int64_t base = (int64_t)blockIdx.x * RLE_TILE;
+  uint32_t c = 0;
+#pragma unroll 4
+  for (int i = 0; i < RLE_ITEMS; ++i) {
+    const int64_t e = base + (int64_t)i * RLE_THREADS + threadIdx.x;
+    if (e < n && (e == 0 || __ldg(k + e) != __ldg(k + e - 1))) ++c;
+  }
+  const uint32_t t = rle_block_sum(c, sh);
+  if (threadIdx.x == 0) tcnt[blockIdx.x] = t;
+}
+
+// Run starts: hp[d] = first key index of run d (toff: exclusive scan of the tile head
+// counts). A thread flags 16 consecutive keys of the tile (staged in shared memory); the
+// tile's starts are collected in shared memory and written out coalesced. The last tile
+// sets hp[nd] = n and meta[0] = nd.
+__global__ void __launch_bounds__(RLE_THREADS) k_rle_starts(const uint32_t* __restrict__ k, int64_t n,
+                                                            const uint32_t* __restrict__ toff, int ntile,
+                                                            uint32_t* __restrict__ hp, uint32_t* __restrict__ meta) {
+  __shared__ uint32_t sh[RLE_THREADS / 32 + 1];
+  __shared__ uint32_t buf[RLE_TILE + RLE_TILE / 32];
+  __shared__ uint32_t first_head;
+#define PADJ(j) ((j) + ((j) >> 5))
+  const int64_t base = (int64_t)blockIdx.x * RLE_TILE;
+  for (int i = 0; i < RLE_ITEMS; ++i) {
+    const int j = i * RLE_THREADS + threadIdx.x;
+    const int64_t e = base + j;
+    buf[PADJ(j)] = e < n ? __ldg(k + e) : 0u;
+  }
+  if (threadIdx.x == 0) first_head = (base == 0 || __ldg(k + base) != __ldg(k + base - 1)) ? 1u : 0u;
+  __syncthreads();
+  uint32_t flags = 0;
+  const int j0 = threadIdx.x * RLE_ITEMS;
+#pragma unroll
+  for (int i = 0; i < RLE_ITEMS; ++i) {
+    const int j = j0 + i;
+    if (base + j < n) {
+      const bool head = j == 0 ? first_head != 0u : buf[PADJ(j)] != buf[PADJ(j - 1)];
+      flags |= (head ? 1u : 0u) << i;
     }
   }
+  uint32_t tot;
+  uint32_t pos = rle_block_excl((uint32_t)__popc(flags), sh, &tot);  // ends with a barrier: buf is free
+#pragma unroll
+  for (int i = 0; i < RLE_ITEMS; ++i)
+    if ((flags >> i) & 1u) buf[pos++] = (uint32_t)(base + j0 + i);
+  __syncthreads();
+  const uint32_t off = toff[blockIdx.x];
+  for (uint32_t j = threadIdx.x; j < tot; j += RLE_THREADS) hp[off + j] = buf[j];
+  if (blockIdx.x == ntile - 1 && threadIdx.x == 0) {
+    hp[off + tot] = (uint32_t)n;
+    meta[0] = off + tot;
+  }
+#undef PADJ
 }
 
-// Entries per run: the multiplicity is stored in 16 bits, so a run longer than 65535
-// takes several entries (zero past the last run).
-__global__ void k_rle_count(const uint32_t* __restrict__ hp, const uint32_t* __restrict__ meta, int64_t n,
-                            uint32_t* __restrict__ m) {
+// Entries past one per run, per tile of runs: a multiplicity above 65535 takes
+// ceil(len / 65535) entries.
+__global__ void __launch_bounds__(RLE_THREADS) k_rle_ecount(const uint32_t* __restrict__ hp,
+                                                            const uint32_t* __restrict__ meta,
+                                                            uint32_t* __restrict__ ecnt) {
+  __shared__ uint32_t sh[RLE_THREADS / 32];
   const uint32_t nd = meta[0];
-  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < n; d += (int64_t)gridDim.x * blockDim.x)
-    m[d] = d < nd ? (hp[d + 1] - hp[d] + 65534u) / 65535u : 0u;
+  const int64_t base = (int64_t)blockIdx.x * RLE_TILE;
+  uint32_t c = 0;
+  for (int i = 0; i < RLE_ITEMS; ++i) {
+    const int64_t d = base + (int64_t)i * RLE_THREADS + threadIdx.x;
+    if (d < nd) c += (hp[d + 1] - hp[d] - 1u) / 65535u;
+  }
+  const uint32_t t = rle_block_sum(c, sh);
+  if (threadIdx.x == 0) ecnt[blockIdx.x] = t;
 }
 
-// Entries of run d at epos[d]: (i_T | multiplicity << 16) and b~ gathered from b. A batch
-// row's entry (c, i) is the row-major index key = (c % ncell_inner) * IT + i over the
-// sampled modes and b is read at ((key / xPafter) * xI + row) * xPafter + key % xPafter
-// (X_(n) row `row`; for a plain solve xI = xPafter = 1 and the index is the key).
-// Entries per cell are added to nd (one atomic per cell and warp).
-__global__ void k_rle_emit(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ hp,
-                           const uint32_t* __restrict__ epos, const uint32_t* __restrict__ meta, int64_t n,
-                           uint32_t IT, uint32_t ncell_inner, int64_t xI, int64_t xPafter, const float* __restrict__ b,
-                           uint32_t* __restrict__ ent, float* __restrict__ bt, uint32_t* __restrict__ nd,
-                           unsigned long long* __restrict__ total) {
+// Entries of run d at d + (entries past one of the runs before d): (i_T | multiplicity << 16)
+// and b~ gathered from b. A batch row's entry (c, i) is the row-major index
+// key = (c % ncell_inner) * IT + i over the sampled modes and b is read at
+// ((key / xPafter) * xI + row) * xPafter + key % xPafter (X_(n) row `row`; for a plain solve
+// xI = xPafter = 1 and the index is the key). Entries per cell are added to nd (one atomic
+// per cell and warp). A tile of runs without long runs (ecnt = 0, nearly all) needs no
+// local scan.
+__global__ void __launch_bounds__(RLE_THREADS) k_rle_emit(const uint32_t* __restrict__ keys,
+                                                          const uint32_t* __restrict__ hp,
+                                                          const uint32_t* __restrict__ ecnt,
+                                                          const uint32_t* __restrict__ eoff,
+                                                          const uint32_t* __restrict__ meta, uint32_t IT,
+                                                          uint32_t ncell_inner, int64_t xI, int64_t xPafter,
+                                                          const float* __restrict__ b, uint32_t* __restrict__ ent,
+                                                          float* __restrict__ bt, uint32_t* __restrict__ nd,
+                                                          unsigned long long* __restrict__ total) {
+  __shared__ uint32_t sh[RLE_THREADS / 32 + 1];
   const uint32_t ndist = meta[0];
-  const int64_t nwork = ((int64_t)ndist + 31) / 32 * 32;
-  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < nwork; d += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t base = (int64_t)blockIdx.x * RLE_TILE;
+  if (base >= ndist) return;  // uniform over the block
+  const bool longruns = ecnt[blockIdx.x] != 0u;
+  uint32_t carry = eoff[blockIdx.x];
+  for (int it = 0; it < RLE_ITEMS; ++it) {
+    const int64_t d = base + (int64_t)it * RLE_THREADS + threadIdx.x;
     const bool live = d < ndist;
-    uint32_t cell = 0, m = 0;
+    uint32_t h0 = 0, cnt = 0, m = 0;
     if (live) {
-      const uint32_t h0 = hp[d];
-      uint32_t cnt = hp[d + 1] - h0;
+      h0 = hp[d];
+      cnt = hp[d + 1] - h0;
+      m = (cnt + 65534u) / 65535u;
+    }
+    uint32_t before = 0, tot = 0;
+    if (longruns) before = rle_block_excl(live ? m - 1u : 0u, sh, &tot);
+    uint32_t cell = 0;
+    if (live) {
       const uint32_t key = keys[h0];
       cell = key / IT;
       const uint32_t i = key - cell * IT;
@@ -252,8 +371,7 @@ __global__ void k_rle_emit(const uint32_t* __restrict__ keys, const uint32_t* __
         const int64_t bi = (xPafter == 1 && xI == 1) ? rk : ((rk / xPafter) * xI + row) * xPafter + rk % xPafter;
         bv = b[bi];
       }
-      uint32_t pos = epos[d];
-      m = (cnt + 65534u) / 65535u;
+      uint32_t pos = (uint32_t)d + carry + before;
       if (d == ndist - 1) total[0] = (unsigned long long)pos + m;
       while (cnt > 0) {
         const uint32_t take = cnt > 65535u ? 65535u : cnt;
@@ -263,6 +381,7 @@ __global__ void k_rle_emit(const uint32_t* __restrict__ keys, const uint32_t* __
         cnt -= take;
       }
     }
+    carry += tot;
     const unsigned act = __ballot_sync(0xffffffffu, live);
     if (live) {
       const unsigned peers = __match_any_sync(act, cell);
@@ -393,7 +512,7 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   uint32_t* keys = cv.take<uint32_t>(s);
   uint32_t* alt = cv.take<uint32_t>(s);
   uint32_t* hp = cv.take<uint32_t>(s + 1);
-  uint32_t* mcnt = cv.take<uint32_t>(s);
+  uint32_t* mcnt = cv.take<uint32_t>(rle_scratch_words(s));
   uint32_t* meta = cv.take<uint32_t>(4);
   unsigned long long* dsum = cv.take<unsigned long long>(1);
   uint16_t* gbuf = cv.take<uint16_t>((size_t)KR_MAX_MODES * GUIDE_MAX);
@@ -443,22 +562,28 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
     Carve sc = cv;
     KR_TRY(kr_radix_sort_u32(ctx, keys, alt, s, nbits, &sorted, sc));
   }
-  uint32_t* dpos = (sorted == keys) ? alt : keys;
-  KR_LAUNCH(ctx, k_rle_heads, grid_for(ctx, s, 256), 256, 0, sorted, s, dpos);
+  // run merge: tile head counts, run starts, long-run extras, entries (small per-tile
+  // arrays carved from the entry-count scratch)
+  const int ntile = (int)((s + RLE_TILE - 1) / RLE_TILE);
+  uint32_t* tcnt = mcnt;
+  uint32_t* toff = tcnt + ntile;
+  uint32_t* ecnt = toff + ntile;
+  uint32_t* eoff = ecnt + ntile;
+  KR_LAUNCH(ctx, k_rle_tcount, ntile, RLE_THREADS, 0, sorted, s, tcnt);
   {
     Carve sc = cv;
-    KR_TRY(kr_scan_u32(ctx, dpos, dpos, s, sc));
+    KR_TRY(kr_scan_u32(ctx, tcnt, toff, ntile, sc));
   }
-  KR_LAUNCH(ctx, k_rle_pos, grid_for(ctx, s, 256), 256, 0, sorted, dpos, s, hp, meta);
-  KR_LAUNCH(ctx, k_rle_count, grid_for(ctx, s, 256), 256, 0, hp, meta, s, mcnt);
+  KR_LAUNCH(ctx, k_rle_starts, ntile, RLE_THREADS, 0, sorted, s, toff, ntile, hp, meta);
+  KR_LAUNCH(ctx, k_rle_ecount, ntile, RLE_THREADS, 0, hp, meta, ecnt);
   {
     Carve sc = cv;
-    KR_TRY(kr_scan_u32(ctx, mcnt, mcnt, s, sc));
+    KR_TRY(kr_scan_u32(ctx, ecnt, eoff, ntile, sc));
   }
   // b may still be arriving on the context's copy stream (host-buffer solves): the gather
   // is its first reader
   if (ctx->b_wait) KR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->b_wait, 0));
-  KR_LAUNCH(ctx, k_rle_emit, grid_for(ctx, s, 256), 256, 0, sorted, hp, mcnt, meta, s, IT, (uint32_t)sk->ncell_inner,
+  KR_LAUNCH(ctx, k_rle_emit, ntile, RLE_THREADS, 0, sorted, hp, ecnt, eoff, meta, IT, (uint32_t)sk->ncell_inner,
             sk->xI, sk->xPafter, b, sk->ent, sk->bt, sk->cell_nd, dsum);
   {
     Carve sc = cv;
@@ -490,7 +615,7 @@ void kr_sketch_scratch_need(int64_t s, int64_t ncell, Need& nd) {
   nd.add<uint32_t>(s);      // keys
   nd.add<uint32_t>(s);      // sort buffer / run index
   nd.add<uint32_t>(s + 1);  // run starts
-  nd.add<uint32_t>(s);      // entries per run / entry positions
+  nd.add<uint32_t>(rle_scratch_words(s));  // run merge: tile head counts and offsets, long-run extras
   nd.add<uint32_t>(4);
   nd.add<unsigned long long>(1);
   nd.add<uint16_t>((size_t)KR_MAX_MODES * GUIDE_MAX);

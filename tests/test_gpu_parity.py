@@ -141,6 +141,32 @@ def test_sketch_grouping_weights_gather(I, R, s):
     sk.free()
 
 
+def test_sketch_long_runs_split_into_entries():
+    """A row drawn more than 65535 times is stored as several entries of the same row (the
+    multiplicity field is 16 bits): per row, the entries' counts add up to the oracle's
+    multiplicity, the dominant row takes ceil(count / 65535) entries, and b~ and the weights
+    are those of the row."""
+    As = f32_factors([np.array([[100.0], [1.0], [1.0]]), np.array([[1.0], [50.0]]),
+                      np.array([[80.0], [1.0], [2.0], [1.0]])])
+    I = [3, 2, 4]
+    b = np.arange(24, dtype=np.float32) + 1.0
+    s = 400000
+    cdfs, probs, t = tables(As)
+    sk = kr.kron_sketch([dev(A) for A in As], t["cdf"], t["prob"], dev(b), s, 21, 3)
+    keys, counts, omega, bt = (host(v) for v in sk.export())
+    sk.free()
+    rk, rc = ko.group_samples(ko.sample_draws(cdfs, s, 21, 3), I)
+    uk, inv = np.unique(keys, return_inverse=True)
+    np.testing.assert_array_equal(uk, rk)
+    np.testing.assert_array_equal(np.bincount(inv, weights=counts).astype(np.int64), rc)
+    assert int(counts.sum()) == s and counts.max() <= 65535
+    top = int(np.argmax(rc))
+    assert rc[top] > 2 * 65535
+    assert int(np.sum(keys == rk[top])) == -(-int(rc[top]) // 65535)
+    np.testing.assert_array_equal(bt, b[keys])
+    np.testing.assert_allclose(omega, ko.sample_weights(keys, counts, probs, I, s), rtol=1e-6)
+
+
 # ------------------------------------------------------------------ KronMatMul, preconditioner
 
 @pytest.mark.parametrize("I,R", SHAPES)
