@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_sums(uint32_t* __restrict
   }
 }
 
-// Phase 3: scan inside each tile (thread-contiguous runs), plus the tile offset.
+// Phase 3: scan inside each tile (thread-contiguous runs), plus the tile offset (none when
+// tile_off is null: a single tile is the whole scan).
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const uint32_t* __restrict__ in, int64_t n,
                                                               const uint32_t* __restrict__ tile_off,
                                                               uint32_t* __restrict__ out) {
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const uint32_t* __r
     s += v[k];
   }
   uint32_t total;
-  uint32_t run = tile_off[blockIdx.x] + block_excl_scan(s, sh, &total);
+  uint32_t run = (tile_off ? tile_off[blockIdx.x] : 0u) + block_excl_scan(s, sh, &total);
 #pragma unroll
   for (int k = 0; k < SCAN_PER_THREAD; ++k) {
     buf[PADJ(threadIdx.x * SCAN_PER_THREAD + k)] = run;
@@ -172,6 +173,10 @@ kr_status kr_scan_u32(kr_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
   uint32_t* ts = cv.take<uint32_t>(ntile + 1);
   if (cv.off > cv.cap) return kr_fail(ctx, KR_ENOMEM, "scan: workspace too small");
   if (ntile == 0) return KR_OK;
+  if (ntile == 1) {  // one block scans it all
+    KR_LAUNCH(ctx, k_scan_apply, 1, SCAN_THREADS, 0, in, n, (const uint32_t*)nullptr, out);
+    return KR_OK;
+  }
   KR_LAUNCH(ctx, k_scan_tiles, (unsigned)ntile, SCAN_THREADS, 0, in, n, ts);
   KR_LAUNCH(ctx, k_scan_sums, 1, SCAN_THREADS, 0, ts, ntile);
   KR_LAUNCH(ctx, k_scan_apply, (unsigned)ntile, SCAN_THREADS, 0, in, n, ts, out);
