@@ -206,8 +206,14 @@ constexpr int RLE_THREADS = 256;
 constexpr int RLE_ITEMS = 16;
 constexpr int RLE_TILE = RLE_THREADS * RLE_ITEMS;  // keys (or runs) per block
 
-// Words of the run merge's per-tile arrays (head counts, their offsets, extras, theirs).
-int64_t rle_scratch_words(int64_t s) { return 4 * ((s + RLE_TILE - 1) / RLE_TILE); }
+constexpr int RUN_ITEMS = 4;                          // runs per thread in the extras count and the emit
+constexpr int RUN_TILE = RLE_THREADS * RUN_ITEMS;      // runs per block there
+
+// Words of the run merge's per-tile arrays: head counts and their offsets per key tile,
+// extras and their offsets per run tile.
+int64_t rle_scratch_words(int64_t s) {
+  return 2 * ((s + RLE_TILE - 1) / RLE_TILE) + 2 * ((s + RUN_TILE - 1) / RUN_TILE);
+}
 
 __device__ __forceinline__ uint32_t rle_block_sum(uint32_t v, uint32_t* sh) {  // sh: RLE_THREADS / 32 words
 #pragma unroll
@@ -316,9 +322,10 @@ __global__ void __launch_bounds__(RLE_THREADS) k_rle_ecount(const uint32_t* __re
                                                             uint32_t* __restrict__ ecnt) {
   __shared__ uint32_t sh[RLE_THREADS / 32];
   const uint32_t nd = meta[0];
-  const int64_t base = (int64_t)blockIdx.x * RLE_TILE;
+  const int64_t base = (int64_t)blockIdx.x * RUN_TILE;
   uint32_t c = 0;
-  for (int i = 0; i < RLE_ITEMS; ++i) {
+#pragma unroll
+  for (int i = 0; i < RUN_ITEMS; ++i) {
     const int64_t d = base + (int64_t)i * RLE_THREADS + threadIdx.x;
     if (d < nd) c += (hp[d + 1] - hp[d] - 1u) / 65535u;
   }
@@ -344,11 +351,12 @@ __global__ void __launch_bounds__(RLE_THREADS) k_rle_emit(const uint32_t* __rest
                                                           unsigned long long* __restrict__ total) {
   __shared__ uint32_t sh[RLE_THREADS / 32 + 1];
   const uint32_t ndist = meta[0];
-  const int64_t base = (int64_t)blockIdx.x * RLE_TILE;
+  const int64_t base = (int64_t)blockIdx.x * RUN_TILE;
   if (base >= ndist) return;  // uniform over the block
   const bool longruns = ecnt[blockIdx.x] != 0u;
   uint32_t carry = eoff[blockIdx.x];
-  for (int it = 0; it < RLE_ITEMS; ++it) {
+#pragma unroll
+  for (int it = 0; it < RUN_ITEMS; ++it) {
     const int64_t d = base + (int64_t)it * RLE_THREADS + threadIdx.x;
     const bool live = d < ndist;
     uint32_t h0 = 0, cnt = 0, m = 0;
@@ -565,25 +573,26 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   // run merge: tile head counts, run starts, long-run extras, entries (small per-tile
   // arrays carved from the entry-count scratch)
   const int ntile = (int)((s + RLE_TILE - 1) / RLE_TILE);
+  const int nrt = (int)((s + RUN_TILE - 1) / RUN_TILE);  // run tiles (the run count is at most s)
   uint32_t* tcnt = mcnt;
   uint32_t* toff = tcnt + ntile;
   uint32_t* ecnt = toff + ntile;
-  uint32_t* eoff = ecnt + ntile;
+  uint32_t* eoff = ecnt + nrt;
   KR_LAUNCH(ctx, k_rle_tcount, ntile, RLE_THREADS, 0, sorted, s, tcnt);
   {
     Carve sc = cv;
     KR_TRY(kr_scan_u32(ctx, tcnt, toff, ntile, sc));
   }
   KR_LAUNCH(ctx, k_rle_starts, ntile, RLE_THREADS, 0, sorted, s, toff, ntile, hp, meta);
-  KR_LAUNCH(ctx, k_rle_ecount, ntile, RLE_THREADS, 0, hp, meta, ecnt);
+  KR_LAUNCH(ctx, k_rle_ecount, nrt, RLE_THREADS, 0, hp, meta, ecnt);
   {
     Carve sc = cv;
-    KR_TRY(kr_scan_u32(ctx, ecnt, eoff, ntile, sc));
+    KR_TRY(kr_scan_u32(ctx, ecnt, eoff, nrt, sc));
   }
   // b may still be arriving on the context's copy stream (host-buffer solves): the gather
   // is its first reader
   if (ctx->b_wait) KR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->b_wait, 0));
-  KR_LAUNCH(ctx, k_rle_emit, ntile, RLE_THREADS, 0, sorted, hp, ecnt, eoff, meta, IT, (uint32_t)sk->ncell_inner,
+  KR_LAUNCH(ctx, k_rle_emit, nrt, RLE_THREADS, 0, sorted, hp, ecnt, eoff, meta, IT, (uint32_t)sk->ncell_inner,
             sk->xI, sk->xPafter, b, sk->ent, sk->bt, sk->cell_nd, dsum);
   {
     Carve sc = cv;
