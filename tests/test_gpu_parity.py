@@ -228,6 +228,9 @@ def _oracle_same_sample(As, b, rep, seed, cid, cdfs, probs, lam, eps):
     ([65], [5], "gauss"),
     ([9, 11, 7, 13], [2, 3, 2, 4], "outliers"),
     ([130, 70, 33], [33, 9, 17], "gauss"),
+    ([1, 60, 45], [1, 6, 5], "gauss"),         # a mode with a single row: one slab of cells
+    ([50, 1, 40], [5, 1, 4], "lognormal_rows"),  # single-row middle mode: cells = slabs
+    ([40, 30, 1], [4, 3, 1], "gauss"),         # single-row last mode: one sampled row per cell
 ])
 def test_regress_matches_oracle_on_same_sample(I, R, dist):
     prob = kron_problem(I, R, dist=dist, seed=12, noise_rel=0.05)
