@@ -318,9 +318,10 @@ struct kr_tiles {
   double* objpart = nullptr;     // ntmax: per-tile sampled objective (FP64; zero past the last)
 };
 
-// Whether the sketch/shape admits the slab pass (single right-hand side, N >= 2,
-// R[N-2] <= 64, R[N-1] <= 64, shared memory for two teams).
-bool kr_slab_eligible(kr_ctx* ctx, const Modes& m, const kr_sketch* sk);
+// Whether the sketch/shape admits the slab pass (N >= 2, R[N-2] <= 64, R[N-1] <= 64,
+// shared memory for two teams; a single right-hand side unless `rows`, where each row of a
+// batched-row sketch is its own group of slabs with its own X1).
+bool kr_slab_eligible(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, bool rows = false);
 void kr_tiles_setup(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, kr_tiles* tl);
 void kr_tiles_own_need(const kr_tiles* tl, int64_t ncell, Need& nd);
 void kr_tiles_layout(kr_tiles* tl, int64_t ncell, Carve& cv);

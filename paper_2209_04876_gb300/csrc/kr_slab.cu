@@ -917,8 +917,8 @@ int grid_n(kr_ctx* ctx, int64_t n, int block = 256) {
 
 }  // namespace
 
-bool kr_slab_eligible(kr_ctx* ctx, const Modes& m, const kr_sketch* sk) {
-  if (m.N < 2 || sk->nrow != 1) return false;
+bool kr_slab_eligible(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, bool rows) {
+  if (m.N < 2 || (sk->nrow != 1 && !rows)) return false;
   const int RT = m.R[m.N - 1], R2 = m.R[m.N - 2];
   if (RT > 64 || R2 > 64 || m.I[m.N - 1] > 65535) return false;
   return slab_layout(m.I[m.N - 1], RT, R2, false).bytes <= ctx->smem_optin;
@@ -930,8 +930,8 @@ void kr_tiles_setup(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, kr_tiles* 
   tl->R2 = m.R[N - 2];
   tl->IT = m.I[N - 1];
   tl->RT = m.R[N - 1];
-  int64_t P = 1;
-  for (int n = 0; n < N - 2; ++n) P *= m.I[n];
+  // slabs: the cells without their last index (a batched-row sketch's row axis included)
+  const int64_t P = sk->ncell / tl->I2;
   tl->P = P;
   tl->cb = cb_for(rt_pad(tl->RT));
   tl->et = ctx->slab_tile_entries;

@@ -364,6 +364,12 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   kr_sketch_setup_rows(&sk, mo, cfg.s, In, In, Pafter);
   const int RT = mo.R[No - 1];
   const int64_t cells = sk.ncell;
+  // two other modes: the sampled products of every row by the fused slab pass (each row is
+  // its own group of slabs, its z block the slab's X1), else the per-cell pass between two
+  // batched mode products
+  const bool slab = ctx->slab_pass && No == 2 && kr_slab_eligible(ctx, mo, &sk, true);
+  kr_tiles tl;
+  if (slab) kr_tiles_setup(ctx, mo, &sk, &tl);
   // largest batched intermediate: forward (In, I_o..., R_T) or the precond (In, Rne); also Rn x Rne batches
   int64_t mx = (int64_t)In * Rne;
   {
@@ -397,7 +403,15 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   nd.add<double>(3 * (int64_t)In + 8);                // row stats, reductions
   nd.add<int>(8);
   nd.add<double>(1024);                               // resid partials
-  kr_sketch_scratch_need(sk.s, cells, nd);
+  if (slab) kr_tiles_own_need(&tl, cells, nd);
+  {
+    Need sc = nd;  // the tile construction reuses the sketch build's scratch
+    kr_sketch_scratch_need(sk.s, cells, nd);
+    if (slab) {
+      kr_tiles_scratch_need(&tl, cells, sc);
+      if (sc.off > nd.off) nd.off = sc.off;
+    }
+  }
   KR_TRY(kr_ws_reserve(ctx, nd.off));
   KR_TRY(kr_hbuf_reserve(ctx, 4096));
   Carve cv(ctx->ws, ctx->ws_size);
@@ -479,6 +493,7 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   double* red = rowstat + 3 * (int64_t)In;
   int* flag = cv.take<int>(8);
   double* rpart = cv.take<double>(1024);
+  if (slab) kr_tiles_layout(&tl, cells, cv);
   (void)spare;
   // A^-1 U (rows: A^-1 applied to each column of G+), capacitance and its inverse
   KR_TRY(base_apply(ctx, to, Rn, w, GpT, AinvUt, t0, t1));
@@ -489,7 +504,11 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     KR_LAUNCH(ctx, k_gauss_jordan, 1, 256, sm, C, Rn, Cinv, flag);
   }
   // batched sketch: row i of X_(n), fresh draws per row (counter row = i)
-  KR_TRY(kr_sketch_fill(ctx, mo, to, X, seed, call_id, 0, &sk, cv));
+  {
+    Carve sc = cv;
+    KR_TRY(kr_sketch_fill(ctx, mo, to, X, seed, call_id, 0, &sk, sc));
+  }
+  if (slab) KR_TRY(kr_tiles_build(ctx, &sk, &tl, cv));
   KR_CUDA(ctx, cudaMemsetAsync(Z, 0, sizeof(float) * ZL, ctx->stream));
   // mode-product plans over the batch axis
   int dfw_in[KR_MAX_MODES], dfw_out[KR_MAX_MODES], trf[KR_MAX_MODES], trb[KR_MAX_MODES];
@@ -512,9 +531,14 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   for (it = 1; it <= cfg.max_iter; ++it) {
     int used = 0;
     // sampled part: Gb = K~^T Omega (b~ - K~ z) per row
-    KR_TRY(kr_kron_apply2(ctx, No + 1, dfw_in, dfw_out, Bf, trf, Z, Y, t0, t1));
-    KR_TRY(kr_sketch_resid(ctx, &sk, mo.A[No - 1], RT, Y, W, rpart, nblk, &used));
-    KR_TRY(kr_kron_apply2(ctx, No + 1, dfw_out, dfw_in, Bf, trb, W, Gb, t0, t1));
+    if (slab) {
+      KR_TRY(kr_slab_pass(ctx, &sk, &tl, mo.A[0], mo.A[1], Z, false));
+      KR_TRY(kr_tile_reduce(ctx, &tl, nullptr, Gb));
+    } else {
+      KR_TRY(kr_kron_apply2(ctx, No + 1, dfw_in, dfw_out, Bf, trf, Z, Y, t0, t1));
+      KR_TRY(kr_sketch_resid(ctx, &sk, mo.A[No - 1], RT, Y, W, rpart, nblk, &used));
+      KR_TRY(kr_kron_apply2(ctx, No + 1, dfw_out, dfw_in, Bf, trb, W, Gb, t0, t1));
+    }
     // grad = w z + G+ (lambda (G+)^T z - w G z) - Gb  (FP64 combination, one block per row)
     KR_LAUNCH(ctx, k_penalty_rows, In, 256, sizeof(double) * Rne, Z, Gn, gp64, Gb, Rn, (int)Rne, cfg.lambda, w, Gr,
               (float*)nullptr);
