@@ -764,6 +764,15 @@ __global__ void __launch_bounds__(256) k_pc_rows(PcModes pm, const float* __rest
   RichSnap snap = {};
   if (threadIdx.x == 0 && ra.st) snap = rich_load(ra.st);
   const int j = blockIdx.x / S, s = blockIdx.x - j * S;
+  float* xr = x + (int64_t)j * Q + (int64_t)s * nq;
+  // this thread's first four entries of x in flight with the slab (the update at the end
+  // uses them; blocks of 256 threads)
+  float xv[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int e = threadIdx.x + k * 256;
+    xv[k] = e < nq ? xr[e] : 0.f;
+  }
   const float* src = in + (int64_t)j * Q;
   for (int e = threadIdx.x; e < Q; e += blockDim.x) full[e] = __ldg(src + e);
   __syncthreads();
@@ -779,8 +788,19 @@ __global__ void __launch_bounds__(256) k_pc_rows(PcModes pm, const float* __rest
   __syncthreads();
   pc_modes_from(pm, sB, boff, t, u, nq, 2, nr);
   float s1 = 0.f, s2 = 0.f, bad = 0.f;
-  float* xr = x + (int64_t)j * Q + (int64_t)s * nq;
-  for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {  // the prefetched entries
+    const int e = threadIdx.x + k * 256;
+    if (e < nq) {
+      const float st = alpha * t[e];
+      const float xn = xv[k] + st;
+      xr[e] = xn;
+      s1 = fmaf(st, st, s1);
+      s2 = fmaf(xn, xn, s2);
+      if (!isfinite(xn)) bad = 1.f;
+    }
+  }
+  for (int e = threadIdx.x + 4 * 256; e < nq; e += blockDim.x) {  // larger slabs: the rest
     const float st = alpha * t[e];
     const float xn = xr[e] + st;
     xr[e] = xn;
