@@ -171,7 +171,7 @@ KR_API kr_status kron_leverage(kr_ctx* ctx, const kr_factors* f, double* const l
 /* ---------------------------------------------------------------- a3 */
 
 /* SampleRows on K from the product distribution (§3 Def. of leverage score
- * sampling; Alg. 2 line "S <- RowSampling(K, s, P)"; coordinates drawn
+ * sampling; the row-sampling step of Alg. 2; coordinates drawn
  * independently per factor, proof of Thm 4.5).
  * Draw t, coordinate m (position in this call's mode list) uses the uniform
  * u = (((wa << 32) | wb) >> 11) * 2^-53 from Philox4x32-10 (Salmon et al. 2011) with
