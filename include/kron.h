@@ -120,7 +120,7 @@ enum {
   KR_K_RESID = 0,      /* sampled residual + transpose accumulation (a7 + a8) */
   KR_K_MODEPROD = 1,   /* mode-n products (KronMatMul, preconditioner) */
   KR_K_SAMPLE = 2,     /* Philox sampling of the row keys (a3) */
-  KR_K_SCATTER = 3,    /* radix sort of the row keys (grouping, a4) */
+  KR_K_SCATTER = 3,    /* grouping of the row keys: radix sort or key-bitmap ranks (a4) */
   KR_K_DEDUP = 4,      /* merge of repeated rows + gather of b (a4 + a5) */
   KR_K_TABLES = 5,     /* Gram, Cholesky, leverage, CDF, eigen (a1 + a2) */
   KR_K_VECTOR = 6,     /* Richardson update, reductions (a10) */
@@ -144,8 +144,20 @@ enum {
  *    concurrently, each by a worker context with its own stream and workspace (created on
  *    first use, kept until kr_destroy). 1 solves them one after another on ctx's stream.
  *    Every problem's result is the same whatever the number of workers.
+ *  KR_OPT_GROUPING (default 0): how the draws of a sketch are grouped into merged rows.
+ *    1 sorts the row keys (stable LSD radix sort) and merges the runs of equal keys; 2 sets
+ *    one bit per draw in a bitmap of the key space (prod I_n keys, at most 2^32; 8 bytes of
+ *    workspace per 32 keys), ranks the set bits and counts the draws per rank with integer
+ *    atomics; 0 takes 2 when the key space is at most 64 times the draw count, else 1. Both
+ *    give identical sketches.
  * Returns KR_EINVAL for an unknown key or a value out of range. */
-enum { KR_OPT_SLAB_PASS = 1, KR_OPT_SLAB_TILE_ENTRIES = 2, KR_OPT_DEVICE_LOOP = 3, KR_OPT_BATCH_WORKERS = 4 };
+enum {
+  KR_OPT_SLAB_PASS = 1,
+  KR_OPT_SLAB_TILE_ENTRIES = 2,
+  KR_OPT_DEVICE_LOOP = 3,
+  KR_OPT_BATCH_WORKERS = 4,
+  KR_OPT_GROUPING = 5
+};
 KR_API kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value);
 
 KR_API kr_status kr_timing_enable(kr_ctx* ctx, int32_t on);

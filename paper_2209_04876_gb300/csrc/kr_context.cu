@@ -74,6 +74,10 @@ extern "C" kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value) {
       if (value < 1 || value > 32) return kr_fail(ctx, KR_EINVAL, "kr_set_option: batch workers must be in [1, 32]");
       ctx->batch_workers = (int)value;
       return KR_OK;
+    case KR_OPT_GROUPING:
+      if (value < 0 || value > 2) return kr_fail(ctx, KR_EINVAL, "kr_set_option: grouping must be 0, 1 or 2");
+      ctx->grouping = (int)value;
+      return KR_OK;
     default:
       return kr_fail(ctx, KR_EINVAL, "kr_set_option: unknown key %d", key);
   }
@@ -236,7 +240,7 @@ int kr_kind_of(const char* k) {
   if (s.find("k_sample") != std::string::npos || s.find("k_draw") != std::string::npos ||
       s.find("k_guide") != std::string::npos)
     return KR_K_SAMPLE;
-  if (s.find("k_radix") != std::string::npos) return KR_K_SCATTER;
+  if (s.find("k_radix") != std::string::npos || s.find("k_bm_") != std::string::npos) return KR_K_SCATTER;
   if (s.find("k_rle") != std::string::npos || s.find("k_cell_w") != std::string::npos) return KR_K_DEDUP;
   if (s.find("k_gram") != std::string::npos || s.find("k_chol") != std::string::npos ||
       s.find("k_leverage") != std::string::npos || s.find("k_cdf") != std::string::npos ||

@@ -34,6 +34,7 @@ struct kr_ctx {
   uint32_t slab_tile_entries = 16384;
   int device_loop = 1;  // Richardson iterations 2.. as one CUDA graph with a conditional loop
   int batch_workers = 4;  // kron_ridge_batched: problems solved concurrently (worker contexts)
+  int grouping = 0;       // draws grouped by: 0 automatic, 1 radix sort, 2 ranks in a key bitmap
   // worker contexts of kron_ridge_batched, each with its own stream and workspace (owned)
   std::vector<kr_ctx*> workers;
   std::vector<cudaStream_t> worker_streams;
@@ -268,7 +269,10 @@ void kr_sketch_setup(kr_sketch* sk, const Modes& m, int64_t s);
 void kr_sketch_setup_rows(kr_sketch* sk, const Modes& m, int64_t s_row, int nrow, int64_t xI, int64_t xPafter);
 void kr_sketch_own_need(const kr_sketch* sk, Need& nd);
 void kr_sketch_layout(kr_sketch* sk, Carve& cv);
-void kr_sketch_scratch_need(int64_t s, int64_t ncell, Need& nd);
+void kr_sketch_scratch_need(const kr_ctx* ctx, int64_t s, int64_t ncell, int64_t IT, Need& nd);
+// Grouping of the draws: by ranks in a bitmap of the key space (ncell * IT keys) or by
+// radix sort (KR_OPT_GROUPING; automatic: ranks when the key space is at most 64 s).
+bool kr_group_by_rank(const kr_ctx* ctx, int64_t s, int64_t keyspace);
 // With defer_distinct the distinct-row count is copied to the context's pinned buffer at
 // KR_HBUF_DISTINCT without a synchronisation (sk->distinct = -1 until the caller reads it
 // after its next stream synchronisation).

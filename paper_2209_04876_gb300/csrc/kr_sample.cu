@@ -131,12 +131,13 @@ __device__ __forceinline__ int guided_search(const uint64_t* thr, const uint16_t
 // Solver path: every draw's row key cell * IT + i_T (cell = r * ncell_inner +
 // (i_1..i_{N-1}) for draw batch r, the linear row index of the batched system). Draws
 // come in nrow batches of s_row (one per Tucker factor row; nrow = 1 for a plain solve);
-// draw t of batch r uses Philox counter row row0 + r. Templated on N so the per-draw
+// draw t of batch r uses Philox counter row row0 + r. With a key bitmap (grouping by
+// rank, below) every draw also sets its key's bit there. Templated on N so the per-draw
 // indices and table pointers stay in registers.
 template <int N>
 __global__ void __launch_bounds__(256) k_draw_keys(DrawModes dm, int64_t s_row, int nrow, uint32_t k0, uint32_t k1,
                                                    uint32_t row0, uint32_t cid, uint32_t ncell_inner,
-                                                   uint32_t* __restrict__ keys) {
+                                                   uint32_t* __restrict__ keys, uint2* __restrict__ bm) {
   __shared__ uint64_t s_thr[THR_SMEM];
   __shared__ uint16_t s_guide[THR_SMEM];
   const uint64_t* thr[N];
@@ -190,7 +191,9 @@ __global__ void __launch_bounds__(256) k_draw_keys(DrawModes dm, int64_t s_row, 
 #pragma unroll
     for (int n = 0; n < N - 1; ++n) cell = cell * (uint32_t)In[n] + (uint32_t)idx[n];
     cell += r * ncell_inner;
-    keys[t] = cell * IT + (uint32_t)idx[N - 1];
+    const uint32_t key = cell * IT + (uint32_t)idx[N - 1];
+    keys[t] = key;
+    if (bm) atomicOr(&bm[key >> 5].x, 1u << (key & 31));
   }
 }
 
@@ -315,8 +318,16 @@ __global__ void __launch_bounds__(RLE_THREADS) k_rle_starts(const uint32_t* __re
 #undef PADJ
 }
 
+// Multiplicity of run d: from the run starts (sorted keys) or the counts (grouping by
+// rank, RANKED).
+template <bool RANKED>
+__device__ __forceinline__ uint32_t run_len(const uint32_t* __restrict__ hp, int64_t d) {
+  return RANKED ? hp[d] : hp[d + 1] - hp[d];
+}
+
 // Entries past one per run, per tile of runs: a multiplicity above 65535 takes
 // ceil(len / 65535) entries.
+template <bool RANKED>
 __global__ void __launch_bounds__(RLE_THREADS) k_rle_ecount(const uint32_t* __restrict__ hp,
                                                             const uint32_t* __restrict__ meta,
                                                             uint32_t* __restrict__ ecnt) {
@@ -327,7 +338,7 @@ __global__ void __launch_bounds__(RLE_THREADS) k_rle_ecount(const uint32_t* __re
 #pragma unroll
   for (int i = 0; i < RUN_ITEMS; ++i) {
     const int64_t d = base + (int64_t)i * RLE_THREADS + threadIdx.x;
-    if (d < nd) c += (hp[d + 1] - hp[d] - 1u) / 65535u;
+    if (d < nd) c += (run_len<RANKED>(hp, d) - 1u) / 65535u;
   }
   const uint32_t t = rle_block_sum(c, sh);
   if (threadIdx.x == 0) ecnt[blockIdx.x] = t;
@@ -339,7 +350,8 @@ __global__ void __launch_bounds__(RLE_THREADS) k_rle_ecount(const uint32_t* __re
 // ((key / xPafter) * xI + row) * xPafter + key % xPafter (X_(n) row `row`; for a plain solve
 // xI = xPafter = 1 and the index is the key). Entries per cell are added to nd (one atomic
 // per cell and warp). A tile of runs without long runs (ecnt = 0, nearly all) needs no
-// local scan.
+// local scan. RANKED (grouping by rank): keys[d] is run d's key and hp[d] its multiplicity.
+template <bool RANKED>
 __global__ void __launch_bounds__(RLE_THREADS) k_rle_emit(const uint32_t* __restrict__ keys,
                                                           const uint32_t* __restrict__ hp,
                                                           const uint32_t* __restrict__ ecnt,
@@ -361,8 +373,8 @@ __global__ void __launch_bounds__(RLE_THREADS) k_rle_emit(const uint32_t* __rest
     const bool live = d < ndist;
     uint32_t h0 = 0, cnt = 0, m = 0;
     if (live) {
-      h0 = hp[d];
-      cnt = hp[d + 1] - h0;
+      h0 = RANKED ? (uint32_t)d : hp[d];
+      cnt = run_len<RANKED>(hp, d);
       m = (cnt + 65534u) / 65535u;
     }
     uint32_t before = 0, tot = 0;
@@ -396,6 +408,116 @@ __global__ void __launch_bounds__(RLE_THREADS) k_rle_emit(const uint32_t* __rest
       const uint32_t sum = __reduce_add_sync(peers, m);
       if ((peers & ((1u << (threadIdx.x & 31)) - 1u)) == 0u) atomicAdd(&nd[cell], sum);
     }
+  }
+}
+
+// ------------------------------------------------------------------ grouping by rank
+//
+// When the key space ncell * IT is not much larger than the number of draws, one bit per
+// possible key replaces the sort. The draws set their keys' bits; a scan of the bitmap's
+// popcounts gives every set bit its rank (the distinct keys in increasing order: the runs
+// of the sorted keys, in the same order), and every draw adds one to the count at its
+// key's rank. Integer additions commute, so the counts are those of the runs whatever the
+// order of the atomics, and the emit above writes the same entries as after a sort.
+// Bitmap words are uint2 {bits, distinct keys before the word}.
+
+constexpr int BM_ITEMS = 8;                      // bitmap words per thread in the rank scan
+constexpr int BM_TILE = RLE_THREADS * BM_ITEMS;  // bitmap words per block
+constexpr int BM_KEYCAP = 6144;                  // keys of a tile staged in shared memory
+
+// Set bits per tile of bitmap words.
+__global__ void __launch_bounds__(RLE_THREADS) k_bm_tcount(const uint2* __restrict__ bm, int64_t nw,
+                                                           uint32_t* __restrict__ tcnt) {
+  __shared__ uint32_t sh[RLE_THREADS / 32];
+  const int64_t base = (int64_t)blockIdx.x * BM_TILE;
+  uint32_t c = 0;
+#pragma unroll
+  for (int i = 0; i < BM_ITEMS; ++i) {
+    const int64_t w = base + (int64_t)i * RLE_THREADS + threadIdx.x;
+    if (w < nw) c += (uint32_t)__popc(__ldg(&bm[w].x));
+  }
+  const uint32_t t = rle_block_sum(c, sh);
+  if (threadIdx.x == 0) tcnt[blockIdx.x] = t;
+}
+
+// Ranks: bm[w].y = distinct keys before word w (toff: exclusive scan of the tile counts),
+// dk[d] = the d-th distinct key, cnt[d] = 0 (the counts are added next). A thread ranks
+// BM_ITEMS consecutive words of the tile (staged in shared memory); the tile's keys are
+// collected in shared memory and written out coalesced (a dense tile with more than
+// BM_KEYCAP keys writes them directly). The last tile sets meta[0] = distinct keys.
+__global__ void __launch_bounds__(RLE_THREADS) k_bm_rank(uint2* __restrict__ bm, int64_t nw,
+                                                         const uint32_t* __restrict__ toff, int ntile,
+                                                         uint32_t* __restrict__ dk, uint32_t* __restrict__ cnt,
+                                                         uint32_t* __restrict__ meta) {
+  __shared__ uint32_t sh[RLE_THREADS / 32 + 1];
+  __shared__ uint32_t bits[BM_TILE + BM_TILE / 32];
+  __shared__ uint32_t pre[BM_TILE + BM_TILE / 32];
+  __shared__ uint32_t skeys[BM_KEYCAP];
+#define PADJ(j) ((j) + ((j) >> 5))
+  const int64_t base = (int64_t)blockIdx.x * BM_TILE;
+  for (int i = 0; i < BM_ITEMS; ++i) {
+    const int j = i * RLE_THREADS + threadIdx.x;
+    const int64_t w = base + j;
+    bits[PADJ(j)] = w < nw ? bm[w].x : 0u;
+  }
+  __syncthreads();
+  const int j0 = threadIdx.x * BM_ITEMS;
+  uint32_t c = 0;
+#pragma unroll
+  for (int i = 0; i < BM_ITEMS; ++i) c += (uint32_t)__popc(bits[PADJ(j0 + i)]);
+  uint32_t tot;
+  uint32_t pos = rle_block_excl(c, sh, &tot);  // ends with a barrier
+  const uint32_t off = toff[blockIdx.x];
+  const bool staged = tot <= (uint32_t)BM_KEYCAP;  // uniform over the block
+#pragma unroll
+  for (int i = 0; i < BM_ITEMS; ++i) {
+    const int j = j0 + i;
+    uint32_t v = bits[PADJ(j)];
+    pre[PADJ(j)] = off + pos;
+    const uint32_t kb = (uint32_t)(base + j) << 5;  // key space <= 2^32: word index < 2^27
+    while (v) {
+      const uint32_t key = kb + (uint32_t)(__ffs(v) - 1);
+      if (staged)
+        skeys[pos] = key;
+      else
+        dk[off + pos] = key;
+      ++pos;
+      v &= v - 1u;
+    }
+  }
+  __syncthreads();
+  for (int i = 0; i < BM_ITEMS; ++i) {
+    const int j = i * RLE_THREADS + threadIdx.x;
+    const int64_t w = base + j;
+    if (w < nw) bm[w].y = pre[PADJ(j)];
+  }
+  for (uint32_t j = threadIdx.x; j < tot; j += RLE_THREADS) {
+    if (staged) dk[off + j] = skeys[j];
+    cnt[off + j] = 0u;
+  }
+  if (blockIdx.x == ntile - 1 && threadIdx.x == 0) meta[0] = off + tot;
+#undef PADJ
+}
+
+// Multiplicities: every draw adds one at its key's rank (four draws in flight per thread).
+__global__ void __launch_bounds__(256) k_bm_count(const uint32_t* __restrict__ keys, int64_t s,
+                                                  const uint2* __restrict__ bm, uint32_t* __restrict__ cnt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; t + 3 * stride < s; t += 4 * stride) {
+    uint32_t k[4];
+    uint2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) k[u] = __ldg(keys + t + u * stride);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = __ldg(bm + (k[u] >> 5));
+#pragma unroll
+    for (int u = 0; u < 4; ++u) atomicAdd(cnt + v[u].y + (uint32_t)__popc(v[u].x & ((1u << (k[u] & 31)) - 1u)), 1u);
+  }
+  for (; t < s; t += stride) {
+    const uint32_t k = __ldg(keys + t);
+    const uint2 v = __ldg(bm + (k >> 5));
+    atomicAdd(cnt + v.y + (uint32_t)__popc(v.x & ((1u << (k & 31)) - 1u)), 1u);
   }
 }
 
@@ -510,8 +632,16 @@ kr_status kr_sketch_check(kr_ctx* ctx, const Modes& m, int64_t s) {
   return KR_OK;
 }
 
+bool kr_group_by_rank(const kr_ctx* ctx, int64_t s, int64_t keyspace) {
+  if (keyspace > (int64_t(1) << 32)) return false;
+  if (ctx->grouping == 1) return false;
+  if (ctx->grouping == 2) return true;
+  return keyspace <= 64 * s;
+}
+
 // Second phase of the sketch build, with scratch carved from `cv`: draw the row keys,
-// sort them, and turn the runs of equal keys into the merged entries of every cell.
+// group them (radix sort and runs of equal keys, or ranks in a bitmap of the key space),
+// and write the merged entries of every cell.
 kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, const float* b, uint64_t seed,
                          uint64_t call_id, int row, kr_sketch* sk, Carve& cv, bool defer_distinct) {
   const int N = m.N;
@@ -524,6 +654,12 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   uint32_t* meta = cv.take<uint32_t>(4);
   unsigned long long* dsum = cv.take<unsigned long long>(1);
   uint16_t* gbuf = cv.take<uint16_t>((size_t)KR_MAX_MODES * GUIDE_MAX);
+  const int64_t keyspace = ncell * (int64_t)IT;
+  const bool ranked = kr_group_by_rank(ctx, s, keyspace);
+  const int64_t nw = ranked ? (keyspace + 31) / 32 : 0;
+  const int nbt = (int)((nw + BM_TILE - 1) / BM_TILE);
+  uint2* bm = ranked ? cv.take<uint2>(nw) : nullptr;
+  uint32_t* btc = ranked ? cv.take<uint32_t>(2 * (size_t)nbt) : nullptr;
   if (cv.off > cv.cap) return kr_fail(ctx, KR_ENOMEM, "sketch: workspace too small");
   SampleModes sm = make_sample_modes(m, t);
   DrawModes dm = {};
@@ -541,13 +677,14 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   }
   KR_CUDA(ctx, cudaMemsetAsync(sk->cell_nd, 0, sizeof(uint32_t) * ncell, ctx->stream));
   KR_CUDA(ctx, cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), ctx->stream));
+  if (ranked) KR_CUDA(ctx, cudaMemsetAsync(bm, 0, sizeof(uint2) * nw, ctx->stream));
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32), cid = (uint32_t)call_id;
   {
     const int gs = grid_for(ctx, s, 256);
 #define KR_DRAW_KEYS(NN)                                                                                         \
   case NN:                                                                                                       \
     KR_LAUNCH(ctx, k_draw_keys<NN>, gs, 256, 0, dm, sk->s_row, sk->nrow, k0, k1, (uint32_t)row, cid,             \
-              (uint32_t)sk->ncell_inner, keys);                                                                  \
+              (uint32_t)sk->ncell_inner, keys, bm);                                                              \
     break;
     switch (N) {
       KR_DRAW_KEYS(1)
@@ -563,28 +700,41 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
     }
 #undef KR_DRAW_KEYS
   }
-  int nbits = 0;
-  while (nbits < 32 && (uint64_t(1) << nbits) < (uint64_t)ncell * IT) ++nbits;
-  uint32_t* sorted = keys;
-  {
-    Carve sc = cv;
-    KR_TRY(kr_radix_sort_u32(ctx, keys, alt, s, nbits, &sorted, sc));
-  }
-  // run merge: tile head counts, run starts, long-run extras, entries (small per-tile
-  // arrays carved from the entry-count scratch)
+  // runs: (key, multiplicity) in increasing key order, as run starts into the sorted keys
+  // (hp) or as distinct keys (alt) with their counts (hp)
   const int ntile = (int)((s + RLE_TILE - 1) / RLE_TILE);
   const int nrt = (int)((s + RUN_TILE - 1) / RUN_TILE);  // run tiles (the run count is at most s)
   uint32_t* tcnt = mcnt;
   uint32_t* toff = tcnt + ntile;
   uint32_t* ecnt = toff + ntile;
   uint32_t* eoff = ecnt + nrt;
-  KR_LAUNCH(ctx, k_rle_tcount, ntile, RLE_THREADS, 0, sorted, s, tcnt);
-  {
-    Carve sc = cv;
-    KR_TRY(kr_scan_u32(ctx, tcnt, toff, ntile, sc));
+  uint32_t* runkeys = alt;
+  if (ranked) {
+    KR_LAUNCH(ctx, k_bm_tcount, nbt, RLE_THREADS, 0, bm, nw, btc);
+    {
+      Carve sc = cv;
+      KR_TRY(kr_scan_u32(ctx, btc, btc + nbt, nbt, sc));
+    }
+    KR_LAUNCH(ctx, k_bm_rank, nbt, RLE_THREADS, 0, bm, nw, btc + nbt, nbt, alt, hp, meta);
+    KR_LAUNCH(ctx, k_bm_count, grid_for(ctx, s, 256), 256, 0, keys, s, bm, hp);
+    KR_LAUNCH(ctx, k_rle_ecount<true>, nrt, RLE_THREADS, 0, hp, meta, ecnt);
+  } else {
+    int nbits = 0;
+    while (nbits < 32 && (uint64_t(1) << nbits) < (uint64_t)keyspace) ++nbits;
+    {
+      Carve sc = cv;
+      KR_TRY(kr_radix_sort_u32(ctx, keys, alt, s, nbits, &runkeys, sc));
+    }
+    // run merge: tile head counts, run starts, long-run extras (small per-tile arrays
+    // carved from the entry-count scratch)
+    KR_LAUNCH(ctx, k_rle_tcount, ntile, RLE_THREADS, 0, runkeys, s, tcnt);
+    {
+      Carve sc = cv;
+      KR_TRY(kr_scan_u32(ctx, tcnt, toff, ntile, sc));
+    }
+    KR_LAUNCH(ctx, k_rle_starts, ntile, RLE_THREADS, 0, runkeys, s, toff, ntile, hp, meta);
+    KR_LAUNCH(ctx, k_rle_ecount<false>, nrt, RLE_THREADS, 0, hp, meta, ecnt);
   }
-  KR_LAUNCH(ctx, k_rle_starts, ntile, RLE_THREADS, 0, sorted, s, toff, ntile, hp, meta);
-  KR_LAUNCH(ctx, k_rle_ecount, nrt, RLE_THREADS, 0, hp, meta, ecnt);
   {
     Carve sc = cv;
     KR_TRY(kr_scan_u32(ctx, ecnt, eoff, nrt, sc));
@@ -592,8 +742,12 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   // b may still be arriving on the context's copy stream (host-buffer solves): the gather
   // is its first reader
   if (ctx->b_wait) KR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->b_wait, 0));
-  KR_LAUNCH(ctx, k_rle_emit, nrt, RLE_THREADS, 0, sorted, hp, ecnt, eoff, meta, IT, (uint32_t)sk->ncell_inner,
-            sk->xI, sk->xPafter, b, sk->ent, sk->bt, sk->cell_nd, dsum);
+  if (ranked)
+    KR_LAUNCH(ctx, k_rle_emit<true>, nrt, RLE_THREADS, 0, runkeys, hp, ecnt, eoff, meta, IT,
+              (uint32_t)sk->ncell_inner, sk->xI, sk->xPafter, b, sk->ent, sk->bt, sk->cell_nd, dsum);
+  else
+    KR_LAUNCH(ctx, k_rle_emit<false>, nrt, RLE_THREADS, 0, runkeys, hp, ecnt, eoff, meta, IT,
+              (uint32_t)sk->ncell_inner, sk->xI, sk->xPafter, b, sk->ent, sk->bt, sk->cell_nd, dsum);
   {
     Carve sc = cv;
     KR_TRY(kr_scan_u32(ctx, sk->cell_nd, sk->cell_start, ncell, sc));
@@ -620,16 +774,24 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   return KR_OK;
 }
 
-void kr_sketch_scratch_need(int64_t s, int64_t ncell, Need& nd) {
+void kr_sketch_scratch_need(const kr_ctx* ctx, int64_t s, int64_t ncell, int64_t IT, Need& nd) {
   nd.add<uint32_t>(s);      // keys
-  nd.add<uint32_t>(s);      // sort buffer / run index
-  nd.add<uint32_t>(s + 1);  // run starts
+  nd.add<uint32_t>(s);      // sort buffer / distinct keys
+  nd.add<uint32_t>(s + 1);  // run starts / multiplicities
   nd.add<uint32_t>(rle_scratch_words(s));  // run merge: tile head counts and offsets, long-run extras
   nd.add<uint32_t>(4);
   nd.add<unsigned long long>(1);
   nd.add<uint16_t>((size_t)KR_MAX_MODES * GUIDE_MAX);
+  if (kr_group_by_rank(ctx, s, ncell * IT)) {
+    const int64_t nw = (ncell * IT + 31) / 32;
+    nd.add<uint2>(nw);                                       // key bitmap with word ranks
+    nd.add<uint32_t>(2 * ((nw + BM_TILE - 1) / BM_TILE));  // its tile counts and offsets
+  }
   Need a, c;
-  kr_radix_need(s, a);
+  if (kr_group_by_rank(ctx, s, ncell * IT))
+    kr_scan_need(((ncell * IT + 31) / 32 + BM_TILE - 1) / BM_TILE, c);
+  else
+    kr_radix_need(s, a);
   kr_scan_need(s, c);
   kr_scan_need(ncell, c);
   kr_perm_need(ncell, c);
@@ -697,7 +859,7 @@ extern "C" kr_status kron_sketch(kr_ctx* ctx, const kr_factors* f, const double*
     nd.add<double>(m.I[n]);
     nd.add<float>(m.I[n]);
   }
-  kr_sketch_scratch_need(s, ncell, nd);
+  kr_sketch_scratch_need(ctx, s, ncell, m.I[m.N - 1], nd);
   KR_TRY(kr_ws_reserve(ctx, nd.off));
   Carve cv(ctx->ws, ctx->ws_size);
   FactorTables t;

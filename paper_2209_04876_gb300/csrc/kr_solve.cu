@@ -1315,7 +1315,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   nd.add<float>(fold0 ? (size_t)m.I[0] * m.R[0] : 0);
   {
     Need sc = nd;
-    kr_sketch_scratch_need(cfg.s, ncell, nd);
+    kr_sketch_scratch_need(ctx, cfg.s, ncell, m.I[m.N - 1], nd);
     if (slab) {
       kr_tiles_scratch_need(&tl, ncell, sc);
       if (sc.off > nd.off) nd.off = sc.off;

@@ -406,7 +406,7 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   if (slab) kr_tiles_own_need(&tl, cells, nd);
   {
     Need sc = nd;  // the tile construction reuses the sketch build's scratch
-    kr_sketch_scratch_need(sk.s, cells, nd);
+    kr_sketch_scratch_need(ctx, sk.s, cells, sk.IT, nd);
     if (slab) {
       kr_tiles_scratch_need(&tl, cells, sc);
       if (sc.off > nd.off) nd.off = sc.off;

@@ -122,9 +122,17 @@ def test_sampler_edge_tables():
 
 # ------------------------------------------------------------------ a4 + a5
 
+@pytest.fixture(params=[1, 2], ids=["radix", "rank"])
+def grouping(request):
+    """Both groupings of the draws: radix sort + runs, ranks in a bitmap of the key space."""
+    kr.set_option(kr.OPT_GROUPING, request.param)
+    yield request.param
+    kr.set_option(kr.OPT_GROUPING, 0)
+
+
 @pytest.mark.parametrize("I,R", SHAPES)
 @pytest.mark.parametrize("s", [1, 997, 60000])
-def test_sketch_grouping_weights_gather(I, R, s):
+def test_sketch_grouping_weights_gather(I, R, s, grouping):
     prob = kron_problem(I, R, dist="lognormal_rows", seed=5, noise_rel=0.1)
     As = f32_factors(prob["As"])
     b = prob["b"].astype(np.float32)
@@ -141,7 +149,7 @@ def test_sketch_grouping_weights_gather(I, R, s):
     sk.free()
 
 
-def test_sketch_long_runs_split_into_entries():
+def test_sketch_long_runs_split_into_entries(grouping):
     """A row drawn more than 65535 times is stored as several entries of the same row (the
     multiplicity field is 16 bits): per row, the entries' counts add up to the oracle's
     multiplicity, the dominant row takes ceil(count / 65535) entries, and b~ and the weights
@@ -165,6 +173,27 @@ def test_sketch_long_runs_split_into_entries():
     assert int(np.sum(keys == rk[top])) == -(-int(rc[top]) // 65535)
     np.testing.assert_array_equal(bt, b[keys])
     np.testing.assert_allclose(omega, ko.sample_weights(keys, counts, probs, I, s), rtol=1e-6)
+
+
+def test_sketch_dense_key_space(grouping):
+    """1.5 M draws on a key space of 122,880 rows: about 40 % of all rows are drawn, so a
+    tile of 65,536 keys of the rank grouping holds 20-28 thousand distinct keys (more than
+    its shared-memory staging takes)."""
+    I, R = [40, 48, 64], [3, 4, 5]
+    prob = kron_problem(I, R, dist="lognormal_rows", seed=5, noise_rel=0.1)
+    As = f32_factors(prob["As"])
+    b = prob["b"].astype(np.float32)
+    cdfs, probs, t = tables(As)
+    s = 1500000
+    sk = kr.kron_sketch([dev(A) for A in As], t["cdf"], t["prob"], dev(b), s, 13, 2)
+    keys, counts, omega, bt = (host(v) for v in sk.export())
+    sk.free()
+    rk, rc = ko.group_samples(ko.sample_draws(cdfs, s, 13, 2), I)
+    assert len(rk) > 40000
+    np.testing.assert_array_equal(keys, rk)
+    np.testing.assert_array_equal(counts, rc)
+    np.testing.assert_array_equal(bt, b[rk])
+    np.testing.assert_allclose(omega, ko.sample_weights(rk, rc, probs, I, s), rtol=1e-6)
 
 
 # ------------------------------------------------------------------ KronMatMul, preconditioner

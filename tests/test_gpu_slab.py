@@ -14,7 +14,7 @@ import torch
 
 import paper_2209_04876_gb300 as kr
 from oracle import kron as ko
-from workloads import kron_problem
+from workloads import kron_problem, tucker_init, tucker_tensor
 
 pytestmark = pytest.mark.gpu
 
@@ -182,7 +182,50 @@ def test_device_loop_stops_at_max_iter():
 
 def test_set_option_rejects_bad_values():
     for key, val in [(kr.OPT_SLAB_PASS, 2), (kr.OPT_SLAB_TILE_ENTRIES, 100), (kr.OPT_SLAB_TILE_ENTRIES, (1 << 22) + 1),
-                     (kr.OPT_DEVICE_LOOP, 7), (kr.OPT_BATCH_WORKERS, 0), (kr.OPT_BATCH_WORKERS, 33), (99, 1)]:
+                     (kr.OPT_DEVICE_LOOP, 7), (kr.OPT_BATCH_WORKERS, 0), (kr.OPT_BATCH_WORKERS, 33),
+                     (kr.OPT_GROUPING, -1), (kr.OPT_GROUPING, 3), (99, 1)]:
         with pytest.raises(kr.KronError) as e:
             kr.set_option(key, val)
         assert e.value.name == "KR_EINVAL"
+
+
+@pytest.mark.parametrize("I,R,dist,lam", [
+    ([256, 256], [16, 16], "gauss", 0.0),
+    ([64, 48, 40], [4, 3, 5], "lognormal_rows", 0.0),
+    ([9, 11, 7, 13], [2, 3, 2, 4], "outliers", 1e-3),
+    ([6, 70, 40], [2, 32, 32], "lognormal_rows", 0.0),
+])
+def test_groupings_give_identical_solves(I, R, dist, lam):
+    """Radix sort + runs and ranks in a key bitmap build the same sketch, so whole solves
+    agree bit for bit (same merged rows, iterations and iterate)."""
+    As, b = _problem(I, R, dist, seed=23)
+    out = []
+    try:
+        for g in (1, 2):
+            kr.set_option(kr.OPT_GROUPING, g)
+            x, rep, launches = _solve(As, b, lam, slab=True)
+            out.append((host(x), rep))
+    finally:
+        kr.set_option(kr.OPT_GROUPING, 0)
+    (x1, r1), (x2, r2) = out
+    assert r1["distinct"] == r2["distinct"] and r1["iters"] == r2["iters"]
+    np.testing.assert_array_equal(x1, x2)
+
+
+def test_groupings_give_identical_tucker_factor_steps():
+    """The batched-row sketch of an Alg. 3 factor step (one draw batch per row of X_(n))
+    through both groupings."""
+    I, R = [24, 20, 18], [3, 3, 2]
+    X = tucker_tensor(I, R, seed=3, noise_rel=0.01)["X"].astype(np.float32)
+    As = [np.asarray(A, np.float32) for A in tucker_init(I, R, seed=4)]
+    G = np.random.default_rng(5).standard_normal(R).astype(np.float32)
+    got = []
+    try:
+        for g in (1, 2):
+            kr.set_option(kr.OPT_GROUPING, g)
+            A_gpu = [dev(A) for A in As]
+            kr.tucker_factor_update(dev(X), A_gpu, dev(G), 1, 1e-3, eps=0.1, seed=9, call_id=2, tol=1e-7, max_iter=500)
+            got.append(host(A_gpu[1]))
+    finally:
+        kr.set_option(kr.OPT_GROUPING, 0)
+    np.testing.assert_array_equal(got[0], got[1])
