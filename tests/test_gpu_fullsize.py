@@ -11,7 +11,7 @@ import torch
 import paper_2209_04876_gb300 as kr
 from oracle import kron as ko
 from oracle import tucker as tk
-from workloads import CONFIGS, kron_problem, tucker_init, tucker_tensor
+from workloads import CONFIGS, batched_shapes, kron_problem, kron_problem_device, tucker_init, tucker_tensor
 
 pytestmark = pytest.mark.gpu
 
@@ -181,3 +181,39 @@ def test_large_1024cubed_r64_outliers():
     opt = ko.objective(As64, b64, ko.closed_form_ls(As64, b64), 0.0)
     f = ko.objective(As64, b64, x.cpu().numpy().astype(np.float64), 0.0)
     assert f <= (1 + eps) * opt
+
+
+def test_batched_ridge_64_problems_full_size():
+    """The batched-ridge workload at its full size: 64 problems, N = 3, I_n ~ U{64..1024},
+    R_n ~ U{4..32}, lambda = 1e-3, Gaussian factors, b = Kronecker signal + 1 % noise
+    (about 41 GB of right-hand sides, generated on the device). Every problem meets
+    f(x) <= (1 + eps) OPT against the exact ridge solution; the results on 1 and 4 worker
+    contexts are bit-identical; the library's OPT of the two smallest problems is pinned
+    by the FP64 closed form (thin SVDs)."""
+    shapes = batched_shapes()
+    lam, eps, seed, cid = 1e-3, 0.1, 5, 900
+    probs = [kron_problem_device(I, R, dist="gauss", seed=3000 + k, noise_rel=0.01) for k, (I, R) in enumerate(shapes)]
+    batch = [(p["As"], p["b"]) for p in probs]
+    out = {}
+    try:
+        for workers in (4, 1):
+            kr.set_option(kr.OPT_BATCH_WORKERS, workers)
+            out[workers] = kr.kron_ridge_batched(batch, lam, eps=eps, seed=seed, call_id=cid, tol=1e-7, max_iter=300)
+    finally:
+        kr.set_option(kr.OPT_BATCH_WORKERS, 4)
+    (xs4, reps4), (xs1, reps1) = out[4], out[1]
+    opts = []
+    for p, (As_d, b_d) in enumerate(batch):
+        assert reps4[p]["converged"]
+        assert torch.equal(xs4[p], xs1[p]) and reps4[p]["iters"] == reps1[p]["iters"]
+        KtB = kr.kron_matmul(As_d, b_d, trans=[1] * 3)
+        xstar = kr.kron_precond(As_d, KtB, lam)
+        opt = kr.kron_objective(As_d, b_d, xstar, lam)
+        f = kr.kron_objective(As_d, b_d, xs4[p], lam)
+        assert f <= (1.0 + eps) * opt, (p, shapes[p], f / opt)
+        opts.append(opt)
+    for p in sorted(range(len(shapes)), key=lambda q: math.prod(shapes[q][0]))[:2]:
+        As64 = [A.cpu().numpy().astype(np.float64) for A in batch[p][0]]
+        b64 = batch[p][1].cpu().numpy().astype(np.float64)
+        opt_cf = ko.objective(As64, b64, ko.closed_form_ridge(As64, b64, lam), lam)
+        assert abs(opts[p] - opt_cf) <= 1e-4 * opt_cf, (p, opts[p], opt_cf)

@@ -18,6 +18,10 @@ float32 for the device):
 * ``tucker_tensor``: X = G x_1 Q1 ... x_N QN + noise, G ~ N(0,1)^{R}, Qn orthonormal
   (QR of a Gaussian), noise scaled to ``noise_rel * ||signal||``.
 * ``batched_shapes``: per-problem I_n ~ U{lo..hi}, R_n ~ U{rlo..rhi}.
+* ``kron_problem_device``: the ``kron_problem`` recipe (b_kind 'kron', relative noise)
+  generated in float32 on a CUDA device with torch's seeded generator, for batches whose
+  right-hand sides (up to 4 GB each) are too slow to build on the host. Same recipe, not
+  the same numbers as the numpy generator.
 """
 import numpy as np
 
@@ -79,6 +83,36 @@ def kron_problem(I, R, dist="gauss", seed=0, noise_abs=None, noise_rel=None, b_k
             noise[:] = 0.0
         b = sig + noise
     return dict(As=As, b=b, x_true=x_true, I=I, R=R)
+
+
+def kron_problem_device(I, R, dist="gauss", seed=0, noise_rel=0.01, sigma=1.0, device="cuda"):
+    """Returns dict(As=[float32 I_n x R_n on device], b=float32 (prod I) on device, I, R)."""
+    import torch
+
+    I = [int(v) for v in I]
+    R = [int(v) for v in R]
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    As = []
+    for In, Rn in zip(I, R):
+        A = torch.randn(In, Rn, generator=g, device=device)
+        if dist == "lognormal_rows":
+            A *= torch.exp(sigma * torch.randn(In, 1, generator=g, device=device))
+        elif dist == "outliers":
+            rows = torch.randperm(In, generator=g, device=device)[:max(1, int(round(0.1 * In)))]
+            A[rows] *= 20.0
+        elif dist != "gauss":
+            raise ValueError(dist)
+        As.append(A.contiguous())
+    T = torch.randn(int(np.prod(R)), generator=g, device=device).reshape(R)
+    for n, A in enumerate(As):
+        T = torch.movedim(torch.tensordot(A, T, dims=([1], [n])), 0, n)
+    b = T.reshape(-1).contiguous()
+    del T
+    noise = torch.randn(b.numel(), generator=g, device=device)
+    noise *= noise_rel * torch.linalg.vector_norm(b) / torch.linalg.vector_norm(noise)
+    b += noise
+    return dict(As=As, b=b, I=I, R=R)
 
 
 def tucker_tensor(I, R, seed=0, noise_rel=0.01):
