@@ -365,7 +365,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--cpu-fraction", type=float, default=0.02)
+    ap.add_argument("--cpu-fraction", type=float, default=0.1)
     ap.add_argument("--ref-fraction", type=float, default=0.01)
     ap.add_argument("--ref-iters", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
