@@ -256,6 +256,158 @@ __global__ void k_row_update(float* __restrict__ z, const float* __restrict__ d,
   }
 }
 
+// One Richardson step of every row of a factor step with at most two other modes (one
+// block per row): the FP64 gradient combination of k_penalty_rows, the Woodbury
+// preconditioner on the row's R1 x R2 block,
+//   D = A^-1 g = (V1 (x) V2) (S1^2 (x) S2^2 + w)^-1 (V1 (x) V2)^T g,   d = D - A^-1 U C^-1 V D,
+// then z <- z - alpha d and the row statistics of k_row_update. One other mode: R1 = 1
+// and V1 = S1 = 1 (V1 == nullptr). Shared memory: z in FP64, two R1 x R2 FP32 buffers.
+constexpr int FR_MAX_RNE = 4096;
+struct RowStep {
+  int R1, R2, Rn, Rne;
+  const float* V1;  // R1 x R1 eigenvectors (columns), or nullptr for R1 = 1
+  const float* V2;  // R2 x R2
+  const float* s1;  // R1 eigenvalues sigma^2 (nullptr for R1 = 1)
+  const float* s2;  // R2
+  const float* Gn;
+  const double* gp64;
+  const float* Vw;      // Rn x Rne: lambda (G+)^T - w G
+  const float* AinvUt;  // Rn x Rne: rows A^-1 applied to the columns of G+
+  const float* Cinv;    // Rn x Rn
+  double lambda, w;
+  float wf, alpha;
+};
+__global__ void __launch_bounds__(256) k_factor_rows(RowStep p, float* __restrict__ Z, const float* __restrict__ gsk,
+                                                     double* __restrict__ rowstat) {
+  extern __shared__ double fr_smem[];
+  const int R1 = p.R1, R2 = p.R2, Rn = p.Rn, Rne = p.Rne;
+  double* zs = fr_smem;                               // Rne
+  float* M = reinterpret_cast<float*>(zs + Rne);      // Rne
+  float* T = M + Rne;                                 // Rne
+  __shared__ double tv[PEN_MAXRN], uv[PEN_MAXRN];
+  __shared__ float u1[PEN_MAXRN], u2[PEN_MAXRN];
+  __shared__ float red[3][8];
+  const int64_t row = blockIdx.x;
+  float* z = Z + row * Rne;
+  const float* g_sk = gsk + row * Rne;
+  for (int k = threadIdx.x; k < Rne; k += blockDim.x) zs[k] = (double)z[k];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // gradient: w z + G+ (lambda (G+)^T z - w G z) - gsk in FP64
+  for (int a = warp; a < Rn; a += nw) {
+    double t = 0.0, u = 0.0;
+    for (int k = lane; k < Rne; k += 32) {
+      t = fma((double)p.Gn[(int64_t)a * Rne + k], zs[k], t);
+      u = fma(p.gp64[(int64_t)k * Rn + a], zs[k], u);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      t += __shfl_xor_sync(0xffffffffu, t, off);
+      u += __shfl_xor_sync(0xffffffffu, u, off);
+    }
+    if (lane == 0) {
+      tv[a] = t;
+      uv[a] = u;
+    }
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < Rn; a += blockDim.x) tv[a] = p.lambda * uv[a] - p.w * tv[a];
+  __syncthreads();
+  for (int k = threadIdx.x; k < Rne; k += blockDim.x) {
+    double c = 0.0;
+    for (int a = 0; a < Rn; ++a) c = fma(p.gp64[(int64_t)k * Rn + a], tv[a], c);
+    M[k] = (float)(p.w * zs[k] + c - (double)g_sk[k]);
+  }
+  __syncthreads();
+  // A^-1 g: T = V1^T M, M = (T V2) / (s1 s2 + w), T = V1 M, M = T V2^T
+  for (int e = threadIdx.x; e < Rne; e += blockDim.x) {
+    const int j = e / R2, l = e - j * R2;
+    float acc = 0.f;
+    if (p.V1)
+      for (int k = 0; k < R1; ++k) acc = fmaf(p.V1[k * R1 + j], M[k * R2 + l], acc);
+    else
+      acc = M[e];
+    T[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < Rne; e += blockDim.x) {
+    const int j = e / R2, l = e - j * R2;
+    float acc = 0.f;
+    for (int r = 0; r < R2; ++r) acc = fmaf(T[j * R2 + r], p.V2[r * R2 + l], acc);
+    float prod = 1.f * p.s2[l];
+    if (p.s1) prod *= p.s1[j];
+    const float d = prod + p.wf;
+    M[e] = d > 0.f ? acc / d : 0.f;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < Rne; e += blockDim.x) {
+    const int j = e / R2, l = e - j * R2;
+    float acc = 0.f;
+    if (p.V1)
+      for (int k = 0; k < R1; ++k) acc = fmaf(p.V1[j * R1 + k], M[k * R2 + l], acc);
+    else
+      acc = M[e];
+    T[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < Rne; e += blockDim.x) {
+    const int j = e / R2, r = e - j * R2;
+    float acc = 0.f;
+    for (int l = 0; l < R2; ++l) acc = fmaf(T[j * R2 + l], p.V2[r * R2 + l], acc);
+    M[e] = acc;
+  }
+  __syncthreads();
+  // Woodbury correction: u1 = V D, u2 = C^-1 u1, d = D - (A^-1 U) u2
+  for (int a = warp; a < Rn; a += nw) {
+    float acc = 0.f;
+    for (int k = lane; k < Rne; k += 32) acc = fmaf(p.Vw[(int64_t)a * Rne + k], M[k], acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) u1[a] = acc;
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < Rn; a += blockDim.x) {
+    float acc = 0.f;
+    for (int b = 0; b < Rn; ++b) acc = fmaf(p.Cinv[a * Rn + b], u1[b], acc);
+    u2[a] = acc;
+  }
+  __syncthreads();
+  float s_1 = 0.f, s_2 = 0.f, bad = 0.f;
+  for (int k = threadIdx.x; k < Rne; k += blockDim.x) {
+    float gr = 0.f;
+    for (int a = 0; a < Rn; ++a) gr = fmaf(p.AinvUt[(int64_t)a * Rne + k], u2[a], gr);
+    const float st = p.alpha * (M[k] - gr);
+    const float zn = (float)zs[k] - st;
+    z[k] = zn;
+    s_1 = fmaf(st, st, s_1);
+    s_2 = fmaf(zn, zn, s_2);
+    if (!isfinite(zn)) bad = 1.f;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    s_1 += __shfl_xor_sync(0xffffffffu, s_1, off);
+    s_2 += __shfl_xor_sync(0xffffffffu, s_2, off);
+    bad = fmaxf(bad, __shfl_xor_sync(0xffffffffu, bad, off));
+  }
+  if (lane == 0) {
+    red[0][warp] = s_1;
+    red[1][warp] = s_2;
+    red[2][warp] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = 0.f, b = 0.f, c = 0.f;
+    for (int k = 0; k < nw; ++k) {
+      a += red[0][k];
+      b += red[1][k];
+      c = fmaxf(c, red[2][k]);
+    }
+    rowstat[3 * row + 0] = (double)a;
+    rowstat[3 * row + 1] = (double)b;
+    rowstat[3 * row + 2] = (double)c;
+  }
+}
+
 // out = {sum ||step||^2, sum ||z||^2, any non-finite, max_r ||step_r|| / ||z_r||} (one block).
 __global__ void k_rows_reduce(const double* __restrict__ rowstat, int nrow, double* __restrict__ out) {
   double s1 = 0, s2 = 0, bad = 0, mx = 0;
@@ -523,6 +675,30 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     trf[k + 1] = 0;
     trb[k + 1] = 1;
   }
+  // one or two other modes: the gradient, the Woodbury preconditioner and the update of
+  // every row in one kernel (k_factor_rows); more: the batched mode-product chain
+  const bool fused_rows = No <= 2 && Rne <= FR_MAX_RNE && Rn <= PEN_MAXRN;
+  RowStep rs = {};
+  if (fused_rows) {
+    rs.R1 = No == 2 ? to.R[0] : 1;
+    rs.R2 = to.R[No - 1];
+    rs.Rn = Rn;
+    rs.Rne = (int)Rne;
+    rs.V1 = No == 2 ? to.V[0] : nullptr;
+    rs.V2 = to.V[No - 1];
+    rs.s1 = No == 2 ? to.sig2[0] : nullptr;
+    rs.s2 = to.sig2[No - 1];
+    rs.Gn = Gn;
+    rs.gp64 = gp64;
+    rs.Vw = Vw;
+    rs.AinvUt = AinvUt;
+    rs.Cinv = Cinv;
+    rs.lambda = cfg.lambda;
+    rs.w = w;
+    rs.wf = (float)w;
+    rs.alpha = (float)cfg.alpha;
+    KR_TRY(kr_smem_attr(ctx, k_factor_rows, (size_t)16 * Rne));
+  }
   const int nblk = kr_resid_blocks(ctx);
   double* h = (double*)ctx->hbuf;
   int it = 0, grow = 0, since_min = 0, converged = 0;
@@ -539,17 +715,22 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
       KR_TRY(kr_sketch_resid(ctx, &sk, mo.A[No - 1], RT, Y, W, rpart, nblk, &used));
       KR_TRY(kr_kron_apply2(ctx, No + 1, dfw_out, dfw_in, Bf, trb, W, Gb, t0, t1));
     }
-    // grad = w z + G+ (lambda (G+)^T z - w G z) - Gb  (FP64 combination, one block per row)
-    KR_LAUNCH(ctx, k_penalty_rows, In, 256, sizeof(double) * Rne, Z, Gn, gp64, Gb, Rn, (int)Rne, cfg.lambda, w, Gr,
-              (float*)nullptr);
-    // d = M^-1 grad (Woodbury)
-    KR_TRY(base_apply(ctx, to, In, w, Gr, D, t0, t1));
-    KR_TRY(kr_mode_product(ctx, D, U1, In, (int)Rne, 1, Rn, Vw, 0));
-    KR_TRY(kr_mode_product(ctx, U1, U2, In, Rn, 1, Rn, Cinv, 0));
-    KR_TRY(kr_mode_product(ctx, U2, Gr, In, Rn, 1, (int)Rne, AinvUt, 1));
-    KR_LAUNCH(ctx, k_lin2, grid_of(ctx, ZL), 256, 0, D, D, 1.f, Gr, -1.f, ZL);
-    // z <- z - alpha d; stopping rule on the largest per-row relative step
-    KR_LAUNCH(ctx, k_row_update, In, 256, 0, Z, D, (float)cfg.alpha, (int)Rne, rowstat);
+    if (fused_rows) {
+      KR_LAUNCH(ctx, k_factor_rows, In, 256, (size_t)16 * Rne, rs, Z, Gb, rowstat);
+    } else {
+      // grad = w z + G+ (lambda (G+)^T z - w G z) - Gb  (FP64 combination, one block per row)
+      KR_LAUNCH(ctx, k_penalty_rows, In, 256, sizeof(double) * Rne, Z, Gn, gp64, Gb, Rn, (int)Rne, cfg.lambda, w, Gr,
+                (float*)nullptr);
+      // d = M^-1 grad (Woodbury)
+      KR_TRY(base_apply(ctx, to, In, w, Gr, D, t0, t1));
+      KR_TRY(kr_mode_product(ctx, D, U1, In, (int)Rne, 1, Rn, Vw, 0));
+      KR_TRY(kr_mode_product(ctx, U1, U2, In, Rn, 1, Rn, Cinv, 0));
+      KR_TRY(kr_mode_product(ctx, U2, Gr, In, Rn, 1, (int)Rne, AinvUt, 1));
+      KR_LAUNCH(ctx, k_lin2, grid_of(ctx, ZL), 256, 0, D, D, 1.f, Gr, -1.f, ZL);
+      // z <- z - alpha d
+      KR_LAUNCH(ctx, k_row_update, In, 256, 0, Z, D, (float)cfg.alpha, (int)Rne, rowstat);
+    }
+    // stopping rule on the largest per-row relative step
     KR_LAUNCH(ctx, k_rows_reduce, 1, 256, 0, rowstat, In, red);
     KR_CUDA(ctx, cudaMemcpyAsync(h, red, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     KR_CUDA(ctx, cudaMemcpyAsync(h + 4, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
