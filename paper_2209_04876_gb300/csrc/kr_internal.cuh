@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -218,6 +219,10 @@ struct FactorTables {
 // and (if want_eig) the eigen-decomposition of each factor Gram matrix. Buffers are
 // carved from `cv` (which must be large enough: see kr_tables_need).
 void kr_tables_need(const Modes& m, bool want_eig, Need& nd);
+// FP64 eigen-decompositions G = V diag(sig2) V^T of nmat FP64 Gram matrices (R[n] <= 64;
+// V row-major with the eigenvectors as columns), by cyclic Jacobi.
+kr_status kr_eig64(kr_ctx* ctx, int nmat, const int* R, const double* const* gram, double* const* V,
+                   double* const* sig2);
 kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv, FactorTables& t,
                           bool check_rank = true);
 
@@ -350,8 +355,41 @@ struct SolveCfg {
 };
 
 enum StepCheck { STEP_CONTINUE, STEP_CONVERGED, STEP_FLOOR, STEP_DIVERGED, STEP_NONFINITE, STEP_MAXITER };
-__host__ __device__ StepCheck step_check(const double* h, double tol, double* prev_step, double* min_step, double* min_rel, int* grow,
-                     int* since_min, double* rel_out, double rel_override);
+// Runs the steps of a Richardson loop as one CUDA graph: a conditional WHILE node whose
+// body is one captured step, body(hnd, 1); the body's last kernel clears the condition.
+// Launches the graph once on ctx->stream, waits for it to end, and returns the launches of one
+// captured step in *per_step; false when graphs are unavailable (nothing ran, the caller
+// continues with its host loop).
+bool kr_graph_while(kr_ctx* ctx, const std::function<kr_status(cudaGraphConditionalHandle, int)>& body,
+                    int64_t* per_step);
+// Stopping rule of the Richardson loops ("until convergence" in Alg. 2 and Alg. 3):
+// converged when ||step|| <= tol ||x||; stalled at the FP32 rounding floor when no new
+// minimum step was seen for 8 iterations and the smallest relative step is within
+// 100 tol; diverged when the step grew 3 times in a row and exceeds 16x its minimum.
+// h = {||step||^2, ||x||^2, non-finite flag}; rel_override >= 0 replaces ||step||/||x||
+// (the batched factor step passes its largest per-row ratio).
+__host__ __device__ inline StepCheck step_check(const double* h, double tol, double* prev_step, double* min_step,
+                                         double* min_rel, int* grow,
+                     int* since_min, double* rel_out, double rel_override) {
+  const double step = sqrt(h[0]), xn = sqrt(h[1]);
+  if (h[2] != 0.0 || !isfinite(step) || !isfinite(xn)) return STEP_NONFINITE;
+  double rel = xn > 0.0 ? step / xn : (step == 0.0 ? 0.0 : INFINITY);
+  if (rel_override >= 0.0) rel = rel_override;
+  *rel_out = rel;
+  if (rel <= tol) return STEP_CONVERGED;
+  if (step < *min_step) {
+    *min_step = step;
+    *since_min = 0;
+  } else {
+    ++*since_min;
+  }
+  if (rel < *min_rel) *min_rel = rel;
+  *grow = (step > *prev_step) ? *grow + 1 : 0;
+  *prev_step = step;
+  if (*grow >= 3 && step > 16.0 * *min_step) return STEP_DIVERGED;
+  if (*since_min >= 8 && *min_rel <= 100.0 * tol) return STEP_FLOOR;
+  return STEP_CONTINUE;
+}
 
 // Alg. 2 on device-resident factors and b; x (R floats) is written.
 kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const SolveCfg& cfg, uint64_t seed,

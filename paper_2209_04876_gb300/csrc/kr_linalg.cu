@@ -11,7 +11,9 @@
 // Precision: Gram, Cholesky, triangular inverse, scores and CDF in FP64 (exact
 // FP32 x FP32 products, FP64 sums). The eigen-decomposition is FP32 Jacobi: the
 // preconditioner only needs to be a spectral approximation of the normal matrix
-// (Lemma 4.2), so its rounding affects the rate, not the fixed point.
+// (Lemma 4.2), so its rounding affects the rate, not the fixed point. The Alg. 3 factor
+// step's Woodbury base (K^T K + w I)^-1 with w >> ||K^T K|| takes an FP64 Jacobi
+// (kr_eig64): there an orthogonality error e of V perturbs K^T K by about w e.
 #include <math.h>
 
 #include "kr_internal.cuh"
@@ -306,24 +308,42 @@ __global__ void __launch_bounds__(CDF_THREADS) k_cdf(ModePtrs mp) {
 
 // Cyclic Jacobi eigen-decomposition (FP32) of each Gram matrix, one block per mode,
 // parallel (round-robin) ordering of disjoint rotations.
-__global__ void k_jacobi(ModePtrs mp) {
+// Cyclic Jacobi eigen-decomposition of the Gram matrices (one block per matrix, round-robin
+// pairs), in T = float (the Alg. 2 preconditioner) or T = double (the Woodbury base of the
+// Alg. 3 factor step, where the penalty w multiplies any non-orthogonality of V).
+template <class T>
+struct JacobiArgs {
+  int R[KR_MAX_MODES];
+  const double* gram[KR_MAX_MODES];
+  T* V[KR_MAX_MODES];
+  T* sig2[KR_MAX_MODES];
+};
+__device__ __forceinline__ float jac_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double jac_rsqrt(double x) { return 1.0 / sqrt(x); }
+
+template <class T>
+__global__ void k_jacobi(JacobiArgs<T> ja) {
   const int n = blockIdx.x;
-  const int R = mp.R[n];
+  const int R = ja.R[n];
   const int m = (R + 1) & ~1;
-  extern __shared__ float fs[];
-  float* A = fs;              // (MAXR+1) x LD
-  float* V = fs + (MAXR + 1) * LD;
-  __shared__ float cs[MAXR / 2 + 1], sn[MAXR / 2 + 1];
+  extern __shared__ __align__(16) unsigned char jac_raw[];
+  T* A = reinterpret_cast<T*>(jac_raw);  // (MAXR+1) x LD
+  T* V = A + (MAXR + 1) * LD;
+  __shared__ T cs[MAXR / 2 + 1], sn[MAXR / 2 + 1];
   __shared__ int pp[MAXR / 2 + 1], qq[MAXR / 2 + 1];
-  __shared__ float red[2];
+  __shared__ T red[2];
   const int tid = threadIdx.x;
+  const T one = T(1), zero = T(0);
   for (int e = tid; e < m * m; e += blockDim.x) {
     int i = e / m, j = e % m;
-    A[i * LD + j] = (i < R && j < R) ? (float)mp.gram[n][i * R + j] : 0.f;
-    V[i * LD + j] = (i == j) ? 1.f : 0.f;
+    A[i * LD + j] = (i < R && j < R) ? (T)ja.gram[n][i * R + j] : zero;
+    V[i * LD + j] = (i == j) ? one : zero;
   }
   __syncthreads();
-  for (int sweep = 0; sweep < 20; ++sweep) {
+  // converged when the off-diagonal squares are below 1e-14 (FP32) / 1e-30 (FP64) of the diagonal's
+  const T conv = sizeof(T) == 4 ? T(1e-14f) : T(1e-30);
+  const int max_sweeps = sizeof(T) == 4 ? 20 : 40;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int r = 0; r < m - 1; ++r) {
       if (tid < m / 2) {
         int k = tid;
@@ -331,12 +351,12 @@ __global__ void k_jacobi(ModePtrs mp) {
         int p = (k == 0) ? 0 : 1 + ((k - 1 + r) % (m - 1));
         int q = 1 + ((m - 2 - k + r) % (m - 1));
         if (p > q) { int t = p; p = q; q = t; }
-        float apq = A[p * LD + q], app = A[p * LD + p], aqq = A[q * LD + q];
-        float c = 1.f, s = 0.f;
-        if (fabsf(apq) > 1e-30f * (fabsf(app) + fabsf(aqq)) && apq != 0.f) {
-          float tau = (aqq - app) / (2.f * apq);
-          float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-          c = rsqrtf(1.f + t * t);
+        T apq = A[p * LD + q], app = A[p * LD + p], aqq = A[q * LD + q];
+        T c = one, s = zero;
+        if (fabs(apq) > T(1e-30f) * (fabs(app) + fabs(aqq)) && apq != zero) {
+          T tau = (aqq - app) / (T(2) * apq);
+          T t = (tau >= zero ? one : -one) / (fabs(tau) + sqrt(one + tau * tau));
+          c = jac_rsqrt(one + t * t);
           s = t * c;
         }
         cs[k] = c; sn[k] = s; pp[k] = p; qq[k] = q;
@@ -344,47 +364,64 @@ __global__ void k_jacobi(ModePtrs mp) {
       __syncthreads();
       for (int w = tid; w < (m / 2) * m; w += blockDim.x) {  // rows: A <- J^T A
         int k = w / m, j = w % m;
-        float c = cs[k], s = sn[k];
-        if (s == 0.f) continue;
+        T c = cs[k], s = sn[k];
+        if (s == zero) continue;
         int p = pp[k], q = qq[k];
-        float ap = A[p * LD + j], aq = A[q * LD + j];
+        T ap = A[p * LD + j], aq = A[q * LD + j];
         A[p * LD + j] = c * ap - s * aq;
         A[q * LD + j] = s * ap + c * aq;
       }
       __syncthreads();
       for (int w = tid; w < (m / 2) * m; w += blockDim.x) {  // columns: A <- A J, V <- V J
         int k = w / m, i = w % m;
-        float c = cs[k], s = sn[k];
-        if (s == 0.f) continue;
+        T c = cs[k], s = sn[k];
+        if (s == zero) continue;
         int p = pp[k], q = qq[k];
-        float ap = A[i * LD + p], aq = A[i * LD + q];
+        T ap = A[i * LD + p], aq = A[i * LD + q];
         A[i * LD + p] = c * ap - s * aq;
         A[i * LD + q] = s * ap + c * aq;
-        float vp = V[i * LD + p], vq = V[i * LD + q];
+        T vp = V[i * LD + p], vq = V[i * LD + q];
         V[i * LD + p] = c * vp - s * vq;
         V[i * LD + q] = s * vp + c * vq;
       }
       __syncthreads();
     }
     if (tid == 0) {
-      float off = 0.f, dg = 0.f;
+      T off = zero, dg = zero;
       for (int i = 0; i < R; ++i)
         for (int j = 0; j < R; ++j) {
-          float v = A[i * LD + j];
+          T v = A[i * LD + j];
           if (i == j) dg += v * v; else off += v * v;
         }
       red[0] = off; red[1] = dg;
     }
     __syncthreads();
-    bool done = red[0] <= 1e-14f * red[1];
+    bool done = red[0] <= conv * red[1];
     __syncthreads();
     if (done) break;
   }
-  for (int e = tid; e < R * R; e += blockDim.x) mp.V[n][e] = V[(e / R) * LD + (e % R)];
-  for (int i = tid; i < R; i += blockDim.x) mp.sig2[n][i] = fmaxf(A[i * LD + i], 0.f);
+  for (int e = tid; e < R * R; e += blockDim.x) ja.V[n][e] = V[(e / R) * LD + (e % R)];
+  for (int i = tid; i < R; i += blockDim.x) ja.sig2[n][i] = fmax(A[i * LD + i], zero);
 }
 
 }  // namespace
+
+kr_status kr_eig64(kr_ctx* ctx, int nmat, const int* R, const double* const* gram, double* const* V,
+                   double* const* sig2) {
+  if (nmat < 1 || nmat > KR_MAX_MODES) return kr_fail(ctx, KR_EINVAL, "eig64: %d matrices", nmat);
+  JacobiArgs<double> ja = {};
+  for (int n = 0; n < nmat; ++n) {
+    if (R[n] < 1 || R[n] > MAXR) return kr_fail(ctx, KR_EINVAL, "eig64: R=%d", R[n]);
+    ja.R[n] = R[n];
+    ja.gram[n] = gram[n];
+    ja.V[n] = V[n];
+    ja.sig2[n] = sig2[n];
+  }
+  const size_t smem = 2 * (MAXR + 1) * LD * sizeof(double);
+  KR_TRY(kr_smem_attr(ctx, k_jacobi<double>, smem));
+  KR_LAUNCH(ctx, k_jacobi<double>, nmat, 256, smem, ja);
+  return KR_OK;
+}
 
 void kr_tables_need(const Modes& m, bool want_eig, Need& nd) {
   for (int n = 0; n < m.N; ++n) {
@@ -436,9 +473,16 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
   const size_t chol_smem = 3 * MAXR * LD * sizeof(double);
   const size_t lev_smem = (MAXR * LD + LEV_ROWS * LD) * sizeof(double);
   const size_t jac_smem = 2 * (MAXR + 1) * LD * sizeof(float);
+  JacobiArgs<float> ja = {};
+  for (int n = 0; n < m.N; ++n) {
+    ja.R[n] = m.R[n];
+    ja.gram[n] = mp.gram[n];
+    ja.V[n] = mp.V[n];
+    ja.sig2[n] = mp.sig2[n];
+  }
   KR_TRY(kr_smem_attr(ctx, k_cholesky, chol_smem));
   KR_TRY(kr_smem_attr(ctx, k_leverage, lev_smem));
-  KR_TRY(kr_smem_attr(ctx, k_jacobi, jac_smem));
+  KR_TRY(kr_smem_attr(ctx, k_jacobi<float>, jac_smem));
   dim3 gg((maxI + GRAM_ROWS - 1) / GRAM_ROWS, m.N);
   KR_LAUNCH(ctx, k_gram_partial, gg, 256, 0, mp);
   int maxR = 0;
@@ -448,7 +492,7 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
   dim3 gl((maxI + LEV_ROWS - 1) / LEV_ROWS, m.N);
   KR_LAUNCH(ctx, k_leverage, gl, LEV_ROWS * 32, lev_smem, mp);
   KR_LAUNCH(ctx, k_cdf, m.N, CDF_THREADS, 0, mp);
-  if (want_eig) KR_LAUNCH(ctx, k_jacobi, m.N, 256, jac_smem, mp);
+  if (want_eig) KR_LAUNCH(ctx, k_jacobi<float>, m.N, 256, jac_smem, ja);
   if (check_rank) {
     KR_TRY(kr_hbuf_reserve(ctx, 4096));
     int* hf = (int*)ctx->hbuf;

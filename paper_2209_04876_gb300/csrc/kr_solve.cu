@@ -1243,35 +1243,43 @@ kr_status sampled_pass(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const I
 
 }  // namespace
 
-// Stopping rule of the Richardson loops ("until convergence" in Alg. 2 and Alg. 3):
-// converged when ||step|| <= tol ||x||; stalled at the FP32 rounding floor when no new
-// minimum step was seen for 8 iterations and the smallest relative step is within
-// 100 tol; diverged when the step grew 3 times in a row and exceeds 16x its minimum.
-// h = {||step||^2, ||x||^2, non-finite flag}; rel_override >= 0 replaces ||step||/||x||
-// (the batched factor step passes its largest per-row ratio).
-__host__ __device__ StepCheck step_check(const double* h, double tol, double* prev_step, double* min_step,
-                                         double* min_rel, int* grow,
-                     int* since_min, double* rel_out, double rel_override) {
-  const double step = sqrt(h[0]), xn = sqrt(h[1]);
-  if (h[2] != 0.0 || !isfinite(step) || !isfinite(xn)) return STEP_NONFINITE;
-  double rel = xn > 0.0 ? step / xn : (step == 0.0 ? 0.0 : INFINITY);
-  if (rel_override >= 0.0) rel = rel_override;
-  *rel_out = rel;
-  if (rel <= tol) return STEP_CONVERGED;
-  if (step < *min_step) {
-    *min_step = step;
-    *since_min = 0;
-  } else {
-    ++*since_min;
-  }
-  if (rel < *min_rel) *min_rel = rel;
-  *grow = (step > *prev_step) ? *grow + 1 : 0;
-  *prev_step = step;
-  if (*grow >= 3 && step > 16.0 * *min_step) return STEP_DIVERGED;
-  if (*since_min >= 8 && *min_rel <= 100.0 * tol) return STEP_FLOOR;
-  return STEP_CONTINUE;
-}
 
+
+bool kr_graph_while(kr_ctx* ctx, const std::function<kr_status(cudaGraphConditionalHandle, int)>& body,
+                    int64_t* per_step) {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle hnd = 0;
+  bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+  ok = ok && cudaGraphConditionalHandleCreate(&hnd, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hnd;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  ok = ok && cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) == cudaSuccess;
+  *per_step = 0;
+  if (ok && cudaStreamBeginCaptureToGraph(ctx->stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+    const int64_t l0 = ctx->launches;
+    const kr_status cs = body(hnd, 1);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &captured);
+    *per_step = ctx->launches - l0;
+    ctx->launches = l0;
+    ok = cs == KR_OK && ce == cudaSuccess;
+  } else {
+    ok = false;
+  }
+  ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+  if (ok) ok = cudaGraphLaunch(exec, ctx->stream) == cudaSuccess;
+  if (ok) ok = cudaStreamSynchronize(ctx->stream) == cudaSuccess;  // the graph ends before it is destroyed
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) cudaGetLastError();  // graphs unavailable: the host loop takes over
+  return ok;
+}
 
 // Core Alg. 2 solve on device-resident inputs. Timings go to rep->t_ms if rep != NULL.
 kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const SolveCfg& cfg, uint64_t seed,
@@ -1394,43 +1402,14 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   KR_TRY(one_step(0, 0));
   KR_TRY(read_state());
   if (hs->status == STEP_CONTINUE && ctx->device_loop && !ctx->timing) {
-    // Steps 2.. as one graph: a conditional WHILE node whose body is one captured step;
-    // k_rich_check clears the condition on convergence, failure or max_iter.
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaGraphConditionalHandle hnd = 0;
-    bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
-    ok = ok && cudaGraphConditionalHandleCreate(&hnd, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = hnd;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    ok = ok && cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    // Steps 2.. as one graph; k_rich_check clears the condition on convergence, failure
+    // or max_iter.
     int64_t per_step = 0;
-    if (ok && cudaStreamBeginCaptureToGraph(ctx->stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                            cudaStreamCaptureModeRelaxed) == cudaSuccess) {
-      const int64_t l0 = ctx->launches;
-      const kr_status cs = one_step(hnd, 1);
-      cudaGraph_t captured = nullptr;
-      const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &captured);
-      per_step = ctx->launches - l0;
-      ctx->launches = l0;
-      ok = cs == KR_OK && ce == cudaSuccess;
-    } else {
-      ok = false;
-    }
-    ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
-    if (ok) {
-      const int it0 = hs->it;
-      KR_CUDA(ctx, cudaGraphLaunch(exec, ctx->stream));
+    const int it0 = hs->it;
+    if (kr_graph_while(ctx, one_step, &per_step)) {
       KR_TRY(read_state());
       ctx->launches += per_step * (hs->it - it0);
     }
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    if (!ok) cudaGetLastError();  // graphs unavailable: the host loop below takes over
   }
   while (hs->status == STEP_CONTINUE) {
     KR_TRY(one_step(0, 0));

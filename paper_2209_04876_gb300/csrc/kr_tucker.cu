@@ -55,13 +55,6 @@ __global__ void k_lin2(float* __restrict__ out, const float* __restrict__ a, flo
     out[i] = ca * a[i] + cb * b[i];
 }
 
-// grad = w z + corr - g_sk  (in place in corr)
-__global__ void k_grad(float* __restrict__ corr, const float* __restrict__ z, float w, const float* __restrict__ gsk,
-                       int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    corr[i] = fmaf(w, z[i], corr[i]) - gsk[i];
-}
-
 // Hinv = L^-T L^-1 = (G_(n) G_(n)^T)^-1 in FP64 from the inverse Cholesky factor (one block).
 __global__ void k_hinv(const double* __restrict__ linv, int Rn, double* __restrict__ hinv) {
   for (int e = threadIdx.x; e < Rn * Rn; e += blockDim.x) {
@@ -165,7 +158,8 @@ __global__ void k_capacitance(const float* __restrict__ Vw, const float* __restr
 }
 
 // Gauss-Jordan inverse with partial pivoting in FP64 (one block, n <= 64).
-__global__ void k_gauss_jordan(const double* __restrict__ C, int n, float* __restrict__ Cinv, int* __restrict__ bad) {
+__global__ void k_gauss_jordan(const double* __restrict__ C, int n, float* __restrict__ Cinv, int* __restrict__ bad,
+                               double* __restrict__ Cinv64) {
   extern __shared__ double aug[];  // n x 2n
   const int w2 = 2 * n;
   __shared__ int piv;
@@ -211,7 +205,11 @@ __global__ void k_gauss_jordan(const double* __restrict__ C, int n, float* __res
       if (i != k) aug[i * w2 + k] = 0.0;
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Cinv[e] = (float)aug[(e / n) * w2 + n + (e % n)];
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const double v = aug[(e / n) * w2 + n + (e % n)];
+    Cinv[e] = (float)v;
+    if (Cinv64) Cinv64[e] = v;
+  }
 }
 
 // z <- z - alpha d, one block per row; rowstat[r] = {||step||^2, ||z||^2, non-finite}.
@@ -256,36 +254,130 @@ __global__ void k_row_update(float* __restrict__ z, const float* __restrict__ d,
   }
 }
 
+// The Woodbury base A^-1 = (K^T K + w I)^-1 = (V1 (x) V2)(S1^2 (x) S2^2 + w)^-1 (V1 (x) V2)^T on
+// one R1 x R2 block in FP64, from FP64 eigen-decompositions of the other modes' Gram
+// matrices. With w >> ||K^T K|| every piece of the Woodbury form is kept in FP64: the
+// capacitance I + V A^-1 U cancels to about 1/((1 + 12/eps) cond(K^T K)) of its terms, and an
+// error e in A^-1 (or in V's orthogonality) acts like a perturbation w e of K^T K, which
+// left in FP32 slows Richardson from ~16 to hundreds of iterations once the factors lose
+// their orthonormality. One other mode: R1 = 1 and V1 = S1 = 1 (V1 == nullptr).
+struct WbBase {
+  int R1, R2;
+  const double* V1;  // R1 x R1 eigenvectors (columns), nullptr for R1 = 1
+  const double* V2;  // R2 x R2
+  const double* s1;  // R1 eigenvalues (nullptr for R1 = 1)
+  const double* s2;  // R2
+  double w;
+};
+
+// M (R1 x R2, shared memory) <- A^-1 M; T is shared scratch of the same size. Called by
+// every thread of the block (it synchronises).
+__device__ void base_apply_block64(const WbBase& b, double* M, double* T) {
+  const int R1 = b.R1, R2 = b.R2, n = R1 * R2;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {  // T = V1^T M
+    const int j = e / R2, l = e - j * R2;
+    double acc = 0.0;
+    if (b.V1)
+      for (int k = 0; k < R1; ++k) acc = fma(b.V1[k * R1 + j], M[k * R2 + l], acc);
+    else
+      acc = M[e];
+    T[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {  // M = (T V2) / (s1 s2 + w)
+    const int j = e / R2, l = e - j * R2;
+    double acc = 0.0;
+    for (int r = 0; r < R2; ++r) acc = fma(T[j * R2 + r], b.V2[r * R2 + l], acc);
+    const double d = (b.s1 ? b.s1[j] * b.s2[l] : b.s2[l]) + b.w;
+    M[e] = d > 0.0 ? acc / d : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {  // T = V1 M
+    const int j = e / R2, l = e - j * R2;
+    double acc = 0.0;
+    if (b.V1)
+      for (int k = 0; k < R1; ++k) acc = fma(b.V1[j * R1 + k], M[k * R2 + l], acc);
+    else
+      acc = M[e];
+    T[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {  // M = T V2^T
+    const int j = e / R2, r = e - j * R2;
+    double acc = 0.0;
+    for (int l = 0; l < R2; ++l) acc = fma(T[j * R2 + l], b.V2[r * R2 + l], acc);
+    M[e] = acc;
+  }
+  __syncthreads();
+}
+
+// AinvU[a] = A^-1 (column a of G+), one block per column (FP64).
+__global__ void __launch_bounds__(256) k_base_cols64(WbBase b, const double* __restrict__ gp64, int Rn, int Rne,
+                                                     double* __restrict__ AinvU) {
+  extern __shared__ double bc_smem[];
+  double* M = bc_smem;
+  double* T = bc_smem + Rne;
+  const int a = blockIdx.x;
+  for (int k = threadIdx.x; k < Rne; k += blockDim.x) M[k] = gp64[(int64_t)k * Rn + a];
+  __syncthreads();
+  base_apply_block64(b, M, T);
+  for (int k = threadIdx.x; k < Rne; k += blockDim.x) AinvU[(int64_t)a * Rne + k] = M[k];
+}
+
+// Vw[a][k] = lambda G+[k][a] - w G_(n)[a][k]  (R_n x Rne, FP64)
+__global__ void k_vw64(const double* __restrict__ gp64, const float* __restrict__ Gn, int Rn, int Rne, double lambda,
+                       double w, double* __restrict__ Vw) {
+  const int64_t tot = (int64_t)Rn * Rne;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e / Rne), k = (int)(e % Rne);
+    Vw[e] = lambda * gp64[(int64_t)k * Rn + a] - w * (double)Gn[e];
+  }
+}
+
+// C[a][b] = delta_ab + sum_k Vw[a][k] AinvU[b][k] from FP64 inputs; block per (a, b).
+__global__ void k_capacitance64(const double* __restrict__ Vw, const double* __restrict__ AinvU, int Rn, int Rne,
+                                double* __restrict__ C) {
+  const int a = blockIdx.x / Rn, b = blockIdx.x % Rn;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < Rne; k += blockDim.x)
+    acc = fma(Vw[(int64_t)a * Rne + k], AinvU[(int64_t)b * Rne + k], acc);
+  __shared__ double red[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    C[blockIdx.x] = t + (a == b ? 1.0 : 0.0);
+  }
+}
+
 // One Richardson step of every row of a factor step with at most two other modes (one
-// block per row): the FP64 gradient combination of k_penalty_rows, the Woodbury
-// preconditioner on the row's R1 x R2 block,
-//   D = A^-1 g = (V1 (x) V2) (S1^2 (x) S2^2 + w)^-1 (V1 (x) V2)^T g,   d = D - A^-1 U C^-1 V D,
-// then z <- z - alpha d and the row statistics of k_row_update. One other mode: R1 = 1
-// and V1 = S1 = 1 (V1 == nullptr). Shared memory: z in FP64, two R1 x R2 FP32 buffers.
+// block per row), all in FP64 up to the FP32 iterate: the gradient combination of
+// k_penalty_rows, the Woodbury preconditioner
+//   D = A^-1 g,   d = D - (A^-1 U) C^-1 V D,
+// then z <- z - alpha d and the row statistics of k_row_update. Shared memory: z, and
+// two R1 x R2 buffers, in FP64.
 constexpr int FR_MAX_RNE = 4096;
 struct RowStep {
-  int R1, R2, Rn, Rne;
-  const float* V1;  // R1 x R1 eigenvectors (columns), or nullptr for R1 = 1
-  const float* V2;  // R2 x R2
-  const float* s1;  // R1 eigenvalues sigma^2 (nullptr for R1 = 1)
-  const float* s2;  // R2
+  WbBase b;
+  int Rn, Rne;
   const float* Gn;
   const double* gp64;
-  const float* Vw;      // Rn x Rne: lambda (G+)^T - w G
-  const float* AinvUt;  // Rn x Rne: rows A^-1 applied to the columns of G+
-  const float* Cinv;    // Rn x Rn
-  double lambda, w;
-  float wf, alpha;
+  const double* Vw;     // Rn x Rne: lambda (G+)^T - w G
+  const double* AinvU;  // Rn x Rne: A^-1 applied to the columns of G+
+  const double* Cinv;   // Rn x Rn
+  double lambda, w, alpha;
 };
 __global__ void __launch_bounds__(256) k_factor_rows(RowStep p, float* __restrict__ Z, const float* __restrict__ gsk,
                                                      double* __restrict__ rowstat) {
   extern __shared__ double fr_smem[];
-  const int R1 = p.R1, R2 = p.R2, Rn = p.Rn, Rne = p.Rne;
-  double* zs = fr_smem;                               // Rne
-  float* M = reinterpret_cast<float*>(zs + Rne);      // Rne
-  float* T = M + Rne;                                 // Rne
+  const int Rn = p.Rn, Rne = p.Rne;
+  double* zs = fr_smem;     // Rne
+  double* M = zs + Rne;     // Rne
+  double* T = M + Rne;      // Rne
   __shared__ double tv[PEN_MAXRN], uv[PEN_MAXRN];
-  __shared__ float u1[PEN_MAXRN], u2[PEN_MAXRN];
   __shared__ float red[3][8];
   const int64_t row = blockIdx.x;
   float* z = Z + row * Rne;
@@ -293,7 +385,7 @@ __global__ void __launch_bounds__(256) k_factor_rows(RowStep p, float* __restric
   for (int k = threadIdx.x; k < Rne; k += blockDim.x) zs[k] = (double)z[k];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // gradient: w z + G+ (lambda (G+)^T z - w G z) - gsk in FP64
+  // gradient: w z + G+ (lambda (G+)^T z - w G z) - gsk
   for (int a = warp; a < Rn; a += nw) {
     double t = 0.0, u = 0.0;
     for (int k = lane; k < Rne; k += 32) {
@@ -316,67 +408,30 @@ __global__ void __launch_bounds__(256) k_factor_rows(RowStep p, float* __restric
   for (int k = threadIdx.x; k < Rne; k += blockDim.x) {
     double c = 0.0;
     for (int a = 0; a < Rn; ++a) c = fma(p.gp64[(int64_t)k * Rn + a], tv[a], c);
-    M[k] = (float)(p.w * zs[k] + c - (double)g_sk[k]);
+    M[k] = p.w * zs[k] + c - (double)g_sk[k];
   }
   __syncthreads();
-  // A^-1 g: T = V1^T M, M = (T V2) / (s1 s2 + w), T = V1 M, M = T V2^T
-  for (int e = threadIdx.x; e < Rne; e += blockDim.x) {
-    const int j = e / R2, l = e - j * R2;
-    float acc = 0.f;
-    if (p.V1)
-      for (int k = 0; k < R1; ++k) acc = fmaf(p.V1[k * R1 + j], M[k * R2 + l], acc);
-    else
-      acc = M[e];
-    T[e] = acc;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < Rne; e += blockDim.x) {
-    const int j = e / R2, l = e - j * R2;
-    float acc = 0.f;
-    for (int r = 0; r < R2; ++r) acc = fmaf(T[j * R2 + r], p.V2[r * R2 + l], acc);
-    float prod = 1.f * p.s2[l];
-    if (p.s1) prod *= p.s1[j];
-    const float d = prod + p.wf;
-    M[e] = d > 0.f ? acc / d : 0.f;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < Rne; e += blockDim.x) {
-    const int j = e / R2, l = e - j * R2;
-    float acc = 0.f;
-    if (p.V1)
-      for (int k = 0; k < R1; ++k) acc = fmaf(p.V1[j * R1 + k], M[k * R2 + l], acc);
-    else
-      acc = M[e];
-    T[e] = acc;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < Rne; e += blockDim.x) {
-    const int j = e / R2, r = e - j * R2;
-    float acc = 0.f;
-    for (int l = 0; l < R2; ++l) acc = fmaf(T[j * R2 + l], p.V2[r * R2 + l], acc);
-    M[e] = acc;
-  }
-  __syncthreads();
-  // Woodbury correction: u1 = V D, u2 = C^-1 u1, d = D - (A^-1 U) u2
+  base_apply_block64(p.b, M, T);  // D = A^-1 g
+  // Woodbury correction: u1 = V D (tv), u2 = C^-1 u1 (uv), d = D - (A^-1 U) u2
   for (int a = warp; a < Rn; a += nw) {
-    float acc = 0.f;
-    for (int k = lane; k < Rne; k += 32) acc = fmaf(p.Vw[(int64_t)a * Rne + k], M[k], acc);
+    double acc = 0.0;
+    for (int k = lane; k < Rne; k += 32) acc = fma(p.Vw[(int64_t)a * Rne + k], M[k], acc);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) u1[a] = acc;
+    if (lane == 0) tv[a] = acc;
   }
   __syncthreads();
   for (int a = threadIdx.x; a < Rn; a += blockDim.x) {
-    float acc = 0.f;
-    for (int b = 0; b < Rn; ++b) acc = fmaf(p.Cinv[a * Rn + b], u1[b], acc);
-    u2[a] = acc;
+    double acc = 0.0;
+    for (int b = 0; b < Rn; ++b) acc = fma(p.Cinv[a * Rn + b], tv[b], acc);
+    uv[a] = acc;
   }
   __syncthreads();
   float s_1 = 0.f, s_2 = 0.f, bad = 0.f;
   for (int k = threadIdx.x; k < Rne; k += blockDim.x) {
-    float gr = 0.f;
-    for (int a = 0; a < Rn; ++a) gr = fmaf(p.AinvUt[(int64_t)a * Rne + k], u2[a], gr);
-    const float st = p.alpha * (M[k] - gr);
+    double gr = 0.0;
+    for (int a = 0; a < Rn; ++a) gr = fma(p.AinvU[(int64_t)a * Rne + k], uv[a], gr);
+    const float st = (float)(p.alpha * (M[k] - gr));
     const float zn = (float)zs[k] - st;
     z[k] = zn;
     s_1 = fmaf(st, st, s_1);
@@ -408,8 +463,31 @@ __global__ void __launch_bounds__(256) k_factor_rows(RowStep p, float* __restric
   }
 }
 
+// State of a factor step's Richardson loop on the device (the stopping rule's history).
+struct FactorLoop {
+  double h[4];
+  double prev_step, min_step, min_rel, rel;
+  int grow, since_min, it, status;
+};
+
+__global__ void k_factor_loop_init(FactorLoop* st) {
+  st->prev_step = INFINITY;
+  st->min_step = INFINITY;
+  st->min_rel = INFINITY;
+  st->rel = INFINITY;
+  st->grow = 0;
+  st->since_min = 0;
+  st->it = 0;
+  st->status = STEP_CONTINUE;
+}
+
 // out = {sum ||step||^2, sum ||z||^2, any non-finite, max_r ||step_r|| / ||z_r||} (one block).
-__global__ void k_rows_reduce(const double* __restrict__ rowstat, int nrow, double* __restrict__ out) {
+// With st, thread 0 then applies the stopping rule (the same function as the host loop,
+// on the largest per-row ratio), counts the iteration, stops at max_iter, and inside a
+// graph sets the loop condition.
+__global__ void k_rows_reduce(const double* __restrict__ rowstat, int nrow, double* __restrict__ out,
+                              FactorLoop* __restrict__ st, double tol, int max_iter, cudaGraphConditionalHandle hnd,
+                              int use_hnd) {
   double s1 = 0, s2 = 0, bad = 0, mx = 0;
   for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
     const double a = rowstat[3 * r], b = rowstat[3 * r + 1];
@@ -446,6 +524,16 @@ __global__ void k_rows_reduce(const double* __restrict__ rowstat, int nrow, doub
     out[1] = b;
     out[2] = c;
     out[3] = d;
+    if (st) {
+      const double hv[4] = {a, b, c, d};
+      for (int k = 0; k < 4; ++k) st->h[k] = hv[k];
+      st->it += 1;
+      int status = step_check(hv, tol, &st->prev_step, &st->min_step, &st->min_rel, &st->grow, &st->since_min,
+                              &st->rel, d);
+      if (status == STEP_CONTINUE && st->it >= max_iter) status = STEP_MAXITER;
+      st->status = status;
+      if (use_hnd) cudaGraphSetConditional(hnd, status == STEP_CONTINUE ? 1u : 0u);
+    }
   }
 }
 
@@ -555,6 +643,19 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   nd.add<double>(3 * (int64_t)In + 8);                // row stats, reductions
   nd.add<int>(8);
   nd.add<double>(1024);                               // resid partials
+  nd.add<FactorLoop>(1);                              // stopping-rule state
+  // one or two other modes: the gradient, the FP64 Woodbury preconditioner and the update
+  // of every row in one kernel (k_factor_rows); more: the batched FP32 mode-product chain
+  const bool fused_rows = No <= 2 && Rne <= FR_MAX_RNE && Rn <= PEN_MAXRN;
+  if (fused_rows) {
+    for (int k = 0; k < No; ++k) {
+      nd.add<double>((int64_t)mo.R[k] * mo.R[k]);  // FP64 eigenvectors
+      nd.add<double>(mo.R[k]);                     // FP64 eigenvalues
+    }
+    nd.add<double>((int64_t)Rn * Rne);  // A^-1 U
+    nd.add<double>((int64_t)Rn * Rne);  // V
+    nd.add<double>((int64_t)Rn * Rn);   // C^-1
+  }
   if (slab) kr_tiles_own_need(&tl, cells, nd);
   {
     Need sc = nd;  // the tile construction reuses the sketch build's scratch
@@ -645,15 +746,64 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   double* red = rowstat + 3 * (int64_t)In;
   int* flag = cv.take<int>(8);
   double* rpart = cv.take<double>(1024);
+  FactorLoop* dloop = cv.take<FactorLoop>(1);
+  RowStep rs = {};
+  double* V64[2] = {nullptr, nullptr};
+  double* s64[2] = {nullptr, nullptr};
+  double *AinvU64 = nullptr, *Vw64 = nullptr, *Cinv64 = nullptr;
+  if (fused_rows) {
+    for (int k = 0; k < No; ++k) {
+      V64[k] = cv.take<double>((int64_t)mo.R[k] * mo.R[k]);
+      s64[k] = cv.take<double>(mo.R[k]);
+    }
+    AinvU64 = cv.take<double>((int64_t)Rn * Rne);
+    Vw64 = cv.take<double>((int64_t)Rn * Rne);
+    Cinv64 = cv.take<double>((int64_t)Rn * Rn);
+  }
   if (slab) kr_tiles_layout(&tl, cells, cv);
   (void)spare;
-  // A^-1 U (rows: A^-1 applied to each column of G+), capacitance and its inverse
-  KR_TRY(base_apply(ctx, to, Rn, w, GpT, AinvUt, t0, t1));
-  KR_LAUNCH(ctx, k_capacitance, Rn * Rn, 256, 0, Vw, AinvUt, Rn, (int)Rne, C);
-  {
-    const size_t sm = (size_t)Rn * 2 * Rn * sizeof(double);
-    KR_TRY(kr_smem_attr(ctx, k_gauss_jordan, sm));
-    KR_LAUNCH(ctx, k_gauss_jordan, 1, 256, sm, C, Rn, Cinv, flag);
+  const size_t gj_smem = (size_t)Rn * 2 * Rn * sizeof(double);
+  KR_TRY(kr_smem_attr(ctx, k_gauss_jordan, gj_smem));
+  if (fused_rows) {
+    // FP64 Woodbury pieces: eigen-decompositions of the other modes' Gram matrices, A^-1 U,
+    // V, the capacitance and its inverse
+    int Ro[2];
+    const double* gr[2];
+    for (int k = 0, j = 0; k < N; ++k) {
+      if (k == n) continue;
+      Ro[j] = m.R[k];
+      gr[j] = ta.gram[k];
+      ++j;
+    }
+    KR_TRY(kr_eig64(ctx, No, Ro, gr, V64, s64));
+    rs.b.R1 = No == 2 ? Ro[0] : 1;
+    rs.b.R2 = Ro[No - 1];
+    rs.b.V1 = No == 2 ? V64[0] : nullptr;
+    rs.b.V2 = V64[No - 1];
+    rs.b.s1 = No == 2 ? s64[0] : nullptr;
+    rs.b.s2 = s64[No - 1];
+    rs.b.w = w;
+    rs.Rn = Rn;
+    rs.Rne = (int)Rne;
+    rs.Gn = Gn;
+    rs.gp64 = gp64;
+    rs.Vw = Vw64;
+    rs.AinvU = AinvU64;
+    rs.Cinv = Cinv64;
+    rs.lambda = cfg.lambda;
+    rs.w = w;
+    rs.alpha = cfg.alpha;
+    KR_LAUNCH(ctx, k_vw64, grid_of(ctx, Rtot), 256, 0, gp64, Gn, Rn, (int)Rne, cfg.lambda, w, Vw64);
+    KR_TRY(kr_smem_attr(ctx, k_base_cols64, (size_t)16 * Rne));
+    KR_LAUNCH(ctx, k_base_cols64, Rn, 256, (size_t)16 * Rne, rs.b, gp64, Rn, (int)Rne, AinvU64);
+    KR_LAUNCH(ctx, k_capacitance64, Rn * Rn, 256, 0, Vw64, AinvU64, Rn, (int)Rne, C);
+    KR_LAUNCH(ctx, k_gauss_jordan, 1, 256, gj_smem, C, Rn, Cinv, flag, Cinv64);
+    KR_TRY(kr_smem_attr(ctx, k_factor_rows, (size_t)24 * Rne));
+  } else {
+    // A^-1 U (rows: A^-1 applied to each column of G+), capacitance and its inverse
+    KR_TRY(base_apply(ctx, to, Rn, w, GpT, AinvUt, t0, t1));
+    KR_LAUNCH(ctx, k_capacitance, Rn * Rn, 256, 0, Vw, AinvUt, Rn, (int)Rne, C);
+    KR_LAUNCH(ctx, k_gauss_jordan, 1, 256, gj_smem, C, Rn, Cinv, flag, (double*)nullptr);
   }
   // batched sketch: row i of X_(n), fresh draws per row (counter row = i)
   {
@@ -675,36 +825,13 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     trf[k + 1] = 0;
     trb[k + 1] = 1;
   }
-  // one or two other modes: the gradient, the Woodbury preconditioner and the update of
-  // every row in one kernel (k_factor_rows); more: the batched mode-product chain
-  const bool fused_rows = No <= 2 && Rne <= FR_MAX_RNE && Rn <= PEN_MAXRN;
-  RowStep rs = {};
-  if (fused_rows) {
-    rs.R1 = No == 2 ? to.R[0] : 1;
-    rs.R2 = to.R[No - 1];
-    rs.Rn = Rn;
-    rs.Rne = (int)Rne;
-    rs.V1 = No == 2 ? to.V[0] : nullptr;
-    rs.V2 = to.V[No - 1];
-    rs.s1 = No == 2 ? to.sig2[0] : nullptr;
-    rs.s2 = to.sig2[No - 1];
-    rs.Gn = Gn;
-    rs.gp64 = gp64;
-    rs.Vw = Vw;
-    rs.AinvUt = AinvUt;
-    rs.Cinv = Cinv;
-    rs.lambda = cfg.lambda;
-    rs.w = w;
-    rs.wf = (float)w;
-    rs.alpha = (float)cfg.alpha;
-    KR_TRY(kr_smem_attr(ctx, k_factor_rows, (size_t)16 * Rne));
-  }
   const int nblk = kr_resid_blocks(ctx);
-  double* h = (double*)ctx->hbuf;
-  int it = 0, grow = 0, since_min = 0, converged = 0;
-  double prev_step = INFINITY, min_step = INFINITY, min_rel = INFINITY, rel = INFINITY;
-  kr_status st = KR_OK;
-  for (it = 1; it <= cfg.max_iter; ++it) {
+  FactorLoop* hl = reinterpret_cast<FactorLoop*>(ctx->hbuf);
+  int* hflag = reinterpret_cast<int*>(static_cast<char*>(ctx->hbuf) + 512);
+  KR_LAUNCH(ctx, k_factor_loop_init, 1, 1, 0, dloop);
+  // One Richardson iteration of every row, then the stopping rule on the device (inside
+  // the graph it also sets the loop condition).
+  auto one_iter = [&](cudaGraphConditionalHandle hnd, int use_hnd) -> kr_status {
     int used = 0;
     // sampled part: Gb = K~^T Omega (b~ - K~ z) per row
     if (slab) {
@@ -716,7 +843,7 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
       KR_TRY(kr_kron_apply2(ctx, No + 1, dfw_out, dfw_in, Bf, trb, W, Gb, t0, t1));
     }
     if (fused_rows) {
-      KR_LAUNCH(ctx, k_factor_rows, In, 256, (size_t)16 * Rne, rs, Z, Gb, rowstat);
+      KR_LAUNCH(ctx, k_factor_rows, In, 256, (size_t)24 * Rne, rs, Z, Gb, rowstat);
     } else {
       // grad = w z + G+ (lambda (G+)^T z - w G z) - Gb  (FP64 combination, one block per row)
       KR_LAUNCH(ctx, k_penalty_rows, In, 256, sizeof(double) * Rne, Z, Gn, gp64, Gb, Rn, (int)Rne, cfg.lambda, w, Gr,
@@ -731,27 +858,40 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
       KR_LAUNCH(ctx, k_row_update, In, 256, 0, Z, D, (float)cfg.alpha, (int)Rne, rowstat);
     }
     // stopping rule on the largest per-row relative step
-    KR_LAUNCH(ctx, k_rows_reduce, 1, 256, 0, rowstat, In, red);
-    KR_CUDA(ctx, cudaMemcpyAsync(h, red, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    KR_CUDA(ctx, cudaMemcpyAsync(h + 4, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    KR_LAUNCH(ctx, k_rows_reduce, 1, 256, 0, rowstat, In, red, dloop, cfg.tol, cfg.max_iter, hnd, use_hnd);
+    return KR_OK;
+  };
+  auto read_state = [&]() -> kr_status {
+    KR_CUDA(ctx, cudaMemcpyAsync(hl, dloop, sizeof(FactorLoop), cudaMemcpyDeviceToHost, ctx->stream));
     KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (it == 1 && *(int*)(h + 4) != 0)
-      return kr_fail(ctx, KR_ERANK, "factor step %d: the Woodbury capacitance matrix is singular", n);
-    StepCheck sc = step_check(h, cfg.tol, &prev_step, &min_step, &min_rel, &grow, &since_min, &rel, h[3]);
-    if (sc == STEP_NONFINITE) {
-      st = kr_fail(ctx, KR_ENONFINITE, "factor step %d: iterate became non-finite at iteration %d", n, it);
-      break;
-    }
-    if (sc == STEP_DIVERGED) {
-      st = kr_fail(ctx, KR_EDIVERGED, "factor step %d: Richardson step grew 3 times past 16x its minimum", n);
-      break;
-    }
-    if (sc == STEP_CONVERGED || sc == STEP_FLOOR) {
-      converged = sc == STEP_CONVERGED ? 1 : 2;
-      break;
+    return KR_OK;
+  };
+  // The first iteration runs from the host (with the capacitance check); iterations 2..
+  // as one graph (KR_OPT_DEVICE_LOOP) or from the host.
+  KR_TRY(one_iter(0, 0));
+  KR_CUDA(ctx, cudaMemcpyAsync(hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  KR_TRY(read_state());
+  if (*hflag != 0) return kr_fail(ctx, KR_ERANK, "factor step %d: the Woodbury capacitance matrix is singular", n);
+  if (hl->status == STEP_CONTINUE && ctx->device_loop && !ctx->timing) {
+    int64_t per_step = 0;
+    const int it0 = hl->it;
+    if (kr_graph_while(ctx, one_iter, &per_step)) {
+      KR_TRY(read_state());
+      ctx->launches += per_step * (hl->it - it0);
     }
   }
-  if (it > cfg.max_iter) it = cfg.max_iter;
+  while (hl->status == STEP_CONTINUE) {
+    KR_TRY(one_iter(0, 0));
+    KR_TRY(read_state());
+  }
+  const int it = hl->it;
+  const double rel = hl->rel;
+  const int converged = hl->status == STEP_CONVERGED ? 1 : (hl->status == STEP_FLOOR ? 2 : 0);
+  kr_status st = KR_OK;
+  if (hl->status == STEP_NONFINITE)
+    st = kr_fail(ctx, KR_ENONFINITE, "factor step %d: iterate became non-finite at iteration %d", n, it);
+  if (hl->status == STEP_DIVERGED)
+    st = kr_fail(ctx, KR_EDIVERGED, "factor step %d: Richardson step grew 3 times past 16x its minimum", n);
   // a_i = (G+)^T z_i  (the new factor rows, FP64 accumulation)
   KR_LAUNCH(ctx, k_penalty_rows, In, 256, sizeof(double) * Rne, Z, Gn, gp64, Gb, Rn, (int)Rne, cfg.lambda, w, Gr,
             An_out);
