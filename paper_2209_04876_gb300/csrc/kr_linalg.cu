@@ -320,6 +320,12 @@ struct JacobiArgs {
 };
 __device__ __forceinline__ float jac_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double jac_rsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float jac_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double jac_abs(double x) { return fabs(x); }
+__device__ __forceinline__ float jac_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double jac_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float jac_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double jac_max(double a, double b) { return fmax(a, b); }
 
 template <class T>
 __global__ void k_jacobi(JacobiArgs<T> ja) {
@@ -340,8 +346,10 @@ __global__ void k_jacobi(JacobiArgs<T> ja) {
     V[i * LD + j] = (i == j) ? one : zero;
   }
   __syncthreads();
-  // converged when the off-diagonal squares are below 1e-14 (FP32) / 1e-30 (FP64) of the diagonal's
-  const T conv = sizeof(T) == 4 ? T(1e-14f) : T(1e-30);
+  // converged when the off-diagonal squares are below 1e-14 (FP32) / 1e-26 (FP64) of the diagonal's
+  // (FP64: an off-diagonal norm ~3e-13 of the matrix's, above the rounding floor of about
+  // R * 1e-16 that a stricter test would never reach)
+  const T conv = sizeof(T) == 4 ? T(1e-14f) : T(1e-26);
   const int max_sweeps = sizeof(T) == 4 ? 20 : 40;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int r = 0; r < m - 1; ++r) {
@@ -353,9 +361,9 @@ __global__ void k_jacobi(JacobiArgs<T> ja) {
         if (p > q) { int t = p; p = q; q = t; }
         T apq = A[p * LD + q], app = A[p * LD + p], aqq = A[q * LD + q];
         T c = one, s = zero;
-        if (fabs(apq) > T(1e-30f) * (fabs(app) + fabs(aqq)) && apq != zero) {
+        if (jac_abs(apq) > T(1e-30f) * (jac_abs(app) + jac_abs(aqq)) && apq != zero) {
           T tau = (aqq - app) / (T(2) * apq);
-          T t = (tau >= zero ? one : -one) / (fabs(tau) + sqrt(one + tau * tau));
+          T t = (tau >= zero ? one : -one) / (jac_abs(tau) + jac_sqrt(one + tau * tau));
           c = jac_rsqrt(one + t * t);
           s = t * c;
         }
@@ -401,7 +409,7 @@ __global__ void k_jacobi(JacobiArgs<T> ja) {
     if (done) break;
   }
   for (int e = tid; e < R * R; e += blockDim.x) ja.V[n][e] = V[(e / R) * LD + (e % R)];
-  for (int i = tid; i < R; i += blockDim.x) ja.sig2[n][i] = fmax(A[i * LD + i], zero);
+  for (int i = tid; i < R; i += blockDim.x) ja.sig2[n][i] = jac_max(A[i * LD + i], zero);
 }
 
 }  // namespace
