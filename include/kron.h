@@ -300,8 +300,10 @@ KR_API kr_status kron_ridge_batched(kr_ctx* ctx, int32_t nprob, const kr_factors
  * G: prod R floats (C-order); A[n] is overwritten. Needs R[n] <= prod_{m != n} R[m]
  * (else KR_EINVAL), prod_{m != n} R[m] <= 24576 (else KR_ENOTIMPL) and a full-row-rank
  * G_(n) (else KR_ERANK). The terms of the update that cancel in the row space of
- * G_(n)^T (w z and G+ (w G z)) and the output rows are formed in FP64; the sampled terms
- * and the preconditioner in FP32. */
+ * G_(n)^T (w z and G+ (w G z)) and the output rows are formed in FP64. With one or two
+ * other modes the Woodbury preconditioner is FP64 as well (FP64 eigen-decompositions of
+ * the other modes' Gram matrices; w multiplies any error of its base inverse); with more
+ * it is FP32. The sampled terms and the iterate z are FP32. */
 KR_API kr_status tucker_factor_update(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R,
                                       const float* X, float* const A[], const float* G, int32_t n,
                                       const kr_opts* opts, kr_report* report);
