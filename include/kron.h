@@ -150,13 +150,20 @@ enum {
  *    workspace per 32 keys), ranks the set bits and counts the draws per rank with integer
  *    atomics; 0 takes 2 when the key space is at most 64 times the draw count, else 1. Both
  *    give identical sketches.
+ *  KR_OPT_HOST_GATHER (default 1): host-buffer solves (kr_opts.host_io) with b in
+ *    page-locked host memory (cudaHostAlloc / cudaHostRegister, mapped into the device's
+ *    address space) gather the sampled entries b~ = S b in place, reading s of the prod I
+ *    entries of b; 0 copies all of b to the device first (on a second stream, overlapped
+ *    with the tables, draws and grouping). Other host memory is always copied. Both give
+ *    identical results.
  * Returns KR_EINVAL for an unknown key or a value out of range. */
 enum {
   KR_OPT_SLAB_PASS = 1,
   KR_OPT_SLAB_TILE_ENTRIES = 2,
   KR_OPT_DEVICE_LOOP = 3,
   KR_OPT_BATCH_WORKERS = 4,
-  KR_OPT_GROUPING = 5
+  KR_OPT_GROUPING = 5,
+  KR_OPT_HOST_GATHER = 6
 };
 KR_API kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value);
 

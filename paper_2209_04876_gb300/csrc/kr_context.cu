@@ -78,6 +78,10 @@ extern "C" kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value) {
       if (value < 0 || value > 2) return kr_fail(ctx, KR_EINVAL, "kr_set_option: grouping must be 0, 1 or 2");
       ctx->grouping = (int)value;
       return KR_OK;
+    case KR_OPT_HOST_GATHER:
+      if (value != 0 && value != 1) return kr_fail(ctx, KR_EINVAL, "kr_set_option: host gather must be 0 or 1");
+      ctx->host_gather = (int)value;
+      return KR_OK;
     default:
       return kr_fail(ctx, KR_EINVAL, "kr_set_option: unknown key %d", key);
   }

@@ -36,6 +36,7 @@ struct kr_ctx {
   int device_loop = 1;  // Richardson iterations 2.. as one CUDA graph with a conditional loop
   int batch_workers = 4;  // kron_ridge_batched: problems solved concurrently (worker contexts)
   int grouping = 0;       // draws grouped by: 0 automatic, 1 radix sort, 2 ranks in a key bitmap
+  int host_gather = 1;    // host-buffer solves: gather b~ from page-locked b in place (no copy of b)
   // worker contexts of kron_ridge_batched, each with its own stream and workspace (owned)
   std::vector<kr_ctx*> workers;
   std::vector<cudaStream_t> worker_streams;

@@ -1499,6 +1499,33 @@ kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr
     md.A[n] = a;
   }
   float* bd = cv.take<float>(I);
+  float* xd = cv.take<float>(R);
+  // b in page-locked host memory is mapped into the device's address space: the gather reads
+  // the s sampled entries in place (Alg. 2 reads b only at the sampled rows) instead of
+  // copying all prod I entries
+  const float* b_mapped = nullptr;
+  if (ctx->host_gather) {
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, b) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+      b_mapped = static_cast<const float*>(pa.devicePointer);
+    else
+      cudaGetLastError();  // not page-locked: copy it
+  }
+  if (b_mapped) {
+    kr_status st = kr_solve_device(ctx, md, b_mapped, cfg, o->seed, o->call_id, xd, rep);
+    if (st == KR_OK || st == KR_ENOTCONV) {
+      KR_CUDA(ctx, cudaMemcpyAsync(x, xd, sizeof(float) * R, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    KR_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+    KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (rep) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      rep->t_ms[6] = ms - rep->t_ms[7];
+      rep->t_ms[7] = ms;
+    }
+    return st;
+  }
   // b on the copy stream, overlapping the tables, draws and sort of the solve stream; the
   // gather waits for it
   if (!ctx->copy_stream) {
@@ -1511,7 +1538,6 @@ kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr
   KR_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->b_ready, 0));
   KR_CUDA(ctx, cudaMemcpyAsync(bd, b, sizeof(float) * I, cudaMemcpyHostToDevice, ctx->copy_stream));
   KR_CUDA(ctx, cudaEventRecord(ctx->b_ready, ctx->copy_stream));
-  float* xd = cv.take<float>(R);
   ctx->b_wait = ctx->b_ready;
   kr_status st = kr_solve_device(ctx, md, bd, cfg, o->seed, o->call_id, xd, rep);
   ctx->b_wait = nullptr;

@@ -306,17 +306,27 @@ def test_objective_full():
 
 @pytest.mark.parametrize("I,R", [([64, 48, 40], [4, 3, 5]),
                                  ([256, 256, 256], [16, 16, 16])])  # b's copy outlasts the draws and sort
-def test_host_io_matches_device_path(I, R):
-    """Host buffers: b is copied on the context's copy stream while the solve stream builds
-    the tables, draws and sorts; the result is the device path's, bit for bit."""
+@pytest.mark.parametrize("gather,pinned", [(1, True), (0, True), (1, False)],
+                         ids=["in-place", "copied", "pageable"])
+def test_host_io_matches_device_path(I, R, gather, pinned):
+    """Host buffers: a page-locked b is read in place at the sampled rows (OPT_HOST_GATHER 1),
+    or copied on the context's copy stream while the solve stream builds the tables, draws
+    and groups (OPT_HOST_GATHER 0, and any pageable b); the result is the device path's,
+    bit for bit."""
     prob = kron_problem(I, R, seed=15, noise_rel=0.05)
     As = [np.asarray(A, dtype=np.float32) for A in prob["As"]]
     b = prob["b"].astype(np.float32)
     xd, rd = kr.kron_regress([dev(A) for A in As], dev(b), eps=0.1, seed=3, call_id=1)
-    xh, rh = kr.kron_regress([torch.tensor(A) for A in As], torch.tensor(b).pin_memory(), eps=0.1, seed=3,
-                             call_id=1, host_io=True)
+    bh = torch.tensor(b)
+    if pinned:
+        bh = bh.pin_memory()
+    try:
+        kr.set_option(kr.OPT_HOST_GATHER, gather)
+        xh, rh = kr.kron_regress([torch.tensor(A) for A in As], bh, eps=0.1, seed=3, call_id=1, host_io=True)
+    finally:
+        kr.set_option(kr.OPT_HOST_GATHER, 1)
     np.testing.assert_array_equal(host(xd), xh.numpy())
-    assert rd["iters"] == rh["iters"]
+    assert rd["iters"] == rh["iters"] and rd["distinct"] == rh["distinct"]
 
 
 def test_deterministic_reruns():

@@ -183,7 +183,7 @@ def test_device_loop_stops_at_max_iter():
 def test_set_option_rejects_bad_values():
     for key, val in [(kr.OPT_SLAB_PASS, 2), (kr.OPT_SLAB_TILE_ENTRIES, 100), (kr.OPT_SLAB_TILE_ENTRIES, (1 << 22) + 1),
                      (kr.OPT_DEVICE_LOOP, 7), (kr.OPT_BATCH_WORKERS, 0), (kr.OPT_BATCH_WORKERS, 33),
-                     (kr.OPT_GROUPING, -1), (kr.OPT_GROUPING, 3), (99, 1)]:
+                     (kr.OPT_GROUPING, -1), (kr.OPT_GROUPING, 3), (kr.OPT_HOST_GATHER, 2), (99, 1)]:
         with pytest.raises(kr.KronError) as e:
             kr.set_option(key, val)
         assert e.value.name == "KR_EINVAL"
