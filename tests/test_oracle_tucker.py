@@ -159,3 +159,43 @@ def test_sampled_als_reaches_exact_als_quality():
     # fixed point is within about (1+eps)^2 of the exact one in reconstruction error
     assert hs[-1] <= (1 + 2 * 0.1) * he[-1]
     assert hs[-1] < 2e-4  # at the 1e-4 noise floor
+
+
+def test_factor_row_richardson_rate_with_large_penalty_needs_exact_eigenvectors():
+    """With factors far from orthonormal the penalty w = (1 + 12/eps) prod sigma_max^2 reaches
+    ~1e10 and dwarfs the smallest eigenvalues of K^T K (~1). With the exact (FP64)
+    eigen-decomposition in the Woodbury base, Alg. 3's Richardson still contracts at the
+    Lemma 4.2 rate (about 24 iterations to 1e-10). An orthogonality error of 1e-5 in the
+    eigenvectors perturbs K^T K by about w * 1e-5 and costs more than five times as many
+    iterations: the reason the GPU factor step keeps its Woodbury chain in FP64."""
+    rng = np.random.default_rng(21)
+    I, R = (24, 20, 18), (4, 4, 3)
+    As = []
+    for i, r in zip(I, R):
+        Q, _ = np.linalg.qr(rng.standard_normal((i, r)))
+        As.append(Q @ np.diag(np.geomspace(100.0, 1.0, r)))
+    G = rng.standard_normal(R)
+    X = tk.reconstruct(G, As) + 0.01 * rng.standard_normal(I)
+    lam, eps, n = 1e-3, 0.1, 0
+    others = [As[m] for m in range(3) if m != n]
+    Gn = tk.unfold(G, n)
+    w = tk.penalty_weight(others, eps)
+    assert w > 1e10
+    s = ko.sample_count(int(np.prod([A.shape[1] for A in others])), eps)
+    smp = tk.row_sample(others, s, seed=3, call_id=5, row=0)
+    b_s = tk.unfold(X, n)[0][smp.keys]
+    _, a, it_exact = tk.row_richardson(others, Gn, b_s, smp, lam, eps, w, tol=1e-10, max_iter=200)
+    assert it_exact <= 30
+    _, ad = tk.row_dense_solve(others, Gn, b_s, smp, lam, w)
+    np.testing.assert_allclose(a, ad, rtol=1e-6, atol=1e-9)
+
+    P = tk.WoodburyPreconditioner(others, Gn, lam, w)
+    r2 = np.random.default_rng(0)
+    P.base.V = [V + 1e-5 * r2.standard_normal(V.shape) for V in P.base.V]
+    # rebuild the pieces that depend on the base inverse
+    P.AinvU = np.stack([P.base.apply(P.U[:, k]) for k in range(P.U.shape[1])], axis=1)
+    P.C = np.eye(Gn.shape[0]) + P.V @ P.AinvU
+    P.Cinv = np.linalg.inv(P.C)
+    with np.errstate(over="ignore", invalid="ignore"):
+        _, _, it_pert = tk.row_richardson(others, Gn, b_s, smp, lam, eps, w, P=P, tol=1e-10, max_iter=200)
+    assert it_pert > 5 * it_exact
