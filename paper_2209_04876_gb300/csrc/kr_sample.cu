@@ -14,9 +14,11 @@
 //
 // Grouping (the sets S_1, S_2 and B_S of the proof of Thm 4.4 with T = {N}):
 // cell = (i_1..i_{N-1}), the last coordinate i_N stays with the sample. Every draw
-// writes its row key cell * I_N + i_N; a stable radix sort of the keys (kr_sort.cu)
-// makes repeated rows adjacent and orders cells; runs of equal keys become the merged
-// entries (i_N, multiplicity) of each cell in increasing i_N order, with b gathered.
+// writes its row key cell * I_N + i_N. The distinct keys and their multiplicities, in
+// increasing key order, come either from ranks in a bitmap of the key space (when it
+// holds at most 64 keys per draw) or from a stable radix sort of the keys (kr_sort.cu)
+// and its runs of equal keys; both give the merged entries (i_N, multiplicity) of each
+// cell in increasing i_N order, with b gathered.
 #include "kr_internal.cuh"
 
 namespace {
