@@ -1591,6 +1591,8 @@ static kr_status kr_workers_reserve(kr_ctx* ctx, int n) {
     w->slab_pass = ctx->slab_pass;
     w->slab_tile_entries = ctx->slab_tile_entries;
     w->device_loop = ctx->device_loop;
+    w->grouping = ctx->grouping;
+    w->host_gather = ctx->host_gather;
     w->timing = false;
   }
   return KR_OK;
