@@ -25,7 +25,9 @@ Readings where the paper is silent (all mirrored by the CUDA path):
   s), at least 1.
 * Duplicated draws are merged: a row drawn c times gets weight omega = c / (s p), which
   gives the same sketched objective as c separate rows of weight 1/(s p).
-* Convergence: stop when ||step|| <= tol * ||x||.
+* Convergence: stop when ||step|| <= tol * ||x||; or (stop="eps") once the Lemma 4.2 bound
+  on the sampled objective's remaining excess falls below theta * eps of its minimum
+  (eps_stop_bound; the O(log 1/eps) iterations of the proof of Thm 4.5).
 """
 import math
 
@@ -326,21 +328,46 @@ def sampled_objective(As, b_s, sample, x, lam):
     return float(np.sum(sample.omega * (u - b_s) ** 2) + lam * np.dot(x, x))
 
 
+def eps_stop_bound(eps):
+    """Constants of the eps-aware stopping rule of `richardson` (reading of "until convergence").
+
+    The proof of Thm 4.5 gives (1 - sqrt(eps)) M <= H <= (1 + sqrt(eps)) M for the sampled
+    normal matrix H = K~^T K~ + lam I and the preconditioner's M = K^T K + lam I (exact Gram,
+    beta = 1). With the step alpha = 1 - sqrt(eps), the eigenvalues of I - alpha M+ H lie in
+    [eps, 2 sqrt(eps) - eps], so the excess e(x) = f~(x) - min f~ contracts by
+    rho^2 = (2 sqrt(eps) - eps)^2 per step (Lemma 4.2), and the gradient g at x bounds it:
+    g^T M+ g >= (1 - sqrt(eps)) e(x). Returns (rho^2, 1 - sqrt(eps))."""
+    se = math.sqrt(eps)
+    return (2.0 * se - eps) ** 2, 1.0 - se
+
+
 def richardson(As, b_s, sample, lam, eps, tol=1e-13, max_iter=2000, step=None, x0=None,
-               history=None):
-    """Alg. 2 Richardson loop: x <- x - (1 - sqrt(eps)) M+ (K~^T K~ x + lam x - K~^T b~)."""
+               history=None, stop="step", theta=0.01):
+    """Alg. 2 Richardson loop: x <- x - (1 - sqrt(eps)) M+ (K~^T K~ x + lam x - K~^T b~).
+
+    stop="step": until ||step|| <= tol ||x||. stop="eps": until the bound on the sampled
+    objective's excess after the step, rho^2 g^T M+ g / (1 - sqrt(eps)) (eps_stop_bound), is at
+    most theta * eps times the lower bound f~(x) - g^T M+ g / (1 - sqrt(eps)) of its minimum."""
     R = int(np.prod([A.shape[1] for A in As]))
     P = KronPreconditioner(As, lam)
     alpha = (1.0 - math.sqrt(eps)) if step is None else step
+    rho2, c1 = eps_stop_bound(eps)
     x = np.zeros(R) if x0 is None else np.array(x0, dtype=np.float64)
     it = 0
     for it in range(1, max_iter + 1):
         g = sampled_gradient(As, b_s, sample, x, lam)
-        d = alpha * P.apply(g)
+        pg = P.apply(g)
+        if stop == "eps":
+            q = float(np.dot(g, pg))
+            floor = sampled_objective(As, b_s, sample, x, lam) - q / c1
+        d = alpha * pg
         x = x - d
         if history is not None:
             history.append(x.copy())
-        if np.linalg.norm(d) <= tol * max(np.linalg.norm(x), 1e-300):
+        if stop == "eps":
+            if rho2 * q / c1 <= theta * eps * max(floor, 0.0):
+                break
+        elif np.linalg.norm(d) <= tol * max(np.linalg.norm(x), 1e-300):
             break
     return x, it
 

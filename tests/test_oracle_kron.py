@@ -304,3 +304,50 @@ def test_paper_table4_losses(d, n, opt_paper, alg2_paper):
     assert abs(np.mean(opts) / opt_paper - 1) < 0.2
     if ratios:
         assert 1.0 <= np.mean(ratios) <= alg2_paper / opt_paper + 0.05
+
+
+def test_eps_stop_bound_holds_each_step():
+    """The eps-aware stopping rule's bounds (proof of Thm 4.5 spectral bounds with Lemma 4.2),
+    checked on a dense problem against the exact sampled minimiser: the sample's
+    M^-1 H spectrum lies in [1 - sqrt(eps), 1 + sqrt(eps)], and at every step the excess
+    e(x_k) <= g^T M^-1 g / (1 - sqrt(eps)) and e(x_{k+1}) <= rho^2 g^T M^-1 g / (1 - sqrt(eps))."""
+    prob = kron_problem([12, 10, 9], [3, 3, 2], dist="lognormal_rows", seed=4, noise_rel=0.1)
+    As, b = prob["As"], prob["b"]
+    eps = 0.1
+    smp = ko.draw_sample(As, ko.sample_count(18, eps), 2, 1)
+    K = ko.kron_dense(As)
+    Ks = ko.sampled_rows(As, smp.keys)
+    H = Ks.T @ (smp.omega[:, None] * Ks)
+    M = K.T @ K
+    ev = np.linalg.eigvals(np.linalg.solve(M, H)).real
+    assert 1 - math.sqrt(eps) <= ev.min() and ev.max() <= 1 + math.sqrt(eps)
+    b_s = b[smp.keys]
+    xs = np.linalg.solve(H, Ks.T @ (smp.omega * b_s))
+    fstar = ko.sampled_objective(As, b_s, smp, xs, 0.0)
+    hist = []
+    ko.richardson(As, b_s, smp, 0.0, eps, tol=0.0, max_iter=10, history=hist)
+    rho2, c1 = ko.eps_stop_bound(eps)
+    x = np.zeros(18)
+    for xn in hist:
+        g = ko.sampled_gradient(As, b_s, smp, x, 0.0)
+        q = float(g @ np.linalg.solve(M, g))
+        assert ko.sampled_objective(As, b_s, smp, x, 0.0) - fstar <= q / c1 * (1 + 1e-9)
+        assert ko.sampled_objective(As, b_s, smp, xn, 0.0) - fstar <= rho2 * q / c1 * (1 + 1e-9)
+        x = xn
+
+
+@pytest.mark.parametrize("dist,noise", [("lognormal_rows", 0.05), ("outliers", 0.3)])
+def test_eps_stopping_rule_certifies_early(dist, noise):
+    """stop='eps' ends after a handful of steps with x as (1+eps)-optimal as the converged one
+    (within a tenth of the eps budget of it)."""
+    I, R, eps = [40, 36, 32], [4, 4, 4], 0.1
+    prob = kron_problem(I, R, dist=dist, seed=3, noise_rel=noise)
+    As, b = prob["As"], prob["b"]
+    opt = ko.objective(As, b, ko.closed_form_ls(As, b), 0.0)
+    smp = ko.draw_sample(As, ko.sample_count(64, eps), 1, 0)
+    x1, it1 = ko.richardson(As, b[smp.keys], smp, 0.0, eps, stop="eps")
+    x2, it2 = ko.richardson(As, b[smp.keys], smp, 0.0, eps, tol=1e-12)
+    assert it1 <= 10 and it1 < it2
+    f1, f2 = ko.objective(As, b, x1, 0.0), ko.objective(As, b, x2, 0.0)
+    assert f1 <= (1 + eps) * opt
+    assert f1 <= f2 * (1 + 0.1 * eps)
