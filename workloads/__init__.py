@@ -86,7 +86,7 @@ def kron_problem(I, R, dist="gauss", seed=0, noise_abs=None, noise_rel=None, b_k
 
 
 def kron_problem_device(I, R, dist="gauss", seed=0, noise_rel=0.01, sigma=1.0, device="cuda"):
-    """Returns dict(As=[float32 I_n x R_n on device], b=float32 (prod I) on device, I, R)."""
+    """Returns dict(As=[float32 I_n x R_n on device], b=float32 (prod I) on device, x_true, I, R)."""
     import torch
 
     I = [int(v) for v in I]
@@ -104,7 +104,8 @@ def kron_problem_device(I, R, dist="gauss", seed=0, noise_rel=0.01, sigma=1.0, d
         elif dist != "gauss":
             raise ValueError(dist)
         As.append(A.contiguous())
-    T = torch.randn(int(np.prod(R)), generator=g, device=device).reshape(R)
+    x_true = torch.randn(int(np.prod(R)), generator=g, device=device)
+    T = x_true.reshape(R)
     for n, A in enumerate(As):
         T = torch.movedim(torch.tensordot(A, T, dims=([1], [n])), 0, n)
     b = T.reshape(-1).contiguous()
@@ -112,7 +113,7 @@ def kron_problem_device(I, R, dist="gauss", seed=0, noise_rel=0.01, sigma=1.0, d
     noise = torch.randn(b.numel(), generator=g, device=device)
     noise *= noise_rel * torch.linalg.vector_norm(b) / torch.linalg.vector_norm(noise)
     b += noise
-    return dict(As=As, b=b, I=I, R=R)
+    return dict(As=As, b=b, x_true=x_true, I=I, R=R)
 
 
 def tucker_tensor(I, R, seed=0, noise_rel=0.01):
