@@ -146,8 +146,9 @@ enum {
  *    Every problem's result is the same whatever the number of workers.
  *  KR_OPT_GROUPING (default 0): how the draws of a sketch are grouped into merged rows.
  *    1 sorts the row keys (stable LSD radix sort) and merges the runs of equal keys; 2 sets
- *    one bit per draw in a bitmap of the key space (prod I_n keys, at most 2^32; 8 bytes of
- *    workspace per 32 keys), ranks the set bits and counts the draws per rank with integer
+ *    one bit per draw in a bitmap of the key space (prod I_n keys, times the factor rows of an
+ *    Alg. 3 step; at most 2^32; 8 bytes of workspace per 32 keys), ranks the set bits and
+ *    counts the draws per rank with integer
  *    atomics; 0 takes 2 when the key space is at most 64 times the draw count, else 1. Both
  *    give identical sketches.
  *  KR_OPT_HOST_GATHER (default 1): host-buffer solves (kr_opts.host_io) with b in
