@@ -13,10 +13,15 @@
 //   M^-1 = A^-1 - A^-1 U (I + V A^-1 U)^-1 V A^-1,  A = K^T K + w I, U = G+, V = lambda (G+)^T - w G,
 // where A^-1 = (x)V_m (S_m^2 (x)... + w)^-1 (x)V_m^T from the factor eigen-decompositions.
 //
-// All rows of the factor run together: the row index is a leading batch axis of every
-// mode product, the sketch keys draws by (row, cell), and b~ is gathered from X_(n).
-// The capacitance I + V A^-1 U is accumulated and inverted in FP64 (its entries cancel
-// to about 1/(1 + 12/eps) of the terms that form them).
+// All rows of the factor run together: the sketch keys draws by (row, cell), b~ is
+// gathered from X_(n), and the sampled products run in the slab pass (two other modes)
+// or between batched mode products. With one or two other modes, everything after the
+// sampled products is one kernel per row (k_factor_rows) in FP64: the Woodbury pieces
+// come from FP64 eigen-decompositions, because w multiplies any error of A^-1 and the
+// capacitance I + V A^-1 U cancels to about 1/((1 + 12/eps) cond(K^T K)) of the terms that
+// form it. With more other modes the batched FP32 mode-product chain applies M^-1 (the
+// capacitance still in FP64). The Richardson iterations after the first run as one CUDA
+// graph with the stopping rule on the device.
 #include <math.h>
 
 #include "kr_internal.cuh"
