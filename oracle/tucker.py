@@ -22,7 +22,9 @@ identity (and the dense inverse of M, checked by a test) has '-'.
 Readings: samples are drawn only over the modes m != n (K excludes mode n), with a
 fresh sketch per factor row (counter row = i); w = (1 + 12/eps) * prod_{m!=n}
 sigma_max(A(m))^2, an upper bound of the paper's ||[K; sqrt(lam)(G^T)^+] N^+||^2
-because N^+ = N is an orthogonal projector and (G^T)^+ N = 0.
+because N^+ = N is an orthogonal projector and (G^T)^+ N = 0. "Until convergence": the
+relative step test, or (stop="eps") the eps-aware rule of oracle.kron.richardson on the
+penalised objective (row_objective).
 """
 import math
 
@@ -113,19 +115,41 @@ def row_gradient(As_other, Gn, Gp, b_s, sample, z, lam, w):
     return g
 
 
+def row_objective(As_other, Gn, Gp, b_s, sample, z, lam, w):
+    """The penalised sketched objective Alg. 3's loop minimises:
+    ||S(K z - b)||^2 + lam ||(G^T)^+ z||^2 + w ||N z||^2, N = I - G+ G."""
+    z = np.asarray(z, dtype=np.float64)
+    r = ko.sampled_forward(As_other, sample.keys, z) - b_s
+    Nz = z - Gp @ (Gn @ z)
+    return float(np.sum(sample.omega * r * r) + lam * np.sum((Gp.T @ z) ** 2) + w * np.dot(Nz, Nz))
+
+
 def row_richardson(As_other, Gn, b_s, sample, lam, eps, w, P=None, tol=1e-13, max_iter=2000,
-                   step=None):
+                   step=None, stop="step", theta=0.01):
+    """Alg. 3's loop for one row. stop="step": until ||step|| <= tol ||z||. stop="eps": the
+    rule of kron.richardson on the penalised objective (its sampled matrix obeys the same
+    bounds (1 - sqrt(eps)) M <= M~ <= (1 + sqrt(eps)) M, since M~ - M = K~^T K~ - K^T K and the
+    penalty terms of M are positive semidefinite)."""
     Gn = np.asarray(Gn, dtype=np.float64)
     Gp = np.linalg.pinv(Gn)
     if P is None:
         P = WoodburyPreconditioner(As_other, Gn, lam, w)
     alpha = (1.0 - math.sqrt(eps)) if step is None else step
+    rho2, c1 = ko.eps_stop_bound(eps)
     z = np.zeros(Gn.shape[1])
     it = 0
     for it in range(1, max_iter + 1):
-        d = alpha * P.apply(row_gradient(As_other, Gn, Gp, b_s, sample, z, lam, w))
+        g = row_gradient(As_other, Gn, Gp, b_s, sample, z, lam, w)
+        pg = P.apply(g)
+        if stop == "eps":
+            q = float(np.dot(g, pg))
+            floor = row_objective(As_other, Gn, Gp, b_s, sample, z, lam, w) - q / c1
+        d = alpha * pg
         z = z - d
-        if np.linalg.norm(d) <= tol * max(np.linalg.norm(z), 1e-300):
+        if stop == "eps":
+            if rho2 * q / c1 <= theta * eps * max(floor, 0.0):
+                break
+        elif np.linalg.norm(d) <= tol * max(np.linalg.norm(z), 1e-300):
             break
     return z, Gp.T @ z, it  # z, a_i (= (G^T)^+ z = z^T G+), iterations
 

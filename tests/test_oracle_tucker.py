@@ -199,3 +199,49 @@ def test_factor_row_richardson_rate_with_large_penalty_needs_exact_eigenvectors(
     with np.errstate(over="ignore", invalid="ignore"):
         _, _, it_pert = tk.row_richardson(others, Gn, b_s, smp, lam, eps, w, P=P, tol=1e-10, max_iter=200)
     assert it_pert > 5 * it_exact
+
+
+def test_factor_row_eps_stopping_rule():
+    """The eps-aware rule on Alg. 3's penalised system: the sample's M^-1 M~ spectrum lies in
+    [1 - sqrt(eps), 1 + sqrt(eps)], the excess bound holds after every step, and the rule
+    stops after a handful of steps with a row that is still a (1+eps) solution of the
+    y-space ridge on the same sample (Lemma 5.2)."""
+    As, G = _setup(5, I=(9, 8, 7), R=(3, 3, 2))
+    X = tk.reconstruct(G, As) + 0.05 * np.random.default_rng(6).standard_normal((9, 8, 7))
+    lam, eps, n = 0.01, 0.1, 1
+    others = [As[m] for m in range(3) if m != n]
+    Gn = tk.unfold(G, n)
+    Gp = np.linalg.pinv(Gn)
+    w = tk.penalty_weight(others, eps)
+    Xn = tk.unfold(X, n)
+    M = tk.dense_penalised_matrix(others, Gn, lam, w)
+    P = tk.WoodburyPreconditioner(others, Gn, lam, w)
+    rho2, c1 = ko.eps_stop_bound(eps)
+    for i in range(3):
+        smp = tk.row_sample(others, ko.sample_count(6, eps), seed=7, call_id=9, row=i)
+        b_s = Xn[i][smp.keys]
+        rows = ko.sampled_rows(others, smp.keys)
+        Mt = M - ko.kron_dense(others).T @ ko.kron_dense(others) + rows.T @ (smp.omega[:, None] * rows)
+        ev = np.linalg.eigvals(np.linalg.solve(M, Mt)).real
+        assert 1 - math.sqrt(eps) <= ev.min() and ev.max() <= 1 + math.sqrt(eps)
+        zs, _ = tk.row_dense_solve(others, Gn, b_s, smp, lam, w)
+        fstar = tk.row_objective(others, Gn, Gp, b_s, smp, zs, lam, w)
+        z = np.zeros(Gn.shape[1])
+        for _ in range(8):
+            g = tk.row_gradient(others, Gn, Gp, b_s, smp, z, lam, w)
+            q = float(g @ P.apply(g))
+            z_next = z - (1 - math.sqrt(eps)) * P.apply(g)
+            # the gradient is that of half the objective: excess(z) = (z - z*)^T M~ (z - z*)
+            assert tk.row_objective(others, Gn, Gp, b_s, smp, z_next, lam, w) - fstar <= rho2 * q / c1 * (1 + 1e-9)
+            z = z_next
+        _, a, it = tk.row_richardson(others, Gn, b_s, smp, lam, eps, w, stop="eps")
+        _, _, it_full = tk.row_richardson(others, Gn, b_s, smp, lam, eps, w, tol=1e-14)
+        assert it <= 12 and it < it_full
+        y = tk.row_ridge_on_sample(others, Gn, b_s, smp, lam)
+        Y = rows @ Gn.T
+
+        def f(v):
+            r = Y @ v - b_s
+            return float(np.sum(smp.omega * r * r) + lam * v @ v)
+
+        assert f(a) <= (1 + eps) * f(y)
