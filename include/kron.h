@@ -25,6 +25,13 @@
  *    reported through status codes, never by trapping the GPU.
  *  - Limits: 1 <= N <= KR_MAX_MODES, 1 <= R_n <= I_n, R_n <= 64, I_n <= 65535,
  *    prod(I_n) < 2^32, number of draws s < 2^31.
+ *  - The calls are synchronous. There are no _async variants: every call reads its
+ *    report (iteration count, distinct rows, objective) back to the host before it
+ *    returns, and the part of a solve that repeats (the Richardson loop) is already run
+ *    by the library as one CUDA graph with the stopping rule on the device.
+ *  - Determinism: every path is deterministic. Sums over blocks, tiles and draws run in
+ *    a fixed order, and the only atomics are integer additions, which commute. Equal
+ *    inputs, seed and call id give bit-identical outputs on the same device.
  */
 #ifndef KRON_H
 #define KRON_H
@@ -54,7 +61,8 @@ typedef enum {
   KR_ERANK = 5,       /* a factor matrix is numerically rank deficient */
   KR_ENOTCONV = 6,    /* max_iter reached before the stopping rule held */
   KR_EDIVERGED = 7,   /* the Richardson step grew 3 times in a row */
-  KR_ETIMEOUT = 8,    /* a bounded device wait ran out */
+  KR_ETIMEOUT = 8,    /* reserved: a bounded device wait ran out. No kernel of this build waits on a
+                         flag that another kernel or device sets, so no call returns it now */
   KR_ENOTIMPL = 9     /* shape outside what this build supports */
 } kr_status;
 
@@ -83,6 +91,20 @@ typedef struct {
   int32_t host_io;       /* 1: factors, b / X and x / A / G are host pointers */
   uint64_t seed;         /* Philox key */
   uint64_t call_id;      /* Philox counter word 3 (distinguishes sketches drawn with one seed) */
+  int32_t partition_T;   /* modes in the partition T of Thm 4.4 (bit n = mode n): 0 or -1 select the
+                            last mode, the only partition this build evaluates; any other mask gives
+                            KR_ENOTIMPL */
+  int32_t deterministic; /* accepted for every value: all paths are deterministic (see above) */
+  int32_t stop_rule;     /* 0: stop when ||step|| <= tol ||x|| ("until convergence" read as a
+                            relative step). 1: the (1+eps)-aware rule: stop once the Lemma 4.2 bound
+                            on the sampled objective's excess after the step,
+                            rho^2 g^T M+ g / (1 - sqrt(eps)) with rho = 2 sqrt(eps) - eps, is at most
+                            theta * eps times the lower bound f~(x) - g^T M+ g / (1 - sqrt(eps)) of
+                            the sampled minimum (the O(log 1/eps) iterations of the proof of
+                            Thm 4.5); the relative-step rule stays in force as a backstop. Applies to
+                            kron_regress / kron_ridge / kron_ridge_batched and the core steps of
+                            tucker_als_sweep. */
+  double theta;          /* fraction of eps of stop_rule 1; <= 0 selects 0.01 */
 } kr_opts;
 
 /* Host-side report filled by the solvers (may be NULL). */
@@ -90,7 +112,8 @@ typedef struct {
   int32_t iters;             /* Richardson iterations taken (last problem / last step) */
   int32_t converged;         /* 1: ||step|| <= tol ||x||; 2: stalled at the FP32 rounding floor
                                 (no new minimum step for 8 iterations, smallest relative step
-                                within 100 tol); 0: not converged */
+                                within 100 tol); 3: the (1+eps)-aware rule held (stop_rule 1);
+                                0: not converged */
   int64_t s;                 /* draws */
   int64_t distinct;          /* distinct sampled rows */
   double obj_sampled;        /* ||S(Kx - b)||^2 + lambda ||x||^2 at the returned x, FP64 accumulation */
@@ -102,8 +125,10 @@ typedef struct {
 
 /* Create a context bound to the current CUDA device and the given stream
  * (cudaStream_t, may be NULL for the legacy default stream). The context owns its
- * workspace, which grows on demand and is freed by kr_destroy. */
-KR_API kr_status kr_create(kr_ctx** ctx, void* cuda_stream);
+ * workspace. workspace_bytes > 0 reserves that much device memory now (KR_ENOMEM if it
+ * cannot); 0 reserves nothing. Either way the workspace grows on demand when a call
+ * needs more, and kr_destroy frees it. */
+KR_API kr_status kr_create(kr_ctx** ctx, void* cuda_stream, size_t workspace_bytes);
 KR_API void kr_destroy(kr_ctx* ctx);
 KR_API kr_status kr_set_stream(kr_ctx* ctx, void* cuda_stream);
 /* Message of the last failed call on this context (static storage, valid until
@@ -171,6 +196,12 @@ KR_API kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value);
 KR_API kr_status kr_timing_enable(kr_ctx* ctx, int32_t on);
 KR_API kr_status kr_timing_read(kr_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
 KR_API kr_status kr_timing_reset(kr_ctx* ctx);
+
+/* The library's default sample count (Alg. 2's s with the experiments' scaled constant):
+ * s = ceil(c R ln(R) / eps) with the natural logarithm, at least 1 (1 when R <= 1); c <= 0
+ * selects 4. The solvers use it when kr_opts.num_samples is 0 (with R = prod R_n, or
+ * prod_{m != n} R_m for an Alg. 3 row). Returns -1 for eps outside (0, 1) or R < 1. */
+KR_API int64_t kron_sample_count(int64_t R, double eps, double c);
 
 /* ---------------------------------------------------------------- a1 + a2 */
 

@@ -347,7 +347,9 @@ def richardson(As, b_s, sample, lam, eps, tol=1e-13, max_iter=2000, step=None, x
 
     stop="step": until ||step|| <= tol ||x||. stop="eps": until the bound on the sampled
     objective's excess after the step, rho^2 g^T M+ g / (1 - sqrt(eps)) (eps_stop_bound), is at
-    most theta * eps times the lower bound f~(x) - g^T M+ g / (1 - sqrt(eps)) of its minimum."""
+    most theta * eps times the lower bound f~(x) - g^T M+ g / (1 - sqrt(eps)) of its minimum; the
+    relative-step test stays in force there too, so a problem whose sampled minimum is zero
+    (where that lower bound never turns positive) still stops."""
     R = int(np.prod([A.shape[1] for A in As]))
     P = KronPreconditioner(As, lam)
     alpha = (1.0 - math.sqrt(eps)) if step is None else step
@@ -364,10 +366,9 @@ def richardson(As, b_s, sample, lam, eps, tol=1e-13, max_iter=2000, step=None, x
         x = x - d
         if history is not None:
             history.append(x.copy())
-        if stop == "eps":
-            if rho2 * q / c1 <= theta * eps * max(floor, 0.0):
-                break
-        elif np.linalg.norm(d) <= tol * max(np.linalg.norm(x), 1e-300):
+        if stop == "eps" and rho2 * q / c1 <= theta * eps * max(floor, 0.0):
+            break
+        if np.linalg.norm(d) <= tol * max(np.linalg.norm(x), 1e-300):
             break
     return x, it
 

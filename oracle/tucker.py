@@ -146,10 +146,9 @@ def row_richardson(As_other, Gn, b_s, sample, lam, eps, w, P=None, tol=1e-13, ma
             floor = row_objective(As_other, Gn, Gp, b_s, sample, z, lam, w) - q / c1
         d = alpha * pg
         z = z - d
-        if stop == "eps":
-            if rho2 * q / c1 <= theta * eps * max(floor, 0.0):
-                break
-        elif np.linalg.norm(d) <= tol * max(np.linalg.norm(z), 1e-300):
+        if stop == "eps" and rho2 * q / c1 <= theta * eps * max(floor, 0.0):
+            break
+        if np.linalg.norm(d) <= tol * max(np.linalg.norm(z), 1e-300):
             break
     return z, Gp.T @ z, it  # z, a_i (= (G^T)^+ z = z^T G+), iterations
 

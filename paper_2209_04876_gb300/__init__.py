@@ -22,7 +22,7 @@ KERNEL_KINDS = {"resid": 0, "modeprod": 1, "sample": 2, "scatter": 3, "dedup": 4
                 "slab": 7}
 OPT_SLAB_PASS, OPT_SLAB_TILE_ENTRIES, OPT_DEVICE_LOOP, OPT_BATCH_WORKERS, OPT_GROUPING, OPT_HOST_GATHER = 1, 2, 3, 4, 5, 6
 EXPORTED = ["kr_create", "kr_destroy", "kr_set_stream", "kr_last_error", "kr_launch_count", "kr_timing_enable",
-            "kr_timing_read", "kr_timing_reset", "kr_set_option", "kron_leverage",
+            "kr_timing_read", "kr_timing_reset", "kr_set_option", "kron_sample_count", "kron_leverage",
             "kron_sample", "kron_sample_noalloc", "kron_sketch", "kron_sketch_distinct", "kron_sketch_export", "kron_sketch_residual",
             "kron_sketch_free", "kron_matmul", "kron_precond", "kron_objective", "kron_regress", "kron_ridge",
             "kron_ridge_batched", "tucker_factor_update", "tucker_als_sweep"]
@@ -44,7 +44,9 @@ class KrOpts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("delta", ctypes.c_double), ("lam", ctypes.c_double),
                 ("sample_scale", ctypes.c_double), ("num_samples", ctypes.c_int64), ("max_iter", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("step", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("host_io", ctypes.c_int32), ("seed", ctypes.c_uint64), ("call_id", ctypes.c_uint64)]
+                ("host_io", ctypes.c_int32), ("seed", ctypes.c_uint64), ("call_id", ctypes.c_uint64),
+                ("partition_T", ctypes.c_int32), ("deterministic", ctypes.c_int32), ("stop_rule", ctypes.c_int32),
+                ("theta", ctypes.c_double)]
 
 
 class KrReport(ctypes.Structure):
@@ -54,7 +56,8 @@ class KrReport(ctypes.Structure):
 
     def as_dict(self):
         names = ["leverage", "sample_group_gather", "unused", "init", "iterate", "final_check", "copies", "total"]
-        return dict(iters=self.iters, converged=bool(self.converged), s=self.s, distinct=self.distinct,
+        return dict(iters=self.iters, converged=bool(self.converged), stop=int(self.converged), s=self.s,
+                    distinct=self.distinct,
                     obj_sampled=self.obj_sampled, rel_update=self.rel_update,
                     t_ms={k: float(v) for k, v in zip(names, self.t_ms)})
 
@@ -74,7 +77,8 @@ def lib():
         vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
         P = ctypes.POINTER
         sig = {
-            "kr_create": (i32, [P(vp), vp]),
+            "kr_create": (i32, [P(vp), vp, ctypes.c_size_t]),
+            "kron_sample_count": (i64, [i64, dbl, dbl]),
             "kr_destroy": (None, [vp]),
             "kr_set_stream": (i32, [vp, vp]),
             "kr_last_error": (ctypes.c_char_p, [vp]),
@@ -115,7 +119,7 @@ def context(device=None):
     if dev not in _ctx:
         with torch.cuda.device(dev):
             h = ctypes.c_void_p()
-            st = L.kr_create(ctypes.byref(h), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+            st = L.kr_create(ctypes.byref(h), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), 0)
             if st != 0:
                 raise KronError(st, "kr_create failed")
             _ctx[dev] = h
@@ -204,20 +208,25 @@ def _ptr_array(ts):
     return arr
 
 
+STOP_STEP, STOP_EPS = 0, 1
+
+
 def _opts(eps=0.1, lam=0.0, seed=0, call_id=0, sample_scale=4.0, num_samples=0, max_iter=100, tol=1e-7, step=0.0,
-          precision=0, host_io=False, delta=0.01):
+          precision=0, host_io=False, delta=0.01, partition_T=0, deterministic=1, stop_rule=STOP_STEP, theta=0.0):
     o = KrOpts()
     o.eps, o.delta, o.lam, o.sample_scale = eps, delta, lam, sample_scale
     o.num_samples, o.max_iter, o.tol, o.step = int(num_samples), int(max_iter), tol, step
     o.precision, o.host_io, o.seed, o.call_id = int(precision), int(bool(host_io)), int(seed), int(call_id)
+    o.partition_T, o.deterministic, o.stop_rule, o.theta = int(partition_T), int(deterministic), int(stop_rule), theta
     return o
 
 
-def sample_count(R, eps, c=4.0):
-    """s = ceil(c R ln R / eps) (the library's default rule, at least 1)."""
-    if R <= 1:
-        return 1
-    return max(1, int(math.ceil(c * R * math.log(R) / eps)))
+def kron_sample_count(R, eps, c=4.0):
+    """The library's default sample count for R unknowns (kron_sample_count in kron.h)."""
+    v = int(lib().kron_sample_count(int(R), float(eps), float(c)))
+    if v < 0:
+        raise ValueError("kron_sample_count: eps must lie in (0, 1) and R >= 1")
+    return v
 
 
 # ---------------------------------------------------------------------------- entry points
@@ -249,19 +258,42 @@ def kron_sample(cdfs, probs, s, seed, call_id, row=0, want_idx=True, want_w=True
     return idx, w
 
 
+def _require(t, name, dtype, numel, dev):
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda or t.device != dev \
+            or not t.is_contiguous() or t.numel() < numel:
+        raise ValueError("%s must be a contiguous %s tensor on %s with at least %d elements" % (name, dtype, dev, numel))
+
+
 def kron_sample_noalloc(cdfs, probs, s, seed, call_id, row=0, idx=None, w=None):
     """kron_sample for callers that cannot allocate device memory: the outputs are the
     caller's (pass preallocated `idx` (s x N int32) / `w` (s float32) tensors, or let this
     wrapper create them before the call), and the library's only scratch is a fixed
-    static device array (sum of table sizes <= 16384 rows)."""
-    h = context()
+    static device array (sum of table sizes <= 16384 rows). The kernel writes through the
+    raw pointers, so every tensor is checked first (dtype, device, contiguity, size)."""
     N = len(cdfs)
-    I = (ctypes.c_int64 * N)(*[c.shape[0] for c in cdfs])
+    if N < 1:
+        raise ValueError("kron_sample_noalloc: at least one table")
     dev = cdfs[0].device
+    for m, c in enumerate(cdfs):
+        _require(c, "cdfs[%d]" % m, torch.float64, c.shape[0] if c.dim() == 1 else -1, dev)
+        if c.dim() != 1:
+            raise ValueError("cdfs[%d] must be one-dimensional" % m)
+    if probs is not None:
+        if len(probs) != N:
+            raise ValueError("kron_sample_noalloc: one probability table per CDF")
+        for m, (p, c) in enumerate(zip(probs, cdfs)):
+            _require(p, "probs[%d]" % m, torch.float64, c.shape[0], dev)
+    h = context()
+    I = (ctypes.c_int64 * N)(*[c.shape[0] for c in cdfs])
     if idx is None:
         idx = torch.empty((s, N), dtype=torch.int32, device=dev)
     if w is None and probs is not None:
         w = torch.empty(s, dtype=torch.float32, device=dev)
+    _require(idx, "idx", torch.int32, int(s) * N, dev)
+    if w is not None:
+        if probs is None:
+            raise ValueError("kron_sample_noalloc: weights need the probability tables")
+        _require(w, "w", torch.float32, int(s), dev)
     st = lib().kron_sample_noalloc(h, N, I, _ptr_array(cdfs), _ptr_array(probs) if probs is not None else None,
                                    int(s), int(seed), int(call_id), int(row), _ptr(idx), _ptr(w))
     _check(st, h)

@@ -1,4 +1,5 @@
 // Context, errors, workspace and argument validation of libkron.
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 
@@ -34,7 +35,17 @@ kr_status kr_func_smem(kr_ctx* ctx, const void* func, size_t bytes) {
   return KR_OK;
 }
 
-extern "C" kr_status kr_create(kr_ctx** out, void* stream) {
+int64_t kr_sample_count(int64_t R, double eps, double c) {
+  if (!(eps > 0.0 && eps < 1.0) || R < 1) return -1;
+  if (!(c > 0.0)) c = 4.0;
+  if (R <= 1) return 1;
+  const double v = ceil(c * (double)R * log((double)R) / eps);
+  return v < 1.0 ? 1 : (int64_t)v;
+}
+
+extern "C" int64_t kron_sample_count(int64_t R, double eps, double c) { return kr_sample_count(R, eps, c); }
+
+extern "C" kr_status kr_create(kr_ctx** out, void* stream, size_t workspace_bytes) {
   if (!out) return KR_EINVAL;
   *out = nullptr;
   kr_ctx* ctx = new kr_ctx();
@@ -50,6 +61,10 @@ extern "C" kr_status kr_create(kr_ctx** out, void* stream) {
     return e == cudaErrorMemoryAllocation ? KR_ENOMEM : KR_ECUDA;
   }
   ctx->stream = (cudaStream_t)stream;
+  if (workspace_bytes > 0 && kr_ws_reserve(ctx, workspace_bytes) != KR_OK) {
+    kr_destroy(ctx);
+    return KR_ENOMEM;
+  }
   *out = ctx;
   return KR_OK;
 }

@@ -195,6 +195,8 @@ struct Modes {
 };
 
 kr_status kr_check_factors(kr_ctx* ctx, const kr_factors* f, Modes* m);
+// s = ceil(c R ln R / eps), at least 1 (c <= 0 selects 4); -1 for eps outside (0, 1) or R < 1.
+int64_t kr_sample_count(int64_t R, double eps, double c);
 int64_t kr_prod_I(const Modes& m);
 int64_t kr_prod_R(const Modes& m);
 

@@ -1456,11 +1456,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
 namespace {
 
 int64_t default_samples(const kr_opts* o, int64_t R) {
-  if (o->num_samples > 0) return o->num_samples;
-  double c = o->sample_scale > 0 ? o->sample_scale : 4.0;
-  if (R <= 1) return 1;
-  double v = ceil(c * (double)R * log((double)R) / o->eps);
-  return v < 1 ? 1 : (int64_t)v;
+  return o->num_samples > 0 ? o->num_samples : kr_sample_count(R, o->eps, o->sample_scale);
 }
 
 kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr_opts* o, float* x, kr_report* rep,
@@ -1471,6 +1467,15 @@ kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr
   KR_TRY(kr_check_factors(ctx, f, &m));
   if (!(o->eps > 0.0 && o->eps < 1.0)) return kr_fail(ctx, KR_EINVAL, "solver: eps=%g outside (0,1)", o->eps);
   if (o->precision != 0) return kr_fail(ctx, KR_ENOTIMPL, "solver: precision=%d (only 0, FP32, is built)", o->precision);
+  if (o->partition_T != 0 && o->partition_T != -1 && o->partition_T != (1 << (m.N - 1)))
+    return kr_fail(ctx, KR_ENOTIMPL, "solver: partition_T=0x%x (only the last mode, 0x%x, is built)", o->partition_T,
+                   1 << (m.N - 1));
+  {
+    int cur = -1;
+    KR_CUDA(ctx, cudaGetDevice(&cur));
+    if (cur != ctx->device)
+      return kr_fail(ctx, KR_EINVAL, "solver: current device %d is not the context's device %d", cur, ctx->device);
+  }
   if (!(lambda >= 0.0) || !isfinite(lambda)) return kr_fail(ctx, KR_EINVAL, "solver: lambda must be finite and >= 0");
   SolveCfg cfg;
   cfg.lambda = lambda;
@@ -1484,10 +1489,21 @@ kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr
   if (!o->host_io) return kr_solve_device(ctx, m, b, cfg, o->seed, o->call_id, x, rep);
   // host buffers: copy factors and b in, x out, inside the call
   cudaEvent_t e0 = ctx->ev[6], e1 = ctx->ev[7];
+  // b in page-locked host memory is mapped into the device's address space: the gather reads
+  // the s sampled entries in place (Alg. 2 reads b only at the sampled rows) instead of
+  // copying all prod I entries, and no device copy of b is needed
+  const float* b_mapped = nullptr;
+  if (ctx->host_gather) {
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, b) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+      b_mapped = static_cast<const float*>(pa.devicePointer);
+    else
+      cudaGetLastError();  // not page-locked: copy it
+  }
   size_t bytes = 0;
   for (int n = 0; n < m.N; ++n) bytes += ((size_t)m.I[n] * m.R[n] * 4 + 255) & ~size_t(255);
-  bytes += ((size_t)I * 4 + 255) & ~size_t(255);
   bytes += ((size_t)R * 4 + 255) & ~size_t(255);
+  if (!b_mapped) bytes += ((size_t)I * 4 + 255) & ~size_t(255);
   KR_TRY(kr_io_reserve(ctx, bytes));
   char* dev = ctx->io;
   KR_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
@@ -1498,19 +1514,8 @@ kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr
     KR_CUDA(ctx, cudaMemcpyAsync(a, m.A[n], sizeof(float) * m.I[n] * m.R[n], cudaMemcpyHostToDevice, ctx->stream));
     md.A[n] = a;
   }
-  float* bd = cv.take<float>(I);
   float* xd = cv.take<float>(R);
-  // b in page-locked host memory is mapped into the device's address space: the gather reads
-  // the s sampled entries in place (Alg. 2 reads b only at the sampled rows) instead of
-  // copying all prod I entries
-  const float* b_mapped = nullptr;
-  if (ctx->host_gather) {
-    cudaPointerAttributes pa;
-    if (cudaPointerGetAttributes(&pa, b) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
-      b_mapped = static_cast<const float*>(pa.devicePointer);
-    else
-      cudaGetLastError();  // not page-locked: copy it
-  }
+  float* bd = b_mapped ? nullptr : cv.take<float>(I);
   if (b_mapped) {
     kr_status st = kr_solve_device(ctx, md, b_mapped, cfg, o->seed, o->call_id, xd, rep);
     if (st == KR_OK || st == KR_ENOTCONV) {
@@ -1578,7 +1583,7 @@ static kr_status kr_workers_reserve(kr_ctx* ctx, int n) {
     cudaStream_t s = nullptr;
     KR_CUDA(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     kr_ctx* w = nullptr;
-    const kr_status st = kr_create(&w, s);
+    const kr_status st = kr_create(&w, s, 0);
     if (st != KR_OK) {
       cudaStreamDestroy(s);
       return kr_fail(ctx, st, "kron_ridge_batched: worker context creation failed");
@@ -1626,9 +1631,16 @@ extern "C" kr_status kron_ridge_batched(kr_ctx* ctx, int32_t nprob, const kr_fac
   for (int i = 0; i < W; ++i) l0[i] = ctx->workers[i]->launches;
   auto run = [&](int wi) {
     kr_ctx* w = ctx->workers[wi];
+    // a new host thread starts on device 0: make the context's device current first
+    const cudaError_t de = cudaSetDevice(ctx->device);
     for (;;) {
       const int p = next.fetch_add(1);
       if (p >= nprob) break;
+      if (de != cudaSuccess) {
+        st[p] = KR_ECUDA;
+        msg[p] = std::string("kron_ridge_batched: cudaSetDevice failed in a worker: ") + cudaGetErrorString(de);
+        continue;
+      }
       kr_opts o = *opts;
       o.call_id = opts->call_id + (uint64_t)p;
       st[p] = solve_entry(w, &probs[p], b[p], &o, x[p], reports ? &reports[p] : nullptr, opts->lambda);

@@ -940,13 +940,7 @@ SolveCfg cfg_from(const kr_opts* o, int64_t Rsz) {
   c.alpha = o->step > 0 ? o->step : 1.0 - sqrt(o->eps);
   c.tol = o->tol > 0 ? o->tol : 1e-7;
   c.max_iter = o->max_iter > 0 ? o->max_iter : 100;
-  if (o->num_samples > 0) {
-    c.s = o->num_samples;
-  } else {
-    const double sc = o->sample_scale > 0 ? o->sample_scale : 4.0;
-    c.s = Rsz <= 1 ? 1 : (int64_t)ceil(sc * (double)Rsz * log((double)Rsz) / o->eps);
-    if (c.s < 1) c.s = 1;
-  }
+  c.s = o->num_samples > 0 ? o->num_samples : kr_sample_count(Rsz, o->eps, o->sample_scale);
   return c;
 }
 

@@ -351,3 +351,59 @@ def test_eps_stopping_rule_certifies_early(dist, noise):
     f1, f2 = ko.objective(As, b, x1, 0.0), ko.objective(As, b, x2, 0.0)
     assert f1 <= (1 + eps) * opt
     assert f1 <= f2 * (1 + 0.1 * eps)
+
+
+def test_sample_weights_hand_enumeration():
+    """omega_j = c_j / (s prod_n p_n(i_n)) on a sample written out by hand: I = (3, 2),
+    p_1 = (1/2, 1/4, 1/4), p_2 = (1/5, 4/5), draws (0,1), (0,1), (2,0), (1,1), so s = 4 and
+    the merged rows are key 1 (drawn twice), key 3 and key 4 (once each)."""
+    probs = [np.array([0.5, 0.25, 0.25]), np.array([0.2, 0.8])]
+    idx = np.array([[0, 1], [0, 1], [2, 0], [1, 1]])
+    keys, counts = ko.group_samples(idx, [3, 2])
+    assert keys.tolist() == [1, 3, 4] and counts.tolist() == [2, 1, 1]
+    om = ko.sample_weights(keys, counts, probs, [3, 2], 4)
+    # 2 / (4 * 1/2 * 4/5) = 1.25;  1 / (4 * 1/4 * 4/5) = 1.25;  1 / (4 * 1/4 * 1/5) = 5
+    np.testing.assert_allclose(om, [1.25, 1.25, 5.0], rtol=1e-15)
+
+
+def test_sample_weights_scale_invariant():
+    """For any sample, sum_j omega_j p(key_j) = sum_j c_j / s = 1 exactly (a global scale
+    error in omega, which the lambda = 0 minimiser would not show, fails this), and
+    E[S^T S] = I: the mean of omega over many independent samples, per row, is 1."""
+    rng = np.random.default_rng(5)
+    I = [7, 5, 3]
+    levs = [rng.uniform(0.1, 1.0, size=i) for i in I]
+    probs = [ko.probabilities(l) for l in levs]
+    cdfs = [ko.cdf_table(l) for l in levs]
+    s = 5000
+    idx = ko.sample_draws(cdfs, s, 3, 4)
+    keys, counts = ko.group_samples(idx, I)
+    om = ko.sample_weights(keys, counts, probs, I, s)
+    sub = ko.unravel(keys, I)
+    p = probs[0][sub[:, 0]] * probs[1][sub[:, 1]] * probs[2][sub[:, 2]]
+    assert abs(float(np.sum(om * p)) - 1.0) < 1e-12
+    tot = np.zeros(int(np.prod(I)))
+    reps = 400
+    for r in range(reps):
+        idx = ko.sample_draws(cdfs, 200, 11, r)
+        k, c = ko.group_samples(idx, I)
+        np.add.at(tot, k, ko.sample_weights(k, c, probs, I, 200))
+    mean = tot / reps
+    # each row's mean weight is 1 +- a few standard errors (sd of omega ~ 1/sqrt(s p))
+    pall = np.einsum("i,j,k->ijk", *probs).reshape(-1)
+    se = np.sqrt((1.0 / (200 * pall)) / reps)
+    assert np.all(np.abs(mean - 1.0) <= 5 * se + 1e-12)
+
+
+def test_eps_rule_stops_on_a_zero_residual_problem():
+    """With b = K x_true exactly, the sampled minimum is 0 and the eps rule's lower bound never
+    turns positive; the relative-step backstop ends the loop well before max_iter with
+    x = x_true."""
+    prob = kron_problem([20, 16, 12], [3, 3, 2], dist="gauss", seed=8)
+    As, xt = prob["As"], prob["x_true"]
+    b = ko.kron_matvec(As, xt)
+    eps = 0.1
+    smp = ko.draw_sample(As, ko.sample_count(18, eps), 1, 2)
+    x, it = ko.richardson(As, b[smp.keys], smp, 0.0, eps, stop="eps", tol=1e-12, max_iter=2000)
+    assert it < 200
+    assert np.linalg.norm(x - xt) <= 1e-10 * np.linalg.norm(xt)
