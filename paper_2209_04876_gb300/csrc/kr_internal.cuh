@@ -324,7 +324,8 @@ struct kr_tiles {
   // backward fold of the last prefix mode (k_tile_reduce): groups p' of Iq slabs, Rq rows
   int64_t Pq = 1;
   int Iq = 1, Rq = 1, nc = 1;
-  float* zred = nullptr;         // nc x Pq x Rq x R2 x RT chunk partials (nc > 1)
+  int nout = 1;                  // weight matrices of the fold (2: a second output, see kr_tile_reduce)
+  float* zred = nullptr;         // nc x nout x Pq x Rq x R2 x RT chunk partials (nc > 1)
   uint32_t* meta = nullptr;      // [0] tiles, [1] non-empty cells, [2] work counter (zero between passes)
   float* zpart = nullptr;        // ntmax x R2 x RT: contributions of tiles of multi-tile slabs
   double* objpart = nullptr;     // ntmax: per-tile sampled objective (FP64; zero past the last)
@@ -343,11 +344,16 @@ kr_status kr_tiles_build(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, Carve& 
 // One fused pass from X1 (P x R2 x RT): every tile's contribution to its slab's
 // Z[p] = sum_i A(N-2)[i]^T W[p, i] goes to tl->zpart (see kr_slab.cu); with want_obj the
 // per-tile objective partials go to tl->objpart (tl->ntmax doubles).
+// rearm: zero the tile counter first (needed when no tile reduction followed the last pass).
 kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const float* A2, const float* AT,
-                       const float* X1, bool want_obj);
+                       const float* X1, bool want_obj, bool rearm);
 // W[p', r, :] = sum over the tiles of the slabs p' * Iq + i of Aq[i, r] zpart[t, :]
-// (Aq = A(N-3) for N >= 3, nullptr for N = 2): Pq x Rq x R2 x RT floats.
-kr_status kr_tile_reduce(kr_ctx* ctx, kr_tiles* tl, const float* Aq, float* W);
+// (Aq = A(N-3) for N >= 3, nullptr for N = 2): Pq x Rq x R2 x RT floats. With Aq2 the same
+// sum with the weights Aq2 goes to W2 (one pass over the tiles for both). With opart the
+// tiles' objective partials of the pass (tl->objpart, written by a want_obj pass) are summed
+// in tile order per chunk: opart[c * Pq + p'] (tl->nc * tl->Pq doubles).
+kr_status kr_tile_reduce(kr_ctx* ctx, kr_tiles* tl, const float* Aq, float* W, double* opart = nullptr,
+                         const float* Aq2 = nullptr, float* W2 = nullptr);
 
 // ------------------------------------------------------------------ solvers
 
@@ -355,9 +361,11 @@ struct SolveCfg {
   double lambda, eps, alpha, tol;
   int max_iter;
   int64_t s;
+  int stop_rule = 0;     // 1: the (1+eps)-aware rule (kr_opts.stop_rule)
+  double theta = 0.01;   // its fraction of eps
 };
 
-enum StepCheck { STEP_CONTINUE, STEP_CONVERGED, STEP_FLOOR, STEP_DIVERGED, STEP_NONFINITE, STEP_MAXITER };
+enum StepCheck { STEP_CONTINUE, STEP_CONVERGED, STEP_FLOOR, STEP_DIVERGED, STEP_NONFINITE, STEP_MAXITER, STEP_EPS };
 // Runs the steps of a Richardson loop as one CUDA graph: a conditional WHILE node whose
 // body is one captured step, body(hnd, 1); the body's last kernel clears the condition.
 // Launches the graph once on ctx->stream, waits for it to end, and returns the launches of one

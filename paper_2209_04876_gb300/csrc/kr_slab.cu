@@ -601,21 +601,29 @@ struct TileReduceSmem {
   int per, rq4, tb;
   size_t bytes;
 };
-TileReduceSmem tile_reduce_smem(int per, int Rq) {
+TileReduceSmem tile_reduce_smem(int per, int Rq, int nout) {
   TileReduceSmem L;
   L.per = per;
   L.rq4 = (Rq + 3) & ~3;
-  const size_t fixed = (68 + (size_t)per * TR_QP + (size_t)per * L.rq4) * sizeof(float);
+  const size_t fixed = (68 + (size_t)per * TR_QP + (size_t)nout * per * L.rq4) * sizeof(float);
   const size_t budget = 48 * 1024;
   int tb = fixed < budget ? (int)((budget - fixed) / (TR_QP * sizeof(float))) : 0;
   L.tb = tb > 256 ? 256 : (tb < 16 ? 16 : tb);
   L.bytes = fixed + (size_t)L.tb * TR_QP * sizeof(float);
   return L;
 }
+// TWO: a second weight matrix Aq2 in the same pass (its sums to part2). With opart, block
+// x = 0 of every (chunk, group) also adds the objective partials of the chunk's tiles in
+// tile order: opart[c * Pq + pq].
+template <bool TWO>
 __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict__ tstart, int Iq,
                                                       const float* __restrict__ zpart, const float* __restrict__ Aq,
-                                                      int Rq, int zn, int nc, int64_t Pq, float* __restrict__ part,
-                                                      uint32_t* __restrict__ counter, int TB) {
+                                                      const float* __restrict__ Aq2, int Rq, int zn, int nc,
+                                                      int64_t Pq, float* __restrict__ part,
+                                                      float* __restrict__ part2, int64_t cstride,
+                                                      uint32_t* __restrict__ counter, int TB,
+                                                      const double* __restrict__ objpart,
+                                                      double* __restrict__ opart) {
   extern __shared__ float4 tr_smem[];
   const int64_t pq = blockIdx.z;
   const int c = blockIdx.y;
@@ -626,11 +634,13 @@ __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict
   uint32_t* s_ts = reinterpret_cast<uint32_t*>(tr_smem);
   float* s_z = reinterpret_cast<float*>(tr_smem) + 68;  // [per][TR_QP]
   float* s_a = s_z + (size_t)per * TR_QP;                // [per][Rq4]
-  float* s_t = s_a + (size_t)per * Rq4;                  // [TB][TR_QP]
+  float* s_a2 = s_a + (size_t)per * Rq4;                 // [per][Rq4] (TWO)
+  float* s_t = s_a + (size_t)(TWO ? 2 : 1) * per * Rq4;  // [TB][TR_QP]
   for (int k = threadIdx.x; k <= S; k += blockDim.x) s_ts[k] = tstart[pq * Iq + i0 + k];
   for (int e = threadIdx.x; e < S * Rq4; e += blockDim.x) {
     const int i = e / Rq4, r = e - i * Rq4;
     s_a[e] = r < Rq ? (Aq ? __ldg(Aq + (size_t)(i0 + i) * Rq + r) : 1.f) : 0.f;
+    if (TWO) s_a2[e] = r < Rq ? __ldg(Aq2 + (size_t)(i0 + i) * Rq + r) : 0.f;
   }
   for (int e = threadIdx.x; e < S * TR_QP; e += blockDim.x) s_z[e] = 0.f;
   kr_pdl_trigger();
@@ -672,12 +682,14 @@ __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict
   }
   // part[c][pq][r][q] = sum_i Aq[i0 + i, r] Z[i, q] in slab order; a thread forms 4 ranks x
   // 2 columns (one 16-byte load of Aq's row and one 8-byte load of Z per slab)
-  float* out = part + ((size_t)c * Pq + pq) * Rq * zn;
+  float* out = part + (size_t)c * cstride + (size_t)pq * Rq * zn;
+  float* out2 = TWO ? part2 + (size_t)c * cstride + (size_t)pq * Rq * zn : nullptr;
   const int R4 = (Rq + 3) >> 2;
   for (int e = threadIdx.x; e < R4 * (TR_QP / 2); e += blockDim.x) {
     const int r4 = e / (TR_QP / 2), q2 = e - r4 * (TR_QP / 2), r0 = 4 * r4, qq = 2 * q2, q = qb + qq;
     if (q >= zn) continue;
     float acc[4][2] = {};
+    float acc2[4][2] = {};
     for (int i = 0; i < S; ++i) {
       const float4 av = *reinterpret_cast<const float4*>(s_a + i * Rq4 + r0);
       const float2 zv = *reinterpret_cast<const float2*>(s_z + i * TR_QP + qq);
@@ -689,31 +701,60 @@ __global__ void __launch_bounds__(256) k_tile_reduce1(const uint32_t* __restrict
       acc[2][1] = fmaf(av.z, zv.y, acc[2][1]);
       acc[3][0] = fmaf(av.w, zv.x, acc[3][0]);
       acc[3][1] = fmaf(av.w, zv.y, acc[3][1]);
+      if (TWO) {
+        const float4 bv = *reinterpret_cast<const float4*>(s_a2 + i * Rq4 + r0);
+        acc2[0][0] = fmaf(bv.x, zv.x, acc2[0][0]);
+        acc2[0][1] = fmaf(bv.x, zv.y, acc2[0][1]);
+        acc2[1][0] = fmaf(bv.y, zv.x, acc2[1][0]);
+        acc2[1][1] = fmaf(bv.y, zv.y, acc2[1][1]);
+        acc2[2][0] = fmaf(bv.z, zv.x, acc2[2][0]);
+        acc2[2][1] = fmaf(bv.z, zv.y, acc2[2][1]);
+        acc2[3][0] = fmaf(bv.w, zv.x, acc2[3][0]);
+        acc2[3][1] = fmaf(bv.w, zv.y, acc2[3][1]);
+      }
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (r0 + j >= Rq) break;
       out[(size_t)(r0 + j) * zn + q] = acc[j][0];
       if (q + 1 < zn) out[(size_t)(r0 + j) * zn + q + 1] = acc[j][1];
+      if (TWO) {
+        out2[(size_t)(r0 + j) * zn + q] = acc2[j][0];
+        if (q + 1 < zn) out2[(size_t)(r0 + j) * zn + q + 1] = acc2[j][1];
+      }
     }
+  }
+  if (opart && blockIdx.x == 0) {  // the chunk's tiles' objective: fixed strides, then a fixed tree
+    __shared__ double s_o[256];
+    double acc = 0.0;
+    for (uint32_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) acc += __ldcg(objpart + t);
+    s_o[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+      if ((int)threadIdx.x < off) s_o[threadIdx.x] += s_o[threadIdx.x + off];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) opart[(size_t)c * Pq + pq] = s_o[0];
   }
 }
 
 // W = sum over the nc chunks of part, in chunk order; four columns per thread when the
-// length allows, the loads of a batch of chunks in flight together.
-__global__ void __launch_bounds__(128) k_tile_reduce2(const float* __restrict__ part, int nc, int64_t total,
-                                                      float* __restrict__ W) {
+// length allows, the loads of a batch of chunks in flight together. Chunk c starts at
+// part + c * cstride; with W2 each chunk holds two outputs back to back (W's total entries,
+// then W2's).
+__global__ void __launch_bounds__(128) k_tile_reduce2(const float* __restrict__ part, int nc, int64_t cstride,
+                                                      int64_t total, float* __restrict__ W, float* __restrict__ W2) {
   kr_pdl_trigger();
   kr_pdl_wait();
   if ((total & 3) == 0) {
-    const int64_t n4 = total >> 2;
+    const int64_t n4 = total >> 2, all4 = W2 ? 2 * n4 : n4, cs4 = cstride >> 2;
     const float4* p4 = reinterpret_cast<const float4*>(part);
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < all4; e += (int64_t)gridDim.x * blockDim.x) {
       float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
       for (int c0 = 0; c0 < nc; c0 += 16) {
         float4 v[16];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = c0 + c < nc ? __ldg(p4 + (size_t)(c0 + c) * n4 + e) : s;
+        for (int c = 0; c < 16; ++c) v[c] = c0 + c < nc ? __ldg(p4 + (size_t)(c0 + c) * cs4 + e) : s;
 #pragma unroll
         for (int c = 0; c < 16; ++c)
           if (c0 + c < nc) {
@@ -727,21 +768,24 @@ __global__ void __launch_bounds__(128) k_tile_reduce2(const float* __restrict__ 
             }
           }
       }
-      reinterpret_cast<float4*>(W)[e] = s;
+      if (e < n4) reinterpret_cast<float4*>(W)[e] = s;
+      else reinterpret_cast<float4*>(W2)[e - n4] = s;
     }
     return;
   }
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t all = W2 ? 2 * total : total;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < all; e += (int64_t)gridDim.x * blockDim.x) {
     float s = 0.f;
     for (int c0 = 0; c0 < nc; c0 += 16) {  // loads of a batch in flight together, added in order
       float v[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) v[c] = c0 + c < nc ? __ldg(part + (size_t)(c0 + c) * total + e) : 0.f;
+      for (int c = 0; c < 16; ++c) v[c] = c0 + c < nc ? __ldg(part + (size_t)(c0 + c) * cstride + e) : 0.f;
 #pragma unroll
       for (int c = 0; c < 16; ++c)
         if (c0 + c < nc) s = (c0 + c == 0) ? v[c] : s + v[c];
     }
-    W[e] = s;
+    if (e < total) W[e] = s;
+    else W2[e - total] = s;
   }
 }
 
@@ -963,7 +1007,7 @@ void kr_tiles_own_need(const kr_tiles* tl, int64_t ncell, Need& nd) {
   nd.add<uint4>(tl->ntmax);
   nd.add<uint2>(tl->P);
   nd.add<uint32_t>(tl->P + 1);
-  nd.add<float>(tl->nc > 1 ? (size_t)tl->nc * tl->Pq * tl->Rq * tl->R2 * tl->RT : 0);
+  nd.add<float>(tl->nc > 1 ? (size_t)tl->nc * tl->nout * tl->Pq * tl->Rq * tl->R2 * tl->RT : 0);
   nd.add<uint32_t>(4);
   nd.add<float>((size_t)tl->ntmax * tl->R2 * tl->RT);
   nd.add<double>(tl->ntmax);
@@ -977,7 +1021,7 @@ void kr_tiles_layout(kr_tiles* tl, int64_t ncell, Carve& cv) {
   tl->tsort = cv.take<uint4>(tl->ntmax);
   tl->slab = cv.take<uint2>(tl->P);
   tl->tstart = cv.take<uint32_t>(tl->P + 1);
-  tl->zred = cv.take<float>(tl->nc > 1 ? (size_t)tl->nc * tl->Pq * tl->Rq * tl->R2 * tl->RT : 0);
+  tl->zred = cv.take<float>(tl->nc > 1 ? (size_t)tl->nc * tl->nout * tl->Pq * tl->Rq * tl->R2 * tl->RT : 0);
   tl->meta = cv.take<uint32_t>(4);
   tl->zpart = cv.take<float>((size_t)tl->ntmax * tl->R2 * tl->RT);
   tl->objpart = cv.take<double>(tl->ntmax);
@@ -1033,7 +1077,7 @@ kr_status kr_tiles_build(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, Carve& 
 }
 
 kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const float* A2, const float* AT,
-                       const float* X1, bool want_obj) {
+                       const float* X1, bool want_obj, bool rearm) {
   SlabLayout L = slab_layout(tl->IT, tl->RT, tl->R2, true);
   if (L.bytes > ctx->smem_optin) L = slab_layout(tl->IT, tl->RT, tl->R2, false);
   if (L.bytes > ctx->smem_optin) return kr_fail(ctx, KR_ENOTIMPL, "slab pass: %zu bytes of shared memory", L.bytes);
@@ -1068,7 +1112,7 @@ kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const flo
   a.o_act = L.o_act;
   a.o_cs = L.o_cs;
   a.o_ctl = L.o_ctl;
-  if (want_obj) KR_CUDA(ctx, cudaMemsetAsync(tl->meta + 2, 0, sizeof(uint32_t), ctx->stream));
+  if (rearm) KR_CUDA(ctx, cudaMemsetAsync(tl->meta + 2, 0, sizeof(uint32_t), ctx->stream));
   kr_status st = L.smem_a ? (want_obj ? launch_slab<true, true>(ctx, L.RTP, a, L.bytes)
                                       : launch_slab<true, false>(ctx, L.RTP, a, L.bytes))
                          : (want_obj ? launch_slab<false, true>(ctx, L.RTP, a, L.bytes)
@@ -1076,17 +1120,31 @@ kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const flo
   return st;
 }
 
-kr_status kr_tile_reduce(kr_ctx* ctx, kr_tiles* tl, const float* Aq, float* W) {
+kr_status kr_tile_reduce(kr_ctx* ctx, kr_tiles* tl, const float* Aq, float* W, double* opart, const float* Aq2,
+                         float* W2) {
   const int zn = tl->R2 * tl->RT;
+  const int nout = Aq2 ? 2 : 1;
+  if (nout > tl->nout) return kr_fail(ctx, KR_EINVAL, "tile reduction: %d outputs, room for %d", nout, tl->nout);
   const dim3 grid((unsigned)((zn + TR_QP - 1) / TR_QP), (unsigned)tl->nc, (unsigned)tl->Pq);
+  const int64_t total = tl->Pq * tl->Rq * zn;
   float* part = tl->nc > 1 ? tl->zred : W;
-  const TileReduceSmem L = tile_reduce_smem((tl->Iq + tl->nc - 1) / tl->nc, tl->Rq);
-  KR_LAUNCH_PDL(ctx, k_tile_reduce1, grid, 256, L.bytes, tl->tstart, tl->Iq, tl->zpart, Aq, tl->Rq, zn, tl->nc, tl->Pq,
-                part, tl->meta + 2, L.tb);
+  float* part2 = tl->nc > 1 ? tl->zred + total : W2;
+  const int64_t cstride = (int64_t)nout * total;
+  const TileReduceSmem L = tile_reduce_smem((tl->Iq + tl->nc - 1) / tl->nc, tl->Rq, nout);
+  if (nout == 2) {
+    KR_TRY(kr_smem_attr(ctx, k_tile_reduce1<true>, L.bytes));
+    KR_LAUNCH_PDL(ctx, k_tile_reduce1<true>, grid, 256, L.bytes, tl->tstart, tl->Iq, tl->zpart, Aq, Aq2, tl->Rq, zn,
+                  tl->nc, tl->Pq, part, part2, cstride, tl->meta + 2, L.tb, (const double*)tl->objpart, opart);
+  } else {
+    KR_TRY(kr_smem_attr(ctx, k_tile_reduce1<false>, L.bytes));
+    KR_LAUNCH_PDL(ctx, k_tile_reduce1<false>, grid, 256, L.bytes, tl->tstart, tl->Iq, tl->zpart, Aq, (const float*)nullptr,
+                  tl->Rq, zn, tl->nc, tl->Pq, part, (float*)nullptr, cstride, tl->meta + 2, L.tb,
+                  (const double*)tl->objpart, opart);
+  }
   if (tl->nc > 1) {
-    const int64_t total = tl->Pq * tl->Rq * zn;
-    const int64_t work = (total & 3) == 0 ? total / 4 : total;
-    KR_LAUNCH_PDL(ctx, k_tile_reduce2, grid_n(ctx, work, 128), 128, 0, tl->zred, tl->nc, total, W);
+    const int64_t work = ((total & 3) == 0 ? total / 4 : total) * nout;
+    KR_LAUNCH_PDL(ctx, k_tile_reduce2, grid_n(ctx, work, 128), 128, 0, (const float*)tl->zred, tl->nc, cstride, total, W,
+                  nout == 2 ? W2 : (float*)nullptr);
   }
   return KR_OK;
 }

@@ -217,56 +217,77 @@ __global__ void k_sub_lambda_x(float* __restrict__ g, const float* __restrict__ 
     g[i] = fmaf(-lambda, x[i], g[i]);
 }
 
-// {||step||^2, ||x||^2, non-finite flag} of the block's elements, written to
-// part[3 * blockIdx.x + 0..2] in FP64. Inside the block the sums are FP32 fixed-order trees
+// {||step||^2, ||x||^2, non-finite flag, g^T step} of the block's elements, written to
+// part[4 * blockIdx.x + 0..3] in FP64. Inside the block the sums are FP32 fixed-order trees
 // (per thread, warp shuffles, then one warp over the warp sums): FP64 arithmetic issues at
 // a small fraction of the FP32 rate on this part, and a stopping-rule norm needs no more
 // than FP32's relative precision (about 1e-6 after the tree). The blocks' partials are
 // added in FP64. Called by all threads of a block of at most 1024 threads, once per kernel.
-__device__ __forceinline__ void step_norms_block(float s1, float s2, float bad, double* __restrict__ part) {
-  __shared__ float red[3][32];
+// The fourth sum, g^T step with g the gradient the step was taken from (lambda term
+// included), gives q = g^T M+ g = g^T step / alpha for the (1+eps)-aware stopping rule; it
+// is zero when the caller passes no gradient.
+constexpr int KR_NPART = 4;
+__device__ __forceinline__ void step_norms_block(float s1, float s2, float bad, float s3, double* __restrict__ part) {
+  __shared__ float red[4][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     s1 += __shfl_xor_sync(0xffffffffu, s1, off);
     s2 += __shfl_xor_sync(0xffffffffu, s2, off);
     bad = fmaxf(bad, __shfl_xor_sync(0xffffffffu, bad, off));
+    s3 += __shfl_xor_sync(0xffffffffu, s3, off);
   }
   if (lane == 0) {
     red[0][w] = s1;
     red[1][w] = s2;
     red[2][w] = bad;
+    red[3][w] = s3;
   }
   __syncthreads();
   if (w == 0) {
     float a = lane < nw ? red[0][lane] : 0.f, b = lane < nw ? red[1][lane] : 0.f, c = lane < nw ? red[2][lane] : 0.f;
+    float d = lane < nw ? red[3][lane] : 0.f;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
       a += __shfl_xor_sync(0xffffffffu, a, off);
       b += __shfl_xor_sync(0xffffffffu, b, off);
       c = fmaxf(c, __shfl_xor_sync(0xffffffffu, c, off));
+      d += __shfl_xor_sync(0xffffffffu, d, off);
     }
     if (lane == 0) {
-      part[3 * blockIdx.x + 0] = (double)a;
-      part[3 * blockIdx.x + 1] = (double)b;
-      part[3 * blockIdx.x + 2] = (double)c;
+      part[KR_NPART * blockIdx.x + 0] = (double)a;
+      part[KR_NPART * blockIdx.x + 1] = (double)b;
+      part[KR_NPART * blockIdx.x + 2] = (double)c;
+      part[KR_NPART * blockIdx.x + 3] = (double)d;
     }
   }
 }
 
+// The gradient a step was taken from, for the stopping rule's g^T step: entry e is
+// g[e] - lam * x_old[e] (g = nullptr: not wanted).
+struct StepGrad {
+  const float* g;
+  float lam;
+};
+__device__ __forceinline__ float step_grad(const StepGrad& sg, int64_t e, float xold) {
+  return sg.g ? fmaf(-sg.lam, xold, __ldg(sg.g + e)) : 0.f;
+}
+
 // x <- x + alpha d, with the step norms (step_norms_block).
 __global__ void __launch_bounds__(256) k_update_reduce(float* __restrict__ x, const float* __restrict__ d, float alpha,
-                                                       int64_t n, double* __restrict__ part) {
-  float s1 = 0.f, s2 = 0.f, bad = 0.f;
+                                                       int64_t n, double* __restrict__ part, StepGrad sg) {
+  float s1 = 0.f, s2 = 0.f, bad = 0.f, s3 = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float st = alpha * d[i];
-    const float xn = x[i] + st;
+    const float xo = x[i];
+    const float xn = xo + st;
     x[i] = xn;
     s1 = fmaf(st, st, s1);
     s2 = fmaf(xn, xn, s2);
+    s3 = fmaf(step_grad(sg, i, xo), st, s3);
     if (!isfinite(xn)) bad = 1.f;
   }
-  step_norms_block(s1, s2, bad, part);
+  step_norms_block(s1, s2, bad, s3, part);
 }
 
 // Richardson state on the device: the stopping rule of Alg. 2 is evaluated on the device
@@ -277,6 +298,7 @@ __global__ void __launch_bounds__(256) k_update_reduce(float* __restrict__ x, co
 struct RichState {
   double h[3];  // last {||step||^2, ||x||^2, non-finite flag}
   double prev_h0, min_h0, min_q;  // previous and smallest ||step||^2, smallest h0 / h1
+  double f, q;  // last step: sampled objective at x before it, g^T M+ g (eps-aware rule only)
   int grow, since_min, it, status;  // status: StepCheck (0 = continue)
 };
 
@@ -285,6 +307,7 @@ struct RichState {
 // does not wait for them.
 struct RichSnap {
   double prev_h0, min_h0, min_q;
+  double xx;  // ||x||^2 before this step (the last step's h[1]; 0 before the first)
   int grow, since_min, it;
 };
 __device__ __forceinline__ RichSnap rich_load(const RichState* st) {
@@ -292,11 +315,32 @@ __device__ __forceinline__ RichSnap rich_load(const RichState* st) {
   r.prev_h0 = __ldcg(&st->prev_h0);
   r.min_h0 = __ldcg(&st->min_h0);
   r.min_q = __ldcg(&st->min_q);
+  r.xx = __ldcg(&st->h[1]);
   r.grow = __ldcg(&st->grow);
   r.since_min = __ldcg(&st->since_min);
   r.it = __ldcg(&st->it);
   return r;
 }
+
+// Stopping-rule arguments handed to the kernel that ends a step.
+struct RichArgs {
+  RichState* st;
+  double tol;
+  int max_iter;
+  cudaGraphConditionalHandle hnd;
+  int use_hnd;
+  unsigned int* ticket;  // zero between steps
+  // The (1+eps)-aware rule (eps_rule = 1): stop once
+  //   rho^2 q / c1 <= theta eps max(f - q / c1, 0)
+  // with f = sampled objective at x before the step (sum of `on` FP64 partials at op, plus
+  // lambda ||x||^2), q = g^T M+ g = g^T step / alpha, c1 = 1 - sqrt(eps) and rho the
+  // contraction factor of the step (Lemma 4.2: the excess after the step is at most
+  // rho^2 q / c1, and f - q / c1 bounds the sampled minimum from below).
+  int eps_rule;
+  double rho2_c1, inv_c1, theta_eps, inv_alpha, lambda;
+  const double* op;
+  int on;
+};
 
 // The rule after one step: the same guards as step_check (converged, diverged: three
 // growths in a row past 16x the smallest step, floor: no new smallest step for 8 steps
@@ -321,73 +365,76 @@ __device__ int step_check_sq(const double* h, double tol, RichSnap& r) {
 }
 
 // The stopping rule of Alg. 2 after one step, evaluated by the first warp of a block: the
-// step's block partials summed in FP64 (strided per lane, then warp shuffles: a fixed
-// order), the rule applied to the state (snapshot `snap`, valid in thread 0), the
-// iteration counted (max_iter ends the loop in any case) and, inside the graph, the loop
-// condition set.
-__device__ void rich_check_block(const double* __restrict__ part, int np, double tol, int max_iter,
-                                 RichState* __restrict__ st, RichSnap snap, cudaGraphConditionalHandle hnd,
-                                 int use_hnd) {
+// step's block partials (and, for the eps-aware rule, the objective partials) summed in
+// FP64 (strided per lane, then warp shuffles: a fixed order), the rule applied to the state
+// (snapshot `snap`, valid in thread 0), the iteration counted (max_iter ends the loop in
+// any case) and, inside the graph, the loop condition set.
+__device__ void rich_check_block(const double* __restrict__ part, int np, const RichArgs& ra, RichSnap snap) {
   if (threadIdx.x >= 32) return;
   const int lane = threadIdx.x;
-  double a = 0.0, b = 0.0, c = 0.0;
+  double a = 0.0, b = 0.0, c = 0.0, d = 0.0, f = 0.0;
   for (int k = lane; k < np; k += 32) {
-    a += __ldcg(part + 3 * k + 0);
-    b += __ldcg(part + 3 * k + 1);
-    c = fmax(c, __ldcg(part + 3 * k + 2));
+    a += __ldcg(part + KR_NPART * k + 0);
+    b += __ldcg(part + KR_NPART * k + 1);
+    c = fmax(c, __ldcg(part + KR_NPART * k + 2));
+    d += __ldcg(part + KR_NPART * k + 3);
   }
+  if (ra.eps_rule)
+    for (int k = lane; k < ra.on; k += 32) f += __ldcg(ra.op + k);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, off);
     b += __shfl_xor_sync(0xffffffffu, b, off);
     c = fmax(c, __shfl_xor_sync(0xffffffffu, c, off));
+    d += __shfl_xor_sync(0xffffffffu, d, off);
+    f += __shfl_xor_sync(0xffffffffu, f, off);
   }
   if (lane == 0) {
+    RichState* st = ra.st;
     const double h[3] = {a, b, c};
-    int status = step_check_sq(h, tol, snap);
+    int status = STEP_CONTINUE;
+    double fx = 0.0, q = 0.0;
+    if (ra.eps_rule) {
+      fx = f + ra.lambda * snap.xx;
+      q = d * ra.inv_alpha;
+      if (h[2] == 0.0 && isfinite(fx) && isfinite(q) && ra.rho2_c1 * q <= ra.theta_eps * fmax(fx - q * ra.inv_c1, 0.0))
+        status = STEP_EPS;
+    }
+    if (status == STEP_CONTINUE) status = step_check_sq(h, ra.tol, snap);
     snap.it += 1;
-    if (status == STEP_CONTINUE && snap.it >= max_iter) status = STEP_MAXITER;
+    if (status == STEP_CONTINUE && snap.it >= ra.max_iter) status = STEP_MAXITER;
     st->h[0] = h[0];
     st->h[1] = h[1];
     st->h[2] = h[2];
     st->prev_h0 = snap.prev_h0;
     st->min_h0 = snap.min_h0;
     st->min_q = snap.min_q;
+    st->f = fx;
+    st->q = q;
     st->grow = snap.grow;
     st->since_min = snap.since_min;
     st->it = snap.it;
     st->status = status;
-    if (use_hnd) cudaGraphSetConditional(hnd, status == STEP_CONTINUE ? 1u : 0u);
+    if (ra.use_hnd) cudaGraphSetConditional(ra.hnd, status == STEP_CONTINUE ? 1u : 0u);
   }
 }
 
 __global__ void k_rich_init(RichState* st) {
   st->h[0] = st->h[1] = st->h[2] = 0.0;
   st->prev_h0 = st->min_h0 = st->min_q = INFINITY;
+  st->f = st->q = 0.0;
   st->grow = st->since_min = st->it = 0;
   st->status = STEP_CONTINUE;
 }
 
 // Sums the step's block partials, applies the stopping rule, counts the iteration (max_iter
 // ends the loop in any case) and, inside the graph, sets the loop condition.
-__global__ void __launch_bounds__(32) k_rich_check(const double* __restrict__ part, int np, double tol, int max_iter,
-                                                    RichState* __restrict__ st, cudaGraphConditionalHandle hnd,
-                                                    int use_hnd) {
+__global__ void __launch_bounds__(32) k_rich_check(const double* __restrict__ part, int np, RichArgs ra) {
   kr_pdl_wait();
   RichSnap snap = {};
-  if (threadIdx.x == 0) snap = rich_load(st);
-  rich_check_block(part, np, tol, max_iter, st, snap, hnd, use_hnd);
+  if (threadIdx.x == 0) snap = rich_load(ra.st);
+  rich_check_block(part, np, ra, snap);
 }
-
-// Stopping-rule arguments handed to the kernel that ends a step.
-struct RichArgs {
-  RichState* st;
-  double tol;
-  int max_iter;
-  cudaGraphConditionalHandle hnd;
-  int use_hnd;
-  unsigned int* ticket;  // zero between steps
-};
 
 // ------------------------------------------------------------------ preconditioned step, fused
 
@@ -416,14 +463,14 @@ constexpr int PC_TQ = 32;
 __global__ void __launch_bounds__(256) k_pc_mode0(const float* __restrict__ in, const float* __restrict__ xl,
                                                   float lambda, const float* __restrict__ B0, int trans, int R0,
                                                   int Q, float* __restrict__ out, float* __restrict__ x,
-                                                  float alpha, double* __restrict__ part) {
+                                                  float alpha, double* __restrict__ part, StepGrad sg) {
   __shared__ float sB[KR_MAX_RANK * KR_MAX_RANK];
   __shared__ float sIn[KR_MAX_RANK * PC_TQ];
   for (int e = threadIdx.x; e < R0 * R0; e += blockDim.x) {
     const int j = e / R0, k = e - j * R0;
     sB[e] = trans ? __ldg(B0 + k * R0 + j) : __ldg(B0 + e);  // sB[j * R0 + k] = B0'[j, k]
   }
-  float s1 = 0.f, s2 = 0.f, bad = 0.f;
+  float s1 = 0.f, s2 = 0.f, bad = 0.f, s3 = 0.f;
   for (int q0 = blockIdx.x * PC_TQ; q0 < Q; q0 += gridDim.x * PC_TQ) {
     const int tq = min(PC_TQ, Q - q0);
     __syncthreads();
@@ -447,17 +494,19 @@ __global__ void __launch_bounds__(256) k_pc_mode0(const float* __restrict__ in, 
       const int64_t gi = (int64_t)j * Q + q0 + c;
       if (x) {
         const float st = alpha * acc;
-        const float xn = x[gi] + st;
+        const float xo = x[gi];
+        const float xn = xo + st;
         x[gi] = xn;
         s1 = fmaf(st, st, s1);
         s2 = fmaf(xn, xn, s2);
+        s3 = fmaf(step_grad(sg, gi, xo), st, s3);
         if (!isfinite(xn)) bad = 1.f;
       } else {
         out[gi] = acc;
       }
     }
   }
-  if (x) step_norms_block(s1, s2, bad, part);
+  if (x) step_norms_block(s1, s2, bad, s3, part);
 }
 
 // In shared memory: t (P0 x R_m0 x ... x R_{N-1}, Q entries) <- B applied along modes
@@ -546,7 +595,7 @@ __global__ void __launch_bounds__(1024) k_pc_fused(PcModes pm, const float* __re
                                                    const float* __restrict__ xl, float lambda,
                                                    const float* __restrict__ B0, int trans0, int rest, int R0, int Q,
                                                    float* __restrict__ out, float* __restrict__ x, float alpha,
-                                                   double* __restrict__ part, RichArgs ra) {
+                                                   double* __restrict__ part, RichArgs ra, StepGrad sg) {
   extern __shared__ float pc_smem[];
   float* full = pc_smem;          // R0 x Q
   float* t = full + (size_t)R0 * Q;
@@ -634,20 +683,23 @@ __global__ void __launch_bounds__(1024) k_pc_fused(PcModes pm, const float* __re
       pc_slab_modes(pm, sB, boff2, t, u, Q);
     }
   }
-  float s1 = 0.f, s2 = 0.f, bad = 0.f;
+  float s1 = 0.f, s2 = 0.f, bad = 0.f, s3 = 0.f;
   for (int e = threadIdx.x; e < Q; e += blockDim.x) {
     if (x) {
+      const int64_t gi = (int64_t)j * Q + e;
       const float st = alpha * t[e];
-      const float xn = x[(int64_t)j * Q + e] + st;
-      x[(int64_t)j * Q + e] = xn;
+      const float xo = x[gi];
+      const float xn = xo + st;
+      x[gi] = xn;
       s1 = fmaf(st, st, s1);
       s2 = fmaf(xn, xn, s2);
+      s3 = fmaf(step_grad(sg, gi, xo), st, s3);
       if (!isfinite(xn)) bad = 1.f;
     } else {
       out[(int64_t)j * Q + e] = t[e];
     }
   }
-  if (x) step_norms_block(s1, s2, bad, part);
+  if (x) step_norms_block(s1, s2, bad, s3, part);
   if (x && ra.st) {  // the last block to finish evaluates the stopping rule
     __shared__ bool last;
     if (threadIdx.x == 0) {
@@ -657,7 +709,7 @@ __global__ void __launch_bounds__(1024) k_pc_fused(PcModes pm, const float* __re
     __syncthreads();
     if (last) {
       __threadfence();
-      rich_check_block(part, gridDim.x, ra.tol, ra.max_iter, ra.st, snap, ra.hnd, ra.use_hnd);
+      rich_check_block(part, gridDim.x, ra, snap);
       if (threadIdx.x == 0) *ra.ticket = 0u;
     }
   }
@@ -668,7 +720,7 @@ __global__ void __launch_bounds__(1024) k_pc_fused(PcModes pm, const float* __re
 // Shared memory: the slab twice, then the matrices of modes 1..N-1 (both sets).
 __global__ void __launch_bounds__(1024) k_pc_slab(PcModes pm, const float* __restrict__ in, int Q,
                                                   float* __restrict__ out, float* __restrict__ x, float alpha,
-                                                  double* __restrict__ part) {
+                                                  double* __restrict__ part, StepGrad sg) {
   extern __shared__ float pc_smem[];
   float* t = pc_smem;
   float* u = pc_smem + Q;
@@ -716,20 +768,23 @@ __global__ void __launch_bounds__(1024) k_pc_slab(PcModes pm, const float* __res
     __syncthreads();
     pc_slab_modes(pm, sB, boff2, t, u, Q);
   }
-  float s1 = 0.f, s2 = 0.f, bad = 0.f;
+  float s1 = 0.f, s2 = 0.f, bad = 0.f, s3 = 0.f;
   for (int e = threadIdx.x; e < Q; e += blockDim.x) {
     if (x) {
+      const int64_t gi = (int64_t)j * Q + e;
       const float st = alpha * t[e];
-      const float xn = x[(int64_t)j * Q + e] + st;
-      x[(int64_t)j * Q + e] = xn;
+      const float xo = x[gi];
+      const float xn = xo + st;
+      x[gi] = xn;
       s1 = fmaf(st, st, s1);
       s2 = fmaf(xn, xn, s2);
+      s3 = fmaf(step_grad(sg, gi, xo), st, s3);
       if (!isfinite(xn)) bad = 1.f;
     } else {
       out[(int64_t)j * Q + e] = t[e];
     }
   }
-  if (x) step_norms_block(s1, s2, bad, part);
+  if (x) step_norms_block(s1, s2, bad, s3, part);
 }
 
 // The step when the first mode of the preconditioner has already been applied (for
@@ -741,7 +796,7 @@ __global__ void __launch_bounds__(1024) k_pc_slab(PcModes pm, const float* __res
 // of the block's rows, the matrices of modes 1..N-1 (transposed).
 __global__ void __launch_bounds__(256) k_pc_rows(PcModes pm, const float* __restrict__ in, int Q, int S,
                                                  float* __restrict__ x, float alpha, double* __restrict__ part,
-                                                 RichArgs ra) {
+                                                 RichArgs ra, StepGrad sg) {
   extern __shared__ float pc_smem[];
   const int R1 = pm.R[1], Q1 = Q / R1, nr = R1 / S, nq = nr * Q1;
   float* full = pc_smem;
@@ -787,7 +842,8 @@ __global__ void __launch_bounds__(256) k_pc_rows(PcModes pm, const float* __rest
   }
   __syncthreads();
   pc_modes_from(pm, sB, boff, t, u, nq, 2, nr);
-  float s1 = 0.f, s2 = 0.f, bad = 0.f;
+  float s1 = 0.f, s2 = 0.f, bad = 0.f, s3 = 0.f;
+  const int64_t r0 = (int64_t)j * Q + (int64_t)s * nq;  // first entry of the block's rows
 #pragma unroll
   for (int k = 0; k < 4; ++k) {  // the prefetched entries
     const int e = threadIdx.x + k * 256;
@@ -797,18 +853,21 @@ __global__ void __launch_bounds__(256) k_pc_rows(PcModes pm, const float* __rest
       xr[e] = xn;
       s1 = fmaf(st, st, s1);
       s2 = fmaf(xn, xn, s2);
+      s3 = fmaf(step_grad(sg, r0 + e, xv[k]), st, s3);
       if (!isfinite(xn)) bad = 1.f;
     }
   }
   for (int e = threadIdx.x + 4 * 256; e < nq; e += blockDim.x) {  // larger slabs: the rest
     const float st = alpha * t[e];
-    const float xn = xr[e] + st;
+    const float xo = xr[e];
+    const float xn = xo + st;
     xr[e] = xn;
     s1 = fmaf(st, st, s1);
     s2 = fmaf(xn, xn, s2);
+    s3 = fmaf(step_grad(sg, r0 + e, xo), st, s3);
     if (!isfinite(xn)) bad = 1.f;
   }
-  step_norms_block(s1, s2, bad, part);
+  step_norms_block(s1, s2, bad, s3, part);
   if (ra.st) {  // the last block to finish evaluates the stopping rule
     __shared__ bool last;
     if (threadIdx.x == 0) {
@@ -818,7 +877,7 @@ __global__ void __launch_bounds__(256) k_pc_rows(PcModes pm, const float* __rest
     __syncthreads();
     if (last) {
       __threadfence();
-      rich_check_block(part, gridDim.x, ra.tol, ra.max_iter, ra.st, snap, ra.hnd, ra.use_hnd);
+      rich_check_block(part, gridDim.x, ra, snap);
       if (threadIdx.x == 0) *ra.ticket = 0u;
     }
   }
@@ -994,7 +1053,9 @@ struct IterBufs {
   float* d;      // R
   float* t0;     // max intermediate
   float* t1;     // max intermediate
-  double* part;  // partials (3 * nblk)
+  double* part;  // step partials (KR_NPART per block)
+  double* opart = nullptr;  // objective partials of the sampled pass (per-cell pass: per block; slab pass:
+                            // per chunk of the tile reduction)
   double* red;   // 4 doubles
   RichState* rich = nullptr;  // device stopping-rule state
   // slab form (tl != nullptr): X1 and Z are P x R_{N-1} x R_N (N >= 3; x and g for N = 2)
@@ -1004,6 +1065,8 @@ struct IterBufs {
   // N = 3, lambda = 0: A(1) G_1^-1, the weights of the tile reduction with the first mode
   // of the preconditioner folded in (then g holds G_1^-1 x_1 gradient)
   float* B1 = nullptr;
+  // with B1 and the eps-aware rule: the gradient itself (a second output of the tile reduction)
+  float* g2 = nullptr;
 };
 
 int64_t max_intermediate(const Modes& m) {
@@ -1030,7 +1093,7 @@ kr_status forward_resid(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const 
     tr[n] = 0;
   }
   KR_TRY(kr_kron_apply2(ctx, N, din, dout, B, tr, bf.x, bf.Y, bf.t0, bf.t1));
-  return kr_sketch_resid(ctx, sk, m.A[N - 1], m.R[N - 1], bf.Y, bf.W, bf.part, nblk, used);
+  return kr_sketch_resid(ctx, sk, m.A[N - 1], m.R[N - 1], bf.Y, bf.W, bf.opart ? bf.opart : bf.part, nblk, used);
 }
 
 kr_status backward(kr_ctx* ctx, const Modes& m, const IterBufs& bf) {
@@ -1067,9 +1130,11 @@ kr_status pc_step_core(kr_ctx* ctx, const FactorTables& t, double lambda, float*
                        int* nparts, bool* checked);
 
 // With mode0_done (lambda = 0, N >= 2) g already holds G_1^-1 x_1 (gradient) and the
-// step applies the other modes only (k_pc_rows).
+// step applies the other modes only (k_pc_rows); graw, if not null, is the gradient itself
+// (for the eps-aware rule's g^T step).
 kr_status pc_step(kr_ctx* ctx, const FactorTables& t, double lambda, float* g, float* x, float alpha, float* tmp0,
-                  float* tmp1, float* tmp2, int ublk, double* part, const RichArgs& ra, bool mode0_done = false) {
+                  float* tmp1, float* tmp2, int ublk, double* part, const RichArgs& ra, bool mode0_done = false,
+                  const float* graw = nullptr) {
   int np = 0;
   bool checked = false;
   if (mode0_done) {
@@ -1093,11 +1158,12 @@ kr_status pc_step(kr_ctx* ctx, const FactorTables& t, double lambda, float* g, f
     bool fits = false;
     KR_TRY(smem_fit(ctx, k_pc_rows, smem, &fits));
     if (!fits) return kr_fail(ctx, KR_EINVAL, "preconditioned step: slab of %lld entries too large", (long long)Q);
-    KR_LAUNCH_PDL(ctx, k_pc_rows, t.R[0] * S, 256, smem, pm, (const float*)g, (int)Q, S, x, alpha, part, ra);
+    const StepGrad sg = {ra.eps_rule ? graw : nullptr, 0.f};
+    KR_LAUNCH_PDL(ctx, k_pc_rows, t.R[0] * S, 256, smem, pm, (const float*)g, (int)Q, S, x, alpha, part, ra, sg);
     return KR_OK;
   }
   KR_TRY(pc_step_core(ctx, t, lambda, g, x, alpha, tmp0, tmp1, tmp2, ublk, part, ra, &np, &checked));
-  if (!checked) KR_LAUNCH(ctx, k_rich_check, 1, 32, 0, part, np, ra.tol, ra.max_iter, ra.st, ra.hnd, ra.use_hnd);
+  if (!checked) KR_LAUNCH(ctx, k_rich_check, 1, 32, 0, part, np, ra);
   return KR_OK;
 }
 
@@ -1114,12 +1180,16 @@ kr_status pc_step_core(kr_ctx* ctx, const FactorTables& t, double lambda, float*
   for (int n = 1; n < N; ++n) nb += (size_t)t.R[n] * t.R[n];
   if (lambda > 0.0) nb *= 2;
   const size_t smem = (2 * (size_t)Q + nb) * sizeof(float);
+  // the gradient of the step for the eps-aware rule's g^T step: g - lambda x_old
+  const StepGrad sg = {ra.eps_rule ? g : nullptr, (float)lambda};
+  const StepGrad sg0 = {ra.eps_rule ? g : nullptr, 0.f};  // g already holds g - lambda x
+  const StepGrad none_sg = {nullptr, 0.f};
   bool split = false;
   if (Q <= (int64_t(1) << 20)) KR_TRY(smem_fit(ctx, k_pc_slab, smem, &split));
   if (!split) {
     if (lambda > 0.0) KR_LAUNCH(ctx, k_sub_lambda_x, ublk, 256, 0, g, x, (float)lambda, R);
     KR_TRY(kr_precond_apply(ctx, t, lambda, g, tmp0, tmp1, tmp2));
-    KR_LAUNCH(ctx, k_update_reduce, ublk, 256, 0, x, tmp0, alpha, R, part);
+    KR_LAUNCH(ctx, k_update_reduce, ublk, 256, 0, x, tmp0, alpha, R, part, sg0);
     *nparts = ublk;
     return KR_OK;
   }
@@ -1145,7 +1215,7 @@ kr_status pc_step_core(kr_ctx* ctx, const FactorTables& t, double lambda, float*
   if (fused) {
     if (lambda == 0.0) {
       KR_LAUNCH_PDL(ctx, k_pc_fused, R0, sthreads, fsmem, pm, g, (const float*)nullptr, 0.f, pm.B[0], 0,
-                    N > 1 ? 1 : 0, R0, Qi, (float*)nullptr, x, alpha, part, ra);
+                    N > 1 ? 1 : 0, R0, Qi, (float*)nullptr, x, alpha, part, ra, sg);
       *nparts = R0;
       *checked = true;
       return KR_OK;
@@ -1153,26 +1223,27 @@ kr_status pc_step_core(kr_ctx* ctx, const FactorTables& t, double lambda, float*
     RichArgs none = ra;
     none.st = nullptr;
     KR_LAUNCH_PDL(ctx, k_pc_fused, R0, sthreads, fsmem, pm, g, (const float*)x, (float)lambda, pm.B[0], 1, 1, R0,
-                  Qi, tmp0, (float*)nullptr, 0.f, part, none);
+                  Qi, tmp0, (float*)nullptr, 0.f, part, none, none_sg);
     KR_LAUNCH_PDL(ctx, k_pc_fused, R0, sthreads, fsmem, pm, (const float*)tmp0, (const float*)nullptr, 0.f,
-                  pm.B2[0], 0, 0, R0, Qi, (float*)nullptr, x, alpha, part, ra);
+                  pm.B2[0], 0, 0, R0, Qi, (float*)nullptr, x, alpha, part, ra, sg);
     *nparts = R0;
     *checked = true;
     return KR_OK;
   }
   if (lambda == 0.0 && N == 1) {
-    KR_LAUNCH(ctx, k_pc_mode0, g0, 256, 0, g, xl, 0.f, pm.B[0], 0, R0, Qi, nullptr, x, alpha, part);
+    KR_LAUNCH(ctx, k_pc_mode0, g0, 256, 0, g, xl, 0.f, pm.B[0], 0, R0, Qi, nullptr, x, alpha, part, sg);
     *nparts = g0;
     return KR_OK;
   }
-  KR_LAUNCH(ctx, k_pc_mode0, g0, 256, 0, g, xl, (float)lambda, pm.B[0], pm.trans, R0, Qi, tmp0, nullptr, 0.f, part);
+  KR_LAUNCH(ctx, k_pc_mode0, g0, 256, 0, g, xl, (float)lambda, pm.B[0], pm.trans, R0, Qi, tmp0, nullptr, 0.f, part,
+            none_sg);
   if (lambda == 0.0) {
-    KR_LAUNCH(ctx, k_pc_slab, R0, sthreads, smem, pm, tmp0, Qi, nullptr, x, alpha, part);
+    KR_LAUNCH(ctx, k_pc_slab, R0, sthreads, smem, pm, tmp0, Qi, nullptr, x, alpha, part, sg);
     *nparts = R0;
     return KR_OK;
   }
-  KR_LAUNCH(ctx, k_pc_slab, R0, sthreads, smem, pm, tmp0, Qi, tmp1, nullptr, 0.f, part);
-  KR_LAUNCH(ctx, k_pc_mode0, g0, 256, 0, tmp1, nullptr, 0.f, pm.B2[0], 0, R0, Qi, nullptr, x, alpha, part);
+  KR_LAUNCH(ctx, k_pc_slab, R0, sthreads, smem, pm, tmp0, Qi, tmp1, nullptr, 0.f, part, none_sg);
+  KR_LAUNCH(ctx, k_pc_mode0, g0, 256, 0, tmp1, nullptr, 0.f, pm.B2[0], 0, R0, Qi, nullptr, x, alpha, part, sg);
   *nparts = g0;
   return KR_OK;
 }
@@ -1189,7 +1260,8 @@ int64_t slab_max_intermediate(const Modes& m) {
 
 // Slab form of the sampled pass: X1 = X x_1 A(1) ... x_{N-2} A(N-2), then the fused slab
 // kernel (Z and the per-tile objective partials in bf.tl->objpart).
-kr_status slab_forward(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const IterBufs& bf, bool want_obj) {
+kr_status slab_forward(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const IterBufs& bf, bool want_obj,
+                       bool rearm) {
   const int N = m.N;
   const float* X1 = bf.x;
   if (N > 2) {
@@ -1204,15 +1276,17 @@ kr_status slab_forward(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const I
     KR_TRY(kr_kron_apply2(ctx, N, din, dout, B, tr, bf.x, bf.X1, bf.t0, bf.t1));
     X1 = bf.X1;
   }
-  return kr_slab_pass(ctx, sk, bf.tl, m.A[N - 2], m.A[N - 1], X1, want_obj);
+  return kr_slab_pass(ctx, sk, bf.tl, m.A[N - 2], m.A[N - 1], X1, want_obj, rearm);
 }
 
 // g = Z x_1 A(1)^T ... x_{N-2} A(N-2)^T: the sum over the tiles folded with the last
 // prefix mode (mode N-2 in the paper's 1-based count), then the earlier prefix modes.
-kr_status slab_backward(kr_ctx* ctx, const Modes& m, const IterBufs& bf) {
+kr_status slab_backward(kr_ctx* ctx, const Modes& m, const IterBufs& bf, double* opart) {
   const int N = m.N;
-  if (N <= 3) return kr_tile_reduce(ctx, bf.tl, N == 3 ? (bf.B1 ? bf.B1 : m.A[0]) : nullptr, bf.g);
-  KR_TRY(kr_tile_reduce(ctx, bf.tl, m.A[N - 3], bf.Z));
+  if (N <= 3)
+    return kr_tile_reduce(ctx, bf.tl, N == 3 ? (bf.B1 ? bf.B1 : m.A[0]) : nullptr, bf.g, opart,
+                          bf.g2 ? m.A[0] : nullptr, bf.g2);
+  KR_TRY(kr_tile_reduce(ctx, bf.tl, m.A[N - 3], bf.Z, opart));
   int din[KR_MAX_MODES], dout[KR_MAX_MODES], tr[KR_MAX_MODES];
   const float* B[KR_MAX_MODES];
   for (int n = 0; n < N; ++n) {
@@ -1225,18 +1299,24 @@ kr_status slab_backward(kr_ctx* ctx, const Modes& m, const IterBufs& bf) {
 }
 
 // Sampled pass at x: g = K~^T Omega (b~ - K~ x) (if want_g) and the objective partials
-// (*op, *on: FP64 values to be summed).
+// (*op, *on: FP64 values to be summed; with want_g only when want_obj).
 kr_status sampled_pass(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const IterBufs& bf, int nblk, bool want_g,
-                       const double** op, int* on) {
+                       const double** op, int* on, bool want_obj = false) {
   if (bf.tl) {
-    KR_TRY(slab_forward(ctx, m, sk, bf, !want_g));
-    *op = bf.tl->objpart;
-    *on = (int)bf.tl->ntmax;
-    return want_g ? slab_backward(ctx, m, bf) : KR_OK;
+    KR_TRY(slab_forward(ctx, m, sk, bf, !want_g || want_obj, !want_g));
+    if (!want_g) {
+      *op = bf.tl->objpart;
+      *on = (int)bf.tl->ntmax;
+      return KR_OK;
+    }
+    // the tile reduction also sums the tiles' objective partials per chunk, in tile order
+    *op = bf.opart;
+    *on = (int)(bf.tl->nc * bf.tl->Pq);
+    return slab_backward(ctx, m, bf, want_obj ? bf.opart : nullptr);
   }
   int used = 0;
   KR_TRY(forward_resid(ctx, m, sk, bf, nblk, &used));
-  *op = bf.part;
+  *op = bf.opart ? bf.opart : bf.part;
   *on = used;
   return want_g ? backward(ctx, m, bf) : KR_OK;
 }
@@ -1299,6 +1379,8 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   int64_t mx = max_intermediate(m);
   if (slab) {
     kr_tiles_setup(ctx, m, &sk, &tl);
+    // folded first preconditioner mode with the eps-aware rule: the reduction also returns g
+    if (N == 3 && cfg.lambda == 0.0 && cfg.stop_rule == 1) tl.nout = 2;
     nyw = 0;
     nx1 = N > 2 ? tl.P * m.R[N - 2] * RT : 0;
     mx = slab_max_intermediate(m);
@@ -1315,12 +1397,17 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   nd.add<float>(R);    // d
   nd.add<float>(mx);   // t0
   nd.add<float>(mx);   // t1
-  nd.add<double>(3 * (size_t)(nblk > 1024 ? nblk : 1024));
+  const size_t npart = (size_t)KR_NPART * (nblk > 1024 ? nblk : 1024);
+  const bool eps_rule = cfg.stop_rule == 1;
+  const size_t nopart = eps_rule ? (slab ? (size_t)(tl.nc * tl.Pq) : (size_t)nblk) : 0;
+  nd.add<double>(npart);
+  nd.add<double>(nopart);
   nd.add<double>(16);
   nd.add<RichState>(1);
   // the first preconditioner mode folded into the tile reduction (lambda = 0, N = 3)
   const bool fold0 = slab && N == 3 && cfg.lambda == 0.0;
   nd.add<float>(fold0 ? (size_t)m.I[0] * m.R[0] : 0);
+  nd.add<float>(fold0 && eps_rule ? (size_t)R : 0);
   {
     Need sc = nd;
     kr_sketch_scratch_need(ctx, cfg.s, ncell, m.I[m.N - 1], nd);
@@ -1352,12 +1439,14 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   bf.d = cv.take<float>(R);
   bf.t0 = cv.take<float>(mx);
   bf.t1 = cv.take<float>(mx);
-  bf.part = cv.take<double>(3 * (size_t)(nblk > 1024 ? nblk : 1024));
+  bf.part = cv.take<double>(npart);
+  bf.opart = eps_rule ? cv.take<double>(nopart) : nullptr;
   bf.red = cv.take<double>(16);
   bf.rich = cv.take<RichState>(1);
   if (fold0) {  // B1 = A(1) G_1^-1 (G_1^-1 symmetric: row i of B1 = G_1^-1 applied to row i of A(1))
     bf.B1 = cv.take<float>((size_t)m.I[0] * m.R[0]);
     KR_TRY(kr_mode_product(ctx, m.A[0], bf.B1, m.I[0], m.R[0], 1, m.R[0], t.ginv[0], 0));
+    if (eps_rule) bf.g2 = cv.take<float>(R);
   }
   {
     Carve sc = cv;
@@ -1380,17 +1469,32 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   // also sets the loop condition).
   unsigned int* ticket = reinterpret_cast<unsigned int*>(bf.red + 8);
   KR_CUDA(ctx, cudaMemsetAsync(ticket, 0, sizeof(unsigned int), ctx->stream));
+  // Constants of the (1+eps)-aware rule: with sampled-to-exact spectral bounds
+  // (1 - sqrt(eps)) M <= H <= (1 + sqrt(eps)) M (proof of Thm 4.5), the step x - alpha M+ g
+  // contracts the excess by rho^2 with rho = max(|1 - alpha (1 - sqrt(eps))|,
+  // |1 - alpha (1 + sqrt(eps))|) (= 2 sqrt(eps) - eps at the paper's alpha = 1 - sqrt(eps);
+  // Lemma 4.2), and g^T M+ g >= (1 - sqrt(eps)) times the excess.
+  const double se = sqrt(cfg.eps), c1 = 1.0 - se;
+  const double rho = fmax(fabs(1.0 - cfg.alpha * (1.0 - se)), fabs(1.0 - cfg.alpha * (1.0 + se)));
   auto one_step = [&](cudaGraphConditionalHandle hnd, int use_hnd) -> kr_status {
-    KR_TRY(sampled_pass(ctx, m, &sk, bf, nblk, true, &op, &on));
-    RichArgs ra;
+    KR_TRY(sampled_pass(ctx, m, &sk, bf, nblk, true, &op, &on, eps_rule));
+    RichArgs ra = {};
     ra.st = bf.rich;
     ra.tol = cfg.tol;
     ra.max_iter = cfg.max_iter;
     ra.hnd = hnd;
     ra.use_hnd = use_hnd;
     ra.ticket = ticket;
+    ra.eps_rule = eps_rule ? 1 : 0;
+    ra.rho2_c1 = rho * rho / c1;
+    ra.inv_c1 = 1.0 / c1;
+    ra.theta_eps = cfg.theta * cfg.eps;
+    ra.inv_alpha = 1.0 / cfg.alpha;
+    ra.lambda = cfg.lambda;
+    ra.op = op;
+    ra.on = on;
     return pc_step(ctx, t, cfg.lambda, bf.g, bf.x, (float)cfg.alpha, bf.d, bf.t0, bf.t1, ublk, bf.part, ra,
-                   bf.B1 != nullptr);
+                   bf.B1 != nullptr, bf.g2);
   };
   auto read_state = [&]() -> kr_status {
     KR_CUDA(ctx, cudaMemcpyAsync(hs, bf.rich, sizeof(RichState), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1422,6 +1526,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     st = kr_fail(ctx, KR_EDIVERGED, "Richardson step grew 3 times in a row past 16x its minimum (iteration %d)", it);
   if (hs->status == STEP_CONVERGED) converged = 1;
   if (hs->status == STEP_FLOOR) converged = 2;
+  if (hs->status == STEP_EPS) converged = 3;
   KR_CUDA(ctx, cudaEventRecord(ev[4], ctx->stream));
   // final sampled objective at the returned x (FP64 accumulation)
   KR_TRY(sampled_pass(ctx, m, &sk, bf, nblk, false, &op, &on));
@@ -1483,6 +1588,9 @@ kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr
   cfg.alpha = o->step > 0 ? o->step : 1.0 - sqrt(o->eps);
   cfg.tol = o->tol > 0 ? o->tol : 1e-7;
   cfg.max_iter = o->max_iter > 0 ? o->max_iter : 100;
+  if (o->stop_rule != 0 && o->stop_rule != 1) return kr_fail(ctx, KR_EINVAL, "solver: stop_rule must be 0 or 1");
+  cfg.stop_rule = o->stop_rule;
+  cfg.theta = o->theta > 0 ? o->theta : 0.01;
   const int64_t R = kr_prod_R(m), I = kr_prod_I(m);
   cfg.s = default_samples(o, R);
   if (rep) *rep = kr_report{};

@@ -840,7 +840,7 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     int used = 0;
     // sampled part: Gb = K~^T Omega (b~ - K~ z) per row
     if (slab) {
-      KR_TRY(kr_slab_pass(ctx, &sk, &tl, mo.A[0], mo.A[1], Z, false));
+      KR_TRY(kr_slab_pass(ctx, &sk, &tl, mo.A[0], mo.A[1], Z, false, false));
       KR_TRY(kr_tile_reduce(ctx, &tl, nullptr, Gb));
     } else {
       KR_TRY(kr_kron_apply2(ctx, No + 1, dfw_in, dfw_out, Bf, trf, Z, Y, t0, t1));
@@ -941,6 +941,8 @@ SolveCfg cfg_from(const kr_opts* o, int64_t Rsz) {
   c.tol = o->tol > 0 ? o->tol : 1e-7;
   c.max_iter = o->max_iter > 0 ? o->max_iter : 100;
   c.s = o->num_samples > 0 ? o->num_samples : kr_sample_count(Rsz, o->eps, o->sample_scale);
+  c.stop_rule = o->stop_rule == 1 ? 1 : 0;  // used by the core steps (Alg. 2 solves)
+  c.theta = o->theta > 0 ? o->theta : 0.01;
   return c;
 }
 
