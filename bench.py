@@ -1,22 +1,26 @@
 """Benchmark of the FastKroneckerRegression hot path on GB300.
 
-One step = one complete Alg. 2 solve through the C ABI (leverage scores and CDFs,
-Philox sampling, grouping, gather of b, Richardson iterations to the stopping
-rule, FP64 final check) of the N=3 workload with 512 x 32 factors (rows scaled by
-log-normal(sigma=1) weights), b = K x_true + 5% relative noise of length 512^3,
-eps = 0.1, s = ceil(4 R ln R / eps) = 13,627,829 draws, FP32 contractions.
-Inputs are resident in HBM for `value`; `e2e` passes host buffers through the same
-C-ABI call (copies inside the timed region). Every solve is certified afterwards:
-f(x) <= (1 + eps) OPT, with OPT from the exact KronMatMul solution computed by the
-library.
+One step = one complete Alg. 2 solve through the C ABI: leverage scores and CDFs, Philox
+sampling, grouping, gather of b, Richardson iterations until the (1+eps)-aware stopping
+rule holds (the proof of Thm 4.5 with Lemma 4.2), and the FP64 final check of the sampled
+objective. The default workload is the largest single-GPU configuration: N = 3, A(n)
+1024 x 64 Gaussian with 10% of the rows scaled by 20 (high-leverage outliers), b a
+rank-(64,64,64) Tucker tensor plus 1% relative noise stored dense (1024^3 FP32, 4 GB),
+eps = 0.05, s = ceil(4 R ln R / eps) = 261,654,300 draws, FP32 contractions. Inputs are
+generated on the device from a seed (synthetic; the paper's data are not used).
 
-Multi-GPU: the path is run as independent replicas (one solve per rank, no data
-exchange; weak scaling).
+`value` times solves on inputs resident in HBM; `e2e` times the same C-ABI call with
+page-locked host buffers (host <-> device traffic inside the timed region). Every timed solve
+is certified afterwards: f(x) <= (1 + eps) OPT, with f(x) the library's FP64 full objective
+and OPT the oracle's FP64 closed form (x* = (A(1)^+ (x) ... (x) A(N)^+) b), computed once on
+the host.
+
+Multi-GPU: the path is run as independent replicas (one solve per rank, no data exchange;
+weak scaling).
 """
 import argparse
 import hashlib
 import json
-import math
 import os
 import subprocess
 import sys
@@ -28,8 +32,13 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="kron_n3_512x32_lognormal", I=[512, 512, 512], R=[32, 32, 32], dist="lognormal_rows",
-                noise_rel=0.05, eps=0.1, lam=0.0, seed=2209, solve_seed=1, call_id=0)
+WORKLOADS = {
+    "kron_n3_1024x64_outliers": dict(I=[1024, 1024, 1024], R=[64, 64, 64], dist="outliers", noise_rel=0.01,
+                                     b_kind="tucker", tucker_rank=[64, 64, 64], eps=0.05, lam=0.0, seed=2210,
+                                     solve_seed=1),
+    "kron_n3_512x32_lognormal": dict(I=[512, 512, 512], R=[32, 32, 32], dist="lognormal_rows", noise_rel=0.05,
+                                     b_kind="kron", tucker_rank=None, eps=0.1, lam=0.0, seed=2209, solve_seed=1),
+}
 METRIC = "sampled rows/s (draws of one time-to-(1+eps) solve per second)"
 PEAKS_FALLBACK = dict(hbm_gbs=6800.0, bf16_tflops=1900.0)
 
@@ -63,7 +72,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -99,14 +108,21 @@ class ClockSampler:
                     reasons=sorted(reasons), samples=len(sm))
 
 
-def make_inputs(seed):
-    from workloads import kron_problem
+def make_inputs(w, seed, device):
+    """The workload's factors and right-hand side (FP32, on `device`), from the seeded
+    device generator (the numpy generator when no CUDA device is present)."""
+    import torch
 
-    w = WORKLOAD
-    prob = kron_problem(w["I"], w["R"], dist=w["dist"], seed=seed, noise_rel=w["noise_rel"])
-    As = [np.ascontiguousarray(A, dtype=np.float32) for A in prob["As"]]
-    b = np.ascontiguousarray(prob["b"], dtype=np.float32)
-    return As, b
+    from workloads import kron_problem, kron_problem_device
+
+    if device != "cpu":
+        p = kron_problem_device(w["I"], w["R"], dist=w["dist"], seed=seed, noise_rel=w["noise_rel"], device=device,
+                                b_kind=w["b_kind"], tucker_rank=w["tucker_rank"])
+        return p["As"], p["b"]
+    p = kron_problem(w["I"], w["R"], dist=w["dist"], seed=seed, noise_rel=w["noise_rel"], b_kind=w["b_kind"],
+                     tucker_rank=w["tucker_rank"])
+    return ([torch.from_numpy(np.ascontiguousarray(A, dtype=np.float32)) for A in p["As"]],
+            torch.from_numpy(np.ascontiguousarray(p["b"], dtype=np.float32)))
 
 
 def dist_setup(args):
@@ -141,23 +157,30 @@ def max_over_ranks(v, world):
 
 # ---------------------------------------------------------------------------- CPU oracle legs
 
-def oracle_rows_per_s(As, b, gpu_iters, frac, call_id=0):
-    """Times the oracle's Alg. 2 pipeline (tables, sampling, grouping, gather and
-    `gpu_iters` Richardson iterations) on a bounded fraction of the workload's draws."""
+def oracle_opt(As64, b64, lam):
+    """OPT = f(x*) with the oracle's FP64 closed form (once per run, on the host)."""
     from oracle import kron as ko
 
-    w = WORKLOAD
+    t0 = time.perf_counter()
+    opt = ko.objective(As64, b64, ko.closed_form_ridge(As64, b64, lam), lam)
+    return opt, time.perf_counter() - t0
+
+
+def oracle_rows_per_s(w, As64, b32, iters, frac, call_id=0):
+    """Times the oracle's Alg. 2 pipeline (tables, sampling, grouping, gather and `iters`
+    FP64 Richardson iterations) on a bounded fraction of the workload's draws; returns
+    (draws / second, draws, seconds)."""
+    from oracle import kron as ko
+
     R = int(np.prod(w["R"]))
-    s_full = ko.sample_count(R, w["eps"])
-    s = max(1, int(s_full * frac))
-    As64 = [A.astype(np.float64) for A in As]
+    s = max(1, int(ko.sample_count(R, w["eps"]) * frac))
     t0 = time.perf_counter()
     levs = [ko.leverage_scores(A) for A in As64]
     cdfs = [ko.cdf_table(l) for l in levs]
     probs = [ko.probabilities(l) for l in levs]
     smp = ko.draw_sample(As64, s, w["solve_seed"], call_id, cdfs=cdfs, probs=probs)
-    b_s = b[smp.keys].astype(np.float64)
-    ko.richardson(As64, b_s, smp, w["lam"], w["eps"], tol=0.0, max_iter=max(1, gpu_iters))
+    b_s = b32[smp.keys].astype(np.float64)
+    ko.richardson(As64, b_s, smp, w["lam"], w["eps"], tol=0.0, max_iter=max(1, iters))
     dt = time.perf_counter() - t0
     return s / dt, s, dt
 
@@ -166,27 +189,35 @@ def run_reference(args, rank, world):
     """--impl reference: the CPU oracle as it stands, on a bounded sample per step."""
     if rank != 0:
         return
-    As, b = make_inputs(WORKLOAD["seed"])
-    frac = args.ref_fraction
-    iters = args.ref_iters
-    for _ in range(args.warmup):
-        oracle_rows_per_s(As, b, 1, frac / 10.0)
+    import torch
+
+    from oracle import kron as ko
+
+    w = WORKLOADS[args.workload]
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    As, b = make_inputs(w, w["seed"], dev)
+    As64 = [A.cpu().double().numpy() for A in As]
+    b32 = b.cpu().numpy()
+    del As, b
+    if dev != "cpu":
+        torch.cuda.empty_cache()
+    frac, iters = args.ref_fraction, args.ref_iters
+    for k in range(args.warmup):
+        oracle_rows_per_s(w, As64, b32, 1, frac / 10.0, call_id=1000 + k)
     vals, secs = [], []
     for k in range(args.steps):
-        v, s, dt = oracle_rows_per_s(As, b, iters, frac, call_id=k)
+        v, s, dt = oracle_rows_per_s(w, As64, b32, iters, frac, call_id=k)
         vals.append(v)
         secs.append(dt)
     value = float(np.mean(vals))
     cores = os.cpu_count()
-    from oracle import kron as ko
-
-    s_full = ko.sample_count(int(np.prod(WORKLOAD["R"])), WORKLOAD["eps"])
-    sample = "%.3g of the workload's %d draws per step (%d draws), %d Richardson iterations" % (
+    s_full = ko.sample_count(int(np.prod(w["R"])), w["eps"])
+    sample = "%.3g of the workload's %d draws per step (%d draws), %d FP64 Richardson iteration(s)" % (
         frac, s_full, s, iters)
     line = dict(impl="reference", metric=METRIC, value=value, unit="rows/s", n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1000.0 * float(np.mean(secs)), higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=WORKLOAD["name"], I=WORKLOAD["I"], R=WORKLOAD["R"], eps=WORKLOAD["eps"]),
+                config=dict(workload=args.workload, I=w["I"], R=w["R"], eps=w["eps"]),
                 cpu_baseline=dict(value=value, unit="rows/s", cores=cores, kind="oracle", sample=sample),
                 e2e=dict(value=value, unit="rows/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
@@ -194,37 +225,34 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------------------- GPU leg
 
-def exact_opt(kr, As_d, b_d):
-    """OPT = f(x*) with x* = (A1^+ (x) ... (x) AN^+) b = (x)(A^T A)^-1 . (x)A^T b via the library."""
-    import torch
-
-    KtB = kr.kron_matmul(As_d, b_d, trans=[1] * len(As_d))
-    xstar = kr.kron_precond(As_d, KtB, 0.0)
-    torch.cuda.synchronize()
-    return kr.kron_objective(As_d, b_d, xstar, 0.0)
-
-
-def slab_traffic():
-    """DRAM bytes per k_slab launch from the committed ncu capture (profiles/traffic.json), or None
-    once the kernel source differs from the captured one."""
-    here = os.path.dirname(os.path.abspath(__file__))
+def slab_traffic(workload):
+    """DRAM bytes per k_slab launch from the committed ncu capture (profiles/traffic.json), or
+    None once the kernel source differs from the captured one."""
     try:
-        rec = json.load(open(os.path.join(here, "profiles", "traffic.json")))["k_slab"]
-        src = open(os.path.join(here, rec["source"]), "rb").read()
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["k_slab"]
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
     except (OSError, KeyError, ValueError):
-        return None
-    if hashlib.sha1(src).hexdigest() != rec["source_sha1"] or rec["workload"] != WORKLOAD["name"]:
-        return None
-    return rec["dram_bytes_per_launch"]
+        return None, None
+    if hashlib.sha1(src).hexdigest() != rec["source_sha1"] or rec["workload"] != workload:
+        return None, None
+    return rec["dram_bytes_per_launch"], rec.get("note")
 
 
-def nonempty_cells(kr, As_d, b_d, s, seed, call_id, IT):
-    """Cells holding at least one sampled row in the sketch of solve `call_id`."""
+def sketch_stats(kr, As_d, b_d, s, seed, call_id, IT):
+    """Distinct rows and non-empty cells of the sketch of solve `call_id`."""
     tab = kr.kron_leverage(As_d)
     sk = kr.kron_sketch(As_d, tab["cdf"], tab["prob"], b_d, s, seed, call_id)
     keys = sk.export()[0]
     sk.free()
-    return int(np.unique(keys.cpu().numpy() // IT).shape[0])
+    distinct = int(keys.numel())
+    cells = int(torch_unique_count(keys // IT))
+    return distinct, cells
+
+
+def torch_unique_count(t):
+    import torch
+
+    return torch.unique_consecutive(t).numel()
 
 
 def run_gpu(args, rank, world, local):
@@ -233,18 +261,23 @@ def run_gpu(args, rank, world, local):
     import paper_2209_04876_gb300 as kr
 
     torch.cuda.set_device(local)
-    w = WORKLOAD
-    As, b = make_inputs(w["seed"] + rank)
-    As_d = [torch.from_numpy(A).cuda() for A in As]
-    b_d = torch.from_numpy(b).cuda()
-    opts = dict(eps=w["eps"], seed=w["solve_seed"], tol=1e-7, max_iter=200)
+    w = WORKLOADS[args.workload]
+    As_d, b_d = make_inputs(w, w["seed"] + rank, "cuda")
     torch.cuda.synchronize()
-    opt = exact_opt(kr, As_d, b_d)
-    # warm-up
+    eps, lam = w["eps"], w["lam"]
+    solve = kr.kron_ridge if lam > 0 else kr.kron_regress
+    lam_kw = dict(lam=lam) if lam > 0 else {}
+    opts = dict(eps=eps, seed=w["solve_seed"], stop_rule=kr.STOP_EPS, max_iter=200, **lam_kw)
+    opts_step = dict(eps=eps, seed=w["solve_seed"], tol=1e-7, max_iter=200, **lam_kw)
+    # OPT from the oracle's FP64 closed form, once, on the host
+    As64 = [A.cpu().double().numpy() for A in As_d]
+    b32 = b_d.cpu().numpy()
+    opt, opt_s = oracle_opt(As64, b32.astype(np.float64), lam)
+    log("oracle OPT %.6e in %.1f s" % (opt, opt_s))
     for k in range(args.warmup):
-        kr.kron_regress(As_d, b_d, call_id=1000 + k, **opts)
+        solve(As_d, b_d, call_id=1000 + k, **opts)
     torch.cuda.synchronize()
-    # timed region: K solves on resident inputs
+    # timed region: K solves on resident inputs (b is 4 GB: larger than L2 on every pass)
     kr.timing_enable(False)
     clocks = ClockSampler(local)
     clocks.start()
@@ -257,7 +290,7 @@ def run_gpu(args, rank, world, local):
     ev0.record()
     reps, xs = [], []
     for k in range(args.steps):
-        x, rep = kr.kron_regress(As_d, b_d, call_id=k, **opts)
+        x, rep = solve(As_d, b_d, call_id=k, **opts)
         reps.append(rep)
         xs.append(x)
     ev1.record()
@@ -269,118 +302,123 @@ def run_gpu(args, rank, world, local):
     elapsed_ms = max_over_ranks(elapsed_ms, world)
     s = reps[0]["s"]
     value = world * args.steps * s / (elapsed_ms / 1000.0)
-    # certify every timed solve: f(x) <= (1 + eps) OPT
-    ratios = [kr.kron_objective(As_d, b_d, x, 0.0) / opt for x in xs]
-    certified = all(r <= 1.0 + w["eps"] for r in ratios)
-    # dominant-kernel timing: one more solve with per-launch events on the library stream
+    # certify every timed solve against the oracle's OPT
+    ratios = [kr.kron_objective(As_d, b_d, x, lam) / opt for x in xs]
+    certified = all(r <= 1.0 + eps for r in ratios)
+    del xs
+    # the same solves with the relative-step rule (tol 1e-7), for the stopping-rule comparison
+    n_step = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    step_reps = [solve(As_d, b_d, call_id=k, **opts_step)[1] for k in range(n_step)]
+    e1.record()
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / n_step
+    # kernel time shares and the dominant kernel's launch time: one more solve with
+    # per-launch event pairs on the library's stream
     kr.timing_reset()
     kr.timing_enable(True)
-    x, rep_t = kr.kron_regress(As_d, b_d, call_id=args.steps, **opts)
+    x, rep_t = solve(As_d, b_d, call_id=args.steps, **opts)
     tim = kr.timing_read()
     kr.timing_enable(False)
-    # end to end through the same C-ABI call with host buffers (pinned)
-    As_h = [torch.from_numpy(A).pin_memory() for A in As]
-    b_h = torch.from_numpy(b).pin_memory()
-    kr.kron_regress(As_h, b_h, call_id=0, host_io=True, **opts)
+    # end to end through the same C-ABI call with page-locked host buffers
+    As_h = [A.cpu().pin_memory() for A in As_d]
+    b_h = b_d.cpu().pin_memory()
+    solve(As_h, b_h, call_id=0, host_io=True, **opts)
     barrier(world)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        xh, _ = kr.kron_regress(As_h, b_h, call_id=k, host_io=True, **opts)
-    e2e_s = time.perf_counter() - t0
-    e2e_s = max_over_ranks(e2e_s, world)
+        xh, rep_h = solve(As_h, b_h, call_id=k, host_io=True, **opts)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e = world * args.steps * s / e2e_s
+    h2d = int(4 * rep_h["distinct"] + sum(A.numel() * 4 for A in As_h))
+    d2h = int(xh.numel() * 4)
     # the same calls with all of b copied in (the library's path for b outside page-locked memory)
     kr.set_option(kr.OPT_HOST_GATHER, 0)
-    kr.kron_regress(As_h, b_h, call_id=0, host_io=True, **opts)
+    solve(As_h, b_h, call_id=0, host_io=True, **opts)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(args.steps):
-        xc, rep_c = kr.kron_regress(As_h, b_h, call_id=k, host_io=True, **opts)
+        solve(As_h, b_h, call_id=k, host_io=True, **opts)
     e2e_copy = world * args.steps * s / max_over_ranks(time.perf_counter() - t0, world)
     kr.set_option(kr.OPT_HOST_GATHER, 1)
-    # the timed calls read b (page-locked) in place at the sampled rows: 4 B per distinct row
-    _, rep_h = kr.kron_regress(As_h, b_h, call_id=args.steps - 1, host_io=True, **opts)
-    h2d = int(4 * rep_h["distinct"] + sum(A.nbytes for A in As))
-    d2h = int(xh.numel() * 4)
+    del As_h, b_h
     if rank != 0:
         return
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel, k_slab (the fused sampled products a6-a8, one launch per
+    # Richardson iteration plus the final check). Algorithmic bytes per launch, per the
+    # method's own accounting: per distinct sampled row its last-mode index (2 B), weight
+    # (4 B) and b~ (4 B); per non-empty cell its Y row read and W row written, 2 R_N 4 B.
     peaks, peak_kind = load_peaks()
     hbm = float(peaks["hbm_gbs"])
     I, R = w["I"], w["R"]
-    ncell = int(np.prod(I[:-1]))
     RT, R2 = R[-1], R[-2]
-    distinct = rep_t["distinct"]
-    if tim["slab"][1]:
-        # fused slab pass: per distinct row 8 B and 4 R_N flops (dot + axpy); per non-empty
-        # cell a 16 B descriptor and 4 R_{N-1} R_N flops (its Y row and its share of Z);
-        # X1 read and Z written once (P x R_{N-1} x R_N floats each)
-        nact = nonempty_cells(kr, As_d, b_d, rep_t["s"], w["solve_seed"], args.steps, I[-1])
-        P = int(np.prod(I[:-2]))
-        alg_bytes = distinct * 8 + nact * 16 + 2 * P * R2 * RT * 4
-        alg_flops = distinct * 4 * RT + nact * 4 * R2 * RT
-        ms_r, n_r = tim["slab"]
-        kname = "k_slab (fused last-two-mode products + sampled residual, a6-a8)"
-    else:
-        # per-cell residual pass: per distinct row 8 B, per cell 8 R_N + 12 B
-        nact = None
-        alg_bytes = distinct * 8 + ncell * (8 * RT + 12)
-        alg_flops = distinct * 4 * RT
-        ms_r, n_r = tim["resid"]
-        kname = "k_resid (sampled residual + transpose, a7+a8)"
-    t_launch = ms_r / n_r / 1000.0 if n_r else None
-    gbs = alg_bytes / t_launch / 1e9 if n_r else None
-    tflops = alg_flops / t_launch / 1e12 if n_r else None
-    # FP32 FMA roof: 152 SMs x 128 lanes x 2 flops x the maximum SM clock
-    alu_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    if n_r and tflops / alu_peak > gbs / hbm:
-        roof = dict(bound="alu", achieved=tflops, peak=alu_peak, unit="TFLOP/s", frac=tflops / alu_peak,
-                    peak_source="FP32 FMA: 152 SMs x 128 lanes x 2 x %.0f MHz" % float(peaks.get("sm_max_mhz", 2070.0)),
-                    hbm_gbs=gbs, hbm_frac=gbs / hbm)
-    else:
-        roof = dict(bound="hbm", achieved=gbs, peak=hbm, unit="GB/s", frac=(gbs / hbm if gbs else None),
-                    peak_source=peak_kind, alu_tflops=tflops, alu_frac=(tflops / alu_peak if tflops else None))
-    roof.update(kernel=kname, traffic=slab_traffic() if tim["slab"][1] else None, alg_bytes_per_launch=alg_bytes,
-                alg_flops_per_launch=alg_flops, nonempty_cells=nact, avg_launch_ms=(ms_r / n_r if n_r else None))
+    distinct, cells = sketch_stats(kr, As_d, b_d, rep_t["s"], w["solve_seed"], args.steps, I[-1])
+    alg_bytes = distinct * 10 + cells * 2 * RT * 4
+    P = int(np.prod(I[:-2]))
+    fused_bytes = distinct * 8 + cells * 16 + 2 * P * R2 * RT * 4
+    alg_flops = distinct * 4 * RT + cells * 4 * R2 * RT
+    ms_r, n_r = tim["slab"]
+    t_launch = ms_r / n_r / 1000.0
+    gbs = alg_bytes / t_launch / 1e9
+    traffic, traffic_note = slab_traffic(args.workload)
+    roof = dict(bound="hbm", achieved=gbs, peak=hbm, unit="GB/s", frac=gbs / hbm,
+                peak_source="%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind, traffic=traffic,
+                kernel="k_slab (fused sampled products a6-a8: last-two-mode products, residual, transpose)",
+                alg_bytes_per_launch=alg_bytes, bytes_rule="10 B per distinct sampled row + 2 R_N 4 B per non-empty cell",
+                distinct_rows=distinct, nonempty_cells=cells, launches=n_r, avg_launch_ms=ms_r / n_r,
+                fused_kernel_bytes_per_launch=fused_bytes, fused_kernel_gbs=fused_bytes / t_launch / 1e9,
+                flops_per_launch=alg_flops, tflops=alg_flops / t_launch / 1e12)
+    if traffic_note:
+        roof["traffic_note"] = traffic_note
     total_timed = sum(v[0] for v in tim.values())
     shares = {k: (round(v[0] / total_timed, 4) if total_timed else None) for k, v in tim.items()}
-    mean = lambda key: float(np.mean([r[key] for r in reps]))
+    mean = lambda rs, key: float(np.mean([r[key] for r in rs]))
+    iters = mean(reps, "iters")
+    t_iter = np.mean([r["t_ms"]["iterate"] for r in reps]) / 1000.0
     line = dict(
         metric=METRIC, value=value, unit="rows/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=elapsed_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
-        data="synthetic",
-        config=dict(workload=w["name"], I=w["I"], R=w["R"], eps=w["eps"], s=s, parallelism="replicas",
-                    l2="inputs larger than L2 (b = %d MB)" % (b.nbytes >> 20)),
-        time_to_solve_ms=elapsed_ms / args.steps,
-        iters=mean("iters"), distinct=mean("distinct"),
-        iter_rows_per_s=mean("distinct") * mean("iters") / (mean("iters") and np.mean([r["t_ms"]["iterate"] for r in reps]) / 1000.0),
-        approx_ratio_max=max(ratios), certified_1_plus_eps=certified,
+        data="synthetic (seeded device generator: outlier factors, Tucker right-hand side + noise)",
+        config=dict(workload=args.workload, I=I, R=R, eps=eps, lam=lam, s=s, parallelism="replicas",
+                    stop_rule="(1+eps)-aware (theta = 0.01)",
+                    l2="inputs larger than L2 (b = %d MB)" % (b32.nbytes >> 20)),
+        time_to_solve_ms=elapsed_ms / args.steps, iters=iters, distinct=mean(reps, "distinct"),
+        iter_rows_per_s=mean(reps, "distinct") * iters / t_iter if t_iter > 0 else None,
+        approx_ratio_max=max(ratios), certified_1_plus_eps=certified, opt=opt, opt_source="oracle FP64 closed form",
+        step_rule=dict(tol=1e-7, ms_per_solve=step_ms, iters=mean(step_reps, "iters")),
         roofline=dict(roof, kernel_time_shares=shares),
         e2e=dict(value=e2e, unit="rows/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
                  b_read="in place at the sampled rows (page-locked host b mapped into the device's address space)",
-                 copy_all_b=dict(value=e2e_copy, unit="rows/s", h2d_bytes_per_step=int(b.nbytes + sum(A.nbytes for A in As)))),
+                 copy_all_b=dict(value=e2e_copy, unit="rows/s",
+                                 h2d_bytes_per_step=int(b32.nbytes + sum(A.numel() * 4 for A in As_d)))),
         gpu_launches=int(launches),
-        clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"]),
+        clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"], samples=clk["samples"]),
         phases_ms={k: float(np.mean([r["t_ms"][k] for r in reps])) for k in reps[0]["t_ms"]},
     )
     if not args.no_cpu_baseline:
-        v, s_c, dt = oracle_rows_per_s(As, b, int(round(mean("iters"))), args.cpu_fraction)
+        it_c = max(1, min(int(round(iters)), args.cpu_iters))
+        v, s_c, dt = oracle_rows_per_s(w, As64, b32, it_c, args.cpu_fraction)
         line["cpu_baseline"] = dict(
             value=v, unit="rows/s", cores=os.cpu_count(), kind="oracle",
-            sample="%d of the %d draws (%.3g), full tables, grouping, gather and %d FP64 Richardson iterations"
-                   % (s_c, s, args.cpu_fraction, int(round(mean("iters")))), seconds=dt)
+            sample="%d of the %d draws (%.3g), full tables, grouping, gather and %d FP64 Richardson iteration(s)"
+                   % (s_c, s, args.cpu_fraction, it_c), seconds=dt)
     print(json.dumps(line), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--cpu-fraction", type=float, default=0.1)
-    ap.add_argument("--ref-fraction", type=float, default=0.01)
-    ap.add_argument("--ref-iters", type=int, default=20)
+    ap.add_argument("--workload", default="kron_n3_1024x64_outliers", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-fraction", type=float, default=0.005)
+    ap.add_argument("--cpu-iters", type=int, default=2)
+    ap.add_argument("--ref-fraction", type=float, default=0.001)
+    ap.add_argument("--ref-iters", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank, world, local = dist_setup(args)

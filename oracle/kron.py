@@ -226,21 +226,25 @@ def sampled_forward(As, keys, x, chunk=1 << 20):
     return u
 
 
-def sampled_transpose(As, keys, r, chunk=1 << 20):
-    """K^T restricted to the sampled rows applied to r: sum_j r_j K[key_j, :]."""
+def sampled_transpose(As, keys, r):
+    """K^T restricted to the sampled rows applied to r: sum_j r_j K[key_j, :].
+
+    With the rows split as in Thm 4.4 (cells = the first N-1 coordinates, T = {N}):
+    W[cell, :] = sum_{j in cell} r_j A_N[i_N(j), :], i.e. W = S A_N for the sparse
+    cells x I_N matrix S holding r_j at (cell_j, i_N(j)) (a library sparse-dense
+    product), then W x_1 A_1^T ... x_{N-1} A_{N-1}^T."""
+    import scipy.sparse as sp
+
     N = len(As)
     I = [A.shape[0] for A in As]
     R = [A.shape[1] for A in As]
     ncell = int(np.prod(I[:-1])) if N > 1 else 1
     AT = np.asarray(As[-1], dtype=np.float64)
-    W = np.zeros((ncell, R[-1]), dtype=np.float64)
     keys = np.asarray(keys, dtype=np.int64)
     r = np.asarray(r, dtype=np.float64)
-    for a in range(0, keys.shape[0], chunk):
-        cell, it = np.divmod(keys[a:a + chunk], I[-1])
-        contrib = AT[it] * r[a:a + chunk, None]
-        for q in range(R[-1]):
-            W[:, q] += np.bincount(cell, weights=contrib[:, q], minlength=ncell)
+    cell, it = np.divmod(keys, I[-1])
+    S = sp.csr_matrix((r, (cell, it)), shape=(ncell, I[-1]))
+    W = np.asarray(S @ AT)
     G = W.reshape(list(I[:-1]) + [R[-1]])
     for n in range(N - 1):
         G = mode_product(G, np.asarray(As[n], dtype=np.float64).T, n)

@@ -7,6 +7,7 @@ import pytest
 import torch
 
 import paper_2209_04876_gb300 as kr
+from _parity import assert_elementwise, solution_bar
 from oracle import kron as ko
 from workloads import kron_problem
 
@@ -61,20 +62,22 @@ def test_batched_matches_individual_solves(workers):
 
 
 def test_batched_against_oracle():
-    """One problem of the batch against the oracle's solve on the same sample."""
+    """Every problem of the batch against the oracle's solve on the same sample."""
     probs = _problems()
     lam, eps, seed, cid = 1e-3, 0.1, 12, 70
     xs, reps = kr.kron_ridge_batched([([dev(A) for A in As], dev(b)) for As, b in probs], lam, eps=eps, seed=seed,
                                      call_id=cid, tol=1e-7, max_iter=300)
-    p = 4
-    As = [A.astype(np.float64) for A in probs[p][0]]
-    b = probs[p][1].astype(np.float64)
-    t = kr.kron_leverage([dev(A) for A in probs[p][0]])
-    smp = ko.draw_sample(As, reps[p]["s"], seed, cid + p, cdfs=[c.cpu().numpy() for c in t["cdf"]],
-                         probs=[q.cpu().numpy() for q in t["prob"]])
-    xs_ref, _ = ko.richardson(As, b[smp.keys], smp, lam, eps, tol=1e-13, max_iter=5000)
-    got = xs[p].cpu().numpy().astype(np.float64)
-    assert np.linalg.norm(got - xs_ref) <= 1e-5 * np.linalg.norm(xs_ref)
+    for p in range(len(probs)):
+        As = [A.astype(np.float64) for A in probs[p][0]]
+        b = probs[p][1].astype(np.float64)
+        t = kr.kron_leverage([dev(A) for A in probs[p][0]])
+        smp = ko.draw_sample(As, reps[p]["s"], seed, cid + p, cdfs=[c.cpu().numpy() for c in t["cdf"]],
+                             probs=[q.cpu().numpy() for q in t["prob"]])
+        assert smp.keys.shape[0] == reps[p]["distinct"]
+        xs_ref, _ = ko.richardson(As, b[smp.keys], smp, lam, eps, tol=1e-13, max_iter=5000)
+        got = xs[p].cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(got - xs_ref) <= 1e-5 * np.linalg.norm(xs_ref), p
+        assert_elementwise(got, xs_ref, solution_bar(As), "x of problem %d" % p)
 
 
 def test_batched_reports_first_hard_error():

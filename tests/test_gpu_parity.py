@@ -1,9 +1,11 @@
 """GPU parity: every step of the hot path, through the C ABI, against the CPU oracle.
 
 Bars: bit-exact for integer work (sampled indices, grouping, multiplicities, gathers);
-FP64 steps (leverage, CDF) to 1e-9 relative; FP32 products to 1e-5 relative (norm-wise,
-a few ulps times the reduction length); solutions of the FP32 path within 1e-5
-relative of the oracle's exact minimiser of the same sampled problem.
+FP64 steps (leverage, CDF) to 1e-9 relative; FP32 products to 1e-5 relative (a few ulps
+times the reduction length); solutions of the FP32 path within 1e-5 relative of the
+oracle's exact minimiser of the same sampled problem. Every floating-point comparison is
+made twice: norm-wise, and element by element (each component within the bar times the
+reference's largest component; the worst component is reported).
 """
 import math
 
@@ -12,6 +14,7 @@ import pytest
 import torch
 
 import paper_2209_04876_gb300 as kr
+from _parity import assert_elementwise, precond_bar, solution_bar, worst_component
 from oracle import kron as ko
 from workloads import kron_problem
 
@@ -70,6 +73,7 @@ def test_leverage_cdf_prob(I, R):
         lev_o = ko.leverage_scores(A)
         lev_g = host(t["lev"][n])
         assert rel(lev_g, lev_o) < 1e-9
+        assert_elementwise(lev_g, lev_o, 1e-9, "leverage scores")
         assert abs(lev_g.sum() - R[n]) < 1e-9 * R[n]
         # same CDF convention as the oracle, bit for bit, given the same scores
         np.testing.assert_array_equal(cdfs[n], ko.cdf_table(lev_g))
@@ -205,9 +209,11 @@ def test_kron_matmul(I, R):
     x = rng.standard_normal(int(np.prod(R))).astype(np.float32)
     y = kr.kron_matmul([dev(A) for A in As], dev(x))
     assert rel(host(y), ko.kron_matvec(As, x)) < 1e-5
+    assert_elementwise(host(y), ko.kron_matvec(As, x), 1e-5, "KronMatMul")
     z = rng.standard_normal(int(np.prod(I))).astype(np.float32)
     g = kr.kron_matmul([dev(A) for A in As], dev(z), trans=[1] * len(As))
     assert rel(host(g), ko.kron_rmatvec(As, z)) < 1e-5
+    assert_elementwise(host(g), ko.kron_rmatvec(As, z), 1e-5, "transposed KronMatMul")
 
 
 @pytest.mark.parametrize("I,R", SHAPES)
@@ -216,8 +222,15 @@ def test_preconditioner(I, R, lam):
     As = f32_factors(kron_problem(I, R, dist="lognormal_rows", seed=8)["As"])
     g = np.random.default_rng(9).standard_normal(int(np.prod(R))).astype(np.float32)
     d = kr.kron_precond([dev(A) for A in As], dev(g), lam)
-    ref = ko.KronPreconditioner(As, lam).apply(g)
-    assert rel(host(d), ref) < (1e-5 if lam == 0 else 1e-4)
+    P = ko.KronPreconditioner(As, lam)
+    ref = P.apply(g)
+    kappa = float(P.D.max() / P.D.min())
+    err = rel(host(d), ref)
+    print("precond I=%s R=%s lam=%g: rel %.3e, elementwise %.3e, kappa(M) %.3e" % (
+        I, R, lam, err, worst_component(host(d), ref)[0], kappa))
+    bar = precond_bar(As, lam)
+    assert err < bar, (err, bar)
+    assert_elementwise(host(d), ref, bar, "M+ g (bar %.2e)" % bar)
 
 
 # ------------------------------------------------------------------ a7 + a8
@@ -238,6 +251,7 @@ def test_sampled_residual_products(I, R):
     r = om * (b[keys] - u)
     g_ref = ko.sampled_transpose(As, keys, r)
     assert rel(host(g), g_ref) < 1e-5
+    assert_elementwise(host(g), g_ref, 1e-5, "K~^T Omega (b~ - K~ x)")
     assert abs(obj - np.sum(om * (b[keys] - u) ** 2)) <= 1e-5 * np.sum(om * (b[keys] - u) ** 2)
     sk.free()
 
@@ -271,6 +285,7 @@ def test_regress_matches_oracle_on_same_sample(I, R, dist):
     cdfs, probs, _ = tables(As)
     xs, smp = _oracle_same_sample(As, b, rep, seed, cid, cdfs, probs, 0.0, eps)
     assert rel(host(x), xs) <= 1e-5
+    assert_elementwise(host(x), xs, solution_bar(As), "x")
     f_s = ko.sampled_objective(As, b[smp.keys], smp, host(x).astype(np.float64), 0.0)
     assert abs(rep["obj_sampled"] - f_s) <= 1e-5 * f_s
     # the (1 + eps) guarantee of Thm 4.5 for this seed
@@ -290,6 +305,7 @@ def test_ridge_matches_oracle_on_same_sample(I, R, lam):
     cdfs, probs, _ = tables(As)
     xs, smp = _oracle_same_sample(As, b, rep, seed, cid, cdfs, probs, lam, eps)
     assert rel(host(x), xs) <= 1e-5
+    assert_elementwise(host(x), xs, solution_bar(As), "x")
     opt = ko.objective(As, b, ko.closed_form_ridge(As, b, lam), lam)
     assert ko.objective(As, b, host(x), lam) <= (1 + eps) * opt
 

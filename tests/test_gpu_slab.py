@@ -13,6 +13,7 @@ import pytest
 import torch
 
 import paper_2209_04876_gb300 as kr
+from _parity import assert_elementwise, solution_bar
 from oracle import kron as ko
 from workloads import kron_problem, tucker_init, tucker_tensor
 
@@ -110,6 +111,7 @@ def test_slab_pass_matches_oracle(I, R, dist, zero, budget):
     assert rep["converged"]
     xs, smp = _oracle(As, b, rep, 0.0)
     assert rel(host(x), xs) <= 1e-5
+    assert_elementwise(host(x), xs, solution_bar(As), "x")
     f_s = ko.sampled_objective(As, b[smp.keys], smp, host(x), 0.0)
     assert abs(rep["obj_sampled"] - f_s) <= 1e-5 * f_s
 
@@ -122,6 +124,7 @@ def test_slab_pass_ridge_matches_oracle(I, R):
     assert launches["slab"][1] > 0
     xs, _ = _oracle(As, b, rep, lam)
     assert rel(host(x), xs) <= 1e-5
+    assert_elementwise(host(x), xs, solution_bar(As), "x")
 
 
 @pytest.mark.parametrize("I,R,dist,zero", [SHAPES[2], SHAPES[4], SHAPES[8]])
@@ -132,6 +135,7 @@ def test_slab_and_per_cell_forms_agree(I, R, dist, zero):
     assert la["slab"][1] > 0 and lb["slab"][1] == 0 and lb["resid"][1] > 0
     assert ra["distinct"] == rb["distinct"]
     assert rel(host(xa), host(xb)) <= 2e-5
+    assert_elementwise(host(xa), host(xb), 2e-5, "slab vs per-cell x")
     assert abs(ra["obj_sampled"] - rb["obj_sampled"]) <= 1e-5 * rb["obj_sampled"]
 
 

@@ -11,6 +11,7 @@ import pytest
 import torch
 
 import paper_2209_04876_gb300 as kr
+from _parity import assert_elementwise
 from oracle import kron as ko
 from oracle import tucker as tk
 from workloads import tucker_init, tucker_tensor
@@ -69,6 +70,7 @@ def test_factor_update_matches_oracle_rows(I, R, lam):
         # up to cond(G_(n)) (Lemma 5.1 substitution); otherwise the FP32-path bar of 1e-5
         bar = max(1e-5, 4 * np.finfo(np.float32).eps * np.linalg.cond(tk.unfold(G, n)))
         assert err.max() <= bar, (n, err.max(), bar)
+        assert_elementwise(got, A_ref, bar, "A[%d] (bar %.2e)" % (n, bar))
         for m in others:  # only A[n] changes
             np.testing.assert_array_equal(host(A_gpu[m]), np.asarray(As[m], np.float32))
 

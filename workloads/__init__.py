@@ -18,10 +18,10 @@ float32 for the device):
 * ``tucker_tensor``: X = G x_1 Q1 ... x_N QN + noise, G ~ N(0,1)^{R}, Qn orthonormal
   (QR of a Gaussian), noise scaled to ``noise_rel * ||signal||``.
 * ``batched_shapes``: per-problem I_n ~ U{lo..hi}, R_n ~ U{rlo..rhi}.
-* ``kron_problem_device``: the ``kron_problem`` recipe (b_kind 'kron', relative noise)
-  generated in float32 on a CUDA device with torch's seeded generator, for batches whose
-  right-hand sides (up to 4 GB each) are too slow to build on the host. Same recipe, not
-  the same numbers as the numpy generator.
+* ``kron_problem_device``: the ``kron_problem`` recipe (b_kind 'kron' or 'tucker', relative
+  noise) generated in float32 on a CUDA device with torch's seeded generator, for batches and
+  workloads whose right-hand sides (up to 4 GB each) are too slow to build on the host. Same
+  recipe, not the same numbers as the numpy generator.
 """
 import numpy as np
 
@@ -85,8 +85,11 @@ def kron_problem(I, R, dist="gauss", seed=0, noise_abs=None, noise_rel=None, b_k
     return dict(As=As, b=b, x_true=x_true, I=I, R=R)
 
 
-def kron_problem_device(I, R, dist="gauss", seed=0, noise_rel=0.01, sigma=1.0, device="cuda"):
-    """Returns dict(As=[float32 I_n x R_n on device], b=float32 (prod I) on device, x_true, I, R)."""
+def kron_problem_device(I, R, dist="gauss", seed=0, noise_rel=0.01, sigma=1.0, device="cuda", b_kind="kron",
+                        tucker_rank=None):
+    """Returns dict(As=[float32 I_n x R_n on device], b=float32 (prod I) on device, x_true, I, R).
+    b_kind 'kron': b = K x_true + noise; 'tucker': b = a rank-(r,...,r) Tucker tensor (Gaussian
+    core and factors, independent of the A(n)) + noise, x_true None."""
     import torch
 
     I = [int(v) for v in I]
@@ -104,9 +107,18 @@ def kron_problem_device(I, R, dist="gauss", seed=0, noise_rel=0.01, sigma=1.0, d
         elif dist != "gauss":
             raise ValueError(dist)
         As.append(A.contiguous())
-    x_true = torch.randn(int(np.prod(R)), generator=g, device=device)
-    T = x_true.reshape(R)
-    for n, A in enumerate(As):
+    if b_kind == "kron":
+        x_true = torch.randn(int(np.prod(R)), generator=g, device=device)
+        T = x_true.reshape(R)
+        facs = As
+    elif b_kind == "tucker":
+        r = [int(v) for v in (tucker_rank or R)]
+        x_true = None
+        T = torch.randn(*r, generator=g, device=device)
+        facs = [torch.randn(In, rn, generator=g, device=device) for In, rn in zip(I, r)]
+    else:
+        raise ValueError(b_kind)
+    for n, A in enumerate(facs):
         T = torch.movedim(torch.tensordot(A, T, dims=([1], [n])), 0, n)
     b = T.reshape(-1).contiguous()
     del T
