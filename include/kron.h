@@ -173,9 +173,11 @@ enum {
  *    1 sorts the row keys (stable LSD radix sort) and merges the runs of equal keys; 2 sets
  *    one bit per draw in a bitmap of the key space (prod I_n keys, times the factor rows of an
  *    Alg. 3 step; at most 2^32; 8 bytes of workspace per 32 keys), ranks the set bits and
- *    counts the draws per rank with integer
- *    atomics; 0 takes 2 when the key space is at most 64 times the draw count, else 1. Both
- *    give identical sketches.
+ *    counts the draws per rank with integer atomics; 3 ranks the same bitmap but every draw
+ *    adds one to a dense per-key counter (4 bytes per key, kept by the context, all zero
+ *    between calls) and only a key's first draw sets its bit, so no key is written per draw;
+ *    0 takes 3 when the key space is at most 64 times the draw count and its counters fit in
+ *    4 GB, else 2 when the first holds, else 1. All give identical sketches.
  *  KR_OPT_HOST_GATHER (default 1): host-buffer solves (kr_opts.host_io) with b in
  *    page-locked host memory (cudaHostAlloc / cudaHostRegister, mapped into the device's
  *    address space) gather the sampled entries b~ = S b in place, reading s of the prod I

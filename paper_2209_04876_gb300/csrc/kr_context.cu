@@ -90,7 +90,7 @@ extern "C" kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value) {
       ctx->batch_workers = (int)value;
       return KR_OK;
     case KR_OPT_GROUPING:
-      if (value < 0 || value > 2) return kr_fail(ctx, KR_EINVAL, "kr_set_option: grouping must be 0, 1 or 2");
+      if (value < 0 || value > 3) return kr_fail(ctx, KR_EINVAL, "kr_set_option: grouping must be 0, 1, 2 or 3");
       ctx->grouping = (int)value;
       return KR_OK;
     case KR_OPT_HOST_GATHER:
@@ -121,6 +121,7 @@ extern "C" void kr_destroy(kr_ctx* ctx) {
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->io) cudaFree(ctx->io);
   if (ctx->split_buf) cudaFree(ctx->split_buf);
+  if (ctx->dcnt) cudaFree(ctx->dcnt);
   if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
   for (int i = 0; i < 10; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);

@@ -30,6 +30,11 @@ struct kr_ctx {
   // pinned host buffer for small read-backs
   char* hbuf = nullptr;
   size_t hbuf_size = 0;
+  // dense per-key draw counters of the rank grouping (grown on demand; all zero between
+  // sketch builds, dcnt_clean false while a build that uses them is in flight on the host)
+  uint32_t* dcnt = nullptr;
+  size_t dcnt_size = 0;
+  bool dcnt_clean = false;
   // options (kr_set_option)
   int slab_pass = 1;
   uint32_t slab_tile_entries = 16384;

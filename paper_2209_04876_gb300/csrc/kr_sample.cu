@@ -134,12 +134,15 @@ __device__ __forceinline__ int guided_search(const uint64_t* thr, const uint16_t
 // (i_1..i_{N-1}) for draw batch r, the linear row index of the batched system). Draws
 // come in nrow batches of s_row (one per Tucker factor row; nrow = 1 for a plain solve);
 // draw t of batch r uses Philox counter row row0 + r. With a key bitmap (grouping by
-// rank, below) every draw also sets its key's bit there. Templated on N so the per-draw
-// indices and table pointers stay in registers.
+// rank, below) every draw also sets its key's bit there. With dense counts (dcnt: one
+// counter per key of the key space, zero on entry) a draw adds one to its key's counter
+// instead of writing the key, and only the first draw of a key (the counter was 0) sets
+// its bit. Templated on N so the per-draw indices and table pointers stay in registers.
 template <int N>
 __global__ void __launch_bounds__(256) k_draw_keys(DrawModes dm, int64_t s_row, int nrow, uint32_t k0, uint32_t k1,
                                                    uint32_t row0, uint32_t cid, uint32_t ncell_inner,
-                                                   uint32_t* __restrict__ keys, uint2* __restrict__ bm) {
+                                                   uint32_t* __restrict__ keys, uint2* __restrict__ bm,
+                                                   uint32_t* __restrict__ dcnt) {
   __shared__ uint64_t s_thr[THR_SMEM];
   __shared__ uint16_t s_guide[THR_SMEM];
   const uint64_t* thr[N];
@@ -194,8 +197,12 @@ __global__ void __launch_bounds__(256) k_draw_keys(DrawModes dm, int64_t s_row, 
     for (int n = 0; n < N - 1; ++n) cell = cell * (uint32_t)In[n] + (uint32_t)idx[n];
     cell += r * ncell_inner;
     const uint32_t key = cell * IT + (uint32_t)idx[N - 1];
-    keys[t] = key;
-    if (bm) atomicOr(&bm[key >> 5].x, 1u << (key & 31));
+    if (dcnt) {
+      if (atomicAdd(dcnt + key, 1u) == 0u) atomicOr(&bm[key >> 5].x, 1u << (key & 31));
+    } else {
+      keys[t] = key;
+      if (bm) atomicOr(&bm[key >> 5].x, 1u << (key & 31));
+    }
   }
 }
 
@@ -443,14 +450,16 @@ __global__ void __launch_bounds__(RLE_THREADS) k_bm_tcount(const uint2* __restri
 }
 
 // Ranks: bm[w].y = distinct keys before word w (toff: exclusive scan of the tile counts),
-// dk[d] = the d-th distinct key, cnt[d] = 0 (the counts are added next). A thread ranks
-// BM_ITEMS consecutive words of the tile (staged in shared memory); the tile's keys are
-// collected in shared memory and written out coalesced (a dense tile with more than
-// BM_KEYCAP keys writes them directly). The last tile sets meta[0] = distinct keys.
+// dk[d] = the d-th distinct key, cnt[d] = 0 (the counts are added next by k_bm_count) or,
+// with dense counts, cnt[d] = dcnt[dk[d]], after which that counter is reset to zero (so
+// the dense counters are all zero again once every tile has run). A thread ranks BM_ITEMS
+// consecutive words of the tile (staged in shared memory); the tile's keys are collected
+// in shared memory and written out coalesced (a dense tile with more than BM_KEYCAP keys
+// writes them directly). The last tile sets meta[0] = distinct keys.
 __global__ void __launch_bounds__(RLE_THREADS) k_bm_rank(uint2* __restrict__ bm, int64_t nw,
                                                          const uint32_t* __restrict__ toff, int ntile,
                                                          uint32_t* __restrict__ dk, uint32_t* __restrict__ cnt,
-                                                         uint32_t* __restrict__ meta) {
+                                                         uint32_t* __restrict__ meta, uint32_t* __restrict__ dcnt) {
   __shared__ uint32_t sh[RLE_THREADS / 32 + 1];
   __shared__ uint32_t bits[BM_TILE + BM_TILE / 32];
   __shared__ uint32_t pre[BM_TILE + BM_TILE / 32];
@@ -494,8 +503,15 @@ __global__ void __launch_bounds__(RLE_THREADS) k_bm_rank(uint2* __restrict__ bm,
     if (w < nw) bm[w].y = pre[PADJ(j)];
   }
   for (uint32_t j = threadIdx.x; j < tot; j += RLE_THREADS) {
-    if (staged) dk[off + j] = skeys[j];
-    cnt[off + j] = 0u;
+    // (unstaged keys were written by other threads of the block before the barrier above)
+    const uint32_t key = staged ? skeys[j] : dk[off + j];
+    if (staged) dk[off + j] = key;
+    if (dcnt) {
+      cnt[off + j] = dcnt[key];
+      dcnt[key] = 0u;
+    } else {
+      cnt[off + j] = 0u;
+    }
   }
   if (blockIdx.x == ntile - 1 && threadIdx.x == 0) meta[0] = off + tot;
 #undef PADJ
@@ -637,8 +653,41 @@ kr_status kr_sketch_check(kr_ctx* ctx, const Modes& m, int64_t s) {
 bool kr_group_by_rank(const kr_ctx* ctx, int64_t s, int64_t keyspace) {
   if (keyspace > (int64_t(1) << 32)) return false;
   if (ctx->grouping == 1) return false;
-  if (ctx->grouping == 2) return true;
+  if (ctx->grouping == 2 || ctx->grouping == 3) return true;
   return keyspace <= 64 * s;
+}
+
+// Grouping by rank with dense per-key counters (the default form of it): the key space's
+// counters (4 bytes per key) must fit the budget.
+static bool kr_group_dense(const kr_ctx* ctx, int64_t s, int64_t keyspace) {
+  if (!kr_group_by_rank(ctx, s, keyspace) || ctx->grouping == 2) return false;
+  return keyspace * (int64_t)sizeof(uint32_t) <= (int64_t(4) << 30);
+}
+
+// The context's dense per-key counters, all zero between sketch builds (the rank kernel
+// resets every counter it reads); grown on demand, zeroed when (re)allocated or left dirty
+// by an interrupted build.
+static kr_status kr_dcnt_reserve(kr_ctx* ctx, int64_t keys) {
+  const size_t bytes = (size_t)keys * sizeof(uint32_t);
+  if (bytes > ctx->dcnt_size) {
+    KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->dcnt) cudaFree(ctx->dcnt);
+    ctx->dcnt = nullptr;
+    ctx->dcnt_size = 0;
+    cudaError_t e = cudaMalloc((void**)&ctx->dcnt, bytes);
+    if (e != cudaSuccess) {
+      ctx->dcnt = nullptr;
+      cudaGetLastError();
+      return kr_fail(ctx, KR_ENOMEM, "dense key counters: allocation of %zu bytes failed", bytes);
+    }
+    ctx->dcnt_size = bytes;
+    ctx->dcnt_clean = false;
+  }
+  if (!ctx->dcnt_clean) {
+    KR_CUDA(ctx, cudaMemsetAsync(ctx->dcnt, 0, ctx->dcnt_size, ctx->stream));
+    ctx->dcnt_clean = true;
+  }
+  return KR_OK;
 }
 
 // Second phase of the sketch build, with scratch carved from `cv`: draw the row keys,
@@ -658,6 +707,7 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   uint16_t* gbuf = cv.take<uint16_t>((size_t)KR_MAX_MODES * GUIDE_MAX);
   const int64_t keyspace = ncell * (int64_t)IT;
   const bool ranked = kr_group_by_rank(ctx, s, keyspace);
+  const bool dense = kr_group_dense(ctx, s, keyspace);
   const int64_t nw = ranked ? (keyspace + 31) / 32 : 0;
   const int nbt = (int)((nw + BM_TILE - 1) / BM_TILE);
   uint2* bm = ranked ? cv.take<uint2>(nw) : nullptr;
@@ -680,13 +730,19 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   KR_CUDA(ctx, cudaMemsetAsync(sk->cell_nd, 0, sizeof(uint32_t) * ncell, ctx->stream));
   KR_CUDA(ctx, cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), ctx->stream));
   if (ranked) KR_CUDA(ctx, cudaMemsetAsync(bm, 0, sizeof(uint2) * nw, ctx->stream));
+  uint32_t* dcnt = nullptr;
+  if (dense) {
+    KR_TRY(kr_dcnt_reserve(ctx, keyspace));
+    dcnt = ctx->dcnt;
+    ctx->dcnt_clean = false;  // until the rank kernel below has been enqueued
+  }
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32), cid = (uint32_t)call_id;
   {
     const int gs = grid_for(ctx, s, 256);
 #define KR_DRAW_KEYS(NN)                                                                                         \
   case NN:                                                                                                       \
     KR_LAUNCH(ctx, k_draw_keys<NN>, gs, 256, 0, dm, sk->s_row, sk->nrow, k0, k1, (uint32_t)row, cid,             \
-              (uint32_t)sk->ncell_inner, keys, bm);                                                              \
+              (uint32_t)sk->ncell_inner, keys, bm, dcnt);                                                        \
     break;
     switch (N) {
       KR_DRAW_KEYS(1)
@@ -717,8 +773,11 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
       Carve sc = cv;
       KR_TRY(kr_scan_u32(ctx, btc, btc + nbt, nbt, sc));
     }
-    KR_LAUNCH(ctx, k_bm_rank, nbt, RLE_THREADS, 0, bm, nw, btc + nbt, nbt, alt, hp, meta);
-    KR_LAUNCH(ctx, k_bm_count, grid_for(ctx, s, 256), 256, 0, keys, s, bm, hp);
+    KR_LAUNCH(ctx, k_bm_rank, nbt, RLE_THREADS, 0, bm, nw, btc + nbt, nbt, alt, hp, meta, dcnt);
+    if (dense)
+      ctx->dcnt_clean = true;  // the rank kernel resets every counter the draws set
+    else
+      KR_LAUNCH(ctx, k_bm_count, grid_for(ctx, s, 256), 256, 0, keys, s, bm, hp);
     KR_LAUNCH(ctx, k_rle_ecount<true>, nrt, RLE_THREADS, 0, hp, meta, ecnt);
   } else {
     int nbits = 0;

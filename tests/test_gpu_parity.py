@@ -126,9 +126,10 @@ def test_sampler_edge_tables():
 
 # ------------------------------------------------------------------ a4 + a5
 
-@pytest.fixture(params=[1, 2], ids=["radix", "rank"])
+@pytest.fixture(params=[1, 2, 3], ids=["radix", "rank", "dense"])
 def grouping(request):
-    """Both groupings of the draws: radix sort + runs, ranks in a bitmap of the key space."""
+    """The groupings of the draws: radix sort + runs; ranks in a bitmap of the key space with
+    the counts added per draw; ranks with dense per-key counters set by the draws."""
     kr.set_option(kr.OPT_GROUPING, request.param)
     yield request.param
     kr.set_option(kr.OPT_GROUPING, 0)

@@ -187,7 +187,7 @@ def test_device_loop_stops_at_max_iter():
 def test_set_option_rejects_bad_values():
     for key, val in [(kr.OPT_SLAB_PASS, 2), (kr.OPT_SLAB_TILE_ENTRIES, 100), (kr.OPT_SLAB_TILE_ENTRIES, (1 << 22) + 1),
                      (kr.OPT_DEVICE_LOOP, 7), (kr.OPT_BATCH_WORKERS, 0), (kr.OPT_BATCH_WORKERS, 33),
-                     (kr.OPT_GROUPING, -1), (kr.OPT_GROUPING, 3), (kr.OPT_HOST_GATHER, 2), (99, 1)]:
+                     (kr.OPT_GROUPING, -1), (kr.OPT_GROUPING, 4), (kr.OPT_HOST_GATHER, 2), (99, 1)]:
         with pytest.raises(kr.KronError) as e:
             kr.set_option(key, val)
         assert e.value.name == "KR_EINVAL"
@@ -200,20 +200,22 @@ def test_set_option_rejects_bad_values():
     ([6, 70, 40], [2, 32, 32], "lognormal_rows", 0.0),
 ])
 def test_groupings_give_identical_solves(I, R, dist, lam):
-    """Radix sort + runs and ranks in a key bitmap build the same sketch, so whole solves
-    agree bit for bit (same merged rows, iterations and iterate)."""
+    """Radix sort + runs, ranks in a key bitmap with per-draw counts, and ranks with dense
+    per-key counters build the same sketch, so whole solves agree bit for bit (same merged
+    rows, iterations and iterate); repeated dense-counter builds leave the counters clean."""
     As, b = _problem(I, R, dist, seed=23)
     out = []
     try:
-        for g in (1, 2):
+        for g in (1, 2, 3, 3):
             kr.set_option(kr.OPT_GROUPING, g)
             x, rep, launches = _solve(As, b, lam, slab=True)
             out.append((host(x), rep))
     finally:
         kr.set_option(kr.OPT_GROUPING, 0)
-    (x1, r1), (x2, r2) = out
-    assert r1["distinct"] == r2["distinct"] and r1["iters"] == r2["iters"]
-    np.testing.assert_array_equal(x1, x2)
+    (x1, r1) = out[0]
+    for x2, r2 in out[1:]:
+        assert r1["distinct"] == r2["distinct"] and r1["iters"] == r2["iters"]
+        np.testing.assert_array_equal(x1, x2)
 
 
 def test_groupings_give_identical_tucker_factor_steps():
@@ -225,7 +227,7 @@ def test_groupings_give_identical_tucker_factor_steps():
     G = np.random.default_rng(5).standard_normal(R).astype(np.float32)
     got = []
     try:
-        for g in (1, 2):
+        for g in (1, 2, 3):
             kr.set_option(kr.OPT_GROUPING, g)
             A_gpu = [dev(A) for A in As]
             kr.tucker_factor_update(dev(X), A_gpu, dev(G), 1, 1e-3, eps=0.1, seed=9, call_id=2, tol=1e-7, max_iter=500)
@@ -233,3 +235,4 @@ def test_groupings_give_identical_tucker_factor_steps():
     finally:
         kr.set_option(kr.OPT_GROUPING, 0)
     np.testing.assert_array_equal(got[0], got[1])
+    np.testing.assert_array_equal(got[0], got[2])
