@@ -220,6 +220,10 @@ struct FactorTables {
   float* sig2[KR_MAX_MODES] = {};    // R: eigenvalues of A^T A (FP32)
   double* gram[KR_MAX_MODES] = {};   // R x R FP64
   double* linv[KR_MAX_MODES] = {};   // R x R FP64: inverse of the Cholesky factor of the Gram
+  double* V64[KR_MAX_MODES] = {};    // R x R: eigenvectors of A^T A (columns, FP64; with the eigen-decomposition)
+  double* sig64[KR_MAX_MODES] = {};  // R: eigenvalues of A^T A (FP64)
+  double sig_max[KR_MAX_MODES] = {}; // host copies of each mode's largest and smallest eigenvalue
+  double sig_min[KR_MAX_MODES] = {}; // (read back with the rank check when the eigen-decomposition is built)
   int rank[KR_MAX_MODES] = {};
 };
 

@@ -9,11 +9,14 @@
 // A^T A = V S^2 V^T when lambda > 0.
 //
 // Precision: Gram, Cholesky, triangular inverse, scores and CDF in FP64 (exact
-// FP32 x FP32 products, FP64 sums). The eigen-decomposition is FP32 Jacobi: the
-// preconditioner only needs to be a spectral approximation of the normal matrix
-// (Lemma 4.2), so its rounding affects the rate, not the fixed point. The Alg. 3 factor
-// step's Woodbury base (K^T K + w I)^-1 with w >> ||K^T K|| takes an FP64 Jacobi
-// (kr_eig64): there an orthogonality error e of V perturbs K^T K by about w e.
+// FP32 x FP32 products, FP64 sums). The eigen-decomposition of the lambda > 0
+// preconditioner is an FP64 Jacobi of the FP64 Gram, rounded to FP32 for the
+// application: the preconditioner has to be a spectral approximation of the normal matrix
+// (Lemma 4.2), and an FP32 Jacobi's eigenvalues carry absolute errors of about
+// u32 ||G||, which for nearly rank-one factors (the paper's synthetic workload, cond(G)
+// near 1e8) exceed the small eigenvalues themselves. The Alg. 3 factor step's Woodbury
+// base (K^T K + w I)^-1 with w >> ||K^T K|| takes the same FP64 Jacobi (kr_eig64): there
+// an orthogonality error e of V perturbs K^T K by about w e.
 #include <math.h>
 
 #include "kr_internal.cuh"
@@ -412,6 +415,26 @@ __global__ void k_jacobi(JacobiArgs<T> ja) {
   for (int i = tid; i < R; i += blockDim.x) ja.sig2[n][i] = jac_max(A[i * LD + i], zero);
 }
 
+// FP32 copies of the FP64 eigenpairs, all modes in one grid (mode n's R x R vectors then
+// its R values, in mode order).
+__global__ void k_eig_to_f32(ModePtrs mp, const double* const* unused, double* const* V64, double* const* s64) {
+  (void)unused;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int n = 0; n < mp.N; ++n) {
+    const int R = mp.R[n], rr = R * R;
+    if (e < rr) {
+      mp.V[n][e] = (float)V64[n][e];
+      return;
+    }
+    e -= rr;
+    if (e < R) {
+      mp.sig2[n][e] = (float)s64[n][e];
+      return;
+    }
+    e -= R;
+  }
+}
+
 }  // namespace
 
 kr_status kr_eig64(kr_ctx* ctx, int nmat, const int* R, const double* const* gram, double* const* V,
@@ -446,12 +469,16 @@ void kr_tables_need(const Modes& m, bool want_eig, Need& nd) {
     if (want_eig) {
       nd.add<float>((size_t)R * R);
       nd.add<float>(R);
+      nd.add<double>((size_t)R * R);  // FP64 eigenvectors
+      nd.add<double>(R);              // FP64 eigenvalues
     }
   }
   nd.add<int>(KR_MAX_MODES);
 }
 
 kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv, FactorTables& t, bool check_rank) {
+  double* V64[KR_MAX_MODES] = {};
+  double* s64[KR_MAX_MODES] = {};
   ModePtrs mp = {};
   mp.N = m.N;
   t.N = m.N;
@@ -472,6 +499,8 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
     if (want_eig) {
       mp.V[n] = t.V[n] = cv.take<float>((size_t)R * R);
       mp.sig2[n] = t.sig2[n] = cv.take<float>(R);
+      V64[n] = t.V64[n] = cv.take<double>((size_t)R * R);
+      s64[n] = t.sig64[n] = cv.take<double>(R);
     }
     maxI = I > maxI ? I : maxI;
   }
@@ -480,17 +509,8 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
 
   const size_t chol_smem = 3 * MAXR * LD * sizeof(double);
   const size_t lev_smem = (MAXR * LD + LEV_ROWS * LD) * sizeof(double);
-  const size_t jac_smem = 2 * (MAXR + 1) * LD * sizeof(float);
-  JacobiArgs<float> ja = {};
-  for (int n = 0; n < m.N; ++n) {
-    ja.R[n] = m.R[n];
-    ja.gram[n] = mp.gram[n];
-    ja.V[n] = mp.V[n];
-    ja.sig2[n] = mp.sig2[n];
-  }
   KR_TRY(kr_smem_attr(ctx, k_cholesky, chol_smem));
   KR_TRY(kr_smem_attr(ctx, k_leverage, lev_smem));
-  KR_TRY(kr_smem_attr(ctx, k_jacobi<float>, jac_smem));
   dim3 gg((maxI + GRAM_ROWS - 1) / GRAM_ROWS, m.N);
   KR_LAUNCH(ctx, k_gram_partial, gg, 256, 0, mp);
   int maxR = 0;
@@ -500,12 +520,41 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
   dim3 gl((maxI + LEV_ROWS - 1) / LEV_ROWS, m.N);
   KR_LAUNCH(ctx, k_leverage, gl, LEV_ROWS * 32, lev_smem, mp);
   KR_LAUNCH(ctx, k_cdf, m.N, CDF_THREADS, 0, mp);
-  if (want_eig) KR_LAUNCH(ctx, k_jacobi<float>, m.N, 256, jac_smem, ja);
+  if (want_eig) {
+    KR_TRY(kr_eig64(ctx, m.N, m.R, mp.gram, V64, s64));
+    int tot = 0;
+    for (int n = 0; n < m.N; ++n) tot += m.R[n] * (m.R[n] + 1);
+    KR_LAUNCH(ctx, k_eig_to_f32, (tot + 255) / 256, 256, 0, mp, (const double* const*)nullptr, V64, s64);
+  }
   if (check_rank) {
-    KR_TRY(kr_hbuf_reserve(ctx, 4096));
+    int ntot = 0;
+    if (want_eig)
+      for (int n = 0; n < m.N; ++n) ntot += m.R[n];
+    KR_TRY(kr_hbuf_reserve(ctx, 4096 + sizeof(double) * (size_t)ntot));
     int* hf = (int*)ctx->hbuf;
+    double* hs = reinterpret_cast<double*>(ctx->hbuf + 4096);  // eigenvalues past the small read-back area
     KR_CUDA(ctx, cudaMemcpyAsync(hf, mp.flags, sizeof(int) * m.N, cudaMemcpyDeviceToHost, ctx->stream));
+    if (want_eig) {
+      int off = 0;
+      for (int n = 0; n < m.N; ++n) {
+        KR_CUDA(ctx, cudaMemcpyAsync(hs + off, s64[n], sizeof(double) * m.R[n], cudaMemcpyDeviceToHost, ctx->stream));
+        off += m.R[n];
+      }
+    }
     KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (want_eig) {
+      int off = 0;
+      for (int n = 0; n < m.N; ++n) {
+        double lo = INFINITY, hi = 0.0;
+        for (int r = 0; r < m.R[n]; ++r) {
+          lo = fmin(lo, hs[off + r]);
+          hi = fmax(hi, hs[off + r]);
+        }
+        t.sig_min[n] = fmax(lo, 0.0);
+        t.sig_max[n] = hi;
+        off += m.R[n];
+      }
+    }
     for (int n = 0; n < m.N; ++n) {
       t.rank[n] = hf[n] ? -1 : m.R[n];
       if (hf[n]) return kr_fail(ctx, KR_ERANK, "factor %d is numerically rank deficient (Cholesky pivot)", n);

@@ -436,6 +436,75 @@ __global__ void __launch_bounds__(32) k_rich_check(const double* __restrict__ pa
   rich_check_block(part, np, ra, snap);
 }
 
+// ------------------------------------------------------------------ preconditioned step in FP64
+//
+// For badly conditioned ridge problems (u32 sqrt(cond(M)) above 1e-3, e.g. the paper's
+// synthetic factors with entries 1 + N(0, 1e-6), cond(A^T A) near 1e8) the FP32 application of
+// M+ = (V1 (x)...(x) VN) D (V1 (x)...(x) VN)^T loses the spectral approximation Lemma 4.2 needs.
+// Then the step applies M+ in FP64 from the FP64 eigenpairs: g - lambda x widened to FP64, the
+// N mode products with V^T, the diagonal, the N products with V, and the FP32 update of x
+// with the step statistics of step_norms_block. The sampled products stay FP32.
+struct Pc64Modes {
+  int N;
+  int R[KR_MAX_MODES];
+  const double* V[KR_MAX_MODES];    // R x R, eigenvectors as columns
+  const double* sig[KR_MAX_MODES];  // R eigenvalues
+};
+
+__global__ void k_grad64(const float* __restrict__ g, const float* __restrict__ x, float lam, int64_t n,
+                         double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (double)g[i] - (double)lam * (double)x[i];
+}
+
+// out[p, j, q] = sum_k B[j, k] in[p, k, q] with B = V (trans = 0) or V^T (trans = 1), V R x R.
+__global__ void k_mode64(const double* __restrict__ in, double* __restrict__ out, int64_t P, int R, int64_t Q,
+                         const double* __restrict__ V, int trans) {
+  const int64_t tot = P * R * Q;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = e % Q;
+    const int64_t pj = e / Q;
+    const int j = (int)(pj % R);
+    const int64_t p = pj / R;
+    const double* col = in + p * R * Q + q;
+    double acc = 0.0;
+    for (int k = 0; k < R; ++k) acc = fma(trans ? V[(int64_t)k * R + j] : V[(int64_t)j * R + k], col[(int64_t)k * Q], acc);
+    out[e] = acc;
+  }
+}
+
+// x[r] /= prod_n sig_n[r_n] + lambda (0 where that is 0), FP64.
+__global__ void k_diag64(double* __restrict__ x, int64_t total, Pc64Modes pm, double lambda) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = i;
+    double prod = 1.0;
+    for (int n = pm.N - 1; n >= 0; --n) {
+      const int r = (int)(rem % pm.R[n]);
+      rem /= pm.R[n];
+      prod *= pm.sig[n][r];
+    }
+    const double d = prod + lambda;
+    x[i] = d > 0.0 ? x[i] / d : 0.0;
+  }
+}
+
+// x <- x + alpha d (d FP64, x FP32) with the step statistics (step_norms_block).
+__global__ void __launch_bounds__(256) k_update64(float* __restrict__ x, const double* __restrict__ d, float alpha,
+                                                  int64_t n, double* __restrict__ part, StepGrad sg) {
+  float s1 = 0.f, s2 = 0.f, bad = 0.f, s3 = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float st = (float)((double)alpha * d[i]);
+    const float xo = x[i];
+    const float xn = xo + st;
+    x[i] = xn;
+    s1 = fmaf(st, st, s1);
+    s2 = fmaf(xn, xn, s2);
+    s3 = fmaf(step_grad(sg, i, xo), st, s3);
+    if (!isfinite(xn)) bad = 1.f;
+  }
+  step_norms_block(s1, s2, bad, s3, part);
+}
+
 // ------------------------------------------------------------------ preconditioned step, fused
 
 // The preconditioner of Alg. 2 is a Kronecker product, M+ = B_1 (x) ... (x) B_N
@@ -1134,9 +1203,41 @@ kr_status pc_step_core(kr_ctx* ctx, const FactorTables& t, double lambda, float*
 // (for the eps-aware rule's g^T step).
 kr_status pc_step(kr_ctx* ctx, const FactorTables& t, double lambda, float* g, float* x, float alpha, float* tmp0,
                   float* tmp1, float* tmp2, int ublk, double* part, const RichArgs& ra, bool mode0_done = false,
-                  const float* graw = nullptr) {
+                  const float* graw = nullptr, double* pc64 = nullptr) {
   int np = 0;
   bool checked = false;
+  if (pc64) {  // FP64 application of M+ (badly conditioned ridge problems); pc64: 2 R doubles
+    const int N = t.N;
+    int64_t R = 1;
+    for (int n = 0; n < N; ++n) R *= t.R[n];
+    Pc64Modes pm = {};
+    pm.N = N;
+    for (int n = 0; n < N; ++n) {
+      pm.R[n] = t.R[n];
+      pm.V[n] = t.V64[n];
+      pm.sig[n] = t.sig64[n];
+    }
+    double* a = pc64;
+    double* b = pc64 + R;
+    const int grid = grid_cap(ctx, R, 256, 4);
+    KR_LAUNCH(ctx, k_grad64, grid, 256, 0, (const float*)g, (const float*)x, (float)lambda, R, a);
+    for (int pass = 0; pass < 2; ++pass) {  // V^T along every mode, then (after D) V
+      if (pass == 1) KR_LAUNCH(ctx, k_diag64, grid, 256, 0, a, R, pm, lambda);
+      int64_t P = 1;
+      for (int n = 0; n < N; ++n) {
+        const int64_t Q = R / P / t.R[n];
+        KR_LAUNCH(ctx, k_mode64, grid, 256, 0, (const double*)a, b, P, t.R[n], Q, t.V64[n], pass == 0 ? 1 : 0);
+        double* tmp = a;
+        a = b;
+        b = tmp;
+        P *= t.R[n];
+      }
+    }
+    const StepGrad sg = {ra.eps_rule ? g : nullptr, (float)lambda};
+    KR_LAUNCH(ctx, k_update64, ublk, 256, 0, x, (const double*)a, alpha, R, part, sg);
+    KR_LAUNCH(ctx, k_rich_check, 1, 32, 0, part, ublk, ra);
+    return KR_OK;
+  }
   if (mode0_done) {
     const int N = t.N;
     int64_t Q = 1;
@@ -1408,6 +1509,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   const bool fold0 = slab && N == 3 && cfg.lambda == 0.0;
   nd.add<float>(fold0 ? (size_t)m.I[0] * m.R[0] : 0);
   nd.add<float>(fold0 && eps_rule ? (size_t)R : 0);
+  nd.add<double>(cfg.lambda > 0.0 ? 2 * (size_t)R : 0);  // FP64 preconditioner buffers (ill-conditioned ridge)
   {
     Need sc = nd;
     kr_sketch_scratch_need(ctx, cfg.s, ncell, m.I[m.N - 1], nd);
@@ -1443,6 +1545,19 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   bf.opart = eps_rule ? cv.take<double>(nopart) : nullptr;
   bf.red = cv.take<double>(16);
   bf.rich = cv.take<RichState>(1);
+  // The ridge preconditioner in FP64 when FP32 rounding of its application, about
+  // u32 sqrt(cond(M)) relative in M's norm, would spoil the spectral approximation.
+  double* pc64 = nullptr;
+  if (cfg.lambda > 0.0) {
+    double* buf = cv.take<double>(2 * (size_t)R);
+    double hi = 1.0, lo = 1.0;
+    for (int n = 0; n < N; ++n) {
+      hi *= t.sig_max[n];
+      lo *= t.sig_min[n];
+    }
+    const double cond = (hi + cfg.lambda) / (lo + cfg.lambda);
+    if (ldexp(sqrt(cond), -24) > 1e-3) pc64 = buf;
+  }
   if (fold0) {  // B1 = A(1) G_1^-1 (G_1^-1 symmetric: row i of B1 = G_1^-1 applied to row i of A(1))
     bf.B1 = cv.take<float>((size_t)m.I[0] * m.R[0]);
     KR_TRY(kr_mode_product(ctx, m.A[0], bf.B1, m.I[0], m.R[0], 1, m.R[0], t.ginv[0], 0));
@@ -1494,7 +1609,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     ra.op = op;
     ra.on = on;
     return pc_step(ctx, t, cfg.lambda, bf.g, bf.x, (float)cfg.alpha, bf.d, bf.t0, bf.t1, ublk, bf.part, ra,
-                   bf.B1 != nullptr, bf.g2);
+                   bf.B1 != nullptr, bf.g2, pc64);
   };
   auto read_state = [&]() -> kr_status {
     KR_CUDA(ctx, cudaMemcpyAsync(hs, bf.rich, sizeof(RichState), cudaMemcpyDeviceToHost, ctx->stream));

@@ -11,7 +11,8 @@ float32 for the device):
 * ``kron_problem``: N factors I_n x R_n. ``dist='gauss'``: i.i.d. N(0,1);
   ``'lognormal_rows'``: each row scaled by exp(z), z ~ N(0, sigma^2) (skewed leverage);
   ``'outliers'``: Gaussian with a seeded 10% of rows scaled by 20 (high-leverage rows);
-  ``'paper_e1'``: entries N(1, 0.001) read as mean 1, standard deviation sqrt(0.001).
+  ``'paper_e1'``: entries N(1, 0.001) read as mean 1, standard deviation 0.001 (the reading
+  under which the closed-form optimum reproduces the paper's printed OPT values).
   Right-hand side: ``b = K x_true + noise`` with x_true ~ N(0,1)^R, noise Gaussian,
   either absolute (``noise_abs``) or scaled to ``noise_rel * ||K x_true||``; or a
   rank-(r,...,r) Tucker tensor plus relative noise (``b_kind='tucker'``); or all ones.
@@ -39,7 +40,7 @@ def make_factors(I, R, dist="gauss", seed=0, sigma=1.0, outlier_frac=0.1, outlie
     As = []
     for In, Rn in zip(I, R):
         if dist == "paper_e1":
-            A = rng.normal(1.0, np.sqrt(1e-3), size=(In, Rn))
+            A = rng.normal(1.0, 1e-3, size=(In, Rn))
         else:
             A = rng.standard_normal((In, Rn))
         if dist == "lognormal_rows":
