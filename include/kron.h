@@ -358,6 +358,27 @@ KR_API kr_status tucker_als_sweep(kr_ctx* ctx, int32_t N, const int64_t* I, cons
                            const float* X, float* const A[], float* G, const kr_opts* opts,
                            int32_t sweeps, kr_report* report);
 
+/* Exact TuckerALS (Alg. 1 with the exact factor and core updates of App. C, by KronMatMul):
+ * the baseline of the sampled sweep. Per sweep, for n = 0..N-1 the factor update
+ *   A(n)^T = (G_(n) (K^T K) G_(n)^T + lambda I)^-1 G_(n) Z_(n)^T,  K = (x)_{m != n} A(m),
+ *   Z = X x_{m != n} A(m)^T  (one pass over X; H and its Cholesky solves in FP64),
+ * then the core update G = (K^T K + lambda I)^-1 K^T vec X with K = (x)_m A(m) (Alg. 2's
+ * preconditioner, applied exactly). X: prod I floats; A[n]: I[n] x R[n] (in/out); G: prod R
+ * (in/out), all device. rre (host, sweeps doubles, may be NULL) receives the relative
+ * reconstruction error ||X - G x_1 A(1) ... x_N A(N)||^2 / ||X||^2 after each sweep.
+ * With lambda = 0 every R[n] must not exceed the product of the other ranks (else the factor
+ * system G_(n) (K^T K) G_(n)^T is singular: KR_EINVAL). Returns KR_ERANK if a factor system
+ * is not positive definite (a rank-deficient core unfolding or factor). */
+KR_API kr_status tucker_als_exact_sweep(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R, const float* X,
+                                        float* const A[], float* G, double lambda, int32_t sweeps, double* rre);
+
+/* Relative reconstruction error of a Tucker decomposition (the paper's RRE, App. D):
+ * ||X - G x_1 A(1) ... x_N A(N)||^2 / ||X||^2, evaluated as
+ * (||X||^2 - 2 <X x_m A(m)^T, G> + <G, G x_m A(m)^T A(m)>) / ||X||^2 with FP64 sums (one pass
+ * over X; the reconstruction is never formed). rre is a host double. */
+KR_API kr_status tucker_rre(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R, const float* X,
+                            const float* const A[], const float* G, double* rre);
+
 #ifdef __cplusplus
 }
 #endif

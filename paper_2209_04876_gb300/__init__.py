@@ -25,7 +25,7 @@ EXPORTED = ["kr_create", "kr_destroy", "kr_set_stream", "kr_last_error", "kr_lau
             "kr_timing_read", "kr_timing_reset", "kr_set_option", "kron_sample_count", "kron_leverage",
             "kron_sample", "kron_sample_noalloc", "kron_sketch", "kron_sketch_distinct", "kron_sketch_export", "kron_sketch_residual",
             "kron_sketch_free", "kron_matmul", "kron_precond", "kron_objective", "kron_regress", "kron_ridge",
-            "kron_ridge_batched", "tucker_factor_update", "tucker_als_sweep"]
+            "kron_ridge_batched", "tucker_factor_update", "tucker_als_sweep", "tucker_als_exact_sweep", "tucker_rre"]
 
 
 class KronError(RuntimeError):
@@ -103,6 +103,8 @@ def lib():
             "kron_ridge_batched": (i32, [vp, i32, P(KrFactors), P(vp), P(KrOpts), P(vp), P(KrReport)]),
             "tucker_factor_update": (i32, [vp, i32, P(i64), P(i32), vp, P(vp), vp, i32, P(KrOpts), P(KrReport)]),
             "tucker_als_sweep": (i32, [vp, i32, P(i64), P(i32), vp, P(vp), vp, P(KrOpts), i32, P(KrReport)]),
+            "tucker_als_exact_sweep": (i32, [vp, i32, P(i64), P(i32), vp, P(vp), vp, dbl, i32, P(dbl)]),
+            "tucker_rre": (i32, [vp, i32, P(i64), P(i32), vp, P(vp), vp, P(dbl)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -482,3 +484,34 @@ def tucker_als_sweep(X, As, G, lam, eps=0.1, sweeps=1, seed=0, call_id=0, **kw):
                                 ctypes.byref(rep))
     _check(st, h)
     return rep.as_dict()
+
+
+def tucker_als_exact_sweep(X, As, G, lam, sweeps=1):
+    """Exact TuckerALS sweeps (KronMatMul factor and core updates); As and G are updated in
+    place (device float32 tensors). Returns the RRE after each sweep."""
+    h = context()
+    N = len(As)
+    X = _dev_f32(X)
+    for k, A in enumerate(As):
+        _inout(A, "As[%d]" % k)
+    _inout(G, "G")
+    I = (ctypes.c_int64 * N)(*[A.shape[0] for A in As])
+    R = (ctypes.c_int32 * N)(*[A.shape[1] for A in As])
+    rre = (ctypes.c_double * max(1, int(sweeps)))()
+    st = lib().tucker_als_exact_sweep(h, N, I, R, _ptr(X), _ptr_array(As), _ptr(G), float(lam), int(sweeps), rre)
+    _check(st, h)
+    return [rre[k] for k in range(int(sweeps))]
+
+
+def tucker_rre(X, As, G):
+    """||X - G x_1 A(1) ... x_N A(N)||^2 / ||X||^2 (FP64 sums on the device)."""
+    h = context()
+    N = len(As)
+    X = _dev_f32(X)
+    As = [_dev_f32(A) for A in As]
+    G = _dev_f32(G)
+    I = (ctypes.c_int64 * N)(*[A.shape[0] for A in As])
+    R = (ctypes.c_int32 * N)(*[A.shape[1] for A in As])
+    out = ctypes.c_double()
+    _check(lib().tucker_rre(h, N, I, R, _ptr(X), _ptr_array(As), _ptr(G), ctypes.byref(out)), h)
+    return out.value

@@ -93,7 +93,8 @@ constexpr int PEN_MAXRN = KR_MAX_RANK;
 __global__ void __launch_bounds__(256) k_penalty_rows(const float* __restrict__ Z, const float* __restrict__ Gn,
                                                       const double* __restrict__ gp64, const float* __restrict__ gsk,
                                                       int Rn, int Rne, double lambda, double w,
-                                                      float* __restrict__ grad, float* __restrict__ out_a) {
+                                                      float* __restrict__ grad, float* __restrict__ out_a,
+                                                      double* __restrict__ grad64) {
   extern __shared__ double zs[];  // Rne
   __shared__ double tv[PEN_MAXRN], uv[PEN_MAXRN];
   const int64_t row = blockIdx.x;
@@ -127,7 +128,11 @@ __global__ void __launch_bounds__(256) k_penalty_rows(const float* __restrict__ 
   for (int k = threadIdx.x; k < Rne; k += blockDim.x) {
     double c = 0.0;
     for (int a = 0; a < Rn; ++a) c = fma(gp64[(int64_t)k * Rn + a], tv[a], c);
-    grad[row * Rne + k] = (float)(w * zs[k] + c - (double)gsk[row * Rne + k]);
+    const double gv = w * zs[k] + c - (double)gsk[row * Rne + k];
+    if (grad64)
+      grad64[row * Rne + k] = gv;
+    else
+      grad[row * Rne + k] = (float)gv;
   }
 }
 
@@ -542,6 +547,123 @@ __global__ void k_rows_reduce(const double* __restrict__ rowstat, int nrow, doub
   }
 }
 
+// ------------------------------------------------------------------ FP64 Woodbury chain
+//
+// Factor steps with three or more other modes (or more unknowns per row than the fused row
+// kernel takes) apply the Woodbury preconditioner as a batched chain over the rows:
+//   D = A^-1 grad,  A^-1 = (x)V_m (S^2 + w)^-1 (x)V_m^T   (mode products, all rows at once)
+//   d = D - (A^-1 U) C^-1 V D                              (per row)
+// in FP64 throughout (the reasons of WbBase hold for any number of modes: w multiplies every
+// error of A^-1), up to the FP32 iterate z.
+
+// out[p, j, q] = sum_k B'[j, k] in[p, k, q], B' = V (trans = 0) or V^T (trans = 1), V R x R.
+__global__ void k_mode_sq64(const double* __restrict__ in, double* __restrict__ out, int64_t P, int R, int64_t Q,
+                            const double* __restrict__ V, int trans) {
+  const int64_t tot = P * R * Q;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = e % Q;
+    const int64_t pj = e / Q;
+    const int j = (int)(pj % R);
+    const int64_t p = pj / R;
+    const double* col = in + p * R * Q + q;
+    double acc = 0.0;
+    for (int k = 0; k < R; ++k) acc = fma(trans ? V[(int64_t)k * R + j] : V[(int64_t)j * R + k], col[(int64_t)k * Q], acc);
+    out[e] = acc;
+  }
+}
+
+struct Diag64 {
+  int No;
+  int R[KR_MAX_MODES];
+  const double* s[KR_MAX_MODES];
+};
+
+// x[b, r] /= prod_m s_m[r_m] + w over the trailing Rne entries of every batch row b.
+__global__ void k_diag_w64(double* __restrict__ x, int64_t total, int64_t Rne, Diag64 d, double w) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = i % Rne;
+    double prod = 1.0;
+    for (int m = d.No - 1; m >= 0; --m) {
+      const int r = (int)(rem % d.R[m]);
+      rem /= d.R[m];
+      prod *= d.s[m][r];
+    }
+    const double dv = prod + w;
+    x[i] = dv > 0.0 ? x[i] / dv : 0.0;
+  }
+}
+
+// out[c][r] = in[r][c] (rows x cols, FP64).
+__global__ void k_transpose64(const double* __restrict__ in, int rows, int cols, double* __restrict__ out) {
+  const int64_t tot = (int64_t)rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    out[c * rows + r] = in[e];
+  }
+}
+
+// One block per row i: u = V D_i (R_n), v = C^-1 u, d = D_i - (A^-1 U)^T v, then z_i <- z_i - alpha d
+// with the row statistics of k_row_update (FP32 step norms).
+__global__ void __launch_bounds__(256) k_wb_rows64(const double* __restrict__ D, const double* __restrict__ Vw,
+                                                   const double* __restrict__ Cinv, const double* __restrict__ AinvU,
+                                                   int Rn, int Rne, float* __restrict__ Z, float alpha,
+                                                   double* __restrict__ rowstat) {
+  __shared__ double uv[KR_MAX_RANK], vv[KR_MAX_RANK];
+  const int64_t row = blockIdx.x;
+  const double* Di = D + row * Rne;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int a = warp; a < Rn; a += nw) {
+    double t = 0.0;
+    for (int k = lane; k < Rne; k += 32) t = fma(Vw[(int64_t)a * Rne + k], Di[k], t);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (lane == 0) uv[a] = t;
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < Rn; a += blockDim.x) {
+    double t = 0.0;
+    for (int b = 0; b < Rn; ++b) t = fma(Cinv[(int64_t)a * Rn + b], uv[b], t);
+    vv[a] = t;
+  }
+  __syncthreads();
+  float s1 = 0.f, s2 = 0.f, bad = 0.f;
+  float* z = Z + row * Rne;
+  for (int k = threadIdx.x; k < Rne; k += blockDim.x) {
+    double c = Di[k];
+    for (int a = 0; a < Rn; ++a) c = fma(-AinvU[(int64_t)a * Rne + k], vv[a], c);
+    const float st = alpha * (float)c;
+    const float zn = z[k] - st;
+    z[k] = zn;
+    s1 = fmaf(st, st, s1);
+    s2 = fmaf(zn, zn, s2);
+    if (!isfinite(zn)) bad = 1.f;
+  }
+  __shared__ float red[3][32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+    bad = fmaxf(bad, __shfl_xor_sync(0xffffffffu, bad, off));
+  }
+  if (lane == 0) {
+    red[0][warp] = s1;
+    red[1][warp] = s2;
+    red[2][warp] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = 0.f, b = 0.f, c = 0.f;
+    for (int k = 0; k < nw; ++k) {
+      a += red[0][k];
+      b += red[1][k];
+      c = fmaxf(c, red[2][k]);
+    }
+    rowstat[3 * row + 0] = (double)a;
+    rowstat[3 * row + 1] = (double)b;
+    rowstat[3 * row + 2] = (double)c;
+  }
+}
+
 int grid_of(kr_ctx* ctx, int64_t work) {
   int64_t g = (work + 255) / 256;
   if (g > ctx->num_sms * 8) g = ctx->num_sms * 8;
@@ -569,6 +691,39 @@ kr_status base_apply(kr_ctx* ctx, const FactorTables& to, int nrow, double w, co
   KR_TRY(kr_diag_scale(ctx, to, w, out, Rne * nrow));
   for (int m = 0; m < No; ++m) tr[m + 1] = 0;
   return kr_kron_apply2(ctx, No + 1, dims, dims, B, tr, out, out, t0, t1);
+}
+
+// Batched FP64 A^-1 = (x)V (S^2 + w)^-1 (x)V^T over the No other modes for `nrow` rows of Rne
+// entries: out = A^-1 in (tmp: nrow * Rne doubles; in aliases neither out nor tmp).
+kr_status base_apply64(kr_ctx* ctx, int No, const int* Ro, double* const* V64, double* const* s64, int nrow, double w,
+                       const double* in, double* out, double* tmp) {
+  int64_t Rne = 1;
+  for (int m = 0; m < No; ++m) Rne *= Ro[m];
+  const int64_t tot = Rne * nrow;
+  const int grid = grid_of(ctx, tot);
+  const double* src = in;
+  int k = 0;
+  for (int pass = 0; pass < 2; ++pass) {  // V^T along every mode, the diagonal, then V
+    int64_t P = nrow, Q = Rne;
+    for (int m = 0; m < No; ++m) {
+      Q /= Ro[m];
+      double* dst = (k & 1) ? out : tmp;  // 2 No products: the last lands in out
+      ++k;
+      KR_LAUNCH(ctx, k_mode_sq64, grid, 256, 0, src, dst, P, Ro[m], Q, (const double*)V64[m], pass == 0 ? 1 : 0);
+      src = dst;
+      P *= Ro[m];
+    }
+    if (pass == 0) {
+      Diag64 dd = {};
+      dd.No = No;
+      for (int m = 0; m < No; ++m) {
+        dd.R[m] = Ro[m];
+        dd.s[m] = s64[m];
+      }
+      KR_LAUNCH(ctx, k_diag_w64, grid, 256, 0, const_cast<double*>(src), tot, Rne, dd, w);
+    }
+  }
+  return KR_OK;
 }
 
 struct FactorStep {
@@ -652,14 +807,12 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   // one or two other modes: the gradient, the FP64 Woodbury preconditioner and the update
   // of every row in one kernel (k_factor_rows); more: the batched FP32 mode-product chain
   const bool fused_rows = No <= 2 && Rne <= FR_MAX_RNE && Rn <= PEN_MAXRN;
-  if (fused_rows) {
-    for (int k = 0; k < No; ++k) {
-      nd.add<double>((int64_t)mo.R[k] * mo.R[k]);  // FP64 eigenvectors
-      nd.add<double>(mo.R[k]);                     // FP64 eigenvalues
-    }
-    nd.add<double>((int64_t)Rn * Rne);  // A^-1 U
-    nd.add<double>((int64_t)Rn * Rne);  // V
-    nd.add<double>((int64_t)Rn * Rn);   // C^-1
+  nd.add<double>((int64_t)Rn * Rne);  // A^-1 U
+  nd.add<double>((int64_t)Rn * Rne);  // V
+  nd.add<double>((int64_t)Rn * Rn);   // C^-1
+  if (!fused_rows) {
+    nd.add<double>((int64_t)Rn * Rne);  // (G+)^T
+    for (int k = 0; k < 3; ++k) nd.add<double>(ZL);  // gradient, A^-1 gradient, scratch (FP64 chain)
   }
   if (slab) kr_tiles_own_need(&tl, cells, nd);
   {
@@ -753,34 +906,34 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   double* rpart = cv.take<double>(1024);
   FactorLoop* dloop = cv.take<FactorLoop>(1);
   RowStep rs = {};
-  double* V64[2] = {nullptr, nullptr};
-  double* s64[2] = {nullptr, nullptr};
+  double* V64[KR_MAX_MODES] = {};
+  double* s64[KR_MAX_MODES] = {};
   double *AinvU64 = nullptr, *Vw64 = nullptr, *Cinv64 = nullptr;
-  if (fused_rows) {
-    for (int k = 0; k < No; ++k) {
-      V64[k] = cv.take<double>((int64_t)mo.R[k] * mo.R[k]);
-      s64[k] = cv.take<double>(mo.R[k]);
-    }
-    AinvU64 = cv.take<double>((int64_t)Rn * Rne);
-    Vw64 = cv.take<double>((int64_t)Rn * Rne);
-    Cinv64 = cv.take<double>((int64_t)Rn * Rn);
+  double *GpT64 = nullptr, *G64 = nullptr, *D64 = nullptr, *T64 = nullptr;
+  AinvU64 = cv.take<double>((int64_t)Rn * Rne);
+  Vw64 = cv.take<double>((int64_t)Rn * Rne);
+  Cinv64 = cv.take<double>((int64_t)Rn * Rn);
+  if (!fused_rows) {
+    GpT64 = cv.take<double>((int64_t)Rn * Rne);
+    G64 = cv.take<double>(ZL);
+    D64 = cv.take<double>(ZL);
+    T64 = cv.take<double>(ZL);
+  }
+  // the other modes' FP64 eigen-decompositions (built with the tables): the Woodbury base
+  int Ro[KR_MAX_MODES];
+  for (int k = 0, j = 0; k < N; ++k) {
+    if (k == n) continue;
+    Ro[j] = m.R[k];
+    V64[j] = ta.V64[k];
+    s64[j] = ta.sig64[k];
+    ++j;
   }
   if (slab) kr_tiles_layout(&tl, cells, cv);
   (void)spare;
   const size_t gj_smem = (size_t)Rn * 2 * Rn * sizeof(double);
   KR_TRY(kr_smem_attr(ctx, k_gauss_jordan, gj_smem));
   if (fused_rows) {
-    // FP64 Woodbury pieces: eigen-decompositions of the other modes' Gram matrices, A^-1 U,
-    // V, the capacitance and its inverse
-    int Ro[2];
-    const double* gr[2];
-    for (int k = 0, j = 0; k < N; ++k) {
-      if (k == n) continue;
-      Ro[j] = m.R[k];
-      gr[j] = ta.gram[k];
-      ++j;
-    }
-    KR_TRY(kr_eig64(ctx, No, Ro, gr, V64, s64));
+    // FP64 Woodbury pieces: A^-1 U, V, the capacitance and its inverse
     rs.b.R1 = No == 2 ? Ro[0] : 1;
     rs.b.R2 = Ro[No - 1];
     rs.b.V1 = No == 2 ? V64[0] : nullptr;
@@ -805,10 +958,13 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     KR_LAUNCH(ctx, k_gauss_jordan, 1, 256, gj_smem, C, Rn, Cinv, flag, Cinv64);
     KR_TRY(kr_smem_attr(ctx, k_factor_rows, (size_t)24 * Rne));
   } else {
-    // A^-1 U (rows: A^-1 applied to each column of G+), capacitance and its inverse
-    KR_TRY(base_apply(ctx, to, Rn, w, GpT, AinvUt, t0, t1));
-    KR_LAUNCH(ctx, k_capacitance, Rn * Rn, 256, 0, Vw, AinvUt, Rn, (int)Rne, C);
-    KR_LAUNCH(ctx, k_gauss_jordan, 1, 256, gj_smem, C, Rn, Cinv, flag, (double*)nullptr);
+    // FP64 chain: A^-1 U (A^-1 applied to each column of G+, batched), V, the capacitance
+    // and its inverse
+    KR_LAUNCH(ctx, k_transpose64, grid_of(ctx, Rtot), 256, 0, (const double*)gp64, (int)Rne, Rn, GpT64);
+    KR_TRY(base_apply64(ctx, No, Ro, V64, s64, Rn, w, GpT64, AinvU64, T64));
+    KR_LAUNCH(ctx, k_vw64, grid_of(ctx, Rtot), 256, 0, gp64, Gn, Rn, (int)Rne, cfg.lambda, w, Vw64);
+    KR_LAUNCH(ctx, k_capacitance64, Rn * Rn, 256, 0, Vw64, AinvU64, Rn, (int)Rne, C);
+    KR_LAUNCH(ctx, k_gauss_jordan, 1, 256, gj_smem, C, Rn, Cinv, flag, Cinv64);
   }
   // batched sketch: row i of X_(n), fresh draws per row (counter row = i)
   {
@@ -850,17 +1006,13 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     if (fused_rows) {
       KR_LAUNCH(ctx, k_factor_rows, In, 256, (size_t)24 * Rne, rs, Z, Gb, rowstat);
     } else {
-      // grad = w z + G+ (lambda (G+)^T z - w G z) - Gb  (FP64 combination, one block per row)
-      KR_LAUNCH(ctx, k_penalty_rows, In, 256, sizeof(double) * Rne, Z, Gn, gp64, Gb, Rn, (int)Rne, cfg.lambda, w, Gr,
-                (float*)nullptr);
-      // d = M^-1 grad (Woodbury)
-      KR_TRY(base_apply(ctx, to, In, w, Gr, D, t0, t1));
-      KR_TRY(kr_mode_product(ctx, D, U1, In, (int)Rne, 1, Rn, Vw, 0));
-      KR_TRY(kr_mode_product(ctx, U1, U2, In, Rn, 1, Rn, Cinv, 0));
-      KR_TRY(kr_mode_product(ctx, U2, Gr, In, Rn, 1, (int)Rne, AinvUt, 1));
-      KR_LAUNCH(ctx, k_lin2, grid_of(ctx, ZL), 256, 0, D, D, 1.f, Gr, -1.f, ZL);
-      // z <- z - alpha d
-      KR_LAUNCH(ctx, k_row_update, In, 256, 0, Z, D, (float)cfg.alpha, (int)Rne, rowstat);
+      // grad = w z + G+ (lambda (G+)^T z - w G z) - Gb  (FP64, one block per row)
+      KR_LAUNCH(ctx, k_penalty_rows, In, 256, sizeof(double) * Rne, Z, Gn, gp64, Gb, Rn, (int)Rne, cfg.lambda, w,
+                (float*)nullptr, (float*)nullptr, G64);
+      // d = M^-1 grad (Woodbury, FP64), z <- z - alpha d
+      KR_TRY(base_apply64(ctx, No, Ro, V64, s64, In, w, G64, D64, T64));
+      KR_LAUNCH(ctx, k_wb_rows64, In, 256, 0, (const double*)D64, (const double*)Vw64, (const double*)Cinv64,
+                (const double*)AinvU64, Rn, (int)Rne, Z, (float)cfg.alpha, rowstat);
     }
     // stopping rule on the largest per-row relative step
     KR_LAUNCH(ctx, k_rows_reduce, 1, 256, 0, rowstat, In, red, dloop, cfg.tol, cfg.max_iter, hnd, use_hnd);
@@ -899,7 +1051,7 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     st = kr_fail(ctx, KR_EDIVERGED, "factor step %d: Richardson step grew 3 times past 16x its minimum", n);
   // a_i = (G+)^T z_i  (the new factor rows, FP64 accumulation)
   KR_LAUNCH(ctx, k_penalty_rows, In, 256, sizeof(double) * Rne, Z, Gn, gp64, Gb, Rn, (int)Rne, cfg.lambda, w, Gr,
-            An_out);
+            An_out, (double*)nullptr);
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (rep) {
     rep->iters = it;

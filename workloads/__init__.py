@@ -18,6 +18,11 @@ float32 for the device):
   rank-(r,...,r) Tucker tensor plus relative noise (``b_kind='tucker'``); or all ones.
 * ``tucker_tensor``: X = G x_1 Q1 ... x_N QN + noise, G ~ N(0,1)^{R}, Qn orthonormal
   (QR of a Gaussian), noise scaled to ``noise_rel * ||signal||``.
+* ``tucker_tensor_device``: the ``tucker_tensor`` recipe generated in float32 on a CUDA device.
+* ``IMAGE_SHAPES``: synthetic stand-ins for the paper's image tensors (App. D): the shapes and
+  decomposition ranks of the cardiac MRI, hyperspectral and COIL-100 tensors, filled with a
+  Tucker tensor of twice the decomposition rank (capped by the mode size) whose core decays
+  as exp(-1.2 r_n / R_n) along every mode, plus 10 % noise.
 * ``batched_shapes``: per-problem I_n ~ U{lo..hi}, R_n ~ U{rlo..rhi}.
 * ``kron_problem_device``: the ``kron_problem`` recipe (b_kind 'kron' or 'tucker', relative
   noise) generated in float32 on a CUDA device with torch's seeded generator, for batches and
@@ -143,6 +148,36 @@ def tucker_tensor(I, R, seed=0, noise_rel=0.01):
     return dict(X=X + noise, core=core, Qs=Qs)
 
 
+def tucker_tensor_device(I, R, seed=0, noise_rel=0.01, device="cuda", decay_rank=None, decay=1.2):
+    """The ``tucker_tensor`` recipe in float32 on a CUDA device with torch's seeded generator
+    (Gaussian core, orthonormal factors from the QR of Gaussians, relative noise): for
+    tensors of hundreds of millions of entries. Same recipe, not the same numbers. With
+    decay_rank, core index r_n is scaled by exp(-decay r_n / decay_rank[n]) (a decaying
+    multilinear spectrum, as in images: a rank-decay_rank decomposition leaves a tail)."""
+    import torch
+
+    I = [int(v) for v in I]
+    R = [int(v) for v in R]
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    T = torch.randn(*R, generator=g, device=device)
+    if decay_rank is not None:
+        for n, (Rn, Dn) in enumerate(zip(R, decay_rank)):
+            w = torch.exp(-decay * torch.arange(Rn, device=device, dtype=torch.float32) / float(Dn))
+            shape = [1] * len(R)
+            shape[n] = Rn
+            T = T * w.reshape(shape)
+    for n, (In, Rn) in enumerate(zip(I, R)):
+        Q, _ = torch.linalg.qr(torch.randn(In, Rn, generator=g, device=device))
+        T = torch.movedim(torch.tensordot(Q, T, dims=([1], [n])), 0, n)
+    X = T.contiguous()
+    del T
+    noise = torch.randn(X.shape, generator=g, device=device)
+    noise *= noise_rel * torch.linalg.vector_norm(X) / torch.linalg.vector_norm(noise)
+    X += noise
+    return X
+
+
 def tucker_init(I, R, seed=0):
     """Initial factors: Q factor of a seeded Gaussian I_n x R_n per mode."""
     rng = np.random.default_rng(seed)
@@ -164,4 +199,14 @@ CONFIGS = {
     "kron_n3_1024x64_outliers": dict(I=[1024, 1024, 1024], R=[64, 64, 64], dist="outliers",
                                      noise_rel=0.01, eps=0.05, lam=0.0, b_kind="tucker",
                                      tucker_rank=[64, 64, 64]),
+}
+
+
+# Shapes and decomposition ranks of the paper's image tensors (App. D; the datasets are not
+# used: synthetic Tucker tensors of these shapes stand in for them).
+IMAGE_SHAPES = {
+    "cardiac_mri_256x256x14x20": dict(I=[256, 256, 14, 20], R=[8, 8, 4, 4]),
+    "hyperspectral_1024x1344x33_r8": dict(I=[1024, 1344, 33], R=[8, 8, 8]),
+    "hyperspectral_1024x1344x33_r16": dict(I=[1024, 1344, 33], R=[16, 16, 4]),
+    "coil100_7200x120x120x3": dict(I=[7200, 120, 120, 3], R=[16, 4, 4, 2]),
 }
