@@ -184,6 +184,15 @@ enum {
  *    entries of b; 0 copies all of b to the device first (on a second stream, overlapped
  *    with the tables, draws and grouping). Other host memory is always copied. Both give
  *    identical results.
+ *  KR_OPT_JL_K (default 0, range [0, 64]): 0 samples by the exact statistical leverage scores;
+ *    k > 0 by JL-approximate ones (the approximate scores of Alg. 2's first steps, App. B's
+ *    Johnson-Lindenstrauss lemma): l~_i = ||a_i^T L^-T Pi||^2 / k with L the FP64 Cholesky factor
+ *    of A(n)^T A(n) and Pi an R_n x k matrix of signs, entry (r, j) from the low bit of word w0 of
+ *    Philox4x32-10 under key (KR_OPT_JL_SEED lo, hi) at counter (r k + j, 0, n, 0) (0: +1, 1: -1),
+ *    n the factor's position in the call. E[l~_i] = l_i. Applies to every table build
+ *    (kron_leverage, the solvers, the Tucker steps); the weights use the same scores, so the
+ *    sketch stays unbiased.
+ *  KR_OPT_JL_SEED (default 0): the Philox key of the JL sign matrices.
  * Returns KR_EINVAL for an unknown key or a value out of range. */
 enum {
   KR_OPT_SLAB_PASS = 1,
@@ -191,7 +200,9 @@ enum {
   KR_OPT_DEVICE_LOOP = 3,
   KR_OPT_BATCH_WORKERS = 4,
   KR_OPT_GROUPING = 5,
-  KR_OPT_HOST_GATHER = 6
+  KR_OPT_HOST_GATHER = 6,
+  KR_OPT_JL_K = 7,
+  KR_OPT_JL_SEED = 8
 };
 KR_API kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value);
 

@@ -101,6 +101,33 @@ def leverage_scores(A, lam=0.0):
     return (U * U) @ f
 
 
+def jl_signs(R, k, seed, mode):
+    """The R x k Rademacher matrix of the JL-approximate scores of factor `mode`: entry (r, j)
+    is +1 or -1 by the low bit of word w0 of Philox4x32-10 under key (seed lo, seed hi) at
+    counter (r * k + j, 0, mode, 0) (0 -> +1, 1 -> -1)."""
+    from .philox import philox4x32_10
+
+    t = np.arange(R * k, dtype=np.uint64)
+    w0, _, _, _ = philox4x32_10(t, np.zeros_like(t), np.full_like(t, int(mode)), np.zeros_like(t),
+                                int(seed) & 0xFFFFFFFF, (int(seed) >> 32) & 0xFFFFFFFF)
+    return np.where((w0 & 1) == 0, 1.0, -1.0).reshape(R, k)
+
+
+def jl_leverage_scores(A, k, seed, mode):
+    """JL-approximate statistical leverage scores (the approximate scores of Alg. 2's first
+    steps, App. B's Johnson-Lindenstrauss lemma): l~_i = ||e_i^T A R^-1 Pi||^2 / k with R the
+    triangular factor of A (QR with a positive diagonal, i.e. the Cholesky factor of A^T A
+    transposed) and Pi = jl_signs(R, k, seed, mode). E[l~_i] = l_i; each is within (1 +- delta)
+    of l_i with high probability for k = O(log(I) / delta^2)."""
+    A = np.asarray(A, dtype=np.float64)
+    Q, Rq = np.linalg.qr(A)
+    sgn = np.where(np.diag(Rq) < 0, -1.0, 1.0)
+    Q = Q * sgn[None, :]  # the QR with a positive diagonal: A R^-1 = Q
+    P = jl_signs(A.shape[1], k, seed, mode)
+    Y = Q @ P
+    return np.sum(Y * Y, axis=1) / float(k)
+
+
 def factor_rank(A):
     A = np.asarray(A, dtype=np.float64)
     return numerical_rank(np.linalg.svd(A, compute_uv=False), A.shape)

@@ -21,6 +21,7 @@ STATUS = {0: "KR_OK", 1: "KR_EINVAL", 2: "KR_ENOMEM", 3: "KR_ECUDA", 4: "KR_ENON
 KERNEL_KINDS = {"resid": 0, "modeprod": 1, "sample": 2, "scatter": 3, "dedup": 4, "tables": 5, "vector": 6,
                 "slab": 7}
 OPT_SLAB_PASS, OPT_SLAB_TILE_ENTRIES, OPT_DEVICE_LOOP, OPT_BATCH_WORKERS, OPT_GROUPING, OPT_HOST_GATHER = 1, 2, 3, 4, 5, 6
+OPT_JL_K, OPT_JL_SEED = 7, 8
 EXPORTED = ["kr_create", "kr_destroy", "kr_set_stream", "kr_last_error", "kr_launch_count", "kr_timing_enable",
             "kr_timing_read", "kr_timing_reset", "kr_set_option", "kron_sample_count", "kron_leverage",
             "kron_sample", "kron_sample_noalloc", "kron_sketch", "kron_sketch_distinct", "kron_sketch_export", "kron_sketch_residual",
@@ -145,8 +146,10 @@ def set_option(key, value):
     per-cell residual pass; OPT_SLAB_TILE_ENTRIES: entry budget of a slab-pass tile;
     OPT_DEVICE_LOOP: 1 Richardson steps as one CUDA graph, 0 host loop; OPT_BATCH_WORKERS:
     problems of kron_ridge_batched solved concurrently, 1..32; OPT_GROUPING: draws grouped
-    by 0 automatic choice, 1 radix sort, 2 ranks in a bitmap of the key space; OPT_HOST_GATHER:
-    1 host-buffer solves gather the sampled entries of a page-locked b in place, 0 copy b)."""
+    by 0 automatic choice, 1 radix sort, 2 ranks in a bitmap of the key space, 3 ranks with dense
+    per-key counters; OPT_HOST_GATHER: 1 host-buffer solves gather the sampled entries of a
+    page-locked b in place, 0 copy b; OPT_JL_K: 0 exact leverage scores, k in [1, 64]
+    JL-approximate scores with k sign columns; OPT_JL_SEED: their Philox key)."""
     h = context()
     _check(lib().kr_set_option(h, int(key), int(value)), h)
 

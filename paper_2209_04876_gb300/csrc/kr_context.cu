@@ -93,6 +93,13 @@ extern "C" kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value) {
       if (value < 0 || value > 3) return kr_fail(ctx, KR_EINVAL, "kr_set_option: grouping must be 0, 1, 2 or 3");
       ctx->grouping = (int)value;
       return KR_OK;
+    case KR_OPT_JL_K:
+      if (value < 0 || value > 64) return kr_fail(ctx, KR_EINVAL, "kr_set_option: JL columns must be in [0, 64]");
+      ctx->jl_k = (int)value;
+      return KR_OK;
+    case KR_OPT_JL_SEED:
+      ctx->jl_seed = (uint64_t)value;
+      return KR_OK;
     case KR_OPT_HOST_GATHER:
       if (value != 0 && value != 1) return kr_fail(ctx, KR_EINVAL, "kr_set_option: host gather must be 0 or 1");
       ctx->host_gather = (int)value;

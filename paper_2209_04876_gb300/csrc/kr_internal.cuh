@@ -12,6 +12,21 @@
 
 #define KR_WARP 32
 
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from that paper's definition: a round
+// maps (x0, x1, x2, x3) to (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2), hi(M0 x0) ^ x3 ^ k1, lo(M0 x0)) with
+// M0 = 0xD2511F53, M1 = 0xCD9E8D57, and the key is bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
 // ------------------------------------------------------------------ context
 
 struct kr_ctx {
@@ -42,6 +57,8 @@ struct kr_ctx {
   int batch_workers = 4;  // kron_ridge_batched: problems solved concurrently (worker contexts)
   int grouping = 0;       // draws grouped by: 0 automatic, 1 radix sort, 2 ranks in a key bitmap
   int host_gather = 1;    // host-buffer solves: gather b~ from page-locked b in place (no copy of b)
+  int jl_k = 0;           // JL-approximate leverage scores with this many sign columns (0: exact scores)
+  uint64_t jl_seed = 0;   // Philox key of the JL sign matrices
   // worker contexts of kron_ridge_batched, each with its own stream and workspace (owned)
   std::vector<kr_ctx*> workers;
   std::vector<cudaStream_t> worker_streams;

@@ -243,6 +243,54 @@ __global__ void __launch_bounds__(LEV_ROWS * 32) k_leverage(ModePtrs mp) {
   if (lane == 0) mp.lev[n][r0 + w] = acc;
 }
 
+// JL-approximate scores (the approximate leverage scores of Alg. 2's first steps, with App. B's
+// Johnson-Lindenstrauss lemma): l~_i = ||a_i^T B||^2 / k with B = L^-T Pi (R x k), L the Cholesky
+// factor of the Gram matrix and Pi an R x k matrix of signs, entry (r, j) from the low bit of
+// word w0 of Philox4x32-10 under the JL key at counter (r k + j, 0, mode, 0) (0: +1, 1: -1).
+// E[l~_i] = l_i. The cost per row is R k instead of about R^2 / 2.
+constexpr int JL_MAXK = 64;
+__global__ void k_jl_basis(ModePtrs mp, int k, uint32_t s0, uint32_t s1, double* const* __restrict__ B) {
+  const int n = blockIdx.y;
+  const int R = mp.R[n];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < R * k; e += gridDim.x * blockDim.x) {
+    const int c = e / k, j = e - c * k;
+    double acc = 0.0;
+    for (int r = c; r < R; ++r) {  // (L^-1)^T: L^-1 is lower triangular
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)(r * k + j), 0u, (uint32_t)n, 0u), s0, s1);
+      const double sg = (w.x & 1u) ? -1.0 : 1.0;
+      acc = fma(mp.linv[n][r * R + c], sg, acc);
+    }
+    B[n][e] = acc;
+  }
+}
+
+// l~_i for LEV_ROWS rows per block, one warp per row, lanes over the k columns of B.
+__global__ void __launch_bounds__(LEV_ROWS * 32) k_leverage_jl(ModePtrs mp, int k, const double* const* __restrict__ B) {
+  const int n = blockIdx.y;
+  const int I = mp.I[n], R = mp.R[n];
+  const int r0 = blockIdx.x * LEV_ROWS;
+  if (r0 >= I) return;
+  extern __shared__ double sm[];
+  double* Bs = sm;                 // R x k
+  double* a = sm + MAXR * JL_MAXK;  // LEV_ROWS x LD
+  const int rows = min(LEV_ROWS, I - r0);
+  for (int e = threadIdx.x; e < R * k; e += blockDim.x) Bs[e] = B[n][e];
+  for (int e = threadIdx.x; e < rows * R; e += blockDim.x)
+    a[(e / R) * LD + (e % R)] = (double)mp.A[n][(int64_t)(r0 + e / R) * R + (e % R)];
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w >= rows) return;
+  double acc = 0.0;
+  for (int j = lane; j < k; j += 32) {
+    double v = 0.0;
+    for (int c = 0; c < R; ++c) v = fma(a[w * LD + c], Bs[c * k + j], v);
+    acc = fma(v, v, acc);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) mp.lev[n][r0 + w] = acc / (double)k;
+}
+
 // One block per mode: left-to-right FP64 prefix of the scores (the convention of the
 // sampling tables), normalised CDF, integer thresholds, probabilities and FP32 inverse
 // probabilities. The prefix is one dependent chain of additions: the scores are staged in
@@ -466,6 +514,7 @@ void kr_tables_need(const Modes& m, bool want_eig, Need& nd) {
     nd.add<uint64_t>(I);
     nd.add<float>(I);
     nd.add<float>((size_t)R * R);
+    nd.add<double>((size_t)R * JL_MAXK);  // JL basis L^-T Pi
     if (want_eig) {
       nd.add<float>((size_t)R * R);
       nd.add<float>(R);
@@ -479,6 +528,7 @@ void kr_tables_need(const Modes& m, bool want_eig, Need& nd) {
 kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv, FactorTables& t, bool check_rank) {
   double* V64[KR_MAX_MODES] = {};
   double* s64[KR_MAX_MODES] = {};
+  double* jlB[KR_MAX_MODES] = {};
   ModePtrs mp = {};
   mp.N = m.N;
   t.N = m.N;
@@ -496,6 +546,7 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
     mp.thr[n] = t.thr[n] = cv.take<uint64_t>(I);
     mp.invp[n] = t.invp[n] = cv.take<float>(I);
     mp.ginv[n] = t.ginv[n] = cv.take<float>((size_t)R * R);
+    jlB[n] = cv.take<double>((size_t)R * JL_MAXK);
     if (want_eig) {
       mp.V[n] = t.V[n] = cv.take<float>((size_t)R * R);
       mp.sig2[n] = t.sig2[n] = cv.take<float>(R);
@@ -518,7 +569,16 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
   KR_LAUNCH(ctx, k_gram_reduce, dim3((maxR * maxR + 255) / 256, m.N), 256, 0, mp);
   KR_LAUNCH(ctx, k_cholesky, m.N, 256, chol_smem, mp);
   dim3 gl((maxI + LEV_ROWS - 1) / LEV_ROWS, m.N);
-  KR_LAUNCH(ctx, k_leverage, gl, LEV_ROWS * 32, lev_smem, mp);
+  if (ctx->jl_k > 0) {
+    const int k = ctx->jl_k;
+    const size_t jl_smem = ((size_t)MAXR * JL_MAXK + LEV_ROWS * LD) * sizeof(double);
+    KR_TRY(kr_smem_attr(ctx, k_leverage_jl, jl_smem));
+    KR_LAUNCH(ctx, k_jl_basis, dim3((maxR * k + 255) / 256, m.N), 256, 0, mp, k, (uint32_t)ctx->jl_seed,
+              (uint32_t)(ctx->jl_seed >> 32), (double* const*)jlB);
+    KR_LAUNCH(ctx, k_leverage_jl, gl, LEV_ROWS * 32, jl_smem, mp, k, (const double* const*)jlB);
+  } else {
+    KR_LAUNCH(ctx, k_leverage, gl, LEV_ROWS * 32, lev_smem, mp);
+  }
   KR_LAUNCH(ctx, k_cdf, m.N, CDF_THREADS, 0, mp);
   if (want_eig) {
     KR_TRY(kr_eig64(ctx, m.N, m.R, mp.gram, V64, s64));

@@ -407,3 +407,28 @@ def test_eps_rule_stops_on_a_zero_residual_problem():
     x, it = ko.richardson(As, b[smp.keys], smp, 0.0, eps, stop="eps", tol=1e-12, max_iter=2000)
     assert it < 200
     assert np.linalg.norm(x - xt) <= 1e-10 * np.linalg.norm(xt)
+
+
+def test_jl_scores_cholesky_route_and_unbiasedness():
+    """JL-approximate scores: (a) the QR route of the oracle equals the Cholesky route
+    l~ = ||A L^-T Pi||^2 / k with L = cholesky(A^T A) on the same signs; (b) the signs are +-1 with
+    mean near 0; (c) averaged over 400 seeds the scores approach the exact ones (E[l~] = l);
+    (d) with k = 4096 every score is within 10 % of the exact one (JL concentration); (e) the
+    scores sum to the rank for any sign matrix."""
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((300, 12)) * np.exp(rng.standard_normal(300))[:, None]
+    k = 16
+    got = ko.jl_leverage_scores(A, k, seed=77, mode=2)
+    L = np.linalg.cholesky(A.T @ A)
+    P = ko.jl_signs(12, k, 77, 2)
+    B = np.linalg.solve(L.T, P)
+    np.testing.assert_allclose(got, np.sum((A @ B) ** 2, axis=1) / k, rtol=1e-10)
+    assert set(np.unique(P)) <= {-1.0, 1.0} and abs(P.mean()) < 0.2
+    exact = ko.leverage_scores(A)
+    mean = np.mean([ko.jl_leverage_scores(A, k, seed=s, mode=0) for s in range(400)], axis=0)
+    assert np.max(np.abs(mean - exact) / exact) < 0.2
+    big = ko.jl_leverage_scores(A, 4096, seed=5, mode=1)
+    assert np.max(np.abs(big - exact) / exact) < 0.1
+    # (e) for any signs the scores sum to the rank: ||Q Pi||_F^2 / k = ||Pi||_F^2 / k = R
+    for kk in (1, 3, 16):
+        assert abs(ko.jl_leverage_scores(A, kk, seed=kk, mode=0).sum() - 12) < 1e-10
