@@ -255,6 +255,66 @@ def torch_unique_count(t):
     return torch.unique_consecutive(t).numel()
 
 
+TUCKER_WORKLOADS = {
+    # Tucker ALS: 256^3 tensor of multilinear rank (16,16,16) + 1% noise, lambda = 1e-3, 10 sweeps
+    "tucker_256x256x256_r16": dict(I=[256, 256, 256], R=[16, 16, 16], Rt=[16, 16, 16], noise_rel=0.01,
+                                   decay=False, lam=1e-3, eps=0.1, sweeps=10, seed=11),
+    # the cardiac MRI tensor's shape and rank (App. D), synthetic: Tucker tensor of twice the rank
+    # with a decaying core spectrum + 10% noise, 5 sweeps
+    "cardiac_mri_256x256x14x20": dict(I=[256, 256, 14, 20], R=[8, 8, 4, 4], Rt=[16, 16, 8, 8], noise_rel=0.1,
+                                      decay=True, lam=1e-3, eps=0.1, sweeps=5, seed=31),
+}
+
+
+def run_tucker(name):
+    """Sampled (Alg. 1 with Alg. 3 factor steps and Alg. 2 core steps) and exact (KronMatMul)
+    TuckerALS sweeps from the same start: milliseconds per sweep (host clock around the
+    synchronous calls, inputs resident) and the RRE after every sweep."""
+    import torch
+
+    import paper_2209_04876_gb300 as kr
+    from workloads import tucker_tensor_device
+
+    w = TUCKER_WORKLOADS[name]
+    I, R = w["I"], w["R"]
+    X = tucker_tensor_device(I, w["Rt"], seed=w["seed"], noise_rel=w["noise_rel"],
+                             decay_rank=R if w["decay"] else None)
+
+    def start():
+        g = torch.Generator(device="cuda")
+        g.manual_seed(w["seed"] + 1)
+        As = [torch.linalg.qr(torch.randn(i, r, generator=g, device="cuda"))[0].contiguous() for i, r in zip(I, R)]
+        return As, kr.kron_matmul(As, X.reshape(-1), trans=[1] * len(As))
+
+    out = dict(I=I, R=R, lam=w["lam"], eps=w["eps"], sweeps=w["sweeps"], timing="host clock, synchronous calls")
+    As, G = start()
+    kr.tucker_als_exact_sweep(X, As, G, w["lam"], sweeps=1)  # warm-up
+    As, G = start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rre_e = kr.tucker_als_exact_sweep(X, As, G, w["lam"], sweeps=w["sweeps"])
+    torch.cuda.synchronize()
+    out["exact"] = dict(ms_per_sweep=1e3 * (time.perf_counter() - t0) / w["sweeps"], rre=rre_e)
+    N = len(I)
+    opts = dict(eps=w["eps"], seed=5, tol=1e-7, max_iter=300, stop_rule=kr.STOP_EPS)
+    As, G = start()
+    kr.tucker_als_sweep(X, As, G, w["lam"], sweeps=1, call_id=50, **opts)  # warm-up
+    As, G = start()
+    rre_s, t = [], 0.0
+    for k in range(w["sweeps"]):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        kr.tucker_als_sweep(X, As, G, w["lam"], sweeps=1, call_id=100 + k * (N + 1), **opts)
+        torch.cuda.synchronize()
+        t += time.perf_counter() - t0
+        rre_s.append(kr.tucker_rre(X, As, G))
+    out["sampled"] = dict(ms_per_sweep=1e3 * t / w["sweeps"], rre=rre_s, stop_rule="(1+eps)-aware")
+    out["rre_ratio_last"] = rre_s[-1] / rre_e[-1]
+    del X, As, G
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args, rank, world, local):
     import torch
 
@@ -398,6 +458,8 @@ def run_gpu(args, rank, world, local):
         clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"], samples=clk["samples"]),
         phases_ms={k: float(np.mean([r["t_ms"][k] for r in reps])) for k in reps[0]["t_ms"]},
     )
+    if not args.no_tucker:
+        line["tucker"] = {name: run_tucker(name) for name in TUCKER_WORKLOADS}
     if not args.no_cpu_baseline:
         it_c = max(1, min(int(round(iters)), args.cpu_iters))
         v, s_c, dt = oracle_rows_per_s(w, As64, b32, it_c, args.cpu_fraction)
@@ -406,6 +468,40 @@ def run_gpu(args, rank, world, local):
             sample="%d of the %d draws (%.3g), full tables, grouping, gather and %d FP64 Richardson iteration(s)"
                    % (s_c, s, args.cpu_fraction, it_c), seconds=dt)
     print(json.dumps(line), flush=True)
+
+
+PROFILE_CASES = ("kron_rmatvec_512x512x1024_r64", "kron_n3_1024x1024x256_r64_outliers")
+
+
+def run_case(name):
+    """Small cases for ncu captures (a few GB on the device): three K^T z products at
+    512 x 512 x 1024 with R = 64 (the tensor-core mode product), or three solves of the
+    1024 x 1024 x 256, R = 64 outlier problem with a quarter of the sample count (the slab
+    pass at the large workload's cell structure)."""
+    import torch
+
+    import paper_2209_04876_gb300 as kr
+    from workloads import kron_problem_device
+
+    torch.cuda.set_device(0)
+    if name == "kron_rmatvec_512x512x1024_r64":
+        I, R = [512, 512, 1024], [64, 64, 64]
+        g = torch.Generator(device="cuda")
+        g.manual_seed(1)
+        As = [torch.randn(i, r, generator=g, device="cuda") for i, r in zip(I, R)]
+        z = torch.randn(int(np.prod(I)), generator=g, device="cuda")
+        for _ in range(3):
+            y = kr.kron_matmul(As, z, trans=[1, 1, 1])
+        torch.cuda.synchronize()
+        print(name, "max|y| %.6g" % float(y.abs().max()))
+    else:
+        p = kron_problem_device([1024, 1024, 256], [64, 64, 64], dist="outliers", seed=2210, noise_rel=0.01,
+                                b_kind="tucker", tucker_rank=[64, 64, 64])
+        s = kr.kron_sample_count(64 ** 3, 0.05) // 4
+        for k in range(3):
+            _, rep = kr.kron_regress(p["As"], p["b"], eps=0.05, seed=1, call_id=k, num_samples=s,
+                                     stop_rule=kr.STOP_EPS, max_iter=200)
+            print(name, "iters", rep["iters"], "distinct", rep["distinct"])
 
 
 def main():
@@ -420,7 +516,12 @@ def main():
     ap.add_argument("--ref-fraction", type=float, default=0.001)
     ap.add_argument("--ref-iters", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tucker", action="store_true", help="skip the TuckerALS sweep timings")
+    ap.add_argument("--case", choices=PROFILE_CASES, help="run one small profiling case and exit")
     args = ap.parse_args()
+    if args.case:
+        run_case(args.case)
+        return
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -61,8 +61,9 @@ typedef enum {
   KR_ERANK = 5,       /* a factor matrix is numerically rank deficient */
   KR_ENOTCONV = 6,    /* max_iter reached before the stopping rule held */
   KR_EDIVERGED = 7,   /* the Richardson step grew 3 times in a row */
-  KR_ETIMEOUT = 8,    /* reserved: a bounded device wait ran out. No kernel of this build waits on a
-                         flag that another kernel or device sets, so no call returns it now */
+  KR_ETIMEOUT = 8,    /* a bounded device wait ran out: the tensor-core mode product's pipeline
+                         waits (TMA, MMA and epilogue mbarriers) give up after about 2 s, free
+                         their tensor memory and report it; the context stays usable */
   KR_ENOTIMPL = 9     /* shape outside what this build supports */
 } kr_status;
 
@@ -137,6 +138,10 @@ KR_API const char* kr_last_error(const kr_ctx* ctx);
 /* Number of kernels this context has launched so far (instrumentation). */
 KR_API int64_t kr_launch_count(const kr_ctx* ctx);
 
+/* Launches of the tcgen05 tensor-core kernel (the 3xTF32 mode product, KR_OPT_TENSOR_CORES)
+ * on this context so far; counted in kr_launch_count too. */
+KR_API int64_t kr_tc_launch_count(const kr_ctx* ctx);
+
 /* Per-kernel timing (instrumentation, off by default). When enabled, the library
  * records a CUDA event pair on its stream around every launch of the kernel kinds
  * below; kr_timing_read synchronises the stream and returns, for one kind, the summed
@@ -193,6 +198,11 @@ enum {
  *    (kron_leverage, the solvers, the Tucker steps); the weights use the same scores, so the
  *    sketch stays unbiased.
  *  KR_OPT_JL_SEED (default 0): the Philox key of the JL sign matrices.
+ *  KR_OPT_TENSOR_CORES (default 1): 1 runs the mode products of KronMatMul (Lemma 4.3) whose
+ *    contracted index is the last, contiguous one (M x K times K x J with M >= 1024 rows,
+ *    K >= 32 and a multiple of 4, J <= 256, the input 16-byte aligned) on the tcgen05 tensor
+ *    cores in 3xTF32 (FP32 accuracy: operands split into TF32 hi and lo parts, FP32
+ *    accumulation); 0 keeps every mode product on the CUDA cores.
  * Returns KR_EINVAL for an unknown key or a value out of range. */
 enum {
   KR_OPT_SLAB_PASS = 1,
@@ -202,7 +212,8 @@ enum {
   KR_OPT_GROUPING = 5,
   KR_OPT_HOST_GATHER = 6,
   KR_OPT_JL_K = 7,
-  KR_OPT_JL_SEED = 8
+  KR_OPT_JL_SEED = 8,
+  KR_OPT_TENSOR_CORES = 9
 };
 KR_API kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value);
 

@@ -21,8 +21,8 @@ STATUS = {0: "KR_OK", 1: "KR_EINVAL", 2: "KR_ENOMEM", 3: "KR_ECUDA", 4: "KR_ENON
 KERNEL_KINDS = {"resid": 0, "modeprod": 1, "sample": 2, "scatter": 3, "dedup": 4, "tables": 5, "vector": 6,
                 "slab": 7}
 OPT_SLAB_PASS, OPT_SLAB_TILE_ENTRIES, OPT_DEVICE_LOOP, OPT_BATCH_WORKERS, OPT_GROUPING, OPT_HOST_GATHER = 1, 2, 3, 4, 5, 6
-OPT_JL_K, OPT_JL_SEED = 7, 8
-EXPORTED = ["kr_create", "kr_destroy", "kr_set_stream", "kr_last_error", "kr_launch_count", "kr_timing_enable",
+OPT_JL_K, OPT_JL_SEED, OPT_TENSOR_CORES = 7, 8, 9
+EXPORTED = ["kr_create", "kr_destroy", "kr_set_stream", "kr_last_error", "kr_launch_count", "kr_tc_launch_count", "kr_timing_enable",
             "kr_timing_read", "kr_timing_reset", "kr_set_option", "kron_sample_count", "kron_leverage",
             "kron_sample", "kron_sample_noalloc", "kron_sketch", "kron_sketch_distinct", "kron_sketch_export", "kron_sketch_residual",
             "kron_sketch_free", "kron_matmul", "kron_precond", "kron_objective", "kron_regress", "kron_ridge",
@@ -84,6 +84,7 @@ def lib():
             "kr_set_stream": (i32, [vp, vp]),
             "kr_last_error": (ctypes.c_char_p, [vp]),
             "kr_launch_count": (i64, [vp]),
+            "kr_tc_launch_count": (i64, [vp]),
             "kr_timing_enable": (i32, [vp, i32]),
             "kr_timing_read": (i32, [vp, i32, P(dbl), P(i64)]),
             "kr_timing_reset": (i32, [vp]),
@@ -136,6 +137,11 @@ def launch_count():
     return int(lib().kr_launch_count(context()))
 
 
+def tc_launch_count():
+    """Launches of the tcgen05 tensor-core mode product on this device's context so far."""
+    return int(lib().kr_tc_launch_count(context()))
+
+
 def timing_enable(on=True):
     h = context()
     _check(lib().kr_timing_enable(h, int(bool(on))), h)
@@ -149,7 +155,8 @@ def set_option(key, value):
     by 0 automatic choice, 1 radix sort, 2 ranks in a bitmap of the key space, 3 ranks with dense
     per-key counters; OPT_HOST_GATHER: 1 host-buffer solves gather the sampled entries of a
     page-locked b in place, 0 copy b; OPT_JL_K: 0 exact leverage scores, k in [1, 64]
-    JL-approximate scores with k sign columns; OPT_JL_SEED: their Philox key)."""
+    JL-approximate scores with k sign columns; OPT_JL_SEED: their Philox key; OPT_TENSOR_CORES:
+    1 contiguous-index mode products of KronMatMul on tcgen05 in 3xTF32, 0 CUDA cores)."""
     h = context()
     _check(lib().kr_set_option(h, int(key), int(value)), h)
 

@@ -54,6 +54,7 @@ extern "C" kr_status kr_create(kr_ctx** out, void* stream, size_t workspace_byte
   int optin = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   ctx->smem_optin = (size_t)optin;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->cc_major, cudaDevAttrComputeCapabilityMajor, ctx->device);
   for (int i = 0; i < 10 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ctx->pev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -100,6 +101,10 @@ extern "C" kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value) {
     case KR_OPT_JL_SEED:
       ctx->jl_seed = (uint64_t)value;
       return KR_OK;
+    case KR_OPT_TENSOR_CORES:
+      if (value != 0 && value != 1) return kr_fail(ctx, KR_EINVAL, "kr_set_option: tensor cores must be 0 or 1");
+      ctx->tensor_cores = (int)value;
+      return KR_OK;
     case KR_OPT_HOST_GATHER:
       if (value != 0 && value != 1) return kr_fail(ctx, KR_EINVAL, "kr_set_option: host gather must be 0 or 1");
       ctx->host_gather = (int)value;
@@ -129,6 +134,8 @@ extern "C" void kr_destroy(kr_ctx* ctx) {
   if (ctx->io) cudaFree(ctx->io);
   if (ctx->split_buf) cudaFree(ctx->split_buf);
   if (ctx->dcnt) cudaFree(ctx->dcnt);
+  if (ctx->tc_buf) cudaFree(ctx->tc_buf);
+  if (ctx->tc_err) cudaFree(ctx->tc_err);
   if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
   for (int i = 0; i < 10; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
@@ -263,7 +270,9 @@ int kr_kind_of(const char* k) {
   std::string s(k);
   if (s.find("k_resid") != std::string::npos) return KR_K_RESID;
   if (s.find("k_slab") != std::string::npos) return KR_K_SLAB;
-  if (s.find("k_mode_product") != std::string::npos) return KR_K_MODEPROD;
+  if (s.find("k_mode_product") != std::string::npos || s.find("k_gemm_tc") != std::string::npos ||
+      s.find("k_tc_split") != std::string::npos)
+    return KR_K_MODEPROD;
   if (s.find("k_sample") != std::string::npos || s.find("k_draw") != std::string::npos ||
       s.find("k_guide") != std::string::npos)
     return KR_K_SAMPLE;

@@ -33,6 +33,7 @@ struct kr_ctx {
   int device = 0;
   int num_sms = 0;
   size_t smem_optin = 0;
+  int cc_major = 0;
   cudaStream_t stream = nullptr;
   std::string err;
   int64_t launches = 0;
@@ -59,6 +60,12 @@ struct kr_ctx {
   int host_gather = 1;    // host-buffer solves: gather b~ from page-locked b in place (no copy of b)
   int jl_k = 0;           // JL-approximate leverage scores with this many sign columns (0: exact scores)
   uint64_t jl_seed = 0;   // Philox key of the JL sign matrices
+  int tensor_cores = 1;   // contiguous-index mode products on tcgen05 (3xTF32) where eligible
+  // split B planes of the tensor-core mode product (grow-on-demand) and its device error word
+  float* tc_buf = nullptr;
+  size_t tc_size = 0;
+  int* tc_err = nullptr;
+  int64_t tc_launches = 0;
   // worker contexts of kron_ridge_batched, each with its own stream and workspace (owned)
   std::vector<kr_ctx*> workers;
   std::vector<cudaStream_t> worker_streams;
@@ -258,6 +265,14 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
 // ------------------------------------------------------------------ mode products
 
 // out[p, j, q] = sum_k B[j, k] * in[p, k, q], B stored J x K (trans = 0) or K x J (trans = 1).
+// Tensor-core (tcgen05, 3xTF32) product Y[m, j] = sum_k X[m, k] B[j, k] (B stored K x J
+// when trans), Y rows ldy floats apart; KR_ENOTIMPL when the shape or the build does not
+// qualify (the caller then uses the CUDA-core kernel). kr_tc_check reads the kernel's
+// error word (synchronises the stream): KR_ETIMEOUT when one of its bounded waits ran out.
+bool kr_tc_eligible(const kr_ctx* ctx, const float* X, int64_t M, int K, int J);
+kr_status kr_gemm_tc(kr_ctx* ctx, const float* X, int64_t M, int K, const float* B, int J, int trans, float* Y,
+                     int64_t ldy);
+kr_status kr_tc_check(kr_ctx* ctx);
 kr_status kr_mode_product(kr_ctx* ctx, const float* in, float* out, int64_t P, int K, int64_t Q, int J,
                           const float* B, int trans);
 // KronMatMul along the modes with B[n] != nullptr (identity elsewhere); intermediates

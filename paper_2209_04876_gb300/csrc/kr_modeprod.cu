@@ -268,6 +268,10 @@ kr_status kr_mode_product(kr_ctx* ctx, const float* in, float* out, int64_t P, i
                           int trans) {
   const int64_t NN = P * Q;
   if (NN == 0 || J == 0) return KR_OK;
+  if (Q == 1 && kr_tc_eligible(ctx, in, P, K, J)) {  // contiguous contraction: tcgen05, 3xTF32
+    const kr_status st = kr_gemm_tc(ctx, in, P, K, B, J, trans, out, J);
+    if (st != KR_ENOTIMPL) return st;
+  }
   const bool aligned = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
   if (Q % 4 == 0 && aligned) {
     // 64-row tiles unless they leave SMs idle (then 32-row tiles double the blocks)
@@ -337,8 +341,19 @@ kr_status kr_kron_apply2(kr_ctx* ctx, int N, const int* dimsIn, const int* dimsO
     KR_CUDA(ctx, cudaMemcpyAsync(tmp0, in, sizeof(float) * tot, cudaMemcpyDeviceToDevice, ctx->stream));
     src = tmp0;
   }
+  // Mode products commute. When the last mode shrinks and its product qualifies for the
+  // tensor cores (contiguous contraction over the whole input), it goes first: the pass over
+  // the largest tensor then runs on tcgen05 and every later product sees the reduced tensor.
+  int order[KR_MAX_MODES];
+  for (int n = 0; n < N; ++n) order[n] = n;
+  if (N > 1 && B[N - 1] && dimsOut[N - 1] < dimsIn[N - 1] && kr_tc_eligible(ctx, src, tot / dimsIn[N - 1],
+                                                                               dimsIn[N - 1], dimsOut[N - 1])) {
+    for (int n = N - 1; n > 0; --n) order[n] = order[n - 1];
+    order[0] = N - 1;
+  }
   int a = 0;
-  for (int n = 0; n < N; ++n) {
+  for (int o = 0; o < N; ++o) {
+    const int n = order[o];
     if (!B[n]) continue;
     int64_t P = 1, Q = 1;
     for (int m = 0; m < n; ++m) P *= cur[m];
@@ -440,7 +455,7 @@ extern "C" kr_status kron_matmul(kr_ctx* ctx, int32_t N, const int64_t* J, const
   float* t1 = cv.take<float>(mx);
   KR_TRY(kr_kron_apply2(ctx, N, din, dout, B, tr, x, y, t0, t1));
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  return KR_OK;
+  return kr_tc_check(ctx);
 }
 
 extern "C" kr_status kron_precond(kr_ctx* ctx, const kr_factors* f, double lambda, const float* g, float* d) {
