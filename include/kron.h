@@ -88,7 +88,18 @@ typedef struct {
   int32_t max_iter;      /* Richardson iteration cap; <= 0 selects 100 */
   double tol;            /* stop when ||step|| <= tol * ||x||; <= 0 selects 1e-7 */
   double step;           /* Richardson step; <= 0 selects the paper's 1 - sqrt(eps) */
-  int32_t precision;     /* 0: FP32 contractions (the only value this build accepts; others give KR_ENOTIMPL) */
+  int32_t precision;     /* contraction format of the sampled products (slab passes of Alg. 2):
+                            0: FP32-accurate (3xTF32 tensor-core products, FP32 residuals);
+                            1: BF16 tensor-core products, 2: FP8 e4m3 with one scale per row of
+                            the non-contracted index (both FP32 accumulation, FP32 residuals).
+                            With 1 or 2 the Richardson loop runs its steps in that format until
+                            its step falls below max(tol, 2^-7) (BF16) or max(tol, 2^-4) (e4m3)
+                            or the stopping rule holds, then continues with FP32-accurate steps
+                            from that point until the stopping rule holds (iterative refinement:
+                            the fixed point is the FP32 path's); the final objective check is
+                            always FP32/FP64. e4m3 needs R_{N-1} % 32 == 0 and BF16
+                            R_{N-1} % 16 == 0 (else the next finer format); the per-cell path
+                            (KR_OPT_SLAB_PASS 0) and the Alg. 3 factor steps ignore it. */
   int32_t host_io;       /* 1: factors, b / X and x / A / G are host pointers */
   uint64_t seed;         /* Philox key */
   uint64_t call_id;      /* Philox counter word 3 (distinguishes sketches drawn with one seed) */
@@ -120,6 +131,9 @@ typedef struct {
   double obj_sampled;        /* ||S(Kx - b)||^2 + lambda ||x||^2 at the returned x, FP64 accumulation */
   double rel_update;         /* last ||step|| / ||x|| */
   float t_ms[8];             /* leverage, sample, group+gather, rhs, iterate, final check, copies, total */
+  int32_t iters_reduced;     /* of iters, the steps whose sampled products ran in reduced precision */
+  int32_t precision_used;    /* contraction format of those steps (kr_opts.precision after the
+                                shape fallback: 0 when every step ran FP32-accurate) */
 } kr_report;
 
 /* ---------------------------------------------------------------- context */

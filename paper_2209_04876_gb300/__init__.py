@@ -53,13 +53,14 @@ class KrOpts(ctypes.Structure):
 class KrReport(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("s", ctypes.c_int64),
                 ("distinct", ctypes.c_int64), ("obj_sampled", ctypes.c_double), ("rel_update", ctypes.c_double),
-                ("t_ms", ctypes.c_float * 8)]
+                ("t_ms", ctypes.c_float * 8), ("iters_reduced", ctypes.c_int32), ("precision_used", ctypes.c_int32)]
 
     def as_dict(self):
         names = ["leverage", "sample_group_gather", "unused", "init", "iterate", "final_check", "copies", "total"]
         return dict(iters=self.iters, converged=bool(self.converged), stop=int(self.converged), s=self.s,
                     distinct=self.distinct,
                     obj_sampled=self.obj_sampled, rel_update=self.rel_update,
+                    iters_reduced=self.iters_reduced, precision_used=self.precision_used,
                     t_ms={k: float(v) for k, v in zip(names, self.t_ms)})
 
 

@@ -387,7 +387,10 @@ kr_status kr_tiles_build(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, Carve& 
 // per-tile objective partials go to tl->objpart (tl->ntmax doubles).
 // rearm: zero the tile counter first (needed when no tile reduction followed the last pass).
 kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const float* A2, const float* AT,
-                       const float* X1, bool want_obj, bool rearm);
+                       const float* X1, bool want_obj, bool rearm, int prec = 0);
+// The contraction format a slab pass asked for `prec` (0 FP32-accurate 3xTF32, 1 BF16,
+// 2 e4m3 with per-row scales) runs at for these ranks (falls back to the next finer one).
+int kr_slab_precision(int R2, int RT, int prec);
 // W[p', r, :] = sum over the tiles of the slabs p' * Iq + i of Aq[i, r] zpart[t, :]
 // (Aq = A(N-3) for N >= 3, nullptr for N = 2): Pq x Rq x R2 x RT floats. With Aq2 the same
 // sum with the weights Aq2 goes to W2 (one pass over the tiles for both). With opart the
@@ -404,6 +407,7 @@ struct SolveCfg {
   int64_t s;
   int stop_rule = 0;     // 1: the (1+eps)-aware rule (kr_opts.stop_rule)
   double theta = 0.01;   // its fraction of eps
+  int prec = 0;          // kr_opts.precision: slab-pass contractions of the first phase
 };
 
 enum StepCheck { STEP_CONTINUE, STEP_CONVERGED, STEP_FLOOR, STEP_DIVERGED, STEP_NONFINITE, STEP_MAXITER, STEP_EPS };

@@ -23,6 +23,8 @@
 // group order afterwards. Every sum has a fixed order, so the pass is deterministic.
 // Slabs split over several tiles are completed by the last of their tiles to finish,
 // which adds the tiles' contributions in tile order.
+#include <cuda_bf16.h>
+
 #include "kr_internal.cuh"
 
 namespace {
@@ -95,6 +97,40 @@ __device__ __forceinline__ void mma_tf32x3(float* c, const uint32_t* ah, const u
   mma_tf32(c, ah, bl);
   mma_tf32(c, ah, bh);
 }
+
+// Reduced-precision products (kr_opts.precision 1 and 2): one BF16 m16n8k16 MMA, or one
+// FP8 (e4m3) m16n8k32 MMA whose operands are scaled per row of the non-contracted index
+// (the scales factor out of the sum and multiply the FP32 result), FP32 accumulation.
+// Pairs and quads pack the element with the smaller k index in the low bits.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// e4m3 pair with saturation to +-448: the first source goes to the high byte
+__device__ __forceinline__ uint32_t cvt_e4m3x2(float hi, float lo) {
+  uint16_t r;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+__device__ __forceinline__ uint32_t pack_e4m3(float x0, float x1, float x2, float x3) {
+  return cvt_e4m3x2(x1, x0) | (cvt_e4m3x2(x3, x2) << 16);
+}
+__device__ __forceinline__ void mma_e4m3(float* c, const uint32_t* a, const uint32_t* b) {
+  asm("mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+constexpr float E4M3_MAX = 448.f;
+// k steps of one MMA and the cell padding of the tile's Z product, per precision
+template <int PREC>
+struct PrecShape {
+  static constexpr int KS = PREC == 0 ? 8 : (PREC == 1 ? 16 : 32);
+};
 
 // Row `it` of A(N), the lane's quads qd[v] (zero past R_N).
 template <int RTP, bool SMEM_A>
@@ -206,12 +242,13 @@ __device__ __forceinline__ void slab_next_cell(float* sYW, float* sPf, const uin
   for (int c = 0; c < S::COLS; ++c) w[c] = 0.f;
 }
 
-template <int RTP, bool SMEM_A, bool OBJ>
+template <int RTP, bool SMEM_A, bool OBJ, int PREC>
 __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
   using S = SlabShape<RTP>;
   constexpr int COLS = S::COLS, G = S::G, NQ = S::NQ, NG = S::NG;
   constexpr int XQ = RTP / 4;
   constexpr int NT8 = RTP >= 8 ? RTP / 8 : 1;   // n tiles of the tensor-core products
+  constexpr int KS = PrecShape<PREC>::KS;       // k of one MMA: cells are padded to it
   const bool mma = RTP >= 8 && a.mma;
   extern __shared__ float4 slab_smem[];
   char* sm = reinterpret_cast<char*>(slab_smem);
@@ -284,25 +321,64 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
       if (tt == na - 1) sCS[na] = ac.y + ac.z;
       const uint32_t i2 = ac.x % (uint32_t)a.I2;
       float* dst = sA2 + tt * R2S;
+      float amax = 0.f;
       if (a.a2vec) {
         const float4* row = reinterpret_cast<const float4*>(a.A2 + (size_t)i2 * R2);
-        for (int k4 = 0; k4 < R2P / 4; ++k4)
-          reinterpret_cast<float4*>(dst)[k4] = 4 * k4 < R2 ? __ldg(row + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k4 = 0; k4 < R2P / 4; ++k4) {
+          const float4 v = 4 * k4 < R2 ? __ldg(row + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+          reinterpret_cast<float4*>(dst)[k4] = v;
+          amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
       } else {
         const float* row = a.A2 + (size_t)i2 * R2;
-        for (int k2 = 0; k2 < R2P; ++k2) dst[k2] = k2 < R2 ? __ldg(row + k2) : 0.f;
+        for (int k2 = 0; k2 < R2P; ++k2) {
+          dst[k2] = k2 < R2 ? __ldg(row + k2) : 0.f;
+          amax = fmaxf(amax, fabsf(dst[k2]));
+        }
       }
-    } else if (mma && tt < ((na + 7) & ~7)) {
-      // rows past the last cell up to the next multiple of 8 are the padding of the
-      // tensor-core Z product's last k step: zero in both operands (A(N-1) rows here, W rows
-      // of sYW below), so they add exactly nothing
+      if (PREC == 2) sPf[tt] = amax > 0.f ? amax / E4M3_MAX : 1.f;  // e4m3 scale of this row
+    } else if (mma && tt < ((na + KS - 1) & ~(KS - 1))) {
+      // rows past the last cell up to the next multiple of the MMA's k are the padding of
+      // the tensor-core Z product's last k step: zero in both operands (A(N-1) rows here, W
+      // rows of sYW below), so they add exactly nothing
       for (int k2 = 0; k2 < R2P; ++k2) sA2[tt * R2S + k2] = 0.f;
 #pragma unroll
       for (int c = 0; c < RTP; ++c) sYW[tt * RTP + c] = 0.f;
+      if (PREC == 2) sPf[tt] = 1.f;
     }
     {
       const float* xp = a.X1 + p * zn;
-      if (mma) {  // X1[p] split once into TF32 hi / lo planes, rows of XS floats
+      if (PREC == 1 && mma) {
+        // X1[p]^T in BF16: row c holds column c of X1[p] (r contiguous), XS32 words a row
+        uint16_t* xt = reinterpret_cast<uint16_t*>(sX1);
+        const int xs2 = 2 * (R2P / 2 + 4);
+        for (int i = tt; i < R2P * RTP; i += SLAB_TEAM) {
+          const int r = i / RTP, c = i % RTP;
+          const float v = (r < R2 && c < RT) ? __ldg(xp + r * RT + c) : 0.f;
+          const __nv_bfloat16 h = __float2bfloat16_rn(v);
+          xt[c * xs2 + r] = *reinterpret_cast<const uint16_t*>(&h);
+        }
+      } else if (PREC == 2 && mma) {
+        // X1[p]^T in e4m3 with one scale per column c of X1[p] (the MMA's n index)
+        float* xsc = sPf + S::CB;
+        if (tt < RTP) {
+          float m = 0.f;
+          if (tt < RT)
+            for (int r = 0; r < R2; ++r) m = fmaxf(m, fabsf(__ldg(xp + r * RT + tt)));
+          xsc[tt] = m > 0.f ? m / E4M3_MAX : 1.f;
+        }
+        team_sync(team);
+        uint8_t* xt = reinterpret_cast<uint8_t*>(sX1);
+        const int xs4 = 4 * (R2P / 4 + 4);
+        for (int i = tt; i < R2P * RTP / 2; i += SLAB_TEAM) {
+          const int r = (2 * i) / RTP, c = (2 * i) % RTP;  // two columns c, c + 1 of row r
+          const float v0 = (r < R2 && c < RT) ? __ldg(xp + r * RT + c) / xsc[c] : 0.f;
+          const float v1 = (r < R2 && c + 1 < RT) ? __ldg(xp + r * RT + c + 1) / xsc[c + 1] : 0.f;
+          const uint32_t q = cvt_e4m3x2(v1, v0);
+          xt[c * xs4 + r] = (uint8_t)(q & 0xFFu);
+          xt[(c + 1) * xs4 + r] = (uint8_t)(q >> 8);
+        }
+      } else if (mma) {  // X1[p] split once into TF32 hi / lo planes, rows of XS floats
         uint32_t* xh = reinterpret_cast<uint32_t*>(sX1);
         uint32_t* xl = xh + R2P * a.XS;
         for (int i = tt; i < R2P * RTP; i += SLAB_TEAM) {
@@ -319,7 +395,68 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
     }
     team_sync(team);
     // ---- Y rows of the tile's cells: sYW[k] = A(N-1)[i_k] X1[p]
-    if (mma) {
+    if (PREC != 0 && mma) {
+      // one 16-row block of cells per warp, all RTP columns: A = rows of A(N-1) (a0 (g, k0),
+      // a1 (g + 8, k0), a2 (g, k1), a3 (g + 8, k1)), B = X1[p]^T rows (b0 at k0, b1 at k1 of
+      // column n = g), C as in the TF32 form; BF16: k0 = 2q.., k1 = 2q + 8..; e4m3: k0 =
+      // 4q.., k1 = 4q + 16.. (g = lane / 4, q = lane % 4)
+      const int fr = lane >> 2, fc = lane & 3;
+      const uint32_t* xt = reinterpret_cast<const uint32_t*>(sX1);
+      const int xs = PREC == 1 ? R2P / 2 + 4 : R2P / 4 + 4;  // words per X1^T row
+      const float* xsc = sPf + S::CB;
+      const int nmt = (na + 15) >> 4;
+      for (int mt = wt; mt < nmt; mt += SLAB_TEAM / 32) {
+        float acc[NT8][4];
+#pragma unroll
+        for (int nt = 0; nt < NT8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+        const float* ar0 = sA2 + (16 * mt + fr) * R2S;
+        const float* ar1 = ar0 + 8 * R2S;
+        float is0 = 1.f, is1 = 1.f;
+        if (PREC == 2) {
+          is0 = 1.f / sPf[16 * mt + fr];
+          is1 = 1.f / sPf[16 * mt + fr + 8];
+        }
+        for (int ks = 0; ks < R2P / KS; ++ks) {
+          uint32_t af[4];
+          if (PREC == 1) {
+            const int k0 = 16 * ks + 2 * fc;
+            af[0] = pack_bf16(ar0[k0], ar0[k0 + 1]);
+            af[1] = pack_bf16(ar1[k0], ar1[k0 + 1]);
+            af[2] = pack_bf16(ar0[k0 + 8], ar0[k0 + 9]);
+            af[3] = pack_bf16(ar1[k0 + 8], ar1[k0 + 9]);
+          } else {
+            const int k0 = 32 * ks + 4 * fc;
+            af[0] = pack_e4m3(ar0[k0] * is0, ar0[k0 + 1] * is0, ar0[k0 + 2] * is0, ar0[k0 + 3] * is0);
+            af[1] = pack_e4m3(ar1[k0] * is1, ar1[k0 + 1] * is1, ar1[k0 + 2] * is1, ar1[k0 + 3] * is1);
+            af[2] = pack_e4m3(ar0[k0 + 16] * is0, ar0[k0 + 17] * is0, ar0[k0 + 18] * is0, ar0[k0 + 19] * is0);
+            af[3] = pack_e4m3(ar1[k0 + 16] * is1, ar1[k0 + 17] * is1, ar1[k0 + 18] * is1, ar1[k0 + 19] * is1);
+          }
+#pragma unroll
+          for (int nt = 0; nt < NT8; ++nt) {
+            // one k step is 32 bytes (8 words) of an X1^T row in both formats; b1 is 16 bytes on
+            const uint32_t* xr = xt + (8 * nt + fr) * xs + 8 * ks + fc;
+            const uint32_t bf[2] = {xr[0], xr[4]};
+            if (PREC == 1) mma_bf16(acc[nt], af, bf);
+            else mma_e4m3(acc[nt], af, bf);
+          }
+        }
+        const int r0 = 16 * mt + fr, r1 = r0 + 8;
+#pragma unroll
+        for (int nt = 0; nt < NT8; ++nt) {
+          const int c0 = 8 * nt + 2 * fc;
+          float s00 = 1.f, s01 = 1.f, s10 = 1.f, s11 = 1.f;
+          if (PREC == 2) {
+            const float sr0 = sPf[r0], sr1 = sPf[r1];
+            s00 = sr0 * xsc[c0];
+            s01 = sr0 * xsc[c0 + 1];
+            s10 = sr1 * xsc[c0];
+            s11 = sr1 * xsc[c0 + 1];
+          }
+          if (r0 < na) *reinterpret_cast<float2*>(sYW + r0 * RTP + c0) = make_float2(acc[nt][0] * s00, acc[nt][1] * s01);
+          if (r1 < na) *reinterpret_cast<float2*>(sYW + r1 * RTP + c0) = make_float2(acc[nt][2] * s10, acc[nt][3] * s11);
+        }
+      }
+    } else if (mma) {
       // one 16-row block of cells per warp, all RTP columns: m16n8k8 fragments (A = rows of
       // A(N-1): a0 (g, q), a1 (g + 8, q), a2 (g, q + 4), a3 (g + 8, q + 4); B = X1[p]: b0 (q, g),
       // b1 (q + 4, g); C: (g, 2q), (g, 2q + 1), (g + 8, 2q), (g + 8, 2q + 1) with g = lane / 4,
@@ -500,6 +637,86 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
     }
     team_sync(team);
     // ---- Z contribution: sum_k A(N-1)[i_k]^T W[k]
+    if (PREC != 0 && mma) {
+      // one 16 x 8 block of Z per warp step over all cells (k): A = A(N-1)^T (m = r, k = cell),
+      // B = W (k = cell, n = column); fragment positions as in the Y product. e4m3: one scale
+      // per row r of A(N-1)^T and per column of W, over the tile's cells
+      const int fr = lane >> 2, fc = lane & 3;
+      float* usc = sPf;        // R2P scales of A(N-1)^T rows
+      float* vsc = sPf + R2P;  // RTP scales of W columns
+      if (PREC == 2) {
+        if (tt < R2P + RTP) {
+          const bool isu = tt < R2P;
+          const int c = isu ? tt : tt - R2P;
+          const float* src = isu ? sA2 + c : sYW + c;
+          const int stride = isu ? R2S : RTP;
+          float m = 0.f;
+          for (int i = 0; i < na; ++i) m = fmaxf(m, fabsf(src[i * stride]));
+          (isu ? usc : vsc)[c] = m > 0.f ? m / E4M3_MAX : 1.f;
+        }
+        team_sync(team);
+      }
+      const int nnt = NT8, nblk = (R2 / 16) * nnt, nks = (na + KS - 1) / KS;
+      float* dst = a.zpart + (size_t)t * zn;
+      for (int b = wt; b < nblk; b += SLAB_TEAM / 32) {
+        const int mt = b / nnt, nt = b - mt * nnt;
+        const int m0 = 16 * mt + fr, n0 = 8 * nt + fr;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        float iu0 = 1.f, iu1 = 1.f, iv = 1.f;
+        if (PREC == 2) {
+          iu0 = 1.f / usc[m0];
+          iu1 = 1.f / usc[m0 + 8];
+          iv = 1.f / vsc[n0];
+        }
+        for (int ks = 0; ks < nks; ++ks) {
+          uint32_t af[4], bf[2];
+          if (PREC == 1) {
+            const int k0 = 16 * ks + 2 * fc;
+            const float* a0 = sA2 + k0 * R2S + m0;
+            const float* w0 = sYW + k0 * RTP + n0;
+            af[0] = pack_bf16(a0[0], a0[R2S]);
+            af[1] = pack_bf16(a0[8], a0[R2S + 8]);
+            af[2] = pack_bf16(a0[8 * R2S], a0[9 * R2S]);
+            af[3] = pack_bf16(a0[8 * R2S + 8], a0[9 * R2S + 8]);
+            bf[0] = pack_bf16(w0[0], w0[RTP]);
+            bf[1] = pack_bf16(w0[8 * RTP], w0[9 * RTP]);
+            mma_bf16(acc, af, bf);
+          } else {
+            const int k0 = 32 * ks + 4 * fc;
+            const float* a0 = sA2 + k0 * R2S + m0;
+            const float* a2 = a0 + 16 * R2S;
+            const float* w0 = sYW + k0 * RTP + n0;
+            const float* w2 = w0 + 16 * RTP;
+            af[0] = pack_e4m3(a0[0] * iu0, a0[R2S] * iu0, a0[2 * R2S] * iu0, a0[3 * R2S] * iu0);
+            af[1] = pack_e4m3(a0[8] * iu1, a0[R2S + 8] * iu1, a0[2 * R2S + 8] * iu1, a0[3 * R2S + 8] * iu1);
+            af[2] = pack_e4m3(a2[0] * iu0, a2[R2S] * iu0, a2[2 * R2S] * iu0, a2[3 * R2S] * iu0);
+            af[3] = pack_e4m3(a2[8] * iu1, a2[R2S + 8] * iu1, a2[2 * R2S + 8] * iu1, a2[3 * R2S + 8] * iu1);
+            bf[0] = pack_e4m3(w0[0] * iv, w0[RTP] * iv, w0[2 * RTP] * iv, w0[3 * RTP] * iv);
+            bf[1] = pack_e4m3(w2[0] * iv, w2[RTP] * iv, w2[2 * RTP] * iv, w2[3 * RTP] * iv);
+            mma_e4m3(acc, af, bf);
+          }
+        }
+        const int r0 = 16 * mt + fr, c0 = 8 * nt + 2 * fc;
+        float s00 = 1.f, s01 = 1.f, s10 = 1.f, s11 = 1.f;
+        if (PREC == 2) {
+          s00 = usc[r0] * vsc[c0];
+          s01 = usc[r0] * vsc[c0 + 1];
+          s10 = usc[r0 + 8] * vsc[c0];
+          s11 = usc[r0 + 8] * vsc[c0 + 1];
+        }
+        float* z0 = dst + r0 * RT;
+        float* z1 = z0 + 8 * RT;
+        if (c0 < RT) {
+          z0[c0] = acc[0] * s00;
+          z1[c0] = acc[2] * s10;
+        }
+        if (c0 + 1 < RT) {
+          z0[c0 + 1] = acc[1] * s01;
+          z1[c0 + 1] = acc[3] * s11;
+        }
+      }
+      continue;
+    }
     if (mma) {
       // one 16 x 8 block of Z per warp step over all cells (k): A = A(N-1)^T (a0 at
       // (m = fr, k = fc): row k of the staged rows, column m), B = W (b0 at (k = fc, n = fr));
@@ -932,23 +1149,31 @@ SlabLayout slab_layout(int IT, int RT, int R2, bool smem_a) {
   return L;
 }
 
-template <int RTP, bool SMEM_A, bool OBJ>
+template <int RTP, bool SMEM_A, bool OBJ, int PREC>
 kr_status launch_slab_t(kr_ctx* ctx, const SlabArgs& a, size_t smem) {
-  KR_TRY(kr_smem_attr(ctx, k_slab<RTP, SMEM_A, OBJ>, smem));
-  KR_LAUNCH_PDL(ctx, (k_slab<RTP, SMEM_A, OBJ>), ctx->num_sms, SLAB_TEAM * SLAB_TEAMS, smem, a);
+  KR_TRY(kr_smem_attr(ctx, k_slab<RTP, SMEM_A, OBJ, PREC>, smem));
+  KR_LAUNCH_PDL(ctx, (k_slab<RTP, SMEM_A, OBJ, PREC>), ctx->num_sms, SLAB_TEAM * SLAB_TEAMS, smem, a);
   return KR_OK;
 }
 
-template <bool SMEM_A, bool OBJ>
-kr_status launch_slab(kr_ctx* ctx, int RTP, const SlabArgs& a, size_t smem) {
+template <bool SMEM_A, bool OBJ, int PREC>
+kr_status launch_slab_p(kr_ctx* ctx, int RTP, const SlabArgs& a, size_t smem) {
   switch (RTP) {
-    case 4: return launch_slab_t<4, SMEM_A, OBJ>(ctx, a, smem);
-    case 8: return launch_slab_t<8, SMEM_A, OBJ>(ctx, a, smem);
-    case 16: return launch_slab_t<16, SMEM_A, OBJ>(ctx, a, smem);
-    case 32: return launch_slab_t<32, SMEM_A, OBJ>(ctx, a, smem);
-    case 64: return launch_slab_t<64, SMEM_A, OBJ>(ctx, a, smem);
+    case 4: return launch_slab_t<4, SMEM_A, OBJ, 0>(ctx, a, smem);  // no tensor-core products
+    case 8: return launch_slab_t<8, SMEM_A, OBJ, PREC>(ctx, a, smem);
+    case 16: return launch_slab_t<16, SMEM_A, OBJ, PREC>(ctx, a, smem);
+    case 32: return launch_slab_t<32, SMEM_A, OBJ, PREC>(ctx, a, smem);
+    case 64: return launch_slab_t<64, SMEM_A, OBJ, PREC>(ctx, a, smem);
     default: return kr_fail(ctx, KR_EINVAL, "slab pass: R_N padded to %d", RTP);
   }
+}
+
+// The objective pass (the final FP64 check) always runs the FP32-accurate products.
+template <bool SMEM_A, bool OBJ>
+kr_status launch_slab(kr_ctx* ctx, int RTP, int prec, const SlabArgs& a, size_t smem) {
+  if (OBJ || prec == 0) return launch_slab_p<SMEM_A, OBJ, 0>(ctx, RTP, a, smem);
+  if (prec == 1) return launch_slab_p<SMEM_A, false, 1>(ctx, RTP, a, smem);
+  return launch_slab_p<SMEM_A, false, 2>(ctx, RTP, a, smem);
 }
 
 int grid_n(kr_ctx* ctx, int64_t n, int block = 256) {
@@ -1076,8 +1301,16 @@ kr_status kr_tiles_build(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, Carve& 
   return KR_OK;
 }
 
+int kr_slab_precision(int R2, int RT, int prec) {
+  // the tensor-core products need R_{N-1} in whole k steps: 32 for e4m3, 16 for BF16
+  // (and the TF32 form: 16); otherwise the pass falls back to the next finer format
+  if (rt_pad(RT) < 8 || R2 % 16 != 0) return 0;
+  if (prec >= 2 && R2 % 32 != 0) prec = 1;
+  return prec < 0 ? 0 : (prec > 2 ? 2 : prec);
+}
+
 kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const float* A2, const float* AT,
-                       const float* X1, bool want_obj, bool rearm) {
+                       const float* X1, bool want_obj, bool rearm, int prec) {
   SlabLayout L = slab_layout(tl->IT, tl->RT, tl->R2, true);
   if (L.bytes > ctx->smem_optin) L = slab_layout(tl->IT, tl->RT, tl->R2, false);
   if (L.bytes > ctx->smem_optin) return kr_fail(ctx, KR_ENOTIMPL, "slab pass: %zu bytes of shared memory", L.bytes);
@@ -1113,10 +1346,11 @@ kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const flo
   a.o_cs = L.o_cs;
   a.o_ctl = L.o_ctl;
   if (rearm) KR_CUDA(ctx, cudaMemsetAsync(tl->meta + 2, 0, sizeof(uint32_t), ctx->stream));
-  kr_status st = L.smem_a ? (want_obj ? launch_slab<true, true>(ctx, L.RTP, a, L.bytes)
-                                      : launch_slab<true, false>(ctx, L.RTP, a, L.bytes))
-                         : (want_obj ? launch_slab<false, true>(ctx, L.RTP, a, L.bytes)
-                                     : launch_slab<false, false>(ctx, L.RTP, a, L.bytes));
+  const int pr = kr_slab_precision(tl->R2, tl->RT, prec);
+  kr_status st = L.smem_a ? (want_obj ? launch_slab<true, true>(ctx, L.RTP, pr, a, L.bytes)
+                                      : launch_slab<true, false>(ctx, L.RTP, pr, a, L.bytes))
+                         : (want_obj ? launch_slab<false, true>(ctx, L.RTP, pr, a, L.bytes)
+                                     : launch_slab<false, false>(ctx, L.RTP, pr, a, L.bytes));
   return st;
 }
 

@@ -419,6 +419,14 @@ __device__ void rich_check_block(const double* __restrict__ part, int np, const 
   }
 }
 
+// Between the reduced-precision phase and the FP32 refinement: the loop continues from the
+// current x with a fresh stall / growth history (the iteration count carries on).
+__global__ void k_rich_resume(RichState* st) {
+  st->prev_h0 = st->min_h0 = st->min_q = INFINITY;
+  st->grow = st->since_min = 0;
+  st->status = STEP_CONTINUE;
+}
+
 __global__ void k_rich_init(RichState* st) {
   st->h[0] = st->h[1] = st->h[2] = 0.0;
   st->prev_h0 = st->min_h0 = st->min_q = INFINITY;
@@ -1362,7 +1370,7 @@ int64_t slab_max_intermediate(const Modes& m) {
 // Slab form of the sampled pass: X1 = X x_1 A(1) ... x_{N-2} A(N-2), then the fused slab
 // kernel (Z and the per-tile objective partials in bf.tl->objpart).
 kr_status slab_forward(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const IterBufs& bf, bool want_obj,
-                       bool rearm) {
+                       bool rearm, int prec = 0) {
   const int N = m.N;
   const float* X1 = bf.x;
   if (N > 2) {
@@ -1377,7 +1385,7 @@ kr_status slab_forward(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const I
     KR_TRY(kr_kron_apply2(ctx, N, din, dout, B, tr, bf.x, bf.X1, bf.t0, bf.t1));
     X1 = bf.X1;
   }
-  return kr_slab_pass(ctx, sk, bf.tl, m.A[N - 2], m.A[N - 1], X1, want_obj, rearm);
+  return kr_slab_pass(ctx, sk, bf.tl, m.A[N - 2], m.A[N - 1], X1, want_obj, rearm, prec);
 }
 
 // g = Z x_1 A(1)^T ... x_{N-2} A(N-2)^T: the sum over the tiles folded with the last
@@ -1402,9 +1410,9 @@ kr_status slab_backward(kr_ctx* ctx, const Modes& m, const IterBufs& bf, double*
 // Sampled pass at x: g = K~^T Omega (b~ - K~ x) (if want_g) and the objective partials
 // (*op, *on: FP64 values to be summed; with want_g only when want_obj).
 kr_status sampled_pass(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const IterBufs& bf, int nblk, bool want_g,
-                       const double** op, int* on, bool want_obj = false) {
+                       const double** op, int* on, bool want_obj = false, int prec = 0) {
   if (bf.tl) {
-    KR_TRY(slab_forward(ctx, m, sk, bf, !want_g || want_obj, !want_g));
+    KR_TRY(slab_forward(ctx, m, sk, bf, !want_g || want_obj, !want_g, prec));
     if (!want_g) {
       *op = bf.tl->objpart;
       *on = (int)bf.tl->ntmax;
@@ -1591,11 +1599,16 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   // Lemma 4.2), and g^T M+ g >= (1 - sqrt(eps)) times the excess.
   const double se = sqrt(cfg.eps), c1 = 1.0 - se;
   const double rho = fmax(fabs(1.0 - cfg.alpha * (1.0 - se)), fabs(1.0 - cfg.alpha * (1.0 + se)));
+  // Reduced-precision contractions (kr_opts.precision) for the first phase of the loop, on
+  // the slab path only; the phase ends at a step tolerance the format can reach.
+  const int prec1 = (slab && cfg.prec > 0) ? kr_slab_precision(tl.R2, tl.RT, cfg.prec) : 0;
+  int cur_prec = prec1;
+  double cur_tol = prec1 == 0 ? cfg.tol : fmax(cfg.tol, prec1 == 1 ? 0.0078125 : 0.0625);
   auto one_step = [&](cudaGraphConditionalHandle hnd, int use_hnd) -> kr_status {
-    KR_TRY(sampled_pass(ctx, m, &sk, bf, nblk, true, &op, &on, eps_rule));
+    KR_TRY(sampled_pass(ctx, m, &sk, bf, nblk, true, &op, &on, eps_rule, cur_prec));
     RichArgs ra = {};
     ra.st = bf.rich;
-    ra.tol = cfg.tol;
+    ra.tol = cur_tol;
     ra.max_iter = cfg.max_iter;
     ra.hnd = hnd;
     ra.use_hnd = use_hnd;
@@ -1616,23 +1629,40 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return KR_OK;
   };
-  // The first step runs from the host: it grows every buffer and sets every kernel
-  // attribute the steps need, so the captured steps allocate nothing.
-  KR_TRY(one_step(0, 0));
-  KR_TRY(read_state());
-  if (hs->status == STEP_CONTINUE && ctx->device_loop && !ctx->timing) {
-    // Steps 2.. as one graph; k_rich_check clears the condition on convergence, failure
-    // or max_iter.
-    int64_t per_step = 0;
-    const int it0 = hs->it;
-    if (kr_graph_while(ctx, one_step, &per_step)) {
-      KR_TRY(read_state());
-      ctx->launches += per_step * (hs->it - it0);
-    }
-  }
-  while (hs->status == STEP_CONTINUE) {
+  auto run_loop = [&]() -> kr_status {
+    // The first step runs from the host: it grows every buffer and sets every kernel
+    // attribute the steps need, so the captured steps allocate nothing.
     KR_TRY(one_step(0, 0));
     KR_TRY(read_state());
+    if (hs->status == STEP_CONTINUE && ctx->device_loop && !ctx->timing) {
+      // Steps 2.. as one graph; k_rich_check clears the condition on convergence, failure
+      // or max_iter.
+      int64_t per_step = 0;
+      const int it0 = hs->it;
+      if (kr_graph_while(ctx, one_step, &per_step)) {
+        KR_TRY(read_state());
+        ctx->launches += per_step * (hs->it - it0);
+      }
+    }
+    while (hs->status == STEP_CONTINUE) {
+      KR_TRY(one_step(0, 0));
+      KR_TRY(read_state());
+    }
+    return KR_OK;
+  };
+  KR_TRY(run_loop());
+  int iters_reduced = 0;
+  if (prec1 > 0) {
+    // FP32 refinement from where the reduced-precision steps stopped (from x = 0 if they
+    // produced a non-finite iterate); max_iter bounds both phases together
+    iters_reduced = hs->it;
+    if (hs->status != STEP_MAXITER) {
+      if (hs->status == STEP_NONFINITE) KR_CUDA(ctx, cudaMemsetAsync(bf.x, 0, sizeof(float) * R, ctx->stream));
+      KR_LAUNCH(ctx, k_rich_resume, 1, 1, 0, bf.rich);
+      cur_prec = 0;
+      cur_tol = cfg.tol;
+      KR_TRY(run_loop());
+    }
   }
   it = hs->it;
   rel = hs->h[1] > 0.0 ? sqrt(hs->h[0]) / sqrt(hs->h[1]) : (hs->h[0] == 0.0 ? 0.0 : INFINITY);
@@ -1667,6 +1697,8 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     cudaEventElapsedTime(&ms, ev[3], ev[4]); rep->t_ms[4] = ms;
     cudaEventElapsedTime(&ms, ev[4], ev[5]); rep->t_ms[5] = ms;
     cudaEventElapsedTime(&ms, ev[0], ev[5]); rep->t_ms[7] = ms;
+    rep->iters_reduced = iters_reduced;
+    rep->precision_used = prec1;
   }
   if (st != KR_OK) return st;
   if (!converged) return kr_fail(ctx, KR_ENOTCONV, "no convergence within %d iterations (rel step %.3e)", cfg.max_iter, rel);
@@ -1686,7 +1718,8 @@ kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr
   Modes m;
   KR_TRY(kr_check_factors(ctx, f, &m));
   if (!(o->eps > 0.0 && o->eps < 1.0)) return kr_fail(ctx, KR_EINVAL, "solver: eps=%g outside (0,1)", o->eps);
-  if (o->precision != 0) return kr_fail(ctx, KR_ENOTIMPL, "solver: precision=%d (only 0, FP32, is built)", o->precision);
+  if (o->precision < 0 || o->precision > 2)
+    return kr_fail(ctx, KR_EINVAL, "solver: precision=%d (0 FP32, 1 BF16, 2 FP8 e4m3)", o->precision);
   if (o->partition_T != 0 && o->partition_T != -1 && o->partition_T != (1 << (m.N - 1)))
     return kr_fail(ctx, KR_ENOTIMPL, "solver: partition_T=0x%x (only the last mode, 0x%x, is built)", o->partition_T,
                    1 << (m.N - 1));
@@ -1706,6 +1739,7 @@ kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr
   if (o->stop_rule != 0 && o->stop_rule != 1) return kr_fail(ctx, KR_EINVAL, "solver: stop_rule must be 0 or 1");
   cfg.stop_rule = o->stop_rule;
   cfg.theta = o->theta > 0 ? o->theta : 0.01;
+  cfg.prec = o->precision;
   const int64_t R = kr_prod_R(m), I = kr_prod_I(m);
   cfg.s = default_samples(o, R);
   if (rep) *rep = kr_report{};

@@ -1072,7 +1072,8 @@ kr_status tucker_args(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R
   if (!o || !I || !R || !X || !A || !G) return kr_fail(ctx, KR_EINVAL, "tucker: null argument");
   if (N < 2 || N > KR_MAX_MODES) return kr_fail(ctx, KR_EINVAL, "tucker: N=%d outside [2,%d]", N, KR_MAX_MODES);
   if (!(o->eps > 0.0 && o->eps < 1.0)) return kr_fail(ctx, KR_EINVAL, "tucker: eps outside (0,1)");
-  if (o->precision != 0) return kr_fail(ctx, KR_ENOTIMPL, "tucker: precision=%d (only 0, FP32, is built)", o->precision);
+  if (o->precision < 0 || o->precision > 2)
+    return kr_fail(ctx, KR_EINVAL, "tucker: precision=%d (0 FP32, 1 BF16, 2 FP8 e4m3)", o->precision);
   if (!(o->lambda >= 0.0) || !isfinite(o->lambda)) return kr_fail(ctx, KR_EINVAL, "tucker: lambda must be >= 0");
   if (o->host_io) return kr_fail(ctx, KR_ENOTIMPL, "tucker: host_io is not supported; pass device pointers");
   kr_factors f = {};
@@ -1095,6 +1096,7 @@ SolveCfg cfg_from(const kr_opts* o, int64_t Rsz) {
   c.s = o->num_samples > 0 ? o->num_samples : kr_sample_count(Rsz, o->eps, o->sample_scale);
   c.stop_rule = o->stop_rule == 1 ? 1 : 0;  // used by the core steps (Alg. 2 solves)
   c.theta = o->theta > 0 ? o->theta : 0.01;
+  c.prec = o->precision;  // the core steps' slab passes (the factor steps run FP32)
   return c;
 }
 

@@ -372,9 +372,10 @@ def test_invalid_arguments():
     with pytest.raises(kr.KronError) as e:  # R > I
         kr.kron_regress([dev(np.ones((2, 3))), As[1]], dev(np.ones(10)), eps=0.1)
     assert e.value.name == "KR_EINVAL"
-    with pytest.raises(kr.KronError) as e:  # only FP32 contractions are built
-        kr.kron_regress(As, b, eps=0.1, precision=1)
-    assert e.value.name == "KR_ENOTIMPL"
+    for p in (-1, 3):  # 0 FP32, 1 BF16, 2 FP8 e4m3
+        with pytest.raises(kr.KronError) as e:
+            kr.kron_regress(As, b, eps=0.1, precision=p)
+        assert e.value.name == "KR_EINVAL"
 
 
 def test_nonfinite_rhs_reports_enonfinite():
