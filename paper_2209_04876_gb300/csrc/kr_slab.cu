@@ -15,6 +15,9 @@
 // of A(N-1) into the slab's Z. The two large mode products of the unfused form (to and
 // from the cells x R_N intermediates) and their HBM round trips disappear.
 //
+// Loads that stream (the entry stream, b~) or that other tiles re-read from L2 (X1[p], rows
+// of A(N-1)) bypass L1, which keeps the rows of A(N) the walk gathers when A(N) is not held
+// in shared memory.
 // A persistent CTA holds A(N) and 1/p_N in shared memory once and runs two teams of 256
 // threads, each taking tiles from a global counter in decreasing-work order. Inside a
 // tile, the entries (contiguous in cell order) are split into equal segments, one per
@@ -319,33 +322,54 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
       sAct[tt] = ac;
       sCS[tt] = ac.y;
       if (tt == na - 1) sCS[na] = ac.y + ac.z;
-      const uint32_t i2 = ac.x % (uint32_t)a.I2;
-      float* dst = sA2 + tt * R2S;
-      float amax = 0.f;
-      if (a.a2vec) {
-        const float4* row = reinterpret_cast<const float4*>(a.A2 + (size_t)i2 * R2);
-        for (int k4 = 0; k4 < R2P / 4; ++k4) {
-          const float4 v = 4 * k4 < R2 ? __ldg(row + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
-          reinterpret_cast<float4*>(dst)[k4] = v;
-          amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+    team_sync(team);
+    // rows of A(N-1) of the tile's cells, loaded by the whole team with four loads in flight
+    // per thread; with the tensor-core products, rows past the last cell up to the next
+    // multiple of the MMA's k are the padding of the Z product's last k step: zero in both
+    // operands (A(N-1) rows here, W rows of sYW below), so they add exactly nothing
+    const int nrow = mma ? ((na + KS - 1) & ~(KS - 1)) : na;
+    if (a.a2vec) {
+      const int q4 = R2P / 4, n4 = nrow * q4;
+      for (int i0 = tt; i0 < n4; i0 += 4 * SLAB_TEAM) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * SLAB_TEAM;
+          const int row = i / q4, k4 = i - row * q4;
+          v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (i < n4 && row < na && 4 * k4 < R2) {
+            const uint32_t i2 = sAct[row].x % (uint32_t)a.I2;
+            v[u] = __ldcg(reinterpret_cast<const float4*>(a.A2 + (size_t)i2 * R2) + k4);
+          }
         }
-      } else {
-        const float* row = a.A2 + (size_t)i2 * R2;
-        for (int k2 = 0; k2 < R2P; ++k2) {
-          dst[k2] = k2 < R2 ? __ldg(row + k2) : 0.f;
-          amax = fmaxf(amax, fabsf(dst[k2]));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * SLAB_TEAM;
+          const int row = i / q4, k4 = i - row * q4;
+          if (i < n4) *reinterpret_cast<float4*>(sA2 + row * R2S + 4 * k4) = v[u];
         }
       }
-      if (PREC == 2) sPf[tt] = amax > 0.f ? amax / E4M3_MAX : 1.f;  // e4m3 scale of this row
-    } else if (mma && tt < ((na + KS - 1) & ~(KS - 1))) {
-      // rows past the last cell up to the next multiple of the MMA's k are the padding of
-      // the tensor-core Z product's last k step: zero in both operands (A(N-1) rows here, W
-      // rows of sYW below), so they add exactly nothing
-      for (int k2 = 0; k2 < R2P; ++k2) sA2[tt * R2S + k2] = 0.f;
+    } else {
+      const int n1 = nrow * R2P;
+      for (int i0 = tt; i0 < n1; i0 += 4 * SLAB_TEAM) {
+        float v[4];
 #pragma unroll
-      for (int c = 0; c < RTP; ++c) sYW[tt * RTP + c] = 0.f;
-      if (PREC == 2) sPf[tt] = 1.f;
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * SLAB_TEAM;
+          const int row = i / R2P, k2 = i - row * R2P;
+          v[u] = 0.f;
+          if (i < n1 && row < na && k2 < R2) v[u] = __ldcg(a.A2 + (size_t)(sAct[row].x % (uint32_t)a.I2) * R2 + k2);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * SLAB_TEAM;
+          const int row = i / R2P, k2 = i - row * R2P;
+          if (i < n1) sA2[row * R2S + k2] = v[u];
+        }
+      }
     }
+    for (int i = tt; i < (nrow - na) * RTP; i += SLAB_TEAM) sYW[na * RTP + i] = 0.f;
     {
       const float* xp = a.X1 + p * zn;
       if (PREC == 1 && mma) {
@@ -354,7 +378,7 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
         const int xs2 = 2 * (R2P / 2 + 4);
         for (int i = tt; i < R2P * RTP; i += SLAB_TEAM) {
           const int r = i / RTP, c = i % RTP;
-          const float v = (r < R2 && c < RT) ? __ldg(xp + r * RT + c) : 0.f;
+          const float v = (r < R2 && c < RT) ? __ldcg(xp + r * RT + c) : 0.f;
           const __nv_bfloat16 h = __float2bfloat16_rn(v);
           xt[c * xs2 + r] = *reinterpret_cast<const uint16_t*>(&h);
         }
@@ -364,7 +388,7 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
         if (tt < RTP) {
           float m = 0.f;
           if (tt < RT)
-            for (int r = 0; r < R2; ++r) m = fmaxf(m, fabsf(__ldg(xp + r * RT + tt)));
+            for (int r = 0; r < R2; ++r) m = fmaxf(m, fabsf(__ldcg(xp + r * RT + tt)));
           xsc[tt] = m > 0.f ? m / E4M3_MAX : 1.f;
         }
         team_sync(team);
@@ -372,28 +396,46 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
         const int xs4 = 4 * (R2P / 4 + 4);
         for (int i = tt; i < R2P * RTP / 2; i += SLAB_TEAM) {
           const int r = (2 * i) / RTP, c = (2 * i) % RTP;  // two columns c, c + 1 of row r
-          const float v0 = (r < R2 && c < RT) ? __ldg(xp + r * RT + c) / xsc[c] : 0.f;
-          const float v1 = (r < R2 && c + 1 < RT) ? __ldg(xp + r * RT + c + 1) / xsc[c + 1] : 0.f;
+          const float v0 = (r < R2 && c < RT) ? __ldcg(xp + r * RT + c) / xsc[c] : 0.f;
+          const float v1 = (r < R2 && c + 1 < RT) ? __ldcg(xp + r * RT + c + 1) / xsc[c + 1] : 0.f;
           const uint32_t q = cvt_e4m3x2(v1, v0);
           xt[c * xs4 + r] = (uint8_t)(q & 0xFFu);
           xt[(c + 1) * xs4 + r] = (uint8_t)(q >> 8);
         }
-      } else if (mma) {  // X1[p] split once into TF32 hi / lo planes, rows of XS floats
+      } else {  // FP32 X1[p] (split once into TF32 hi / lo planes, rows of XS floats, for the MMAs)
         uint32_t* xh = reinterpret_cast<uint32_t*>(sX1);
         uint32_t* xl = xh + R2P * a.XS;
-        for (int i = tt; i < R2P * RTP; i += SLAB_TEAM) {
-          const int r = i / RTP, c = i % RTP;
-          const float v = (r < R2 && c < RT) ? __ldg(xp + r * RT + c) : 0.f;
-          tf32_split(v, xh[r * a.XS + c], xl[r * a.XS + c]);
-        }
-      } else {
-        for (int i = tt; i < R2P * RTP; i += SLAB_TEAM) {
-          const int r = i / RTP, c = i % RTP;
-          sX1[i] = (r < R2 && c < RT) ? __ldg(xp + r * RT + c) : 0.f;
+        const int nx = R2P * RTP;
+        for (int i0 = tt; i0 < nx; i0 += 8 * SLAB_TEAM) {
+          float v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * SLAB_TEAM;
+            const int r = i / RTP, c = i % RTP;
+            v[u] = (i < nx && r < R2 && c < RT) ? __ldcg(xp + r * RT + c) : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * SLAB_TEAM;
+            const int r = i / RTP, c = i % RTP;
+            if (i < nx) {
+              if (mma) tf32_split(v[u], xh[r * a.XS + c], xl[r * a.XS + c]);
+              else sX1[i] = v[u];
+            }
+          }
         }
       }
     }
     team_sync(team);
+    if (PREC == 2 && mma) {  // e4m3 scale of each row of A(N-1) in the tile (1 for padding rows)
+      if (tt < nrow) {
+        float m = 0.f;
+        if (tt < na)
+          for (int k2 = 0; k2 < R2; ++k2) m = fmaxf(m, fabsf(sA2[tt * R2S + k2]));
+        sPf[tt] = m > 0.f ? m / E4M3_MAX : 1.f;
+      }
+      team_sync(team);
+    }
     // ---- Y rows of the tile's cells: sYW[k] = A(N-1)[i_k] X1[p]
     if (PREC != 0 && mma) {
       // one 16-row block of cells per warp, all RTP columns: A = rows of A(N-1) (a0 (g, k0),
@@ -570,8 +612,8 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
     for (int d = 0; d < SLAB_D; ++d) {
       const uint32_t j = j0 + (uint32_t)d * G + g;
       const bool on = j < j1;
-      re[d] = on ? __ldg(ent + j) : 0u;
-      rb[d] = on ? __ldg(bt + j) : 0.f;
+      re[d] = on ? __ldcs(ent + j) : 0u;
+      rb[d] = on ? __ldcs(bt + j) : 0.f;
     }
     for (uint32_t u0 = 0; u0 < nchunk; u0 += SLAB_D) {
 #pragma unroll
@@ -581,8 +623,8 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
         {  // refill this slot SLAB_D chunks ahead
           const uint32_t j = j0 + (u0 + d + SLAB_D) * G + g;
           const bool on = j < j1;
-          re[d] = on ? __ldg(ent + j) : 0u;
-          rb[d] = on ? __ldg(bt + j) : 0.f;
+          re[d] = on ? __ldcs(ent + j) : 0u;
+          rb[d] = on ? __ldcs(bt + j) : 0.f;
         }
         if (u0 + d >= nchunk) continue;  // uniform over the team
 #pragma unroll
