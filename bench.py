@@ -460,6 +460,8 @@ def run_gpu(args, rank, world, local):
     )
     if not args.no_tucker:
         line["tucker"] = {name: run_tucker(name) for name in TUCKER_WORKLOADS}
+    if not args.no_batched:
+        line["batched_ridge"] = run_batched()
     if not args.no_cpu_baseline:
         it_c = max(1, min(int(round(iters)), args.cpu_iters))
         v, s_c, dt = oracle_rows_per_s(w, As64, b32, it_c, args.cpu_fraction)
@@ -468,6 +470,64 @@ def run_gpu(args, rank, world, local):
             sample="%d of the %d draws (%.3g), full tables, grouping, gather and %d FP64 Richardson iteration(s)"
                    % (s_c, s, args.cpu_fraction, it_c), seconds=dt)
     print(json.dumps(line), flush=True)
+
+
+def run_batched(problems=64, seed=4):
+    """The batched-ridge workload: 64 independent N = 3 ridge problems (lambda = 1e-3, eps =
+    0.1), I_n uniform in [64, 1024], R_n uniform in [4, 32], Gaussian factors, b = K x + 1%
+    noise. Milliseconds per batch (host clock around synchronous calls, best of 3) for the 64
+    single solves one after another, the worker-context batch, the fused batch (one CUDA graph
+    for all Richardson loops) and the fused batch with the tile-budget autotuner, whose
+    choices are recorded."""
+    import torch
+
+    import paper_2209_04876_gb300 as kr
+    from workloads import kron_problem_device
+
+    rng = np.random.default_rng(seed)
+    probs, shapes = [], []
+    for k in range(problems):
+        I = [int(v) for v in rng.integers(64, 1025, size=3)]
+        R = [int(v) for v in rng.integers(4, 33, size=3)]
+        p = kron_problem_device(I, R, dist="gauss", seed=500 + k, noise_rel=0.01, b_kind="kron")
+        probs.append((p["As"], p["b"]))
+        shapes.append((I, R))
+    torch.cuda.synchronize()
+    lam, kw = 1e-3, dict(eps=0.1, seed=3, tol=1e-7, max_iter=300)
+
+    def seq():
+        return [kr.kron_ridge(As, b, lam, call_id=10 + p, **kw)[0] for p, (As, b) in enumerate(probs)]
+
+    def batch():
+        return kr.kron_ridge_batched(probs, lam, call_id=10, **kw)[0]
+
+    out = dict(problems=problems, lam=lam, eps=0.1, timing="host clock, synchronous calls, best of 3")
+    ref = None
+    for name, fn, mode, tune in (("sequential", seq, 0, 0), ("workers", batch, 0, 0), ("fused", batch, 1, 0),
+                                 ("fused_autotune", batch, 1, 1)):
+        kr.set_option(kr.OPT_BATCH_MODE, mode)
+        kr.set_option(kr.OPT_AUTOTUNE, tune)
+        xs = fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            xs = fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        out[name + "_ms"] = 1e3 * min(ts)
+        if ref is None:
+            ref = xs
+        elif not tune:
+            out[name + "_bit_identical"] = all(torch.equal(a, b) for a, b in zip(xs, ref))
+    kr.set_option(kr.OPT_BATCH_MODE, 0)
+    kr.set_option(kr.OPT_AUTOTUNE, 0)
+    for name in ("workers", "fused", "fused_autotune"):
+        out[name + "_speedup"] = out["sequential_ms"] / out[name + "_ms"]
+    out["autotune_choices"] = [dict(key=list(e["key"]), budget=e["budget"]) for e in kr.autotune_report()]
+    del probs
+    torch.cuda.empty_cache()
+    return out
 
 
 PROFILE_CASES = ("kron_rmatvec_512x512x1024_r64", "kron_n3_1024x1024x256_r64_outliers")
@@ -517,6 +577,7 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tucker", action="store_true", help="skip the TuckerALS sweep timings")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-ridge timings")
     ap.add_argument("--case", choices=PROFILE_CASES, help="run one small profiling case and exit")
     args = ap.parse_args()
     if args.case:

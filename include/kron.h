@@ -156,6 +156,11 @@ KR_API int64_t kr_launch_count(const kr_ctx* ctx);
  * on this context so far; counted in kr_launch_count too. */
 KR_API int64_t kr_tc_launch_count(const kr_ctx* ctx);
 
+/* The autotuner's choices (KR_OPT_AUTOTUNE) as text, one shape class per line:
+ * "N I_{N-1} R_{N-1} I_N R_N log2s budget ms@2048 ms@4096 ms@8192 ms@16384 ms@32768".
+ * Writes at most cap bytes (NUL-terminated when cap > 0); returns the length of the full text. */
+KR_API int64_t kr_autotune_report(kr_ctx* ctx, char* buf, int64_t cap);
+
 /* Per-kernel timing (instrumentation, off by default). When enabled, the library
  * records a CUDA event pair on its stream around every launch of the kernel kinds
  * below; kr_timing_read synchronises the stream and returns, for one kind, the summed
@@ -217,6 +222,19 @@ enum {
  *    K >= 32 and a multiple of 4, J <= 256, the input 16-byte aligned) on the tcgen05 tensor
  *    cores in 3xTF32 (FP32 accuracy: operands split into TF32 hi and lo parts, FP32
  *    accumulation); 0 keeps every mode product on the CUDA cores.
+ *  KR_OPT_BATCH_MODE (default 0): how kron_ridge_batched runs its problems. 0: on
+ *    KR_OPT_BATCH_WORKERS worker contexts, each solving one problem after another. 1 (fused):
+ *    one context and host thread per problem set up every problem concurrently on its own
+ *    stream; the problems' Richardson loops (device-side conditional loops) then run as
+ *    concurrent nodes of ONE CUDA graph, launched once for the whole batch, and each problem
+ *    finishes with its final check. Results are bit-identical to the per-problem solves with
+ *    the same options. The fused mode groups draws by ranks in a key bitmap (KR_OPT_GROUPING
+ *    0 selects 2 there: no per-context dense counters) and keeps nprob contexts with their
+ *    workspaces until kr_destroy.
+ *  KR_OPT_AUTOTUNE (default 0): 1 chooses the slab pass's tile entry budget by measurement:
+ *    the first solve of a shape class (N, I_{N-1}, R_{N-1}, I_N, R_N, floor(log2 s)) times one
+ *    slab pass at each budget in {2048, 4096, 8192, 16384, 32768} and keeps the fastest for the
+ *    class; kr_autotune_report lists the choices. A batch's contexts share the table.
  * Returns KR_EINVAL for an unknown key or a value out of range. */
 enum {
   KR_OPT_SLAB_PASS = 1,
@@ -227,7 +245,9 @@ enum {
   KR_OPT_HOST_GATHER = 6,
   KR_OPT_JL_K = 7,
   KR_OPT_JL_SEED = 8,
-  KR_OPT_TENSOR_CORES = 9
+  KR_OPT_TENSOR_CORES = 9,
+  KR_OPT_BATCH_MODE = 10,
+  KR_OPT_AUTOTUNE = 11
 };
 KR_API kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value);
 

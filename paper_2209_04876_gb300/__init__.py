@@ -21,8 +21,8 @@ STATUS = {0: "KR_OK", 1: "KR_EINVAL", 2: "KR_ENOMEM", 3: "KR_ECUDA", 4: "KR_ENON
 KERNEL_KINDS = {"resid": 0, "modeprod": 1, "sample": 2, "scatter": 3, "dedup": 4, "tables": 5, "vector": 6,
                 "slab": 7}
 OPT_SLAB_PASS, OPT_SLAB_TILE_ENTRIES, OPT_DEVICE_LOOP, OPT_BATCH_WORKERS, OPT_GROUPING, OPT_HOST_GATHER = 1, 2, 3, 4, 5, 6
-OPT_JL_K, OPT_JL_SEED, OPT_TENSOR_CORES = 7, 8, 9
-EXPORTED = ["kr_create", "kr_destroy", "kr_set_stream", "kr_last_error", "kr_launch_count", "kr_tc_launch_count", "kr_timing_enable",
+OPT_JL_K, OPT_JL_SEED, OPT_TENSOR_CORES, OPT_BATCH_MODE, OPT_AUTOTUNE = 7, 8, 9, 10, 11
+EXPORTED = ["kr_create", "kr_destroy", "kr_set_stream", "kr_last_error", "kr_launch_count", "kr_tc_launch_count", "kr_autotune_report", "kr_timing_enable",
             "kr_timing_read", "kr_timing_reset", "kr_set_option", "kron_sample_count", "kron_leverage",
             "kron_sample", "kron_sample_noalloc", "kron_sketch", "kron_sketch_distinct", "kron_sketch_export", "kron_sketch_residual",
             "kron_sketch_free", "kron_matmul", "kron_precond", "kron_objective", "kron_regress", "kron_ridge",
@@ -86,6 +86,7 @@ def lib():
             "kr_last_error": (ctypes.c_char_p, [vp]),
             "kr_launch_count": (i64, [vp]),
             "kr_tc_launch_count": (i64, [vp]),
+            "kr_autotune_report": (i64, [vp, ctypes.c_char_p, i64]),
             "kr_timing_enable": (i32, [vp, i32]),
             "kr_timing_read": (i32, [vp, i32, P(dbl), P(i64)]),
             "kr_timing_reset": (i32, [vp]),
@@ -143,6 +144,22 @@ def tc_launch_count():
     return int(lib().kr_tc_launch_count(context()))
 
 
+def autotune_report():
+    """The autotuner's choices (OPT_AUTOTUNE): one dict per shape class with its key
+    (N, I_{N-1}, R_{N-1}, I_N, R_N, floor(log2 s)), the chosen slab tile budget and the
+    measured slab-pass milliseconds at each candidate budget."""
+    h = context()
+    n = int(lib().kr_autotune_report(h, None, 0))
+    buf = ctypes.create_string_buffer(n + 1)
+    lib().kr_autotune_report(h, buf, n + 1)
+    out = []
+    for line in buf.value.decode().splitlines():
+        f = line.split()
+        out.append(dict(key=tuple(int(v) for v in f[:6]), budget=int(f[6]),
+                        ms={c: float(v) for c, v in zip((2048, 4096, 8192, 16384, 32768), f[7:])}))
+    return out
+
+
 def timing_enable(on=True):
     h = context()
     _check(lib().kr_timing_enable(h, int(bool(on))), h)
@@ -157,7 +174,10 @@ def set_option(key, value):
     per-key counters; OPT_HOST_GATHER: 1 host-buffer solves gather the sampled entries of a
     page-locked b in place, 0 copy b; OPT_JL_K: 0 exact leverage scores, k in [1, 64]
     JL-approximate scores with k sign columns; OPT_JL_SEED: their Philox key; OPT_TENSOR_CORES:
-    1 contiguous-index mode products of KronMatMul on tcgen05 in 3xTF32, 0 CUDA cores)."""
+    1 contiguous-index mode products of KronMatMul on tcgen05 in 3xTF32, 0 CUDA cores;
+    OPT_BATCH_MODE: kron_ridge_batched 0 on worker contexts, 1 fused (one context per problem,
+    all Richardson loops as concurrent nodes of one CUDA graph); OPT_AUTOTUNE: 1 chooses the
+    slab tile budget per shape class by measurement, see autotune_report())."""
     h = context()
     _check(lib().kr_set_option(h, int(key), int(value)), h)
 

@@ -105,6 +105,14 @@ extern "C" kr_status kr_set_option(kr_ctx* ctx, int32_t key, int64_t value) {
       if (value != 0 && value != 1) return kr_fail(ctx, KR_EINVAL, "kr_set_option: tensor cores must be 0 or 1");
       ctx->tensor_cores = (int)value;
       return KR_OK;
+    case KR_OPT_BATCH_MODE:
+      if (value != 0 && value != 1) return kr_fail(ctx, KR_EINVAL, "kr_set_option: batch mode must be 0 or 1");
+      ctx->batch_mode = (int)value;
+      return KR_OK;
+    case KR_OPT_AUTOTUNE:
+      if (value != 0 && value != 1) return kr_fail(ctx, KR_EINVAL, "kr_set_option: autotune must be 0 or 1");
+      ctx->autotune = (int)value;
+      return KR_OK;
     case KR_OPT_HOST_GATHER:
       if (value != 0 && value != 1) return kr_fail(ctx, KR_EINVAL, "kr_set_option: host gather must be 0 or 1");
       ctx->host_gather = (int)value;
@@ -135,6 +143,10 @@ extern "C" void kr_destroy(kr_ctx* ctx) {
   if (ctx->split_buf) cudaFree(ctx->split_buf);
   if (ctx->dcnt) cudaFree(ctx->dcnt);
   if (ctx->tc_buf) cudaFree(ctx->tc_buf);
+  if (ctx->loop_ev) cudaEventDestroy(ctx->loop_ev);
+  for (cudaEvent_t e : ctx->tune_ev)
+    if (e) cudaEventDestroy(e);
+  kr_tune_free(ctx);
   if (ctx->tc_err) cudaFree(ctx->tc_err);
   if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
   for (int i = 0; i < 10; ++i)

@@ -29,6 +29,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 
 // ------------------------------------------------------------------ context
 
+struct kr_shared_loop;  // a fused batch's rendezvous: the problems' device loops in one graph
+struct kr_tune_table;   // the autotuner's measured choices, per shape class
+
 struct kr_ctx {
   int device = 0;
   int num_sms = 0;
@@ -61,6 +64,13 @@ struct kr_ctx {
   int jl_k = 0;           // JL-approximate leverage scores with this many sign columns (0: exact scores)
   uint64_t jl_seed = 0;   // Philox key of the JL sign matrices
   int tensor_cores = 1;   // contiguous-index mode products on tcgen05 (3xTF32) where eligible
+  int batch_mode = 0;     // kron_ridge_batched: 0 worker contexts, 1 fused (one graph for all loops)
+  int autotune = 0;       // slab-pass tile budget chosen by measurement per shape class
+  kr_shared_loop* shared_loop = nullptr;  // set on the per-problem contexts of a fused batch
+  kr_tune_table* tune = nullptr;          // the autotuner's table (owned when tune_owned)
+  bool tune_owned = false;
+  cudaEvent_t loop_ev = nullptr;          // end of this context's work before a shared round (owned)
+  cudaEvent_t tune_ev[2] = {};            // the autotuner's timing pair (owned)
   // split B planes of the tensor-core mode product (grow-on-demand) and its device error word
   float* tc_buf = nullptr;
   size_t tc_size = 0;
@@ -418,6 +428,20 @@ enum StepCheck { STEP_CONTINUE, STEP_CONVERGED, STEP_FLOOR, STEP_DIVERGED, STEP_
 // continues with its host loop).
 bool kr_graph_while(kr_ctx* ctx, const std::function<kr_status(cudaGraphConditionalHandle, int)>& body,
                     int64_t* per_step);
+// A fused batch's problems each add their device loop (body captured on their own stream) as
+// one more conditional WHILE node of a shared graph; the last active problem to arrive
+// launches the graph on the batch's stream, after every member's earlier work, and waits for
+// it. Returns false when the round could not run (the caller continues with its host loop).
+bool kr_shared_loop_run(kr_shared_loop* sl, kr_ctx* ctx,
+                        const std::function<kr_status(cudaGraphConditionalHandle, int)>& body, int64_t* per_step);
+// A problem that will add no further loop (its solve returned) leaves the rendezvous.
+void kr_shared_loop_leave(kr_shared_loop* sl);
+kr_shared_loop* kr_shared_loop_new(cudaStream_t stream, int members);
+void kr_shared_loop_delete(kr_shared_loop* sl);
+// Autotuner table: the slab tile budget measured best for a shape class, or 0 if unknown.
+uint32_t kr_tune_lookup(kr_ctx* ctx, const int64_t* key);
+void kr_tune_record(kr_ctx* ctx, const int64_t* key, uint32_t et, const float* ms, int nc);
+void kr_tune_free(kr_ctx* ctx);
 // Stopping rule of the Richardson loops ("until convergence" in Alg. 2 and Alg. 3):
 // converged when ||step|| <= tol ||x||; stalled at the FP32 rounding floor when no new
 // minimum step was seen for 8 iterations and the smallest relative step is within

@@ -1486,8 +1486,18 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   kr_tiles tl;
   int64_t nyw = ncell * RT, nx1 = 0;  // floats of Y / W (per-cell form) or X1 / Z (slab form, N >= 3)
   int64_t mx = max_intermediate(m);
+  // the autotuner's shape class and its candidate tile budgets (the tiles' arrays are sized
+  // for the smallest, which needs the most tiles)
+  static const uint32_t kTuneEt[5] = {2048, 4096, 8192, 16384, 32768};
+  int64_t tkey[6] = {N, m.I[N > 1 ? N - 2 : 0], m.R[N > 1 ? N - 2 : 0], m.I[N - 1], RT, 0};
+  for (int64_t v = cfg.s; v > 1; v >>= 1) ++tkey[5];
+  uint32_t tuned_et = (slab && ctx->autotune) ? kr_tune_lookup(ctx, tkey) : 0;
+  const bool tune_now = slab && ctx->autotune && tuned_et == 0;
   if (slab) {
+    const uint32_t et_keep = ctx->slab_tile_entries;
+    if (ctx->autotune) ctx->slab_tile_entries = tune_now ? kTuneEt[0] : tuned_et;
     kr_tiles_setup(ctx, m, &sk, &tl);
+    ctx->slab_tile_entries = et_keep;
     // folded first preconditioner mode with the eps-aware rule: the reduction also returns g
     if (N == 3 && cfg.lambda == 0.0 && cfg.stop_rule == 1) tl.nout = 2;
     nyw = 0;
@@ -1575,9 +1585,43 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     Carve sc = cv;
     KR_TRY(kr_sketch_fill(ctx, m, t, b, seed, call_id, 0, &sk, sc, true));
   }
-  if (slab) KR_TRY(kr_tiles_build(ctx, &sk, &tl, cv));
-  KR_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
   KR_CUDA(ctx, cudaMemsetAsync(bf.x, 0, sizeof(float) * R, ctx->stream));
+  if (tune_now) {
+    // one slab pass (its cost does not depend on x) timed at every candidate budget; the
+    // fastest is kept for the shape class
+    for (int i = 0; i < 2; ++i)
+      if (!ctx->tune_ev[i]) KR_CUDA(ctx, cudaEventCreate(&ctx->tune_ev[i]));
+    float ms[5];
+    int best = 0;
+    for (int c = 0; c < 5; ++c) {
+      tl.et = kTuneEt[c];
+      {
+        Carve sc = cv;  // the final build below takes the same scratch
+        KR_TRY(kr_tiles_build(ctx, &sk, &tl, sc));
+      }
+      KR_TRY(slab_forward(ctx, m, &sk, bf, false, true));  // warm
+      // the fastest of three passes: other streams' work (a fused batch's other problems)
+      // can only add time
+      ms[c] = INFINITY;
+      for (int rep = 0; rep < 3; ++rep) {
+        KR_CUDA(ctx, cudaEventRecord(ctx->tune_ev[0], ctx->stream));
+        KR_TRY(slab_forward(ctx, m, &sk, bf, false, true));
+        KR_CUDA(ctx, cudaEventRecord(ctx->tune_ev[1], ctx->stream));
+        KR_CUDA(ctx, cudaEventSynchronize(ctx->tune_ev[1]));
+        float t = 0.f;
+        KR_CUDA(ctx, cudaEventElapsedTime(&t, ctx->tune_ev[0], ctx->tune_ev[1]));
+        ms[c] = fminf(ms[c], t);
+      }
+      if (ms[c] < ms[best]) best = c;
+    }
+    tuned_et = kTuneEt[best];
+    kr_tune_record(ctx, tkey, tuned_et, ms, 5);
+  }
+  if (slab) {
+    if (ctx->autotune) tl.et = tuned_et;
+    KR_TRY(kr_tiles_build(ctx, &sk, &tl, cv));
+  }
+  KR_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
   KR_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
   double* h = (double*)ctx->hbuf;
   const int ublk = grid_cap(ctx, R, 256, 4);
@@ -1635,11 +1679,13 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     KR_TRY(one_step(0, 0));
     KR_TRY(read_state());
     if (hs->status == STEP_CONTINUE && ctx->device_loop && !ctx->timing) {
-      // Steps 2.. as one graph; k_rich_check clears the condition on convergence, failure
-      // or max_iter.
+      // Steps 2.. as one graph (in a fused batch: one node of the batch's shared graph);
+      // k_rich_check clears the condition on convergence, failure or max_iter.
       int64_t per_step = 0;
       const int it0 = hs->it;
-      if (kr_graph_while(ctx, one_step, &per_step)) {
+      const bool ran = ctx->shared_loop ? kr_shared_loop_run(ctx->shared_loop, ctx, one_step, &per_step)
+                                        : kr_graph_while(ctx, one_step, &per_step);
+      if (ran) {
         KR_TRY(read_state());
         ctx->launches += per_step * (hs->it - it0);
       }
@@ -1855,9 +1901,75 @@ static kr_status kr_workers_reserve(kr_ctx* ctx, int n) {
     w->device_loop = ctx->device_loop;
     w->grouping = ctx->grouping;
     w->host_gather = ctx->host_gather;
+    w->jl_k = ctx->jl_k;
+    w->jl_seed = ctx->jl_seed;
+    w->tensor_cores = ctx->tensor_cores;
+    w->autotune = ctx->autotune;
+    if (ctx->autotune && !ctx->tune) kr_tune_lookup(ctx, nullptr);  // creates ctx's table
+    if (w->tune_owned) kr_tune_free(w);
+    w->tune = ctx->tune;  // one table for the batch
+    w->shared_loop = nullptr;
     w->timing = false;
   }
   return KR_OK;
+}
+
+// Fused batch (KR_OPT_BATCH_MODE 1): a context and a host thread per problem. Every problem
+// builds its tables, sketch and tiles concurrently on its own stream and takes its first
+// Richardson step; the problems' remaining steps (device-side conditional loops) then run as
+// the concurrent nodes of one CUDA graph, launched once on ctx's stream (kr_shared_loop_run),
+// and every problem ends with its own final objective check. Each problem runs the kernels of
+// its single solve in the same order, so its result is bit-identical to that solve's.
+static kr_status batched_fused(kr_ctx* ctx, int32_t nprob, const kr_factors* probs, const float* const b[],
+                               const kr_opts* opts, float* const x[], kr_report* reports) {
+  KR_TRY(kr_workers_reserve(ctx, nprob));
+  kr_shared_loop* sl = kr_shared_loop_new(ctx->stream, nprob);
+  for (int p = 0; p < nprob; ++p) {
+    kr_ctx* w = ctx->workers[p];
+    w->shared_loop = sl;
+    if (w->grouping == 0) w->grouping = 2;  // key bitmap: no 4 GB dense counters per context
+  }
+  KR_CUDA(ctx, cudaEventRecord(ctx->ev[9], ctx->stream));
+  for (int p = 0; p < nprob; ++p) KR_CUDA(ctx, cudaStreamWaitEvent(ctx->worker_streams[p], ctx->ev[9], 0));
+  std::vector<kr_status> st(nprob, KR_OK);
+  std::vector<std::string> msg(nprob);
+  std::vector<int64_t> l0(nprob);
+  for (int p = 0; p < nprob; ++p) l0[p] = ctx->workers[p]->launches;
+  auto run = [&](int p) {
+    kr_ctx* w = ctx->workers[p];
+    const cudaError_t de = cudaSetDevice(ctx->device);
+    if (de != cudaSuccess) {
+      st[p] = KR_ECUDA;
+      msg[p] = std::string("kron_ridge_batched: cudaSetDevice failed in a worker: ") + cudaGetErrorString(de);
+    } else {
+      kr_opts o = *opts;
+      o.call_id = opts->call_id + (uint64_t)p;
+      st[p] = solve_entry(w, &probs[p], b[p], &o, x[p], reports ? &reports[p] : nullptr, opts->lambda);
+      if (st[p] != KR_OK) msg[p] = w->err;
+    }
+    kr_shared_loop_leave(sl);  // in every case: the other problems do not wait for this one
+  };
+  std::vector<std::thread> pool;
+  for (int p = 1; p < nprob; ++p) pool.emplace_back(run, p);
+  run(0);
+  for (auto& t : pool) t.join();
+  kr_shared_loop_delete(sl);
+  for (int p = 0; p < nprob; ++p) {
+    ctx->workers[p]->shared_loop = nullptr;
+    ctx->launches += ctx->workers[p]->launches - l0[p];
+  }
+  kr_status worst = KR_OK;
+  for (int p = 0; p < nprob; ++p) {
+    if (st[p] != KR_OK && st[p] != KR_ENOTCONV) {
+      ctx->err = msg[p];
+      return st[p];
+    }
+    if (st[p] == KR_ENOTCONV && worst == KR_OK) {
+      worst = KR_ENOTCONV;
+      ctx->err = msg[p];
+    }
+  }
+  return worst;
 }
 
 extern "C" kr_status kron_ridge_batched(kr_ctx* ctx, int32_t nprob, const kr_factors* probs, const float* const b[],
@@ -1865,6 +1977,7 @@ extern "C" kr_status kron_ridge_batched(kr_ctx* ctx, int32_t nprob, const kr_fac
   if (!ctx) return KR_EINVAL;
   if (nprob < 0 || (nprob > 0 && (!probs || !b || !x || !opts)))
     return kr_fail(ctx, KR_EINVAL, "kron_ridge_batched: bad arguments");
+  if (ctx->batch_mode == 1 && nprob > 1) return batched_fused(ctx, nprob, probs, b, opts, x, reports);
   const int W = nprob < ctx->batch_workers ? nprob : ctx->batch_workers;
   if (W <= 1) {  // one after another on ctx's stream
     kr_status worst = KR_OK;

@@ -87,3 +87,81 @@ def test_batched_reports_first_hard_error():
     with pytest.raises(kr.KronError) as e:
         kr.kron_ridge_batched(batch, 1e-3, eps=0.1, seed=1, call_id=0)
     assert e.value.name == "KR_EINVAL"
+
+
+@pytest.fixture
+def _fused_modes():
+    yield
+    kr.set_option(kr.OPT_BATCH_MODE, 0)
+    kr.set_option(kr.OPT_AUTOTUNE, 0)
+    kr.set_option(kr.OPT_SLAB_TILE_ENTRIES, 16384)
+
+
+def _batch_shapes(count, seed):
+    # the batched-ridge recipe: N = 3, I_n uniform in [64, 256], R_n uniform in [4, 16]
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        I = [int(v) for v in rng.integers(64, 257, size=3)]
+        R = [int(v) for v in rng.integers(4, 17, size=3)]
+        prob = kron_problem(I, R, dist="gauss", seed=300 + k, noise_rel=0.01)
+        out.append(([A.astype(np.float32) for A in prob["As"]], prob["b"].astype(np.float32)))
+    return out
+
+
+def test_fused_batch_bit_identical(_fused_modes):
+    """One context per problem, every Richardson loop a node of one CUDA graph: each x and
+    report equals the problem's single solve bit for bit (and the worker-context mode's)."""
+    probs = _batch_shapes(12, 77)
+    lam, eps, seed, cid = 1e-3, 0.1, 5, 10
+    args = [([dev(A) for A in As], dev(b)) for As, b in probs]
+    kr.set_option(kr.OPT_BATCH_MODE, 1)
+    xs_f, reps_f = kr.kron_ridge_batched(args, lam, eps=eps, seed=seed, call_id=cid, tol=1e-7, max_iter=300)
+    kr.set_option(kr.OPT_BATCH_MODE, 0)
+    xs_w, _ = kr.kron_ridge_batched(args, lam, eps=eps, seed=seed, call_id=cid, tol=1e-7, max_iter=300)
+    for p, (As, b) in enumerate(args):
+        x1, r1 = kr.kron_ridge(As, b, lam, eps=eps, seed=seed, call_id=cid + p, tol=1e-7, max_iter=300)
+        assert torch.equal(xs_f[p], x1), p
+        assert torch.equal(xs_w[p], x1), p
+        assert reps_f[p]["iters"] == r1["iters"] and reps_f[p]["distinct"] == r1["distinct"]
+        assert reps_f[p]["obj_sampled"] == r1["obj_sampled"]
+
+
+def test_fused_batch_eps_rule_and_precision(_fused_modes):
+    """Problems that stop after different numbers of steps, with a second loop round for the
+    FP32 refinement of reduced-precision steps: still bit-identical to single solves."""
+    probs = _batch_shapes(6, 78)
+    lam, eps, seed, cid = 1e-3, 0.1, 6, 30
+    args = [([dev(A) for A in As], dev(b)) for As, b in probs]
+    kr.set_option(kr.OPT_BATCH_MODE, 1)
+    kw = dict(eps=eps, seed=seed, tol=1e-7, max_iter=300, stop_rule=kr.STOP_EPS, precision=1)
+    xs_f, reps_f = kr.kron_ridge_batched(args, lam, call_id=cid, **kw)
+    for p, (As, b) in enumerate(args):
+        x1, r1 = kr.kron_ridge(As, b, lam, call_id=cid + p, **kw)
+        assert torch.equal(xs_f[p], x1), p
+        assert reps_f[p]["iters"] == r1["iters"] and reps_f[p]["iters_reduced"] == r1["iters_reduced"]
+
+
+def test_autotune_records_choices_and_reproduces(_fused_modes):
+    """The autotuner times one slab pass per candidate tile budget for each new shape class,
+    keeps the fastest, and a solve with that budget set by hand reproduces the tuned solve."""
+    probs = _batch_shapes(4, 79)
+    lam, eps, seed, cid = 1e-3, 0.1, 7, 50
+    args = [([dev(A) for A in As], dev(b)) for As, b in probs]
+    kr.set_option(kr.OPT_AUTOTUNE, 1)
+    kr.set_option(kr.OPT_BATCH_MODE, 1)
+    xs, reps = kr.kron_ridge_batched(args, lam, eps=eps, seed=seed, call_id=cid, tol=1e-7, max_iter=300)
+    table = {e["key"]: e for e in kr.autotune_report()}
+    kr.set_option(kr.OPT_AUTOTUNE, 0)
+    kr.set_option(kr.OPT_BATCH_MODE, 0)
+    for p, (As, b) in enumerate(args):
+        I = [A.shape[0] for A in As]
+        R = [A.shape[1] for A in As]
+        key = (3, I[1], R[1], I[2], R[2], int(reps[p]["s"]).bit_length() - 1)
+        assert key in table, (key, list(table))
+        e = table[key]
+        assert e["budget"] in (2048, 4096, 8192, 16384, 32768)
+        assert e["ms"][e["budget"]] == min(e["ms"].values())
+        kr.set_option(kr.OPT_SLAB_TILE_ENTRIES, e["budget"])
+        x1, _ = kr.kron_ridge(As, b, lam, eps=eps, seed=seed, call_id=cid + p, tol=1e-7, max_iter=300)
+        assert torch.equal(xs[p], x1), p
