@@ -567,11 +567,11 @@ def run_case(name):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=90)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="kron_n3_1024x64_outliers", choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-fraction", type=float, default=0.005)
+    ap.add_argument("--cpu-fraction", type=float, default=0.05)
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--ref-fraction", type=float, default=0.001)
     ap.add_argument("--ref-iters", type=int, default=1)

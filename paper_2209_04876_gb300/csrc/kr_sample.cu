@@ -110,7 +110,44 @@ struct DrawModes {
   int M[KR_MAX_MODES];      // guide entries
   const uint64_t* thr[KR_MAX_MODES];
   const uint16_t* guide[KR_MAX_MODES];
+  const uint16_t* prk[KR_MAX_MODES];  // rows ranked by decreasing probability (dense counters; or null)
 };
+
+// Dense counters are addressed by each index's rank in its mode's decreasing-probability
+// order (the key's bitmap bit and every output stay in the original key order). Draws
+// concentrate on the most probable rows (high-leverage rows: a few per cent of a mode's
+// rows can carry most of its mass), so this packs the busiest counters into a corner of
+// the array and their atomic updates touch far fewer L2 sectors. Modes of at most PRK_MAX
+// rows (a rank table of uint16 per mode).
+constexpr int PRK_MAX = 4096;
+
+struct ProbRanks {
+  int I[KR_MAX_MODES];
+  const double* prob[KR_MAX_MODES];
+  uint16_t* out[KR_MAX_MODES];
+};
+
+// out[n][i] = #{ j : p_j > p_i, or p_j = p_i and j < i }: row i's place when mode n's rows
+// are sorted by decreasing probability (ties by index). Block (n, c) ranks rows
+// [256 c, 256 c + 256) of mode n.
+__global__ void __launch_bounds__(256) k_prob_rank(ProbRanks pr) {
+  __shared__ double sp[PRK_MAX];
+  const int n = blockIdx.x, I = pr.I[n];
+  if (256 * (int)blockIdx.y >= I) return;
+  for (int i = threadIdx.x; i < I; i += blockDim.x) sp[i] = pr.prob[n][i];
+  __syncthreads();
+  {
+    const int i = 256 * blockIdx.y + threadIdx.x;
+    if (i >= I) return;
+    const double pi = sp[i];
+    int r = 0;
+    for (int j = 0; j < I; ++j) {
+      const double pj = sp[j];
+      r += (pj > pi || (pj == pi && j < i)) ? 1 : 0;
+    }
+    pr.out[n][i] = (uint16_t)r;
+  }
+}
 
 __device__ __forceinline__ int guided_search(const uint64_t* thr, const uint16_t* guide, int shift, uint64_t U) {
   int i = guide[U >> shift];
@@ -133,8 +170,10 @@ __global__ void __launch_bounds__(256) k_draw_keys(DrawModes dm, int64_t s_row, 
                                                    uint32_t* __restrict__ dcnt) {
   __shared__ uint64_t s_thr[THR_SMEM];
   __shared__ uint16_t s_guide[THR_SMEM];
+  __shared__ uint16_t s_prk[THR_SMEM];
   const uint64_t* thr[N];
   const uint16_t* guide[N];
+  const uint16_t* prk[N];
   int In[N], sh[N];
   {
     int ti = 0, tm = 0;
@@ -152,13 +191,17 @@ __global__ void __launch_bounds__(256) k_draw_keys(DrawModes dm, int64_t s_row, 
       if (fit) {
         for (int i = threadIdx.x; i < In[n]; i += blockDim.x) s_thr[oi + i] = dm.thr[n][i];
         for (int i = threadIdx.x; i < dm.M[n]; i += blockDim.x) s_guide[om + i] = dm.guide[n][i];
+        if (dm.prk[0])
+          for (int i = threadIdx.x; i < In[n]; i += blockDim.x) s_prk[oi + i] = dm.prk[n][i];
         thr[n] = s_thr + oi;
         guide[n] = s_guide + om;
+        prk[n] = s_prk + oi;
         oi += In[n];
         om += dm.M[n];
       } else {
         thr[n] = dm.thr[n];
         guide[n] = dm.guide[n];
+        prk[n] = dm.prk[n];
       }
     }
     __syncthreads();
@@ -186,7 +229,14 @@ __global__ void __launch_bounds__(256) k_draw_keys(DrawModes dm, int64_t s_row, 
     cell += r * ncell_inner;
     const uint32_t key = cell * IT + (uint32_t)idx[N - 1];
     if (dcnt) {
-      if (atomicAdd(dcnt + key, 1u) == 0u) atomicOr(&bm[key >> 5].x, 1u << (key & 31));
+      uint32_t ckey = key;  // the key's counter
+      if (dm.prk[0]) {
+        uint32_t pc = 0;
+#pragma unroll
+        for (int n = 0; n < N - 1; ++n) pc = pc * (uint32_t)In[n] + (uint32_t)prk[n][idx[n]];
+        ckey = (pc + r * ncell_inner) * IT + (uint32_t)prk[N - 1][idx[N - 1]];
+      }
+      if (atomicAdd(dcnt + ckey, 1u) == 0u) atomicOr(&bm[key >> 5].x, 1u << (key & 31));
     } else {
       keys[t] = key;
       if (bm) atomicOr(&bm[key >> 5].x, 1u << (key & 31));
@@ -444,10 +494,34 @@ __global__ void __launch_bounds__(RLE_THREADS) k_bm_tcount(const uint2* __restri
 // consecutive words of the tile (staged in shared memory); the tile's keys are collected
 // in shared memory and written out coalesced (a dense tile with more than BM_KEYCAP keys
 // writes them directly). The last tile sets meta[0] = distinct keys.
+// Where a key's dense counter lives (k_draw_keys): the key with each index replaced by its
+// rank in its mode's decreasing-probability order (prk[0] null: the key itself).
+struct CountMap {
+  int N;
+  uint32_t I[KR_MAX_MODES];
+  uint32_t IT, ncell_inner;
+  const uint16_t* prk[KR_MAX_MODES];
+};
+__device__ __forceinline__ uint32_t count_slot(const CountMap& cm, uint32_t key) {
+  if (!cm.prk[0]) return key;
+  const int N = cm.N;
+  const uint32_t cell = key / cm.IT, iT = key - cell * cm.IT;
+  const uint32_t r = cell / cm.ncell_inner;
+  uint32_t inner = cell - r * cm.ncell_inner, pc = 0, mult = 1;
+  for (int n = N - 2; n >= 0; --n) {
+    const uint32_t q = inner / cm.I[n];
+    pc += (uint32_t)cm.prk[n][inner - q * cm.I[n]] * mult;
+    mult *= cm.I[n];
+    inner = q;
+  }
+  return (pc + r * cm.ncell_inner) * cm.IT + (uint32_t)cm.prk[N - 1][iT];
+}
+
 __global__ void __launch_bounds__(RLE_THREADS) k_bm_rank(uint2* __restrict__ bm, int64_t nw,
                                                          const uint32_t* __restrict__ toff, int ntile,
                                                          uint32_t* __restrict__ dk, uint32_t* __restrict__ cnt,
-                                                         uint32_t* __restrict__ meta, uint32_t* __restrict__ dcnt) {
+                                                         uint32_t* __restrict__ meta, uint32_t* __restrict__ dcnt,
+                                                         CountMap cm) {
   __shared__ uint32_t sh[RLE_THREADS / 32 + 1];
   __shared__ uint32_t bits[BM_TILE + BM_TILE / 32];
   __shared__ uint32_t pre[BM_TILE + BM_TILE / 32];
@@ -495,8 +569,9 @@ __global__ void __launch_bounds__(RLE_THREADS) k_bm_rank(uint2* __restrict__ bm,
     const uint32_t key = staged ? skeys[j] : dk[off + j];
     if (staged) dk[off + j] = key;
     if (dcnt) {
-      cnt[off + j] = dcnt[key];
-      dcnt[key] = 0u;
+      const uint32_t slot = count_slot(cm, key);
+      cnt[off + j] = dcnt[slot];
+      dcnt[slot] = 0u;
     } else {
       cnt[off + j] = 0u;
     }
@@ -693,6 +768,7 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   uint32_t* meta = cv.take<uint32_t>(4);
   unsigned long long* dsum = cv.take<unsigned long long>(1);
   uint16_t* gbuf = cv.take<uint16_t>((size_t)KR_MAX_MODES * GUIDE_MAX);
+  uint16_t* prkbuf = cv.take<uint16_t>((size_t)KR_MAX_MODES * PRK_MAX);
   const int64_t keyspace = ncell * (int64_t)IT;
   const bool ranked = kr_group_by_rank(ctx, s, keyspace);
   const bool dense = kr_group_dense(ctx, s, keyspace);
@@ -719,10 +795,30 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   KR_CUDA(ctx, cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), ctx->stream));
   if (ranked) KR_CUDA(ctx, cudaMemsetAsync(bm, 0, sizeof(uint2) * nw, ctx->stream));
   uint32_t* dcnt = nullptr;
+  CountMap cmap = {};
+  cmap.N = N;
+  cmap.IT = IT;
+  cmap.ncell_inner = (uint32_t)sk->ncell_inner;
   if (dense) {
     KR_TRY(kr_dcnt_reserve(ctx, keyspace));
     dcnt = ctx->dcnt;
     ctx->dcnt_clean = false;  // until the rank kernel below has been enqueued
+    bool small = true;
+    for (int n = 0; n < N; ++n) small = small && m.I[n] <= PRK_MAX;
+    if (small) {  // counters addressed by probability ranks
+      ProbRanks pr = {};
+      for (int n = 0; n < N; ++n) {
+        pr.I[n] = m.I[n];
+        pr.prob[n] = t.prob[n];
+        pr.out[n] = prkbuf + (size_t)n * PRK_MAX;
+        dm.prk[n] = pr.out[n];
+        cmap.I[n] = (uint32_t)m.I[n];
+        cmap.prk[n] = pr.out[n];
+      }
+      int imax = 1;
+      for (int n = 0; n < N; ++n) imax = m.I[n] > imax ? m.I[n] : imax;
+      KR_LAUNCH(ctx, k_prob_rank, dim3(N, (imax + 255) / 256), 256, 0, pr);
+    }
   }
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32), cid = (uint32_t)call_id;
   {
@@ -761,7 +857,7 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
       Carve sc = cv;
       KR_TRY(kr_scan_u32(ctx, btc, btc + nbt, nbt, sc));
     }
-    KR_LAUNCH(ctx, k_bm_rank, nbt, RLE_THREADS, 0, bm, nw, btc + nbt, nbt, alt, hp, meta, dcnt);
+    KR_LAUNCH(ctx, k_bm_rank, nbt, RLE_THREADS, 0, bm, nw, btc + nbt, nbt, alt, hp, meta, dcnt, cmap);
     if (dense)
       ctx->dcnt_clean = true;  // the rank kernel resets every counter the draws set
     else
@@ -831,6 +927,7 @@ void kr_sketch_scratch_need(const kr_ctx* ctx, int64_t s, int64_t ncell, int64_t
   nd.add<uint32_t>(4);
   nd.add<unsigned long long>(1);
   nd.add<uint16_t>((size_t)KR_MAX_MODES * GUIDE_MAX);
+  nd.add<uint16_t>((size_t)KR_MAX_MODES * PRK_MAX);
   if (kr_group_by_rank(ctx, s, ncell * IT)) {
     const int64_t nw = (ncell * IT + 31) / 32;
     nd.add<uint2>(nw);                                       // key bitmap with word ranks
