@@ -225,11 +225,11 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------------------- GPU leg
 
-def slab_traffic(workload):
-    """DRAM bytes per k_slab launch from the committed ncu capture (profiles/traffic.json), or
-    None once the kernel source differs from the captured one."""
+def kernel_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture at this workload
+    (profiles/traffic.json), or None once the kernel's source differs from the captured one."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["k_slab"]
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
         src = open(os.path.join(ROOT, rec["source"]), "rb").read()
     except (OSError, KeyError, ValueError):
         return None, None
@@ -407,13 +407,19 @@ def run_gpu(args, rank, world, local):
     del As_h, b_h
     if rank != 0:
         return
-    # roofline of the dominant kernel, k_slab (the fused sampled products a6-a8, one launch per
-    # Richardson iteration plus the final check). Algorithmic bytes per launch, per the
-    # method's own accounting: per distinct sampled row its last-mode index (2 B), weight
-    # (4 B) and b~ (4 B); per non-empty cell its Y row read and W row written, 2 R_N 4 B.
+    # Roofline of the dominant kernel of a solve, by the library's per-kind launch timing:
+    # k_draw_keys (the draws, a3, with the dense grouping's per-key counts and key bitmap, a4,
+    # in the same launch) or k_slab (the fused sampled products a6-a8, one launch per
+    # Richardson iteration plus the final check); the other one is reported beside it.
+    # Algorithmic bytes per launch, per the method's own accounting: a3 writes 4 N + 4 B per
+    # draw (indices, weight) and a4 reads about three 12-byte passes per draw and writes 8 B
+    # per distinct row; a6-a8 move 10 B per distinct sampled row (last-mode index, weight, b~)
+    # and 2 R_N 4 B per non-empty cell (its Y row read and W row written).
     peaks, peak_kind = load_peaks()
     hbm = float(peaks["hbm_gbs"])
+    peak_source = "%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
     I, R = w["I"], w["R"]
+    N = len(I)
     RT, R2 = R[-1], R[-2]
     distinct, cells = sketch_stats(kr, As_d, b_d, rep_t["s"], w["solve_seed"], args.steps, I[-1])
     alg_bytes = distinct * 10 + cells * 2 * RT * 4
@@ -423,16 +429,37 @@ def run_gpu(args, rank, world, local):
     ms_r, n_r = tim["slab"]
     t_launch = ms_r / n_r / 1000.0
     gbs = alg_bytes / t_launch / 1e9
-    traffic, traffic_note = slab_traffic(args.workload)
-    roof = dict(bound="hbm", achieved=gbs, peak=hbm, unit="GB/s", frac=gbs / hbm,
-                peak_source="%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind, traffic=traffic,
-                kernel="k_slab (fused sampled products a6-a8: last-two-mode products, residual, transpose)",
-                alg_bytes_per_launch=alg_bytes, bytes_rule="10 B per distinct sampled row + 2 R_N 4 B per non-empty cell",
-                distinct_rows=distinct, nonempty_cells=cells, launches=n_r, avg_launch_ms=ms_r / n_r,
-                fused_kernel_bytes_per_launch=fused_bytes, fused_kernel_gbs=fused_bytes / t_launch / 1e9,
-                flops_per_launch=alg_flops, tflops=alg_flops / t_launch / 1e12)
+    traffic, traffic_note = kernel_traffic("k_slab", args.workload)
+    slab_roof = dict(bound="hbm", achieved=gbs, peak=hbm, unit="GB/s", frac=gbs / hbm, peak_source=peak_source,
+                     traffic=traffic,
+                     kernel="k_slab (fused sampled products a6-a8: last-two-mode products, residual, transpose)",
+                     alg_bytes_per_launch=alg_bytes,
+                     bytes_rule="10 B per distinct sampled row + 2 R_N 4 B per non-empty cell",
+                     distinct_rows=distinct, nonempty_cells=cells, launches=n_r, avg_launch_ms=ms_r / n_r,
+                     fused_kernel_bytes_per_launch=fused_bytes, fused_kernel_gbs=fused_bytes / t_launch / 1e9,
+                     flops_per_launch=alg_flops, tflops=alg_flops / t_launch / 1e12)
     if traffic_note:
-        roof["traffic_note"] = traffic_note
+        slab_roof["traffic_note"] = traffic_note
+    ms_d, n_d = tim["sample"]
+    s_draws = int(rep_t["s"])
+    draw_bytes = s_draws * (4 * N + 4 + 36) + distinct * 8
+    t_draw = ms_d / max(n_d, 1) / 1000.0
+    dtraffic, dnote = kernel_traffic("k_draw_keys", args.workload)
+    draw_roof = dict(bound="hbm", achieved=draw_bytes / t_draw / 1e9, peak=hbm, unit="GB/s",
+                     frac=draw_bytes / t_draw / 1e9 / hbm, peak_source=peak_source, traffic=dtraffic,
+                     kernel="k_draw_keys (Philox draws from the product distribution, inverse CDF, dense "
+                            "per-key counts and the key bitmap: a3 + a4 in one launch)",
+                     alg_bytes_per_launch=draw_bytes,
+                     bytes_rule="per draw 4 N + 4 B (a3: indices and weight) + 36 B (a4: three 12-byte passes); "
+                                "8 B per distinct row",
+                     draws=s_draws, distinct_rows=distinct, launches=n_d, avg_launch_ms=ms_d / max(n_d, 1),
+                     draws_per_s=s_draws / t_draw)
+    if dnote:
+        draw_roof["traffic_note"] = dnote
+    if ms_d >= ms_r:
+        roof = dict(draw_roof, secondary=slab_roof)
+    else:
+        roof = dict(slab_roof, secondary=draw_roof)
     total_timed = sum(v[0] for v in tim.values())
     shares = {k: (round(v[0] / total_timed, 4) if total_timed else None) for k, v in tim.items()}
     mean = lambda rs, key: float(np.mean([r[key] for r in rs]))
@@ -567,11 +594,11 @@ def run_case(name):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=90)
+    ap.add_argument("--steps", type=int, default=110)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="kron_n3_1024x64_outliers", choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-fraction", type=float, default=0.05)
+    ap.add_argument("--cpu-fraction", type=float, default=0.1)
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--ref-fraction", type=float, default=0.001)
     ap.add_argument("--ref-iters", type=int, default=1)

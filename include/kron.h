@@ -168,10 +168,11 @@ KR_API int64_t kr_autotune_report(kr_ctx* ctx, char* buf, int64_t cap);
 enum {
   KR_K_RESID = 0,      /* sampled residual + transpose accumulation (a7 + a8) */
   KR_K_MODEPROD = 1,   /* mode-n products (KronMatMul, preconditioner) */
-  KR_K_SAMPLE = 2,     /* Philox sampling of the row keys (a3) */
+  KR_K_SAMPLE = 2,     /* Philox sampling of the row keys (a3; with the dense grouping also its
+                          per-key counts and key bitmap, a4, in the same kernel) */
   KR_K_SCATTER = 3,    /* grouping of the row keys: radix sort or key-bitmap ranks (a4) */
   KR_K_DEDUP = 4,      /* merge of repeated rows + gather of b (a4 + a5) */
-  KR_K_TABLES = 5,     /* Gram, Cholesky, leverage, CDF, eigen (a1 + a2) */
+  KR_K_TABLES = 5,     /* Gram, Cholesky, leverage, CDF, eigen, guide tables, probability ranks (a1 + a2) */
   KR_K_VECTOR = 6,     /* Richardson update, reductions (a10) */
   KR_K_SLAB = 7,       /* fused slab pass: last-two-mode products + sampled residual (a6-a8) */
   KR_K_KINDS = 8

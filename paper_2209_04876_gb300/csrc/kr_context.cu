@@ -285,9 +285,8 @@ int kr_kind_of(const char* k) {
   if (s.find("k_mode_product") != std::string::npos || s.find("k_gemm_tc") != std::string::npos ||
       s.find("k_tc_split") != std::string::npos)
     return KR_K_MODEPROD;
-  if (s.find("k_sample") != std::string::npos || s.find("k_draw") != std::string::npos ||
-      s.find("k_guide") != std::string::npos || s.find("k_prob_rank") != std::string::npos)
-    return KR_K_SAMPLE;
+  if (s.find("k_sample") != std::string::npos || s.find("k_draw") != std::string::npos) return KR_K_SAMPLE;
+  if (s.find("k_guide") != std::string::npos || s.find("k_prob_rank") != std::string::npos) return KR_K_TABLES;
   if (s.find("k_radix") != std::string::npos || s.find("k_bm_") != std::string::npos) return KR_K_SCATTER;
   if (s.find("k_rle") != std::string::npos || s.find("k_cell_w") != std::string::npos) return KR_K_DEDUP;
   if (s.find("k_gram") != std::string::npos || s.find("k_chol") != std::string::npos ||
