@@ -156,6 +156,9 @@ KR_API int64_t kr_launch_count(const kr_ctx* ctx);
  * on this context so far; counted in kr_launch_count too. */
 KR_API int64_t kr_tc_launch_count(const kr_ctx* ctx);
 
+/* CUDA graphs launched on this context so far (the device-side Richardson loops). */
+KR_API int64_t kr_graph_count(const kr_ctx* ctx);
+
 /* The autotuner's choices (KR_OPT_AUTOTUNE) as text, one shape class per line:
  * "N I_{N-1} R_{N-1} I_N R_N log2s budget ms@2048 ms@4096 ms@8192 ms@16384 ms@32768".
  * Writes at most cap bytes (NUL-terminated when cap > 0); returns the length of the full text. */

@@ -22,7 +22,7 @@ KERNEL_KINDS = {"resid": 0, "modeprod": 1, "sample": 2, "scatter": 3, "dedup": 4
                 "slab": 7}
 OPT_SLAB_PASS, OPT_SLAB_TILE_ENTRIES, OPT_DEVICE_LOOP, OPT_BATCH_WORKERS, OPT_GROUPING, OPT_HOST_GATHER = 1, 2, 3, 4, 5, 6
 OPT_JL_K, OPT_JL_SEED, OPT_TENSOR_CORES, OPT_BATCH_MODE, OPT_AUTOTUNE = 7, 8, 9, 10, 11
-EXPORTED = ["kr_create", "kr_destroy", "kr_set_stream", "kr_last_error", "kr_launch_count", "kr_tc_launch_count", "kr_autotune_report", "kr_timing_enable",
+EXPORTED = ["kr_create", "kr_destroy", "kr_set_stream", "kr_last_error", "kr_launch_count", "kr_tc_launch_count", "kr_graph_count", "kr_autotune_report", "kr_timing_enable",
             "kr_timing_read", "kr_timing_reset", "kr_set_option", "kron_sample_count", "kron_leverage",
             "kron_sample", "kron_sample_noalloc", "kron_sketch", "kron_sketch_distinct", "kron_sketch_export", "kron_sketch_residual",
             "kron_sketch_free", "kron_matmul", "kron_precond", "kron_objective", "kron_regress", "kron_ridge",
@@ -86,6 +86,7 @@ def lib():
             "kr_last_error": (ctypes.c_char_p, [vp]),
             "kr_launch_count": (i64, [vp]),
             "kr_tc_launch_count": (i64, [vp]),
+            "kr_graph_count": (i64, [vp]),
             "kr_autotune_report": (i64, [vp, ctypes.c_char_p, i64]),
             "kr_timing_enable": (i32, [vp, i32]),
             "kr_timing_read": (i32, [vp, i32, P(dbl), P(i64)]),
@@ -142,6 +143,11 @@ def launch_count():
 def tc_launch_count():
     """Launches of the tcgen05 tensor-core mode product on this device's context so far."""
     return int(lib().kr_tc_launch_count(context()))
+
+
+def graph_count():
+    """CUDA graphs the library launched on this device's context so far."""
+    return int(lib().kr_graph_count(context()))
 
 
 def autotune_report():

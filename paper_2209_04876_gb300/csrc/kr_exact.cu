@@ -275,11 +275,22 @@ kr_status ex_dot(kr_ctx* ctx, const float* a, const BT* bv, int64_t n, const ExB
 }
 
 // red[0] = ||X||^2, red[1] = <g, G>, red[2] = <G, G x_m Gram_m> for the current factors.
+// The three terms nearly cancel (an RRE of 1e-4 comes from terms of order 1), so g is
+// projected on the CUDA cores: the tensor-core product's rounding is biased (its FP32
+// accumulation truncates, error of one sign about 1e-6 of the product), which the cancellation
+// would turn into a percent-level RRE error, while the CUDA-core sum's errors are unbiased and
+// average out over the R terms of <g, G>.
 kr_status ex_rre_terms(kr_ctx* ctx, const Modes& m, const float* X, const float* G, const FactorTables& t,
                        const ExBufs& b, bool have_g) {
   const int64_t R = kr_prod_R(m);
   KR_TRY(ex_dot<float>(ctx, X, X, kr_prod_I(m), b, 0));
-  if (!have_g) KR_TRY(ex_project(ctx, m, X, -1, b, b.Z));
+  if (!have_g || ctx->tensor_cores) {
+    const int tc = ctx->tensor_cores;
+    ctx->tensor_cores = 0;
+    const kr_status st = ex_project(ctx, m, X, -1, b, b.Z);
+    ctx->tensor_cores = tc;
+    KR_TRY(st);
+  }
   KR_TRY(ex_dot<float>(ctx, b.Z, G, R, b, 1));
   const double* W = nullptr;
   KR_TRY(ex_gram_apply(ctx, m, t, G, -1, b, &W));

@@ -76,6 +76,8 @@ struct kr_ctx {
   size_t tc_size = 0;
   int* tc_err = nullptr;
   int64_t tc_launches = 0;
+  int tc_attr = 0;  // dynamic shared memory the tensor-core kernel has been allowed
+  int64_t graphs = 0;  // CUDA graphs this context launched (device loops, sweeps)
   // worker contexts of kron_ridge_batched, each with its own stream and workspace (owned)
   std::vector<kr_ctx*> workers;
   std::vector<cudaStream_t> worker_streams;

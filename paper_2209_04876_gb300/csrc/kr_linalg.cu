@@ -249,7 +249,14 @@ __global__ void __launch_bounds__(LEV_ROWS * 32) k_leverage(ModePtrs mp) {
 // word w0 of Philox4x32-10 under the JL key at counter (r k + j, 0, mode, 0) (0: +1, 1: -1).
 // E[l~_i] = l_i. The cost per row is R k instead of about R^2 / 2.
 constexpr int JL_MAXK = 64;
-__global__ void k_jl_basis(ModePtrs mp, int k, uint32_t s0, uint32_t s1, double* const* __restrict__ B) {
+// Per-mode device pointers passed to a kernel by value (inside its parameter block): a
+// kernel must never receive a host array of device pointers, which would outlive neither the
+// host frame that holds it nor a device without access to host memory.
+struct PtrSet {
+  double* p[KR_MAX_MODES];
+};
+
+__global__ void k_jl_basis(ModePtrs mp, int k, uint32_t s0, uint32_t s1, PtrSet B) {
   const int n = blockIdx.y;
   const int R = mp.R[n];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < R * k; e += gridDim.x * blockDim.x) {
@@ -260,12 +267,12 @@ __global__ void k_jl_basis(ModePtrs mp, int k, uint32_t s0, uint32_t s1, double*
       const double sg = (w.x & 1u) ? -1.0 : 1.0;
       acc = fma(mp.linv[n][r * R + c], sg, acc);
     }
-    B[n][e] = acc;
+    B.p[n][e] = acc;
   }
 }
 
 // l~_i for LEV_ROWS rows per block, one warp per row, lanes over the k columns of B.
-__global__ void __launch_bounds__(LEV_ROWS * 32) k_leverage_jl(ModePtrs mp, int k, const double* const* __restrict__ B) {
+__global__ void __launch_bounds__(LEV_ROWS * 32) k_leverage_jl(ModePtrs mp, int k, PtrSet B) {
   const int n = blockIdx.y;
   const int I = mp.I[n], R = mp.R[n];
   const int r0 = blockIdx.x * LEV_ROWS;
@@ -274,7 +281,7 @@ __global__ void __launch_bounds__(LEV_ROWS * 32) k_leverage_jl(ModePtrs mp, int 
   double* Bs = sm;                 // R x k
   double* a = sm + MAXR * JL_MAXK;  // LEV_ROWS x LD
   const int rows = min(LEV_ROWS, I - r0);
-  for (int e = threadIdx.x; e < R * k; e += blockDim.x) Bs[e] = B[n][e];
+  for (int e = threadIdx.x; e < R * k; e += blockDim.x) Bs[e] = B.p[n][e];
   for (int e = threadIdx.x; e < rows * R; e += blockDim.x)
     a[(e / R) * LD + (e % R)] = (double)mp.A[n][(int64_t)(r0 + e / R) * R + (e % R)];
   __syncthreads();
@@ -465,18 +472,17 @@ __global__ void k_jacobi(JacobiArgs<T> ja) {
 
 // FP32 copies of the FP64 eigenpairs, all modes in one grid (mode n's R x R vectors then
 // its R values, in mode order).
-__global__ void k_eig_to_f32(ModePtrs mp, const double* const* unused, double* const* V64, double* const* s64) {
-  (void)unused;
+__global__ void k_eig_to_f32(ModePtrs mp, PtrSet V64, PtrSet s64) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   for (int n = 0; n < mp.N; ++n) {
     const int R = mp.R[n], rr = R * R;
     if (e < rr) {
-      mp.V[n][e] = (float)V64[n][e];
+      mp.V[n][e] = (float)V64.p[n][e];
       return;
     }
     e -= rr;
     if (e < R) {
-      mp.sig2[n][e] = (float)s64[n][e];
+      mp.sig2[n][e] = (float)s64.p[n][e];
       return;
     }
     e -= R;
@@ -573,9 +579,11 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
     const int k = ctx->jl_k;
     const size_t jl_smem = ((size_t)MAXR * JL_MAXK + LEV_ROWS * LD) * sizeof(double);
     KR_TRY(kr_smem_attr(ctx, k_leverage_jl, jl_smem));
+    PtrSet jls = {};
+    for (int n = 0; n < m.N; ++n) jls.p[n] = jlB[n];
     KR_LAUNCH(ctx, k_jl_basis, dim3((maxR * k + 255) / 256, m.N), 256, 0, mp, k, (uint32_t)ctx->jl_seed,
-              (uint32_t)(ctx->jl_seed >> 32), (double* const*)jlB);
-    KR_LAUNCH(ctx, k_leverage_jl, gl, LEV_ROWS * 32, jl_smem, mp, k, (const double* const*)jlB);
+              (uint32_t)(ctx->jl_seed >> 32), jls);
+    KR_LAUNCH(ctx, k_leverage_jl, gl, LEV_ROWS * 32, jl_smem, mp, k, jls);
   } else {
     KR_LAUNCH(ctx, k_leverage, gl, LEV_ROWS * 32, lev_smem, mp);
   }
@@ -584,7 +592,12 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
     KR_TRY(kr_eig64(ctx, m.N, m.R, mp.gram, V64, s64));
     int tot = 0;
     for (int n = 0; n < m.N; ++n) tot += m.R[n] * (m.R[n] + 1);
-    KR_LAUNCH(ctx, k_eig_to_f32, (tot + 255) / 256, 256, 0, mp, (const double* const*)nullptr, V64, s64);
+    PtrSet vs = {}, ss = {};
+    for (int n = 0; n < m.N; ++n) {
+      vs.p[n] = V64[n];
+      ss.p[n] = s64[n];
+    }
+    KR_LAUNCH(ctx, k_eig_to_f32, (tot + 255) / 256, 256, 0, mp, vs, ss);
   }
   if (check_rank) {
     int ntot = 0;

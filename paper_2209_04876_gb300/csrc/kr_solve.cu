@@ -1467,6 +1467,7 @@ bool kr_graph_while(kr_ctx* ctx, const std::function<kr_status(cudaGraphConditio
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
   if (!ok) cudaGetLastError();  // graphs unavailable: the host loop takes over
+  if (ok) ctx->graphs++;
   return ok;
 }
 

@@ -472,7 +472,10 @@ kr_status kr_gemm_tc(kr_ctx* ctx, const float* X, int64_t M, int K, const float*
     if (blocks > ctx->num_sms * 4) blocks = ctx->num_sms * 4;
     KR_LAUNCH(ctx, k_tc_split_b, blocks, 256, 0, B, J, K, trans, bh, bl);
   }
-  KR_CUDA(ctx, cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem));
+  if ((int)sh.smem > ctx->tc_attr) {  // once per context (not again inside a stream capture)
+    KR_CUDA(ctx, cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin));
+    ctx->tc_attr = (int)ctx->smem_optin;
+  }
   TcArgs a;
   a.Y = Y;
   a.M = M;
@@ -511,3 +514,5 @@ kr_status kr_tc_check(kr_ctx* ctx) {
 }
 
 extern "C" int64_t kr_tc_launch_count(const kr_ctx* ctx) { return ctx ? ctx->tc_launches : 0; }
+
+extern "C" int64_t kr_graph_count(const kr_ctx* ctx) { return ctx ? ctx->graphs : 0; }
