@@ -156,7 +156,8 @@ KR_API int64_t kr_launch_count(const kr_ctx* ctx);
  * on this context so far; counted in kr_launch_count too. */
 KR_API int64_t kr_tc_launch_count(const kr_ctx* ctx);
 
-/* CUDA graphs launched on this context so far (the device-side Richardson loops). */
+/* CUDA graphs launched on this context so far: the device-side Richardson loops, and the
+ * sweeps after the first of tucker_als_exact_sweep (captured together as one graph). */
 KR_API int64_t kr_graph_count(const kr_ctx* ctx);
 
 /* The autotuner's choices (KR_OPT_AUTOTUNE) as text, one shape class per line:
@@ -428,7 +429,11 @@ KR_API kr_status tucker_als_sweep(kr_ctx* ctx, int32_t N, const int64_t* I, cons
  * reconstruction error ||X - G x_1 A(1) ... x_N A(N)||^2 / ||X||^2 after each sweep.
  * With lambda = 0 every R[n] must not exceed the product of the other ranks (else the factor
  * system G_(n) (K^T K) G_(n)^T is singular: KR_EINVAL). Returns KR_ERANK if a factor system
- * is not positive definite (a rank-deficient core unfolding or factor). */
+ * is not positive definite (a rank-deficient core unfolding or factor; checked on the device
+ * and reported after the last sweep). The first sweep runs from the host; with
+ * KR_OPT_DEVICE_LOOP 1 (the default) every later sweep (its N factor updates, the core update
+ * and its RRE terms) is captured into ONE CUDA graph launched once (kr_graph_count counts it),
+ * with results bit-identical to running the same sweeps from the host. */
 KR_API kr_status tucker_als_exact_sweep(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R, const float* X,
                                         float* const A[], float* G, double lambda, int32_t sweeps, double* rre);
 

@@ -119,19 +119,39 @@ def lib():
     return _lib
 
 
+_lib_streams = {}
+
+
+def _stream_for(dev):
+    """The stream the library runs on: torch's current stream, or, when that is the legacy
+    default stream (which CUDA graphs cannot capture, so the device-side loops would fall
+    back to host loops), a per-device library stream that first waits for the current
+    stream's work. Every library call synchronises its stream before it returns, so results
+    are complete when the call returns."""
+    cur = torch.cuda.current_stream(dev)
+    if cur.cuda_stream != 0:
+        return cur
+    s = _lib_streams.get(dev)
+    if s is None:
+        s = _lib_streams[dev] = torch.cuda.Stream(dev)
+    s.wait_stream(cur)
+    return s
+
+
 def context(device=None):
-    """Per-device library context, bound to the current torch stream at each call."""
+    """Per-device library context, bound at each call to torch's current stream (or to the
+    library stream that stands in for the legacy default stream)."""
     dev = torch.cuda.current_device() if device is None else int(device)
     L = lib()
     if dev not in _ctx:
         with torch.cuda.device(dev):
             h = ctypes.c_void_p()
-            st = L.kr_create(ctypes.byref(h), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), 0)
+            st = L.kr_create(ctypes.byref(h), ctypes.c_void_p(_stream_for(dev).cuda_stream), 0)
             if st != 0:
                 raise KronError(st, "kr_create failed")
             _ctx[dev] = h
     h = _ctx[dev]
-    L.kr_set_stream(h, ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))
+    L.kr_set_stream(h, ctypes.c_void_p(_stream_for(dev).cuda_stream))
     return h
 
 

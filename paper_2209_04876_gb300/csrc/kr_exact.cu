@@ -14,6 +14,8 @@
 // with g = X x_m A(m)^T at the same factors (one pass over X, no reconstruction).
 #include <math.h>
 
+#include <string>
+
 #include "kr_internal.cuh"
 
 namespace {
@@ -298,6 +300,15 @@ kr_status ex_rre_terms(kr_ctx* ctx, const Modes& m, const float* X, const float*
   return KR_OK;
 }
 
+// OR of a table build's per-mode pivot flags into the sweep's flag.
+__global__ void k_flags_or(const int* __restrict__ f, int n, int* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    int v = 0;
+    for (int i = 0; i < n; ++i) v |= f[i];
+    if (v) atomicOr(out, 1);
+  }
+}
+
 double ex_rre_from(const double* h) { return h[0] > 0.0 ? (h[0] - 2.0 * h[1] + h[2]) / h[0] : 0.0; }
 
 kr_status ex_args(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R, const float* X, const float* const A[],
@@ -331,16 +342,22 @@ extern "C" kr_status tucker_als_exact_sweep(kr_ctx* ctx, int32_t N, const int64_
                        "tucker_als_exact_sweep: lambda = 0 needs R[n] <= prod of the other ranks (mode %d: %d > %lld)", n,
                        m.R[n], (long long)(Rt / m.R[n]));
   }
+  const size_t nrre = 3 * (size_t)(sweeps > 0 ? sweeps : 1);  // the RRE terms of every sweep
   Need nd;
+  nd.add<double>(nrre);
   KR_TRY(ex_need(m, nd));
   KR_TRY(kr_ws_reserve(ctx, nd.off));
-  KR_TRY(kr_hbuf_reserve(ctx, 4096));
+  KR_TRY(kr_hbuf_reserve(ctx, 4096 + sizeof(double) * nrre));
   Carve cv(ctx->ws, ctx->ws_size);
+  double* rre_dev = cv.take<double>(nrre);
   ExBufs b = ex_carve(m, cv);
   const Carve tables_cv = cv;
   KR_CUDA(ctx, cudaMemsetAsync(b.flag, 0, sizeof(int), ctx->stream));
-  const int64_t Rtot = kr_prod_R(m);
-  for (int k = 0; k < sweeps; ++k) {
+  // One sweep: the N factor updates, the core update, and the sweep's RRE terms into
+  // rre_dev[3 k..]. Nothing in it reads device data on the host (rank-deficient factors are
+  // flagged on the device), so the sweeps after the first, which sizes every buffer and sets
+  // every kernel attribute, can be captured into one graph.
+  auto one_sweep = [&](int k) -> kr_status {
     for (int n = 0; n < N; ++n) {
       Carve tc = tables_cv;
       FactorTables t;
@@ -364,21 +381,65 @@ extern "C" kr_status tucker_als_exact_sweep(kr_ctx* ctx, int32_t N, const int64_
     // core: g = X x_m A(m)^T, G = (K^T K + lambda I)^-1 g (Alg. 2's preconditioner, exact)
     Carve tc = tables_cv;
     FactorTables t;
-    KR_TRY(kr_tables_build(ctx, m, lambda > 0.0, tc, t, true));
+    KR_TRY(kr_tables_build(ctx, m, lambda > 0.0, tc, t, false));
+    KR_LAUNCH(ctx, k_flags_or, 1, 32, 0, (const int*)t.flags, N, b.flag);
     KR_TRY(ex_project(ctx, m, X, -1, b, b.Z));
     KR_TRY(kr_precond_apply(ctx, t, lambda, b.Z, G, b.t0, b.t1));
     if (rre) {
       KR_TRY(ex_rre_terms(ctx, m, X, G, t, b, true));
-      KR_CUDA(ctx, cudaMemcpyAsync(ctx->hbuf, b.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-      KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-      rre[k] = ex_rre_from((const double*)ctx->hbuf);
+      KR_CUDA(ctx, cudaMemcpyAsync(rre_dev + 3 * k, b.red, 3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    return KR_OK;
+  };
+  int done = 0;
+  if (sweeps > 0) {
+    KR_TRY(one_sweep(0));
+    done = 1;
+  }
+  if (sweeps > 1 && ctx->device_loop && !ctx->timing) {
+    // sweeps 2.. captured into ONE CUDA graph, launched once
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const int64_t l0 = ctx->launches;
+    std::string why;
+    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) why = std::string("begin capture: ") + cudaGetErrorString(e);
+    if (why.empty()) {
+      kr_status cs = KR_OK;
+      for (int k = 1; k < sweeps && cs == KR_OK; ++k) cs = one_sweep(k);
+      if (cs != KR_OK) why = "capture: " + ctx->err;
+      e = cudaStreamEndCapture(ctx->stream, &graph);
+      if (e != cudaSuccess && why.empty()) why = std::string("end capture: ") + cudaGetErrorString(e);
+    }
+    if (why.empty() && (e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
+      why = std::string("instantiate: ") + cudaGetErrorString(e);
+    if (why.empty() && (e = cudaGraphLaunch(exec, ctx->stream)) != cudaSuccess)
+      why = std::string("launch: ") + cudaGetErrorString(e);
+    if (why.empty() && (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+      why = std::string("run: ") + cudaGetErrorString(e);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (why.empty()) {
+      done = sweeps;
+      ctx->graphs++;
+    } else {
+      cudaGetLastError();  // graphs unavailable: the remaining sweeps run from the host
+      ctx->launches = l0;
+      ctx->err = "tucker_als_exact_sweep: sweeps 2.. ran from the host (" + why + ")";
     }
   }
+  for (int k = done; k < sweeps; ++k) KR_TRY(one_sweep(k));
+  double* hr = reinterpret_cast<double*>(ctx->hbuf + 64);
+  if (rre && sweeps > 0)
+    KR_CUDA(ctx, cudaMemcpyAsync(hr, rre_dev, sizeof(double) * 3 * (size_t)sweeps, cudaMemcpyDeviceToHost, ctx->stream));
   KR_CUDA(ctx, cudaMemcpyAsync(ctx->hbuf, b.flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  (void)Rtot;
-  if (*(const int*)ctx->hbuf) return kr_fail(ctx, KR_ERANK, "tucker_als_exact_sweep: a factor system is not positive definite");
-  return KR_OK;
+  if (rre)
+    for (int k = 0; k < sweeps; ++k) rre[k] = ex_rre_from(hr + 3 * k);
+  if (*(const int*)ctx->hbuf)
+    return kr_fail(ctx, KR_ERANK, "tucker_als_exact_sweep: a factor system is not positive definite or a factor is "
+                                  "rank deficient");
+  return kr_tc_check(ctx);
 }
 
 extern "C" kr_status tucker_rre(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R, const float* X,

@@ -261,6 +261,7 @@ struct FactorTables {
   double sig_max[KR_MAX_MODES] = {}; // host copies of each mode's largest and smallest eigenvalue
   double sig_min[KR_MAX_MODES] = {}; // (read back with the rank check when the eigen-decomposition is built)
   int rank[KR_MAX_MODES] = {};
+  int* flags = nullptr;              // device: per mode, nonzero when its Cholesky met a non-positive pivot
 };
 
 // Computes Gram, Cholesky, leverage scores, CDF, thresholds, inverse probabilities,

@@ -561,7 +561,7 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
     }
     maxI = I > maxI ? I : maxI;
   }
-  mp.flags = cv.take<int>(KR_MAX_MODES);
+  mp.flags = t.flags = cv.take<int>(KR_MAX_MODES);
   if (cv.off > cv.cap) return kr_fail(ctx, KR_ENOMEM, "tables: workspace too small");
 
   const size_t chol_smem = 3 * MAXR * LD * sizeof(double);

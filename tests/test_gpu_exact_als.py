@@ -84,3 +84,25 @@ def test_exact_sweep_rejects_singular_factor_systems():
     with pytest.raises(kr.KronError) as e:
         kr.tucker_als_exact_sweep(dev(X), [dev(A) for A in As], dev(G), 0.0, sweeps=1)
     assert e.value.name == "KR_EINVAL"
+
+
+@pytest.mark.parametrize("lam", [0.0, 1e-3])
+def test_exact_sweeps_as_one_graph_match_host_sweeps(lam):
+    """Sweeps after the first are captured into one CUDA graph (N factor updates, the core
+    update and the RRE terms of each): factors, core and RRE equal the host-driven sweeps bit
+    for bit, and exactly one graph ran for the call."""
+    X, As, G = _state([40, 36, 30], [5, 4, 6], seed=21)
+    out = {}
+    for loop in (0, 1):
+        kr.set_option(kr.OPT_DEVICE_LOOP, loop)
+        A_gpu = [dev(A) for A in As]
+        G_gpu = dev(G)
+        g0 = kr.graph_count()
+        rre = kr.tucker_als_exact_sweep(dev(X), A_gpu, G_gpu, lam, sweeps=4)
+        out[loop] = ([A.cpu() for A in A_gpu], G_gpu.cpu(), rre, kr.graph_count() - g0)
+    kr.set_option(kr.OPT_DEVICE_LOOP, 1)
+    assert out[0][3] == 0 and out[1][3] == 1
+    for a, b in zip(out[0][0], out[1][0]):
+        assert torch.equal(a, b)
+    assert torch.equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
