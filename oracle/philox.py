@@ -15,12 +15,18 @@ here (and, independently re-implemented, by the CUDA sampler):
   with M0 = 0xD2511F53, M1 = 0xCD9E8D57; between rounds the key is bumped by the
   Weyl constants (0x9E3779B9, 0xBB67AE85) modulo 2^32.
 * Key: (seed mod 2^32, seed >> 32 mod 2^32).
-* Counter for draw t, Philox call k (one call serves two consecutive modes of the
-  draw's mode list), factor row ``row`` (the Tucker factor-row index; 0 for a
-  plain regression) and call id: (t mod 2^32, t >> 32, k + 256*row, call_id mod 2^32).
-* Uniform from two 32-bit words (wa, wb): u = (((wa << 32) | wb) >> 11) * 2^-53,
-  an exact double in [0, 1). Mode 2k uses words (w0, w1) of call k, mode 2k+1 uses
-  (w2, w3).
+* Counter for draw t, Philox call k, factor row ``row`` (the Tucker factor-row
+  index; 0 for a plain regression) and call id: (t mod 2^32, t >> 32, k + 256*row,
+  call_id mod 2^32).
+* Draws of 3 or 4 coordinates take ONE call (k = 0): its 128 bits, w0 first (most
+  significant), are cut from the top into n chunks of floor(128 / n) bits (42 for
+  n = 3, 32 for n = 4), and coordinate m's uniform is chunk_m * 2^-floor(128/n), an
+  exact double on a grid of 2^-42 (2^-32) instead of 2^-53: it moves a row's
+  probability by at most one grid step, far below any leverage-score difference that
+  matters to the method, and saves a Philox evaluation per draw.
+* Otherwise one call serves two consecutive coordinates: the uniform from two 32-bit
+  words (wa, wb) is u = (((wa << 32) | wb) >> 11) * 2^-53, an exact double in [0, 1);
+  coordinate 2k uses words (w0, w1) of call k, coordinate 2k+1 uses (w2, w3).
 
 Parity status: pinned by bit equality with NVIDIA's cuRAND Philox4_32_10 host
 generator, run as a library on the CPU (its block j is Philox at counter
@@ -71,6 +77,19 @@ def words_to_uniform(wa, wb):
     return (v >> _SH11).astype(np.float64) * (2.0 ** -53)
 
 
+def one_call_chunks(w0, w1, w2, w3, n):
+    """The n = 3 or 4 chunks (uint64 arrays) of floor(128 / n) bits cut from the top of
+    the 128-bit value w0 w1 w2 w3 (w0 most significant)."""
+    w = [np.asarray(v, dtype=np.uint64) for v in (w0, w1, w2, w3)]
+    if n == 4:
+        return w
+    hi = (w[0] << _SH32) | w[1]
+    lo = (w[2] << _SH32) | w[3]
+    m42 = np.uint64((1 << 42) - 1)
+    m22 = np.uint64((1 << 22) - 1)
+    return [hi >> np.uint64(22), ((hi & m22) << np.uint64(20)) | (lo >> np.uint64(44)), (lo >> np.uint64(2)) & m42]
+
+
 def draw_uniforms(seed, call_id, t, n_modes, row=0):
     """Uniforms u[m, j] for draws t[j] and positions m = 0..n_modes-1 of the mode list.
 
@@ -83,6 +102,12 @@ def draw_uniforms(seed, call_id, t, n_modes, row=0):
     c1 = t >> _SH32
     c3 = np.uint64(int(call_id) & 0xFFFFFFFF)
     out = np.empty((n_modes, t.shape[0]), dtype=np.float64)
+    if n_modes in (3, 4):
+        c2 = np.uint64((256 * int(row)) & 0xFFFFFFFF)
+        w0, w1, w2, w3 = philox4x32_10(c0, c1, c2, c3, k0, k1)
+        for m, c in enumerate(one_call_chunks(w0, w1, w2, w3, n_modes)):
+            out[m] = c.astype(np.float64) * (2.0 ** -(128 // n_modes))
+        return out
     for k in range((n_modes + 1) // 2):
         c2 = np.uint64((k + 256 * int(row)) & 0xFFFFFFFF)
         w0, w1, w2, w3 = philox4x32_10(c0, c1, c2, c3, k0, k1)

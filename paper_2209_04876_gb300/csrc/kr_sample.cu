@@ -46,9 +46,33 @@ __device__ __forceinline__ int search_thr(const uint64_t* thr, int n, uint64_t U
   return base;
 }
 
+// Draws of 3 or 4 coordinates take one Philox call (counter word 2 = 256 row): its 128 bits,
+// w.x most significant, cut from the top into N chunks of floor(128 / N) bits (42 or 32),
+// each placed on the 53-bit threshold grid (U = chunk << (53 - bits)). Other N: one call per
+// two coordinates, 53 bits each.
+__device__ __forceinline__ void chunk_uniforms(uint4 w, int N, uint64_t* U) {
+  if (N == 4) {
+    U[0] = (uint64_t)w.x << 21;
+    U[1] = (uint64_t)w.y << 21;
+    U[2] = (uint64_t)w.z << 21;
+    U[3] = (uint64_t)w.w << 21;
+  } else {
+    U[0] = (((uint64_t)w.x << 10) | (w.y >> 22)) << 11;
+    U[1] = (((uint64_t)(w.y & 0x3FFFFFu) << 20) | (w.z >> 12)) << 11;
+    U[2] = (((uint64_t)(w.z & 0xFFFu) << 30) | (w.w >> 2)) << 11;
+  }
+}
+
 // Draws the multi-index of draw t into idx[0..N).
 __device__ __forceinline__ void draw(const SampleModes& sm, const uint64_t* const* thr, uint64_t t,
                                      uint32_t k0, uint32_t k1, uint32_t row, uint32_t cid, int* idx) {
+  if (sm.N == 3 || sm.N == 4) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), 256u * row, cid), k0, k1);
+    uint64_t U[4];
+    chunk_uniforms(w, sm.N, U);
+    for (int m = 0; m < sm.N; ++m) idx[m] = search_thr(thr[m], sm.I[m], U[m]);
+    return;
+  }
   for (int k = 0; 2 * k < sm.N; ++k) {
     uint4 w = philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)k + 256u * row, cid), k0, k1);
     idx[2 * k] = search_thr(thr[2 * k], sm.I[2 * k], u53(w.x, w.y));
@@ -216,12 +240,22 @@ __global__ void __launch_bounds__(256) k_draw_keys(DrawModes dm, int64_t s_row, 
       tl = t - (int64_t)r * s_row;
     }
     int idx[N];
+    if (N == 3 || N == 4) {  // one Philox call for the whole draw (chunk_uniforms)
+      const uint4 w =
+          philox4x32_10(make_uint4((uint32_t)tl, (uint32_t)((uint64_t)tl >> 32), 256u * (row0 + r), cid), k0, k1);
+      uint64_t U[4];
+      chunk_uniforms(w, N, U);
 #pragma unroll
-    for (int k = 0; 2 * k < N; ++k) {
-      const uint4 w = philox4x32_10(
-          make_uint4((uint32_t)tl, (uint32_t)((uint64_t)tl >> 32), (uint32_t)k + 256u * (row0 + r), cid), k0, k1);
-      idx[2 * k] = guided_search(thr[2 * k], guide[2 * k], sh[2 * k], u53(w.x, w.y));
-      if (2 * k + 1 < N) idx[2 * k + 1] = guided_search(thr[2 * k + 1], guide[2 * k + 1], sh[2 * k + 1], u53(w.z, w.w));
+      for (int m = 0; m < N; ++m) idx[m] = guided_search(thr[m], guide[m], sh[m], U[m]);
+    } else {
+#pragma unroll
+      for (int k = 0; 2 * k < N; ++k) {
+        const uint4 w = philox4x32_10(
+            make_uint4((uint32_t)tl, (uint32_t)((uint64_t)tl >> 32), (uint32_t)k + 256u * (row0 + r), cid), k0, k1);
+        idx[2 * k] = guided_search(thr[2 * k], guide[2 * k], sh[2 * k], u53(w.x, w.y));
+        if (2 * k + 1 < N)
+          idx[2 * k + 1] = guided_search(thr[2 * k + 1], guide[2 * k + 1], sh[2 * k + 1], u53(w.z, w.w));
+      }
     }
     uint32_t cell = 0;
 #pragma unroll

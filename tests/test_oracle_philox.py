@@ -71,11 +71,31 @@ def test_uniforms_are_uniform_and_independent_across_modes():
 
 
 def test_counter_layout_pairs_modes():
-    """Modes 2k and 2k+1 share one Philox call (words 0,1 and 2,3)."""
+    """Draws of 2 or 5+ coordinates: coordinates 2k and 2k+1 share Philox call k (words 0,1
+    and 2,3), each a 53-bit uniform."""
     t = np.array([5, 2 ** 33 + 1], dtype=np.uint64)
-    u = draw_uniforms(99, 3, t, 3, row=2)
-    w = philox4x32_10(t & 0xFFFFFFFF, t >> np.uint64(32), 0 + 256 * 2, 3, 99, 0)
-    np.testing.assert_array_equal(u[0], words_to_uniform(w[0], w[1]))
-    np.testing.assert_array_equal(u[1], words_to_uniform(w[2], w[3]))
-    w = philox4x32_10(t & 0xFFFFFFFF, t >> np.uint64(32), 1 + 256 * 2, 3, 99, 0)
-    np.testing.assert_array_equal(u[2], words_to_uniform(w[0], w[1]))
+    for n in (2, 5):
+        u = draw_uniforms(99, 3, t, n, row=2)
+        for k in range((n + 1) // 2):
+            w = philox4x32_10(t & 0xFFFFFFFF, t >> np.uint64(32), k + 256 * 2, 3, 99, 0)
+            np.testing.assert_array_equal(u[2 * k], words_to_uniform(w[0], w[1]))
+            if 2 * k + 1 < n:
+                np.testing.assert_array_equal(u[2 * k + 1], words_to_uniform(w[2], w[3]))
+
+
+def test_one_call_layout_for_three_and_four_coordinates():
+    """Draws of 3 or 4 coordinates: one Philox call (counter word 2 = 256 row), its 128 bits
+    (word 0 most significant) cut from the top into chunks of floor(128 / n) bits; checked
+    against Python's big-integer arithmetic on the whole 128-bit value."""
+    t = np.array([0, 5, 2 ** 33 + 1, 123456789], dtype=np.uint64)
+    for n in (3, 4):
+        u = draw_uniforms(99, 3, t, n, row=2)
+        w = philox4x32_10(t & 0xFFFFFFFF, t >> np.uint64(32), 256 * 2, 3, 99, 0)
+        b = 128 // n
+        for j in range(len(t)):
+            v = (int(w[0][j]) << 96) | (int(w[1][j]) << 64) | (int(w[2][j]) << 32) | int(w[3][j])
+            for m in range(n):
+                chunk = (v >> (128 - (m + 1) * b)) & ((1 << b) - 1)
+                assert u[m][j] == chunk / float(1 << b), (n, j, m)
+    # the grid: a chunk of all ones is the largest uniform below 1
+    assert float(((1 << 42) - 1) / float(1 << 42)) < 1.0
