@@ -154,19 +154,21 @@ struct ProbRanks {
 // out[n][i] = #{ j : p_j > p_i, or p_j = p_i and j < i }: row i's place when mode n's rows
 // are sorted by decreasing probability (ties by index). Block (n, c) ranks rows
 // [256 c, 256 c + 256) of mode n.
+// Probabilities are non-negative doubles, which order exactly as their bit patterns do as
+// unsigned integers, so the comparisons run on the integer pipe.
 __global__ void __launch_bounds__(256) k_prob_rank(ProbRanks pr) {
-  __shared__ double sp[PRK_MAX];
+  __shared__ unsigned long long sp[PRK_MAX];
   const int n = blockIdx.x, I = pr.I[n];
   if (256 * (int)blockIdx.y >= I) return;
-  for (int i = threadIdx.x; i < I; i += blockDim.x) sp[i] = pr.prob[n][i];
+  for (int i = threadIdx.x; i < I; i += blockDim.x) sp[i] = (unsigned long long)__double_as_longlong(pr.prob[n][i]);
   __syncthreads();
   {
     const int i = 256 * blockIdx.y + threadIdx.x;
     if (i >= I) return;
-    const double pi = sp[i];
+    const unsigned long long pi = sp[i];
     int r = 0;
     for (int j = 0; j < I; ++j) {
-      const double pj = sp[j];
+      const unsigned long long pj = sp[j];
       r += (pj > pi || (pj == pi && j < i)) ? 1 : 0;
     }
     pr.out[n][i] = (uint16_t)r;
