@@ -144,6 +144,7 @@ extern "C" void kr_destroy(kr_ctx* ctx) {
   if (ctx->dcnt) cudaFree(ctx->dcnt);
   if (ctx->tc_buf) cudaFree(ctx->tc_buf);
   if (ctx->loop_ev) cudaEventDestroy(ctx->loop_ev);
+  if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
   for (cudaEvent_t e : ctx->tune_ev)
     if (e) cudaEventDestroy(e);
   kr_tune_free(ctx);
@@ -168,6 +169,7 @@ extern "C" int64_t kr_launch_count(const kr_ctx* ctx) { return ctx ? ctx->launch
 
 kr_status kr_io_reserve(kr_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->io_size) return KR_OK;
+  if (ctx->gm.on) return kr_fail(ctx, KR_ENOTIMPL, "graph sweep: the host-buffer staging would grow inside the capture");
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->copy_stream) KR_CUDA(ctx, cudaStreamSynchronize(ctx->copy_stream));
   if (ctx->io) {
@@ -187,6 +189,7 @@ kr_status kr_io_reserve(kr_ctx* ctx, size_t bytes) {
 
 kr_status kr_ws_reserve(kr_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->ws_size) return KR_OK;
+  if (ctx->gm.on) return kr_fail(ctx, KR_ENOTIMPL, "graph sweep: the workspace would grow inside the capture");
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->ws) {
     cudaFree(ctx->ws);
@@ -206,6 +209,7 @@ kr_status kr_ws_reserve(kr_ctx* ctx, size_t bytes) {
 
 kr_status kr_split_reserve(kr_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->split_size) return KR_OK;
+  if (ctx->gm.on) return kr_fail(ctx, KR_ENOTIMPL, "graph sweep: the split-K buffer would grow inside the capture");
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->split_buf) cudaFree(ctx->split_buf);
   ctx->split_buf = nullptr;
@@ -222,6 +226,7 @@ kr_status kr_split_reserve(kr_ctx* ctx, size_t bytes) {
 
 kr_status kr_hbuf_reserve(kr_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->hbuf_size) return KR_OK;
+  if (ctx->gm.on) return kr_fail(ctx, KR_ENOTIMPL, "graph sweep: the pinned read-back buffer would grow inside the capture");
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
   ctx->hbuf = nullptr;

@@ -78,6 +78,27 @@ struct kr_ctx {
   int64_t tc_launches = 0;
   int tc_attr = 0;  // dynamic shared memory the tensor-core kernel has been allowed
   int64_t graphs = 0;  // CUDA graphs this context launched (device loops, sweeps)
+  // Set while tucker_als_sweep captures sweeps into one graph: the steps read nothing back
+  // on the host, keep their checks on the device (gm.err bits, gm.status slots, gm.w slots),
+  // and put each Richardson loop into the capture as a conditional WHILE node.
+  struct GraphMode {
+    bool on = false;
+    void* mem = nullptr;     // one device allocation holding the arrays below (owned)
+    int* err = nullptr;      // OR of KR_GM_* bits
+    int* status = nullptr;   // {StepCheck, iteration count} per loop, in capture order
+    double* w = nullptr;     // one Woodbury penalty per factor step, in capture order
+    double* obj = nullptr;   // the last core step's sampled {residual, ||x||^2}
+    void* last = nullptr;    // the last core step's Richardson state
+    unsigned long long* distinct = nullptr;  // the last sketch's distinct rows
+    int nstatus = 0, nw = 0, slot = 0, wslot = 0;
+    std::vector<int64_t> body_launches;  // kernels per iteration of each captured loop
+    std::vector<int> base_slot;          // loop whose count a resumed loop continues, or -1
+    std::vector<int> owner;              // each loop's step: factor mode n, or -1 for a core step
+    int cur_owner = -1;                  // the step being captured
+    int64_t last_s = 0;                  // the last core step's sample count
+    int last_prec = 0;                   // and the precision of its first phase
+  } gm;
+  cudaStream_t side_stream = nullptr;  // captures a loop body inside an ongoing capture (owned)
   // worker contexts of kron_ridge_batched, each with its own stream and workspace (owned)
   std::vector<kr_ctx*> workers;
   std::vector<cudaStream_t> worker_streams;
@@ -421,6 +442,7 @@ struct SolveCfg {
   int stop_rule = 0;     // 1: the (1+eps)-aware rule (kr_opts.stop_rule)
   double theta = 0.01;   // its fraction of eps
   int prec = 0;          // kr_opts.precision: slab-pass contractions of the first phase
+  bool pc64_always = false;  // the ridge preconditioner in FP64 whatever the factors' conditioning
 };
 
 enum StepCheck { STEP_CONTINUE, STEP_CONVERGED, STEP_FLOOR, STEP_DIVERGED, STEP_NONFINITE, STEP_MAXITER, STEP_EPS };
@@ -431,6 +453,26 @@ enum StepCheck { STEP_CONTINUE, STEP_CONVERGED, STEP_FLOOR, STEP_DIVERGED, STEP_
 // continues with its host loop).
 bool kr_graph_while(kr_ctx* ctx, const std::function<kr_status(cudaGraphConditionalHandle, int)>& body,
                     int64_t* per_step);
+// Inside an ongoing capture of ctx->stream: a condition handle of the capture's graph whose
+// value is dflt at every launch (1: the loop runs at least once; 0: a kernel captured before
+// the loop decides), and a conditional WHILE node after the captured work with body(hnd, 1)
+// captured into it (its last kernel sets the condition). *per_body = kernels per iteration.
+kr_status kr_gm_handle(kr_ctx* ctx, unsigned dflt, cudaGraphConditionalHandle* hnd);
+kr_status kr_capture_while(kr_ctx* ctx, cudaGraphConditionalHandle hnd,
+                           const std::function<kr_status(cudaGraphConditionalHandle, int)>& body, int64_t* per_body);
+// Graph-mode bookkeeping (kr_ctx::gm): bits of the device error word; a kernel that ORs a
+// table build's pivot flags (or a capacitance flag) into it; one that stores a loop's final
+// {status, iteration count} in the next slot (*slot_out = its index; base_slot: the loop a
+// resumed loop continues, whose count is subtracted when launches are tallied).
+enum { KR_GM_FACTOR_RANK = 1, KR_GM_CORE_UNFOLD_RANK = 2, KR_GM_CAPACITANCE = 4 };
+kr_status kr_gm_flags(kr_ctx* ctx, const int* flags, int n, int bit);
+// After a captured sweep ran (stream synchronised): the last core step's report fields
+// (converged, rel_update, obj_sampled, distinct, s, precision_used) from the device copies.
+kr_status kr_gm_core_report(kr_ctx* ctx, double lambda, kr_report* rep);
+// Bytes of the device copy of a core step's Richardson state.
+size_t kr_gm_state_bytes();
+kr_status kr_gm_status(kr_ctx* ctx, const int* status, const int* it, int64_t per_body, int base_slot,
+                       int* slot_out);
 // A fused batch's problems each add their device loop (body captured on their own stream) as
 // one more conditional WHILE node of a shared graph; the last active problem to arrive
 // launches the graph on the batch's stream, after every member's earlier work, and waits for

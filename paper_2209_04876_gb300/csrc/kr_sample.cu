@@ -769,6 +769,7 @@ static bool kr_group_dense(const kr_ctx* ctx, int64_t s, int64_t keyspace) {
 static kr_status kr_dcnt_reserve(kr_ctx* ctx, int64_t keys) {
   const size_t bytes = (size_t)keys * sizeof(uint32_t);
   if (bytes > ctx->dcnt_size) {
+    if (ctx->gm.on) return kr_fail(ctx, KR_ENOTIMPL, "graph sweep: the key counters would grow inside the capture");
     KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (ctx->dcnt) cudaFree(ctx->dcnt);
     ctx->dcnt = nullptr;
@@ -943,6 +944,12 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   }
   KR_CUDA(ctx, cudaMemcpyAsync(sk->invpT, t.invp[N - 1], sizeof(float) * IT, cudaMemcpyDeviceToDevice, ctx->stream));
   KR_TRY(kr_hbuf_reserve(ctx, 4096));
+  if (ctx->gm.on) {  // a captured sweep: the count stays on the device for the sweep's report
+    KR_CUDA(ctx, cudaMemcpyAsync(ctx->gm.distinct, dsum, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+    sk->distinct = -1;
+    return KR_OK;
+  }
   if (defer_distinct) {  // read by the caller after its next synchronisation
     KR_CUDA(ctx, cudaMemcpyAsync((char*)ctx->hbuf + KR_HBUF_DISTINCT, dsum, sizeof(unsigned long long),
                                  cudaMemcpyDeviceToHost, ctx->stream));

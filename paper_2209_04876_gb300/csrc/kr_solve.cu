@@ -15,6 +15,8 @@
 #include <atomic>
 #include <thread>
 
+#include <vector>
+
 #include "kr_internal.cuh"
 
 namespace {
@@ -425,6 +427,25 @@ __global__ void k_rich_resume(RichState* st) {
   st->prev_h0 = st->min_h0 = st->min_q = INFINITY;
   st->grow = st->since_min = 0;
   st->status = STEP_CONTINUE;
+}
+
+// The refinement's entry inside a captured sweep: unless the first phase stopped at max_iter
+// (which bounds both phases), the state is reset as k_rich_resume does and the loop runs.
+__global__ void k_rich_resume_dev(RichState* st, cudaGraphConditionalHandle hnd) {
+  const bool go = st->status != STEP_MAXITER;
+  if (go) {
+    st->prev_h0 = st->min_h0 = st->min_q = INFINITY;
+    st->grow = st->since_min = 0;
+    st->status = STEP_CONTINUE;
+  }
+  cudaGraphSetConditional(hnd, go ? 1u : 0u);
+}
+
+// x = 0 when *status == which (a non-finite first phase restarts the refinement from 0).
+__global__ void k_zero_if_status(float* __restrict__ x, int64_t n, const int* __restrict__ status, int which) {
+  if (*status != which) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = 0.f;
 }
 
 __global__ void k_rich_init(RichState* st) {
@@ -1471,6 +1492,106 @@ bool kr_graph_while(kr_ctx* ctx, const std::function<kr_status(cudaGraphConditio
   return ok;
 }
 
+kr_status kr_gm_handle(kr_ctx* ctx, unsigned dflt, cudaGraphConditionalHandle* hnd) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t graph = nullptr;
+  KR_CUDA(ctx, cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &graph, nullptr, nullptr, nullptr));
+  if (cs != cudaStreamCaptureStatusActive) return kr_fail(ctx, KR_EINVAL, "graph sweep: the stream is not capturing");
+  KR_CUDA(ctx, cudaGraphConditionalHandleCreate(hnd, graph, dflt, cudaGraphCondAssignDefault));
+  return KR_OK;
+}
+
+kr_status kr_capture_while(kr_ctx* ctx, cudaGraphConditionalHandle hnd,
+                           const std::function<kr_status(cudaGraphConditionalHandle, int)>& body, int64_t* per_body) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t ndeps = 0;
+  KR_CUDA(ctx, cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &graph, &deps, &edges, &ndeps));
+  if (cs != cudaStreamCaptureStatusActive) return kr_fail(ctx, KR_EINVAL, "graph sweep: the stream is not capturing");
+  if (!ctx->side_stream) return kr_fail(ctx, KR_EINVAL, "graph sweep: no side stream for the loop bodies");
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hnd;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  // full dependencies on everything captured so far on the stream
+  std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+  KR_CUDA(ctx, cudaGraphAddNode(&node, graph, dv.empty() ? nullptr : dv.data(), nullptr, dv.size(), &cp));
+  KR_CUDA(ctx, cudaStreamUpdateCaptureDependencies(ctx->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  const cudaStream_t main = ctx->stream;
+  KR_CUDA(ctx, cudaStreamBeginCaptureToGraph(ctx->side_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeRelaxed));
+  const int64_t l0 = ctx->launches;
+  ctx->stream = ctx->side_stream;
+  const kr_status st = body(hnd, 1);
+  ctx->stream = main;
+  *per_body = ctx->launches - l0;
+  ctx->launches = l0;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(ctx->side_stream, &captured);
+  if (st != KR_OK) return st;
+  if (ce != cudaSuccess) return kr_fail_cuda(ctx, ce, "graph sweep: end of a loop body's capture", __FILE__, __LINE__);
+  return KR_OK;
+}
+
+namespace {
+__global__ void k_gm_flags(const int* __restrict__ f, int n, int bit, int* __restrict__ err) {
+  if (threadIdx.x == 0) {
+    int v = 0;
+    for (int i = 0; i < n; ++i) v |= f[i];
+    if (v) atomicOr(err, bit);
+  }
+}
+__global__ void k_gm_store(const int* __restrict__ status, const int* __restrict__ it, int* __restrict__ dst) {
+  if (threadIdx.x == 0) {
+    dst[0] = *status;
+    dst[1] = *it;
+  }
+}
+}  // namespace
+
+kr_status kr_gm_flags(kr_ctx* ctx, const int* flags, int n, int bit) {
+  KR_LAUNCH(ctx, k_gm_flags, 1, 32, 0, flags, n, bit, ctx->gm.err);
+  return KR_OK;
+}
+
+kr_status kr_gm_status(kr_ctx* ctx, const int* status, const int* it, int64_t per_body, int base_slot,
+                       int* slot_out) {
+  if (ctx->gm.slot >= ctx->gm.nstatus) return kr_fail(ctx, KR_EINVAL, "graph sweep: more loops than status slots");
+  KR_LAUNCH(ctx, k_gm_store, 1, 32, 0, status, it, ctx->gm.status + 2 * ctx->gm.slot);
+  ctx->gm.body_launches.push_back(per_body);
+  ctx->gm.base_slot.push_back(base_slot);
+  ctx->gm.owner.push_back(ctx->gm.cur_owner);
+  if (slot_out) *slot_out = ctx->gm.slot;
+  ctx->gm.slot++;
+  return KR_OK;
+}
+
+size_t kr_gm_state_bytes() { return sizeof(RichState); }
+
+kr_status kr_gm_core_report(kr_ctx* ctx, double lambda, kr_report* rep) {
+  KR_TRY(kr_hbuf_reserve(ctx, 4096));
+  char* h = static_cast<char*>(ctx->hbuf);
+  RichState* hs = reinterpret_cast<RichState*>(h);
+  double* obj = reinterpret_cast<double*>(h + 1024);
+  unsigned long long* dist = reinterpret_cast<unsigned long long*>(h + 1040);
+  KR_CUDA(ctx, cudaMemcpyAsync(hs, ctx->gm.last, sizeof(RichState), cudaMemcpyDeviceToHost, ctx->stream));
+  KR_CUDA(ctx, cudaMemcpyAsync(obj, ctx->gm.obj, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  KR_CUDA(ctx, cudaMemcpyAsync(dist, ctx->gm.distinct, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+  KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  rep->iters = hs->it;
+  rep->converged = hs->status == STEP_CONVERGED ? 1 : hs->status == STEP_FLOOR ? 2 : hs->status == STEP_EPS ? 3 : 0;
+  rep->rel_update = hs->h[1] > 0.0 ? sqrt(hs->h[0]) / sqrt(hs->h[1]) : (hs->h[0] == 0.0 ? 0.0 : INFINITY);
+  rep->obj_sampled = obj[0] + lambda * obj[1];
+  rep->distinct = (int64_t)*dist;
+  rep->s = ctx->gm.last_s;
+  rep->precision_used = ctx->gm.last_prec;
+  return KR_OK;
+}
+
 // Core Alg. 2 solve on device-resident inputs. Timings go to rep->t_ms if rep != NULL.
 kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const SolveCfg& cfg, uint64_t seed,
                           uint64_t call_id, float* x_out, kr_report* rep) {
@@ -1492,11 +1613,16 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   static const uint32_t kTuneEt[5] = {2048, 4096, 8192, 16384, 32768};
   int64_t tkey[6] = {N, m.I[N > 1 ? N - 2 : 0], m.R[N > 1 ? N - 2 : 0], m.I[N - 1], RT, 0};
   for (int64_t v = cfg.s; v > 1; v >>= 1) ++tkey[5];
+  // inside a captured sweep (ctx->gm.on) nothing is read back, timed or tuned: checks go to
+  // the device error word, each loop is a conditional node, and an untuned class keeps the
+  // context's tile budget
+  const bool gm = ctx->gm.on;
   uint32_t tuned_et = (slab && ctx->autotune) ? kr_tune_lookup(ctx, tkey) : 0;
-  const bool tune_now = slab && ctx->autotune && tuned_et == 0;
+  const bool tune_now = slab && ctx->autotune && tuned_et == 0 && !gm;
+  const bool use_tuned = ctx->autotune && (tuned_et != 0 || tune_now);
   if (slab) {
     const uint32_t et_keep = ctx->slab_tile_entries;
-    if (ctx->autotune) ctx->slab_tile_entries = tune_now ? kTuneEt[0] : tuned_et;
+    if (use_tuned) ctx->slab_tile_entries = tune_now ? kTuneEt[0] : tuned_et;
     kr_tiles_setup(ctx, m, &sk, &tl);
     ctx->slab_tile_entries = et_keep;
     // folded first preconditioner mode with the eps-aware rule: the reduction also returns g
@@ -1541,10 +1667,15 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   KR_TRY(kr_hbuf_reserve(ctx, 4096));
   Carve cv(ctx->ws, ctx->ws_size);
   cudaEvent_t* ev = ctx->ev;
-  KR_CUDA(ctx, cudaEventRecord(ev[0], ctx->stream));
+  auto mark = [&](int i) -> kr_status {
+    if (!gm) KR_CUDA(ctx, cudaEventRecord(ev[i], ctx->stream));
+    return KR_OK;
+  };
+  KR_TRY(mark(0));
   FactorTables t;
-  KR_TRY(kr_tables_build(ctx, m, cfg.lambda > 0.0, cv, t, true));
-  KR_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
+  KR_TRY(kr_tables_build(ctx, m, cfg.lambda > 0.0, cv, t, !gm));
+  if (gm) KR_TRY(kr_gm_flags(ctx, t.flags, N, KR_GM_FACTOR_RANK));
+  KR_TRY(mark(1));
   kr_sketch_layout(&sk, cv);
   IterBufs bf;
   if (slab) {
@@ -1569,13 +1700,17 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   double* pc64 = nullptr;
   if (cfg.lambda > 0.0) {
     double* buf = cv.take<double>(2 * (size_t)R);
-    double hi = 1.0, lo = 1.0;
-    for (int n = 0; n < N; ++n) {
-      hi *= t.sig_max[n];
-      lo *= t.sig_min[n];
+    if (cfg.pc64_always) {
+      pc64 = buf;
+    } else {
+      double hi = 1.0, lo = 1.0;
+      for (int n = 0; n < N; ++n) {
+        hi *= t.sig_max[n];
+        lo *= t.sig_min[n];
+      }
+      const double cond = (hi + cfg.lambda) / (lo + cfg.lambda);
+      if (ldexp(sqrt(cond), -24) > 1e-3) pc64 = buf;
     }
-    const double cond = (hi + cfg.lambda) / (lo + cfg.lambda);
-    if (ldexp(sqrt(cond), -24) > 1e-3) pc64 = buf;
   }
   if (fold0) {  // B1 = A(1) G_1^-1 (G_1^-1 symmetric: row i of B1 = G_1^-1 applied to row i of A(1))
     bf.B1 = cv.take<float>((size_t)m.I[0] * m.R[0]);
@@ -1619,11 +1754,11 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     kr_tune_record(ctx, tkey, tuned_et, ms, 5);
   }
   if (slab) {
-    if (ctx->autotune) tl.et = tuned_et;
+    if (use_tuned) tl.et = tuned_et;
     KR_TRY(kr_tiles_build(ctx, &sk, &tl, cv));
   }
-  KR_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
-  KR_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
+  KR_TRY(mark(2));
+  KR_TRY(mark(3));
   double* h = (double*)ctx->hbuf;
   const int ublk = grid_cap(ctx, R, 256, 4);
   int it = 0, converged = 0;
@@ -1697,6 +1832,37 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     }
     return KR_OK;
   };
+  if (gm) {
+    // the loop (and the FP32 refinement, entered on the device when the first phase did
+    // not stop at max_iter) as conditional nodes of the sweep's graph
+    cudaGraphConditionalHandle h1 = 0;
+    int64_t pb = 0;
+    int slot1 = -1;
+    KR_TRY(kr_gm_handle(ctx, 1, &h1));
+    KR_TRY(kr_capture_while(ctx, h1, one_step, &pb));
+    KR_TRY(kr_gm_status(ctx, &bf.rich->status, &bf.rich->it, pb, -1, &slot1));
+    if (prec1 > 0) {
+      cudaGraphConditionalHandle h2 = 0;
+      KR_TRY(kr_gm_handle(ctx, 0, &h2));
+      KR_LAUNCH(ctx, k_zero_if_status, grid_cap(ctx, R, 256, 4), 256, 0, bf.x, R, &bf.rich->status,
+                (int)STEP_NONFINITE);
+      KR_LAUNCH(ctx, k_rich_resume_dev, 1, 1, 0, bf.rich, h2);
+      cur_prec = 0;
+      cur_tol = cfg.tol;
+      KR_TRY(kr_capture_while(ctx, h2, one_step, &pb));
+      KR_TRY(kr_gm_status(ctx, &bf.rich->status, &bf.rich->it, pb, slot1, nullptr));
+    }
+    // the sampled objective at the returned x and the final state, for the sweep's report
+    KR_TRY(sampled_pass(ctx, m, &sk, bf, nblk, false, &op, &on));
+    KR_LAUNCH(ctx, k_reduce_partials, 1, 256, 0, op, on, 1, 0, bf.red);
+    KR_LAUNCH(ctx, k_dot_self, ublk, 256, 0, bf.x, R, bf.part + 1024);
+    KR_LAUNCH(ctx, k_reduce_partials, 1, 256, 0, bf.part + 1024, ublk, 1, 0, bf.red + 1);
+    KR_CUDA(ctx, cudaMemcpyAsync(ctx->gm.obj, bf.red, 2 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    KR_CUDA(ctx, cudaMemcpyAsync(ctx->gm.last, bf.rich, sizeof(RichState), cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->gm.last_s = cfg.s;
+    ctx->gm.last_prec = prec1;
+    return KR_OK;
+  }
   KR_TRY(run_loop());
   int iters_reduced = 0;
   if (prec1 > 0) {

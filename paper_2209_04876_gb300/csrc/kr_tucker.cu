@@ -23,6 +23,7 @@
 // capacitance still in FP64). The Richardson iterations after the first run as one CUDA
 // graph with the stopping rule on the device.
 #include <math.h>
+#include <stdio.h>
 
 #include "kr_internal.cuh"
 
@@ -92,10 +93,11 @@ __global__ void k_gp64(const float* __restrict__ Gt, const double* __restrict__ 
 constexpr int PEN_MAXRN = KR_MAX_RANK;
 __global__ void __launch_bounds__(256) k_penalty_rows(const float* __restrict__ Z, const float* __restrict__ Gn,
                                                       const double* __restrict__ gp64, const float* __restrict__ gsk,
-                                                      int Rn, int Rne, double lambda, double w,
+                                                      int Rn, int Rne, double lambda, double w_arg,
                                                       float* __restrict__ grad, float* __restrict__ out_a,
-                                                      double* __restrict__ grad64) {
+                                                      double* __restrict__ grad64, const double* __restrict__ wp) {
   extern __shared__ double zs[];  // Rne
+  const double w = wp ? *wp : w_arg;  // the penalty on the device (graph sweeps) or by value
   __shared__ double tv[PEN_MAXRN], uv[PEN_MAXRN];
   const int64_t row = blockIdx.x;
   const float* z = Z + row * Rne;
@@ -137,8 +139,9 @@ __global__ void __launch_bounds__(256) k_penalty_rows(const float* __restrict__ 
 }
 
 // Vw[a][k] = lambda * Gp[k][a] - w * Gn[a][k]  (R_n x Rne);  GpT[a][k] = Gp[k][a]
-__global__ void k_vw(const float* __restrict__ Gp, const float* __restrict__ Gn, int Rn, int Rne, float lambda, float w,
-                     float* __restrict__ Vw, float* __restrict__ GpT) {
+__global__ void k_vw(const float* __restrict__ Gp, const float* __restrict__ Gn, int Rn, int Rne, float lambda,
+                     float w_arg, float* __restrict__ Vw, float* __restrict__ GpT, const double* __restrict__ wp) {
+  const float w = wp ? (float)*wp : w_arg;
   const int64_t tot = (int64_t)Rn * Rne;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int a = (int)(e / Rne), k = (int)(e % Rne);
@@ -278,12 +281,14 @@ struct WbBase {
   const double* s1;  // R1 eigenvalues (nullptr for R1 = 1)
   const double* s2;  // R2
   double w;
+  const double* wp;  // when set, the penalty is read here (computed on the device) instead of w
 };
 
 // M (R1 x R2, shared memory) <- A^-1 M; T is shared scratch of the same size. Called by
 // every thread of the block (it synchronises).
 __device__ void base_apply_block64(const WbBase& b, double* M, double* T) {
   const int R1 = b.R1, R2 = b.R2, n = R1 * R2;
+  const double bw = b.wp ? *b.wp : b.w;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {  // T = V1^T M
     const int j = e / R2, l = e - j * R2;
     double acc = 0.0;
@@ -298,7 +303,7 @@ __device__ void base_apply_block64(const WbBase& b, double* M, double* T) {
     const int j = e / R2, l = e - j * R2;
     double acc = 0.0;
     for (int r = 0; r < R2; ++r) acc = fma(T[j * R2 + r], b.V2[r * R2 + l], acc);
-    const double d = (b.s1 ? b.s1[j] * b.s2[l] : b.s2[l]) + b.w;
+    const double d = (b.s1 ? b.s1[j] * b.s2[l] : b.s2[l]) + bw;
     M[e] = d > 0.0 ? acc / d : 0.0;
   }
   __syncthreads();
@@ -336,7 +341,8 @@ __global__ void __launch_bounds__(256) k_base_cols64(WbBase b, const double* __r
 
 // Vw[a][k] = lambda G+[k][a] - w G_(n)[a][k]  (R_n x Rne, FP64)
 __global__ void k_vw64(const double* __restrict__ gp64, const float* __restrict__ Gn, int Rn, int Rne, double lambda,
-                       double w, double* __restrict__ Vw) {
+                       double w_arg, double* __restrict__ Vw, const double* __restrict__ wp) {
+  const double w = wp ? *wp : w_arg;
   const int64_t tot = (int64_t)Rn * Rne;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int a = (int)(e / Rne), k = (int)(e % Rne);
@@ -379,6 +385,7 @@ struct RowStep {
   const double* AinvU;  // Rn x Rne: A^-1 applied to the columns of G+
   const double* Cinv;   // Rn x Rn
   double lambda, w, alpha;
+  const double* wp;  // when set, the penalty is read here instead of w
 };
 __global__ void __launch_bounds__(256) k_factor_rows(RowStep p, float* __restrict__ Z, const float* __restrict__ gsk,
                                                      double* __restrict__ rowstat) {
@@ -392,6 +399,7 @@ __global__ void __launch_bounds__(256) k_factor_rows(RowStep p, float* __restric
   const int64_t row = blockIdx.x;
   float* z = Z + row * Rne;
   const float* g_sk = gsk + row * Rne;
+  const double pw = p.wp ? *p.wp : p.w;
   for (int k = threadIdx.x; k < Rne; k += blockDim.x) zs[k] = (double)z[k];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -413,12 +421,12 @@ __global__ void __launch_bounds__(256) k_factor_rows(RowStep p, float* __restric
     }
   }
   __syncthreads();
-  for (int a = threadIdx.x; a < Rn; a += blockDim.x) tv[a] = p.lambda * uv[a] - p.w * tv[a];
+  for (int a = threadIdx.x; a < Rn; a += blockDim.x) tv[a] = p.lambda * uv[a] - pw * tv[a];
   __syncthreads();
   for (int k = threadIdx.x; k < Rne; k += blockDim.x) {
     double c = 0.0;
     for (int a = 0; a < Rn; ++a) c = fma(p.gp64[(int64_t)k * Rn + a], tv[a], c);
-    M[k] = p.w * zs[k] + c - (double)g_sk[k];
+    M[k] = pw * zs[k] + c - (double)g_sk[k];
   }
   __syncthreads();
   base_apply_block64(p.b, M, T);  // D = A^-1 g
@@ -576,10 +584,12 @@ struct Diag64 {
   int No;
   int R[KR_MAX_MODES];
   const double* s[KR_MAX_MODES];
+  const double* wp;  // when set, the penalty is read here instead of the w argument
 };
 
 // x[b, r] /= prod_m s_m[r_m] + w over the trailing Rne entries of every batch row b.
-__global__ void k_diag_w64(double* __restrict__ x, int64_t total, int64_t Rne, Diag64 d, double w) {
+__global__ void k_diag_w64(double* __restrict__ x, int64_t total, int64_t Rne, Diag64 d, double w_arg) {
+  const double w = d.wp ? *d.wp : w_arg;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     int64_t rem = i % Rne;
     double prod = 1.0;
@@ -696,7 +706,7 @@ kr_status base_apply(kr_ctx* ctx, const FactorTables& to, int nrow, double w, co
 // Batched FP64 A^-1 = (x)V (S^2 + w)^-1 (x)V^T over the No other modes for `nrow` rows of Rne
 // entries: out = A^-1 in (tmp: nrow * Rne doubles; in aliases neither out nor tmp).
 kr_status base_apply64(kr_ctx* ctx, int No, const int* Ro, double* const* V64, double* const* s64, int nrow, double w,
-                       const double* in, double* out, double* tmp) {
+                       const double* in, double* out, double* tmp, const double* wp = nullptr) {
   int64_t Rne = 1;
   for (int m = 0; m < No; ++m) Rne *= Ro[m];
   const int64_t tot = Rne * nrow;
@@ -716,6 +726,7 @@ kr_status base_apply64(kr_ctx* ctx, int No, const int* Ro, double* const* V64, d
     if (pass == 0) {
       Diag64 dd = {};
       dd.No = No;
+      dd.wp = wp;
       for (int m = 0; m < No; ++m) {
         dd.R[m] = Ro[m];
         dd.s[m] = s64[m];
@@ -724,6 +735,26 @@ kr_status base_apply64(kr_ctx* ctx, int No, const int* Ro, double* const* V64, d
     }
   }
   return KR_OK;
+}
+
+// The other modes' FP32 eigenvalue arrays sigma^2 (for the penalty w on the device).
+struct SigMax {
+  int n;
+  int R[KR_MAX_MODES];
+  const float* s[KR_MAX_MODES];
+};
+
+// *w = (1 + 12/eps) prod_k max_i s[k][i]: the host formula, in the same order and precision
+// (FP32 maxima from 0, FP64 products), so the graph sweep's w is bit-identical.
+__global__ void k_penalty_w(SigMax sm, double eps, double* __restrict__ w) {
+  if (threadIdx.x != 0) return;
+  double v = 1.0 + 12.0 / eps;
+  for (int k = 0; k < sm.n; ++k) {
+    float mxv = 0.f;
+    for (int i = 0; i < sm.R[k]; ++i) mxv = sm.s[k][i] > mxv ? sm.s[k][i] : mxv;
+    v *= (double)mxv;
+  }
+  *w = v;
 }
 
 struct FactorStep {
@@ -825,9 +856,14 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   }
   KR_TRY(kr_ws_reserve(ctx, nd.off));
   KR_TRY(kr_hbuf_reserve(ctx, 4096));
+  // inside a captured sweep (ctx->gm.on) nothing is read back: rank and capacitance checks
+  // go to the device error word, the penalty w is computed on the device, and the loop is a
+  // conditional node of the sweep's graph
+  const bool gm = ctx->gm.on;
   Carve cv(ctx->ws, ctx->ws_size);
   FactorTables ta;
-  KR_TRY(kr_tables_build(ctx, m, true, cv, ta, true));
+  KR_TRY(kr_tables_build(ctx, m, true, cv, ta, !gm));
+  if (gm) KR_TRY(kr_gm_flags(ctx, ta.flags, N, KR_GM_FACTOR_RANK));
   FactorTables to;  // the other modes' tables
   to.N = No;
   for (int k = 0, j = 0; k < N; ++k) {
@@ -857,9 +893,10 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   mg.A[0] = Gt;
   FactorTables tg;
   {
-    kr_status st = kr_tables_build(ctx, mg, false, cv, tg, true);
+    kr_status st = kr_tables_build(ctx, mg, false, cv, tg, !gm);
     if (st == KR_ERANK) return kr_fail(ctx, KR_ERANK, "factor step %d: the core unfolding G_(n) is rank deficient", n);
     KR_TRY(st);
+    if (gm) KR_TRY(kr_gm_flags(ctx, tg.flags, 1, KR_GM_CORE_UNFOLD_RANK));
   }
   KR_TRY(kr_smem_attr(ctx, k_penalty_rows, sizeof(double) * Rne));
   // G+ = G_(n)^T (G_(n) G_(n)^T)^-1 in FP64 (and FP32 for the preconditioner)
@@ -868,21 +905,33 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   KR_LAUNCH(ctx, k_hinv, 1, 256, 0, tg.linv[0], Rn, hinv);
   KR_LAUNCH(ctx, k_gp64, grid_of(ctx, Rtot), 256, 0, Gt, hinv, Rn, Rne, gp64, Gp);
   // w = (1 + 12/eps) prod_{m != n} sigma_max^2 (eigenvalues of the other Gram matrices)
-  {
+  double w = 1.0 + 12.0 / cfg.eps;
+  const double* wdev = nullptr;
+  if (gm) {
+    if (ctx->gm.wslot >= ctx->gm.nw) return kr_fail(ctx, KR_EINVAL, "graph sweep: more factor steps than penalty slots");
+    double* wd = ctx->gm.w + ctx->gm.wslot++;
+    SigMax sm = {};
+    sm.n = No;
+    for (int k = 0; k < No; ++k) {
+      sm.s[k] = to.sig2[k];
+      sm.R[k] = to.R[k];
+    }
+    KR_LAUNCH(ctx, k_penalty_w, 1, 32, 0, sm, cfg.eps, wd);
+    wdev = wd;
+  } else {
     float* hs = (float*)ctx->hbuf;
     for (int k = 0; k < No; ++k)
       KR_CUDA(ctx, cudaMemcpyAsync(hs + 64 * k, to.sig2[k], sizeof(float) * to.R[k], cudaMemcpyDeviceToHost, ctx->stream));
     KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  }
-  double w = 1.0 + 12.0 / cfg.eps;
-  for (int k = 0; k < No; ++k) {
-    float mxv = 0.f;
-    const float* hs = (const float*)ctx->hbuf + 64 * k;
-    for (int i = 0; i < to.R[k]; ++i) mxv = hs[i] > mxv ? hs[i] : mxv;
-    w *= (double)mxv;
+    for (int k = 0; k < No; ++k) {
+      float mxv = 0.f;
+      const float* hsk = (const float*)ctx->hbuf + 64 * k;
+      for (int i = 0; i < to.R[k]; ++i) mxv = hsk[i] > mxv ? hsk[i] : mxv;
+      w *= (double)mxv;
+    }
   }
   const float wf = (float)w, lf = (float)cfg.lambda;
-  KR_LAUNCH(ctx, k_vw, grid_of(ctx, Rtot), 256, 0, Gp, Gn, Rn, (int)Rne, lf, wf, Vw, GpT);
+  KR_LAUNCH(ctx, k_vw, grid_of(ctx, Rtot), 256, 0, Gp, Gn, Rn, (int)Rne, lf, wf, Vw, GpT, wdev);
   // iteration buffers
   kr_sketch_layout(&sk, cv);
   float* Z = cv.take<float>(ZL);
@@ -941,6 +990,7 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     rs.b.s1 = No == 2 ? s64[0] : nullptr;
     rs.b.s2 = s64[No - 1];
     rs.b.w = w;
+    rs.b.wp = wdev;
     rs.Rn = Rn;
     rs.Rne = (int)Rne;
     rs.Gn = Gn;
@@ -950,26 +1000,29 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     rs.Cinv = Cinv64;
     rs.lambda = cfg.lambda;
     rs.w = w;
+    rs.wp = wdev;
     rs.alpha = cfg.alpha;
-    KR_LAUNCH(ctx, k_vw64, grid_of(ctx, Rtot), 256, 0, gp64, Gn, Rn, (int)Rne, cfg.lambda, w, Vw64);
+    KR_LAUNCH(ctx, k_vw64, grid_of(ctx, Rtot), 256, 0, gp64, Gn, Rn, (int)Rne, cfg.lambda, w, Vw64, wdev);
     KR_TRY(kr_smem_attr(ctx, k_base_cols64, (size_t)16 * Rne));
     KR_LAUNCH(ctx, k_base_cols64, Rn, 256, (size_t)16 * Rne, rs.b, gp64, Rn, (int)Rne, AinvU64);
     KR_LAUNCH(ctx, k_capacitance64, Rn * Rn, 256, 0, Vw64, AinvU64, Rn, (int)Rne, C);
     KR_LAUNCH(ctx, k_gauss_jordan, 1, 256, gj_smem, C, Rn, Cinv, flag, Cinv64);
+    if (gm) KR_TRY(kr_gm_flags(ctx, flag, 1, KR_GM_CAPACITANCE));
     KR_TRY(kr_smem_attr(ctx, k_factor_rows, (size_t)24 * Rne));
   } else {
     // FP64 chain: A^-1 U (A^-1 applied to each column of G+, batched), V, the capacitance
     // and its inverse
     KR_LAUNCH(ctx, k_transpose64, grid_of(ctx, Rtot), 256, 0, (const double*)gp64, (int)Rne, Rn, GpT64);
-    KR_TRY(base_apply64(ctx, No, Ro, V64, s64, Rn, w, GpT64, AinvU64, T64));
-    KR_LAUNCH(ctx, k_vw64, grid_of(ctx, Rtot), 256, 0, gp64, Gn, Rn, (int)Rne, cfg.lambda, w, Vw64);
+    KR_TRY(base_apply64(ctx, No, Ro, V64, s64, Rn, w, GpT64, AinvU64, T64, wdev));
+    KR_LAUNCH(ctx, k_vw64, grid_of(ctx, Rtot), 256, 0, gp64, Gn, Rn, (int)Rne, cfg.lambda, w, Vw64, wdev);
     KR_LAUNCH(ctx, k_capacitance64, Rn * Rn, 256, 0, Vw64, AinvU64, Rn, (int)Rne, C);
     KR_LAUNCH(ctx, k_gauss_jordan, 1, 256, gj_smem, C, Rn, Cinv, flag, Cinv64);
+    if (gm) KR_TRY(kr_gm_flags(ctx, flag, 1, KR_GM_CAPACITANCE));
   }
   // batched sketch: row i of X_(n), fresh draws per row (counter row = i)
   {
     Carve sc = cv;
-    KR_TRY(kr_sketch_fill(ctx, mo, to, X, seed, call_id, 0, &sk, sc));
+    KR_TRY(kr_sketch_fill(ctx, mo, to, X, seed, call_id, 0, &sk, sc, gm));
   }
   if (slab) KR_TRY(kr_tiles_build(ctx, &sk, &tl, cv));
   KR_CUDA(ctx, cudaMemsetAsync(Z, 0, sizeof(float) * ZL, ctx->stream));
@@ -1008,9 +1061,9 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     } else {
       // grad = w z + G+ (lambda (G+)^T z - w G z) - Gb  (FP64, one block per row)
       KR_LAUNCH(ctx, k_penalty_rows, In, 256, sizeof(double) * Rne, Z, Gn, gp64, Gb, Rn, (int)Rne, cfg.lambda, w,
-                (float*)nullptr, (float*)nullptr, G64);
+                (float*)nullptr, (float*)nullptr, G64, wdev);
       // d = M^-1 grad (Woodbury, FP64), z <- z - alpha d
-      KR_TRY(base_apply64(ctx, No, Ro, V64, s64, In, w, G64, D64, T64));
+      KR_TRY(base_apply64(ctx, No, Ro, V64, s64, In, w, G64, D64, T64, wdev));
       KR_LAUNCH(ctx, k_wb_rows64, In, 256, 0, (const double*)D64, (const double*)Vw64, (const double*)Cinv64,
                 (const double*)AinvU64, Rn, (int)Rne, Z, (float)cfg.alpha, rowstat);
     }
@@ -1023,6 +1076,18 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return KR_OK;
   };
+  if (gm) {
+    // every iteration inside the WHILE node (it runs at least once, as the host loop does),
+    // then the new factor rows a_i = (G+)^T z_i
+    cudaGraphConditionalHandle h = 0;
+    int64_t pb = 0;
+    KR_TRY(kr_gm_handle(ctx, 1, &h));
+    KR_TRY(kr_capture_while(ctx, h, one_iter, &pb));
+    KR_TRY(kr_gm_status(ctx, &dloop->status, &dloop->it, pb, -1, nullptr));
+    KR_LAUNCH(ctx, k_penalty_rows, In, 256, sizeof(double) * Rne, Z, Gn, gp64, Gb, Rn, (int)Rne, cfg.lambda, w, Gr,
+              An_out, (double*)nullptr, wdev);
+    return KR_OK;
+  }
   // The first iteration runs from the host (with the capacitance check); iterations 2..
   // as one graph (KR_OPT_DEVICE_LOOP) or from the host.
   KR_TRY(one_iter(0, 0));
@@ -1051,7 +1116,7 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     st = kr_fail(ctx, KR_EDIVERGED, "factor step %d: Richardson step grew 3 times past 16x its minimum", n);
   // a_i = (G+)^T z_i  (the new factor rows, FP64 accumulation)
   KR_LAUNCH(ctx, k_penalty_rows, In, 256, sizeof(double) * Rne, Z, Gn, gp64, Gb, Rn, (int)Rne, cfg.lambda, w, Gr,
-            An_out, (double*)nullptr);
+            An_out, (double*)nullptr, wdev);
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (rep) {
     rep->iters = it;
@@ -1117,6 +1182,156 @@ extern "C" kr_status tucker_factor_update(kr_ctx* ctx, int32_t N, const int64_t*
   return kr_factor_step(ctx, m, X, G, n, cfg, opts->seed, opts->call_id, A[n], report);
 }
 
+namespace {
+
+// Sweeps k0..k1-1 of the sampled TuckerALS captured into ONE CUDA graph (ctx->gm.on while
+// capturing): the factor steps' and core steps' Richardson loops become conditional WHILE
+// nodes, their checks device words. *ran is false when the graph could not be built or
+// launched (nothing ran; ctx->err says why and the caller continues from the host).
+kr_status graph_sweeps(kr_ctx* ctx, const Modes& m, const float* X, float* G, const kr_opts* opts, int k0, int k1,
+                       const std::function<kr_status(int, int)>& step, kr_report* r, int* total_iters, bool* ran) {
+  *ran = false;
+  const int N = m.N;
+  const int nloops = (k1 - k0) * (N + 2);  // a core step's loop and its FP32 refinement
+  const int nw = (k1 - k0) * N;
+  const size_t off_status = 16, off_w = off_status + 8 * (size_t)nloops, off_obj = off_w + 8 * (size_t)nw;
+  const size_t off_last = off_obj + 16, off_dist = off_last + ((kr_gm_state_bytes() + 15) / 16) * 16;
+  const size_t bytes = off_dist + 16;
+  KR_TRY(kr_hbuf_reserve(ctx, 4096 + 8 * (size_t)nloops));
+  if (!ctx->side_stream) KR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking));
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->err = "tucker_als_sweep: sweeps 2.. ran from the host (no memory for the graph's state)";
+    return KR_OK;
+  }
+  char* b = static_cast<char*>(mem);
+  kr_ctx::GraphMode& g = ctx->gm;
+  g.mem = mem;
+  g.err = reinterpret_cast<int*>(b);
+  g.status = reinterpret_cast<int*>(b + off_status);
+  g.w = reinterpret_cast<double*>(b + off_w);
+  g.obj = reinterpret_cast<double*>(b + off_obj);
+  g.last = b + off_last;
+  g.distinct = reinterpret_cast<unsigned long long*>(b + off_dist);
+  g.nstatus = nloops;
+  g.nw = nw;
+  g.slot = g.wslot = 0;
+  g.body_launches.clear();
+  g.base_slot.clear();
+  g.owner.clear();
+  auto release = [&]() {
+    cudaFree(g.mem);
+    g = kr_ctx::GraphMode();
+  };
+  {
+    const cudaError_t e = cudaMemsetAsync(mem, 0, bytes, ctx->stream);
+    if (e != cudaSuccess) {
+      release();
+      return kr_fail_cuda(ctx, e, "graph sweep: state reset", __FILE__, __LINE__);
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const int64_t l0 = ctx->launches;
+  std::string why;
+  cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) why = std::string("begin capture: ") + cudaGetErrorString(e);
+  if (why.empty()) {
+    g.on = true;
+    kr_status cs = KR_OK;
+    for (int k = k0; k < k1 && cs == KR_OK; ++k)
+      for (int n = 0; n <= N && cs == KR_OK; ++n) {
+        g.cur_owner = n < N ? n : -1;
+        cs = step(k, n);
+      }
+    g.on = false;
+    if (cs != KR_OK) why = "capture: " + ctx->err;
+    e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (e != cudaSuccess && why.empty()) why = std::string("end capture: ") + cudaGetErrorString(e);
+  }
+  if (why.empty() && (e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
+    why = std::string("instantiate: ") + cudaGetErrorString(e);
+  if (why.empty() && (e = cudaGraphLaunch(exec, ctx->stream)) != cudaSuccess)
+    why = std::string("launch: ") + cudaGetErrorString(e);
+  if (!why.empty()) {
+    // nothing ran: the captured counter reset did not happen either
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    ctx->launches = l0;
+    ctx->dcnt_clean = false;
+    cudaStreamSynchronize(ctx->stream);
+    release();
+    ctx->err = "tucker_als_sweep: sweeps 2.. ran from the host (" + why + ")";
+    return KR_OK;
+  }
+  *ran = true;
+  ctx->graphs++;
+  e = cudaStreamSynchronize(ctx->stream);
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    release();
+    return kr_fail_cuda(ctx, e, "graph sweep: run", __FILE__, __LINE__);
+  }
+  // the checks: the error word, then every loop's final status (a resumed loop's base is
+  // superseded by it), in capture order
+  int* h = reinterpret_cast<int*>(ctx->hbuf);
+  kr_status st = KR_OK;
+  if (cudaMemcpy(h, mem, off_w, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    release();
+    return kr_fail(ctx, KR_ECUDA, "graph sweep: reading its checks: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  const int err = h[0];
+  const int* stat = h + off_status / sizeof(int);
+  const int nl = g.slot;
+  std::vector<char> superseded((size_t)nl, 0);
+  for (int i = 0; i < nl; ++i)
+    if (g.base_slot[(size_t)i] >= 0) superseded[(size_t)g.base_slot[(size_t)i]] = 1;
+  for (int i = 0; i < nl; ++i) {
+    const int base = g.base_slot[(size_t)i];
+    const int runs = stat[2 * i + 1] - (base >= 0 ? stat[2 * base + 1] : 0);
+    ctx->launches += g.body_launches[(size_t)i] * (runs > 0 ? runs : 0);
+    if (superseded[(size_t)i]) continue;
+    *total_iters += stat[2 * i + 1];
+    const int status = stat[2 * i];
+    const int who = g.owner[(size_t)i];
+    char what[64];
+    if (who >= 0) snprintf(what, sizeof(what), "factor step %d", who);
+    else snprintf(what, sizeof(what), "core step");
+    if (st != KR_OK) continue;
+    if (status == STEP_NONFINITE)
+      st = kr_fail(ctx, KR_ENONFINITE, "tucker_als_sweep (graph): %s: iterate became non-finite", what);
+    else if (status == STEP_DIVERGED)
+      st = kr_fail(ctx, KR_EDIVERGED, "tucker_als_sweep (graph): %s: Richardson step diverged", what);
+  }
+  if (err & KR_GM_FACTOR_RANK)
+    st = kr_fail(ctx, KR_ERANK, "tucker_als_sweep (graph): a factor is numerically rank deficient (Cholesky pivot)");
+  else if (err & KR_GM_CORE_UNFOLD_RANK)
+    st = kr_fail(ctx, KR_ERANK, "tucker_als_sweep (graph): a core unfolding G_(n) is rank deficient");
+  else if (err & KR_GM_CAPACITANCE)
+    st = kr_fail(ctx, KR_ERANK, "tucker_als_sweep (graph): a Woodbury capacitance matrix is singular");
+  if (st == KR_OK) {
+    st = kr_gm_core_report(ctx, opts->lambda, r);
+    // the last core step's reduced-precision phase, when it had one
+    r->iters_reduced = 0;
+    for (int i = nl - 1; i >= 0; --i)
+      if (g.owner[(size_t)i] < 0) {
+        const int base = g.base_slot[(size_t)i];
+        if (base >= 0) r->iters_reduced = stat[2 * base + 1];
+        break;
+      }
+    for (int i = 0; i < 6; ++i) r->t_ms[i] = 0.f;  // phases are not timed inside the graph
+  }
+  (void)X;
+  (void)G;
+  release();
+  return st;
+}
+
+}  // namespace
+
 extern "C" kr_status tucker_als_sweep(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R, const float* X,
                                       float* const A[], float* G, const kr_opts* opts, int32_t sweeps,
                                       kr_report* report) {
@@ -1129,24 +1344,40 @@ extern "C" kr_status tucker_als_sweep(kr_ctx* ctx, int32_t N, const int64_t* I, 
   KR_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
   int total_iters = 0;
   kr_report r = {};
-  for (int k = 0; k < sweeps; ++k) {
-    for (int n = 0; n < N; ++n) {
+  // step n < N of sweep k: the factor update of mode n; n = N: the core step, Alg. 2 with
+  // b = vec X, K = A(1) (x) ... (x) A(N). A step that stops at max_iter does not end the sweep.
+  auto step = [&](int k, int n) -> kr_status {
+    const uint64_t cid = opts->call_id + (uint64_t)k * (N + 1) + n;
+    kr_status st;
+    if (n < N) {
       int64_t Rne = 1;
       for (int j = 0; j < N; ++j)
         if (j != n) Rne *= R[j];
       SolveCfg cfg = cfg_from(opts, Rne);
-      const uint64_t cid = opts->call_id + (uint64_t)k * (N + 1) + n;
-      kr_status st = kr_factor_step(ctx, m, X, G, n, cfg, opts->seed, cid, A[n], &r);
-      total_iters += r.iters;
-      if (st != KR_OK && st != KR_ENOTCONV) return st;
+      st = kr_factor_step(ctx, m, X, G, n, cfg, opts->seed, cid, A[n], &r);
+    } else {
+      SolveCfg cfg = cfg_from(opts, kr_prod_R(m));
+      // inside the graph the factors' spectra are not read back: the ridge preconditioner
+      // runs in FP64 (the choice the host makes for badly conditioned factors)
+      cfg.pc64_always = ctx->gm.on;
+      st = kr_solve_device(ctx, m, X, cfg, opts->seed, cid, G, &r);
     }
-    // core step: Alg. 2 with b = vec X, K = A(1) (x) ... (x) A(N)
-    SolveCfg cfg = cfg_from(opts, kr_prod_R(m));
-    const uint64_t cid = opts->call_id + (uint64_t)k * (N + 1) + N;
-    kr_status st = kr_solve_device(ctx, m, X, cfg, opts->seed, cid, G, &r);
-    total_iters += r.iters;
-    if (st != KR_OK && st != KR_ENOTCONV) return st;
+    if (!ctx->gm.on) total_iters += r.iters;
+    return st == KR_ENOTCONV ? KR_OK : st;
+  };
+  int done = 0;
+  if (sweeps > 0) {
+    for (int n = 0; n <= N; ++n) KR_TRY(step(0, n));
+    done = 1;
   }
+  if (sweeps > 1 && ctx->device_loop && !ctx->timing) {
+    // sweeps 2.. as one CUDA graph (the first sized every buffer and tuned every shape)
+    bool ran = false;
+    KR_TRY(graph_sweeps(ctx, m, X, G, opts, 1, sweeps, step, &r, &total_iters, &ran));
+    if (ran) done = sweeps;
+  }
+  for (int k = done; k < sweeps; ++k)
+    for (int n = 0; n <= N; ++n) KR_TRY(step(k, n));
   KR_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (report) {

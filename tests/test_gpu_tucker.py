@@ -91,6 +91,67 @@ def test_tucker_sweeps_reach_exact_als_quality():
     assert rre_gpu < 2e-4  # 1% relative noise -> ~1e-4 floor
 
 
+GRAPH_CASES = [
+    ([32, 28, 24], [3, 3, 3], 0.0, 0),
+    ([32, 28, 24], [3, 3, 3], 1e-3, 0),
+    ([40, 48, 36], [4, 16, 8], 0.0, 1),
+]
+
+
+@pytest.mark.parametrize("I,R,lam,prec", GRAPH_CASES)
+def test_sampled_sweeps_as_one_graph(I, R, lam, prec):
+    """Sweeps after the first are captured into ONE CUDA graph: every factor step's and core
+    step's Richardson loop is a conditional WHILE node (the BF16 core steps' FP32 refinement
+    a second one, entered on the device), the rank and capacitance checks and the penalty w
+    device words. Against host-driven sweeps (OPT_DEVICE_LOOP 0): bit for bit where the
+    host sweeps are themselves reproducible and the same arithmetic runs (lambda = 0);
+    with lambda > 0 the graph applies the core steps' preconditioner in FP64, so factors,
+    core and RRE agree to FP32 rounding. Exactly one graph more than a one-sweep call."""
+    X, As, G = _state(I, R, seed=13)
+    eps = 0.1
+
+    def run(loop, sweeps):
+        kr.set_option(kr.OPT_DEVICE_LOOP, loop)
+        A_gpu = [dev(A) for A in As]
+        G_gpu = dev(G)
+        g0 = kr.graph_count()
+        rep = kr.tucker_als_sweep(dev(X), A_gpu, G_gpu, lam, eps=eps, sweeps=sweeps, seed=5, call_id=0, tol=1e-7,
+                                  max_iter=300, precision=prec)
+        return [host(A) for A in A_gpu] + [host(G_gpu)], rep, kr.graph_count() - g0
+
+    try:
+        h1, hrep, hg = run(0, 4)
+        h2, _, _ = run(0, 4)
+        _, _, g_one = run(1, 1)
+        gr, grep_, gg = run(1, 4)
+    finally:
+        kr.set_option(kr.OPT_DEVICE_LOOP, 1)
+    assert hg == 0
+    assert gg == g_one + 1, (gg, g_one)
+    reproducible = all(np.array_equal(a, b) for a, b in zip(h1, h2))
+    rre_h = tk.rre(X, h1[-1].reshape(R), h1[:-1])
+    rre_g = tk.rre(X, gr[-1].reshape(R), gr[:-1])
+    dev_max = max(np.abs(a - b).max() / np.abs(a).max() for a, b in zip(h1, gr))
+    print("I=%s R=%s lam %g prec %d: host reproducible %s, graph vs host max rel diff %.2e, RRE %.6e / %.6e, "
+          "iters %d / %d" % (I, R, lam, prec, reproducible, dev_max, rre_h, rre_g, hrep["iters"], grep_["iters"]))
+    assert grep_["precision_used"] == hrep["precision_used"]
+    if prec:
+        assert grep_["precision_used"] == prec and grep_["iters_reduced"] > 0
+    if reproducible and lam == 0.0:
+        for a, b in zip(h1, gr):
+            np.testing.assert_array_equal(a, b)
+        assert grep_["iters"] == hrep["iters"]
+        assert grep_["iters_reduced"] == hrep["iters_reduced"]
+        assert grep_["distinct"] == hrep["distinct"] and grep_["s"] == hrep["s"]
+        assert grep_["obj_sampled"] == hrep["obj_sampled"]
+    else:
+        assert dev_max <= 1e-3
+        assert abs(rre_g - rre_h) <= 1e-4 * rre_h
+    he = []
+    tk.tucker_als(X, As, G, lam, 4, sampled=False, history=he)
+    assert rre_g <= (1 + 2 * eps) * he[-1]
+
+
 def test_tucker_core_step_is_alg2_on_vec_x():
     """The core step of a sweep equals kron_ridge on vec(X) with the updated factors."""
     I, R = [20, 18, 16], [2, 3, 2]
