@@ -310,6 +310,16 @@ def run_tucker(name):
         rre_s.append(kr.tucker_rre(X, As, G))
     out["sampled"] = dict(ms_per_sweep=1e3 * t / w["sweeps"], rre=rre_s, stop_rule="(1+eps)-aware")
     out["rre_ratio_last"] = rre_s[-1] / rre_e[-1]
+    # the same sweeps (same Philox streams) in one call: sweeps 2.. run as one CUDA graph
+    As, G = start()
+    torch.cuda.synchronize()
+    g0 = kr.graph_count()
+    t0 = time.perf_counter()
+    kr.tucker_als_sweep(X, As, G, w["lam"], sweeps=w["sweeps"], call_id=100, **opts)
+    torch.cuda.synchronize()
+    out["sampled_one_call"] = dict(ms_per_sweep=1e3 * (time.perf_counter() - t0) / w["sweeps"],
+                                   rre_last=kr.tucker_rre(X, As, G), graphs=kr.graph_count() - g0,
+                                   form="sweep 1 from the host, sweeps 2.. as one CUDA graph")
     del X, As, G
     torch.cuda.empty_cache()
     return out

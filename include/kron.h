@@ -414,7 +414,20 @@ KR_API kr_status tucker_factor_update(kr_ctx* ctx, int32_t N, const int64_t* I, 
  * Woodbury preconditioner) and sampled core updates (Alg. 2 with b = vec X).
  * X: prod I floats; A[n]: I[n] x R[n] floats (in/out); G: prod R floats (in/out).
  * Sweep k, step n (0..N-1 factor steps, N core step) draws with call id
- * opts->call_id + k*(N+1) + n; factor row i uses counter row i. */
+ * opts->call_id + k*(N+1) + n; factor row i uses counter row i. A step that stops at
+ * max_iter does not end the sweeps. The first sweep runs from the host; with
+ * KR_OPT_DEVICE_LOOP 1 (the default, and no timing) the sweeps after it are captured into ONE
+ * CUDA graph launched once (kr_graph_count counts it): each step's Richardson loop is a
+ * conditional WHILE node (a reduced-precision core step's FP32 refinement a second one,
+ * entered on the device), the Woodbury weight w is computed on the device in the host's
+ * order, and the rank, pivot and capacitance checks are device flags read after the graph
+ * (KR_ERANK then names the check, not the step; the later steps have run on the failed
+ * state). Inside the graph a core step with lambda > 0 applies its preconditioner in FP64
+ * (the host sweep does so only for badly conditioned factors); otherwise the results are
+ * bit-identical to the host sweeps. If the graph cannot be built (a buffer would have to
+ * grow, the stream is the legacy default stream, ...) nothing of it runs and the sweeps
+ * continue from the host; kr_last_error says why. report: the last core step's report, with
+ * iters the total over all steps and the phase times of graph-run steps 0. */
 KR_API kr_status tucker_als_sweep(kr_ctx* ctx, int32_t N, const int64_t* I, const int32_t* R,
                            const float* X, float* const A[], float* G, const kr_opts* opts,
                            int32_t sweeps, kr_report* report);

@@ -92,14 +92,16 @@ def test_tucker_sweeps_reach_exact_als_quality():
 
 
 GRAPH_CASES = [
-    ([32, 28, 24], [3, 3, 3], 0.0, 0),
-    ([32, 28, 24], [3, 3, 3], 1e-3, 0),
-    ([40, 48, 36], [4, 16, 8], 0.0, 1),
+    ([32, 28, 24], [3, 3, 3], 0.0, 0, 0),
+    ([32, 28, 24], [3, 3, 3], 1e-3, 0, 0),
+    ([40, 48, 36], [4, 16, 8], 0.0, 1, 0),
+    ([40, 48, 36], [4, 16, 8], 0.0, 0, 1),
+    ([20, 18, 16, 14], [2, 3, 2, 3], 0.0, 0, 0),
 ]
 
 
-@pytest.mark.parametrize("I,R,lam,prec", GRAPH_CASES)
-def test_sampled_sweeps_as_one_graph(I, R, lam, prec):
+@pytest.mark.parametrize("I,R,lam,prec,stop", GRAPH_CASES)
+def test_sampled_sweeps_as_one_graph(I, R, lam, prec, stop):
     """Sweeps after the first are captured into ONE CUDA graph: every factor step's and core
     step's Richardson loop is a conditional WHILE node (the BF16 core steps' FP32 refinement
     a second one, entered on the device), the rank and capacitance checks and the penalty w
@@ -116,7 +118,7 @@ def test_sampled_sweeps_as_one_graph(I, R, lam, prec):
         G_gpu = dev(G)
         g0 = kr.graph_count()
         rep = kr.tucker_als_sweep(dev(X), A_gpu, G_gpu, lam, eps=eps, sweeps=sweeps, seed=5, call_id=0, tol=1e-7,
-                                  max_iter=300, precision=prec)
+                                  max_iter=300, precision=prec, stop_rule=stop)
         return [host(A) for A in A_gpu] + [host(G_gpu)], rep, kr.graph_count() - g0
 
     try:
@@ -132,8 +134,8 @@ def test_sampled_sweeps_as_one_graph(I, R, lam, prec):
     rre_h = tk.rre(X, h1[-1].reshape(R), h1[:-1])
     rre_g = tk.rre(X, gr[-1].reshape(R), gr[:-1])
     dev_max = max(np.abs(a - b).max() / np.abs(a).max() for a, b in zip(h1, gr))
-    print("I=%s R=%s lam %g prec %d: host reproducible %s, graph vs host max rel diff %.2e, RRE %.6e / %.6e, "
-          "iters %d / %d" % (I, R, lam, prec, reproducible, dev_max, rre_h, rre_g, hrep["iters"], grep_["iters"]))
+    print("I=%s R=%s lam %g prec %d stop %d: host reproducible %s, graph vs host max rel diff %.2e, RRE %.6e / %.6e, "
+          "iters %d / %d" % (I, R, lam, prec, stop, reproducible, dev_max, rre_h, rre_g, hrep["iters"], grep_["iters"]))
     assert grep_["precision_used"] == hrep["precision_used"]
     if prec:
         assert grep_["precision_used"] == prec and grep_["iters_reduced"] > 0
