@@ -382,6 +382,44 @@ KR_API kr_status kron_regress(kr_ctx* ctx, const kr_factors* f, const float* b, 
 KR_API kr_status kron_ridge(kr_ctx* ctx, const kr_factors* f, const float* b, const kr_opts* opts,
                      float* x, kr_report* report);
 
+/* The report of an asynchronous solve, written in DEVICE memory when the solve completes. */
+typedef struct {
+  int32_t status;          /* the solve's kr_status: KR_OK, KR_ENOTCONV (x written), KR_ENONFINITE,
+                              KR_EDIVERGED, or KR_ERANK (a factor numerically rank deficient) */
+  int32_t iters;           /* Richardson iterations (both phases of a reduced-precision solve) */
+  int32_t converged;       /* as kr_report.converged */
+  int32_t iters_reduced;   /* as kr_report.iters_reduced */
+  int32_t precision_used;  /* as kr_report.precision_used */
+  int32_t reserved;
+  int64_t s;               /* draws */
+  int64_t distinct;        /* distinct sampled rows */
+  double obj_sampled;      /* as kr_report.obj_sampled (FP64) */
+  double rel_update;       /* as kr_report.rel_update */
+} kr_dev_report;
+
+/* kron_regress / kron_ridge enqueued on the context's stream without waiting: the call
+ * returns once the work is enqueued, and *report (device memory, 56 bytes) holds the
+ * outcome when the stream reaches the end of the solve. Device pointers only (host_io 0;
+ * else KR_EINVAL); argument errors are returned at once, errors of the solve itself in
+ * report->status. If the stream is being captured (cudaStreamBeginCapture, any mode), the
+ * whole solve is captured into the caller's graph, its Richardson loop (and the FP32
+ * refinement of a reduced-precision solve) as conditional WHILE nodes, so one graph launch
+ * replays the whole solve; otherwise the kernels are enqueued and each loop is launched as
+ * a graph of its own, nothing is read back, and the stream is synchronised only when a
+ * buffer of the context has to grow. Inside a capture a buffer cannot grow (KR_ENOTIMPL,
+ * with part of the solve captured: discard the graph): run the same or a larger solve once
+ * before capturing. A captured graph uses the context's workspace, so it stays valid while
+ * the context lives and its workspace does not grow, and instances of it must not run
+ * concurrently with each other or with other calls on the context. The results equal the
+ * synchronous solve's bit for bit, except that with lambda > 0 the preconditioner is always
+ * applied in FP64 (the synchronous solve reads the factors' spectra on the host to decide).
+ * The autotuner (KR_OPT_AUTOTUNE) uses its recorded choice for the shape class, else the
+ * context's tile budget; kr_launch_count counts a loop's kernels once. */
+KR_API kr_status kron_regress_async(kr_ctx* ctx, const kr_factors* f, const float* b, const kr_opts* opts,
+                                    float* x, kr_dev_report* report);
+KR_API kr_status kron_ridge_async(kr_ctx* ctx, const kr_factors* f, const float* b, const kr_opts* opts,
+                                  float* x, kr_dev_report* report);
+
 /* nprob independent ridge problems (host arrays of descriptors and pointers); each
  * uses opts with call_id + problem index. reports: host array of nprob (may be NULL).
  * The problems run concurrently on KR_OPT_BATCH_WORKERS worker contexts (host threads,

@@ -25,7 +25,7 @@ OPT_JL_K, OPT_JL_SEED, OPT_TENSOR_CORES, OPT_BATCH_MODE, OPT_AUTOTUNE = 7, 8, 9,
 EXPORTED = ["kr_create", "kr_destroy", "kr_set_stream", "kr_last_error", "kr_launch_count", "kr_tc_launch_count", "kr_graph_count", "kr_autotune_report", "kr_timing_enable",
             "kr_timing_read", "kr_timing_reset", "kr_set_option", "kron_sample_count", "kron_leverage",
             "kron_sample", "kron_sample_noalloc", "kron_sketch", "kron_sketch_distinct", "kron_sketch_export", "kron_sketch_residual",
-            "kron_sketch_free", "kron_matmul", "kron_precond", "kron_objective", "kron_regress", "kron_ridge",
+            "kron_sketch_free", "kron_matmul", "kron_precond", "kron_objective", "kron_regress", "kron_ridge", "kron_regress_async", "kron_ridge_async",
             "kron_ridge_batched", "tucker_factor_update", "tucker_als_sweep", "tucker_als_exact_sweep", "tucker_rre"]
 
 
@@ -62,6 +62,14 @@ class KrReport(ctypes.Structure):
                     obj_sampled=self.obj_sampled, rel_update=self.rel_update,
                     iters_reduced=self.iters_reduced, precision_used=self.precision_used,
                     t_ms={k: float(v) for k, v in zip(names, self.t_ms)})
+
+
+class KrDevReport(ctypes.Structure):
+    """kr_dev_report: an asynchronous solve's report, written in device memory."""
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("iters_reduced", ctypes.c_int32), ("precision_used", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("s", ctypes.c_int64), ("distinct", ctypes.c_int64), ("obj_sampled", ctypes.c_double),
+                ("rel_update", ctypes.c_double)]
 
 
 _lib = None
@@ -105,6 +113,8 @@ def lib():
             "kron_objective": (i32, [vp, P(KrFactors), vp, vp, dbl, P(dbl)]),
             "kron_regress": (i32, [vp, P(KrFactors), vp, P(KrOpts), vp, P(KrReport)]),
             "kron_ridge": (i32, [vp, P(KrFactors), vp, P(KrOpts), vp, P(KrReport)]),
+            "kron_regress_async": (i32, [vp, P(KrFactors), vp, P(KrOpts), vp, vp]),
+            "kron_ridge_async": (i32, [vp, P(KrFactors), vp, P(KrOpts), vp, vp]),
             "kron_ridge_batched": (i32, [vp, i32, P(KrFactors), P(vp), P(KrOpts), P(vp), P(KrReport)]),
             "tucker_factor_update": (i32, [vp, i32, P(i64), P(i32), vp, P(vp), vp, i32, P(KrOpts), P(KrReport)]),
             "tucker_als_sweep": (i32, [vp, i32, P(i64), P(i32), vp, P(vp), vp, P(KrOpts), i32, P(KrReport)]),
@@ -482,6 +492,54 @@ def kron_ridge(As, b, lam, eps=0.1, seed=0, call_id=0, raise_notconv=True, host_
     """Alg. 2 with lambda > 0; returns (x, report)."""
     return _solve(lib().kron_ridge, As, b, raise_notconv, host_io, eps=eps, lam=lam, seed=seed, call_id=call_id,
                   **kw)
+
+
+def _solve_async(fn, As, b, x, report, **kw):
+    h = context()
+    # no staging copies: the solve may still be running (or be replayed) after this returns
+    As = [_inout(A, "As[%d]" % k) for k, A in enumerate(As)]
+    b = _inout(b, "b")
+    R = int(math.prod(A.shape[1] for A in As))
+    if x is None:
+        x = torch.empty(R, dtype=torch.float32, device=b.device)
+    _inout(x, "x")
+    if x.numel() != R:
+        raise ValueError("x must hold prod R = %d floats" % R)
+    nb = ctypes.sizeof(KrDevReport)
+    if report is None:
+        report = torch.zeros(nb, dtype=torch.uint8, device=b.device)
+    if not (report.is_cuda and report.dtype == torch.uint8 and report.is_contiguous() and report.numel() >= nb):
+        raise ValueError("report must be a contiguous CUDA uint8 tensor of at least %d bytes" % nb)
+    f = _factors(As)
+    o = _opts(**kw)
+    _check(fn(h, ctypes.byref(f), _ptr(b), ctypes.byref(o), _ptr(x), _ptr(report)), h)
+    dev = b.device.index if b.device.index is not None else torch.cuda.current_device()
+    cur = torch.cuda.current_stream(dev)
+    if cur.cuda_stream == 0 and dev in _lib_streams:  # later work on the current stream follows the solve
+        cur.wait_stream(_lib_streams[dev])
+    return x, report
+
+
+def kron_regress_async(As, b, eps=0.1, seed=0, call_id=0, x=None, report=None, **kw):
+    """kron_regress enqueued without waiting (or captured into the caller's CUDA graph when
+    torch's current stream is capturing). Returns (x, report): report is a device uint8
+    tensor holding a kr_dev_report once the solve has run; read it with read_dev_report."""
+    return _solve_async(lib().kron_regress_async, As, b, x, report, eps=eps, seed=seed, call_id=call_id, **kw)
+
+
+def kron_ridge_async(As, b, lam, eps=0.1, seed=0, call_id=0, x=None, report=None, **kw):
+    """kron_ridge enqueued without waiting; see kron_regress_async."""
+    return _solve_async(lib().kron_ridge_async, As, b, x, report, eps=eps, lam=lam, seed=seed, call_id=call_id,
+                        **kw)
+
+
+def read_dev_report(report):
+    """The kr_dev_report in a device tensor, as a dict (copies it to the host: waits for the solve)."""
+    nb = ctypes.sizeof(KrDevReport)
+    r = KrDevReport.from_buffer_copy(bytes(report[:nb].cpu().numpy()))
+    return dict(status=STATUS.get(r.status, r.status), iters=r.iters, converged=bool(r.converged),
+                stop=int(r.converged), iters_reduced=r.iters_reduced, precision_used=r.precision_used, s=r.s,
+                distinct=r.distinct, obj_sampled=r.obj_sampled, rel_update=r.rel_update)
 
 
 def kron_ridge_batched(problems, lam, eps=0.1, seed=0, call_id=0, **kw):

@@ -62,6 +62,14 @@ extern "C" kr_status kr_create(kr_ctx** out, void* stream, size_t workspace_byte
     return e == cudaErrorMemoryAllocation ? KR_ENOMEM : KR_ECUDA;
   }
   ctx->stream = (cudaStream_t)stream;
+  // an asynchronous solve's device state and the side stream of captured loop bodies, made
+  // here so that a solve captured into the caller's graph allocates nothing
+  if (cudaMalloc(&ctx->gm_async, KR_GM_ASYNC_BYTES) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    kr_destroy(ctx);
+    return KR_ENOMEM;
+  }
   if (workspace_bytes > 0 && kr_ws_reserve(ctx, workspace_bytes) != KR_OK) {
     kr_destroy(ctx);
     return KR_ENOMEM;
@@ -145,6 +153,7 @@ extern "C" void kr_destroy(kr_ctx* ctx) {
   if (ctx->tc_buf) cudaFree(ctx->tc_buf);
   if (ctx->loop_ev) cudaEventDestroy(ctx->loop_ev);
   if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+  if (ctx->gm_async) cudaFree(ctx->gm_async);
   for (cudaEvent_t e : ctx->tune_ev)
     if (e) cudaEventDestroy(e);
   kr_tune_free(ctx);
@@ -169,7 +178,7 @@ extern "C" int64_t kr_launch_count(const kr_ctx* ctx) { return ctx ? ctx->launch
 
 kr_status kr_io_reserve(kr_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->io_size) return KR_OK;
-  if (ctx->gm.on) return kr_fail(ctx, KR_ENOTIMPL, "graph sweep: the host-buffer staging would grow inside the capture");
+  if (ctx->gm.on && ctx->gm.capturing) return kr_fail(ctx, KR_ENOTIMPL, "inside a capture: the host-buffer staging would have to grow (run the call once outside the capture first)");
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->copy_stream) KR_CUDA(ctx, cudaStreamSynchronize(ctx->copy_stream));
   if (ctx->io) {
@@ -189,7 +198,7 @@ kr_status kr_io_reserve(kr_ctx* ctx, size_t bytes) {
 
 kr_status kr_ws_reserve(kr_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->ws_size) return KR_OK;
-  if (ctx->gm.on) return kr_fail(ctx, KR_ENOTIMPL, "graph sweep: the workspace would grow inside the capture");
+  if (ctx->gm.on && ctx->gm.capturing) return kr_fail(ctx, KR_ENOTIMPL, "inside a capture: the workspace would have to grow (run the call once outside the capture first)");
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->ws) {
     cudaFree(ctx->ws);
@@ -209,7 +218,7 @@ kr_status kr_ws_reserve(kr_ctx* ctx, size_t bytes) {
 
 kr_status kr_split_reserve(kr_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->split_size) return KR_OK;
-  if (ctx->gm.on) return kr_fail(ctx, KR_ENOTIMPL, "graph sweep: the split-K buffer would grow inside the capture");
+  if (ctx->gm.on && ctx->gm.capturing) return kr_fail(ctx, KR_ENOTIMPL, "inside a capture: the split-K buffer would have to grow (run the call once outside the capture first)");
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->split_buf) cudaFree(ctx->split_buf);
   ctx->split_buf = nullptr;
@@ -226,7 +235,7 @@ kr_status kr_split_reserve(kr_ctx* ctx, size_t bytes) {
 
 kr_status kr_hbuf_reserve(kr_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->hbuf_size) return KR_OK;
-  if (ctx->gm.on) return kr_fail(ctx, KR_ENOTIMPL, "graph sweep: the pinned read-back buffer would grow inside the capture");
+  if (ctx->gm.on && ctx->gm.capturing) return kr_fail(ctx, KR_ENOTIMPL, "inside a capture: the pinned read-back buffer would have to grow (run the call once outside the capture first)");
   KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
   ctx->hbuf = nullptr;

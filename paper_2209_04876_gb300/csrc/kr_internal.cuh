@@ -83,6 +83,9 @@ struct kr_ctx {
   // and put each Richardson loop into the capture as a conditional WHILE node.
   struct GraphMode {
     bool on = false;
+    bool capturing = true;   // loops go into the ongoing capture; else each is its own graph,
+                             // launched without waiting (an asynchronous solve outside capture)
+    void* report = nullptr;  // kr_dev_report of an asynchronous solve (device)
     void* mem = nullptr;     // one device allocation holding the arrays below (owned)
     int* err = nullptr;      // OR of KR_GM_* bits
     int* status = nullptr;   // {StepCheck, iteration count} per loop, in capture order
@@ -99,6 +102,7 @@ struct kr_ctx {
     int last_prec = 0;                   // and the precision of its first phase
   } gm;
   cudaStream_t side_stream = nullptr;  // captures a loop body inside an ongoing capture (owned)
+  void* gm_async = nullptr;  // an asynchronous solve's device state (GraphMode arrays; owned)
   // worker contexts of kron_ridge_batched, each with its own stream and workspace (owned)
   std::vector<kr_ctx*> workers;
   std::vector<cudaStream_t> worker_streams;
@@ -442,7 +446,6 @@ struct SolveCfg {
   int stop_rule = 0;     // 1: the (1+eps)-aware rule (kr_opts.stop_rule)
   double theta = 0.01;   // its fraction of eps
   int prec = 0;          // kr_opts.precision: slab-pass contractions of the first phase
-  bool pc64_always = false;  // the ridge preconditioner in FP64 whatever the factors' conditioning
 };
 
 enum StepCheck { STEP_CONTINUE, STEP_CONVERGED, STEP_FLOOR, STEP_DIVERGED, STEP_NONFINITE, STEP_MAXITER, STEP_EPS };
@@ -465,7 +468,12 @@ kr_status kr_capture_while(kr_ctx* ctx, cudaGraphConditionalHandle hnd,
 // {status, iteration count} in the next slot (*slot_out = its index; base_slot: the loop a
 // resumed loop continues, whose count is subtracted when launches are tallied).
 enum { KR_GM_FACTOR_RANK = 1, KR_GM_CORE_UNFOLD_RANK = 2, KR_GM_CAPACITANCE = 4 };
+constexpr size_t KR_GM_ASYNC_BYTES = 1024;  // kr_ctx::gm_async
 kr_status kr_gm_flags(kr_ctx* ctx, const int* flags, int n, int bit);
+// Runs fn, which adds loops (kr_gm_handle / kr_capture_while), where they belong: into the
+// ongoing capture, or (an asynchronous solve outside capture) captured on its own and
+// launched on the stream as one graph without waiting.
+kr_status kr_gm_section(kr_ctx* ctx, const std::function<kr_status()>& fn);
 // After a captured sweep ran (stream synchronised): the last core step's report fields
 // (converged, rel_update, obj_sampled, distinct, s, precision_used) from the device copies.
 kr_status kr_gm_core_report(kr_ctx* ctx, double lambda, kr_report* rep);

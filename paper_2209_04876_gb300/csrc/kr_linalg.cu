@@ -359,8 +359,10 @@ __global__ void __launch_bounds__(CDF_THREADS) k_cdf(ModePtrs mp) {
     double l = lev[i];
     mp.prob[n][i] = __ddiv_rn(l, T);
     mp.invp[n][i] = l > 0.0 ? (float)__ddiv_rn(T, l) : 0.f;
-    // u < c  <=>  U < ceil(c * 2^53) for the 53-bit integer U with u = U * 2^-53
-    mp.thr[n][i] = (uint64_t)ceil(c * 9007199254740992.0);
+    // u < c  <=>  U < ceil(c * 2^53) for the 53-bit integer U with u = U * 2^-53; the last
+    // threshold is 2^53 whatever the scores were (all zero or not finite for a factor that
+    // failed its rank check on the device), so the sampler's search stays in the table
+    mp.thr[n][i] = i == I - 1 ? (uint64_t(1) << 53) : (uint64_t)ceil(c * 9007199254740992.0);
   }
 }
 

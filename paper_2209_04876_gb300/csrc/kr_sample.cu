@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(256) k_prob_rank(ProbRanks pr) {
   }
 }
 
+// thr[I - 1] = 2^53 > U (both table builders set it), so the forward steps end in the table.
 __device__ __forceinline__ int guided_search(const uint64_t* thr, const uint16_t* guide, int shift, uint64_t U) {
   int i = guide[U >> shift];
   while (thr[i] <= U) ++i;
@@ -769,7 +770,8 @@ static bool kr_group_dense(const kr_ctx* ctx, int64_t s, int64_t keyspace) {
 static kr_status kr_dcnt_reserve(kr_ctx* ctx, int64_t keys) {
   const size_t bytes = (size_t)keys * sizeof(uint32_t);
   if (bytes > ctx->dcnt_size) {
-    if (ctx->gm.on) return kr_fail(ctx, KR_ENOTIMPL, "graph sweep: the key counters would grow inside the capture");
+    if (ctx->gm.on && ctx->gm.capturing)
+      return kr_fail(ctx, KR_ENOTIMPL, "inside a capture: the key counters would have to grow (run the call once outside the capture first)");
     KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (ctx->dcnt) cudaFree(ctx->dcnt);
     ctx->dcnt = nullptr;
@@ -944,7 +946,7 @@ kr_status kr_sketch_fill(kr_ctx* ctx, const Modes& m, const FactorTables& t, con
   }
   KR_CUDA(ctx, cudaMemcpyAsync(sk->invpT, t.invp[N - 1], sizeof(float) * IT, cudaMemcpyDeviceToDevice, ctx->stream));
   KR_TRY(kr_hbuf_reserve(ctx, 4096));
-  if (ctx->gm.on) {  // a captured sweep: the count stays on the device for the sweep's report
+  if (ctx->gm.on) {  // a captured sweep or an asynchronous solve: the count stays on the device
     KR_CUDA(ctx, cudaMemcpyAsync(ctx->gm.distinct, dsum, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
                                  ctx->stream));
     sk->distinct = -1;
@@ -1026,9 +1028,12 @@ extern "C" kr_status kron_sample(kr_ctx* ctx, int32_t N, const int64_t* I, const
   return KR_OK;
 }
 
+// The last threshold is 2^53, above every U, whatever cdf[n - 1] holds: a table whose last
+// entry is below 1 (or not a number) clamps to the last row, as the bounded binary search
+// does, and the guided search never steps past the table.
 __global__ void k_thr_from_cdf(const double* cdf, uint64_t* thr, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    thr[i] = (uint64_t)ceil(cdf[i] * 9007199254740992.0);
+    thr[i] = i == n - 1 ? (uint64_t(1) << 53) : (uint64_t)ceil(cdf[i] * 9007199254740992.0);
 }
 
 extern "C" kr_status kron_sketch(kr_ctx* ctx, const kr_factors* f, const double* const cdf[], const double* const prob[],

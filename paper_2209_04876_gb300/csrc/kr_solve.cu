@@ -448,6 +448,31 @@ __global__ void k_zero_if_status(float* __restrict__ x, int64_t n, const int* __
     x[i] = 0.f;
 }
 
+// An asynchronous solve's report, from the final state and objective (one thread). slots:
+// the loops' {status, count}; refined: slot 0 was the reduced-precision phase.
+__global__ void k_async_report(const RichState* st, const double* obj, const unsigned long long* distinct,
+                               const int* err, const int* slots, int refined, double lambda, int64_t s, int prec,
+                               kr_dev_report* out) {
+  if (threadIdx.x != 0) return;
+  kr_dev_report r = {};
+  const int stt = st->status;
+  r.iters = st->it;
+  r.converged = stt == STEP_CONVERGED ? 1 : stt == STEP_FLOOR ? 2 : stt == STEP_EPS ? 3 : 0;
+  r.status = *err             ? KR_ERANK
+             : r.converged    ? KR_OK
+             : stt == STEP_NONFINITE ? KR_ENONFINITE
+             : stt == STEP_DIVERGED  ? KR_EDIVERGED
+                                     : KR_ENOTCONV;
+  r.iters_reduced = refined ? slots[1] : 0;
+  r.precision_used = prec;
+  r.s = s;
+  r.distinct = (int64_t)*distinct;
+  r.obj_sampled = obj[0] + lambda * obj[1];
+  const double h0 = st->h[0], h1 = st->h[1];
+  r.rel_update = h1 > 0.0 ? sqrt(h0) / sqrt(h1) : (h0 == 0.0 ? 0.0 : INFINITY);
+  *out = r;
+}
+
 __global__ void k_rich_init(RichState* st) {
   st->h[0] = st->h[1] = st->h[2] = 0.0;
   st->prev_h0 = st->min_h0 = st->min_q = INFINITY;
@@ -1537,6 +1562,27 @@ kr_status kr_capture_while(kr_ctx* ctx, cudaGraphConditionalHandle hnd,
   return KR_OK;
 }
 
+kr_status kr_gm_section(kr_ctx* ctx, const std::function<kr_status()>& fn) {
+  if (ctx->gm.capturing) return fn();
+  KR_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed));
+  const kr_status st = fn();
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+  if (st != KR_OK || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (st != KR_OK) return st;
+    return kr_fail_cuda(ctx, ce, "asynchronous solve: capture of a loop", __FILE__, __LINE__);
+  }
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ex, ctx->stream);
+  if (ex) cudaGraphExecDestroy(ex);  // an executable still running is freed when it completes
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return kr_fail_cuda(ctx, e, "asynchronous solve: launch of a loop graph", __FILE__, __LINE__);
+  ctx->graphs++;
+  return KR_OK;
+}
+
 namespace {
 __global__ void k_gm_flags(const int* __restrict__ f, int n, int bit, int* __restrict__ err) {
   if (threadIdx.x == 0) {
@@ -1571,6 +1617,7 @@ kr_status kr_gm_status(kr_ctx* ctx, const int* status, const int* it, int64_t pe
 }
 
 size_t kr_gm_state_bytes() { return sizeof(RichState); }
+static_assert(64 + sizeof(RichState) <= KR_GM_ASYNC_BYTES, "an asynchronous solve's state must fit kr_ctx::gm_async");
 
 kr_status kr_gm_core_report(kr_ctx* ctx, double lambda, kr_report* rep) {
   KR_TRY(kr_hbuf_reserve(ctx, 4096));
@@ -1700,7 +1747,7 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   double* pc64 = nullptr;
   if (cfg.lambda > 0.0) {
     double* buf = cv.take<double>(2 * (size_t)R);
-    if (cfg.pc64_always) {
+    if (gm) {  // the factors' spectra, which decide it, are not read back
       pc64 = buf;
     } else {
       double hi = 1.0, lo = 1.0;
@@ -1834,23 +1881,29 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
   };
   if (gm) {
     // the loop (and the FP32 refinement, entered on the device when the first phase did
-    // not stop at max_iter) as conditional nodes of the sweep's graph
-    cudaGraphConditionalHandle h1 = 0;
-    int64_t pb = 0;
+    // not stop at max_iter) as conditional nodes of the sweep's graph or, for an
+    // asynchronous solve outside capture, of graphs of their own
     int slot1 = -1;
-    KR_TRY(kr_gm_handle(ctx, 1, &h1));
-    KR_TRY(kr_capture_while(ctx, h1, one_step, &pb));
-    KR_TRY(kr_gm_status(ctx, &bf.rich->status, &bf.rich->it, pb, -1, &slot1));
+    KR_TRY(kr_gm_section(ctx, [&]() -> kr_status {
+      cudaGraphConditionalHandle h1 = 0;
+      int64_t pb = 0;
+      KR_TRY(kr_gm_handle(ctx, 1, &h1));
+      KR_TRY(kr_capture_while(ctx, h1, one_step, &pb));
+      return kr_gm_status(ctx, &bf.rich->status, &bf.rich->it, pb, -1, &slot1);
+    }));
     if (prec1 > 0) {
-      cudaGraphConditionalHandle h2 = 0;
-      KR_TRY(kr_gm_handle(ctx, 0, &h2));
-      KR_LAUNCH(ctx, k_zero_if_status, grid_cap(ctx, R, 256, 4), 256, 0, bf.x, R, &bf.rich->status,
-                (int)STEP_NONFINITE);
-      KR_LAUNCH(ctx, k_rich_resume_dev, 1, 1, 0, bf.rich, h2);
-      cur_prec = 0;
-      cur_tol = cfg.tol;
-      KR_TRY(kr_capture_while(ctx, h2, one_step, &pb));
-      KR_TRY(kr_gm_status(ctx, &bf.rich->status, &bf.rich->it, pb, slot1, nullptr));
+      KR_TRY(kr_gm_section(ctx, [&]() -> kr_status {
+        cudaGraphConditionalHandle h2 = 0;
+        int64_t pb = 0;
+        KR_TRY(kr_gm_handle(ctx, 0, &h2));
+        KR_LAUNCH(ctx, k_zero_if_status, grid_cap(ctx, R, 256, 4), 256, 0, bf.x, R, &bf.rich->status,
+                  (int)STEP_NONFINITE);
+        KR_LAUNCH(ctx, k_rich_resume_dev, 1, 1, 0, bf.rich, h2);
+        cur_prec = 0;
+        cur_tol = cfg.tol;
+        KR_TRY(kr_capture_while(ctx, h2, one_step, &pb));
+        return kr_gm_status(ctx, &bf.rich->status, &bf.rich->it, pb, slot1, nullptr);
+      }));
     }
     // the sampled objective at the returned x and the final state, for the sweep's report
     KR_TRY(sampled_pass(ctx, m, &sk, bf, nblk, false, &op, &on));
@@ -1861,6 +1914,10 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     KR_CUDA(ctx, cudaMemcpyAsync(ctx->gm.last, bf.rich, sizeof(RichState), cudaMemcpyDeviceToDevice, ctx->stream));
     ctx->gm.last_s = cfg.s;
     ctx->gm.last_prec = prec1;
+    if (ctx->gm.report)
+      KR_LAUNCH(ctx, k_async_report, 1, 32, 0, (const RichState*)bf.rich, (const double*)bf.red,
+                (const unsigned long long*)ctx->gm.distinct, (const int*)ctx->gm.err, (const int*)ctx->gm.status,
+                prec1 > 0 ? 1 : 0, cfg.lambda, cfg.s, prec1, static_cast<kr_dev_report*>(ctx->gm.report));
     return KR_OK;
   }
   KR_TRY(run_loop());
@@ -1924,11 +1981,13 @@ int64_t default_samples(const kr_opts* o, int64_t R) {
   return o->num_samples > 0 ? o->num_samples : kr_sample_count(R, o->eps, o->sample_scale);
 }
 
-kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr_opts* o, float* x, kr_report* rep,
-                      double lambda) {
+// The solvers' argument checks and configuration (shared by the synchronous and the
+// asynchronous entry points).
+kr_status solve_setup(kr_ctx* ctx, const kr_factors* f, const float* b, const kr_opts* o, float* x, double lambda,
+                      Modes* mp, SolveCfg* cp) {
   if (!ctx) return KR_EINVAL;
   if (!o || !b || !x) return kr_fail(ctx, KR_EINVAL, "solver: null opts, b or x");
-  Modes m;
+  Modes& m = *mp;
   KR_TRY(kr_check_factors(ctx, f, &m));
   if (!(o->eps > 0.0 && o->eps < 1.0)) return kr_fail(ctx, KR_EINVAL, "solver: eps=%g outside (0,1)", o->eps);
   if (o->precision < 0 || o->precision > 2)
@@ -1943,7 +2002,7 @@ kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr
       return kr_fail(ctx, KR_EINVAL, "solver: current device %d is not the context's device %d", cur, ctx->device);
   }
   if (!(lambda >= 0.0) || !isfinite(lambda)) return kr_fail(ctx, KR_EINVAL, "solver: lambda must be finite and >= 0");
-  SolveCfg cfg;
+  SolveCfg& cfg = *cp;
   cfg.lambda = lambda;
   cfg.eps = o->eps;
   cfg.alpha = o->step > 0 ? o->step : 1.0 - sqrt(o->eps);
@@ -1953,8 +2012,16 @@ kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr
   cfg.stop_rule = o->stop_rule;
   cfg.theta = o->theta > 0 ? o->theta : 0.01;
   cfg.prec = o->precision;
+  cfg.s = default_samples(o, kr_prod_R(m));
+  return KR_OK;
+}
+
+kr_status solve_entry(kr_ctx* ctx, const kr_factors* f, const float* b, const kr_opts* o, float* x, kr_report* rep,
+                      double lambda) {
+  Modes m;
+  SolveCfg cfg;
+  KR_TRY(solve_setup(ctx, f, b, o, x, lambda, &m, &cfg));
   const int64_t R = kr_prod_R(m), I = kr_prod_I(m);
-  cfg.s = default_samples(o, R);
   if (rep) *rep = kr_report{};
   if (!o->host_io) return kr_solve_device(ctx, m, b, cfg, o->seed, o->call_id, x, rep);
   // host buffers: copy factors and b in, x out, inside the call
@@ -2044,6 +2111,61 @@ extern "C" kr_status kron_ridge(kr_ctx* ctx, const kr_factors* f, const float* b
   if (!ctx) return KR_EINVAL;
   if (!opts || !(opts->lambda > 0.0)) return kr_fail(ctx, KR_EINVAL, "kron_ridge: opts->lambda must be > 0");
   return solve_entry(ctx, f, b, opts, x, report, opts->lambda);
+}
+
+namespace {
+
+kr_status solve_async(kr_ctx* ctx, const kr_factors* f, const float* b, const kr_opts* o, float* x,
+                      kr_dev_report* report, double lambda) {
+  Modes m;
+  SolveCfg cfg;
+  KR_TRY(solve_setup(ctx, f, b, o, x, lambda, &m, &cfg));
+  if (!report) return kr_fail(ctx, KR_EINVAL, "asynchronous solve: null report");
+  if (o->host_io) return kr_fail(ctx, KR_EINVAL, "asynchronous solve: device pointers only (host_io must be 0)");
+  if (ctx->gm.on) return kr_fail(ctx, KR_EINVAL, "asynchronous solve: the context is capturing a sweep");
+  if (!ctx->gm_async || !ctx->side_stream) return kr_fail(ctx, KR_ENOMEM, "asynchronous solve: no device state");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  KR_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
+  if (cs == cudaStreamCaptureStatusInvalidated)
+    return kr_fail(ctx, KR_EINVAL, "asynchronous solve: the stream's capture has been invalidated");
+  if (cs == cudaStreamCaptureStatusNone && (ctx->stream == nullptr || ctx->stream == cudaStreamLegacy))
+    return kr_fail(ctx, KR_EINVAL, "asynchronous solve: the legacy default stream cannot run its loop graphs");
+  // the device state: error word, two loop slots, objective, final state, distinct count
+  char* d = static_cast<char*>(ctx->gm_async);
+  kr_ctx::GraphMode& g = ctx->gm;
+  g = kr_ctx::GraphMode();
+  g.err = reinterpret_cast<int*>(d);
+  g.status = reinterpret_cast<int*>(d + 16);
+  g.obj = reinterpret_cast<double*>(d + 32);
+  g.distinct = reinterpret_cast<unsigned long long*>(d + 48);
+  g.last = d + 64;
+  g.nstatus = 2;
+  g.report = report;
+  g.capturing = cs == cudaStreamCaptureStatusActive;
+  g.on = true;
+  const int timing = ctx->timing;
+  ctx->timing = 0;  // nothing is timed or read back
+  kr_status st = KR_OK;
+  const cudaError_t e = cudaMemsetAsync(g.err, 0, 16, ctx->stream);
+  if (e != cudaSuccess) st = kr_fail_cuda(ctx, e, "asynchronous solve: state reset", __FILE__, __LINE__);
+  if (st == KR_OK) st = kr_solve_device(ctx, m, b, cfg, o->seed, o->call_id, x, nullptr);
+  ctx->timing = timing;
+  g = kr_ctx::GraphMode();
+  return st;
+}
+
+}  // namespace
+
+extern "C" kr_status kron_regress_async(kr_ctx* ctx, const kr_factors* f, const float* b, const kr_opts* opts,
+                                        float* x, kr_dev_report* report) {
+  return solve_async(ctx, f, b, opts, x, report, 0.0);
+}
+
+extern "C" kr_status kron_ridge_async(kr_ctx* ctx, const kr_factors* f, const float* b, const kr_opts* opts, float* x,
+                                      kr_dev_report* report) {
+  if (!ctx) return KR_EINVAL;
+  if (!opts || !(opts->lambda > 0.0)) return kr_fail(ctx, KR_EINVAL, "kron_ridge_async: opts->lambda must be > 0");
+  return solve_async(ctx, f, b, opts, x, report, opts->lambda);
 }
 
 // Worker contexts for concurrent problems: a context each, on its own non-blocking stream,

@@ -1357,9 +1357,6 @@ extern "C" kr_status tucker_als_sweep(kr_ctx* ctx, int32_t N, const int64_t* I, 
       st = kr_factor_step(ctx, m, X, G, n, cfg, opts->seed, cid, A[n], &r);
     } else {
       SolveCfg cfg = cfg_from(opts, kr_prod_R(m));
-      // inside the graph the factors' spectra are not read back: the ridge preconditioner
-      // runs in FP64 (the choice the host makes for badly conditioned factors)
-      cfg.pc64_always = ctx->gm.on;
       st = kr_solve_device(ctx, m, X, cfg, opts->seed, cid, G, &r);
     }
     if (!ctx->gm.on) total_iters += r.iters;

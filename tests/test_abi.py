@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(libpath):
 
 
 def test_struct_layouts_match_header(libpath, tmp_path):
-    """ctypes mirrors of kr_factors / kr_opts / kr_report have the C compiler's layout."""
+    """ctypes mirrors of kr_factors / kr_opts / kr_report / kr_dev_report have the C compiler's layout."""
     import shutil
     import subprocess
 
@@ -50,16 +50,18 @@ def test_struct_layouts_match_header(libpath, tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "%s/include/kron.h"\n'
-        'int main(void){printf("%%zu %%zu %%zu %%zu %%zu %%zu %%zu %%zu %%zu\\n", sizeof(kr_factors),'
+        'int main(void){printf("%%zu %%zu %%zu %%zu %%zu %%zu %%zu %%zu %%zu %%zu %%zu %%zu\\n", sizeof(kr_factors),'
         ' offsetof(kr_factors, A), sizeof(kr_opts), offsetof(kr_opts, seed), sizeof(kr_report),'
         ' offsetof(kr_report, t_ms), offsetof(kr_opts, host_io), offsetof(kr_opts, stop_rule),'
-        ' offsetof(kr_opts, theta)); return 0;}\n' % ROOT)
+        ' offsetof(kr_opts, theta), sizeof(kr_dev_report), offsetof(kr_dev_report, s),'
+        ' offsetof(kr_dev_report, rel_update)); return 0;}\n' % ROOT)
     exe = tmp_path / "layout"
     subprocess.run([cc, str(src), "-o", str(exe)], check=True)
     got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()))
     want = [ctypes.sizeof(kr.KrFactors), kr.KrFactors.A.offset, ctypes.sizeof(kr.KrOpts), kr.KrOpts.seed.offset,
             ctypes.sizeof(kr.KrReport), kr.KrReport.t_ms.offset, kr.KrOpts.host_io.offset, kr.KrOpts.stop_rule.offset,
-            kr.KrOpts.theta.offset]
+            kr.KrOpts.theta.offset, ctypes.sizeof(kr.KrDevReport), kr.KrDevReport.s.offset,
+            kr.KrDevReport.rel_update.offset]
     assert got == want
 
 
