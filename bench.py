@@ -144,15 +144,31 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(v, world):
+def _reduce(v, world, op):
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
 
     t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(v, world):
+    import torch.distributed as dist
+
+    return _reduce(v, world, dist.ReduceOp.MAX if world > 1 else None)
+
+
+def whole_job_rate(units, seconds, world):
+    """Replicas run side by side: the units every rank processed over the slowest rank's time.
+    Returns (rate, slowest seconds)."""
+    import torch.distributed as dist
+
+    total = _reduce(float(units), world, dist.ReduceOp.SUM if world > 1 else None)
+    slowest = _reduce(float(seconds), world, dist.ReduceOp.MAX if world > 1 else None)
+    return total / slowest, slowest
 
 
 # ---------------------------------------------------------------------------- CPU oracle legs
@@ -369,9 +385,9 @@ def run_gpu(args, rank, world, local):
     launches = kr.launch_count() - l0
     elapsed_ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    elapsed_ms = max_over_ranks(elapsed_ms, world)
     s = reps[0]["s"]
-    value = world * args.steps * s / (elapsed_ms / 1000.0)
+    value, elapsed_s = whole_job_rate(args.steps * s, elapsed_ms / 1000.0, world)
+    elapsed_ms = 1000.0 * elapsed_s
     # certify every timed solve against the oracle's OPT
     ratios = [kr.kron_objective(As_d, b_d, x, lam) / opt for x in xs]
     certified = all(r <= 1.0 + eps for r in ratios)
@@ -401,8 +417,7 @@ def run_gpu(args, rank, world, local):
     t0 = time.perf_counter()
     for k in range(args.steps):
         xh, rep_h = solve(As_h, b_h, call_id=k, host_io=True, **opts)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e = world * args.steps * s / e2e_s
+    e2e, e2e_s = whole_job_rate(args.steps * s, time.perf_counter() - t0, world)
     h2d = int(4 * rep_h["distinct"] + sum(A.numel() * 4 for A in As_h))
     d2h = int(xh.numel() * 4)
     # the same calls with all of b copied in (the library's path for b outside page-locked memory)
@@ -412,7 +427,7 @@ def run_gpu(args, rank, world, local):
     t0 = time.perf_counter()
     for k in range(args.steps):
         solve(As_h, b_h, call_id=k, host_io=True, **opts)
-    e2e_copy = world * args.steps * s / max_over_ranks(time.perf_counter() - t0, world)
+    e2e_copy = whole_job_rate(args.steps * s, time.perf_counter() - t0, world)[0]
     kr.set_option(kr.OPT_HOST_GATHER, 1)
     del As_h, b_h
     if rank != 0:

@@ -97,6 +97,7 @@ GRAPH_CASES = [
     ([40, 48, 36], [4, 16, 8], 0.0, 1, 0),
     ([40, 48, 36], [4, 16, 8], 0.0, 0, 1),
     ([20, 18, 16, 14], [2, 3, 2, 3], 0.0, 0, 0),
+    ([40, 36], [5, 5], 0.0, 0, 0),
 ]
 
 
