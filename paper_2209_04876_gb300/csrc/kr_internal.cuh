@@ -424,8 +424,11 @@ kr_status kr_tiles_build(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, Carve& 
 // Z[p] = sum_i A(N-2)[i]^T W[p, i] goes to tl->zpart (see kr_slab.cu); with want_obj the
 // per-tile objective partials go to tl->objpart (tl->ntmax doubles).
 // rearm: zero the tile counter first (needed when no tile reduction followed the last pass).
+// flags: KR_SLAB_ZERO_X when X1 is zero (the first Richardson step; X1 is not read),
+// KR_SLAB_OBJ_ONLY when only the objective partials are wanted (no tile Z is written).
+enum { KR_SLAB_ZERO_X = 1, KR_SLAB_OBJ_ONLY = 2 };
 kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const float* A2, const float* AT,
-                       const float* X1, bool want_obj, bool rearm, int prec = 0);
+                       const float* X1, bool want_obj, bool rearm, int prec = 0, int flags = 0);
 // The contraction format a slab pass asked for `prec` (0 FP32-accurate 3xTF32, 1 BF16,
 // 2 e4m3 with per-row scales) runs at for these ranks (falls back to the next finer one).
 int kr_slab_precision(int R2, int RT, int prec);

@@ -69,6 +69,8 @@ struct SlabArgs {
   int mma, XS;  // Y and Z on tensor cores (3xTF32); row stride of the split X1[p] (floats)
   int64_t P;
   int a2vec, atvec;
+  int zero_x;    // X1 is zero (the first Richardson step): Y = 0, the residual is b~
+  int obj_only;  // only the objective is wanted: no W accumulation, no Z
   // shared-memory layout (bytes)
   uint32_t team_off, team_bytes, o_a2, o_x1, o_pf, o_act, o_cs, o_ctl;
 };
@@ -198,19 +200,21 @@ __device__ __forceinline__ float group_sum(float v, unsigned gmask) {
 
 // One sampled row against the current cell: r = omega (b~ - <a, y>), w += r a (and the
 // objective term r (b~ - <a, y>) when OBJ).
+// zx: y is zero (the product is skipped; the residual is b~ exactly as with the product);
+// wskip: the objective only (no W accumulation). Both are uniform over the kernel.
 template <int RTP, bool SMEM_A, bool OBJ>
 __device__ __forceinline__ void slab_entry(const SlabArgs& a, const float* sA, const float* sInvp, const int* qd,
                                            unsigned gmask, uint32_t e, float bj, float cw, const float* y, float* w,
-                                           float& objc) {
+                                           float& objc, bool zx, bool wskip) {
   using S = SlabShape<RTP>;
   const int it = (int)(e & 0xFFFFu);
   float4 av[S::NQ];
   load_arow<RTP, SMEM_A>(a, sA, it, qd, av);
-  const float pr = group_sum<S::G>(dot_quads<S::NQ>(av, y), gmask);
+  const float pr = zx ? 0.f : group_sum<S::G>(dot_quads<S::NQ>(av, y), gmask);
   const float om = (float)(e >> 16) * cw * sInvp[it];  // 0 past the segment (count 0)
   const float res = bj - pr;
   const float rr = om * res;
-  axpy_quads<S::NQ>(rr, av, w);
+  if (!wskip) axpy_quads<S::NQ>(rr, av, w);
   if (OBJ) objc = fmaf(rr, res, objc);
 }
 
@@ -370,7 +374,7 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
       }
     }
     for (int i = tt; i < (nrow - na) * RTP; i += SLAB_TEAM) sYW[na * RTP + i] = 0.f;
-    {
+    if (!a.zero_x) {  // X1[p], staged for the Y product
       const float* xp = a.X1 + p * zn;
       if (PREC == 1 && mma) {
         // X1[p]^T in BF16: row c holds column c of X1[p] (r contiguous), XS32 words a row
@@ -436,8 +440,10 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
       }
       team_sync(team);
     }
-    // ---- Y rows of the tile's cells: sYW[k] = A(N-1)[i_k] X1[p]
-    if (PREC != 0 && mma) {
+    // ---- Y rows of the tile's cells: sYW[k] = A(N-1)[i_k] X1[p] (0 when X1 is)
+    if (a.zero_x) {
+      for (int i = tt; i < na * RTP; i += SLAB_TEAM) sYW[i] = 0.f;
+    } else if (PREC != 0 && mma) {
       // one 16-row block of cells per warp, all RTP columns: A = rows of A(N-1) (a0 (g, k0),
       // a1 (g + 8, k0), a2 (g, k1), a3 (g + 8, k1)), B = X1[p]^T rows (b0 at k0, b1 at k1 of
       // column n = g), C as in the TF32 form; BF16: k0 = 2q.., k1 = 2q + 8..; e4m3: k0 =
@@ -604,6 +610,7 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
     double objt = 0.0;
     team_sync(team);  // every group holds its first y before owners overwrite Y with W
     const uint32_t nchunk = (L + G - 1) / G;
+    const bool zx = a.zero_x != 0, wskip = a.obj_only != 0;
     const uint32_t* ent = a.ent + e0;
     const float* bt = a.bt + e0;
     uint32_t re[SLAB_D];
@@ -634,7 +641,7 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
           const float bj = G > 1 ? __shfl_sync(0xffffffffu, b_m, gbase + sidx) : b_m;
           if (j < j1 && j == nb)
             slab_next_cell<RTP, OBJ>(sYW, sPf, sCS, sAct, e0, q, qd, k, nb, cw, foreign, y, w, objc, objt);
-          slab_entry<RTP, SMEM_A, OBJ>(a, sA, sInvp, qd, 0xffffffffu, e, bj, cw, y, w, objc);
+          slab_entry<RTP, SMEM_A, OBJ>(a, sA, sInvp, qd, 0xffffffffu, e, bj, cw, y, w, objc, zx, wskip);
         }
       }
     }
@@ -678,6 +685,7 @@ __global__ void __launch_bounds__(SLAB_TEAM* SLAB_TEAMS, 1) k_slab(SlabArgs a) {
       a.objpart[t] = s;
     }
     team_sync(team);
+    if (a.obj_only) continue;  // the tiles' Z is not wanted
     // ---- Z contribution: sum_k A(N-1)[i_k]^T W[k]
     if (PREC != 0 && mma) {
       // one 16 x 8 block of Z per warp step over all cells (k): A = A(N-1)^T (m = r, k = cell),
@@ -1352,7 +1360,7 @@ int kr_slab_precision(int R2, int RT, int prec) {
 }
 
 kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const float* A2, const float* AT,
-                       const float* X1, bool want_obj, bool rearm, int prec) {
+                       const float* X1, bool want_obj, bool rearm, int prec, int flags) {
   SlabLayout L = slab_layout(tl->IT, tl->RT, tl->R2, true);
   if (L.bytes > ctx->smem_optin) L = slab_layout(tl->IT, tl->RT, tl->R2, false);
   if (L.bytes > ctx->smem_optin) return kr_fail(ctx, KR_ENOTIMPL, "slab pass: %zu bytes of shared memory", L.bytes);
@@ -1379,6 +1387,8 @@ kr_status kr_slab_pass(kr_ctx* ctx, const kr_sketch* sk, kr_tiles* tl, const flo
   a.P = tl->P;
   a.a2vec = (tl->R2 % 4 == 0) && ((reinterpret_cast<uintptr_t>(A2) & 15) == 0);
   a.atvec = (tl->RT % 4 == 0) && ((reinterpret_cast<uintptr_t>(AT) & 15) == 0);
+  a.zero_x = (flags & KR_SLAB_ZERO_X) ? 1 : 0;
+  a.obj_only = (flags & KR_SLAB_OBJ_ONLY) && want_obj ? 1 : 0;
   a.team_off = L.team_off;
   a.team_bytes = L.team_bytes;
   a.o_a2 = L.o_a2;

@@ -1190,6 +1190,7 @@ struct IterBufs {
   float* B1 = nullptr;
   // with B1 and the eps-aware rule: the gradient itself (a second output of the tile reduction)
   float* g2 = nullptr;
+  bool x_zero = false;  // x is zero (a solve's first step): the slab pass skips its forward product
 };
 
 int64_t max_intermediate(const Modes& m) {
@@ -1416,10 +1417,11 @@ int64_t slab_max_intermediate(const Modes& m) {
 // Slab form of the sampled pass: X1 = X x_1 A(1) ... x_{N-2} A(N-2), then the fused slab
 // kernel (Z and the per-tile objective partials in bf.tl->objpart).
 kr_status slab_forward(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const IterBufs& bf, bool want_obj,
-                       bool rearm, int prec = 0) {
+                       bool rearm, int prec = 0, int flags = 0) {
   const int N = m.N;
   const float* X1 = bf.x;
-  if (N > 2) {
+  if (bf.x_zero) flags |= KR_SLAB_ZERO_X;  // X1 = 0 as well: not formed
+  if (N > 2 && !bf.x_zero) {
     int din[KR_MAX_MODES], dout[KR_MAX_MODES], tr[KR_MAX_MODES];
     const float* B[KR_MAX_MODES];
     for (int n = 0; n < N; ++n) {
@@ -1431,7 +1433,7 @@ kr_status slab_forward(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const I
     KR_TRY(kr_kron_apply2(ctx, N, din, dout, B, tr, bf.x, bf.X1, bf.t0, bf.t1));
     X1 = bf.X1;
   }
-  return kr_slab_pass(ctx, sk, bf.tl, m.A[N - 2], m.A[N - 1], X1, want_obj, rearm, prec);
+  return kr_slab_pass(ctx, sk, bf.tl, m.A[N - 2], m.A[N - 1], X1, want_obj, rearm, prec, flags);
 }
 
 // g = Z x_1 A(1)^T ... x_{N-2} A(N-2)^T: the sum over the tiles folded with the last
@@ -1458,7 +1460,7 @@ kr_status slab_backward(kr_ctx* ctx, const Modes& m, const IterBufs& bf, double*
 kr_status sampled_pass(kr_ctx* ctx, const Modes& m, const kr_sketch* sk, const IterBufs& bf, int nblk, bool want_g,
                        const double** op, int* on, bool want_obj = false, int prec = 0) {
   if (bf.tl) {
-    KR_TRY(slab_forward(ctx, m, sk, bf, !want_g || want_obj, !want_g, prec));
+    KR_TRY(slab_forward(ctx, m, sk, bf, !want_g || want_obj, !want_g, prec, want_g ? 0 : KR_SLAB_OBJ_ONLY));
     if (!want_g) {
       *op = bf.tl->objpart;
       *on = (int)bf.tl->ntmax;
@@ -1856,10 +1858,15 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     KR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return KR_OK;
   };
+  bool from_zero = true;  // x = 0 before the first step
   auto run_loop = [&]() -> kr_status {
     // The first step runs from the host: it grows every buffer and sets every kernel
     // attribute the steps need, so the captured steps allocate nothing.
-    KR_TRY(one_step(0, 0));
+    bf.x_zero = from_zero;
+    const kr_status st0 = one_step(0, 0);
+    bf.x_zero = false;
+    from_zero = false;
+    KR_TRY(st0);
     KR_TRY(read_state());
     if (hs->status == STEP_CONTINUE && ctx->device_loop && !ctx->timing) {
       // Steps 2.. as one graph (in a fused batch: one node of the batch's shared graph);

@@ -1045,11 +1045,12 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   KR_LAUNCH(ctx, k_factor_loop_init, 1, 1, 0, dloop);
   // One Richardson iteration of every row, then the stopping rule on the device (inside
   // the graph it also sets the loop condition).
+  bool z_zero = false;  // z is zero (the first iteration from the host)
   auto one_iter = [&](cudaGraphConditionalHandle hnd, int use_hnd) -> kr_status {
     int used = 0;
     // sampled part: Gb = K~^T Omega (b~ - K~ z) per row
     if (slab) {
-      KR_TRY(kr_slab_pass(ctx, &sk, &tl, mo.A[0], mo.A[1], Z, false, false));
+      KR_TRY(kr_slab_pass(ctx, &sk, &tl, mo.A[0], mo.A[1], Z, false, false, 0, z_zero ? KR_SLAB_ZERO_X : 0));
       KR_TRY(kr_tile_reduce(ctx, &tl, nullptr, Gb));
     } else {
       KR_TRY(kr_kron_apply2(ctx, No + 1, dfw_in, dfw_out, Bf, trf, Z, Y, t0, t1));
@@ -1088,9 +1089,13 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
               An_out, (double*)nullptr, wdev);
     return KR_OK;
   }
-  // The first iteration runs from the host (with the capacitance check); iterations 2..
-  // as one graph (KR_OPT_DEVICE_LOOP) or from the host.
-  KR_TRY(one_iter(0, 0));
+  // The first iteration runs from the host (with the capacitance check; z = 0, so the
+  // slab pass skips its forward product); iterations 2.. as one graph (KR_OPT_DEVICE_LOOP)
+  // or from the host.
+  z_zero = true;
+  const kr_status st1 = one_iter(0, 0);
+  z_zero = false;
+  KR_TRY(st1);
   KR_CUDA(ctx, cudaMemcpyAsync(hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   KR_TRY(read_state());
   if (*hflag != 0) return kr_fail(ctx, KR_ERANK, "factor step %d: the Woodbury capacitance matrix is singular", n);
