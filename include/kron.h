@@ -115,7 +115,11 @@ typedef struct {
                             the sampled minimum (the O(log 1/eps) iterations of the proof of
                             Thm 4.5); the relative-step rule stays in force as a backstop. Applies to
                             kron_regress / kron_ridge / kron_ridge_batched and the core steps of
-                            tucker_als_sweep. */
+                            tucker_als_sweep, and to the factor steps (tucker_factor_update and the
+                            sweep's) with two other modes on the slab path: there each row's rule is
+                            the same bound on its penalised objective (sampled term plus
+                            lambda ||(G+)^T z||^2 + w ||(I - G+ G) z||^2), and the loop ends once every
+                            row's rule holds (report converged = 3). */
   double theta;          /* fraction of eps of stop_rule 1; <= 0 selects 0.01 */
 } kr_opts;
 

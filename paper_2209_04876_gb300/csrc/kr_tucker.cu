@@ -386,16 +386,23 @@ struct RowStep {
   const double* Cinv;   // Rn x Rn
   double lambda, w, alpha;
   const double* wp;  // when set, the penalty is read here instead of w
+  // the (1+eps)-aware rule: per row, q = g^T M+ g and the penalty part of the row's objective
+  // at z before the step, lambda ||(G+)^T z||^2 + w ||(I - G+ G) z||^2 (null: not wanted)
+  double* rowq;
+  double* rowpen;
 };
 __global__ void __launch_bounds__(256) k_factor_rows(RowStep p, float* __restrict__ Z, const float* __restrict__ gsk,
                                                      double* __restrict__ rowstat) {
   extern __shared__ double fr_smem[];
   const int Rn = p.Rn, Rne = p.Rne;
+  const bool eps = p.rowq != nullptr;
   double* zs = fr_smem;     // Rne
   double* M = zs + Rne;     // Rne
   double* T = M + Rne;      // Rne
-  __shared__ double tv[PEN_MAXRN], uv[PEN_MAXRN];
+  double* G4 = T + Rne;     // Rne: the gradient (eps rule only)
+  __shared__ double tv[PEN_MAXRN], uv[PEN_MAXRN], gz[PEN_MAXRN];
   __shared__ float red[3][8];
+  __shared__ double dred[2][8];
   const int64_t row = blockIdx.x;
   float* z = Z + row * Rne;
   const float* g_sk = gsk + row * Rne;
@@ -418,8 +425,13 @@ __global__ void __launch_bounds__(256) k_factor_rows(RowStep p, float* __restric
     if (lane == 0) {
       tv[a] = t;
       uv[a] = u;
+      gz[a] = t;
     }
   }
+  __syncthreads();
+  double pen = 0.0;  // this thread's part of the penalty terms (eps rule)
+  if (eps)
+    for (int a = threadIdx.x; a < Rn; a += blockDim.x) pen = fma(p.lambda * uv[a], uv[a], pen);
   __syncthreads();
   for (int a = threadIdx.x; a < Rn; a += blockDim.x) tv[a] = p.lambda * uv[a] - pw * tv[a];
   __syncthreads();
@@ -427,6 +439,13 @@ __global__ void __launch_bounds__(256) k_factor_rows(RowStep p, float* __restric
     double c = 0.0;
     for (int a = 0; a < Rn; ++a) c = fma(p.gp64[(int64_t)k * Rn + a], tv[a], c);
     M[k] = pw * zs[k] + c - (double)g_sk[k];
+    if (eps) {  // (I - G+ G) z at k
+      double gg = 0.0;
+      for (int a = 0; a < Rn; ++a) gg = fma(p.gp64[(int64_t)k * Rn + a], gz[a], gg);
+      const double nz = zs[k] - gg;
+      pen = fma(pw * nz, nz, pen);
+      G4[k] = M[k];
+    }
   }
   __syncthreads();
   base_apply_block64(p.b, M, T);  // D = A^-1 g
@@ -446,9 +465,11 @@ __global__ void __launch_bounds__(256) k_factor_rows(RowStep p, float* __restric
   }
   __syncthreads();
   float s_1 = 0.f, s_2 = 0.f, bad = 0.f;
+  double q = 0.0;  // this thread's part of g^T M+ g (eps rule)
   for (int k = threadIdx.x; k < Rne; k += blockDim.x) {
     double gr = 0.0;
     for (int a = 0; a < Rn; ++a) gr = fma(p.AinvU[(int64_t)a * Rne + k], uv[a], gr);
+    if (eps) q = fma(G4[k], M[k] - gr, q);
     const float st = (float)(p.alpha * (M[k] - gr));
     const float zn = (float)zs[k] - st;
     z[k] = zn;
@@ -462,22 +483,38 @@ __global__ void __launch_bounds__(256) k_factor_rows(RowStep p, float* __restric
     s_2 += __shfl_xor_sync(0xffffffffu, s_2, off);
     bad = fmaxf(bad, __shfl_xor_sync(0xffffffffu, bad, off));
   }
+  if (eps) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      q += __shfl_xor_sync(0xffffffffu, q, off);
+      pen += __shfl_xor_sync(0xffffffffu, pen, off);
+    }
+  }
   if (lane == 0) {
     red[0][warp] = s_1;
     red[1][warp] = s_2;
     red[2][warp] = bad;
+    dred[0][warp] = q;
+    dred[1][warp] = pen;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     float a = 0.f, b = 0.f, c = 0.f;
+    double qs = 0.0, ps = 0.0;
     for (int k = 0; k < nw; ++k) {
       a += red[0][k];
       b += red[1][k];
       c = fmaxf(c, red[2][k]);
+      qs += dred[0][k];
+      ps += dred[1][k];
     }
     rowstat[3 * row + 0] = (double)a;
     rowstat[3 * row + 1] = (double)b;
     rowstat[3 * row + 2] = (double)c;
+    if (eps) {
+      p.rowq[row] = qs;
+      p.rowpen[row] = ps;
+    }
   }
 }
 
@@ -503,10 +540,23 @@ __global__ void k_factor_loop_init(FactorLoop* st) {
 // With st, thread 0 then applies the stopping rule (the same function as the host loop,
 // on the largest per-row ratio), counts the iteration, stops at max_iter, and inside a
 // graph sets the loop condition.
+// The (1+eps)-aware rule of the rows (on): row i's objective before the step is its slab's
+// tile objective partials (the sampled term, tiles [tstart[i], tstart[i + 1])) plus pen[i],
+// and the rule holds for it when rho^2 q_i / c1 <= theta eps (f_i - q_i / c1) (Lemma 4.2 and
+// the proof of Thm 4.5, with the bounds of the penalised sampled matrix).
+struct RowsEps {
+  int on;
+  const double* q;
+  const double* pen;
+  const double* objpart;
+  const uint32_t* tstart;
+  double rho2_c1, inv_c1, theta_eps;
+};
+
 __global__ void k_rows_reduce(const double* __restrict__ rowstat, int nrow, double* __restrict__ out,
                               FactorLoop* __restrict__ st, double tol, int max_iter, cudaGraphConditionalHandle hnd,
-                              int use_hnd) {
-  double s1 = 0, s2 = 0, bad = 0, mx = 0;
+                              int use_hnd, RowsEps re) {
+  double s1 = 0, s2 = 0, bad = 0, mx = 0, fail = 0;
   for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
     const double a = rowstat[3 * r], b = rowstat[3 * r + 1];
     s1 += a;
@@ -514,29 +564,39 @@ __global__ void k_rows_reduce(const double* __restrict__ rowstat, int nrow, doub
     bad = fmax(bad, rowstat[3 * r + 2]);
     const double rel = b > 0.0 ? sqrt(a / b) : (a > 0.0 ? INFINITY : 0.0);
     mx = fmax(mx, rel);
+    if (re.on) {
+      double f = re.pen[r];
+      for (uint32_t t = re.tstart[r]; t < re.tstart[r + 1]; ++t) f += re.objpart[t];
+      const double q = re.q[r];
+      const bool ok = isfinite(f) && isfinite(q) && re.rho2_c1 * q <= re.theta_eps * fmax(f - q * re.inv_c1, 0.0);
+      if (!ok) fail = 1.0;
+    }
   }
-  __shared__ double red[4][32];
+  __shared__ double red[5][32];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     s1 += __shfl_xor_sync(0xffffffffu, s1, off);
     s2 += __shfl_xor_sync(0xffffffffu, s2, off);
     bad = fmax(bad, __shfl_xor_sync(0xffffffffu, bad, off));
     mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    fail = fmax(fail, __shfl_xor_sync(0xffffffffu, fail, off));
   }
   if ((threadIdx.x & 31) == 0) {
     red[0][threadIdx.x >> 5] = s1;
     red[1][threadIdx.x >> 5] = s2;
     red[2][threadIdx.x >> 5] = bad;
     red[3][threadIdx.x >> 5] = mx;
+    red[4][threadIdx.x >> 5] = fail;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0, b = 0, c = 0, d = 0;
+    double a = 0, b = 0, c = 0, d = 0, e = 0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
       a += red[0][k];
       b += red[1][k];
       c = fmax(c, red[2][k]);
       d = fmax(d, red[3][k]);
+      e = fmax(e, red[4][k]);
     }
     out[0] = a;
     out[1] = b;
@@ -546,8 +606,11 @@ __global__ void k_rows_reduce(const double* __restrict__ rowstat, int nrow, doub
       const double hv[4] = {a, b, c, d};
       for (int k = 0; k < 4; ++k) st->h[k] = hv[k];
       st->it += 1;
-      int status = step_check(hv, tol, &st->prev_step, &st->min_step, &st->min_rel, &st->grow, &st->since_min,
-                              &st->rel, d);
+      int status = STEP_CONTINUE;
+      if (re.on && e == 0.0 && c == 0.0) status = STEP_EPS;  // every row's rule holds
+      if (status == STEP_CONTINUE)
+        status = step_check(hv, tol, &st->prev_step, &st->min_step, &st->min_rel, &st->grow, &st->since_min,
+                            &st->rel, d);
       if (status == STEP_CONTINUE && st->it >= max_iter) status = STEP_MAXITER;
       st->status = status;
       if (use_hnd) cudaGraphSetConditional(hnd, status == STEP_CONTINUE ? 1u : 0u);
@@ -832,6 +895,7 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   nd.add<double>((int64_t)Rn * Rn);                   // C
   nd.add<float>((int64_t)Rn * Rn);                    // Cinv
   nd.add<double>(3 * (int64_t)In + 8);                // row stats, reductions
+  nd.add<double>(2 * (int64_t)In);                    // per-row q and penalty terms (eps rule)
   nd.add<int>(8);
   nd.add<double>(1024);                               // resid partials
   nd.add<FactorLoop>(1);                              // stopping-rule state
@@ -950,6 +1014,7 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   double* C = cv.take<double>((int64_t)Rn * Rn);
   float* Cinv = cv.take<float>((int64_t)Rn * Rn);
   double* rowstat = cv.take<double>(3 * (int64_t)In + 8);
+  double* roweps = cv.take<double>(2 * (int64_t)In);
   double* red = rowstat + 3 * (int64_t)In;
   int* flag = cv.take<int>(8);
   double* rpart = cv.take<double>(1024);
@@ -979,6 +1044,24 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   }
   if (slab) kr_tiles_layout(&tl, cells, cv);
   (void)spare;
+  // The (1+eps)-aware rule (kr_opts.stop_rule 1) for the rows: on the slab path (each row
+  // its own slab, whose tiles give the row's sampled objective) with the fused row kernel
+  // (which forms q and the penalty terms); otherwise the relative-step rule.
+  const bool eps_rows = cfg.stop_rule == 1 && slab && fused_rows;
+  const size_t fr_smem = (size_t)(eps_rows ? 32 : 24) * Rne;
+  RowsEps reps = {};
+  if (eps_rows) {
+    const double se = sqrt(cfg.eps), c1 = 1.0 - se;
+    const double rho = fmax(fabs(1.0 - cfg.alpha * (1.0 - se)), fabs(1.0 - cfg.alpha * (1.0 + se)));
+    reps.on = 1;
+    reps.q = roweps;
+    reps.pen = roweps + In;
+    reps.objpart = tl.objpart;
+    reps.tstart = tl.tstart;
+    reps.rho2_c1 = rho * rho / c1;
+    reps.inv_c1 = 1.0 / c1;
+    reps.theta_eps = cfg.theta * cfg.eps;
+  }
   const size_t gj_smem = (size_t)Rn * 2 * Rn * sizeof(double);
   KR_TRY(kr_smem_attr(ctx, k_gauss_jordan, gj_smem));
   if (fused_rows) {
@@ -1008,7 +1091,11 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     KR_LAUNCH(ctx, k_capacitance64, Rn * Rn, 256, 0, Vw64, AinvU64, Rn, (int)Rne, C);
     KR_LAUNCH(ctx, k_gauss_jordan, 1, 256, gj_smem, C, Rn, Cinv, flag, Cinv64);
     if (gm) KR_TRY(kr_gm_flags(ctx, flag, 1, KR_GM_CAPACITANCE));
-    KR_TRY(kr_smem_attr(ctx, k_factor_rows, (size_t)24 * Rne));
+    if (eps_rows) {
+      rs.rowq = roweps;
+      rs.rowpen = roweps + In;
+    }
+    KR_TRY(kr_smem_attr(ctx, k_factor_rows, fr_smem));
   } else {
     // FP64 chain: A^-1 U (A^-1 applied to each column of G+, batched), V, the capacitance
     // and its inverse
@@ -1050,7 +1137,7 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     int used = 0;
     // sampled part: Gb = K~^T Omega (b~ - K~ z) per row
     if (slab) {
-      KR_TRY(kr_slab_pass(ctx, &sk, &tl, mo.A[0], mo.A[1], Z, false, false, 0, z_zero ? KR_SLAB_ZERO_X : 0));
+      KR_TRY(kr_slab_pass(ctx, &sk, &tl, mo.A[0], mo.A[1], Z, eps_rows, false, 0, z_zero ? KR_SLAB_ZERO_X : 0));
       KR_TRY(kr_tile_reduce(ctx, &tl, nullptr, Gb));
     } else {
       KR_TRY(kr_kron_apply2(ctx, No + 1, dfw_in, dfw_out, Bf, trf, Z, Y, t0, t1));
@@ -1058,7 +1145,7 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
       KR_TRY(kr_kron_apply2(ctx, No + 1, dfw_out, dfw_in, Bf, trb, W, Gb, t0, t1));
     }
     if (fused_rows) {
-      KR_LAUNCH(ctx, k_factor_rows, In, 256, (size_t)24 * Rne, rs, Z, Gb, rowstat);
+      KR_LAUNCH(ctx, k_factor_rows, In, 256, fr_smem, rs, Z, Gb, rowstat);
     } else {
       // grad = w z + G+ (lambda (G+)^T z - w G z) - Gb  (FP64, one block per row)
       KR_LAUNCH(ctx, k_penalty_rows, In, 256, sizeof(double) * Rne, Z, Gn, gp64, Gb, Rn, (int)Rne, cfg.lambda, w,
@@ -1069,7 +1156,7 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
                 (const double*)AinvU64, Rn, (int)Rne, Z, (float)cfg.alpha, rowstat);
     }
     // stopping rule on the largest per-row relative step
-    KR_LAUNCH(ctx, k_rows_reduce, 1, 256, 0, rowstat, In, red, dloop, cfg.tol, cfg.max_iter, hnd, use_hnd);
+    KR_LAUNCH(ctx, k_rows_reduce, 1, 256, 0, rowstat, In, red, dloop, cfg.tol, cfg.max_iter, hnd, use_hnd, reps);
     return KR_OK;
   };
   auto read_state = [&]() -> kr_status {
@@ -1113,7 +1200,7 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
   }
   const int it = hl->it;
   const double rel = hl->rel;
-  const int converged = hl->status == STEP_CONVERGED ? 1 : (hl->status == STEP_FLOOR ? 2 : 0);
+  const int converged = hl->status == STEP_CONVERGED ? 1 : hl->status == STEP_FLOOR ? 2 : hl->status == STEP_EPS ? 3 : 0;
   kr_status st = KR_OK;
   if (hl->status == STEP_NONFINITE)
     st = kr_fail(ctx, KR_ENONFINITE, "factor step %d: iterate became non-finite at iteration %d", n, it);

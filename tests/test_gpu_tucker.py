@@ -75,6 +75,55 @@ def test_factor_update_matches_oracle_rows(I, R, lam):
             np.testing.assert_array_equal(host(A_gpu[m]), np.asarray(As[m], np.float32))
 
 
+@pytest.mark.parametrize("n", [0, 1])
+def test_factor_update_eps_rule_matches_oracle(n):
+    """kr_opts.stop_rule 1 in the factor step (slab path, two other modes): the rows' (1+eps)-aware
+    rule on the device (q = g^T M+ g from the row kernel, the row objective from its slab's
+    tile partials plus the penalty terms) ends the loop once every row's rule holds, which is
+    where the oracle's row rule has stopped its slowest row, within one iteration; every row is
+    then a (1+eps)-approximate ridge solution on its sample, the guarantee the rule certifies."""
+    I, R, lam = [24, 20, 18], [3, 3, 2], 1e-3
+    X, As, G = _state(I, R, seed=3)
+    eps, seed, cid = 0.1, 17, 40
+    N = len(I)
+    A_gpu = [dev(A) for A in As]
+    rep = kr.tucker_factor_update(dev(X), A_gpu, dev(G), n, lam, eps=eps, seed=seed, call_id=cid, tol=1e-7,
+                                  max_iter=500, stop_rule=kr.STOP_EPS)
+    assert rep["stop"] == 3, rep
+    others = [m for m in range(N) if m != n]
+    tab = kr.kron_leverage([A_gpu[m] for m in others])
+    cdfs = [c.cpu().numpy() for c in tab["cdf"]]
+    probs = [p.cpu().numpy() for p in tab["prob"]]
+    As_o = [As[m] for m in others]
+    Gn = tk.unfold(G, n)
+    w = tk.penalty_weight(As_o, eps)
+    P = tk.WoodburyPreconditioner(As_o, Gn, lam, w)
+    Xn = tk.unfold(X, n)
+    s = rep["s"]
+    got = host(A_gpu[n])
+    its = []
+    worst = 0.0
+    for i in range(I[n]):
+        smp = tk.row_sample(As_o, s, seed, cid, i, cdfs=cdfs, probs=probs)
+        b_s = Xn[i][smp.keys]
+        _, _, it = tk.row_richardson(As_o, Gn, b_s, smp, lam, eps, w, P=P, max_iter=500, stop="eps")
+        its.append(it)
+        rows = ko.sampled_rows(As_o, smp.keys)
+        Y = rows @ Gn.T
+        y = tk.row_ridge_on_sample(As_o, Gn, b_s, smp, lam)
+
+        def f(v):
+            r = Y @ v - b_s
+            return float(np.sum(smp.omega * r * r) + lam * v @ v)
+
+        ratio = f(got[i]) / f(y)
+        worst = max(worst, ratio)
+        assert ratio <= 1 + eps, (i, ratio)
+    print("mode %d: device stopped at %d, oracle rows at %d..%d; worst f(a)/f(y*) %.6f" % (
+        n, rep["iters"], min(its), max(its), worst))
+    assert abs(rep["iters"] - max(its)) <= 1
+
+
 def test_tucker_sweeps_reach_exact_als_quality():
     I, R = [32, 28, 24], [3, 3, 3]
     X, As, G = _state(I, R, seed=7)
