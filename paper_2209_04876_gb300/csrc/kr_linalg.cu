@@ -110,27 +110,19 @@ __device__ __forceinline__ double rsqrt_fp64(double d) {
   return y;
 }
 
-// One block per mode: Cholesky G = L L^T (FP64), L^-1, and (A^T A)^-1 in FP32.
-// L^-1 by block doubling: with L padded to RP = 2^k rows by the identity, every level
-// turns inverted diagonal blocks of size bs into inverted blocks of size 2 bs through
-// [A 0; C D]^-1 = [A^-1 0; -D^-1 C A^-1, D^-1] (two bs x bs products per level).
+// One block per mode: the Cholesky factor G = L L^T in FP64, written (lower triangle, R x R)
+// over the mode's Gram partials (mp.part, no longer needed once the Gram matrix is formed),
+// and the pivot flag. L^-1 and (A^T A)^-1 follow in k_trinv and k_ginv, spread over blocks.
 __global__ void k_cholesky(ModePtrs mp) {
   const int n = blockIdx.x;
   const int R = mp.R[n];
-  int RP = 1;
-  while (RP < R) RP <<= 1;
   extern __shared__ double sm[];
-  double* L = sm;                  // RP x LD
-  double* X = sm + MAXR * LD;      // RP x LD (L^-1)
-  double* S = sm + 2 * MAXR * LD;  // RP x LD (scratch products)
+  double* L = sm;  // R x LD
   __shared__ int bad;
   __shared__ double maxdiag;
   __shared__ double pinv;
   const int tid = threadIdx.x;
-  for (int e = tid; e < RP * RP; e += blockDim.x) {
-    const int i = e / RP, j = e % RP;
-    L[i * LD + j] = (i < R && j < R) ? mp.gram[n][i * R + j] : (i == j ? 1.0 : 0.0);
-  }
+  for (int e = tid; e < R * R; e += blockDim.x) L[(e / R) * LD + e % R] = mp.gram[n][e];
   if (tid == 0) {
     bad = 0;
     double md = 0.0;
@@ -161,57 +153,57 @@ __global__ void k_cholesky(ModePtrs mp) {
     }
     __syncthreads();
   }
-  // L^-1: diagonal blocks of size 1, then doubling
-  for (int e = tid; e < RP * RP; e += blockDim.x) {
-    const int i = e / RP, j = e % RP;
-    X[i * LD + j] = (i == j) ? 1.0 / L[i * LD + i] : 0.0;
-  }
-  __syncthreads();
-  for (int bs = 1; bs < RP; bs <<= 1) {
-    const int per = bs * bs, npair = RP / (2 * bs);
-    // S[B, A] = L[B, A] X[A, A]
-    for (int e = tid; e < npair * per; e += blockDim.x) {
-      const int pr = e / per, rc = e - pr * per, r = rc / bs, c = rc - r * bs;
-      const int a0 = pr * 2 * bs, b0 = a0 + bs;
-      double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
-      int t = c;  // X[A, A] is lower triangular: rows t >= c
-      for (; t + 3 < bs; t += 4) {
-        p0 = fma(L[(b0 + r) * LD + a0 + t], X[(a0 + t) * LD + a0 + c], p0);
-        p1 = fma(L[(b0 + r) * LD + a0 + t + 1], X[(a0 + t + 1) * LD + a0 + c], p1);
-        p2 = fma(L[(b0 + r) * LD + a0 + t + 2], X[(a0 + t + 2) * LD + a0 + c], p2);
-        p3 = fma(L[(b0 + r) * LD + a0 + t + 3], X[(a0 + t + 3) * LD + a0 + c], p3);
-      }
-      for (; t < bs; ++t) p0 = fma(L[(b0 + r) * LD + a0 + t], X[(a0 + t) * LD + a0 + c], p0);
-      S[(b0 + r) * LD + a0 + c] = (p0 + p1) + (p2 + p3);
-    }
-    __syncthreads();
-    // X[B, A] = -X[B, B] S[B, A]
-    for (int e = tid; e < npair * per; e += blockDim.x) {
-      const int pr = e / per, rc = e - pr * per, r = rc / bs, c = rc - r * bs;
-      const int a0 = pr * 2 * bs, b0 = a0 + bs;
-      double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
-      int t = 0;  // X[B, B] is lower triangular: columns t <= r
-      for (; t + 3 <= r; t += 4) {
-        p0 = fma(X[(b0 + r) * LD + b0 + t], S[(b0 + t) * LD + a0 + c], p0);
-        p1 = fma(X[(b0 + r) * LD + b0 + t + 1], S[(b0 + t + 1) * LD + a0 + c], p1);
-        p2 = fma(X[(b0 + r) * LD + b0 + t + 2], S[(b0 + t + 2) * LD + a0 + c], p2);
-        p3 = fma(X[(b0 + r) * LD + b0 + t + 3], S[(b0 + t + 3) * LD + a0 + c], p3);
-      }
-      for (; t <= r; ++t) p0 = fma(X[(b0 + r) * LD + b0 + t], S[(b0 + t) * LD + a0 + c], p0);
-      X[(b0 + r) * LD + a0 + c] = -((p0 + p1) + (p2 + p3));
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < R * R; e += blockDim.x) mp.linv[n][e] = X[(e / R) * LD + (e % R)];
-  // (A^T A)^-1 = X^T X in FP32 (a preconditioner only needs a spectral approximation).
+  double* Lout = mp.part[n];
   for (int e = tid; e < R * R; e += blockDim.x) {
-    int i = e / R, j = e % R;
-    int k0 = i > j ? i : j;
-    float acc = 0.f;
-    for (int k = k0; k < R; ++k) acc = fmaf((float)X[k * LD + i], (float)X[k * LD + j], acc);
-    mp.ginv[n][e] = acc;
+    const int i = e / R, j = e % R;
+    Lout[e] = j <= i ? L[i * LD + j] : 0.0;
   }
   if (tid == 0) mp.flags[n] = bad;
+}
+
+// Column j of L^-1 (block (j, mode); one warp), by forward substitution in FP64:
+// x_j = 1 / L_jj, x_i = -(sum_{j <= k < i} L_ik x_k) / L_ii for i > j, 0 above the diagonal.
+__global__ void __launch_bounds__(32) k_trinv(ModePtrs mp) {
+  const int n = blockIdx.y, j = blockIdx.x, R = mp.R[n];
+  if (j >= R) return;
+  __shared__ double Ls[MAXR * LD];
+  __shared__ double x[MAXR], rd[MAXR];
+  const double* L = mp.part[n];
+  const int lane = threadIdx.x;
+  for (int e = lane; e < R * R; e += 32) {
+    const int i = e / R, k = e % R;
+    if (i >= j && k >= j && k <= i) Ls[i * LD + k] = L[e];
+  }
+  for (int i = lane; i < R; i += 32) {
+    rd[i] = i >= j ? 1.0 / L[i * R + i] : 0.0;
+    x[i] = 0.0;
+  }
+  __syncwarp();
+  if (lane == 0) x[j] = rd[j];
+  __syncwarp();
+  for (int i = j + 1; i < R; ++i) {
+    double acc = 0.0;
+    for (int k = j + lane; k < i; k += 32) acc = fma(Ls[i * LD + k], x[k], acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) x[i] = -acc * rd[i];
+    __syncwarp();
+  }
+  for (int i = lane; i < R; i += 32) mp.linv[n][i * R + j] = x[i];
+}
+
+// Row i of (A^T A)^-1 = X^T X with X = L^-1, in FP32 (a preconditioner only needs a
+// spectral approximation): block (i, mode).
+__global__ void __launch_bounds__(64) k_ginv(ModePtrs mp) {
+  const int n = blockIdx.y, i = blockIdx.x, R = mp.R[n];
+  if (i >= R) return;
+  const double* X = mp.linv[n];
+  for (int j = threadIdx.x; j < R; j += blockDim.x) {
+    const int k0 = i > j ? i : j;
+    float acc = 0.f;
+    for (int k = k0; k < R; ++k) acc = fmaf((float)X[k * R + i], (float)X[k * R + j], acc);
+    mp.ginv[n][i * R + j] = acc;
+  }
 }
 
 // l_i = ||L^-1 a_i||^2 in FP64: LEV_ROWS rows per block, one warp per row, a lane per
@@ -566,7 +558,7 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
   mp.flags = t.flags = cv.take<int>(KR_MAX_MODES);
   if (cv.off > cv.cap) return kr_fail(ctx, KR_ENOMEM, "tables: workspace too small");
 
-  const size_t chol_smem = 3 * MAXR * LD * sizeof(double);
+  const size_t chol_smem = (size_t)MAXR * LD * sizeof(double);
   const size_t lev_smem = (MAXR * LD + LEV_ROWS * LD) * sizeof(double);
   KR_TRY(kr_smem_attr(ctx, k_cholesky, chol_smem));
   KR_TRY(kr_smem_attr(ctx, k_leverage, lev_smem));
@@ -576,6 +568,8 @@ kr_status kr_tables_build(kr_ctx* ctx, const Modes& m, bool want_eig, Carve& cv,
   for (int n = 0; n < m.N; ++n) maxR = m.R[n] > maxR ? m.R[n] : maxR;
   KR_LAUNCH(ctx, k_gram_reduce, dim3((maxR * maxR + 255) / 256, m.N), 256, 0, mp);
   KR_LAUNCH(ctx, k_cholesky, m.N, 256, chol_smem, mp);
+  KR_LAUNCH(ctx, k_trinv, dim3(maxR, m.N), 32, 0, mp);
+  KR_LAUNCH(ctx, k_ginv, dim3(maxR, m.N), 64, 0, mp);
   dim3 gl((maxI + LEV_ROWS - 1) / LEV_ROWS, m.N);
   if (ctx->jl_k > 0) {
     const int k = ctx->jl_k;

@@ -1894,7 +1894,13 @@ kr_status kr_solve_device(kr_ctx* ctx, const Modes& m, const float* b, const Sol
     KR_TRY(kr_gm_section(ctx, [&]() -> kr_status {
       cudaGraphConditionalHandle h1 = 0;
       int64_t pb = 0;
-      KR_TRY(kr_gm_handle(ctx, 1, &h1));
+      KR_TRY(kr_gm_handle(ctx, 0, &h1));
+      // the first step from x = 0 ahead of the node, as the host loop runs it; its check
+      // sets the node's condition
+      bf.x_zero = true;
+      const kr_status s1 = one_step(h1, 1);
+      bf.x_zero = false;
+      KR_TRY(s1);
       KR_TRY(kr_capture_while(ctx, h1, one_step, &pb));
       return kr_gm_status(ctx, &bf.rich->status, &bf.rich->it, pb, -1, &slot1);
     }));

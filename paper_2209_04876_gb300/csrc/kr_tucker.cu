@@ -1165,11 +1165,16 @@ kr_status kr_factor_step(kr_ctx* ctx, const Modes& m, const float* X, const floa
     return KR_OK;
   };
   if (gm) {
-    // every iteration inside the WHILE node (it runs at least once, as the host loop does),
-    // then the new factor rows a_i = (G+)^T z_i
+    // the first iteration (z = 0) ahead of the WHILE node, as the host loop runs it, its check
+    // setting the node's condition; the rest inside the node; then the new factor rows
+    // a_i = (G+)^T z_i
     cudaGraphConditionalHandle h = 0;
     int64_t pb = 0;
-    KR_TRY(kr_gm_handle(ctx, 1, &h));
+    KR_TRY(kr_gm_handle(ctx, 0, &h));
+    z_zero = true;
+    const kr_status s1 = one_iter(h, 1);
+    z_zero = false;
+    KR_TRY(s1);
     KR_TRY(kr_capture_while(ctx, h, one_iter, &pb));
     KR_TRY(kr_gm_status(ctx, &dloop->status, &dloop->it, pb, -1, nullptr));
     KR_LAUNCH(ctx, k_penalty_rows, In, 256, sizeof(double) * Rne, Z, Gn, gp64, Gb, Rn, (int)Rne, cfg.lambda, w, Gr,
@@ -1383,7 +1388,8 @@ kr_status graph_sweeps(kr_ctx* ctx, const Modes& m, const float* X, float* G, co
     if (g.base_slot[(size_t)i] >= 0) superseded[(size_t)g.base_slot[(size_t)i]] = 1;
   for (int i = 0; i < nl; ++i) {
     const int base = g.base_slot[(size_t)i];
-    const int runs = stat[2 * i + 1] - (base >= 0 ? stat[2 * base + 1] : 0);
+    // a first loop's first iteration ran ahead of its node; a resumed loop's all ran inside
+    const int runs = stat[2 * i + 1] - (base >= 0 ? stat[2 * base + 1] : 1);
     ctx->launches += g.body_launches[(size_t)i] * (runs > 0 ? runs : 0);
     if (superseded[(size_t)i]) continue;
     *total_iters += stat[2 * i + 1];
