@@ -26,6 +26,39 @@ def test_unfolding_identity():
         np.testing.assert_allclose(tk.fold(tk.unfold(X, n), n, X.shape), X)
 
 
+def test_reconstruct_brute_force_and_kron():
+    """X = G x_1 A(1) x_2 A(2) x_3 A(3), entry by entry as the quadruple sum, and as
+    (A(1) (x) A(2) (x) A(3)) vec G with np.kron (C-order vec)."""
+    As, G = _setup(2, I=(4, 3, 5), R=(2, 3, 2))
+    X = tk.reconstruct(G, As)
+    for i in range(4):
+        for j in range(3):
+            for k in range(5):
+                v = sum(G[a, b, c] * As[0][i, a] * As[1][j, b] * As[2][k, c]
+                        for a in range(2) for b in range(3) for c in range(2))
+                assert abs(X[i, j, k] - v) <= 1e-12 * (1 + abs(v))
+    K = np.kron(np.kron(As[0], As[1]), As[2])
+    np.testing.assert_allclose(X.reshape(-1), K @ G.reshape(-1), rtol=1e-12, atol=1e-12)
+
+
+def test_rre_and_tucker_loss_closed_forms():
+    """RRE = ||X^ - X||^2 / ||X||^2 and the regularised loss ||X^ - X||^2 + lam (||G||^2 +
+    sum ||A(n)||^2), on cases whose values are known: an exact decomposition (RRE 0), X twice
+    the reconstruction (RRE 1/4), a zero core (RRE 1), and a rank-one 2 x 2 example by hand."""
+    As, G = _setup(3)
+    Xh = tk.reconstruct(G, As)
+    assert tk.rre(Xh, G, As) == pytest.approx(0.0, abs=1e-28)
+    assert tk.rre(2.0 * Xh, G, As) == pytest.approx(0.25, rel=1e-12)
+    assert tk.rre(Xh, np.zeros_like(G), As) == pytest.approx(1.0, rel=1e-12)
+    # X = [[1, 2], [3, 4]], G = [[2]], a = [1, 1], b = [1, 2]: X^ = 2 a b^T = [[2, 4], [2, 4]],
+    # X^ - X = [[1, 2], [-1, 0]]: ||.||^2 = 6, ||X||^2 = 30; ||G||^2 + ||a||^2 + ||b||^2 = 4 + 2 + 5
+    X = np.array([[1.0, 2.0], [3.0, 4.0]])
+    G1 = np.array([[2.0]])
+    A1 = [np.array([[1.0], [1.0]]), np.array([[1.0], [2.0]])]
+    assert tk.rre(X, G1, A1) == pytest.approx(6.0 / 30.0, rel=1e-14)
+    assert tk.tucker_loss(X, G1, A1, 0.5) == pytest.approx(6.0 + 0.5 * 11.0, rel=1e-14)
+
+
 @pytest.mark.parametrize("lam", [0.0, 0.05])
 def test_woodbury_matches_dense_inverse(lam):
     """The Woodbury form with the standard minus sign equals inv(M) (App. C)."""
