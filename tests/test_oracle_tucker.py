@@ -234,15 +234,17 @@ def test_factor_row_richardson_rate_with_large_penalty_needs_exact_eigenvectors(
     assert it_pert > 5 * it_exact
 
 
-def test_factor_row_eps_stopping_rule():
+@pytest.mark.parametrize("I,R,n", [((9, 8, 7), (3, 3, 2), 1), ((7, 6, 5, 4), (2, 2, 2, 2), 0)])
+def test_factor_row_eps_stopping_rule(I, R, n):
     """The eps-aware rule on Alg. 3's penalised system: the sample's M^-1 M~ spectrum lies in
     [1 - sqrt(eps), 1 + sqrt(eps)], the excess bound holds after every step, and the rule
     stops after a handful of steps with a row that is still a (1+eps) solution of the
-    y-space ridge on the same sample (Lemma 5.2)."""
-    As, G = _setup(5, I=(9, 8, 7), R=(3, 3, 2))
-    X = tk.reconstruct(G, As) + 0.05 * np.random.default_rng(6).standard_normal((9, 8, 7))
-    lam, eps, n = 0.01, 0.1, 1
-    others = [As[m] for m in range(3) if m != n]
+    y-space ridge on the same sample (Lemma 5.2); with two and with three other modes."""
+    As, G = _setup(5, I=I, R=R)
+    X = tk.reconstruct(G, As) + 0.05 * np.random.default_rng(6).standard_normal(I)
+    lam, eps = 0.01, 0.1
+    N = len(I)
+    others = [As[m] for m in range(N) if m != n]
     Gn = tk.unfold(G, n)
     Gp = np.linalg.pinv(Gn)
     w = tk.penalty_weight(others, eps)
@@ -251,7 +253,8 @@ def test_factor_row_eps_stopping_rule():
     P = tk.WoodburyPreconditioner(others, Gn, lam, w)
     rho2, c1 = ko.eps_stop_bound(eps)
     for i in range(3):
-        smp = tk.row_sample(others, ko.sample_count(6, eps), seed=7, call_id=9, row=i)
+        smp = tk.row_sample(others, ko.sample_count(int(np.prod([A.shape[1] for A in others])), eps), seed=7,
+                            call_id=9, row=i)
         b_s = Xn[i][smp.keys]
         rows = ko.sampled_rows(others, smp.keys)
         Mt = M - ko.kron_dense(others).T @ ko.kron_dense(others) + rows.T @ (smp.omega[:, None] * rows)
