@@ -146,7 +146,10 @@ typedef struct {
  * (cudaStream_t, may be NULL for the legacy default stream). The context owns its
  * workspace. workspace_bytes > 0 reserves that much device memory now (KR_ENOMEM if it
  * cannot); 0 reserves nothing. Either way the workspace grows on demand when a call
- * needs more, and kr_destroy frees it. */
+ * needs more, and kr_destroy frees it. The context also creates a non-blocking stream of
+ * its own (loop bodies captured into graphs are recorded there) and 1 KB of device state
+ * for the asynchronous solves, so that a solve captured into a caller's graph allocates
+ * nothing (KR_ENOMEM if either fails). */
 KR_API kr_status kr_create(kr_ctx** ctx, void* cuda_stream, size_t workspace_bytes);
 KR_API void kr_destroy(kr_ctx* ctx);
 KR_API kr_status kr_set_stream(kr_ctx* ctx, void* cuda_stream);
